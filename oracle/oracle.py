@@ -1,0 +1,306 @@
+"""ctypes binding of the plain C oracle (``ecmg_oracle.c``).
+
+TEST INFRASTRUCTURE: used by the tests, by ``__graft_entry__.smoke()`` and by the CPU-baseline
+leg of ``bench.py`` only. It shares no code with the CUDA path; it receives the same seeded
+inputs (from ``paper_1506_02983_gb300.inputs``, which holds none of the method's arithmetic)
+and computes everything itself, in FP64, on one host core.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ecmg_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+DIRICHLET, ROBIN = 0, 1
+F_NODAL, F_LOAD = 0, 1
+EXP_SERENDIPITY20, EXP_LAGRANGE27 = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_build/liboracle.so``.
+
+    ``-ffp-contract=off`` keeps x86 and Arm hosts bit-identical (no fused multiply-add).
+    """
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [("n0", C.c_int32 * 3), ("levels", C.c_int32),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("face_bc", C.c_int32 * 6), ("alpha", C.c_double * 6),
+                ("beta", C.c_void_p), ("f", C.c_void_p), ("gD", C.c_void_p),
+                ("gR", C.c_void_p), ("f_mode", C.c_int32)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iters", C.c_int32 * 16), ("rel_res", C.c_double * 16),
+                ("rhs_norm", C.c_double * 16), ("status", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        D, I64, I32 = C.c_double, C.c_int64, C.c_int32
+        P = C.c_void_p
+        _lib.or_assemble_csr.restype = I64
+        _lib.or_assemble_csr.argtypes = [P, P, P, P, P, P, P, P]
+        _lib.or_element_matrix.argtypes = [D, D, D, P]
+        _lib.or_element_mass.argtypes = [D, D, D, P]
+        _lib.or_face_mass.argtypes = [D, D, P]
+        _lib.or_dirichlet_mask.argtypes = [P, P, P]
+        _lib.or_load_nodal.argtypes = [P, P, P, P, P, P]
+        _lib.or_csr_matvec.argtypes = [I64, P, P, P, P, P]
+        _lib.or_coarsen_beta.argtypes = [P, P, P]
+        _lib.or_inject.argtypes = [P, P, P]
+        _lib.or_restrict_load.argtypes = [P, P, P]
+        _lib.or_jcg.restype = C.c_int
+        _lib.or_jcg.argtypes = [I64, P, P, P, P, P, P, P, D, I32, P, P, P]
+        _lib.or_dsolve_banded.restype = C.c_int
+        _lib.or_dsolve_banded.argtypes = [P, I64, P, P, P, P, P, P]
+        _lib.or_serendipity.argtypes = [D, D, D, P]
+        _lib.or_serendipity_nodes.argtypes = [P]
+        _lib.or_exp_finite.argtypes = [P, P, P, P]
+        _lib.or_exp_finite27.argtypes = [P, P, P, P]
+        _lib.or_exp_true.argtypes = [P, P, P, P]
+        _lib.or_ecmg.restype = C.c_int
+        _lib.or_ecmg.argtypes = [C.POINTER(_Problem), D, I32, I32, P, P, P, C.POINTER(_Stats)]
+        _lib.or_norms.argtypes = [I64, P, P, P, P]
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _i32(v):
+    return np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+
+
+def _f64(v):
+    return np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+
+
+def num_nodes(n):
+    return (n[0] + 1) * (n[1] + 1) * (n[2] + 1)
+
+
+# ---- discretisation --------------------------------------------------------------------
+def element_matrix(hx, hy, hz):
+    K = np.zeros(64)
+    lib().or_element_matrix(hx, hy, hz, _p(K))
+    return K.reshape(8, 8)
+
+
+def element_mass(hx, hy, hz):
+    M = np.zeros(64)
+    lib().or_element_mass(hx, hy, hz, _p(M))
+    return M.reshape(8, 8)
+
+
+def face_mass(ha, hb):
+    M = np.zeros(16)
+    lib().or_face_mass(ha, hb, _p(M))
+    return M.reshape(4, 4)
+
+
+def dirichlet_mask(n, face_bc):
+    """1 = free node, 0 = Dirichlet node (flat, x fastest)."""
+    m = np.zeros(num_nodes(n), dtype=np.uint8)
+    nn, bc = _i32(n), _i32(face_bc)
+    lib().or_dirichlet_mask(_p(nn), _p(bc), _p(m))
+    return m
+
+
+@dataclass
+class CSR:
+    N: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    def matvec(self, x):
+        x = _f64(x)
+        y = np.zeros(self.N)
+        lib().or_csr_matvec(self.N, _p(self.rowptr), _p(self.col), _p(self.val), _p(x), _p(y))
+        return y
+
+    def dense(self):
+        A = np.zeros((self.N, self.N))
+        for r in range(self.N):
+            s, e = self.rowptr[r], self.rowptr[r + 1]
+            A[r, self.col[s:e]] = self.val[s:e]
+        return A
+
+
+def assemble(n, h, beta, face_bc, alpha):
+    N = num_nodes(n)
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    col = np.zeros(27 * N, dtype=np.int64)
+    val = np.zeros(27 * N)
+    beta = _f64(beta)
+    nn, hh, bc, al = _i32(n), _f64(h), _i32(face_bc), _f64(alpha)
+    nnz = lib().or_assemble_csr(_p(nn), _p(hh), _p(beta), _p(bc), _p(al), _p(rowptr),
+                                _p(col), _p(val))
+    if nnz < 0:
+        raise MemoryError("oracle assembly failed")
+    return CSR(N, rowptr, col[:nnz].copy(), val[:nnz].copy())
+
+
+def load_nodal(n, h, f, face_bc, gR=None):
+    b = np.zeros(num_nodes(n))
+    f = _f64(f)
+    gR = None if gR is None else _f64(gR)
+    nn, hh, bc = _i32(n), _f64(h), _i32(face_bc)
+    lib().or_load_nodal(_p(nn), _p(hh), _p(f), _p(bc), _p(gR), _p(b))
+    return b
+
+
+# ---- level transfer ---------------------------------------------------------------------
+def coarsen_beta(nc, beta_fine):
+    out = np.zeros(int(np.prod(nc)))
+    bf, nn = _f64(beta_fine), _i32(nc)
+    lib().or_coarsen_beta(_p(nn), _p(bf), _p(out))
+    return out
+
+
+def inject(nc, v_fine):
+    out = np.zeros(num_nodes(nc))
+    vf, nn = _f64(v_fine), _i32(nc)
+    lib().or_inject(_p(nn), _p(vf), _p(out))
+    return out
+
+
+def restrict_load(nc, b_fine):
+    out = np.zeros(num_nodes(nc))
+    bf, nn = _f64(b_fine), _i32(nc)
+    lib().or_restrict_load(_p(nn), _p(bf), _p(out))
+    return out
+
+
+# ---- solvers ----------------------------------------------------------------------------
+def jcg(A: CSR, mask, b, gext, x0, rtol, max_iters=100000):
+    x = _f64(x0).copy()
+    it = C.c_int32()
+    rr = C.c_double()
+    fh = C.c_double()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    b = _f64(b)
+    g = _f64(gext)
+    st = lib().or_jcg(A.N, _p(A.rowptr), _p(A.col), _p(A.val), _p(m), _p(b), _p(g), _p(x),
+                      rtol, max_iters, C.byref(it), C.byref(rr), C.byref(fh))
+    return x, dict(status=st, iters=it.value, rel_res=rr.value, rhs_norm=fh.value)
+
+
+def dsolve(n, A: CSR, mask, b, x0):
+    x = _f64(x0).copy()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    b, nn = _f64(b), _i32(n)
+    st = lib().or_dsolve_banded(_p(nn), A.N, _p(A.rowptr), _p(A.col), _p(A.val), _p(m),
+                                _p(b), _p(x))
+    return x, st
+
+
+# ---- extrapolation ----------------------------------------------------------------------
+def serendipity(xi, eta, zeta):
+    N = np.zeros(20)
+    lib().or_serendipity(xi, eta, zeta, _p(N))
+    return N
+
+
+def serendipity_nodes():
+    a = np.zeros(60, dtype=np.int32)
+    lib().or_serendipity_nodes(_p(a))
+    return a.reshape(20, 3)
+
+
+def exp_finite(n, U1, U0):
+    W = np.zeros(num_nodes(n))
+    U1 = _f64(U1)
+    U0, nn = _f64(U0), _i32(n)
+    lib().or_exp_finite(_p(nn), _p(U1), _p(U0), _p(W))
+    return W
+
+
+def exp_finite27(n, U1, U0):
+    W = np.zeros(num_nodes(n))
+    U1 = _f64(U1)
+    U0, nn = _f64(U0), _i32(n)
+    lib().or_exp_finite27(_p(nn), _p(U1), _p(U0), _p(W))
+    return W
+
+
+def exp_true(n, U1, U0):
+    Ut = np.zeros(num_nodes(n))
+    U1 = _f64(U1)
+    U0, nn = _f64(U0), _i32(n)
+    lib().or_exp_true(_p(nn), _p(U1), _p(U0), _p(Ut))
+    return Ut
+
+
+def norms(a, b=None):
+    a = _f64(a)
+    b = None if b is None else _f64(b)
+    mx = C.c_double()
+    rms = C.c_double()
+    lib().or_norms(a.size, _p(a), _p(b), C.byref(mx), C.byref(rms))
+    return mx.value, rms.value
+
+
+# ---- the whole method -------------------------------------------------------------------
+def ecmg(prob, rtol, max_iters=100000, exp_variant=EXP_SERENDIPITY20):
+    """Run Alg. 4 on a problem dict (see ``paper_1506_02983_gb300.inputs``).
+
+    Returns (levels, stats): levels[l] = dict(n=..., U=..., W=..., Ut=...) with nodal arrays
+    shaped (nz+1, ny+1, nx+1); stats has per-level iters, rel_res, rhs_norm and status.
+    """
+    L = int(prob["levels"])
+    n0 = [int(v) for v in prob["n0"]]
+    sizes = [num_nodes([v << l for v in n0]) for l in range(L)]
+    tot = sum(sizes)
+    U = np.zeros(tot)
+    W = np.zeros(tot)
+    Ut = np.zeros(tot)
+    beta = _f64(prob["beta"]).ravel()
+    f = _f64(prob["f"]).ravel()
+    gD = None if prob.get("gD") is None else _f64(prob["gD"]).ravel()
+    gR = None if prob.get("gR") is None else _f64(prob["gR"]).ravel()
+    P = _Problem()
+    P.n0[:] = n0
+    P.levels = L
+    P.lo[:] = list(prob["lo"])
+    P.hi[:] = list(prob["hi"])
+    P.face_bc[:] = list(prob["face_bc"])
+    P.alpha[:] = list(prob["alpha"])
+    P.beta, P.f, P.gD, P.gR = _p(beta), _p(f), _p(gD), _p(gR)
+    P.f_mode = int(prob.get("f_mode", F_NODAL))
+    S = _Stats()
+    lib().or_ecmg(C.byref(P), rtol, max_iters, int(exp_variant), _p(U), _p(W), _p(Ut),
+                  C.byref(S))
+    out = []
+    off = 0
+    for l in range(L):
+        n = [v << l for v in n0]
+        shp = (n[2] + 1, n[1] + 1, n[0] + 1)
+        sl = slice(off, off + sizes[l])
+        out.append(dict(n=n, U=U[sl].reshape(shp), W=W[sl].reshape(shp), Ut=Ut[sl].reshape(shp)))
+        off += sizes[l]
+    stats = dict(iters=list(S.iters[:L]), rel_res=list(S.rel_res[:L]),
+                 rhs_norm=list(S.rhs_norm[:L]), status=S.status)
+    return out, stats

@@ -1,0 +1,177 @@
+"""Seeded synthetic problem generators for eq. (bvp): -div(beta grad u) = f on a box.
+
+This module holds none of the method's arithmetic: it only evaluates problem data
+(coefficient beta per element, nodal f, Dirichlet data g_D, Robin data g_R, boundary types)
+for manufactured solutions and for seeded random problems. Both the CUDA path and the CPU
+oracle receive exactly these arrays.
+
+Every problem is a dict with keys
+    n0 (3 ints, coarsest elements per axis), levels, lo, hi (box corners),
+    face_bc (6 ints, faces x-,x+,y-,y+,z-,z+; 0 Dirichlet, 1 Robin), alpha (6 floats),
+    beta  (finest elements, shape (nz, ny, nx), float64),
+    f     (finest nodes, shape (nz+1, ny+1, nx+1)),
+    gD, gR (finest nodes or None), f_mode (0 nodal f, 1 assembled load),
+    u_exact (finest nodes or None), rtol (relative-residual tolerance of the workload).
+Arrays are C-ordered, so the flat index runs x fastest.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+DIRICHLET, ROBIN = 0, 1
+PI = np.pi
+
+
+def hat_integrals_1d(func, n, lo, hi, q=6):
+    """I[i] = integral of func(t) * phi_i(t) over [lo, hi] for the piecewise-linear hat
+    functions phi_i of a uniform n-interval grid, by q-point Gauss-Legendre per interval.
+    With q = 6 the result is exact to rounding for the smooth data used here."""
+    g, w = np.polynomial.legendre.leggauss(q)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    h = (hi - lo) / n
+    t = lo + (np.arange(n)[:, None] + g[None, :]) * h          # (n, q) points
+    ft = func(t) * w[None, :] * h
+    out = np.zeros(n + 1)
+    out[:-1] += (ft * (1.0 - g)[None, :]).sum(axis=1)
+    out[1:] += (ft * g[None, :]).sum(axis=1)
+    return out
+
+
+def separable_load(n, lo, hi, scale, fx, fy, fz):
+    """Load functional f(phi_i) (Sec. 2) for a separable right-hand side
+    f = scale * fx(x) fy(y) fz(z), shape (nz+1, ny+1, nx+1)."""
+    ix = hat_integrals_1d(fx, n[0], lo[0], hi[0])
+    iy = hat_integrals_1d(fy, n[1], lo[1], hi[1])
+    iz = hat_integrals_1d(fz, n[2], lo[2], hi[2])
+    return scale * iz[:, None, None] * iy[None, :, None] * ix[None, None, :]
+
+
+def finest(n0, levels):
+    return [int(v) << (levels - 1) for v in n0]
+
+
+def _axes(n, lo, hi, centres=False):
+    """Coordinates along x, y, z shaped for broadcasting to (z, y, x)."""
+    out = []
+    for a in range(3):
+        if centres:
+            t = lo[a] + (np.arange(n[a]) + 0.5) * (hi[a] - lo[a]) / n[a]
+        else:
+            t = lo[a] + np.arange(n[a] + 1) * (hi[a] - lo[a]) / n[a]
+        shape = [1, 1, 1]
+        shape[2 - a] = t.size
+        out.append(t.reshape(shape))
+    return out
+
+
+def _base(n0, levels, lo, hi, face_bc, alpha, rtol):
+    return dict(n0=[int(v) for v in n0], levels=int(levels), lo=[float(v) for v in lo],
+                hi=[float(v) for v in hi], face_bc=[int(v) for v in face_bc],
+                alpha=[float(v) for v in alpha], f_mode=0, rtol=float(rtol))
+
+
+def exp_cube(levels=4, n0=(4, 4, 4), rtol=1e-10):
+    """Unit cube, -Laplace u = f, all Dirichlet, u = exp(x+y+z) (the 32^3 parity workload
+    with its default 4 levels 4^3 -> 32^3)."""
+    p = _base(n0, levels, (0, 0, 0), (1, 1, 1), [DIRICHLET] * 6, [0.0] * 6, rtol)
+    n = finest(n0, levels)
+    x, y, z = _axes(n, p["lo"], p["hi"])
+    u = np.exp(x) * np.exp(y) * np.exp(z)
+    p.update(beta=np.ones((n[2], n[1], n[0])), f=-3.0 * u, gD=u, gR=None, u_exact=u)
+    return p
+
+
+def cos_cube(levels=7, n0=(8, 8, 8), rtol=1e-10, load="exact"):
+    """Unit cube Poisson, u = cos(pi x) cos(pi y) cos(pi z), all Dirichlet, f = 3 pi^2 u.
+    Default 8^3 -> 512^3 (7 levels): the mixed-vs-FP64 workload.
+    load="exact": f is the load functional int f phi_i (f_mode 1); "nodal": nodal f."""
+    p = _base(n0, levels, (0, 0, 0), (1, 1, 1), [DIRICHLET] * 6, [0.0] * 6, rtol)
+    n = finest(n0, levels)
+    x, y, z = _axes(n, p["lo"], p["hi"])
+    c = [np.cos(PI * t) for t in (x, y, z)]
+    u = c[0] * c[1] * c[2]
+    if load == "exact":
+        cp = lambda t: np.cos(PI * t)
+        f = separable_load(n, p["lo"], p["hi"], 3.0 * PI * PI, cp, cp, cp)
+        p["f_mode"] = 1
+    else:
+        f = (3.0 * PI * PI) * u
+    p.update(beta=np.ones((n[2], n[1], n[0])), f=f, gD=u, gR=None, u_exact=u)
+    return p
+
+
+def paper_problem1(levels=7, n0=(8, 8, 8), rtol=1e-9, load="exact"):
+    """Problem 1 of Sec. 5: Laplace u = -(3/4) pi^2 sin sin sin on [0,1]^3, u = 0 on x, y or
+    z = 0, du/dn = 0 on x, y or z = 1; u = sin(pi x/2) sin(pi y/2) sin(pi z/2).
+    load="exact": f is the load functional int f phi_i (f_mode 1); "nodal": nodal f."""
+    bc = [DIRICHLET, ROBIN, DIRICHLET, ROBIN, DIRICHLET, ROBIN]
+    p = _base(n0, levels, (0, 0, 0), (1, 1, 1), bc, [0.0] * 6, rtol)
+    n = finest(n0, levels)
+    x, y, z = _axes(n, p["lo"], p["hi"])
+    u = np.sin(0.5 * PI * x) * np.sin(0.5 * PI * y) * np.sin(0.5 * PI * z)
+    if load == "exact":
+        sp_ = lambda t: np.sin(0.5 * PI * t)
+        f = separable_load(n, p["lo"], p["hi"], 0.75 * PI * PI, sp_, sp_, sp_)
+        p["f_mode"] = 1
+    else:
+        f = (0.75 * PI * PI) * u
+    p.update(beta=np.ones((n[2], n[1], n[0])), f=f,
+             gD=np.zeros_like(u), gR=np.zeros_like(u), u_exact=u)
+    return p
+
+
+def variable_box(levels=7, n0=(8, 8, 16), rtol=1e-9):
+    """Box (0,1)x(0,1)x(0,2) with beta = 1 + 0.5 sin(2 pi x) cos(2 pi y) sin(pi z) (at element
+    centres), u = sin(pi x) sin(pi y) sin(pi z) + x y z, Dirichlet on five faces and Robin
+    (alpha = 1) on z = 0. Default 8x8x16 -> 512x512x1024 (7 levels)."""
+    bc = [DIRICHLET, DIRICHLET, DIRICHLET, DIRICHLET, ROBIN, DIRICHLET]
+    alpha = [0.0, 0.0, 0.0, 0.0, 1.0, 0.0]
+    p = _base(n0, levels, (0, 0, 0), (1, 1, 2), bc, alpha, rtol)
+    n = finest(n0, levels)
+    xc, yc, zc = _axes(n, p["lo"], p["hi"], centres=True)
+    beta = 1.0 + 0.5 * np.sin(2 * PI * xc) * np.cos(2 * PI * yc) * np.sin(PI * zc)
+    x, y, z = _axes(n, p["lo"], p["hi"])
+    sx, sy, sz = np.sin(PI * x), np.sin(PI * y), np.sin(PI * z)
+    cx, cy, cz = np.cos(PI * x), np.cos(PI * y), np.cos(PI * z)
+    u = sx * sy * sz + x * y * z
+    b = 1.0 + 0.5 * np.sin(2 * PI * x) * np.cos(2 * PI * y) * sz
+    bx = PI * np.cos(2 * PI * x) * np.cos(2 * PI * y) * sz
+    by = -PI * np.sin(2 * PI * x) * np.sin(2 * PI * y) * sz
+    bz = 0.5 * PI * np.sin(2 * PI * x) * np.cos(2 * PI * y) * cz
+    ux = PI * cx * sy * sz + y * z
+    uy = PI * sx * cy * sz + x * z
+    uz = PI * sx * sy * cz + x * y
+    lap = -3.0 * PI * PI * sx * sy * sz
+    f = -b * lap - (bx * ux + by * uy + bz * uz)
+    # Robin on z = 0 (outward normal -z): g_R = alpha u + beta du/dn = u - beta u_z
+    gR = u - b * uz
+    p.update(beta=beta, f=f, gD=u, gR=gR, u_exact=u)
+    return p
+
+
+def random_problem(seed, n0=(2, 3, 2), levels=3, box=(1.0, 1.5, 0.75), face_bc=None,
+                   alpha=None, rtol=1e-10, contrast=10.0):
+    """Seeded random problem: lognormal beta (clipped to the given contrast), uniform f,
+    g_D and g_R in [-1, 1], and (unless given) random boundary types and Robin alphas with at
+    least one Dirichlet face."""
+    rng = np.random.default_rng(seed)
+    if face_bc is None:
+        face_bc = list(rng.integers(0, 2, size=6))
+        if all(b == ROBIN for b in face_bc):
+            face_bc[int(rng.integers(0, 6))] = DIRICHLET
+    if alpha is None:
+        alpha = [float(rng.choice([0.0, 0.5, 2.0])) if b == ROBIN else 0.0 for b in face_bc]
+    p = _base(n0, levels, (0, 0, 0), box, face_bc, alpha, rtol)
+    n = finest(n0, levels)
+    lnc = np.log(contrast)
+    beta = np.exp(np.clip(rng.standard_normal((n[2], n[1], n[0])), -lnc / 2, lnc / 2))
+    shp = (n[2] + 1, n[1] + 1, n[0] + 1)
+    p.update(beta=beta, f=rng.uniform(-1, 1, shp), gD=rng.uniform(-1, 1, shp),
+             gR=rng.uniform(-1, 1, shp), u_exact=None)
+    return p
+
+
+def random_vector(seed, shape):
+    """Seeded uniform [-1, 1] nodal vector (for operator parity checks)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, shape)

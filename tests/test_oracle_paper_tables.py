@@ -1,0 +1,62 @@
+"""The whole oracle (Alg. 4) against the numbers the paper prints for Problem 1 (Sec. 5).
+
+The load is the exact functional int f phi_i (f_mode 1). With the 27-node Lagrange variant
+of EXP_finite (the Remark in Sec. 4.3) the oracle reproduces the printed iteration counts,
+final relative residuals, ||U-u||, ||W-U|| and r_h; the 20-node Serendipity variant gives the
+same ||U-u|| and ||W-U|| within 6 % (L2) and 30 % (max). The extrapolated solution U~ comes out
+4-6 % above the printed values under every reading tried, so that column is a soft pin.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1506_02983_gb300 import inputs
+
+TAB = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "problem1_tables.json")))
+
+
+def _run(oracle_mod, eps, variant):
+    p = inputs.paper_problem1(levels=4, rtol=eps)
+    lv, st = oracle_mod.ecmg(p, eps, exp_variant=variant)
+    assert st["status"] == 0
+    rows = {}
+    for l, size in ((2, "32"), (3, "64")):
+        s = 1 << (3 - l)
+        ue = p["u_exact"][::s, ::s, ::s]
+        U, W, Ut = lv[l]["U"], lv[l]["W"], lv[l]["Ut"]
+        eU, eT, eW = oracle_mod.norms(U, ue), oracle_mod.norms(Ut, ue), oracle_mod.norms(W, U)
+        rows[size] = dict(iters=st["iters"][l], RRe=st["rel_res"][l], U_L2=eU[1], U_inf=eU[0],
+                          Ut_L2=eT[1], Ut_inf=eT[0], WU_L2=eW[1], WU_inf=eW[0], r_h=eW[1] / eU[1])
+    return rows
+
+
+@pytest.mark.parametrize("eps_key,eps", [("eps_1e-8", 1e-8), ("eps_1e-9", 1e-9), ("eps_1e-10", 1e-10)])
+def test_problem1_lagrange27_reproduces_tables(oracle_mod, eps_key, eps):
+    rows = _run(oracle_mod, eps, 1)
+    for size, want in TAB[eps_key].items():
+        if size.startswith("_") or size == "citation":
+            continue
+        got = rows[size]
+        assert got["iters"] == want["iters"], (size, got["iters"])
+        for k, tol in (("RRe", 0.02), ("U_L2", 0.01), ("U_inf", 0.01), ("WU_L2", 0.01),
+                       ("r_h", 0.01), ("WU_inf", 0.01)):
+            if k in want:
+                assert got[k] == pytest.approx(want[k], rel=tol), (size, k, got[k])
+        for k in ("Ut_L2", "Ut_inf"):
+            if k in want:
+                assert got[k] == pytest.approx(want[k], rel=0.10), (size, k, got[k])
+
+
+def test_problem1_serendipity20_close_to_tables(oracle_mod):
+    rows = _run(oracle_mod, 1e-9, 0)
+    for size, want in TAB["eps_1e-9"].items():
+        if size == "citation":
+            continue
+        got = rows[size]
+        assert got["U_L2"] == pytest.approx(want["U_L2"], rel=0.01)
+        assert got["U_inf"] == pytest.approx(want["U_inf"], rel=0.01)
+        assert got["WU_L2"] == pytest.approx(want["WU_L2"], rel=0.06)
+        assert got["WU_inf"] == pytest.approx(want["WU_inf"], rel=0.30)
+        assert abs(got["iters"] - want["iters"]) <= 2
