@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 ECMG_jcg solve: -Laplace u = f on the unit cube, u = cos(pi x)
+cos(pi y) cos(pi z), all-Dirichlet, Q1 elements, coarsest 8^3, 7 levels up to 512^3,
+relative residual tolerance 1e-10, exact load functional; synthetic data.
+
+One step = one complete ecmg_solve (level set-up, DSOLVE, EXP_finite / JCG / EXP_true on every
+level) in MIXED precision from inputs resident in HBM. value = finest free dofs / step time
+(Gdof/s). The same problem is also solved in plain FP64 (reported beside it, with both
+max-norm errors against the exact solution), end to end through the C ABI from pinned host
+buffers (e2e), and by the CPU oracle on a bounded sample (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): independent replicas, one per rank, max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ECMG solve time & Gdof/s at 512^3 (mixed vs FP64, same error); stencil HBM GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n0", type=int, default=8)
+    ap.add_argument("--levels", type=int, default=7)
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-levels", type=int, default=5, help="oracle sample: 8^3 -> 8*2^(L-1)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--kernels", default="0,1,2,5,6,7", help="kernels timed alone for the report")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), mx=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("pcap", "sw_power_cap")):
+            if any(r[key].lower().startswith("active") for r in loaded):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded), "sm_max_mhz": max(r["mx"] for r in rows),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def free_dofs(n):
+    return (n - 1) ** 3
+
+
+def cpu_baseline(args, levels):
+    """The oracle as it stands, one host core, on cos_cube up to 8*2^(levels-1)."""
+    import oracle
+    from paper_1506_02983_gb300 import inputs
+    oracle.build()
+    p = inputs.cos_cube(levels=levels, n0=(args.n0,) * 3, rtol=args.rtol)
+    t0 = time.perf_counter()
+    lv, st = oracle.ecmg(p, p["rtol"])
+    dt = time.perf_counter() - t0
+    nf = args.n0 << (levels - 1)
+    return dict(value=free_dofs(nf) / dt / 1e9, unit="Gdof/s", cores=1, kind="oracle",
+                sample="oracle ECMG_jcg FP64 on the same problem up to %d^3 (%d levels), %.1f s, "
+                       "finest free dofs / wall time" % (nf, levels, dt), seconds=dt)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    levels = min(args.cpu_levels, 4) if steps + warm > 4 else args.cpu_levels
+    import oracle
+    from paper_1506_02983_gb300 import inputs
+    oracle.build()
+    p = inputs.cos_cube(levels=levels, n0=(args.n0,) * 3, rtol=args.rtol)
+    for _ in range(warm):
+        oracle.ecmg(p, p["rtol"])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.ecmg(p, p["rtol"])
+    dt = (time.perf_counter() - t0) / steps
+    nf = args.n0 << (levels - 1)
+    v = free_dofs(nf) / dt / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gdof/s", "n_gpus": args.gpus,
+           "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "cos_cube Poisson, 8^3 -> %d^3 (%d levels), rtol %g, oracle sample"
+                      % (nf, levels, args.rtol)},
+           "cpu_baseline": {"value": v, "unit": "Gdof/s", "cores": 1, "kind": "oracle",
+                            "sample": "plain C FP64 oracle (CSR assembly, banded Cholesky, JCG) up to %d^3 per step" % nf},
+           "e2e": {"value": v, "unit": "Gdof/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1506_02983_gb300 import build, inputs
+    build.build()
+    from paper_1506_02983_gb300 import ecmg
+
+    L, n0 = args.levels, args.n0
+    nf = n0 << (L - 1)
+    p = inputs.cos_cube(levels=L, n0=(n0,) * 3, rtol=args.rtol)
+    dev = torch.device("cuda", local)
+    host = {k: torch.from_numpy(np.ascontiguousarray(p[k], dtype=np.float64)).pin_memory()
+            for k in ("beta", "f", "gD")}
+    d = {k: v.to(dev) for k, v in host.items()}
+    u_exact = torch.from_numpy(np.ascontiguousarray(p["u_exact"])).to(dev)
+    del p["beta"], p["f"], p["gD"]
+
+    def make(precision):
+        return ecmg.Solver(p["n0"], L, p["lo"], p["hi"], p["face_bc"], p["alpha"], d["beta"], d["f"],
+                           d["gD"], None, f_mode=ecmg.ECMG_F_LOAD, rtol=args.rtol, precision=precision,
+                           max_iters=args.max_iters)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return ms
+
+    mixed = make(ecmg.ECMG_MIXED)
+    u_out = torch.empty_like(u_exact)
+    for _ in range(args.warmup):
+        st_mixed, status = mixed.solve(u_out)
+        assert status == 0, st_mixed
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ecmg.kernel_launches()
+    ms_mixed = timed(lambda: mixed.solve(u_out), args.steps)
+    launches = (ecmg.kernel_launches() - launches0) // args.steps
+    clk = clocks.stop()
+    st_mixed, _ = mixed.solve(u_out)
+    err_mixed = mixed.norms(u_out, u_exact)[0]
+
+    # kernels alone (finest level), for the roofline
+    pk = peaks()
+    hbm_peak = pk.get("hbm_gbs")
+    kern = {}
+    names = {0: "k_pq<float> (K1 FP32)", 1: "k_update<float> (K2 FP32)", 2: "k_res<float> (FP64 residual)",
+             5: "k_res<double>", 6: "k_exp_finite", 7: "k_exp_true"}
+    for w in [int(x) for x in args.kernels.split(",") if x != ""]:
+        if w in (3, 4):
+            continue
+        ms, nb = mixed.time_kernel(w, -1, reps=10)
+        kern[names.get(w, str(w))] = {"ms": ms, "algorithmic_bytes": nb, "GBps": nb / ms / 1e6}
+    k1_ms, k1_bytes = mixed.time_kernel(0, -1, reps=20)
+
+    # end to end through the C ABI from pinned host buffers
+    u_host = torch.empty(u_exact.shape, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        for k in ("beta", "f", "gD"):
+            d[k].copy_(host[k], non_blocking=True)
+        mixed.solve(u_out)
+        u_host.copy_(u_out, non_blocking=True)
+
+    ms_e2e = timed(e2e_step, args.e2e_steps)
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = u_host.numel() * 8
+    mixed.close()
+
+    fp64 = make(ecmg.ECMG_FP64)
+    st64, status = fp64.solve(u_out)
+    assert status == 0, st64
+    ms_fp64 = timed(lambda: fp64.solve(u_out), args.fp64_steps)
+    err_fp64 = fp64.norms(u_out, u_exact)[0]
+    fp64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, args.cpu_levels)
+
+    dofs = free_dofs(nf) * world
+    value = dofs / (ms_mixed * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "k_pq_float_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("n") == nf:
+                traffic = tj.get("dram_bytes_per_launch")
+        except ValueError:
+            pass
+    k1_gbps = k1_bytes / k1_ms / 1e6
+    out = {
+        "metric": METRIC, "value": value, "unit": "Gdof/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": {"workload": "cos_cube Poisson unit cube, u=cos(pi x)cos(pi y)cos(pi z), all-Dirichlet, "
+                               "Q1, %d^3 -> %d^3 (%d levels), rtol %g, exact load functional" % (n0, nf, L, args.rtol),
+                   "precision": "MIXED (FP32 JCG, FP64 residual replacement)",
+                   "l2": "inputs and finest vectors (>1 GB each) larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
+        "solve_ms_mixed": ms_mixed, "solve_ms_fp64": ms_fp64, "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
+        "max_err_mixed": err_mixed, "max_err_fp64": err_fp64,
+        "err_ratio_mixed_over_fp64": err_mixed / err_fp64,
+        "iters_mixed": st_mixed["iters"], "updates_mixed": st_mixed["updates"], "iters_fp64": st64["iters"],
+        "rel_res_mixed": st_mixed["rel_res"], "gdofs_fp64": dofs / (ms_fp64 * 1e-3) / 1e9,
+        "roofline": {"kernel": "k_pq<float> (FP32 search direction + 27-point operator), finest level, timed alone",
+                     "bound": "hbm", "achieved": k1_gbps, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": (k1_gbps / hbm_peak) if hbm_peak else None, "traffic": traffic,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy; of measured)"},
+        "kernels_alone": kern,
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": {"value": dofs / (ms_e2e * 1e-3) / 1e9, "unit": "Gdof/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

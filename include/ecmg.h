@@ -1,0 +1,186 @@
+/*
+ * ecmg.h -- C ABI of the GB300 ECMG_jcg library (libecmg.so).
+ *
+ * The library solves the model problem of Pan, He and Hu (arXiv 1506.02983), Sec. 1,
+ * eq. (bvp):
+ *
+ *     -div(beta grad u) = f      in a box Omega,
+ *     u = g_D                    on the Dirichlet faces,
+ *     alpha u + beta du/dn = g_R on the Robin faces (alpha = 0 is Neumann),
+ *
+ * discretised by trilinear (Q1) finite elements on nested uniform hexahedral grids (Sec. 2),
+ * with the extrapolation cascadic multigrid method ECMG_jcg of Alg. 4: a direct solve on the
+ * two coarsest grids, then on every finer grid an extrapolated initial guess (EXP_finite,
+ * Sec. 4.2-4.3), Jacobi-preconditioned CG until ||A u - f||_2 <= rtol ||f||_2, and a fourth
+ * order Richardson-extrapolated solution (EXP_true, Sec. 4.2.1 and 4.3).
+ *
+ * Memory and ownership
+ *   - Every pointer argument documented as "device" is a CUDA device pointer on the current
+ *     device; "host" pointers are ordinary host memory. Inputs are read, never written.
+ *   - The caller owns every array it passes. ecmg_create records the problem description and
+ *     the input pointers; the input arrays must stay valid and unchanged until the last
+ *     ecmg_solve on the handle has completed (ecmg_solve reads them on the device).
+ *   - The handle owns the device workspace it allocates in ecmg_create (all levels, all
+ *     vectors) and frees it in ecmg_destroy.
+ *   - All work is ordered on the CUDA stream passed to ecmg_create (NULL = legacy default
+ *     stream). Functions that return values on the host synchronise that stream.
+ *
+ * Layout of caller arrays (the "dense" layout)
+ *   - Nodal arrays of a level with n = (nx, ny, nz) elements hold (nx+1)(ny+1)(nz+1) doubles,
+ *     index i + (nx+1) (j + (ny+1) k), x fastest.
+ *   - Element arrays hold nx ny nz doubles, index i + nx (j + ny k).
+ *
+ * Errors
+ *   Every function returns an ecmg_status. Nothing aborts and no kernel traps: a failure on
+ *   the device (breakdown, iteration cap) is recorded in a status word that the host reads
+ *   back; the best iterate stays in place. ECMG_ERR_CUDA reports a CUDA runtime error; the
+ *   message of the last error is available from ecmg_last_error().
+ */
+#ifndef ECMG_H
+#define ECMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ECMG_OK = 0,
+    ECMG_ERR_INVALID_ARG = 1,    /* bad size, pointer, option or level                      */
+    ECMG_ERR_SINGULAR = 2,       /* no Dirichlet face and every Robin alpha is zero          */
+    ECMG_ERR_NO_CONVERGENCE = 3, /* a level hit options.max_iters                            */
+    ECMG_ERR_BREAKDOWN = 4,      /* p.q <= 0 or a non-finite value in JCG                    */
+    ECMG_ERR_OOM = 5,            /* device allocation failed                                 */
+    ECMG_ERR_CUDA = 6            /* any other CUDA runtime error                             */
+} ecmg_status;
+
+enum { ECMG_BC_DIRICHLET = 0, ECMG_BC_ROBIN = 1 };
+/* f is nodal values of f (load b = M f_I + sum_F M_F g_R,I per level), or the finest
+ * assembled load functional b_i = f(phi_i) of Sec. 2 (coarse loads b_{l-1} = P^T b_l). */
+enum { ECMG_F_NODAL = 0, ECMG_F_LOAD = 1 };
+enum { ECMG_FP64 = 0, ECMG_MIXED = 1 };
+/* EXP_finite variant: the 20-node Serendipity interpolation of Sec. 4.3, or the 27-node
+ * tri-quadratic Lagrange variant of the Remark that follows it. */
+enum { ECMG_EXP_SERENDIPITY20 = 0, ECMG_EXP_LAGRANGE27 = 1 };
+/* ecmg_get_level: which vector */
+enum { ECMG_VEC_U = 0, ECMG_VEC_W = 1, ECMG_VEC_UTILDE = 2, ECMG_VEC_B = 3, ECMG_VEC_BETA = 4 };
+
+/* Problem statement of eq. (bvp) (Sec. 1) on the finest grid. */
+typedef struct {
+    int32_t n0[3];          /* coarsest grid elements per axis, >= 1                        */
+    int32_t levels;         /* total nested levels, 3..12; level l has n0 * 2^l elements  */
+    double lo[3], hi[3];    /* box corners, hi > lo                                          */
+    int32_t face_bc[6];     /* faces x-,x+,y-,y+,z-,z+: ECMG_BC_DIRICHLET or ECMG_BC_ROBIN  */
+    double robin_alpha[6];  /* alpha on each Robin face (>= 0); ignored on Dirichlet faces  */
+    const double* beta;     /* device, finest elements, > 0 (dense element layout)          */
+    const double* f;        /* device, finest nodes: f values or load functional (f_mode)   */
+    const double* g_D;      /* device, finest nodes, read on Dirichlet nodes; NULL = 0      */
+    const double* g_R;      /* device, finest nodes, read on Robin faces (nodal f_mode only);
+                               NULL = 0                                                      */
+    int32_t f_mode;         /* ECMG_F_NODAL or ECMG_F_LOAD                                  */
+} ecmg_problem;
+
+/* Solver options. ecmg_default_options fills the defaults given in brackets. */
+typedef struct {
+    double rtol;            /* relative residual tolerance epsilon of Alg. 4 line 7 [1e-9]  */
+    int32_t precision;      /* ECMG_FP64 or ECMG_MIXED                        [ECMG_FP64]   */
+    double inner_rtol;      /* MIXED: FP32 inner reduction between FP64 residual
+                               replacements                                  [1e-2]        */
+    int32_t max_iters;      /* per-level JCG iteration cap                   [100000]      */
+    int32_t use_graph;      /* 1: one CUDA graph per solve with device-side loop control;
+                               0: host-driven loop (debugging)               [1]           */
+    double dsolve_rtol;     /* relative residual of the direct solve on levels 0, 1 [1e-14]*/
+    int32_t exp_variant;    /* ECMG_EXP_SERENDIPITY20 / ECMG_EXP_LAGRANGE27  [SERENDIPITY20]*/
+    int32_t true_residual;  /* 1: report the true FP64 residual of every level [1]         */
+} ecmg_options;
+
+/* Per-solve statistics, one entry per level (coarsest first). */
+typedef struct {
+    int32_t levels;
+    int32_t iters[16];      /* JCG iterations (FP32 inner iterations in MIXED mode)         */
+    int32_t updates[16];    /* MIXED: FP64 residual replacements; FP64: 0                   */
+    double rel_res[16];     /* ||b - A u||_2 / ||f_h||_2 on exit (true residual if enabled, */
+                            /* else the recursive one)                                      */
+    double rhs_norm[16];    /* ||f_h||_2, the free-node right-hand side with g_D moved over */
+    int32_t status;         /* ecmg_status of the solve                                     */
+} ecmg_stats;
+
+typedef struct ecmg_handle ecmg_handle;
+
+/* Fill *opt with the defaults listed in ecmg_options. */
+void ecmg_default_options(ecmg_options* opt);
+
+/* Validate the problem, allocate the device workspace of every level and record the problem
+ * (Alg. 4 inputs). stream: a cudaStream_t (NULL = default stream). *out receives the handle.
+ * Returns ECMG_ERR_INVALID_ARG for bad sizes or options, ECMG_ERR_SINGULAR when no face is
+ * Dirichlet and every Robin alpha is 0, ECMG_ERR_OOM when allocation fails. */
+ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void* stream,
+                        ecmg_handle** out);
+
+/* Run Alg. 4: level set-up from the current input arrays (beta averaging, loads, Jacobi
+ * diagonals), DSOLVE on levels 0 and 1, then for each finer level EXP_finite, JCG and
+ * EXP_true. u_out: device, finest nodes (dense layout), may be NULL. stats: host, may be
+ * NULL. Synchronises the stream. Returns the worst status over the levels. */
+ecmg_status ecmg_solve(ecmg_handle* h, double* u_out, ecmg_stats* stats);
+
+/* Copy the fourth-order extrapolated solution U~ (EXP_true) of level `level` (-1 = finest,
+ * 2..levels-1 otherwise) into u_tilde_out (device, dense nodal layout of that level). Valid
+ * after ecmg_solve. Ordered on the handle's stream; does not synchronise. */
+ecmg_status ecmg_extrapolate(ecmg_handle* h, int32_t level, double* u_tilde_out);
+
+/* Copy one stored vector of a level (ECMG_VEC_U solution, ECMG_VEC_W initial guess,
+ * ECMG_VEC_UTILDE extrapolated solution, ECMG_VEC_B assembled load, ECMG_VEC_BETA element
+ * coefficients) into out (device, dense layout of that level). level -1 = finest. */
+ecmg_status ecmg_get_level(ecmg_handle* h, int32_t level, int32_t which, double* out);
+
+/* Overwrite the stored solution U of a level (device, dense layout). With ecmg_solve_from this
+ * resumes Alg. 4 at any level >= 2 from the two stored coarser solutions. */
+ecmg_status ecmg_set_level(ecmg_handle* h, int32_t level, const double* in);
+
+/* Run Alg. 4 from level `first` (>= 2) upwards, using the stored U of levels first-1 and
+ * first-2 (after a previous ecmg_solve or ecmg_set_level). Same outputs as ecmg_solve. */
+ecmg_status ecmg_solve_from(ecmg_handle* h, int32_t first, double* u_out, ecmg_stats* stats);
+
+/* y = A_l x for level `level` (-1 = finest) with the level's matrix of Sec. 2 (Robin terms
+ * included, no boundary elimination): x, y device, dense nodal layout. Valid after the
+ * level set-up of an ecmg_solve. precision ECMG_FP64 or ECMG_MIXED (FP32 arithmetic on FP32
+ * rounded x). Ordered on the handle's stream. */
+ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision,
+                                const double* x, double* y);
+
+/* Error norms between two device vectors of one level (dense nodal layout): max |a - b| and
+ * root-mean-square over all nodes (the max and "L2" norms of the tables of Sec. 5).
+ * b may be NULL (norms of a). Results on the host; synchronises the stream. */
+ecmg_status ecmg_error_norms(ecmg_handle* h, int32_t level, const double* a, const double* b,
+                             double* max_abs, double* rms);
+
+void ecmg_destroy(ecmg_handle* h);
+const char* ecmg_status_string(ecmg_status s);
+const char* ecmg_last_error(void);
+
+/* ---- measurement helpers (no counterpart in the paper) --------------------------------- */
+
+/* Total kernel executions of this library in the process so far (counted on the device by
+ * every kernel; a kernel that finds its level already finished still counts). out: host. */
+ecmg_status ecmg_kernel_launches(uint64_t* out);
+
+/* Time one kernel of the solve alone on level `level` (-1 = finest): `reps` launches, each
+ * bracketed by CUDA events on the handle's stream, after one untimed launch. which:
+ * 0 K1 FP32 (search direction + operator), 1 K2 FP32 (residual update), 2 FP64 residual with
+ * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true.
+ * ms_out: mean duration of one launch (host). bytes_out: the algorithmic bytes one launch
+ * must move (each owned input read once, each output written once; host). Valid after
+ * ecmg_solve; it overwrites the level's work vectors and U~ (kernel 3 uses U~ as its
+ * iterate); U and W are never changed. Synchronises the stream. */
+ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,
+                             double* ms_out, double* bytes_out);
+
+/* Bytes of device workspace ecmg_create allocates for this problem and options. */
+ecmg_status ecmg_workspace_bytes(const ecmg_problem* prob, const ecmg_options* opt,
+                                 uint64_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,734 @@
+// api.cu -- host driver of ECMG_jcg (Alg. 4) behind the C ABI of include/ecmg.h.
+//
+// ecmg_solve records the whole method -- set-up of every level, DSOLVE on levels 0 and 1,
+// then EXP_finite / JCG / EXP_true on every finer level -- into one CUDA graph on first use.
+// Each level's JCG loop is a conditional WHILE node whose condition the kernels themselves
+// set (see jcg.cu); in MIXED precision the FP64 residual replacement is a conditional IF node
+// inside the loop body. A solve is therefore one graph launch and one stream synchronisation.
+// With options.use_graph = 0 the same kernels run eagerly and the host reads the level state
+// after every iteration (for debugging).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ecmg.h"
+#include "ecmg_internal.cuh"
+#include "exp.cuh"
+#include "jcg.cuh"
+
+using namespace ecmg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct CudaFail {
+    cudaError_t e;
+};
+
+inline void ck(cudaError_t e)
+{
+    if (e != cudaSuccess) throw CudaFail{e};
+}
+
+struct Level {
+    Grid g;
+    Op op;
+    // FP64 vectors
+    double *U = nullptr, *W = nullptr, *Ut = nullptr, *b = nullptr, *beta = nullptr, *dinv = nullptr;
+    double *f = nullptr, *gD = nullptr, *gR = nullptr;  // injected data (nodal mode); f = load (load mode)
+    double *r = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr;
+    // FP32 vectors (mixed precision)
+    float *beta32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *pA32 = nullptr, *pB32 = nullptr,
+          *q32 = nullptr, *e32 = nullptr;
+};
+
+}  // namespace
+
+struct ecmg_handle {
+    ecmg_problem prob;
+    ecmg_options opt;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams (graph + 2 nesting levels)
+    int L = 0;
+    Level lv[MAX_LEVELS];
+    SolveState* states = nullptr;  // device, one per level
+    Partials part{nullptr, 0};
+    double* norm_part = nullptr;   // device, per-block norm partials
+    std::vector<void*> allocs;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    SolveState* host_states = nullptr;  // pinned
+    double* host_norms = nullptr;       // pinned
+    int graph_first = -1;               // first level of the recorded graph
+};
+
+namespace {
+
+ecmg_status fail(ecmg_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+Grid make_grid(const ecmg_problem& p, int l)
+{
+    Grid g;
+    g.nx = p.n0[0] << l;
+    g.ny = p.n0[1] << l;
+    g.nz = p.n0[2] << l;
+    g.pitch = ((g.nx + 1 + XL + 2) + 31) / 32 * 32;
+    g.plane = (int64_t)g.pitch * (g.ny + 3);
+    g.total = g.plane * (g.nz + 3);
+    for (int a = 0; a < 3; ++a) g.h[a] = (p.hi[a] - p.lo[a]) / (double)(p.n0[a] << l);
+    return g;
+}
+
+ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
+{
+    if (!p || !o) return fail(ECMG_ERR_INVALID_ARG, "null problem or options");
+    if (p->levels < 3 || p->levels > 12) return fail(ECMG_ERR_INVALID_ARG, "levels must be 3..12");
+    for (int a = 0; a < 3; ++a) {
+        if (p->n0[a] < 1) return fail(ECMG_ERR_INVALID_ARG, "n0 must be >= 1");
+        if (!(p->hi[a] > p->lo[a])) return fail(ECMG_ERR_INVALID_ARG, "hi must exceed lo");
+        int64_t nf = (int64_t)p->n0[a] << (p->levels - 1);
+        if (nf > 16384) return fail(ECMG_ERR_INVALID_ARG, "finest grid too large");
+    }
+    if (!p->beta || !p->f) return fail(ECMG_ERR_INVALID_ARG, "beta and f are required");
+    if (p->f_mode != ECMG_F_NODAL && p->f_mode != ECMG_F_LOAD)
+        return fail(ECMG_ERR_INVALID_ARG, "bad f_mode");
+    bool dir = false, alpha = false;
+    for (int f = 0; f < 6; ++f) {
+        if (p->face_bc[f] != ECMG_BC_DIRICHLET && p->face_bc[f] != ECMG_BC_ROBIN)
+            return fail(ECMG_ERR_INVALID_ARG, "bad face_bc");
+        if (p->face_bc[f] == ECMG_BC_DIRICHLET) dir = true;
+        else {
+            if (!(p->robin_alpha[f] >= 0.0) || !std::isfinite(p->robin_alpha[f]))
+                return fail(ECMG_ERR_INVALID_ARG, "robin_alpha must be finite and >= 0");
+            if (p->robin_alpha[f] > 0.0) alpha = true;
+        }
+    }
+    if (!dir && !alpha) return fail(ECMG_ERR_SINGULAR, "no Dirichlet face and every Robin alpha is 0");
+    if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return fail(ECMG_ERR_INVALID_ARG, "rtol must be in (0,1)");
+    if (o->precision != ECMG_FP64 && o->precision != ECMG_MIXED)
+        return fail(ECMG_ERR_INVALID_ARG, "bad precision");
+    if (o->precision == ECMG_MIXED && !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0))
+        return fail(ECMG_ERR_INVALID_ARG, "inner_rtol must be in (0,1)");
+    if (o->max_iters < 1) return fail(ECMG_ERR_INVALID_ARG, "max_iters must be >= 1");
+    if (!(o->dsolve_rtol > 0.0 && o->dsolve_rtol < 1.0))
+        return fail(ECMG_ERR_INVALID_ARG, "dsolve_rtol must be in (0,1)");
+    if (o->exp_variant != ECMG_EXP_SERENDIPITY20 && o->exp_variant != ECMG_EXP_LAGRANGE27)
+        return fail(ECMG_ERR_INVALID_ARG, "bad exp_variant");
+    return ECMG_OK;
+}
+
+// Byte count of the per-level vectors (the same arithmetic allocate() performs).
+uint64_t level_bytes(const Grid& g, bool mixed)
+{
+    const uint64_t n = (uint64_t)g.total;
+    uint64_t b = n * 8ull * 14ull;  // U W Ut b beta dinv f gD gR r pA pB q (+1 spare alignment)
+    if (mixed) b += n * 4ull * 7ull;
+    return b;
+}
+
+template <typename T>
+T* dalloc(ecmg_handle* h, int64_t n)
+{
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (size_t)n * sizeof(T));
+    if (e != cudaSuccess) throw CudaFail{e};
+    h->allocs.push_back(p);
+    ck(cudaMemsetAsync(p, 0, (size_t)n * sizeof(T), h->cap[0]));
+    return (T*)p;
+}
+
+// ---- recording: graph capture with conditional nodes, or eager execution ------------------
+struct Rec {
+    ecmg_handle* h;
+    bool graph;
+    int depth = 0;
+    cudaStream_t s() const { return graph ? h->cap[depth] : h->user_stream; }
+
+    // A conditional handle on the graph being captured on s(); its value is reset to 0 at every
+    // graph launch and set by the kernels.
+    cudaGraphConditionalHandle new_handle()
+    {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg;
+        ck(cudaStreamGetCaptureInfo(s(), &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle hd;
+        ck(cudaGraphConditionalHandleCreate(&hd, cg, 0, cudaGraphCondAssignDefault));
+        return hd;
+    }
+    // Append a WHILE / IF node after everything captured so far on s() and continue capturing
+    // into its body on the next stream until close().
+    void open(cudaGraphConditionalHandle hd, cudaGraphConditionalNodeType type)
+    {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* ed = nullptr;
+        size_t nd = 0;
+        ck(cudaStreamGetCaptureInfo(s(), &cs, nullptr, &cg, &deps, &ed, &nd));
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = hd;
+        np.conditional.type = type;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        ck(cudaGraphAddNode(&node, cg, deps, ed, nd, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        ck(cudaStreamUpdateCaptureDependencies(s(), &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        ++depth;
+        ck(cudaStreamBeginCaptureToGraph(s(), body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    }
+    void close()
+    {
+        cudaGraph_t g;
+        ck(cudaStreamEndCapture(s(), &g));
+        --depth;
+    }
+};
+
+void host_state(ecmg_handle* h, int l, SolveState* out)
+{
+    ck(cudaMemcpyAsync(out, h->states + l, sizeof(SolveState), cudaMemcpyDeviceToHost, h->user_stream));
+    ck(cudaStreamSynchronize(h->user_stream));
+}
+
+// ---- level set-up (finest to coarsest) -------------------------------------------------------
+void record_setup(Rec& R)
+{
+    ecmg_handle* h = R.h;
+    const ecmg_problem& p = h->prob;
+    cudaStream_t s = R.s();
+    const bool mixed = h->opt.precision == ECMG_MIXED;
+    const int L = h->L;
+    for (int l = L - 1; l >= 0; --l) {
+        Level& v = h->lv[l];
+        if (l == L - 1) {
+            pack_elements(v.g, p.beta, v.beta, s);
+            pack_nodal(v.g, p.f, v.f, s);
+            if (p.g_D) pack_nodal(v.g, p.g_D, v.gD, s);
+            if (p.g_R) pack_nodal(v.g, p.g_R, v.gR, s);
+        } else {
+            Level& u = h->lv[l + 1];
+            coarsen_beta(v.g, u.beta, u.g, v.beta, s);
+            if (p.f_mode == ECMG_F_LOAD) restrict_load(v.g, u.b, u.g, v.b, s);
+            else inject_nodal(v.g, u.f, u.g, v.f, s);
+            if (p.g_D) inject_nodal(v.g, u.gD, u.g, v.gD, s);
+            if (p.g_R) inject_nodal(v.g, u.gR, u.g, v.gR, s);
+        }
+        if (p.f_mode == ECMG_F_LOAD) {
+            if (l == L - 1) ck(cudaMemcpyAsync(v.b, v.f, (size_t)v.g.total * 8, cudaMemcpyDeviceToDevice, s));
+        } else {
+            nodal_load(v.g, v.op, v.f, p.g_R ? v.gR : nullptr, v.b, s);
+        }
+        jacobi_diag(v.g, v.op, v.beta, v.dinv, mixed ? v.dinv32 : nullptr, mixed ? v.beta32 : nullptr, s);
+    }
+}
+
+// ---- one level of Alg. 4 ------------------------------------------------------------------------
+void record_level(Rec& R, int l)
+{
+    ecmg_handle* h = R.h;
+    Level& v = h->lv[l];
+    SolveState* st = h->states + l;
+    const ecmg_options& o = h->opt;
+    const bool direct = l < 2;
+    const bool mixed = o.precision == ECMG_MIXED && !direct;
+    const double rtol = direct ? o.dsolve_rtol : o.rtol;
+    CondHandles none{0, 0, 0};
+
+    launch_state_init(st, rtol, o.inner_rtol, o.max_iters, R.s());
+    dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s());
+    launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_FH2, none, R.s());
+    if (!direct) {
+        const Level& u1 = h->lv[l - 1];
+        const Level& u0 = h->lv[l - 2];
+        launch_exp_finite(o.exp_variant, v.g, v.op, u1.g, u1.U, u0.g, u0.U, v.U, v.W, R.s());
+    } else {
+        ck(cudaMemcpyAsync(v.W, v.U, (size_t)v.g.total * 8, cudaMemcpyDeviceToDevice, R.s()));
+    }
+
+    if (!mixed) {
+        ck(cudaMemsetAsync(v.pA, 0, (size_t)v.g.total * 8, R.s()));
+        ck(cudaMemsetAsync(v.pB, 0, (size_t)v.g.total * 8, R.s()));
+        auto half = [&](CondHandles ch, const double* pin, double* pout, int idx) {
+            launch_pq64(v.g, v.op, v.beta, v.r, v.dinv, pin, pout, v.q, v.U, st, h->part, idx, ch, R.s());
+            launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, ch, R.s());
+        };
+        if (R.graph) {
+            const cudaGraphConditionalHandle loop = R.new_handle();
+            const CondHandles ch{loop, 0, 1};
+            launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_INIT, ch, R.s());
+            R.open(loop, cudaGraphCondTypeWhile);
+            half(ch, v.pA, v.pB, 1);
+            half(ch, v.pB, v.pA, 0);
+            R.close();
+        } else {
+            launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_INIT, none, R.s());
+            SolveState hs;
+            host_state(h, l, &hs);
+            int parity = 0;
+            while (!hs.done) {
+                if (parity == 0) half(none, v.pA, v.pB, 1);
+                else half(none, v.pB, v.pA, 0);
+                parity ^= 1;
+                host_state(h, l, &hs);
+            }
+        }
+        launch_final64(v.g, v.U, v.pA, v.pB, st, R.s());
+        if (o.true_residual)
+            launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, R.s());
+    } else {
+        ck(cudaMemsetAsync(v.pA32, 0, (size_t)v.g.total * 4, R.s()));
+        ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
+        ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
+        auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
+            launch_pq32(v.g, v.op, v.beta32, v.r32, v.dinv32, pin, pout, v.q32, v.e32, st, h->part, idx, ch, R.s());
+            launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
+        };
+        auto replace = [&](float* pnew) {
+            launch_fold32(v.g, v.U, v.e32, pnew, st, R.s());
+            launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPLACE, none, R.s());
+        };
+        if (R.graph) {
+            const cudaGraphConditionalHandle loop = R.new_handle();
+            launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT,
+                         CondHandles{loop, 0, 1}, R.s());
+            R.open(loop, cudaGraphCondTypeWhile);
+            for (int half = 0; half < 2; ++half) {
+                const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
+                const CondHandles ch{loop, upd, 1};
+                float* pin = half ? v.pB32 : v.pA32;
+                float* pout = half ? v.pA32 : v.pB32;
+                step(ch, pin, pout, half ? 0 : 1);
+                R.open(upd, cudaGraphCondTypeIf);
+                replace(pout);
+                R.close();
+            }
+            R.close();
+        } else {
+            launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT, none, R.s());
+            SolveState hs;
+            host_state(h, l, &hs);
+            int parity = 0;
+            while (!hs.done) {
+                float* pin = parity ? v.pB32 : v.pA32;
+                float* pout = parity ? v.pA32 : v.pB32;
+                step(none, pin, pout, parity ? 0 : 1);
+                host_state(h, l, &hs);
+                if (hs.need_update && !hs.done) {
+                    replace(pout);
+                    host_state(h, l, &hs);
+                }
+                parity ^= 1;
+            }
+        }
+    }
+    if (!direct) {
+        const Level& u1 = h->lv[l - 1];
+        launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s());
+    }
+}
+
+void record_solve(Rec& R, int first)
+{
+    if (first == 0) record_setup(R);
+    for (int l = first; l < R.h->L; ++l) record_level(R, l);
+}
+
+ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stats)
+{
+    try {
+        if (h->opt.use_graph) {
+            if (!h->exec || h->graph_first != first) {
+                if (h->exec) {
+                    cudaGraphExecDestroy(h->exec);
+                    h->exec = nullptr;
+                }
+                if (h->graph) {
+                    cudaGraphDestroy(h->graph);
+                    h->graph = nullptr;
+                }
+                Rec R{h, true, 0};
+                ck(cudaStreamBeginCapture(h->cap[0], cudaStreamCaptureModeThreadLocal));
+                try {
+                    record_solve(R, first);
+                } catch (...) {
+                    cudaGraph_t junk;
+                    cudaStreamEndCapture(h->cap[0], &junk);
+                    if (junk) cudaGraphDestroy(junk);
+                    throw;
+                }
+                ck(cudaStreamEndCapture(h->cap[0], &h->graph));
+                ck(cudaGraphInstantiate(&h->exec, h->graph, 0));
+                h->graph_first = first;
+            }
+            ck(cudaGraphLaunch(h->exec, h->user_stream));
+        } else {
+            Rec R{h, false, 0};
+            record_solve(R, first);
+        }
+        Level& fin = h->lv[h->L - 1];
+        if (u_out) unpack_nodal(fin.g, fin.U, u_out, h->user_stream);
+        ck(cudaGetLastError());
+        ck(cudaMemcpyAsync(h->host_states, h->states, sizeof(SolveState) * h->L, cudaMemcpyDeviceToHost,
+                           h->user_stream));
+        ck(cudaStreamSynchronize(h->user_stream));
+    } catch (CudaFail& f) {
+        return fail(ECMG_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(f.e));
+    }
+    ecmg_status worst = ECMG_OK;
+    ecmg_stats st;
+    memset(&st, 0, sizeof(st));
+    st.levels = h->L;
+    for (int l = 0; l < h->L; ++l) {
+        const SolveState& s = h->host_states[l];
+        if (l < first) continue;
+        st.iters[l] = s.iters;
+        st.updates[l] = s.updates;
+        st.rhs_norm[l] = std::sqrt(s.fh2);
+        const bool have_true = h->opt.true_residual || (h->opt.precision == ECMG_MIXED && l >= 2);
+        const double rr = have_true ? s.rr_true : s.rr;
+        st.rel_res[l] = s.fh2 > 0 ? std::sqrt(rr / s.fh2) : std::sqrt(rr);
+        ecmg_status ls = ECMG_OK;
+        if (s.status == 3) ls = ECMG_ERR_NO_CONVERGENCE;
+        if (s.status == 4) ls = ECMG_ERR_BREAKDOWN;
+        if (ls == ECMG_ERR_BREAKDOWN || (ls != ECMG_OK && worst == ECMG_OK)) worst = ls;
+    }
+    st.status = worst;
+    if (stats) *stats = st;
+    if (worst != ECMG_OK) g_last_error = ecmg_status_string(worst);
+    return worst;
+}
+
+int resolve_level(ecmg_handle* h, int level) { return level < 0 ? h->L - 1 : level; }
+
+}  // namespace
+
+extern "C" {
+
+void ecmg_default_options(ecmg_options* o)
+{
+    if (!o) return;
+    o->rtol = 1e-9;
+    o->precision = ECMG_FP64;
+    o->inner_rtol = 1e-2;
+    o->max_iters = 100000;
+    o->use_graph = 1;
+    o->dsolve_rtol = 1e-14;
+    o->exp_variant = ECMG_EXP_SERENDIPITY20;
+    o->true_residual = 1;
+}
+
+ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, uint64_t* bytes)
+{
+    ecmg_status s = validate(p, o);
+    if (s != ECMG_OK) return s;
+    if (!bytes) return fail(ECMG_ERR_INVALID_ARG, "bytes is null");
+    uint64_t b = 0;
+    int maxb = 0;
+    for (int l = 0; l < p->levels; ++l) {
+        Grid g = make_grid(*p, l);
+        b += level_bytes(g, o->precision == ECMG_MIXED);
+        maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
+    }
+    b += (uint64_t)maxb * 3 * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
+    *bytes = b;
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void* stream,
+                        ecmg_handle** out)
+{
+    if (!out) return fail(ECMG_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    ecmg_status s = validate(prob, opt);
+    if (s != ECMG_OK) return s;
+    ecmg_handle* h = new ecmg_handle();
+    h->prob = *prob;
+    h->opt = *opt;
+    h->user_stream = (cudaStream_t)stream;
+    h->L = prob->levels;
+    try {
+        for (int i = 0; i < 3; ++i) ck(cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
+        ck(exp_init_tables());
+        const bool mixed = opt->precision == ECMG_MIXED;
+        int maxb = 0;
+        for (int l = 0; l < h->L; ++l) {
+            Level& v = h->lv[l];
+            v.g = make_grid(*prob, l);
+            v.op = make_op(v.g.h, prob->face_bc, prob->robin_alpha);
+            const int64_t n = v.g.total;
+            v.U = dalloc<double>(h, n);
+            v.W = dalloc<double>(h, n);
+            v.Ut = dalloc<double>(h, n);
+            v.b = dalloc<double>(h, n);
+            v.beta = dalloc<double>(h, n);
+            v.dinv = dalloc<double>(h, n);
+            v.f = dalloc<double>(h, n);
+            v.gD = dalloc<double>(h, n);
+            v.gR = dalloc<double>(h, n);
+            v.r = dalloc<double>(h, n);
+            v.pA = dalloc<double>(h, n);
+            v.pB = dalloc<double>(h, n);
+            v.q = dalloc<double>(h, n);
+            if (mixed) {
+                v.beta32 = dalloc<float>(h, n);
+                v.dinv32 = dalloc<float>(h, n);
+                v.r32 = dalloc<float>(h, n);
+                v.pA32 = dalloc<float>(h, n);
+                v.pB32 = dalloc<float>(h, n);
+                v.q32 = dalloc<float>(h, n);
+                v.e32 = dalloc<float>(h, n);
+            }
+            maxb = std::max(maxb, std::max(max_stencil_blocks(v.g), max_stream_blocks()));
+        }
+        h->part.buf = dalloc<double>(h, (int64_t)maxb * 3);
+        h->part.max_blocks = maxb;
+        h->states = dalloc<SolveState>(h, MAX_LEVELS);
+        h->norm_part = dalloc<double>(h, 2048);
+        ck(cudaMallocHost(&h->host_states, sizeof(SolveState) * MAX_LEVELS));
+        ck(cudaMallocHost(&h->host_norms, sizeof(double) * 2048));
+        ck(cudaStreamSynchronize(h->cap[0]));
+    } catch (CudaFail& f) {
+        ecmg_destroy(h);
+        if (f.e == cudaErrorMemoryAllocation) return fail(ECMG_ERR_OOM, "device allocation failed");
+        return fail(ECMG_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(f.e));
+    }
+    *out = h;
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_solve(ecmg_handle* h, double* u_out, ecmg_stats* stats)
+{
+    if (!h) return fail(ECMG_ERR_INVALID_ARG, "null handle");
+    return run_solve(h, 0, u_out, stats);
+}
+
+ecmg_status ecmg_solve_from(ecmg_handle* h, int32_t first, double* u_out, ecmg_stats* stats)
+{
+    if (!h) return fail(ECMG_ERR_INVALID_ARG, "null handle");
+    if (first < 2 || first >= h->L) return fail(ECMG_ERR_INVALID_ARG, "first must be in 2..levels-1");
+    return run_solve(h, first, u_out, stats);
+}
+
+ecmg_status ecmg_extrapolate(ecmg_handle* h, int32_t level, double* u_tilde_out)
+{
+    return ecmg_get_level(h, level, ECMG_VEC_UTILDE, u_tilde_out);
+}
+
+ecmg_status ecmg_get_level(ecmg_handle* h, int32_t level, int32_t which, double* out)
+{
+    if (!h || !out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    Level& v = h->lv[l];
+    const double* src = nullptr;
+    switch (which) {
+    case ECMG_VEC_U: src = v.U; break;
+    case ECMG_VEC_W: src = v.W; break;
+    case ECMG_VEC_UTILDE:
+        if (l < 2) return fail(ECMG_ERR_INVALID_ARG, "U~ exists on levels >= 2 only");
+        src = v.Ut;
+        break;
+    case ECMG_VEC_B: src = v.b; break;
+    case ECMG_VEC_BETA: src = v.beta; break;
+    default: return fail(ECMG_ERR_INVALID_ARG, "bad vector selector");
+    }
+    if (which == ECMG_VEC_BETA) {
+        // element (i,j,k) sits at the node offset of its lowest corner; copy row by row
+        for (int k = 0; k < v.g.nz; ++k)
+            for (int j = 0; j < v.g.ny; ++j) {
+                cudaError_t e = cudaMemcpyAsync(out + (size_t)v.g.nx * (j + (size_t)v.g.ny * k),
+                                                src + v.g.off(0, j, k), (size_t)v.g.nx * 8,
+                                                cudaMemcpyDeviceToDevice, h->user_stream);
+                if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
+            }
+        return ECMG_OK;
+    }
+    unpack_nodal(v.g, src, out, h->user_stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_set_level(ecmg_handle* h, int32_t level, const double* in)
+{
+    if (!h || !in) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    pack_nodal(h->lv[l].g, in, h->lv[l].U, h->user_stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision, const double* x,
+                                double* y)
+{
+    if (!h || !x || !y) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    Level& v = h->lv[l];
+    cudaStream_t s = h->user_stream;
+    // x -> padded (into r), y <- padded (from q)
+    pack_nodal(v.g, x, v.r, s);
+    if (precision == ECMG_MIXED) {
+        if (!v.r32) return fail(ECMG_ERR_INVALID_ARG, "handle was created without MIXED precision");
+        convert_f32(v.r, v.r32, v.g.total, s);
+        launch_apply32(v.g, v.op, v.beta32, v.r32, v.q, s);
+    } else if (precision == ECMG_FP64) {
+        launch_apply64(v.g, v.op, v.beta, v.r, v.q, s);
+    } else {
+        return fail(ECMG_ERR_INVALID_ARG, "bad precision");
+    }
+    unpack_nodal(v.g, v.q, y, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_error_norms(ecmg_handle* h, int32_t level, const double* a, const double* b,
+                             double* max_abs, double* rms)
+{
+    if (!h || !a || !max_abs || !rms) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    Level& v = h->lv[l];
+    cudaStream_t s = h->user_stream;
+    try {
+        pack_nodal(v.g, a, v.r, s);
+        if (b) pack_nodal(v.g, b, v.q, s);
+        launch_norms(v.g, v.r, b ? v.q : nullptr, h->norm_part, s);
+        const int nb = norms_blocks(v.g);
+        ck(cudaMemcpyAsync(h->host_norms, h->norm_part, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        double mx = 0.0, ss = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            mx = std::max(mx, h->host_norms[2 * i]);
+            ss += h->host_norms[2 * i + 1];
+        }
+        *max_abs = mx;
+        *rms = std::sqrt(ss / (double)((int64_t)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1)));
+    } catch (CudaFail& f) {
+        return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+    }
+    return ECMG_OK;
+}
+
+void ecmg_destroy(ecmg_handle* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->user_stream);
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->host_states) cudaFreeHost(h->host_states);
+    if (h->host_norms) cudaFreeHost(h->host_norms);
+    for (int i = 0; i < 3; ++i)
+        if (h->cap[i]) cudaStreamDestroy(h->cap[i]);
+    delete h;
+}
+
+const char* ecmg_status_string(ecmg_status s)
+{
+    switch (s) {
+    case ECMG_OK: return "ok";
+    case ECMG_ERR_INVALID_ARG: return "invalid argument";
+    case ECMG_ERR_SINGULAR: return "singular problem (no Dirichlet face and all Robin alpha = 0)";
+    case ECMG_ERR_NO_CONVERGENCE: return "iteration cap reached before the tolerance";
+    case ECMG_ERR_BREAKDOWN: return "JCG breakdown (p.q <= 0 or non-finite value)";
+    case ECMG_ERR_OOM: return "device allocation failed";
+    case ECMG_ERR_CUDA: return "CUDA runtime error";
+    }
+    return "unknown status";
+}
+
+const char* ecmg_last_error(void) { return g_last_error.c_str(); }
+
+ecmg_status ecmg_kernel_launches(uint64_t* out)
+{
+    if (!out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    *out = launches_setup() + launches_jcg() + launches_exp();
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,
+                             double* ms_out, double* bytes_out)
+{
+    if (!h || !ms_out || !bytes_out || reps < 1) return fail(ECMG_ERR_INVALID_ARG, "bad argument");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    if (which < 0 || which > 7) return fail(ECMG_ERR_INVALID_ARG, "bad kernel selector");
+    Level& v = h->lv[l];
+    if (which <= 2 && !v.r32) return fail(ECMG_ERR_INVALID_ARG, "handle has no FP32 vectors");
+    if (which >= 6 && l < 2) return fail(ECMG_ERR_INVALID_ARG, "EXP kernels need level >= 2");
+    const double N = (double)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1);
+    const double E = (double)v.g.nx * v.g.ny * v.g.nz;
+    const double bytes[8] = {28 * N + 4 * E, 16 * N, 24 * N + 8 * E, 56 * N + 8 * E,
+                             32 * N,         32 * N + 8 * E, 16 * N + 8 * (N / 8 + N / 64), 17 * N};
+    *bytes_out = bytes[which];
+    SolveState* st = h->states + (MAX_LEVELS - 1);  // scratch state, never used by a solve
+    SolveState tmpl = {};
+    tmpl.rho = 1.0;
+    tmpl.beta = 0.5;
+    tmpl.alpha = 1e-30;
+    tmpl.alpha_prev = 1e-30;
+    tmpl.max_iters = 1 << 30;
+    tmpl.thresh2 = -1.0;
+    tmpl.inner2 = -1.0;
+    cudaStream_t s = h->user_stream;
+    const CondHandles none{0, 0, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double total = 0.0;
+    try {
+        ck(cudaEventCreate(&e0));
+        ck(cudaEventCreate(&e1));
+        for (int rep = 0; rep <= reps; ++rep) {
+            ck(cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s));
+            ck(cudaEventRecord(e0, s));
+            switch (which) {
+            case 0: launch_pq32(v.g, v.op, v.beta32, v.r32, v.dinv32, v.pA32, v.pB32, v.q32, v.e32, st, h->part, 1, none, s); break;
+            case 1: launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
+            case 2: launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
+            case 3: launch_pq64(v.g, v.op, v.beta, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
+            case 4: launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, none, s); break;
+            case 5: launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, s); break;
+            case 6: {
+                const Level& u1 = h->lv[l - 1];
+                const Level& u0 = h->lv[l - 2];
+                launch_exp_finite(h->opt.exp_variant, v.g, v.op, u1.g, u1.U, u0.g, u0.U, v.r, v.q, s);
+                break;
+            }
+            default: {
+                const Level& u1 = h->lv[l - 1];
+                launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, s);
+                break;
+            }
+            }
+            ck(cudaEventRecord(e1, s));
+            ck(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) total += ms;
+        }
+        ck(cudaGetLastError());
+    } catch (CudaFail& f) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = total / reps;
+    return ECMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// ecmg_internal.cuh -- shared definitions of the CUDA implementation of ECMG_jcg.
+//
+// Device data layout (every vector of a level, nodal or element, FP64 or FP32):
+//   node (i, j, k), i in -1..nx+1 (one ghost layer on each side), is stored at
+//       off(i, j, k) = (k + 1) * plane + (j + 1) * pitch + (i + XL)
+//   with XL = 4 (so node i = 0 starts a 16-byte aligned run for both FP64 and FP32) and
+//   pitch = round_up(nx + 1 + XL + 2, 32) elements. Element (ex, ey, ez) of the level is
+//   stored at the offset of its lowest corner node, so elements -1..nx are addressable and
+//   the ghost elements hold beta = 0. Ghost entries are zero and are never written; a kernel
+//   may therefore read the 27 neighbours of any owned node, and the 8 elements around it,
+//   without bounds checks.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ecmg {
+
+constexpr int XL = 4;            // left pad in elements (16 B for FP32, 32 B for FP64)
+constexpr int MAX_LEVELS = 16;
+
+struct Grid {
+    int nx, ny, nz;              // elements per axis
+    int pitch;                   // row pitch in elements
+    int64_t plane;               // plane pitch in elements
+    int64_t total;               // elements in one stored vector
+    double h[3];                 // element sides
+    __host__ __device__ int64_t off(int i, int j, int k) const {
+        return (int64_t)(k + 1) * plane + (int64_t)(j + 1) * pitch + (i + XL);
+    }
+};
+
+// Operator of one level (Sec. 2): per-element stiffness entries by neighbour class for
+// beta = 1, and the Robin face terms.  For the element matrix
+//   K = kx(x)my(x)mz + mx(x)ky(x)mz + mx(x)my(x)kz,  k(0) = 1/h, k(1) = -1/h, m(0) = h/3,
+//   m(1) = h/6,
+// the entry between two nodes of one element depends only on which axes differ:
+//   w_c: all three differ; w_e[a]: the two axes other than a differ; w_f[a]: only axis a
+//   differs; w_0: same node.
+struct Op {
+    double w0, wc, we[3], wf[3];
+    // Robin: alpha on each face (0 when Dirichlet or Neumann) and the in-face 1D mass entries
+    double alpha[6];
+    int bc[6];                   // 0 Dirichlet, 1 Robin
+};
+
+__host__ inline Op make_op(const double h[3], const int bc[6], const double alpha[6])
+{
+    Op o;
+    auto k = [&](int a, int d) { return (d ? -1.0 : 1.0) / h[a]; };
+    auto m = [&](int a, int d) { return h[a] * (d ? 1.0 : 2.0) / 6.0; };
+    auto K = [&](int dx, int dy, int dz) {
+        return k(0, dx) * m(1, dy) * m(2, dz) + m(0, dx) * k(1, dy) * m(2, dz) +
+               m(0, dx) * m(1, dy) * k(2, dz);
+    };
+    o.w0 = K(0, 0, 0);
+    o.wc = K(1, 1, 1);
+    o.we[0] = K(0, 1, 1);
+    o.we[1] = K(1, 0, 1);
+    o.we[2] = K(1, 1, 0);
+    o.wf[0] = K(1, 0, 0);
+    o.wf[1] = K(0, 1, 0);
+    o.wf[2] = K(0, 0, 1);
+    for (int f = 0; f < 6; ++f) {
+        o.bc[f] = bc[f];
+        o.alpha[f] = (bc[f] == 1) ? alpha[f] : 0.0;
+    }
+    return o;
+}
+
+// Device-side state of one JCG / mixed solve on one level. Written by the last block of each
+// reducing kernel, read by the next kernel. All scalars FP64.
+struct SolveState {
+    double rho;          // r . z of the current residual
+    double pq;           // p . q of the current iteration
+    double alpha;        // step of the current iteration
+    double alpha_prev;   // step not yet applied to the iterate (deferred update)
+    double beta;         // coefficient of the next search direction
+    double rr;           // ||r||^2, recursive (or true right after a residual evaluation)
+    double rr_ref;       // MIXED: ||r||^2 at the last FP64 residual replacement
+    double thresh2;      // (rtol ||f_h||)^2
+    double fh2;          // ||f_h||^2
+    double inner2;       // MIXED: inner_rtol^2
+    double rr_true;      // last true ||r||^2
+    double rtol2;        // rtol^2
+    int iters;           // JCG iterations done
+    int updates;         // MIXED: FP64 residual replacements done
+    int max_iters;
+    int status;          // 0 running/ok, 3 no convergence, 4 breakdown
+    int done;            // 1 when the level has finished
+    int need_update;     // MIXED: 1 when the next step is an FP64 residual replacement
+    int stop_after_update; // MIXED: iteration cap reached, finish after the next replacement
+    int p_latest;        // which of the two search-direction buffers holds the newest p
+    unsigned int arrive; // block arrival counter of the last-block reductions
+};
+
+// Launch helper of one reducing kernel: where its per-block partial sums go.
+struct Partials {
+    double* buf;         // >= 3 * max_blocks doubles
+    int max_blocks;
+};
+
+// ---- set-up kernels (setup.cu) -------------------------------------------------------
+void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s);
+void pack_elements(const Grid& g, const double* dense, double* dst, cudaStream_t s);
+void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s);
+void coarsen_beta(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
+void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, cudaStream_t s);
+void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
+void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
+                cudaStream_t s);
+void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
+                 float* beta32, cudaStream_t s);
+void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x,
+                         cudaStream_t s);
+void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+
+// Kernel executions counted on the device, per source file (for the benchmark's launch count).
+unsigned long long launches_setup();
+unsigned long long launches_jcg();
+unsigned long long launches_exp();
+
+}  // namespace ecmg

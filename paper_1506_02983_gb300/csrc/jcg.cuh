@@ -1,0 +1,63 @@
+// jcg.cuh -- host-side launch interface of the JCG kernels (jcg.cu).
+#pragma once
+
+#include "ecmg_internal.cuh"
+
+namespace ecmg {
+
+// What the last block of a residual evaluation does with ||r||^2 and r.z.
+enum ResMode : int {
+    RES_FH2 = 0,      // store ||f_h||^2 (x = Dirichlet extension) and the stopping threshold
+    RES_INIT = 1,     // initial residual of a level: start JCG (or finish with 0 iterations)
+    RES_REPLACE = 2,  // MIXED: FP64 residual replacement after folding the FP32 correction
+    RES_REPORT = 3    // report the true residual after JCG has stopped
+};
+
+struct CondHandles {
+    cudaGraphConditionalHandle loop;   // WHILE node of the level's JCG loop
+    cudaGraphConditionalHandle update; // MIXED: IF node of the residual replacement
+    int use;                           // 0 when the kernels run outside a graph
+};
+
+// Tiled z-marching stencil launches.
+// p_new = dinv r + beta p_old on the fly; q = A p_new; x += alpha_prev p_old; state.alpha.
+void launch_pq64(const Grid& g, const Op& op, const double* beta, const double* r,
+                 const double* dinv, const double* pold, double* pnew, double* q, double* x,
+                 SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
+void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
+                 const float* dinv, const float* pold, float* pnew, float* q, float* e,
+                 SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
+// r = b - A x (FP64 arithmetic) on free nodes, 0 on Dirichlet nodes; r stored as double or
+// float; ||r||^2 and r.dinv.r reduced; last block acts by ResMode.
+void launch_res64(const Grid& g, const Op& op, const double* beta, const double* x,
+                  const double* b, const double* dinv, double* r, SolveState* st, Partials pr,
+                  ResMode mode, CondHandles ch, cudaStream_t s);
+void launch_res32(const Grid& g, const Op& op, const double* beta, const double* x,
+                  const double* b, const float* dinv, float* r, SolveState* st, Partials pr,
+                  ResMode mode, CondHandles ch, cudaStream_t s);
+// y = A x with the full matrix (no boundary masking), FP64 or FP32 arithmetic.
+void launch_apply64(const Grid& g, const Op& op, const double* beta, const double* x, double* y,
+                    cudaStream_t s);
+void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y,
+                    cudaStream_t s);
+
+// r -= alpha q; z = dinv r; r.z and r.r; last block: convergence / next beta.
+void launch_update64(const Grid& g, double* r, const double* q, const double* dinv,
+                     SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);
+void launch_update32(const Grid& g, float* r, const float* q, const float* dinv,
+                     SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);
+
+// x += alpha_prev p_latest (FP64 JCG exit).
+void launch_final64(const Grid& g, double* x, const double* pA, const double* pB,
+                    SolveState* st, cudaStream_t s);
+// MIXED: x64 += e + alpha_prev p; e = 0.
+void launch_fold32(const Grid& g, double* x, float* e, const float* p, SolveState* st,
+                   cudaStream_t s);
+// Reset the level state before a solve.
+void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters,
+                       cudaStream_t s);
+
+int max_stencil_blocks(const Grid& g);
+int max_stream_blocks();
+
+}  // namespace ecmg

@@ -1,0 +1,285 @@
+// setup.cu -- per-level set-up of Alg. 4: packing of the caller's finest arrays into the
+// ghost-padded device layout, beta averaging, injection, load vectors (Sec. 2) and the
+// Jacobi diagonal of JCG. All of it runs once per level per solve; FP64 throughout.
+#include "ecmg_internal.cuh"
+
+namespace ecmg {
+
+namespace {
+
+__device__ unsigned long long g_launches = 0;  // kernel executions of this file
+#define COUNT_LAUNCH()                                                                   \
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0) \
+        atomicAdd(&g_launches, 1ull)
+
+constexpr int TPB = 256;
+
+inline int blocks_for(int64_t n) { return (int)((n + TPB - 1) / TPB); }
+
+__device__ __forceinline__ bool on_dirichlet(const Grid& g, const Op& op, int i, int j, int k)
+{
+    return (i == 0 && op.bc[0] == 0) || (i == g.nx && op.bc[1] == 0) ||
+           (j == 0 && op.bc[2] == 0) || (j == g.ny && op.bc[3] == 0) ||
+           (k == 0 && op.bc[4] == 0) || (k == g.nz && op.bc[5] == 0);
+}
+
+__global__ void k_pack_nodal(Grid g, const double* __restrict__ dense, double* __restrict__ dst)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % (g.nx + 1));
+    int64_t r = t / (g.nx + 1);
+    int j = (int)(r % (g.ny + 1));
+    int k = (int)(r / (g.ny + 1));
+    dst[g.off(i, j, k)] = dense[t];
+}
+
+__global__ void k_unpack_nodal(Grid g, const double* __restrict__ src, double* __restrict__ dense)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % (g.nx + 1));
+    int64_t r = t / (g.nx + 1);
+    int j = (int)(r % (g.ny + 1));
+    int k = (int)(r / (g.ny + 1));
+    dense[t] = src[g.off(i, j, k)];
+}
+
+__global__ void k_pack_elements(Grid g, const double* __restrict__ dense, double* __restrict__ dst)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % g.nx);
+    int64_t r = t / g.nx;
+    int j = (int)(r % g.ny);
+    int k = (int)(r / g.ny);
+    dst[g.off(i, j, k)] = dense[t];
+}
+
+// Coarse element = mean of its 8 children, summed x fastest then y then z.
+__global__ void k_coarsen_beta(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)gc.nx * gc.ny * gc.nz;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % gc.nx);
+    int64_t r = t / gc.nx;
+    int j = (int)(r % gc.ny);
+    int k = (int)(r / gc.ny);
+    double s = 0.0;
+    for (int c = 0; c < 8; ++c)
+        s += bf[gf.off(2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + (c >> 2))];
+    bc[gc.off(i, j, k)] = s / 8.0;
+}
+
+__global__ void k_inject(Grid gc, const double* __restrict__ vf, Grid gf, double* __restrict__ vc)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)(gc.nx + 1) * (gc.ny + 1) * (gc.nz + 1);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % (gc.nx + 1));
+    int64_t r = t / (gc.nx + 1);
+    int j = (int)(r % (gc.ny + 1));
+    int k = (int)(r / (gc.ny + 1));
+    vc[gc.off(i, j, k)] = vf[gf.off(2 * i, 2 * j, 2 * k)];
+}
+
+// b_c = P^T b_f with P trilinear prolongation: fine node 2I + d contributes with weight
+// prod_a w(d_a), w(0) = 1, w(+-1) = 1/2. Fine ghost nodes hold 0, so no bounds checks.
+__global__ void k_restrict(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)(gc.nx + 1) * (gc.ny + 1) * (gc.nz + 1);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % (gc.nx + 1));
+    int64_t r = t / (gc.nx + 1);
+    int j = (int)(r % (gc.ny + 1));
+    int k = (int)(r / (gc.ny + 1));
+    double s = 0.0;
+    for (int dk = -1; dk <= 1; ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);
+                s += w * bf[gf.off(2 * i + di, 2 * j + dj, 2 * k + dk)];
+            }
+    bc[gc.off(i, j, k)] = s;
+}
+
+// Element count along one axis between node index a and a + d (d in -1..1).
+__device__ __forceinline__ int cnt1(int a, int n, int d)
+{
+    if (d < 0) return a >= 1;
+    if (d > 0) return a < n;
+    return (a >= 1) + (a < n);
+}
+
+// b = M f_I + sum over Robin faces of M_F gR_I (consistent mass matrices of Sec. 2). The
+// element mass is a tensor product, so the assembled row is prod_a cnt_a(d_a) m_a(d_a) with
+// m(0) = h/3, m(+-1) = h/6 per element.
+__global__ void k_nodal_load(Grid g, Op op, const double* __restrict__ f,
+                             const double* __restrict__ gR, double* __restrict__ b)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % (g.nx + 1));
+    int64_t r = t / (g.nx + 1);
+    int j = (int)(r % (g.ny + 1));
+    int k = (int)(r / (g.ny + 1));
+    const int idx[3] = {i, j, k};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    double wa[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int d = -1; d <= 1; ++d)
+            wa[a][d + 1] = cnt1(idx[a], nn[a], d) * g.h[a] * (d ? 1.0 : 2.0) / 6.0;
+    double s = 0.0;
+    for (int dk = -1; dk <= 1; ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                double w = wa[0][di + 1] * wa[1][dj + 1] * wa[2][dk + 1];
+                if (w != 0.0) s += w * f[g.off(i + di, j + dj, k + dk)];
+            }
+    if (gR) {
+        for (int fc = 0; fc < 6; ++fc) {
+            if (op.bc[fc] != 1) continue;
+            int an = fc / 2;
+            if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
+            int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
+            for (int db = -1; db <= 1; ++db)
+                for (int da = -1; da <= 1; ++da) {
+                    double w = cnt1(idx[aa], nn[aa], da) * g.h[aa] * (da ? 1.0 : 2.0) / 6.0 *
+                               cnt1(idx[ab], nn[ab], db) * g.h[ab] * (db ? 1.0 : 2.0) / 6.0;
+                    if (w == 0.0) continue;
+                    int o[3] = {0, 0, 0};
+                    o[aa] = da;
+                    o[ab] = db;
+                    s += w * gR[g.off(i + o[0], j + o[1], k + o[2])];
+                }
+        }
+    }
+    b[g.off(i, j, k)] = s;
+}
+
+// Jacobi diagonal: diag = w0 * (sum of the 8 element betas) + Robin face mass diagonal.
+// Dirichlet nodes get dinv = 0, which also masks them in every JCG kernel.
+__global__ void k_jacobi(Grid g, Op op, const double* __restrict__ beta, double* __restrict__ dinv64,
+                         float* __restrict__ dinv32, float* __restrict__ beta32)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % (g.nx + 1));
+    int64_t r = t / (g.nx + 1);
+    int j = (int)(r % (g.ny + 1));
+    int k = (int)(r / (g.ny + 1));
+    const int64_t o = g.off(i, j, k);
+    if (beta32 && i < g.nx && j < g.ny && k < g.nz) beta32[o] = (float)beta[o];
+    double B = 0.0;
+    for (int c = 0; c < 8; ++c)
+        B += beta[g.off(i - 1 + (c & 1), j - 1 + ((c >> 1) & 1), k - 1 + (c >> 2))];
+    double d = op.w0 * B;
+    const int idx[3] = {i, j, k};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int fc = 0; fc < 6; ++fc) {
+        if (op.alpha[fc] == 0.0) continue;
+        int an = fc / 2;
+        if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
+        int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
+        d += op.alpha[fc] * cnt1(idx[aa], nn[aa], 0) * g.h[aa] / 3.0 *
+             cnt1(idx[ab], nn[ab], 0) * g.h[ab] / 3.0;
+    }
+    double v = on_dirichlet(g, op, i, j, k) ? 0.0 : 1.0 / d;
+    dinv64[o] = v;
+    if (dinv32) dinv32[o] = (float)v;
+}
+
+// x = g_D on Dirichlet nodes, 0 on free nodes (gD == nullptr: zero everywhere).
+__global__ void k_dirichlet_ext(Grid g, Op op, const double* __restrict__ gD, double* __restrict__ x)
+{
+    COUNT_LAUNCH();
+    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = (int)(t % (g.nx + 1));
+    int64_t r = t / (g.nx + 1);
+    int j = (int)(r % (g.ny + 1));
+    int k = (int)(r / (g.ny + 1));
+    const int64_t o = g.off(i, j, k);
+    x[o] = (gD && on_dirichlet(g, op, i, j, k)) ? gD[o] : 0.0;
+}
+
+__global__ void k_convert_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n)
+{
+    COUNT_LAUNCH();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
+}
+
+inline int64_t nodes(const Grid& g) { return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
+
+}  // namespace
+
+void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s)
+{
+    int b = blocks_for(n);
+    k_convert_f32<<<b < 4096 ? b : 4096, TPB, 0, s>>>(src, dst, n);
+}
+
+void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s)
+{
+    k_pack_nodal<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, dense, dst);
+}
+void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s)
+{
+    k_unpack_nodal<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, src, dense);
+}
+void pack_elements(const Grid& g, const double* dense, double* dst, cudaStream_t s)
+{
+    k_pack_elements<<<blocks_for((int64_t)g.nx * g.ny * g.nz), TPB, 0, s>>>(g, dense, dst);
+}
+void coarsen_beta(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s)
+{
+    k_coarsen_beta<<<blocks_for((int64_t)gc.nx * gc.ny * gc.nz), TPB, 0, s>>>(gc, bf, gf, bc);
+}
+void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, cudaStream_t s)
+{
+    k_inject<<<blocks_for(nodes(gc)), TPB, 0, s>>>(gc, vf, gf, vc);
+}
+void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s)
+{
+    k_restrict<<<blocks_for(nodes(gc)), TPB, 0, s>>>(gc, bf, gf, bc);
+}
+void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
+                cudaStream_t s)
+{
+    k_nodal_load<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, f, gR, b);
+}
+void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
+                 float* beta32, cudaStream_t s)
+{
+    k_jacobi<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, beta, dinv64, dinv32, beta32);
+}
+void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x, cudaStream_t s)
+{
+    k_dirichlet_ext<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, gD, x);
+}
+
+unsigned long long launches_setup()
+{
+    unsigned long long v = 0;
+    cudaMemcpyFromSymbol(&v, g_launches, sizeof(v));
+    return v;
+}
+
+}  // namespace ecmg
