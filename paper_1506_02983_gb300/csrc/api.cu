@@ -20,6 +20,7 @@
 #include "ecmg_internal.cuh"
 #include "exp.cuh"
 #include "jcg.cuh"
+#include "pq_tma.cuh"
 
 using namespace ecmg;
 
@@ -46,6 +47,8 @@ struct Level {
     // FP32 vectors (mixed precision)
     float *beta32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *pA32 = nullptr, *pB32 = nullptr,
           *q32 = nullptr, *e32 = nullptr;
+    PlaneMaps maps;  // TMA descriptors of the FP32 vectors
+    int* uniform = nullptr;  // device flag: one beta on the whole level
 };
 
 }  // namespace
@@ -229,6 +232,7 @@ void record_setup(Rec& R)
             nodal_load(v.g, v.op, v.f, p.g_R ? v.gR : nullptr, v.b, s);
         }
         jacobi_diag(v.g, v.op, v.beta, v.dinv, mixed ? v.dinv32 : nullptr, mixed ? v.beta32 : nullptr, s);
+        uniform_check(v.g, v.beta, v.uniform, s);
     }
 }
 
@@ -246,7 +250,7 @@ void record_level(Rec& R, int l)
 
     launch_state_init(st, rtol, o.inner_rtol, o.max_iters, R.s());
     dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s());
-    launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_FH2, none, R.s());
+    launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_FH2, none, R.s());
     if (!direct) {
         const Level& u1 = h->lv[l - 1];
         const Level& u0 = h->lv[l - 2];
@@ -259,19 +263,19 @@ void record_level(Rec& R, int l)
         ck(cudaMemsetAsync(v.pA, 0, (size_t)v.g.total * 8, R.s()));
         ck(cudaMemsetAsync(v.pB, 0, (size_t)v.g.total * 8, R.s()));
         auto half = [&](CondHandles ch, const double* pin, double* pout, int idx) {
-            launch_pq64(v.g, v.op, v.beta, v.r, v.dinv, pin, pout, v.q, v.U, st, h->part, idx, ch, R.s());
+            launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, pin, pout, v.q, v.U, st, h->part, idx, ch, R.s());
             launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, ch, R.s());
         };
         if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
             const CondHandles ch{loop, 0, 1};
-            launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_INIT, ch, R.s());
+            launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_INIT, ch, R.s());
             R.open(loop, cudaGraphCondTypeWhile);
             half(ch, v.pA, v.pB, 1);
             half(ch, v.pB, v.pA, 0);
             R.close();
         } else {
-            launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_INIT, none, R.s());
+            launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_INIT, none, R.s());
             SolveState hs;
             host_state(h, l, &hs);
             int parity = 0;
@@ -284,22 +288,22 @@ void record_level(Rec& R, int l)
         }
         launch_final64(v.g, v.U, v.pA, v.pB, st, R.s());
         if (o.true_residual)
-            launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, R.s());
+            launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, R.s());
     } else {
         ck(cudaMemsetAsync(v.pA32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
         auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
-            launch_pq32(v.g, v.op, v.beta32, v.r32, v.dinv32, pin, pout, v.q32, v.e32, st, h->part, idx, ch, R.s());
+            launch_pq32_tma(v.maps, pin == v.pB32, v.g, v.op, pout, v.q32, v.e32, st, h->part, idx, ch, R.s());
             launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
         };
         auto replace = [&](float* pnew) {
             launch_fold32(v.g, v.U, v.e32, pnew, st, R.s());
-            launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPLACE, none, R.s());
+            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPLACE, none, R.s());
         };
         if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
-            launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT,
+            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT,
                          CondHandles{loop, 0, 1}, R.s());
             R.open(loop, cudaGraphCondTypeWhile);
             for (int half = 0; half < 2; ++half) {
@@ -314,7 +318,7 @@ void record_level(Rec& R, int l)
             }
             R.close();
         } else {
-            launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT, none, R.s());
+            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT, none, R.s());
             SolveState hs;
             host_state(h, l, &hs);
             int parity = 0;
@@ -438,6 +442,7 @@ ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, u
         Grid g = make_grid(*p, l);
         b += level_bytes(g, o->precision == ECMG_MIXED);
         maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
+        if (o->precision == ECMG_MIXED) maxb = std::max(maxb, max_tma_blocks(g));
     }
     b += (uint64_t)maxb * 3 * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
     *bytes = b;
@@ -487,12 +492,19 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
                 v.pB32 = dalloc<float>(h, n);
                 v.q32 = dalloc<float>(h, n);
                 v.e32 = dalloc<float>(h, n);
+                if (!make_plane_map(&v.maps.r, v.r32, v.g) || !make_plane_map(&v.maps.pA, v.pA32, v.g) ||
+                    !make_plane_map(&v.maps.pB, v.pB32, v.g) || !make_plane_map(&v.maps.dinv, v.dinv32, v.g) ||
+                    !make_plane_map(&v.maps.beta, v.beta32, v.g))
+                    throw CudaFail{cudaErrorNotSupported};
+                maxb = std::max(maxb, max_tma_blocks(v.g));
             }
             maxb = std::max(maxb, std::max(max_stencil_blocks(v.g), max_stream_blocks()));
         }
         h->part.buf = dalloc<double>(h, (int64_t)maxb * 3);
         h->part.max_blocks = maxb;
         h->states = dalloc<SolveState>(h, MAX_LEVELS);
+        int* flags = dalloc<int>(h, MAX_LEVELS);
+        for (int l = 0; l < h->L; ++l) h->lv[l].uniform = flags + l;
         h->norm_part = dalloc<double>(h, 2048);
         ck(cudaMallocHost(&h->host_states, sizeof(SolveState) * MAX_LEVELS));
         ck(cudaMallocHost(&h->host_norms, sizeof(double) * 2048));
@@ -585,7 +597,7 @@ ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision
         convert_f32(v.r, v.r32, v.g.total, s);
         launch_apply32(v.g, v.op, v.beta32, v.r32, v.q, s);
     } else if (precision == ECMG_FP64) {
-        launch_apply64(v.g, v.op, v.beta, v.r, v.q, s);
+        launch_apply64(v.g, v.op, v.beta, v.uniform, v.r, v.q, s);
     } else {
         return fail(ECMG_ERR_INVALID_ARG, "bad precision");
     }
@@ -656,7 +668,7 @@ const char* ecmg_last_error(void) { return g_last_error.c_str(); }
 ecmg_status ecmg_kernel_launches(uint64_t* out)
 {
     if (!out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
-    *out = launches_setup() + launches_jcg() + launches_exp();
+    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma();
     return ECMG_OK;
 }
 
@@ -695,12 +707,12 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
             ck(cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s));
             ck(cudaEventRecord(e0, s));
             switch (which) {
-            case 0: launch_pq32(v.g, v.op, v.beta32, v.r32, v.dinv32, v.pA32, v.pB32, v.q32, v.e32, st, h->part, 1, none, s); break;
+            case 0: launch_pq32_tma(v.maps, 0, v.g, v.op, v.pB32, v.q32, v.e32, st, h->part, 1, none, s); break;
             case 1: launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
-            case 2: launch_res32(v.g, v.op, v.beta, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
-            case 3: launch_pq64(v.g, v.op, v.beta, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
+            case 2: launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
+            case 3: launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
             case 4: launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, none, s); break;
-            case 5: launch_res64(v.g, v.op, v.beta, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, s); break;
+            case 5: launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, s); break;
             case 6: {
                 const Level& u1 = h->lv[l - 1];
                 const Level& u0 = h->lv[l - 2];

@@ -26,8 +26,13 @@ struct Grid {
     int64_t total;               // elements in one stored vector
     double h[3];                 // element sides
     __host__ __device__ int64_t off(int i, int j, int k) const {
-        return (int64_t)(k + 1) * plane + (int64_t)(j + 1) * pitch + (i + XL);
+        return plane_base(k) + in_plane(i, j);
     }
+    // 64-bit offset of node plane k, and the 32-bit offset of (i, j) inside a plane. Kernels
+    // that visit many nodes of one plane form the product once: wide integer multiplies are
+    // not free on GB300.
+    __host__ __device__ int64_t plane_base(int k) const { return (int64_t)(k + 1) * plane; }
+    __host__ __device__ int in_plane(int i, int j) const { return (j + 1) * pitch + (i + XL); }
 };
 
 // Operator of one level (Sec. 2): per-element stiffness entries by neighbour class for
@@ -39,6 +44,8 @@ struct Grid {
 //   differs; w_0: same node.
 struct Op {
     double w0, wc, we[3], wf[3];
+    int cube;                    // 1 when hx = hy = hz (face weights 0, edge weight = corner weight)
+    float wc32, we32[3], wf32[3];  // the same weights rounded to FP32 on the host
     // Robin: alpha on each face (0 when Dirichlet or Neumann) and the in-face 1D mass entries
     double alpha[6];
     int bc[6];                   // 0 Dirichlet, 1 Robin
@@ -61,6 +68,12 @@ __host__ inline Op make_op(const double h[3], const int bc[6], const double alph
     o.wf[0] = K(1, 0, 0);
     o.wf[1] = K(0, 1, 0);
     o.wf[2] = K(0, 0, 1);
+    o.cube = (h[0] == h[1] && h[1] == h[2]) ? 1 : 0;
+    o.wc32 = (float)o.wc;
+    for (int a = 0; a < 3; ++a) {
+        o.we32[a] = (float)o.we[a];
+        o.wf32[a] = (float)o.wf[a];
+    }
     for (int f = 0; f < 6; ++f) {
         o.bc[f] = bc[f];
         o.alpha[f] = (bc[f] == 1) ? alpha[f] : 0.0;
@@ -114,6 +127,8 @@ void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64
 void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x,
                          cudaStream_t s);
 void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+// flag = 1 when every element of the level has the same beta, else 0.
+void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s);
 
 // Kernel executions counted on the device, per source file (for the benchmark's launch count).
 unsigned long long launches_setup();

@@ -10,11 +10,9 @@
 // stopping test of Alg. 4 line 7 and beta after K2. Inside a CUDA graph it also sets the
 // condition of the level's WHILE node, so a level runs with no host round trip.
 //
-// The stencil: with S_d(i) the sum of beta over the elements that contain both node i and
-// node i+d, and K(d) the beta=1 element matrix entry for that offset class,
-//     (A v)_i = sum_{d != 0} K(d) S_d(i) (v_{i+d} - v_i) + Robin face terms,
-// which holds because every element matrix has zero row sums (Sec. 2 bilinear form).
+// The operator at a node is q1_apply (stencil_core.cuh).
 #include "jcg.cuh"
+#include "stencil_core.cuh"
 
 #include <cmath>
 
@@ -30,13 +28,6 @@ constexpr int BX = 32, BY = 8, NT = BX * BY;
 constexpr int KZ_TARGET = 64;
 constexpr int UPD_TPB = 256;
 constexpr int UPD_MAX_BLOCKS = 152 * 8;
-
-__device__ __forceinline__ bool on_dirichlet(const Grid& g, const Op& op, int i, int j, int k)
-{
-    return (i == 0 && op.bc[0] == 0) || (i == g.nx && op.bc[1] == 0) ||
-           (j == 0 && op.bc[2] == 0) || (j == g.ny && op.bc[3] == 0) ||
-           (k == 0 && op.bc[4] == 0) || (k == g.nz && op.bc[5] == 0);
-}
 
 // ---- compensated FP32 accumulation ------------------------------------------------------
 // Products are split exactly (TwoProduct with an FMA) and summed with TwoSum, so a thread's
@@ -130,7 +121,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NP], double* partials, unsi
 // Each block owns a BX x BY column of nodes over planes [kb, ke). Three node planes of the
 // operand (k-1, k, k+1) and two element slabs of beta (k-1, k) live in shared memory; the
 // operand of a plane is produced by src(offset), so K1 can form p on the fly.
-template <typename VT, typename BT, typename SRC, typename BODY>
+template <bool ROBIN, bool CUBE, typename VT, typename BT, typename SRC, typename BODY>
 __device__ __forceinline__ void march(const Grid& g, const Op& op, const BT* __restrict__ beta,
                                       int kz, SRC src, BODY body)
 {
@@ -140,28 +131,27 @@ __device__ __forceinline__ void march(const Grid& g, const Op& op, const BT* __r
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int kb = blockIdx.z * kz;
     const int ke = min(kb + kz, g.nz + 1);
-    const VT wf0 = (VT)op.wf[0], wf1 = (VT)op.wf[1], wf2 = (VT)op.wf[2];
-    const VT we0 = (VT)op.we[0], we1 = (VT)op.we[1], we2 = (VT)op.we[2], wc = (VT)op.wc;
-    const bool any_robin = (op.alpha[0] != 0.0) | (op.alpha[1] != 0.0) | (op.alpha[2] != 0.0) |
-                           (op.alpha[3] != 0.0) | (op.alpha[4] != 0.0) | (op.alpha[5] != 0.0);
+    const Weights<VT> wts(op);
 
     auto load_plane = [&](int k) {
         VT(*dst)[BX + 2] = sv[(k + 3) % 3];
+        const int64_t base = g.plane_base(k);
         for (int c = tid; c < (BX + 2) * (BY + 2); c += NT) {
             const int ci = c % (BX + 2), cj = c / (BX + 2);
             const int i = i0 - 1 + ci, j = j0 - 1 + cj;
             VT v = VT(0);
-            if (i <= g.nx + 1 && j <= g.ny + 1) v = src(g.off(i, j, k));
+            if (i <= g.nx + 1 && j <= g.ny + 1) v = src(base + g.in_plane(i, j));
             dst[cj][ci] = v;
         }
     };
     auto load_slab = [&](int ez) {
         VT(*dst)[BX + 1] = sb[(ez + 2) % 2];
+        const int64_t base = g.plane_base(ez);
         for (int c = tid; c < (BX + 1) * (BY + 1); c += NT) {
             const int ci = c % (BX + 1), cj = c / (BX + 1);
             const int ex = i0 - 1 + ci, ey = j0 - 1 + cj;
             VT v = VT(0);
-            if (ex <= g.nx + 1 && ey <= g.ny + 1) v = (VT)beta[g.off(ex, ey, ez)];
+            if (ex <= g.nx + 1 && ey <= g.ny + 1) v = (VT)beta[base + g.in_plane(ex, ey)];
             dst[cj][ci] = v;
         }
     };
@@ -175,86 +165,173 @@ __device__ __forceinline__ void march(const Grid& g, const Op& op, const BT* __r
         __syncthreads();
         const int i = i0 + tx, j = j0 + ty;
         if (i <= g.nx && j <= g.ny) {
-            const int pl[3] = {(k + 2) % 3, k % 3, (k + 1) % 3};
+            const int pm = (k + 2) % 3, p0 = k % 3, pp = (k + 1) % 3;
             const int s0 = (k + 1) % 2, s1 = k % 2;
-            auto V = [&](int dx, int dy, int dz) -> VT { return sv[pl[dz + 1]][ty + 1 + dy][tx + 1 + dx]; };
+            auto V = [&](int dx, int dy, int dz) -> VT {
+                return sv[dz < 0 ? pm : (dz > 0 ? pp : p0)][ty + 1 + dy][tx + 1 + dx];
+            };
             const VT xc = V(0, 0, 0);
-            // betas of the 8 elements around the node: b<ex><ey><ez>
-            const VT b000 = sb[s0][ty][tx], b100 = sb[s0][ty][tx + 1];
-            const VT b010 = sb[s0][ty + 1][tx], b110 = sb[s0][ty + 1][tx + 1];
-            const VT b001 = sb[s1][ty][tx], b101 = sb[s1][ty][tx + 1];
-            const VT b011 = sb[s1][ty + 1][tx], b111 = sb[s1][ty + 1][tx + 1];
-            // pair sums over the axis the offset does not cross
-            const VT sx00 = b000 + b100, sx01 = b010 + b110, sx10 = b001 + b101, sx11 = b011 + b111;  // [ez][ey]
-            const VT sy00 = b000 + b010, sy01 = b100 + b110, sy10 = b001 + b011, sy11 = b101 + b111;  // [ez][ex]
-            const VT sz00 = b000 + b001, sz01 = b100 + b101, sz10 = b010 + b011, sz11 = b110 + b111;  // [ey][ex]
-            const VT fx = (sz01 + sz11) * (V(1, 0, 0) - xc) + (sz00 + sz10) * (V(-1, 0, 0) - xc);
-            const VT fy = (sx01 + sx11) * (V(0, 1, 0) - xc) + (sx00 + sx10) * (V(0, -1, 0) - xc);
-            const VT fz = (sx10 + sx11) * (V(0, 0, 1) - xc) + (sx00 + sx01) * (V(0, 0, -1) - xc);
-            const VT ex = sx00 * (V(0, -1, -1) - xc) + sx01 * (V(0, 1, -1) - xc) +
-                          sx10 * (V(0, -1, 1) - xc) + sx11 * (V(0, 1, 1) - xc);
-            const VT ey = sy00 * (V(-1, 0, -1) - xc) + sy01 * (V(1, 0, -1) - xc) +
-                          sy10 * (V(-1, 0, 1) - xc) + sy11 * (V(1, 0, 1) - xc);
-            const VT ez = sz00 * (V(-1, -1, 0) - xc) + sz01 * (V(1, -1, 0) - xc) +
-                          sz10 * (V(-1, 1, 0) - xc) + sz11 * (V(1, 1, 0) - xc);
-            const VT cc = b000 * (V(-1, -1, -1) - xc) + b100 * (V(1, -1, -1) - xc) +
-                          b010 * (V(-1, 1, -1) - xc) + b110 * (V(1, 1, -1) - xc) +
-                          b001 * (V(-1, -1, 1) - xc) + b101 * (V(1, -1, 1) - xc) +
-                          b011 * (V(-1, 1, 1) - xc) + b111 * (V(1, 1, 1) - xc);
-            VT Av = wf0 * fx + wf1 * fy + wf2 * fz + we0 * ex + we1 * ey + we2 * ez + wc * cc;
-            if (any_robin && (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz)) {
-                // alpha * (face mass matrix) on every Robin face through the node
-                const int idx[3] = {i, j, k};
-                const int nn[3] = {g.nx, g.ny, g.nz};
-                for (int f = 0; f < 6; ++f) {
-                    if (op.alpha[f] == 0.0) continue;
-                    const int an = f / 2;
-                    if (idx[an] != ((f & 1) ? nn[an] : 0)) continue;
-                    const int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
-                    for (int db = -1; db <= 1; ++db)
-                        for (int da = -1; da <= 1; ++da) {
-                            const int ca = (da < 0) ? (idx[aa] >= 1) : (da > 0) ? (idx[aa] < nn[aa])
-                                                                           : (idx[aa] >= 1) + (idx[aa] < nn[aa]);
-                            const int cb = (db < 0) ? (idx[ab] >= 1) : (db > 0) ? (idx[ab] < nn[ab])
-                                                                           : (idx[ab] >= 1) + (idx[ab] < nn[ab]);
-                            if (!ca || !cb) continue;
-                            const double w = op.alpha[f] * ca * g.h[aa] * (da ? 1.0 : 2.0) / 6.0 *
-                                             cb * g.h[ab] * (db ? 1.0 : 2.0) / 6.0;
-                            int o[3] = {0, 0, 0};
-                            o[aa] = da;
-                            o[ab] = db;
-                            Av += (VT)w * V(o[0], o[1], o[2]);
-                        }
-                }
-            }
-            body(i, j, k, g.off(i, j, k), Av, xc);
+            const VT Av = q1_apply<true, ROBIN, CUBE, VT>(V, sb[s0][ty][tx], sb[s0][ty][tx + 1], sb[s0][ty + 1][tx],
+                                                          sb[s0][ty + 1][tx + 1], sb[s1][ty][tx], sb[s1][ty][tx + 1],
+                                                          sb[s1][ty + 1][tx], sb[s1][ty + 1][tx + 1], i, j, k, g, op, wts);
+            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Av, xc);
         }
         __syncthreads();
     }
 }
 
+// ---- the z-march for a level with one beta everywhere (FP64) ------------------------------
+// With constant beta the assembled matrix is the tensor product
+//     A = beta (Kx(x)My(x)Mz + Mx(x)Ky(x)Mz + Mx(x)My(x)Kz),
+// with the assembled 1D matrices K = -(1/h) d2 and M = (h/6) S, d2 = [1 -2 1] and
+// S = [1 4 1]. At an interior node therefore
+//     (A v)_i = -(beta/36) (hy hz/hx Sy Sz Lx + hx hz/hy Sx Sz Ly + hx hy/hz Sx Sy Lz),
+// L_a = d2_a v. The second differences are formed first (neighbouring values nearly cancel
+// exactly) and only then smoothed, so the evaluation is as accurate as the difference form
+// while costing about 24 FP64 operations per node instead of about 60. Nodes on the box
+// boundary (one-sided 1D rows, Robin terms) take the general difference form.
+// full_rows: also evaluate Dirichlet rows (callers that mask them pass false).
+template <bool ROBIN, bool CUBE, typename SRC, typename BODY>
+__device__ __forceinline__ void march_uniform(const Grid& g, const Op& op, double bu, int kz, bool full_rows,
+                                              SRC src, BODY body)
+{
+    __shared__ double X[3][BY + 2][BX + 2];
+    __shared__ double LX[BY + 2][BX];
+    __shared__ double LY[BY][BX + 2];
+    __shared__ double LZ[BY + 2][BX + 2];
+    __shared__ double UZ[BY + 2][BX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int kb = blockIdx.z * kz;
+    const int ke = min(kb + kz, g.nz + 1);
+    const Weights<double> wts(op);
+    const double cx = -bu / 36.0 * g.h[1] * g.h[2] / g.h[0];
+    const double cy = -bu / 36.0 * g.h[0] * g.h[2] / g.h[1];
+    const double cz = -bu / 36.0 * g.h[0] * g.h[1] / g.h[2];
+
+    auto load_plane = [&](int k) {
+        double(*dst)[BX + 2] = X[(k + 3) % 3];
+        const int64_t base = g.plane_base(k);
+        for (int c = tid; c < (BX + 2) * (BY + 2); c += NT) {
+            const int ci = c % (BX + 2), cj = c / (BX + 2);
+            const int i = i0 - 1 + ci, j = j0 - 1 + cj;
+            double v = 0.0;
+            if (i <= g.nx + 1 && j <= g.ny + 1) v = src(base + g.in_plane(i, j));
+            dst[cj][ci] = v;
+        }
+    };
+    // second differences along x and y of plane k (for the smoothing in y and x)
+    auto form_lxy = [&](int k) {
+        const double(*P)[BX + 2] = X[(k + 3) % 3];
+        for (int c = tid; c < BX * (BY + 2); c += NT) {
+            const int ci = c % BX, cj = c / BX;
+            LX[cj][ci] = (P[cj][ci] + P[cj][ci + 2]) - 2.0 * P[cj][ci + 1];
+        }
+        for (int c = tid; c < (BX + 2) * BY; c += NT) {
+            const int ci = c % (BX + 2), cj = c / (BX + 2);
+            LY[cj][ci] = (P[cj][ci] + P[cj + 2][ci]) - 2.0 * P[cj + 1][ci];
+        }
+    };
+    const int i = i0 + tx, j = j0 + ty;
+    double txm = 0, tx0 = 0, tym = 0, ty0 = 0;
+    load_plane(kb - 1);
+    __syncthreads();
+    form_lxy(kb - 1);
+    __syncthreads();
+    txm = LX[ty][tx] + 4.0 * LX[ty + 1][tx] + LX[ty + 2][tx];
+    tym = LY[ty][tx] + 4.0 * LY[ty][tx + 1] + LY[ty][tx + 2];
+    load_plane(kb);
+    __syncthreads();
+    form_lxy(kb);
+    __syncthreads();
+    tx0 = LX[ty][tx] + 4.0 * LX[ty + 1][tx] + LX[ty + 2][tx];
+    ty0 = LY[ty][tx] + 4.0 * LY[ty][tx + 1] + LY[ty][tx + 2];
+    for (int k = kb; k < ke; ++k) {
+        load_plane(k + 1);
+        __syncthreads();
+        form_lxy(k + 1);
+        {
+            const double(*Pm)[BX + 2] = X[(k + 2) % 3];
+            const double(*P0)[BX + 2] = X[k % 3];
+            const double(*Pp)[BX + 2] = X[(k + 1) % 3];
+            for (int c = tid; c < (BX + 2) * (BY + 2); c += NT) {
+                const int ci = c % (BX + 2), cj = c / (BX + 2);
+                LZ[cj][ci] = (Pm[cj][ci] + Pp[cj][ci]) - 2.0 * P0[cj][ci];
+            }
+        }
+        __syncthreads();
+        const double txp = LX[ty][tx] + 4.0 * LX[ty + 1][tx] + LX[ty + 2][tx];
+        const double typ = LY[ty][tx] + 4.0 * LY[ty][tx + 1] + LY[ty][tx + 2];
+        for (int c = tid; c < BX * (BY + 2); c += NT) {
+            const int ci = c % BX, cj = c / BX;
+            UZ[cj][ci] = LZ[cj][ci] + 4.0 * LZ[cj][ci + 1] + LZ[cj][ci + 2];
+        }
+        __syncthreads();
+        if (i <= g.nx && j <= g.ny) {
+            const int pm = (k + 2) % 3, p0 = k % 3, pp = (k + 1) % 3;
+            auto V = [&](int dx, int dy, int dz) -> double {
+                return X[dz < 0 ? pm : (dz > 0 ? pp : p0)][ty + 1 + dy][tx + 1 + dx];
+            };
+            double Av;
+            if (i > 0 && i < g.nx && j > 0 && j < g.ny && k > 0 && k < g.nz) {
+                const double A = txm + 4.0 * tx0 + txp;
+                const double B = tym + 4.0 * ty0 + typ;
+                const double C = UZ[ty][tx] + 4.0 * UZ[ty + 1][tx] + UZ[ty + 2][tx];
+                Av = cx * A + cy * B + cz * C;
+            } else if (!full_rows && on_dirichlet(g, op, i, j, k)) {
+                Av = 0.0;  // row discarded by the caller
+            } else {
+                // one-sided rows: general form with the elements that exist
+                auto be = [&](int ex, int ey, int ez) {
+                    const int a = i - 1 + ex, b = j - 1 + ey, c = k - 1 + ez;
+                    return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz) ? bu : 0.0;
+                };
+                Av = q1_apply<true, ROBIN, CUBE, double>(V, be(0, 0, 0), be(1, 0, 0), be(0, 1, 0), be(1, 1, 0),
+                                                         be(0, 0, 1), be(1, 0, 1), be(0, 1, 1), be(1, 1, 1), i, j, k,
+                                                         g, op, wts);
+            }
+            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Av, V(0, 0, 0));
+        }
+        __syncthreads();  // the boundary rows above read plane k-1, which the next load replaces
+        txm = tx0;
+        tx0 = txp;
+        tym = ty0;
+        ty0 = typ;
+    }
+}
+
+// Uniform-beta dispatch of the FP64 kernels: *uniform is set per level by the set-up.
+#define ECMG_FP64_MARCH(T, ROBIN, CUBE, FULL, SRC, BODY)                                    \
+    do {                                                                                  \
+        if (sizeof(T) == 8 && uniform && *uniform)                                        \
+            march_uniform<ROBIN, CUBE>(g, op, (double)beta[g.off(0, 0, 0)], kz, FULL, SRC, BODY); \
+        else                                                                              \
+            march<ROBIN, CUBE, T, T>(g, op, beta, kz, SRC, BODY);                          \
+    } while (0)
+
 // ---- K1: search direction and operator ------------------------------------------------------
-template <typename T>
+template <typename T, bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(NT) k_pq(const Grid g, const Op op, const T* __restrict__ beta,
-                                           const T* __restrict__ r, const T* __restrict__ dinv,
-                                           const T* __restrict__ pold, T* __restrict__ pnew,
-                                           T* __restrict__ q, T* __restrict__ x, SolveState* st,
-                                           double* partials, int pidx, CondHandles ch, int kz)
+                                           const int* uniform, const T* __restrict__ r,
+                                           const T* __restrict__ dinv, const T* __restrict__ pold,
+                                           T* __restrict__ pnew, T* __restrict__ q, T* __restrict__ x,
+                                           SolveState* st, double* partials, int pidx, CondHandles ch, int kz)
 {
     COUNT_LAUNCH();
     if (st->done) return;
     const T bcg = (T)st->beta;
     const T ap = (T)st->alpha_prev;
     Acc<T> acc;
-    march<T, T>(
-        g, op, beta, kz, [&](int64_t o) -> T { return dinv[o] * r[o] + bcg * pold[o]; },
-        [&](int i, int j, int k, int64_t o, T Av, T pn) {
-            const T qv = on_dirichlet(g, op, i, j, k) ? T(0) : Av;
-            pnew[o] = pn;
-            q[o] = qv;
-            if (ap != T(0)) x[o] += ap * pold[o];
-            acc.add_prod(pn, qv);
-        });
+    auto src = [&](int64_t o) -> T { return dinv[o] * r[o] + bcg * pold[o]; };
+    auto body = [&](int i, int j, int k, int64_t o, T Av, T pn) {
+        const T qv = on_dirichlet(g, op, i, j, k) ? T(0) : Av;
+        pnew[o] = pn;
+        q[o] = qv;
+        if (ap != T(0)) x[o] += ap * pold[o];
+        acc.add_prod(pn, qv);
+    };
+    if constexpr (sizeof(T) == 8) ECMG_FP64_MARCH(T, ROBIN, CUBE, false, src, body);
+    else march<ROBIN, CUBE, T, T>(g, op, beta, kz, src, body);
     double v[1] = {acc.value()};
     if (grid_sum<1>(v, partials, &st->arrive)) {
         const double pq = v[0];
@@ -323,39 +400,41 @@ __device__ void res_epilogue(SolveState* st, double rr, double rz, int mode, Con
     }
 }
 
-template <typename OT>
+template <typename OT, bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const double* __restrict__ beta,
-                                            const double* __restrict__ x, const double* __restrict__ b,
-                                            const OT* __restrict__ dinv, OT* __restrict__ r,
-                                            SolveState* st, double* partials, int mode, CondHandles ch,
-                                            int kz)
+                                            const int* uniform, const double* __restrict__ x,
+                                            const double* __restrict__ b, const OT* __restrict__ dinv,
+                                            OT* __restrict__ r, SolveState* st, double* partials, int mode,
+                                            CondHandles ch, int kz)
 {
     COUNT_LAUNCH();
     if (mode == RES_REPLACE && st->done) return;
     double rr = 0.0, rz = 0.0;
-    march<double, double>(
-        g, op, beta, kz, [&](int64_t o) -> double { return x[o]; },
-        [&](int i, int j, int k, int64_t o, double Av, double) {
-            const double rv = on_dirichlet(g, op, i, j, k) ? 0.0 : b[o] - Av;
-            const OT ro = (OT)rv;
-            r[o] = ro;
-            rr = fma(rv, rv, rr);
-            const double rd = (double)ro;
-            rz = fma(rd * (double)dinv[o], rd, rz);
-        });
+    auto src = [&](int64_t o) -> double { return x[o]; };
+    auto body = [&](int i, int j, int k, int64_t o, double Av, double) {
+        const double rv = on_dirichlet(g, op, i, j, k) ? 0.0 : b[o] - Av;
+        const OT ro = (OT)rv;
+        r[o] = ro;
+        rr = fma(rv, rv, rr);
+        const double rd = (double)ro;
+        rz = fma(rd * (double)dinv[o], rd, rz);
+    };
+    ECMG_FP64_MARCH(double, ROBIN, CUBE, false, src, body);
     double v[2] = {rr, rz};
     if (grid_sum<2>(v, partials, &st->arrive)) res_epilogue(st, v[0], v[1], mode, ch);
 }
 
 // ---- y = A x (full matrix, for operator checks) ---------------------------------------------
-template <typename T>
+template <typename T, bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(NT) k_apply(const Grid g, const Op op, const T* __restrict__ beta,
-                                              const T* __restrict__ x, double* __restrict__ y, int kz)
+                                              const int* uniform, const T* __restrict__ x,
+                                              double* __restrict__ y, int kz)
 {
     COUNT_LAUNCH();
-    march<T, T>(
-        g, op, beta, kz, [&](int64_t o) -> T { return x[o]; },
-        [&](int, int, int, int64_t o, T Av, T) { y[o] = (double)Av; });
+    auto src = [&](int64_t o) -> T { return x[o]; };
+    auto body = [&](int, int, int, int64_t o, T Av, T) { y[o] = (double)Av; };
+    if constexpr (sizeof(T) == 8) ECMG_FP64_MARCH(T, ROBIN, CUBE, true, src, body);
+    else march<ROBIN, CUBE, T, T>(g, op, beta, kz, src, body);
 }
 
 // ---- K2: residual update and stopping test ----------------------------------------------------
@@ -454,6 +533,13 @@ __global__ void k_state_init(SolveState* st, double rtol, double inner, int max_
     *st = s;
 }
 
+inline bool has_robin(const Op& op)
+{
+    for (int f = 0; f < 6; ++f)
+        if (op.alpha[f] != 0.0) return true;
+    return false;
+}
+
 inline int stencil_kz(const Grid& g)
 {
     const int gx = (g.nx + 1 + BX - 1) / BX, gy = (g.ny + 1 + BY - 1) / BY;
@@ -485,49 +571,53 @@ int max_stencil_blocks(const Grid& g)
 }
 int max_stream_blocks() { return UPD_MAX_BLOCKS; }
 
-void launch_pq64(const Grid& g, const Op& op, const double* beta, const double* r,
+// Kernel variant for the level: Robin terms present, cubic elements.
+#define ECMG_VARIANT(KERNEL, ...)                                                              \
+    (has_robin(op) ? (op.cube ? KERNEL<__VA_ARGS__, true, true> : KERNEL<__VA_ARGS__, true, false>) \
+                   : (op.cube ? KERNEL<__VA_ARGS__, false, true> : KERNEL<__VA_ARGS__, false, false>))
+
+void launch_pq64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* r,
                  const double* dinv, const double* pold, double* pnew, double* q, double* x,
                  SolveState* st, Partials pr, int pidx, CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    k_pq<double><<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, r, dinv, pold, pnew, q, x, st,
-                                                            pr.buf, pidx, ch, kz);
+    ECMG_VARIANT(k_pq, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, r, dinv, pold,
+                                                                           pnew, q, x, st, pr.buf, pidx, ch, kz);
 }
 void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r, const float* dinv,
                  const float* pold, float* pnew, float* q, float* e, SolveState* st, Partials pr,
                  int pidx, CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    k_pq<float><<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, r, dinv, pold, pnew, q, e, st,
-                                                           pr.buf, pidx, ch, kz);
+    ECMG_VARIANT(k_pq, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, nullptr, r, dinv, pold,
+                                                                          pnew, q, e, st, pr.buf, pidx, ch, kz);
 }
-void launch_res64(const Grid& g, const Op& op, const double* beta, const double* x, const double* b,
-                  const double* dinv, double* r, SolveState* st, Partials pr, ResMode mode,
+void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
+                  const double* b, const double* dinv, double* r, SolveState* st, Partials pr, ResMode mode,
                   CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    k_res<double><<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, x, b, dinv, r, st, pr.buf,
-                                                             (int)mode, ch, kz);
+    ECMG_VARIANT(k_res, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
+                                                                            st, pr.buf, (int)mode, ch, kz);
 }
-void launch_res32(const Grid& g, const Op& op, const double* beta, const double* x, const double* b,
-                  const float* dinv, float* r, SolveState* st, Partials pr, ResMode mode,
+void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
+                  const double* b, const float* dinv, float* r, SolveState* st, Partials pr, ResMode mode,
                   CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    k_res<float><<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, x, b, dinv, r, st, pr.buf,
-                                                            (int)mode, ch, kz);
+    ECMG_VARIANT(k_res, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
+                                                                           st, pr.buf, (int)mode, ch, kz);
 }
-void launch_apply64(const Grid& g, const Op& op, const double* beta, const double* x, double* y,
-                    cudaStream_t s)
+void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
+                    double* y, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    k_apply<double><<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, x, y, kz);
+    ECMG_VARIANT(k_apply, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, y, kz);
 }
-void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y,
-                    cudaStream_t s)
+void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    k_apply<float><<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, x, y, kz);
+    ECMG_VARIANT(k_apply, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, nullptr, x, y, kz);
 }
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv, SolveState* st,
                      Partials pr, CondHandles ch, cudaStream_t s)

@@ -19,9 +19,10 @@ struct CondHandles {
     int use;                           // 0 when the kernels run outside a graph
 };
 
-// Tiled z-marching stencil launches.
+// Tiled z-marching stencil launches. uniform: device flag of the level (1 = one beta
+// everywhere, which selects the tensor-product evaluation in FP64), or nullptr.
 // p_new = dinv r + beta p_old on the fly; q = A p_new; x += alpha_prev p_old; state.alpha.
-void launch_pq64(const Grid& g, const Op& op, const double* beta, const double* r,
+void launch_pq64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* r,
                  const double* dinv, const double* pold, double* pnew, double* q, double* x,
                  SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
 void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
@@ -29,15 +30,15 @@ void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
                  SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
 // r = b - A x (FP64 arithmetic) on free nodes, 0 on Dirichlet nodes; r stored as double or
 // float; ||r||^2 and r.dinv.r reduced; last block acts by ResMode.
-void launch_res64(const Grid& g, const Op& op, const double* beta, const double* x,
+void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const double* dinv, double* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s);
-void launch_res32(const Grid& g, const Op& op, const double* beta, const double* x,
+void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s);
 // y = A x with the full matrix (no boundary masking), FP64 or FP32 arithmetic.
-void launch_apply64(const Grid& g, const Op& op, const double* beta, const double* x, double* y,
-                    cudaStream_t s);
+void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
+                    double* y, cudaStream_t s);
 void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y,
                     cudaStream_t s);
 

@@ -219,6 +219,26 @@ __global__ void k_dirichlet_ext(Grid g, Op op, const double* __restrict__ gD, do
     x[o] = (gD && on_dirichlet(g, op, i, j, k)) ? gD[o] : 0.0;
 }
 
+__global__ void k_uniform(Grid g, const double* __restrict__ beta, int* flag)
+{
+    COUNT_LAUNCH();
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    const double b0 = beta[g.off(0, 0, 0)];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx);
+        const int64_t r = t / g.nx;
+        const int j = (int)(r % g.ny);
+        const int k = (int)(r / g.ny);
+        if (beta[g.off(i, j, k)] != b0) *flag = 0;  // every writer stores the same value
+    }
+}
+
+__global__ void k_set_flag(int* flag)
+{
+    COUNT_LAUNCH();
+    *flag = 1;
+}
+
 __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n)
 {
     COUNT_LAUNCH();
@@ -229,6 +249,14 @@ __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict_
 inline int64_t nodes(const Grid& g) { return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
 
 }  // namespace
+
+void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s)
+{
+    k_set_flag<<<1, 1, 0, s>>>(flag);
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    int b = blocks_for(n);
+    k_uniform<<<b < 2048 ? b : 2048, TPB, 0, s>>>(g, beta, flag);
+}
 
 void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s)
 {

@@ -51,6 +51,10 @@ PROBLEMS = {
     "random_mixed_bc_1": lambda: inputs.random_problem(1, n0=(3, 2, 2), levels=3, rtol=1e-10),
     "problem1_load": lambda: inputs.paper_problem1(levels=4, rtol=1e-9),
     "variable_box": lambda: inputs.variable_box(levels=3, n0=(2, 2, 4), rtol=1e-9),
+    # one beta everywhere (tensor-product FP64 path) on non-cubic elements with Robin faces
+    "aniso_uniform_robin": lambda: inputs.random_problem(7, n0=(2, 3, 2), levels=4, rtol=1e-10, contrast=1.0,
+                                                         face_bc=[1, 0, 1, 0, 1, 1],
+                                                         alpha=[0.5, 0.0, 2.0, 0.0, 0.0, 1.0]),
 }
 
 
@@ -142,6 +146,11 @@ def test_mixed_solve_reaches_tolerance_and_fp64_accuracy(E, oracle_mod, name):
     L = p["levels"]
     for l in range(2, L):
         assert gst["rel_res"][l] <= p["rtol"], (l, gst["rel_res"])
+        # FP32 inner iterations with FP64 residual replacement keep the Krylov recurrence: on
+        # most problems they take exactly the FP64 iteration count. Problem 1 (a single
+        # eigenmode, where FP64 JCG converges unusually fast) loses that edge to FP32 rounding
+        # and needs up to about 2.5x; a broken recurrence would need far more.
+        assert gst["iters"][l] <= 3 * ost["iters"][l] + 2, (l, gst["iters"], ost["iters"])
         U = _np(s.get(E.ECMG_VEC_U, l))
         # the mixed solution satisfies the same residual test, so it differs from the oracle's
         # by at most what two solutions inside the tolerance can differ by
