@@ -176,6 +176,29 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
 ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,
                              double* ms_out, double* bytes_out);
 
+/* ---- error norms without device allocation (no counterpart in the paper) ---------------
+ *
+ * The same two norms as ecmg_error_norms -- max |a - b| and sqrt(sum (a - b)^2 / n) -- for
+ * callers that may not allocate device memory where they need them. cudaMalloc and cudaFree
+ * can synchronise the whole device, so code inside a latency-critical loop or a host
+ * callback, or code under a framework that owns every device allocation, must avoid them.
+ * This entry point allocates nothing and needs no handle: its scratch (one partial pair per
+ * block of 16384 elements, plus the final pair) is a fixed array of 512 KiB inside the
+ * library, which every device that loads the library holds until the process exits.
+ *
+ * a, b: device arrays of n doubles (any layout; b may be NULL for the norms of a). n must be
+ * 1..ECMG_NOALLOC_MAX_ELEMS; a larger n is rejected with ECMG_ERR_INVALID_ARG before any
+ * device work. stream: a cudaStream_t (NULL = default stream), synchronised before return.
+ * max_abs, rms: host outputs.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. Every call overwrites
+ * the whole part of the array it reads, so nothing has to start at zero, but all calls share
+ * the one array: calls that overlap on the GPU (different streams, or different host threads
+ * on one device) race and may return wrong norms. */
+#define ECMG_NOALLOC_MAX_ELEMS 536870912LL
+ecmg_status ecmg_error_norms_noalloc(const double* a, const double* b, int64_t n, void* stream,
+                                     double* max_abs, double* rms);
+
 /* Bytes of device workspace ecmg_create allocates for this problem and options. */
 ecmg_status ecmg_workspace_bytes(const ecmg_problem* prob, const ecmg_options* opt,
                                  uint64_t* bytes);

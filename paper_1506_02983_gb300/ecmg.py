@@ -25,6 +25,7 @@ ECMG_F_NODAL, ECMG_F_LOAD = 0, 1
 ECMG_FP64, ECMG_MIXED = 0, 1
 ECMG_EXP_SERENDIPITY20, ECMG_EXP_LAGRANGE27 = 0, 1
 ECMG_VEC_U, ECMG_VEC_W, ECMG_VEC_UTILDE, ECMG_VEC_B, ECMG_VEC_BETA = 0, 1, 2, 3, 4
+ECMG_NOALLOC_MAX_ELEMS = 536870912  # include/ecmg.h
 
 
 class ecmg_problem(C.Structure):
@@ -65,6 +66,7 @@ _SIGS = {
     "ecmg_workspace_bytes": (_I32, [C.POINTER(ecmg_problem), C.POINTER(ecmg_options),
                                     C.POINTER(C.c_uint64)]),
     "ecmg_kernel_launches": (_I32, [C.POINTER(C.c_uint64)]),
+    "ecmg_error_norms_noalloc": (_I32, [_P, _P, C.c_int64, _P, C.POINTER(_D), C.POINTER(_D)]),
     "ecmg_time_kernel": (_I32, [_H, _I32, _I32, _I32, C.POINTER(_D), C.POINTER(_D)]),
 }
 for _name, (_res, _args) in _SIGS.items():
