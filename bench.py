@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iters", type=int, default=20000)
     ap.add_argument("--kernels", default="0,1,2,5,6,7", help="kernels timed alone for the report")
+    ap.add_argument("--eager", action="store_true",
+                    help="host-driven level loops instead of one CUDA graph per solve (same kernels); "
+                         "ncu cannot profile kernel nodes of graphs that hold conditional nodes")
     return ap.parse_args()
 
 
@@ -189,7 +192,7 @@ def main():
     def make(precision):
         return ecmg.Solver(p["n0"], L, p["lo"], p["hi"], p["face_bc"], p["alpha"], d["beta"], d["f"],
                            d["gD"], None, f_mode=ecmg.ECMG_F_LOAD, rtol=args.rtol, precision=precision,
-                           max_iters=args.max_iters)
+                           max_iters=args.max_iters, use_graph=0 if args.eager else 1)
 
     def barrier():
         torch.cuda.synchronize()
@@ -222,7 +225,9 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ecmg.kernel_launches()
+    torch.cuda.nvtx.range_push("ecmg_mixed_timed")
     ms_mixed = timed(lambda: mixed.solve(u_out), args.steps)
+    torch.cuda.nvtx.range_pop()
     launches = (ecmg.kernel_launches() - launches0) // args.steps
     clk = clocks.stop()
     st_mixed, _ = mixed.solve(u_out)
@@ -258,7 +263,9 @@ def main():
     fp64 = make(ecmg.ECMG_FP64)
     st64, status = fp64.solve(u_out)
     assert status == 0, st64
+    torch.cuda.nvtx.range_push("ecmg_fp64_timed")
     ms_fp64 = timed(lambda: fp64.solve(u_out), args.fp64_steps)
+    torch.cuda.nvtx.range_pop()
     err_fp64 = fp64.norms(u_out, u_exact)[0]
     fp64.close()
 
@@ -285,7 +292,8 @@ def main():
         "config": {"workload": "cos_cube Poisson unit cube, u=cos(pi x)cos(pi y)cos(pi z), all-Dirichlet, "
                                "Q1, %d^3 -> %d^3 (%d levels), rtol %g, exact load functional" % (n0, nf, L, args.rtol),
                    "precision": "MIXED (FP32 JCG, FP64 residual replacement)",
-                   "l2": "inputs and finest vectors (>1 GB each) larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "l2": "inputs and finest vectors (>1 GB each) larger than L2", "parallelism": "replicas" if world > 1 else "single GPU",
+                   "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes"},
         "solve_ms_mixed": ms_mixed, "solve_ms_fp64": ms_fp64, "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
         "max_err_mixed": err_mixed, "max_err_fp64": err_fp64,
         "err_ratio_mixed_over_fp64": err_mixed / err_fp64,
