@@ -85,7 +85,7 @@ Grid make_grid(const ecmg_problem& p, int l)
     g.nx = p.n0[0] << l;
     g.ny = p.n0[1] << l;
     g.nz = p.n0[2] << l;
-    g.pitch = ((g.nx + 1 + XL + 2) + 31) / 32 * 32;
+    g.pitch = ((g.nx + 1 + XL + 2) + 7) / 8 * 8;  // rows 32-byte aligned (FP32), 16-byte TMA strides
     g.plane = (int64_t)g.pitch * (g.ny + 3);
     g.total = g.plane * (g.nz + 3);
     for (int a = 0; a < 3; ++a) g.h[a] = (p.hi[a] - p.lo[a]) / (double)(p.n0[a] << l);
@@ -250,7 +250,7 @@ void record_level(Rec& R, int l)
 
     launch_state_init(st, rtol, o.inner_rtol, o.max_iters, R.s());
     dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s());
-    launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_FH2, none, R.s());
+    launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s());
     if (!direct) {
         const Level& u1 = h->lv[l - 1];
         const Level& u0 = h->lv[l - 2];
@@ -463,7 +463,6 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
     h->L = prob->levels;
     try {
         for (int i = 0; i < 3; ++i) ck(cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
-        ck(exp_init_tables());
         const bool mixed = opt->precision == ECMG_MIXED;
         int maxb = 0;
         for (int l = 0; l < h->L; ++l) {

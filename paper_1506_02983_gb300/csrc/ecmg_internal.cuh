@@ -4,7 +4,8 @@
 //   node (i, j, k), i in -1..nx+1 (one ghost layer on each side), is stored at
 //       off(i, j, k) = (k + 1) * plane + (j + 1) * pitch + (i + XL)
 //   with XL = 4 (so node i = 0 starts a 16-byte aligned run for both FP64 and FP32) and
-//   pitch = round_up(nx + 1 + XL + 2, 32) elements. Element (ex, ey, ez) of the level is
+//   pitch = round_up(nx + 1 + XL + 2, 8) elements (rows start on 32-byte sectors; every
+//   stride is a multiple of 16 bytes, as TMA requires). Element (ex, ey, ez) of the level is
 //   stored at the offset of its lowest corner node, so elements -1..nx are addressable and
 //   the ghost elements hold beta = 0. Ghost entries are zero and are never written; a kernel
 //   may therefore read the 27 neighbours of any owned node, and the 8 elements around it,

@@ -7,9 +7,9 @@
 //   edge midpoints:     W = U^1_mid + (U^1_A - U^0_A + U^1_B - U^0_B) / 8      eq. (zhongdian)
 //   (Lagrange variant)  face and body centres: mean of (zhongdian) over the diagonals
 //                       through them (Remark in Sec. 4.3)
-// and every patch node is the fixed linear combination sum_m N_m(xi, eta, zeta) W_m with the
-// 20-node Serendipity functions of Sec. 4.3 (or the 27-node tri-quadratic Lagrange basis).
-// The 125 x 20 (125 x 27) weight tables are evaluated once on the host from those formulas.
+// and every patch node is sum_m N_m(xi, eta, zeta) W_m with the 20-node Serendipity functions
+// of Sec. 4.3 (or the 27-node tri-quadratic Lagrange basis), evaluated below by sum
+// factorisation.
 //
 // EXP_true (line 10; Sec. 4.2.1 and 4.3): with d = U^l - U^{l-1} at the level-(l-1) nodes,
 //   U~ = U^l + (1/3) I(d),  I = trilinear interpolation from the coarse nodes,
@@ -18,6 +18,7 @@
 #include "exp.cuh"
 
 #include <cstring>
+#include <type_traits>
 
 namespace ecmg {
 namespace {
@@ -28,134 +29,229 @@ __device__ unsigned long long g_launches = 0;  // kernel executions of this file
         atomicAdd(&g_launches, 1ull)
 
 constexpr int TPB = 256;
-__constant__ double c_ser[125 * 20];
-__constant__ double c_lag[125 * 27];
-
-// The 20 Serendipity nodes of the patch: corners, then x-, y-, z-direction edge midpoints
-// (the paper's nodes 1,5,21,25,101,105,121,125 / 3,23,103,123 / 11,15,111,115 / 51,55,71,75).
-__host__ __device__ constexpr int ser_node(int m, int axis)
+// Quadratic Lagrange interpolation on the nodes -1, 0, 1 (values v0, v1, v2) at the five
+// points -1, -1/2, 0, 1/2, 1 (m = 0..4).
+template <int M>
+__device__ __forceinline__ double quad5(double v0, double v1, double v2)
 {
-    constexpr int T[20][3] = {{0, 0, 0}, {4, 0, 0}, {0, 4, 0}, {4, 4, 0}, {0, 0, 4}, {4, 0, 4}, {0, 4, 4},
-                              {4, 4, 4}, {2, 0, 0}, {2, 4, 0}, {2, 0, 4}, {2, 4, 4}, {0, 2, 0}, {4, 2, 0},
-                              {0, 2, 4}, {4, 2, 4}, {0, 0, 2}, {4, 0, 2}, {0, 4, 2}, {4, 4, 2}};
-    return T[m][axis];
+    if (M == 0) return v0;
+    if (M == 2) return v1;
+    if (M == 4) return v2;
+    if (M == 1) return fma(0.375, v0, fma(0.75, v1, -0.125 * v2));
+    return fma(-0.125, v0, fma(0.75, v1, 0.375 * v2));
 }
 
-__device__ __forceinline__ bool on_dirichlet(const Grid& g, const Op& op, int i, int j, int k)
-{
-    return (i == 0 && op.bc[0] == 0) || (i == g.nx && op.bc[1] == 0) ||
-           (j == 0 && op.bc[2] == 0) || (j == g.ny && op.bc[3] == 0) ||
-           (k == 0 && op.bc[4] == 0) || (k == g.nz && op.bc[5] == 0);
-}
-
-// Value of the coarse-grid interpolation node (local patch position a, b, c in {0,2,4})
-// from U^1 (level l-1, grid g1) and U^0 (level l-2, grid g0) for the element (ex, ey, ez).
-struct Src {
-    Grid g1, g0;
-    const double* U1;
-    const double* U0;
-    int ex, ey, ez;
-    __device__ __forceinline__ double u1(int a, int b, int c) const
-    {
-        return U1[g1.off(2 * ex + a / 2, 2 * ey + b / 2, 2 * ez + c / 2)];
-    }
-    __device__ __forceinline__ double d(int a, int b, int c) const  // U^1 - U^0 at a corner
-    {
-        return u1(a, b, c) - U0[g0.off(ex + a / 4, ey + b / 4, ez + c / 4)];
-    }
-};
-
+// EXP_finite, one thread per level-(l-2) element. The element's interpolant is tri-quadratic
+// for both variants (every Serendipity monomial has degree <= 2 in each variable), so it is
+// fixed by its values at the 3x3x3 level-(l-1) nodes of the element: the 20 extrapolated
+// values and, for Serendipity, the interpolant's own face and body centre values
+// (N_i at a face centre: -1/4 at the face's corners, 1/2 at its edge midpoints; at the body
+// centre: -1/4 at the corners, 1/4 at the edge midpoints). The fine nodes then follow by sum
+// factorisation, z first, then y, then x. A thread writes the fine nodes (4 ex + a, ...),
+// a = 0..3, plus a = 4 on the last element of an axis.
 template <int VARIANT>
-__global__ void k_exp_finite(Grid g, Op op, Grid g1, const double* __restrict__ U1, Grid g0,
-                             const double* __restrict__ U0, double* __restrict__ x,
-                             double* __restrict__ W)
+__global__ void __launch_bounds__(128) k_exp_finite(Grid g, Op op, Grid g1, const double* __restrict__ U1, Grid g0,
+                                                    const double* __restrict__ U0, double* __restrict__ x,
+                                                    double* __restrict__ W)
 {
     COUNT_LAUNCH();
-    const int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    const int64_t ne = (int64_t)g0.nx * g0.ny * g0.nz;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int I = (int)(t % (g.nx + 1));
-    const int64_t rr = t / (g.nx + 1);
-    const int J = (int)(rr % (g.ny + 1));
-    const int K = (int)(rr / (g.ny + 1));
-    const int64_t o = g.off(I, J, K);
-    if (on_dirichlet(g, op, I, J, K)) {
-        W[o] = x[o];
-        return;
-    }
-    Src s{g1, g0, U1, U0, min(I >> 2, g0.nx - 1), min(J >> 2, g0.ny - 1), min(K >> 2, g0.nz - 1)};
-    const int a = I - 4 * s.ex, b = J - 4 * s.ey, c = K - 4 * s.ez;
-    const int pt = a + 5 * b + 25 * c;
-    double w = 0.0;
-    if (VARIANT == 0) {
+    if (t >= ne) return;
+    const int ex = (int)(t % g0.nx);
+    const int64_t r_ = t / g0.nx;
+    const int ey = (int)(r_ % g0.ny);
+    const int ez = (int)(r_ / g0.ny);
+    double u1[3][3][3], d[2][2][2], V[3][3][3];  // [c][b][a]
 #pragma unroll
-        for (int m = 0; m < 20; ++m) {
-            const int na = ser_node(m, 0), nb = ser_node(m, 1), nc = ser_node(m, 2);
-            double v;
-            if (m < 8) {
-                v = s.u1(na, nb, nc) + s.d(na, nb, nc) / 4.0;  // (5 U^1 - U^0)/4
-            } else {
-                const int dir = (m < 12) ? 0 : (m < 16) ? 1 : 2;
-                int A[3] = {na, nb, nc}, B[3] = {na, nb, nc};
-                A[dir] = 0;
-                B[dir] = 4;
-                v = s.u1(na, nb, nc) + (s.d(A[0], A[1], A[2]) + s.d(B[0], B[1], B[2])) / 8.0;
-            }
-            w += c_ser[pt * 20 + m] * v;
-        }
-    } else {
-        // 27 values at the level-(l-1) nodes of the element, (zhongdian) averaged over every
-        // diagonal through the non-corner ones
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            const int qa = 2 * (q % 3), qb = 2 * ((q / 3) % 3), qc = 2 * (q / 9);
-            const int nodd = (qa == 2) + (qb == 2) + (qc == 2);
-            double v;
-            if (nodd == 0) {
-                v = s.u1(qa, qb, qc) + s.d(qa, qb, qc) / 4.0;  // (5 U^1 - U^0)/4
-            } else {
-                // (zhongdian) on one diagonal adds (d_A + d_B)/8; the mean over the 2^(nodd-1)
-                // diagonals adds (sum of d over the 2^nodd corners) / 2^(nodd+2)
-                double sum = 0.0;
-                for (int cc = 0; cc < 8; ++cc) {
-                    const int ca = (qa == 2) ? 4 * (cc & 1) : qa;
-                    const int cb = (qb == 2) ? 4 * ((cc >> 1) & 1) : qb;
-                    const int cz = (qc == 2) ? 4 * (cc >> 2) : qc;
-                    if ((qa != 2 && (cc & 1)) || (qb != 2 && ((cc >> 1) & 1)) || (qc != 2 && (cc >> 2)))
-                        continue;
-                    sum += s.d(ca, cb, cz);
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) u1[c][b][a] = U1[g1.off(2 * ex + a, 2 * ey + b, 2 * ez + c)];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) d[c][b][a] = u1[2 * c][2 * b][2 * a] - U0[g0.off(ex + a, ey + b, ez + c)];
+    // corners: eq. (jiedian); edge midpoints: eq. (zhongdian) along the edge
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int nodd = (a == 1) + (b == 1) + (c == 1);
+                if (nodd == 0) {
+                    V[c][b][a] = fma(0.25, d[c / 2][b / 2][a / 2], u1[c][b][a]);
+                } else if (nodd == 1) {
+                    const double sd = (a == 1) ? d[c / 2][b / 2][0] + d[c / 2][b / 2][1]
+                                    : (b == 1) ? d[c / 2][0][a / 2] + d[c / 2][1][a / 2]
+                                               : d[0][b / 2][a / 2] + d[1][b / 2][a / 2];
+                    V[c][b][a] = fma(0.125, sd, u1[c][b][a]);
                 }
-                v = s.u1(qa, qb, qc) + sum / (double)(4 << nodd);
             }
-            w += c_lag[pt * 27 + q] * v;
-        }
+    if (VARIANT == 0) {
+        // face and body centres of the Serendipity interpolant
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int nodd = (a == 1) + (b == 1) + (c == 1);
+                    if (nodd == 2) {
+                        double corners, edges;
+                        if (c != 1) {  // face normal z
+                            corners = V[c][0][0] + V[c][0][2] + V[c][2][0] + V[c][2][2];
+                            edges = V[c][1][0] + V[c][1][2] + V[c][0][1] + V[c][2][1];
+                        } else if (b != 1) {  // face normal y
+                            corners = V[0][b][0] + V[0][b][2] + V[2][b][0] + V[2][b][2];
+                            edges = V[1][b][0] + V[1][b][2] + V[0][b][1] + V[2][b][1];
+                        } else {  // face normal x
+                            corners = V[0][0][a] + V[0][2][a] + V[2][0][a] + V[2][2][a];
+                            edges = V[1][0][a] + V[1][2][a] + V[0][1][a] + V[2][1][a];
+                        }
+                        V[c][b][a] = fma(0.5, edges, -0.25 * corners);
+                    }
+                }
+        double corners = 0.0, edges = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int nodd = (a == 1) + (b == 1) + (c == 1);
+                    if (nodd == 0) corners += V[c][b][a];
+                    if (nodd == 1) edges += V[c][b][a];
+                }
+        V[1][1][1] = 0.25 * (edges - corners);
+    } else {
+        // Remark of Sec. 4.3: (zhongdian) averaged over the diagonals through the centre
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int nodd = (a == 1) + (b == 1) + (c == 1);
+                    if (nodd < 2) continue;
+                    double sd = 0.0;
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                            for (int aa = 0; aa < 2; ++aa) {
+                                if ((a != 1 && aa != a / 2) || (b != 1 && bb != b / 2) || (c != 1 && cc != c / 2)) continue;
+                                sd += d[cc][bb][aa];
+                            }
+                    V[c][b][a] = fma(nodd == 2 ? 1.0 / 16.0 : 1.0 / 32.0, sd, u1[c][b][a]);
+                }
     }
-    x[o] = w;
-    W[o] = w;
+    // sum factorisation over the owned fine nodes
+    const int na = (ex == g0.nx - 1) ? 5 : 4, nb = (ey == g0.ny - 1) ? 5 : 4, nc = (ez == g0.nz - 1) ? 5 : 4;
+    const bool dx0 = op.bc[0] == 0, dx1 = op.bc[1] == 0, dy0 = op.bc[2] == 0, dy1 = op.bc[3] == 0;
+    const bool dz0 = op.bc[4] == 0, dz1 = op.bc[5] == 0;
+    auto zstage = [&](auto mc, int c) {
+        constexpr int MC = decltype(mc)::value;
+        double Z[3][3];
+#pragma unroll
+        for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+            for (int qa = 0; qa < 3; ++qa) Z[qb][qa] = quad5<MC>(V[0][qb][qa], V[1][qb][qa], V[2][qb][qa]);
+        const int K = 4 * ez + c;
+        const bool dk = (dz0 && K == 0) || (dz1 && K == g.nz);
+        auto ystage = [&](auto mb, int b) {
+            constexpr int MB = decltype(mb)::value;
+            double Y[3];
+#pragma unroll
+            for (int qa = 0; qa < 3; ++qa) Y[qa] = quad5<MB>(Z[0][qa], Z[1][qa], Z[2][qa]);
+            const int J = 4 * ey + b;
+            const bool djk = dk || (dy0 && J == 0) || (dy1 && J == g.ny);
+            const int64_t orow = g.off(4 * ex, J, K);
+            auto put = [&](int a, double w) {
+                const int I = 4 * ex + a;
+                const int64_t o = orow + a;
+                if (djk || (dx0 && I == 0) || (dx1 && I == g.nx)) {
+                    W[o] = x[o];
+                } else {
+                    x[o] = w;
+                    W[o] = w;
+                }
+            };
+            put(0, quad5<0>(Y[0], Y[1], Y[2]));
+            put(1, quad5<1>(Y[0], Y[1], Y[2]));
+            put(2, quad5<2>(Y[0], Y[1], Y[2]));
+            put(3, quad5<3>(Y[0], Y[1], Y[2]));
+            if (na == 5) put(4, quad5<4>(Y[0], Y[1], Y[2]));
+        };
+        ystage(std::integral_constant<int, 0>(), 0);
+        ystage(std::integral_constant<int, 1>(), 1);
+        ystage(std::integral_constant<int, 2>(), 2);
+        ystage(std::integral_constant<int, 3>(), 3);
+        if (nb == 5) ystage(std::integral_constant<int, 4>(), 4);
+    };
+    zstage(std::integral_constant<int, 0>(), 0);
+    zstage(std::integral_constant<int, 1>(), 1);
+    zstage(std::integral_constant<int, 2>(), 2);
+    zstage(std::integral_constant<int, 3>(), 3);
+    if (nc == 5) zstage(std::integral_constant<int, 4>(), 4);
 }
 
-__global__ void k_exp_true(Grid g, const double* __restrict__ U1, Grid gc, const double* __restrict__ U0,
-                           double* __restrict__ Ut)
+// EXP_true, one thread per level-(l-1) element: d = U^l - U^{l-1} at its 8 corners, divided
+// by 3, interpolated trilinearly to the element's 3x3x3 level-l nodes (halves and quarters of
+// corner values) and added to U^l. A thread writes the nodes (2 ex + a, ...), a = 0, 1, plus
+// a = 2 on the last element of an axis.
+__global__ void __launch_bounds__(128) k_exp_true(Grid g, const double* __restrict__ U1, Grid gc,
+                                                  const double* __restrict__ U0, double* __restrict__ Ut)
 {
     COUNT_LAUNCH();
-    const int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    const int64_t ne = (int64_t)gc.nx * gc.ny * gc.nz;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int I = (int)(t % (g.nx + 1));
-    const int64_t rr = t / (g.nx + 1);
-    const int J = (int)(rr % (g.ny + 1));
-    const int K = (int)(rr / (g.ny + 1));
-    const int oi = I & 1, oj = J & 1, ok = K & 1;
-    double s = 0.0;
-    for (int c = 0; c <= ok; ++c)
-        for (int b = 0; b <= oj; ++b)
-            for (int a = 0; a <= oi; ++a) {
-                const int ci = (I >> 1) + a, cj = (J >> 1) + b, ck = (K >> 1) + c;
-                s += U1[g.off(2 * ci, 2 * cj, 2 * ck)] - U0[gc.off(ci, cj, ck)];
+    if (t >= ne) return;
+    const int ex = (int)(t % gc.nx);
+    const int64_t r_ = t / gc.nx;
+    const int ey = (int)(r_ % gc.ny);
+    const int ez = (int)(r_ / gc.ny);
+    double D[3][3][3];  // trilinear interpolant of (U^l - U^{l-1}) / 3 at the 3x3x3 nodes
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                D[2 * c][2 * b][2 * a] = (U1[g.off(2 * (ex + a), 2 * (ey + b), 2 * (ez + c))] -
+                                          U0[gc.off(ex + a, ey + b, ez + c)]) * (1.0 / 3.0);  // no FP64 divide
+#pragma unroll
+    for (int c = 0; c < 3; c += 2)
+#pragma unroll
+        for (int b = 0; b < 3; b += 2) D[c][b][1] = 0.5 * (D[c][b][0] + D[c][b][2]);
+#pragma unroll
+    for (int c = 0; c < 3; c += 2)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) D[c][1][a] = 0.5 * (D[c][0][a] + D[c][2][a]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) D[1][b][a] = 0.5 * (D[0][b][a] + D[2][b][a]);
+    const int na = (ex == gc.nx - 1) ? 3 : 2, nb = (ey == gc.ny - 1) ? 3 : 2, nc = (ez == gc.nz - 1) ? 3 : 2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (c >= nc) break;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (b >= nb) break;
+            const int64_t orow = g.off(2 * ex, 2 * ey + b, 2 * ez + c);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a >= na) break;
+                Ut[orow + a] = U1[orow + a] + D[c][b][a];
             }
-    const double scale = 1.0 / (3.0 * (double)(1 << (oi + oj + ok)));
-    const int64_t o = g.off(I, J, K);
-    Ut[o] = U1[o] + scale * s;
+        }
+    }
 }
 
 // Per-block max |a-b| and sum (a-b)^2 over the owned nodes of a level.
@@ -197,72 +293,27 @@ __global__ void k_norms(Grid g, const double* __restrict__ a, const double* __re
     }
 }
 
-// Host evaluation of the interpolation weights of every patch point.
-void ser_weights(double* out)
-{
-    for (int c = 0; c < 5; ++c)
-        for (int b = 0; b < 5; ++b)
-            for (int a = 0; a < 5; ++a) {
-                const double xi = (a - 2) / 2.0, eta = (b - 2) / 2.0, zeta = (c - 2) / 2.0;
-                for (int m = 0; m < 20; ++m) {
-                    const double xi_i = (ser_node(m, 0) - 2) / 2.0, eta_i = (ser_node(m, 1) - 2) / 2.0,
-                                 zeta_i = (ser_node(m, 2) - 2) / 2.0;
-                    double N;
-                    if (m < 8)
-                        N = 0.125 * (1 + xi_i * xi) * (1 + eta_i * eta) * (1 + zeta_i * zeta) *
-                            (xi_i * xi + eta_i * eta + zeta_i * zeta - 2);
-                    else if (m < 12)
-                        N = 0.25 * (1 - xi * xi) * (1 + eta_i * eta) * (1 + zeta_i * zeta);
-                    else if (m < 16)
-                        N = 0.25 * (1 - eta * eta) * (1 + xi_i * xi) * (1 + zeta_i * zeta);
-                    else
-                        N = 0.25 * (1 - zeta * zeta) * (1 + xi_i * xi) * (1 + eta_i * eta);
-                    out[(a + 5 * b + 25 * c) * 20 + m] = N;
-                }
-            }
-}
-
-void lag_weights(double* out)
-{
-    auto L = [](int node, double t) {
-        return node == 0 ? 0.5 * t * (t - 1) : node == 1 ? 1 - t * t : 0.5 * t * (t + 1);
-    };
-    for (int c = 0; c < 5; ++c)
-        for (int b = 0; b < 5; ++b)
-            for (int a = 0; a < 5; ++a)
-                for (int q = 0; q < 27; ++q)
-                    out[(a + 5 * b + 25 * c) * 27 + q] =
-                        L(q % 3, (a - 2) / 2.0) * L((q / 3) % 3, (b - 2) / 2.0) * L(q / 9, (c - 2) / 2.0);
-}
-
 inline int blocks_for(int64_t n) { return (int)((n + TPB - 1) / TPB); }
 inline int64_t nodes(const Grid& g) { return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
 
 }  // namespace
 
-cudaError_t exp_init_tables()
-{
-    static double ser[125 * 20], lag[125 * 27];
-    ser_weights(ser);
-    lag_weights(lag);
-    cudaError_t e = cudaMemcpyToSymbol(c_ser, ser, sizeof(ser));
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(c_lag, lag, sizeof(lag));
-}
-
 void launch_exp_finite(int variant, const Grid& g, const Op& op, const Grid& g1, const double* U1,
                        const Grid& g0, const double* U0, double* x, double* W, cudaStream_t s)
 {
+    const int64_t ne = (int64_t)g0.nx * g0.ny * g0.nz;
+    const int nb = (int)((ne + 127) / 128);
     if (variant == 1)
-        k_exp_finite<1><<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, g1, U1, g0, U0, x, W);
+        k_exp_finite<1><<<nb, 128, 0, s>>>(g, op, g1, U1, g0, U0, x, W);
     else
-        k_exp_finite<0><<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, g1, U1, g0, U0, x, W);
+        k_exp_finite<0><<<nb, 128, 0, s>>>(g, op, g1, U1, g0, U0, x, W);
 }
 
 void launch_exp_true(const Grid& g, const double* U1, const Grid& gc, const double* U0, double* Ut,
                      cudaStream_t s)
 {
-    k_exp_true<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, U1, gc, U0, Ut);
+    const int64_t ne = (int64_t)gc.nx * gc.ny * gc.nz;
+    k_exp_true<<<(int)((ne + 127) / 128), 128, 0, s>>>(g, U1, gc, U0, Ut);
 }
 
 int norms_blocks(const Grid& g)

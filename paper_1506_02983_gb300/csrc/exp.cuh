@@ -5,9 +5,6 @@
 
 namespace ecmg {
 
-// Upload the Serendipity / Lagrange weight tables to constant memory (once per device).
-cudaError_t exp_init_tables();
-
 // EXP_finite: level-l grid g from U1 (level l-1, grid g1) and U0 (level l-2, grid g0).
 // Writes W on every node (Dirichlet nodes copy x, which holds g_D there) and x on free nodes.
 void launch_exp_finite(int variant, const Grid& g, const Op& op, const Grid& g1, const double* U1,

@@ -409,19 +409,62 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
 {
     COUNT_LAUNCH();
     if (mode == RES_REPLACE && st->done) return;
-    double rr = 0.0, rz = 0.0;
+    double rr = 0.0;
+    Acc<OT> rz;  // r.z in the precision of the iteration that uses it (z = D^-1 r rounded)
     auto src = [&](int64_t o) -> double { return x[o]; };
     auto body = [&](int i, int j, int k, int64_t o, double Av, double) {
         const double rv = on_dirichlet(g, op, i, j, k) ? 0.0 : b[o] - Av;
         const OT ro = (OT)rv;
         r[o] = ro;
         rr = fma(rv, rv, rr);
-        const double rd = (double)ro;
-        rz = fma(rd * (double)dinv[o], rd, rz);
+        rz.add_prod(ro, dinv[o] * ro);
     };
     ECMG_FP64_MARCH(double, ROBIN, CUBE, false, src, body);
-    double v[2] = {rr, rz};
+    double v[2] = {rr, rz.value()};
     if (grid_sum<2>(v, partials, &st->arrive)) res_epilogue(st, v[0], v[1], mode, ch);
+}
+
+// ---- ||f_h||: the free-node right-hand side with the Dirichlet values moved over -------------
+// x holds g_D on Dirichlet nodes and 0 elsewhere, so (A x)_i vanishes at every free node with
+// no Dirichlet neighbour: there f_h,i = b_i. Only the layer next to a Dirichlet face needs the
+// stencil, evaluated here straight from global memory.
+template <bool ROBIN, bool CUBE>
+__global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, const double* __restrict__ beta,
+                                                 const double* __restrict__ x, const double* __restrict__ b,
+                                                 SolveState* st, double* partials)
+{
+    COUNT_LAUNCH();
+    const int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    const Weights<double> wts(op);
+    const bool dx0 = op.bc[0] == 0, dx1 = op.bc[1] == 0, dy0 = op.bc[2] == 0, dy1 = op.bc[3] == 0;
+    const bool dz0 = op.bc[4] == 0, dz1 = op.bc[5] == 0;
+    double ss = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % (g.nx + 1));
+        const int64_t rr_ = t / (g.nx + 1);
+        const int j = (int)(rr_ % (g.ny + 1));
+        const int k = (int)(rr_ / (g.ny + 1));
+        if (on_dirichlet(g, op, i, j, k)) continue;
+        const int64_t o = g.off(i, j, k);
+        double f = b[o];
+        const bool near = (dx0 && i <= 1) || (dx1 && i >= g.nx - 1) || (dy0 && j <= 1) || (dy1 && j >= g.ny - 1) ||
+                          (dz0 && k <= 1) || (dz1 && k >= g.nz - 1);
+        if (near) {
+            auto V = [&](int ddx, int ddy, int ddz) -> double {
+                return x[o + (int64_t)ddz * g.plane + (int64_t)ddy * g.pitch + ddx];
+            };
+            auto be = [&](int ex, int ey, int ez) { return beta[g.off(i - 1 + ex, j - 1 + ey, k - 1 + ez)]; };
+            f -= q1_apply<true, ROBIN, CUBE, double>(V, be(0, 0, 0), be(1, 0, 0), be(0, 1, 0), be(1, 1, 0),
+                                                     be(0, 0, 1), be(1, 0, 1), be(0, 1, 1), be(1, 1, 1), i, j, k, g,
+                                                     op, wts);
+        }
+        ss = fma(f, f, ss);
+    }
+    double v[1] = {ss};
+    if (grid_sum<1>(v, partials, &st->arrive)) {
+        st->fh2 = v[0];
+        st->thresh2 = st->rtol2 * v[0];
+    }
 }
 
 // ---- y = A x (full matrix, for operator checks) ---------------------------------------------
@@ -438,6 +481,13 @@ __global__ void __launch_bounds__(NT) k_apply(const Grid g, const Op op, const T
 }
 
 // ---- K2: residual update and stopping test ----------------------------------------------------
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+__device__ __forceinline__ float& vget(float4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+__device__ __forceinline__ double& vget(double2& v, int c) { return c == 0 ? v.x : v.y; }
+
+// Flat over the padded vector, 16-byte vectors (the layout keeps total a multiple of 8).
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r, const T* __restrict__ q,
                                                     const T* __restrict__ dinv, SolveState* st,
@@ -451,15 +501,27 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
         }
         return;
     }
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::n;
     const T a = (T)st->alpha;
     Acc<T> rz, rr;
+    const int64_t nv = n / W;
+    V* __restrict__ rv4 = reinterpret_cast<V*>(r);
+    const V* __restrict__ qv4 = reinterpret_cast<const V*>(q);
+    const V* __restrict__ dv4 = reinterpret_cast<const V*>(dinv);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
-        T rv = r[t] - a * q[t];
-        r[t] = rv;
-        const T zv = dinv[t] * rv;
-        rz.add_prod(rv, zv);
-        rr.add_prod(rv, rv);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += stride) {
+        V rr4 = rv4[t];
+        const V q4 = qv4[t], d4 = dv4[t];
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const T rv = vget(rr4, c) - a * vget(const_cast<V&>(q4), c);
+            vget(rr4, c) = rv;
+            const T zv = vget(const_cast<V&>(d4), c) * rv;
+            rz.add_prod(rv, zv);
+            rr.add_prod(rv, rv);
+        }
+        rv4[t] = rr4;
     }
     double v[2] = {rz.value(), rr.value()};
     if (grid_sum<2>(v, partials, &st->arrive)) {
@@ -618,6 +680,12 @@ void launch_apply32(const Grid& g, const Op& op, const float* beta, const float*
 {
     const int kz = stencil_kz(g);
     ECMG_VARIANT(k_apply, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, nullptr, x, y, kz);
+}
+void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
+                Partials pr, cudaStream_t s)
+{
+    (has_robin(op) ? (op.cube ? k_fh2<true, true> : k_fh2<true, false>)
+                   : (op.cube ? k_fh2<false, true> : k_fh2<false, false>))<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g, op, beta, x, b, st, pr.buf);
 }
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv, SolveState* st,
                      Partials pr, CondHandles ch, cudaStream_t s)

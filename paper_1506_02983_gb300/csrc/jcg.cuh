@@ -42,6 +42,9 @@ void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* 
 void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y,
                     cudaStream_t s);
 
+// ||f_h||^2 into the level state (x = Dirichlet extension), and the stopping threshold.
+void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
+                Partials pr, cudaStream_t s);
 // r -= alpha q; z = dinv r; r.z and r.r; last block: convergence / next beta.
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv,
                      SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);

@@ -123,7 +123,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NP], double* sh)
 }
 
 template <bool ROBIN, bool CUBE>
-__global__ void __launch_bounds__(NT, 4)
+__global__ void __launch_bounds__(NT, ROBIN ? 3 : 4)
 k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
            const __grid_constant__ CUtensorMap m_dinv, const __grid_constant__ CUtensorMap m_beta,
            const Grid g, const Op op, float* __restrict__ pnew, float* __restrict__ q,
@@ -178,15 +178,30 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
 
     // offset of this thread's node on the plane computed next (plane kb at step t = 2)
     int64_t o = g.plane_base(P0 - 1) + g.in_plane(min(i, g.nx + 1), min(j, g.ny + 1));
-    float w[3][3][3];   // p window [z][y][x], z = k-1, k, k+1
-    float bl[2][2], bh[2][2];  // element betas of slabs k-1 and k, [ey][ex]
-    float pown_prev = 0.f;     // p_old of this thread's node, plane k
-    CSum acc;
-    int t_done = -1;           // last stage waited for
+    // the cells this thread forms in every plane (PX*PY = 340 cells, at most 2 per thread)
+    const int c1 = tid + NT;
+    const bool has1 = c1 < PX * PY;
+    const int sidx0 = (tid / PX) * SX + (tid % PX) + 3;
+    const int sidx1 = has1 ? (c1 / PX) * SX + (c1 % PX) + 3 : 0;
+    // the i, j part of the Dirichlet test is fixed for the thread's column
+    const bool dir_ij = (i == 0 && op.bc[0] == 0) || (i == g.nx && op.bc[1] == 0) ||
+                        (j == 0 && op.bc[2] == 0) || (j == g.ny && op.bc[3] == 0);
+    const bool dir_k0 = op.bc[4] == 0, dir_kn = op.bc[5] == 0;
 
+    float wA[3][3], wB[3][3], wC[3][3];  // three planes of the p window, [y][x]
+    float bA[2][2], bB[2][2];            // element betas of two slabs, [ey][ex]
+    float pown_prev = 0.f;               // p_old of this thread's node, plane k
     float e_cur = 0.f;
-#pragma unroll 3
-    for (int t = 0; t < nplanes; ++t) {
+    CSum acc;
+    int t_done = -1;                     // last stage waited for
+    int t = 0;
+    bool stop = false;
+
+    // One plane: stage t brings node plane kk = P0 + t into wp and beta slab kk-1 into bn;
+    // then node plane kk-1 is computed from the window (wm, w0, wp) = planes (kk-2, kk-1, kk)
+    // and the slabs (bo, bn) = (kk-2, kk-1). The caller rotates the arrays instead of moving
+    // values, so the unrolled loop below needs no register copies.
+    auto step = [&](float(&wm)[3][3], float(&w0)[3][3], float(&wp)[3][3], float(&bo)[2][2], float(&bn)[2][2]) {
         const int kk = P0 + t;
         Stage& S = stage[t % NSTAGE];
         // prefetch e of the node computed at the next step (plane kk), one step ahead
@@ -195,55 +210,63 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
         if (!mbar_wait(&bar[t % NSTAGE], (uint32_t)((t / NSTAGE) & 1))) bad = 1;
         t_done = t;
         // form p of plane kk for the tile plus halo (stage column = node column - (i0 - 4))
-        float(*Pk)[PX] = P[kk & 1];
-        for (int c = tid; c < PX * PY; c += NT) {
-            const int ci = c % PX, cj = c / PX;
-            const int sidx = cj * SX + ci + 3;
-            Pk[cj][ci] = fmaf(S.dinv[sidx], S.r[sidx], bcg * S.pold[sidx]);
-        }
+        float* Pk = &P[kk & 1][0][0];
+        Pk[tid] = fmaf(S.dinv[sidx0], S.r[sidx0], bcg * S.pold[sidx0]);
+        if (has1) Pk[c1] = fmaf(S.dinv[sidx1], S.r[sidx1], bcg * S.pold[sidx1]);
         const float pown_new = S.pold[(ty + 1) * SX + tx + 4];
         __syncthreads();
-        if (bad) break;
+        if (bad) {
+            stop = true;
+            return;
+        }
         if (tid == 0 && t >= 1 && t - 1 + NSTAGE < nplanes) {
             issue(t - 1 + NSTAGE);
             issued_hi = t - 1 + NSTAGE;
         }
+        const float(*Pp)[PX] = P[kk & 1];
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) w[2][dy][dx] = Pk[ty + dy][tx + dx];
+            for (int dx = 0; dx < 3; ++dx) wp[dy][dx] = Pp[ty + dy][tx + dx];
 #pragma unroll
         for (int ey = 0; ey < 2; ++ey)
 #pragma unroll
-            for (int ex = 0; ex < 2; ++ex) bh[ey][ex] = S.beta[(ty + ey) * SX + tx + 3 + ex];
+            for (int ex = 0; ex < 2; ++ex) bn[ey][ex] = S.beta[(ty + ey) * SX + tx + 3 + ex];
 
         if (t >= 2 && owned) {
             const int k = kk - 1;
-            const float xc = w[1][1][1];
-            auto V = [&](int dx, int dy, int dz) -> float { return w[dz + 1][dy + 1][dx + 1]; };
-            const float Av = q1_apply<false, ROBIN, CUBE, float>(V, bl[0][0], bl[0][1], bl[1][0], bl[1][1], bh[0][0], bh[0][1],
-                                             bh[1][0], bh[1][1], i, j, k, g, op, wts);
-            const float qv = on_dirichlet(g, op, i, j, k) ? 0.f : Av;
+            const float xc = w0[1][1];
+            auto V = [&](int dx, int dy, int dz) -> float {
+                return dz < 0 ? wm[dy + 1][dx + 1] : (dz > 0 ? wp[dy + 1][dx + 1] : w0[dy + 1][dx + 1]);
+            };
+            const float Av = q1_apply<false, ROBIN, CUBE, float>(V, bo[0][0], bo[0][1], bo[1][0], bo[1][1], bn[0][0],
+                                                                 bn[0][1], bn[1][0], bn[1][1], i, j, k, g, op, wts);
+            const bool dir = dir_ij || (k == 0 && dir_k0) || (k == g.nz && dir_kn);
+            const float qv = dir ? 0.f : Av;
             pnew[o] = xc;
             q[o] = qv;
             if (ap != 0.f) e[o] = fmaf(ap, pown_prev, e_cur);
             acc.add_prod(xc, qv);
         }
-        // shift the window
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                w[0][dy][dx] = w[1][dy][dx];
-                w[1][dy][dx] = w[2][dy][dx];
-            }
-#pragma unroll
-        for (int ey = 0; ey < 2; ++ey)
-#pragma unroll
-            for (int ex = 0; ex < 2; ++ex) bl[ey][ex] = bh[ey][ex];
         pown_prev = pown_new;
         e_cur = e_next;
         o += g.plane;
+        if (++t >= nplanes) stop = true;
+    };
+    // period 6 = lcm(3 window planes, 2 beta slabs)
+    for (;;) {
+        step(wA, wB, wC, bA, bB);
+        if (stop) break;
+        step(wB, wC, wA, bB, bA);
+        if (stop) break;
+        step(wC, wA, wB, bA, bB);
+        if (stop) break;
+        step(wA, wB, wC, bB, bA);
+        if (stop) break;
+        step(wB, wC, wA, bA, bB);
+        if (stop) break;
+        step(wC, wA, wB, bB, bA);
+        if (stop) break;
     }
 
     if (bad) {
