@@ -93,6 +93,9 @@ typedef struct {
     double dsolve_rtol;     /* relative residual of the direct solve on levels 0, 1 [1e-14]*/
     int32_t exp_variant;    /* ECMG_EXP_SERENDIPITY20 / ECMG_EXP_LAGRANGE27  [SERENDIPITY20]*/
     int32_t true_residual;  /* 1: report the true FP64 residual of every level [1]         */
+    int32_t autotune;       /* MIXED: 1 = ecmg_create times the tile shapes of the FP32
+                               stencil kernel on every level of >= 2^18 nodes and keeps the
+                               fastest (ecmg_autotune); 0 = built-in shape       [0]       */
 } ecmg_options;
 
 /* Per-solve statistics, one entry per level (coarsest first). */
@@ -170,11 +173,29 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
  * 0 K1 FP32 (search direction + operator), 1 K2 FP32 (residual update), 2 FP64 residual with
  * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true.
  * ms_out: mean duration of one launch (host). bytes_out: the algorithmic bytes one launch
- * must move (each owned input read once, each output written once; host). Valid after
+ * must move (each owned input read once, each output written once; host); for kernel 0 the
+ * nodes counted are those off the Dirichlet faces, the only ones it visits. Valid after
  * ecmg_solve; it overwrites the level's work vectors and U~ (kernel 3 uses U~ as its
  * iterate); U and W are never changed. Synchronises the stream. */
 ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,
                              double* ms_out, double* bytes_out);
+
+/* ---- tile shapes of the FP32 stencil kernel (no counterpart in the paper) --------------
+ *
+ * In MIXED mode the stencil kernel of every level runs on tiles of 32 x (8 ry) nodes, each
+ * thread computing ry vertically adjacent nodes, with each block marching kz node planes.
+ * Shapes change only the launch geometry and the order of the partial sums of p.q. */
+
+/* Force the shape of one level (-1 = finest): ry in {1, 2}, kz in 4..1024. Invalid shapes
+ * return ECMG_ERR_INVALID_ARG; FP64 handles have no such kernel (ECMG_ERR_INVALID_ARG). */
+ecmg_status ecmg_set_tiles(ecmg_handle* h, int32_t level, int32_t ry, int32_t kz);
+/* Read the shape of one level into *ry, *kz (host). */
+ecmg_status ecmg_get_tiles(ecmg_handle* h, int32_t level, int32_t* ry, int32_t* kz);
+/* Autotuner: on every MIXED level of at least 2^18 nodes, time each candidate shape (ry in
+ * {1, 2} x kz in {16, 32, 64, 128}) and the current one with `reps` launches each (CUDA
+ * events on the handle's stream) and keep the fastest. Overwrites the level's work vectors;
+ * call it before a solve or between solves. Synchronises the stream. */
+ecmg_status ecmg_autotune(ecmg_handle* h, int32_t reps);
 
 /* ---- error norms without device allocation (no counterpart in the paper) ---------------
  *

@@ -48,6 +48,7 @@ struct Level {
     float *beta32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *pA32 = nullptr, *pB32 = nullptr,
           *q32 = nullptr, *e32 = nullptr;
     PlaneMaps maps;  // TMA descriptors of the FP32 vectors
+    K1Config k1{1, 128};  // tile shape of the FP32 stencil kernel
     int* uniform = nullptr;  // device flag: one beta on the whole level
 };
 
@@ -127,6 +128,7 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
         return fail(ECMG_ERR_INVALID_ARG, "dsolve_rtol must be in (0,1)");
     if (o->exp_variant != ECMG_EXP_SERENDIPITY20 && o->exp_variant != ECMG_EXP_LAGRANGE27)
         return fail(ECMG_ERR_INVALID_ARG, "bad exp_variant");
+    if (o->autotune != 0 && o->autotune != 1) return fail(ECMG_ERR_INVALID_ARG, "autotune must be 0 or 1");
     return ECMG_OK;
 }
 
@@ -294,7 +296,7 @@ void record_level(Rec& R, int l)
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
         auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
-            launch_pq32_tma(v.maps, pin == v.pB32, v.g, v.op, pout, v.q32, v.e32, st, h->part, idx, ch, R.s());
+            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, pout, v.q32, v.e32, st, h->part, idx, ch, R.s());
             launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
         };
         auto replace = [&](float* pnew) {
@@ -404,6 +406,7 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
         ecmg_status ls = ECMG_OK;
         if (s.status == 3) ls = ECMG_ERR_NO_CONVERGENCE;
         if (s.status == 4) ls = ECMG_ERR_BREAKDOWN;
+        if (s.status == 5) ls = ECMG_ERR_CUDA;  // a staged copy of the FP32 stencil never arrived
         if (ls == ECMG_ERR_BREAKDOWN || (ls != ECMG_OK && worst == ECMG_OK)) worst = ls;
     }
     st.status = worst;
@@ -413,6 +416,108 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
 }
 
 int resolve_level(ecmg_handle* h, int level) { return level < 0 ? h->L - 1 : level; }
+
+// Forget the recorded graph (it holds launch shapes that no longer apply).
+void drop_graph(ecmg_handle* h)
+{
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    h->graph_first = -1;
+}
+
+// Mean milliseconds of `reps` launches of one kernel on level l (CUDA events on the handle's
+// stream, one untimed launch first), on a scratch level state that no solve uses.
+double time_launches(ecmg_handle* h, int l, int which, int reps)
+{
+    Level& v = h->lv[l];
+    SolveState* st = h->states + (MAX_LEVELS - 1);
+    SolveState tmpl = {};
+    tmpl.rho = 1.0;
+    tmpl.beta = 0.5;
+    tmpl.alpha = 1e-30;
+    tmpl.alpha_prev = 1e-30;
+    tmpl.max_iters = 1 << 30;
+    tmpl.thresh2 = -1.0;
+    tmpl.inner2 = -1.0;
+    cudaStream_t s = h->user_stream;
+    const CondHandles none{0, 0, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double total = 0.0;
+    try {
+        ck(cudaEventCreate(&e0));
+        ck(cudaEventCreate(&e1));
+        for (int rep = 0; rep <= reps; ++rep) {
+            ck(cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s));
+            ck(cudaEventRecord(e0, s));
+            switch (which) {
+            case 0: launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, v.pB32, v.q32, v.e32, st, h->part, 1, none, s); break;
+            case 1: launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
+            case 2: launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
+            case 3: launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
+            case 4: launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, none, s); break;
+            case 5: launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, s); break;
+            case 6: {
+                const Level& u1 = h->lv[l - 1];
+                const Level& u0 = h->lv[l - 2];
+                launch_exp_finite(h->opt.exp_variant, v.g, v.op, u1.g, u1.U, u0.g, u0.U, v.r, v.q, s);
+                break;
+            }
+            default: {
+                const Level& u1 = h->lv[l - 1];
+                launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, s);
+                break;
+            }
+            }
+            ck(cudaEventRecord(e1, s));
+            ck(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) total += ms;
+        }
+        ck(cudaGetLastError());
+    } catch (CudaFail&) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return total / reps;
+}
+
+// Levels below this many nodes keep the heuristic shape: their stencil time is launch-bound.
+constexpr int64_t AUTOTUNE_MIN_NODES = 1 << 18;
+
+// Time every candidate tile shape of the FP32 stencil kernel on each MIXED level that is large
+// enough, and keep the fastest (ties keep the earlier candidate, so the choice is repeatable
+// when timings agree).
+void autotune(ecmg_handle* h, int reps)
+{
+    bool changed = false;
+    for (int l = 2; l < h->L; ++l) {
+        Level& v = h->lv[l];
+        if (!v.r32) continue;
+        if ((int64_t)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1) < AUTOTUNE_MIN_NODES) continue;
+        K1Config cand[32];
+        const int n = k1_candidates(v.g, cand, 32);
+        const K1Config start = v.k1;
+        K1Config best = start;
+        double best_ms = time_launches(h, l, 0, reps);
+        for (int c = 0; c < n; ++c) {
+            v.k1 = cand[c];
+            const double ms = time_launches(h, l, 0, reps);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand[c];
+            }
+        }
+        v.k1 = best;
+        changed |= best.ry != start.ry || best.kz != start.kz;
+    }
+    if (changed) drop_graph(h);
+}
 
 }  // namespace
 
@@ -429,6 +534,7 @@ void ecmg_default_options(ecmg_options* o)
     o->dsolve_rtol = 1e-14;
     o->exp_variant = ECMG_EXP_SERENDIPITY20;
     o->true_residual = 1;
+    o->autotune = 0;
 }
 
 ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, uint64_t* bytes)
@@ -464,6 +570,7 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
     try {
         for (int i = 0; i < 3; ++i) ck(cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
         const bool mixed = opt->precision == ECMG_MIXED;
+        if (mixed) ck(k1_prepare());
         int maxb = 0;
         for (int l = 0; l < h->L; ++l) {
             Level& v = h->lv[l];
@@ -491,10 +598,9 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
                 v.pB32 = dalloc<float>(h, n);
                 v.q32 = dalloc<float>(h, n);
                 v.e32 = dalloc<float>(h, n);
-                if (!make_plane_map(&v.maps.r, v.r32, v.g) || !make_plane_map(&v.maps.pA, v.pA32, v.g) ||
-                    !make_plane_map(&v.maps.pB, v.pB32, v.g) || !make_plane_map(&v.maps.dinv, v.dinv32, v.g) ||
-                    !make_plane_map(&v.maps.beta, v.beta32, v.g))
+                if (!make_plane_maps(&v.maps, v.r32, v.pA32, v.pB32, v.dinv32, v.beta32, v.g))
                     throw CudaFail{cudaErrorNotSupported};
+                v.k1 = k1_default(v.g, v.op);
                 maxb = std::max(maxb, max_tma_blocks(v.g));
             }
             maxb = std::max(maxb, std::max(max_stencil_blocks(v.g), max_stream_blocks()));
@@ -508,6 +614,7 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
         ck(cudaMallocHost(&h->host_states, sizeof(SolveState) * MAX_LEVELS));
         ck(cudaMallocHost(&h->host_norms, sizeof(double) * 2048));
         ck(cudaStreamSynchronize(h->cap[0]));
+        if (mixed && opt->autotune) autotune(h, 3);
     } catch (CudaFail& f) {
         ecmg_destroy(h);
         if (f.e == cudaErrorMemoryAllocation) return fail(ECMG_ERR_OOM, "device allocation failed");
@@ -683,62 +790,51 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
     if (which >= 6 && l < 2) return fail(ECMG_ERR_INVALID_ARG, "EXP kernels need level >= 2");
     const double N = (double)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1);
     const double E = (double)v.g.nx * v.g.ny * v.g.nz;
-    const double bytes[8] = {28 * N + 4 * E, 16 * N, 24 * N + 8 * E, 56 * N + 8 * E,
+    // K1 visits only the nodes off the Dirichlet faces (p = q = 0 there stay untouched)
+    const double N1 = (double)k1_nodes(v.g, v.op);
+    const double bytes[8] = {28 * N1 + 4 * E, 16 * N, 24 * N + 8 * E, 56 * N + 8 * E,
                              32 * N,         32 * N + 8 * E, 16 * N + 8 * (N / 8 + N / 64), 17 * N};
     *bytes_out = bytes[which];
-    SolveState* st = h->states + (MAX_LEVELS - 1);  // scratch state, never used by a solve
-    SolveState tmpl = {};
-    tmpl.rho = 1.0;
-    tmpl.beta = 0.5;
-    tmpl.alpha = 1e-30;
-    tmpl.alpha_prev = 1e-30;
-    tmpl.max_iters = 1 << 30;
-    tmpl.thresh2 = -1.0;
-    tmpl.inner2 = -1.0;
-    cudaStream_t s = h->user_stream;
-    const CondHandles none{0, 0, 0};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double total = 0.0;
     try {
-        ck(cudaEventCreate(&e0));
-        ck(cudaEventCreate(&e1));
-        for (int rep = 0; rep <= reps; ++rep) {
-            ck(cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s));
-            ck(cudaEventRecord(e0, s));
-            switch (which) {
-            case 0: launch_pq32_tma(v.maps, 0, v.g, v.op, v.pB32, v.q32, v.e32, st, h->part, 1, none, s); break;
-            case 1: launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
-            case 2: launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
-            case 3: launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
-            case 4: launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, none, s); break;
-            case 5: launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, s); break;
-            case 6: {
-                const Level& u1 = h->lv[l - 1];
-                const Level& u0 = h->lv[l - 2];
-                launch_exp_finite(h->opt.exp_variant, v.g, v.op, u1.g, u1.U, u0.g, u0.U, v.r, v.q, s);
-                break;
-            }
-            default: {
-                const Level& u1 = h->lv[l - 1];
-                launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, s);
-                break;
-            }
-            }
-            ck(cudaEventRecord(e1, s));
-            ck(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            ck(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) total += ms;
-        }
-        ck(cudaGetLastError());
+        *ms_out = time_launches(h, l, which, reps);
     } catch (CudaFail& f) {
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
         return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    *ms_out = total / reps;
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_set_tiles(ecmg_handle* h, int32_t level, int32_t ry, int32_t kz)
+{
+    if (!h) return fail(ECMG_ERR_INVALID_ARG, "null handle");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    if (!h->lv[l].r32) return fail(ECMG_ERR_INVALID_ARG, "handle has no FP32 vectors");
+    const K1Config c{ry, kz};
+    if (!k1_valid(c)) return fail(ECMG_ERR_INVALID_ARG, "tile shape: ry must be 1 or 2 and kz in 4..1024");
+    h->lv[l].k1 = c;
+    drop_graph(h);
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_get_tiles(ecmg_handle* h, int32_t level, int32_t* ry, int32_t* kz)
+{
+    if (!h || !ry || !kz) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    if (!h->lv[l].r32) return fail(ECMG_ERR_INVALID_ARG, "handle has no FP32 vectors");
+    *ry = h->lv[l].k1.ry;
+    *kz = h->lv[l].k1.kz;
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_autotune(ecmg_handle* h, int32_t reps)
+{
+    if (!h || reps < 1) return fail(ECMG_ERR_INVALID_ARG, "bad argument");
+    try {
+        autotune(h, reps);
+    } catch (CudaFail& f) {
+        return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+    }
     return ECMG_OK;
 }
 

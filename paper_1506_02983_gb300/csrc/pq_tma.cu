@@ -28,21 +28,48 @@ __device__ unsigned long long g_launches = 0;  // kernel executions of this file
         atomicAdd(&g_launches, 1ull)
 
 constexpr int TBX = 32, TBY = 8, NT = TBX * TBY;
-constexpr int SX = 40, SY = 10;            // staged box: columns from node i0-4, rows from j0-1
-constexpr int BOXF = SX * SY;              // floats per staged vector
-constexpr int BOXF_PAD = 416;              // 1664 B: keeps every TMA destination 128 B aligned
+constexpr int SX = 40;                     // staged columns: from the 16-byte boundary at or below node i0-1
 constexpr int NSTAGE = 4;
-constexpr int PX = TBX + 2, PY = TBY + 2;  // formed plane of p: tile plus one-node halo
-constexpr uint32_t STAGE_BYTES = 4u * BOXF * sizeof(float);
 constexpr long long WAIT_LIMIT = 1ll << 22; // polls before a wait is declared lost
-constexpr int KZ_TARGET = 64;
 
-struct __align__(128) Stage {
-    float r[BOXF_PAD];
-    float pold[BOXF_PAD];
-    float dinv[BOXF_PAD];
-    float beta[BOXF_PAD];
+// Sizes of a tile whose threads compute RY node rows each.
+template <int RY>
+struct Shape {
+    static constexpr int NY = TBY * RY;                   // node rows of the tile
+    static constexpr int SY = NY + 2;                     // staged rows: from node j0-1
+    static constexpr int BOXF = SX * SY;                  // floats per staged vector
+    static constexpr int BOXF_PAD = (BOXF + 31) / 32 * 32;  // 128 B multiple: TMA destinations stay aligned
+    static constexpr int PX = TBX + 2, PY = NY + 2;       // formed plane of p: tile plus one-node halo
+    static constexpr int NCELL = PX * PY;
+    static constexpr int NFORM = (NCELL + NT - 1) / NT;   // formed cells per thread (at most)
+    static constexpr uint32_t STAGE_BYTES = 4u * BOXF * sizeof(float);
 };
+
+template <int RY>
+struct __align__(128) Stage {
+    float r[Shape<RY>::BOXF_PAD];
+    float pold[Shape<RY>::BOXF_PAD];
+    float dinv[Shape<RY>::BOXF_PAD];
+    float beta[Shape<RY>::BOXF_PAD];
+};
+// Dynamic shared memory of a block: the stage ring plus slack to align it to 128 B (TMA
+// destinations must be 128-byte aligned; the runtime only guarantees 16).
+template <int RY>
+constexpr size_t stage_smem()
+{
+    return NSTAGE * sizeof(Stage<RY>) + 128;
+}
+
+// Nodes K1 visits: every node not on a Dirichlet face (those keep p = q = 0).
+struct Range {
+    int ilo, ihi, jlo, jhi, klo, khi;
+};
+inline Range k1_range(const Grid& g, const Op& op)
+{
+    return Range{op.bc[0] == 0 ? 1 : 0, op.bc[1] == 0 ? g.nx - 1 : g.nx,
+                 op.bc[2] == 0 ? 1 : 0, op.bc[3] == 0 ? g.ny - 1 : g.ny,
+                 op.bc[4] == 0 ? 1 : 0, op.bc[5] == 0 ? g.nz - 1 : g.nz};
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -122,16 +149,18 @@ __device__ __forceinline__ void block_sum(double (&v)[NP], double* sh)
     __syncthreads();
 }
 
-template <bool ROBIN, bool CUBE>
-__global__ void __launch_bounds__(NT, ROBIN ? 3 : 4)
+template <bool ROBIN, bool CUBE, int RY>
+__global__ void __launch_bounds__(NT, RY == 1 ? (ROBIN ? 3 : 4) : 2)
 k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
            const __grid_constant__ CUtensorMap m_dinv, const __grid_constant__ CUtensorMap m_beta,
-           const Grid g, const Op op, float* __restrict__ pnew, float* __restrict__ q,
+           const Grid g, const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q,
            float* __restrict__ e, SolveState* st, double* partials, int pidx, CondHandles ch, int kz)
 {
+    using S = Shape<RY>;
     COUNT_LAUNCH();
-    __shared__ Stage stage[NSTAGE];
-    __shared__ float P[2][PY][PX];
+    extern __shared__ __align__(128) unsigned char k1_smem[];
+    Stage<RY>* stage = reinterpret_cast<Stage<RY>*>(k1_smem + ((128u - (smem_u32(k1_smem) & 127u)) & 127u));
+    __shared__ float P[2][S::PY][S::PX];
     __shared__ __align__(8) uint64_t bar[NSTAGE];
     __shared__ double red[32];
     __shared__ int bad;
@@ -140,13 +169,17 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
 
     if (st->done) return;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TBX * ty;
-    const int i0 = blockIdx.x * TBX, j0 = blockIdx.y * TBY;
-    const int kb = blockIdx.z * kz;
-    const int ke = min(kb + kz, g.nz + 1);
+    const int i0 = rg.ilo + blockIdx.x * TBX, j0 = rg.jlo + blockIdx.y * S::NY;
+    const int kb = rg.klo + blockIdx.z * kz;
+    const int ke = min(kb + kz, rg.khi + 1);
     const int P0 = kb - 1;                 // first staged node plane
     const int nplanes = ke - kb + 2;       // planes kb-1 .. ke
     const float bcg = (float)st->beta;
     const float ap = (float)st->alpha_prev;
+    // Node i sits in column i + XL of the padded layout. The box starts at the 16-byte
+    // boundary bx at or below node i0-1's column, and node i0-1 is staged column sh.
+    const int bx = (i0 + XL - 1) & ~3;
+    const int sh = i0 + XL - 1 - bx;
 
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
@@ -156,42 +189,43 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     __syncthreads();
 
     // Stage t holds node plane P0+t (memory plane P0+t+1) and element slab P0+t-1 (memory
-    // plane P0+t). Column i0 of the padded layout is node i0-4, row j0 is node j0-1.
+    // plane P0+t); row 0 of a box is node row j0-1 (memory row j0).
     auto issue = [&](int t) {
-        Stage& S = stage[t % NSTAGE];
+        Stage<RY>& St = stage[t % NSTAGE];
         uint64_t* b = &bar[t % NSTAGE];
         const int kk = P0 + t;
-        mbar_expect_tx(b, STAGE_BYTES);
-        tma_load_3d(S.r, &m_r, i0, j0, kk + 1, b);
-        tma_load_3d(S.pold, &m_pold, i0, j0, kk + 1, b);
-        tma_load_3d(S.dinv, &m_dinv, i0, j0, kk + 1, b);
-        tma_load_3d(S.beta, &m_beta, i0, j0, kk, b);
+        mbar_expect_tx(b, S::STAGE_BYTES);
+        tma_load_3d(St.r, &m_r, bx, j0, kk + 1, b);
+        tma_load_3d(St.pold, &m_pold, bx, j0, kk + 1, b);
+        tma_load_3d(St.dinv, &m_dinv, bx, j0, kk + 1, b);
+        tma_load_3d(St.beta, &m_beta, bx, j0, kk, b);
     };
     if (tid == 0) {
         for (int t = 0; t < NSTAGE && t < nplanes; ++t) issue(t);
         issued_hi = min(NSTAGE, nplanes) - 1;
     }
 
-    const int i = i0 + tx, j = j0 + ty;
-    const bool owned = (i <= g.nx) && (j <= g.ny);
+    // this thread: column i, node rows jt .. jt+RY-1, of which the first nown are in range
+    const int i = i0 + tx, jt = j0 + ty * RY;
+    const int nown = i <= rg.ihi ? min(RY, rg.jhi - jt + 1) : 0;
     const Weights<float> wts(op);
+    const int pitch = g.pitch;
 
-    // offset of this thread's node on the plane computed next (plane kb at step t = 2)
-    int64_t o = g.plane_base(P0 - 1) + g.in_plane(min(i, g.nx + 1), min(j, g.ny + 1));
-    // the cells this thread forms in every plane (PX*PY = 340 cells, at most 2 per thread)
-    const int c1 = tid + NT;
-    const bool has1 = c1 < PX * PY;
-    const int sidx0 = (tid / PX) * SX + (tid % PX) + 3;
-    const int sidx1 = has1 ? (c1 / PX) * SX + (c1 % PX) + 3 : 0;
-    // the i, j part of the Dirichlet test is fixed for the thread's column
-    const bool dir_ij = (i == 0 && op.bc[0] == 0) || (i == g.nx && op.bc[1] == 0) ||
-                        (j == 0 && op.bc[2] == 0) || (j == g.ny && op.bc[3] == 0);
-    const bool dir_k0 = op.bc[4] == 0, dir_kn = op.bc[5] == 0;
+    // offset of the thread's first node on the plane computed next (plane kb at step t = 2)
+    int64_t o = g.plane_base(P0 - 1) + g.in_plane(min(i, g.nx + 1), min(jt, g.ny + 1));
+    // the cells of the formed plane this thread fills, as staged offsets
+    int sidx[S::NFORM];
+#pragma unroll
+    for (int f = 0; f < S::NFORM; ++f) {
+        const int c = tid + f * NT;
+        sidx[f] = c < S::NCELL ? (c / S::PX) * SX + (c % S::PX) + sh : -1;
+    }
 
-    float wA[3][3], wB[3][3], wC[3][3];  // three planes of the p window, [y][x]
-    float bA[2][2], bB[2][2];            // element betas of two slabs, [ey][ex]
-    float pown_prev = 0.f;               // p_old of this thread's node, plane k
-    float e_cur = 0.f;
+    float wA[RY + 2][3], wB[RY + 2][3], wC[RY + 2][3];  // three planes of the p window, [y][x]
+    float bA[RY + 1][2], bB[RY + 1][2];                 // element betas of two slabs, [ey][ex]
+    float pown_prev[RY], e_cur[RY];                     // p_old and e of the own nodes, plane k
+#pragma unroll
+    for (int r = 0; r < RY; ++r) pown_prev[r] = e_cur[r] = 0.f;
     CSum acc;
     int t_done = -1;                     // last stage waited for
     int t = 0;
@@ -201,19 +235,27 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     // then node plane kk-1 is computed from the window (wm, w0, wp) = planes (kk-2, kk-1, kk)
     // and the slabs (bo, bn) = (kk-2, kk-1). The caller rotates the arrays instead of moving
     // values, so the unrolled loop below needs no register copies.
-    auto step = [&](float(&wm)[3][3], float(&w0)[3][3], float(&wp)[3][3], float(&bo)[2][2], float(&bn)[2][2]) {
+    auto step = [&](float(&wm)[RY + 2][3], float(&w0)[RY + 2][3], float(&wp)[RY + 2][3],
+                    float(&bo)[RY + 1][2], float(&bn)[RY + 1][2]) {
         const int kk = P0 + t;
-        Stage& S = stage[t % NSTAGE];
-        // prefetch e of the node computed at the next step (plane kk), one step ahead
-        float e_next = 0.f;
-        if (ap != 0.f && owned && t >= 1) e_next = e[o + g.plane];
+        Stage<RY>& St = stage[t % NSTAGE];
+        // prefetch e of the nodes computed at the next step (plane kk), one step ahead
+        float e_next[RY];
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+            e_next[r] = (ap != 0.f && r < nown && t >= 1) ? e[o + g.plane + r * pitch] : 0.f;
         if (!mbar_wait(&bar[t % NSTAGE], (uint32_t)((t / NSTAGE) & 1))) bad = 1;
         t_done = t;
-        // form p of plane kk for the tile plus halo (stage column = node column - (i0 - 4))
+        // form p of plane kk for the tile plus halo
         float* Pk = &P[kk & 1][0][0];
-        Pk[tid] = fmaf(S.dinv[sidx0], S.r[sidx0], bcg * S.pold[sidx0]);
-        if (has1) Pk[c1] = fmaf(S.dinv[sidx1], S.r[sidx1], bcg * S.pold[sidx1]);
-        const float pown_new = S.pold[(ty + 1) * SX + tx + 4];
+#pragma unroll
+        for (int f = 0; f < S::NFORM; ++f) {
+            const int s = sidx[f];
+            if ((f + 1) * NT <= S::NCELL || s >= 0) Pk[tid + f * NT] = fmaf(St.dinv[s], St.r[s], bcg * St.pold[s]);
+        }
+        float pown_new[RY];
+#pragma unroll
+        for (int r = 0; r < RY; ++r) pown_new[r] = St.pold[(ty * RY + r + 1) * SX + tx + 1 + sh];
         __syncthreads();
         if (bad) {
             stop = true;
@@ -223,33 +265,43 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
             issue(t - 1 + NSTAGE);
             issued_hi = t - 1 + NSTAGE;
         }
-        const float(*Pp)[PX] = P[kk & 1];
+        const float(*Pp)[S::PX] = P[kk & 1];
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
+        for (int yy = 0; yy < RY + 2; ++yy)
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) wp[dy][dx] = Pp[ty + dy][tx + dx];
+            for (int dx = 0; dx < 3; ++dx) wp[yy][dx] = Pp[ty * RY + yy][tx + dx];
+        const float* Sb = St.beta + ty * RY * SX + tx + sh;
 #pragma unroll
-        for (int ey = 0; ey < 2; ++ey)
+        for (int yy = 0; yy < RY + 1; ++yy)
 #pragma unroll
-            for (int ex = 0; ex < 2; ++ex) bn[ey][ex] = S.beta[(ty + ey) * SX + tx + 3 + ex];
+            for (int ex = 0; ex < 2; ++ex) bn[yy][ex] = Sb[yy * SX + ex];
 
-        if (t >= 2 && owned) {
+        if (t >= 2) {
             const int k = kk - 1;
-            const float xc = w0[1][1];
-            auto V = [&](int dx, int dy, int dz) -> float {
-                return dz < 0 ? wm[dy + 1][dx + 1] : (dz > 0 ? wp[dy + 1][dx + 1] : w0[dy + 1][dx + 1]);
-            };
-            const float Av = q1_apply<false, ROBIN, CUBE, float>(V, bo[0][0], bo[0][1], bo[1][0], bo[1][1], bn[0][0],
-                                                                 bn[0][1], bn[1][0], bn[1][1], i, j, k, g, op, wts);
-            const bool dir = dir_ij || (k == 0 && dir_k0) || (k == g.nz && dir_kn);
-            const float qv = dir ? 0.f : Av;
-            pnew[o] = xc;
-            q[o] = qv;
-            if (ap != 0.f) e[o] = fmaf(ap, pown_prev, e_cur);
-            acc.add_prod(xc, qv);
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                if (r < nown) {
+                    auto V = [&](int dx, int dy, int dz) -> float {
+                        return dz < 0 ? wm[r + 1 + dy][dx + 1]
+                                      : (dz > 0 ? wp[r + 1 + dy][dx + 1] : w0[r + 1 + dy][dx + 1]);
+                    };
+                    const float xc = w0[r + 1][1];
+                    const float Av = q1_apply<false, ROBIN, CUBE, float>(
+                        V, bo[r][0], bo[r][1], bo[r + 1][0], bo[r + 1][1], bn[r][0], bn[r][1], bn[r + 1][0],
+                        bn[r + 1][1], i, jt + r, k, g, op, wts);
+                    const int64_t orr = o + r * pitch;
+                    pnew[orr] = xc;
+                    q[orr] = Av;
+                    if (ap != 0.f) e[orr] = fmaf(ap, pown_prev[r], e_cur[r]);
+                    acc.add_prod(xc, Av);
+                }
+            }
         }
-        pown_prev = pown_new;
-        e_cur = e_next;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            pown_prev[r] = pown_new[r];
+            e_cur[r] = e_next[r];
+        }
         o += g.plane;
         if (++t >= nplanes) stop = true;
     };
@@ -312,20 +364,15 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     }
 }
 
-inline int tma_kz(const Grid& g)
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+inline dim3 k1_grid(const Range& rg, const K1Config& c)
 {
-    const int gx = (g.nx + 1 + TBX - 1) / TBX, gy = (g.ny + 1 + TBY - 1) / TBY;
-    int gz = (152 * 3 + gx * gy - 1) / (gx * gy);
-    int kz = (g.nz + 1 + gz - 1) / gz;
-    if (kz < 8) kz = 8;
-    if (kz > KZ_TARGET) kz = KZ_TARGET;
-    return kz;
+    return dim3(cdiv(max(rg.ihi - rg.ilo + 1, 1), TBX), cdiv(max(rg.jhi - rg.jlo + 1, 1), TBY * c.ry),
+                cdiv(max(rg.khi - rg.klo + 1, 1), c.kz));
 }
 
-inline dim3 tma_grid(const Grid& g, int kz)
-{
-    return dim3((g.nx + 1 + TBX - 1) / TBX, (g.ny + 1 + TBY - 1) / TBY, (g.nz + 1 + kz - 1) / kz);
-}
+int ry_index(int ry) { return ry == 1 ? 0 : 1; }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -345,36 +392,120 @@ EncodeTiled encoder()
     return fn;
 }
 
-}  // namespace
-
-bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g)
+bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy)
 {
     EncodeTiled enc = encoder();
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 3), (cuuint64_t)(g.nz + 3)};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
-    const cuuint32_t box[3] = {SX, SY, 1};
+    const cuuint32_t box[3] = {SX, (cuuint32_t)sy, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int max_tma_blocks(const Grid& g)
+template <bool ROBIN, bool CUBE, int RY>
+cudaError_t prepare_one()
 {
-    const dim3 d = tma_grid(g, tma_kz(g));
-    return (int)(d.x * d.y * d.z);
+    return cudaFuncSetAttribute(k_pq32_tma<ROBIN, CUBE, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem<RY>());
 }
 
-void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const Grid& g, const Op& op, float* pnew, float* q,
-                     float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, cudaStream_t s)
+template <int RY>
+cudaError_t prepare_ry()
 {
-    const int kz = tma_kz(g);
+    cudaError_t e = prepare_one<false, false, RY>();
+    if (e == cudaSuccess) e = prepare_one<false, true, RY>();
+    if (e == cudaSuccess) e = prepare_one<true, false, RY>();
+    if (e == cudaSuccess) e = prepare_one<true, true, RY>();
+    return e;
+}
+
+template <int RY>
+void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, float* pnew,
+               float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, cudaStream_t s)
+{
+    const int v = ry_index(RY);
+    const Range rg = k1_range(g, op);
     bool robin = false;
     for (int f = 0; f < 6; ++f) robin |= op.alpha[f] != 0.0;
-    (robin ? (op.cube ? k_pq32_tma<true, true> : k_pq32_tma<true, false>)
-           : (op.cube ? k_pq32_tma<false, true> : k_pq32_tma<false, false>))<<<tma_grid(g, kz), dim3(TBX, TBY), 0, s>>>(m.r, pold_is_b ? m.pB : m.pA, m.dinv, m.beta, g, op, pnew,
-                                                        q, e, st, pr.buf, pidx, ch, kz);
+    auto kern = robin ? (op.cube ? k_pq32_tma<true, true, RY> : k_pq32_tma<true, false, RY>)
+                      : (op.cube ? k_pq32_tma<false, true, RY> : k_pq32_tma<false, false, RY>);
+    kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY>(), s>>>(m.r[v], pold_is_b ? m.pB[v] : m.pA[v], m.dinv[v],
+                                                                  m.beta[v], g, op, rg, pnew, q, e, st, pr.buf,
+                                                                  pidx, ch, c.kz);
+}
+
+}  // namespace
+
+bool make_plane_maps(PlaneMaps* m, const float* r, const float* pA, const float* pB, const float* dinv,
+                     const float* beta, const Grid& g)
+{
+    for (int v = 0; v < K1_NRY; ++v) {
+        const int sy = TBY * K1_RY[v] + 2;
+        if (!make_plane_map(&m->r[v], r, g, sy) || !make_plane_map(&m->pA[v], pA, g, sy) ||
+            !make_plane_map(&m->pB[v], pB, g, sy) || !make_plane_map(&m->dinv[v], dinv, g, sy) ||
+            !make_plane_map(&m->beta[v], beta, g, sy))
+            return false;
+    }
+    return true;
+}
+
+cudaError_t k1_prepare()
+{
+    cudaError_t e = prepare_ry<1>();
+    if (e == cudaSuccess) e = prepare_ry<2>();
+    return e;
+}
+
+bool k1_valid(const K1Config& c)
+{
+    return (c.ry == 1 || c.ry == 2) && c.kz >= 4 && c.kz <= 1024;
+}
+
+// One node row per thread (measured fastest on cubes of 256^3 and 512^3 nodes), and enough
+// blocks for about three per SM (152 SMs) with at most 128 planes per block.
+K1Config k1_default(const Grid& g, const Op& op)
+{
+    K1Config c{1, 128};
+    const Range rg = k1_range(g, op);
+    const dim3 d = k1_grid(rg, K1Config{c.ry, 1 << 30});
+    const int nk = max(rg.khi - rg.klo + 1, 1);
+    const int gz = cdiv(152 * 3, (int)(d.x * d.y));
+    c.kz = min(max(cdiv(nk, gz), 8), 128);
+    return c;
+}
+
+int k1_candidates(const Grid& g, K1Config* out, int cap)
+{
+    (void)g;
+    const int kzs[4] = {16, 32, 64, 128};
+    int n = 0;
+    for (int v = 0; v < K1_NRY; ++v)
+        for (int z = 0; z < 4; ++z)
+            if (n < cap) out[n++] = K1Config{K1_RY[v], kzs[z]};
+    return n;
+}
+
+int64_t k1_nodes(const Grid& g, const Op& op)
+{
+    const Range rg = k1_range(g, op);
+    return (int64_t)max(rg.ihi - rg.ilo + 1, 0) * max(rg.jhi - rg.jlo + 1, 0) * max(rg.khi - rg.klo + 1, 0);
+}
+
+int max_tma_blocks(const Grid& g)
+{
+    // largest grid of any valid shape: ry = 1, kz = 4, all nodes in range
+    return cdiv(g.nx + 1, TBX) * cdiv(g.ny + 1, TBY) * cdiv(g.nz + 1, 4);
+}
+
+void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op,
+                     float* pnew, float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch,
+                     cudaStream_t s)
+{
+    if (c.ry == 1) launch_ry<1>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, s);
+    else launch_ry<2>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, s);
 }
 
 unsigned long long launches_pq_tma()

@@ -7,20 +7,41 @@
 
 namespace ecmg {
 
-// Tensor maps of one level's FP32 vectors for plane boxes of 40 x 10 x 1 elements.
+// Node rows a thread of K1 computes (the tile is 32 x 8*ry nodes), one tensor-map set each.
+constexpr int K1_NRY = 2;
+constexpr int K1_RY[K1_NRY] = {1, 2};
+
+// Tensor maps of one level's FP32 vectors; set v stages boxes of 40 x (8*K1_RY[v]+2) x 1.
 struct PlaneMaps {
-    CUtensorMap r, pA, pB, dinv, beta;
+    CUtensorMap r[K1_NRY], pA[K1_NRY], pB[K1_NRY], dinv[K1_NRY], beta[K1_NRY];
 };
 
-// Encode a 3D tensor map over one padded FP32 level vector. False if the driver entry point
-// is unavailable or the encoding is rejected.
-bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g);
+// Tile shape of K1 on one level: ry node rows per thread, kz planes marched per block.
+struct K1Config {
+    int ry;
+    int kz;
+};
 
+// Encode the tensor maps of one level. False if the driver entry point is unavailable or an
+// encoding is rejected.
+bool make_plane_maps(PlaneMaps* m, const float* r, const float* pA, const float* pB, const float* dinv,
+                     const float* beta, const Grid& g);
+
+// Set the shared-memory limit of every K1 instantiation on the current device.
+cudaError_t k1_prepare();
+// Heuristic tile shape, the candidate shapes an autotuner may try, and validity.
+K1Config k1_default(const Grid& g, const Op& op);
+int k1_candidates(const Grid& g, K1Config* out, int cap);
+bool k1_valid(const K1Config& c);
+// Nodes K1 computes on this level: every node off the Dirichlet faces.
+int64_t k1_nodes(const Grid& g, const Op& op);
+// Most blocks any valid shape launches on this grid (size of the partials buffer).
 int max_tma_blocks(const Grid& g);
 
 // p = D^-1 r + beta p_old (p_old = pA or pB), q = A p, e += alpha_prev p_old, p.q.
-void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const Grid& g, const Op& op, float* pnew, float* q,
-                     float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, cudaStream_t s);
+void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op,
+                     float* pnew, float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch,
+                     cudaStream_t s);
 
 unsigned long long launches_pq_tma();
 

@@ -39,7 +39,7 @@ class ecmg_problem(C.Structure):
 class ecmg_options(C.Structure):
     _fields_ = [("rtol", C.c_double), ("precision", C.c_int32), ("inner_rtol", C.c_double),
                 ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("dsolve_rtol", C.c_double),
-                ("exp_variant", C.c_int32), ("true_residual", C.c_int32)]
+                ("exp_variant", C.c_int32), ("true_residual", C.c_int32), ("autotune", C.c_int32)]
 
 
 class ecmg_stats(C.Structure):
@@ -68,6 +68,9 @@ _SIGS = {
     "ecmg_kernel_launches": (_I32, [C.POINTER(C.c_uint64)]),
     "ecmg_error_norms_noalloc": (_I32, [_P, _P, C.c_int64, _P, C.POINTER(_D), C.POINTER(_D)]),
     "ecmg_time_kernel": (_I32, [_H, _I32, _I32, _I32, C.POINTER(_D), C.POINTER(_D)]),
+    "ecmg_set_tiles": (_I32, [_H, _I32, _I32, _I32]),
+    "ecmg_get_tiles": (_I32, [_H, _I32, C.POINTER(_I32), C.POINTER(_I32)]),
+    "ecmg_autotune": (_I32, [_H, _I32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -196,6 +199,19 @@ class Solver:
         check(ecmg_time_kernel(self.handle, int(level), int(which), int(reps), C.byref(ms), C.byref(nb)),
               "ecmg_time_kernel")
         return ms.value, nb.value
+
+    def set_tiles(self, ry, kz, level=-1):
+        """Force the FP32 stencil tile shape of a level (MIXED handles)."""
+        check(ecmg_set_tiles(self.handle, int(level), int(ry), int(kz)), "ecmg_set_tiles")
+
+    def get_tiles(self, level=-1):
+        ry, kz = C.c_int32(), C.c_int32()
+        check(ecmg_get_tiles(self.handle, int(level), C.byref(ry), C.byref(kz)), "ecmg_get_tiles")
+        return ry.value, kz.value
+
+    def autotune(self, reps=3):
+        """Time the candidate stencil tile shapes on every large MIXED level; keep the fastest."""
+        check(ecmg_autotune(self.handle, int(reps)), "ecmg_autotune")
 
     def close(self):
         if getattr(self, "handle", None):

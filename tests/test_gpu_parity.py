@@ -187,3 +187,76 @@ def test_repeated_solves_are_deterministic(E):
     u2 = _np(s.get(E.ECMG_VEC_U))
     assert np.array_equal(u1, u2)
     s.close()
+
+
+# Problems whose finest grids span several stencil tiles in x and y with ragged last tiles,
+# and many z-blocks at small kz; one all-Dirichlet cube (cubic-element path) and one box with
+# Robin faces on x-, y+ and z-.
+TILE_PROBLEMS = {
+    "cos_cube_40": lambda: inputs.cos_cube(levels=4, n0=(5, 5, 5), rtol=1e-10),
+    "random_box_robin": lambda: inputs.random_problem(11, n0=(5, 3, 4), levels=4, rtol=1e-10,
+                                                      face_bc=[1, 0, 0, 1, 1, 0],
+                                                      alpha=[0.5, 0.0, 0.0, 2.0, 1.0, 0.0]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TILE_PROBLEMS))
+def test_mixed_tile_shapes_agree(E, oracle_mod, name):
+    """Every FP32 stencil tile shape gives the same mixed solve (up to the order of the p.q
+    partial sums), within the mixed bar of the oracle."""
+    p = TILE_PROBLEMS[name]()
+    L = p["levels"]
+    lv, ost = oracle_mod.ecmg(p, p["rtol"])
+    s = E.solver_from_problem(p, precision=1)
+    ref, status = s.solve()
+    assert status == 0, ref
+    U_ref = _np(s.get(E.ECMG_VEC_U))
+    for ry, kz in [(1, 4), (1, 16), (2, 4), (2, 8), (2, 64)]:
+        for l in range(2, L):
+            s.set_tiles(ry, kz, level=l)
+        assert s.get_tiles(-1) == (ry, kz)
+        st, status = s.solve()
+        assert status == 0, (ry, kz, st)
+        for l in range(2, L):
+            assert st["rel_res"][l] <= p["rtol"], (ry, kz, l, st["rel_res"])
+            assert abs(st["iters"][l] - ref["iters"][l]) <= 1, (ry, kz, st["iters"], ref["iters"])
+        U = _np(s.get(E.ECMG_VEC_U))
+        assert _rel(U, U_ref) <= 1e-7, (ry, kz, _rel(U, U_ref))
+        assert _rel(U, lv[L - 1]["U"]) <= 1e-7, (ry, kz, _rel(U, lv[L - 1]["U"]))
+    s.close()
+
+
+def test_tile_shape_validation(E):
+    p = PROBLEMS["exp_cube"]()
+    s = E.solver_from_problem(p, precision=1)
+    for ry, kz in [(3, 16), (4, 16), (0, 16), (1, 3), (2, 2048)]:
+        with pytest.raises(E.EcmgError):
+            s.set_tiles(ry, kz)
+    with pytest.raises(E.EcmgError):
+        s.set_tiles(1, 16, level=99)
+    s.close()
+    s64 = E.solver_from_problem(p, precision=0)
+    with pytest.raises(E.EcmgError):
+        s64.set_tiles(1, 16)
+    with pytest.raises(E.EcmgError):
+        s64.get_tiles()
+    s64.close()
+
+
+def test_autotuned_solve_matches_oracle(E, oracle_mod):
+    """autotune=1 picks a shape on the 64^3 level (>= 2^18 nodes) and the solve keeps the
+    mixed bar."""
+    p = inputs.cos_cube(levels=5, n0=(4, 4, 4), rtol=1e-10)
+    L = p["levels"]
+    lv, ost = oracle_mod.ecmg(p, p["rtol"])
+    s = E.solver_from_problem(p, precision=1, autotune=1)
+    ry, kz = s.get_tiles(-1)
+    assert ry in (1, 2) and 4 <= kz <= 1024
+    st, status = s.solve()
+    assert status == 0, st
+    assert st["rel_res"][L - 1] <= p["rtol"]
+    U = _np(s.get(E.ECMG_VEC_U))
+    assert _rel(U, lv[L - 1]["U"]) <= 1e-7
+    ue = np.asarray(p["u_exact"])
+    assert np.abs(U - ue).max() == pytest.approx(np.abs(lv[L - 1]["U"] - ue).max(), rel=0.01)
+    s.close()
