@@ -62,7 +62,7 @@ struct ecmg_handle {
     int L = 0;
     Level lv[MAX_LEVELS];
     SolveState* states = nullptr;  // device, one per level
-    Partials part{nullptr, 0};
+    Partials part{nullptr, 0, nullptr};
     double* norm_part = nullptr;   // device, per-block norm partials
     std::vector<void*> allocs;
     cudaGraphExec_t exec = nullptr;
@@ -607,6 +607,7 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
         }
         h->part.buf = dalloc<double>(h, (int64_t)maxb * 3);
         h->part.max_blocks = maxb;
+        h->part.fs = dalloc<FixedScale>(h, 1);
         h->states = dalloc<SolveState>(h, MAX_LEVELS);
         int* flags = dalloc<int>(h, MAX_LEVELS);
         for (int l = 0; l < h->L; ++l) h->lv[l].uniform = flags + l;
@@ -703,7 +704,7 @@ ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision
         convert_f32(v.r, v.r32, v.g.total, s);
         launch_apply32(v.g, v.op, v.beta32, v.r32, v.q, s);
     } else if (precision == ECMG_FP64) {
-        launch_apply64(v.g, v.op, v.beta, v.uniform, v.r, v.q, s);
+        launch_apply64(v.g, v.op, v.beta, v.uniform, v.r, v.q, h->part, s);
     } else {
         return fail(ECMG_ERR_INVALID_ARG, "bad precision");
     }

@@ -108,10 +108,18 @@ struct SolveState {
     unsigned int arrive; // block arrival counter of the last-block reductions
 };
 
+// Fixed-point scale of an iterate: bit pattern of max |x| (nonnegative doubles order like their
+// bit patterns) and the block arrival counter of the reduction that forms it.
+struct FixedScale {
+    unsigned long long bits;
+    unsigned int arrive;
+};
+
 // Launch helper of one reducing kernel: where its per-block partial sums go.
 struct Partials {
     double* buf;         // >= 3 * max_blocks doubles
     int max_blocks;
+    FixedScale* fs;      // fixed-point scale of the exact residual (one per handle)
 };
 
 // ---- set-up kernels (setup.cu) -------------------------------------------------------

@@ -300,6 +300,235 @@ __device__ __forceinline__ void march_uniform(const Grid& g, const Op& op, doubl
     }
 }
 
+
+// ---- exact operator for a level with one beta everywhere ------------------------------------
+// With one beta the assembled matrix of the whole box, boundary rows included, is the tensor
+// product beta (Kx(x)My(x)Mz + Mx(x)Ky(x)Mz + Mx(x)My(x)Kz) of the assembled 1D matrices
+// K = -(1/h) D and M = (h/6) S: at interior nodes D = [1 -2 1] and S = [1 4 1], and at the two
+// end nodes each row loses its outer entry, D = [-1 1] and S = [2 1]. A Robin face F adds
+// alpha_F (h_a h_b / 36) S_a(x)S_b on its nodes (a, b the in-face axes). All these factors have
+// integer entries, so with the iterate in fixed point, x = X 2^-s with 64-bit integers X, the
+// parts
+//     I_x = Sy Sz Dx X,   I_y = Sx Sz Dy X,   I_z = Sx Sy Dz X,   I_F = S_a S_b X
+// are exact integer sums (second differences first, then the [1 4 1] smoothing), and
+//     A x = 2^-s ( -(beta/36) (hy hz/hx I_x + hx hz/hy I_y + hx hy/hz I_z)
+//                  + sum_F alpha_F (h_a h_b/36) I_F )
+// takes a few FP64 operations per node instead of about 30 -- FP64 runs at 1/64 of the FP32
+// rate on GB300, integer adds at full rate. The scale puts max |x| just below 2^53, so every
+// |I| <= 3 * 144 * 2^53 < 2^63, and writing x in fixed point moves each value by less than
+// 2^-53 max |x|, below the rounding error of evaluating the difference form in FP64.
+
+// Per-level scale: the bit pattern of max |x| (k_absmax), read by every block.
+struct FixedFrame {
+    int s;          // x = X 2^-s
+    double inv;     // 2^-s
+    bool finite;    // false when x holds an Inf or NaN
+};
+__device__ __forceinline__ FixedFrame fixed_frame(unsigned long long bits)
+{
+    FixedFrame f;
+    const int E = (int)((bits >> 52) & 0x7ff);  // biased exponent of max |x|
+    f.finite = E != 0x7ff;
+    f.s = (bits == 0ull || !f.finite) ? 0 : 1075 - E;  // max |x| < 2^(E-1022), so max |X| < 2^53
+    f.inv = ldexp(1.0, -f.s);
+    return f;
+}
+// X = trunc(x 2^s) from the bits of x (integer operations only; |x| <= max |x| keeps the shift
+// non-positive).
+__device__ __forceinline__ long long to_fixed(double x, int s)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const long long m = (b & 0xfffffffffffffll) | 0x10000000000000ll;
+    const int sh = e - 1075 + s;
+    long long v = 0;
+    if (e != 0 && sh > -64) v = sh >= 0 ? (long long)((unsigned long long)m << sh) : (m >> -sh);
+    return b < 0 ? -v : v;
+}
+// c v with c = 4 (interior node) or 2 (end node): the centre entry of S
+__device__ __forceinline__ long long s_mid(long long v, bool end)
+{
+    return (long long)((unsigned long long)v << (end ? 1 : 2));
+}
+// c v with c = 2 (interior) or 1 (end): the centre entry of -D
+__device__ __forceinline__ long long d_mid(long long v, bool end) { return end ? v : v + v; }
+
+template <bool ROBIN, typename SRC, typename BODY>
+__device__ __forceinline__ void march_fixed(const Grid& g, const Op& op, double bu, const FixedFrame& fr, int kz,
+                                            SRC src, BODY body)
+{
+    __shared__ long long X[3][BY + 2][BX + 2];
+    __shared__ long long LX[BY + 2][BX];
+    __shared__ long long LY[BY][BX + 2];
+    __shared__ long long LZ[BY + 2][BX + 2];
+    __shared__ long long UZ[BY + 2][BX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int kb = blockIdx.z * kz;
+    const int ke = min(kb + kz, g.nz + 1);
+    const double cx = -bu / 36.0 * g.h[1] * g.h[2] / g.h[0] * fr.inv;
+    const double cy = -bu / 36.0 * g.h[0] * g.h[2] / g.h[1] * fr.inv;
+    const double cz = -bu / 36.0 * g.h[0] * g.h[1] / g.h[2] * fr.inv;
+    double af[6];  // Robin face coefficients, times 2^-s
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int an = f / 2, a = an == 0 ? 1 : 0, b = an == 2 ? 1 : 2;
+        af[f] = ROBIN ? op.alpha[f] * g.h[a] * g.h[b] / 36.0 * fr.inv : 0.0;
+    }
+
+    auto load_plane = [&](int k) {
+        long long(*dst)[BX + 2] = X[(k + 3) % 3];
+        const int64_t base = g.plane_base(k);
+        const bool kin = k >= 0 && k <= g.nz;
+        for (int c = tid; c < (BX + 2) * (BY + 2); c += NT) {
+            const int ci = c % (BX + 2), cj = c / (BX + 2);
+            const int i = i0 - 1 + ci, j = j0 - 1 + cj;
+            long long v = 0;
+            if (kin && i >= 0 && i <= g.nx && j >= 0 && j <= g.ny) v = to_fixed(src(base + g.in_plane(i, j)), fr.s);
+            dst[cj][ci] = v;
+        }
+    };
+    // Dx and Dy of plane k: LX at nodes (i0+ci, j0-1+cj), LY at nodes (i0-1+ci, j0+cj)
+    auto form_lxy = [&](int k) {
+        const long long(*P)[BX + 2] = X[(k + 3) % 3];
+        for (int c = tid; c < BX * (BY + 2); c += NT) {
+            const int ci = c % BX, cj = c / BX;
+            const int i = i0 + ci;
+            LX[cj][ci] = (P[cj][ci] + P[cj][ci + 2]) - d_mid(P[cj][ci + 1], i == 0 || i == g.nx);
+        }
+        for (int c = tid; c < (BX + 2) * BY; c += NT) {
+            const int ci = c % (BX + 2), cj = c / (BX + 2);
+            const int j = j0 + cj;
+            LY[cj][ci] = (P[cj][ci] + P[cj + 2][ci]) - d_mid(P[cj + 1][ci], j == 0 || j == g.ny);
+        }
+    };
+    const int i = i0 + tx, j = j0 + ty;
+    const bool iend = i == 0 || i == g.nx, jend = j == 0 || j == g.ny;
+    auto sy_lx = [&]() { return LX[ty][tx] + s_mid(LX[ty + 1][tx], jend) + LX[ty + 2][tx]; };
+    auto sx_ly = [&]() { return LY[ty][tx] + s_mid(LY[ty][tx + 1], iend) + LY[ty][tx + 2]; };
+    long long txm, tx0, tym, ty0;
+    load_plane(kb - 1);
+    __syncthreads();
+    form_lxy(kb - 1);
+    __syncthreads();
+    txm = sy_lx();
+    tym = sx_ly();
+    load_plane(kb);
+    __syncthreads();
+    form_lxy(kb);
+    __syncthreads();
+    tx0 = sy_lx();
+    ty0 = sx_ly();
+    for (int k = kb; k < ke; ++k) {
+        const bool kend = k == 0 || k == g.nz;
+        load_plane(k + 1);
+        __syncthreads();
+        form_lxy(k + 1);
+        {
+            const long long(*Pm)[BX + 2] = X[(k + 2) % 3];
+            const long long(*P0)[BX + 2] = X[k % 3];
+            const long long(*Pp)[BX + 2] = X[(k + 1) % 3];
+            for (int c = tid; c < (BX + 2) * (BY + 2); c += NT) {
+                const int ci = c % (BX + 2), cj = c / (BX + 2);
+                LZ[cj][ci] = (Pm[cj][ci] + Pp[cj][ci]) - d_mid(P0[cj][ci], kend);
+            }
+        }
+        __syncthreads();
+        const long long txp = sy_lx();
+        const long long typ = sx_ly();
+        for (int c = tid; c < BX * (BY + 2); c += NT) {
+            const int ci = c % BX, cj = c / BX;
+            const int ii = i0 + ci;
+            UZ[cj][ci] = LZ[cj][ci] + s_mid(LZ[cj][ci + 1], ii == 0 || ii == g.nx) + LZ[cj][ci + 2];
+        }
+        __syncthreads();
+        if (i <= g.nx && j <= g.ny) {
+            const long long Ix = txm + s_mid(tx0, kend) + txp;
+            const long long Iy = tym + s_mid(ty0, kend) + typ;
+            const long long Iz = UZ[ty][tx] + s_mid(UZ[ty + 1][tx], jend) + UZ[ty + 2][tx];
+            double Av = cx * (double)Ix + cy * (double)Iy + cz * (double)Iz;
+            if (ROBIN && (iend || jend || kend)) {
+                const int pm = (k + 2) % 3, p0 = k % 3, pp = (k + 1) % 3;
+                // S_y S_z X on the node's column (x faces)
+                auto fx = [&](int p) { return X[p][ty][tx + 1] + s_mid(X[p][ty + 1][tx + 1], jend) + X[p][ty + 2][tx + 1]; };
+                // S_x S_z X on the node's row (y faces)
+                auto fy = [&](int p) { return X[p][ty + 1][tx] + s_mid(X[p][ty + 1][tx + 1], iend) + X[p][ty + 1][tx + 2]; };
+                // S_x on row r of the node's plane (z faces)
+                auto fz = [&](int r) { return X[p0][ty + r][tx] + s_mid(X[p0][ty + r][tx + 1], iend) + X[p0][ty + r][tx + 2]; };
+                if (iend) {
+                    const long long I = fx(pm) + s_mid(fx(p0), kend) + fx(pp);
+                    if (i == 0) Av += af[0] * (double)I;
+                    if (i == g.nx) Av += af[1] * (double)I;
+                }
+                if (jend) {
+                    const long long I = fy(pm) + s_mid(fy(p0), kend) + fy(pp);
+                    if (j == 0) Av += af[2] * (double)I;
+                    if (j == g.ny) Av += af[3] * (double)I;
+                }
+                if (kend) {
+                    const long long I = fz(0) + s_mid(fz(1), jend) + fz(2);
+                    if (k == 0) Av += af[4] * (double)I;
+                    if (k == g.nz) Av += af[5] * (double)I;
+                }
+            }
+            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Av, 0.0);
+        }
+        __syncthreads();  // the Robin rows above read plane k-1, which the next load replaces
+        txm = tx0;
+        tx0 = txp;
+        tym = ty0;
+        ty0 = typ;
+    }
+}
+
+// max |x| over a level vector into fs->bits (bit patterns of nonnegative doubles order like the
+// values; any Inf or NaN gives exponent 0x7ff). Skipped when the level has more than one beta,
+// or when a residual replacement is not going to run.
+__global__ void __launch_bounds__(UPD_TPB) k_absmax(int64_t n, const double* __restrict__ x, const int* uniform,
+                                                   const SolveState* st, int mode, FixedScale* fs,
+                                                   unsigned long long* partials)
+{
+    COUNT_LAUNCH();
+    if (!*uniform) return;
+    if (st && mode == RES_REPLACE && st->done) return;
+    __shared__ unsigned long long sh[UPD_TPB / 32];
+    __shared__ unsigned int ticket;
+    unsigned long long m = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n / 2; t += stride) {
+        const double2 v = x2[t];
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(v.x)));
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(v.y)));
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(x[n - 1])));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
+        partials[blockIdx.x] = m;
+        __threadfence();
+        ticket = atomicAdd(&fs->arrive, 1u);
+    }
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    m = 0ull;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = max(m, __ldcg(&partials[b]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if (lane == 0) sh[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
+        fs->bits = m;
+        fs->arrive = 0u;
+    }
+}
+
 // Uniform-beta dispatch of the FP64 kernels: *uniform is set per level by the set-up.
 #define ECMG_FP64_MARCH(T, ROBIN, CUBE, FULL, SRC, BODY)                                    \
     do {                                                                                  \
@@ -405,7 +634,7 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
                                             const int* uniform, const double* __restrict__ x,
                                             const double* __restrict__ b, const OT* __restrict__ dinv,
                                             OT* __restrict__ r, SolveState* st, double* partials, int mode,
-                                            CondHandles ch, int kz)
+                                            CondHandles ch, int kz, const FixedScale* fs)
 {
     COUNT_LAUNCH();
     if (mode == RES_REPLACE && st->done) return;
@@ -419,7 +648,13 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
         rr = fma(rv, rv, rr);
         rz.add_prod(ro, dinv[o] * ro);
     };
-    ECMG_FP64_MARCH(double, ROBIN, CUBE, false, src, body);
+    if (*uniform) {
+        const FixedFrame fr = fixed_frame(fs->bits);
+        if (fr.finite) march_fixed<ROBIN>(g, op, beta[g.off(0, 0, 0)], fr, kz, src, body);
+        else if (threadIdx.x == 0 && threadIdx.y == 0) rr = nan("");  // breakdown: the iterate is not finite
+    } else {
+        march<ROBIN, CUBE, double, double>(g, op, beta, kz, src, body);
+    }
     double v[2] = {rr, rz.value()};
     if (grid_sum<2>(v, partials, &st->arrive)) res_epilogue(st, v[0], v[1], mode, ch);
 }
@@ -471,13 +706,22 @@ __global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, cons
 template <typename T, bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(NT) k_apply(const Grid g, const Op op, const T* __restrict__ beta,
                                               const int* uniform, const T* __restrict__ x,
-                                              double* __restrict__ y, int kz)
+                                              double* __restrict__ y, int kz, const FixedScale* fs)
 {
     COUNT_LAUNCH();
     auto src = [&](int64_t o) -> T { return x[o]; };
     auto body = [&](int, int, int, int64_t o, T Av, T) { y[o] = (double)Av; };
-    if constexpr (sizeof(T) == 8) ECMG_FP64_MARCH(T, ROBIN, CUBE, true, src, body);
-    else march<ROBIN, CUBE, T, T>(g, op, beta, kz, src, body);
+    if constexpr (sizeof(T) == 8) {
+        if (*uniform) {
+            const FixedFrame fr = fixed_frame(fs->bits);
+            auto body64 = [&](int, int, int, int64_t o, double Av, double) { y[o] = fr.finite ? Av : nan(""); };
+            march_fixed<ROBIN>(g, op, beta[g.off(0, 0, 0)], fr, kz, src, body64);
+        } else {
+            march<ROBIN, CUBE, T, T>(g, op, beta, kz, src, body);
+        }
+    } else {
+        march<ROBIN, CUBE, T, T>(g, op, beta, kz, src, body);
+    }
 }
 
 // ---- K2: residual update and stopping test ----------------------------------------------------
@@ -654,32 +898,44 @@ void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
     ECMG_VARIANT(k_pq, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, nullptr, r, dinv, pold,
                                                                           pnew, q, e, st, pr.buf, pidx, ch, kz);
 }
+// max |x| for the fixed-point evaluation (a no-op on levels with more than one beta)
+inline void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
+                          Partials pr, cudaStream_t s)
+{
+    k_absmax<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, uniform, st, mode, pr.fs,
+                                                        reinterpret_cast<unsigned long long*>(pr.buf));
+}
 void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const double* dinv, double* r, SolveState* st, Partials pr, ResMode mode,
                   CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
+    launch_absmax(g, x, uniform, st, (int)mode, pr, s);
     ECMG_VARIANT(k_res, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
-                                                                            st, pr.buf, (int)mode, ch, kz);
+                                                                            st, pr.buf, (int)mode, ch, kz, pr.fs);
 }
 void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr, ResMode mode,
                   CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
+    launch_absmax(g, x, uniform, st, (int)mode, pr, s);
     ECMG_VARIANT(k_res, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
-                                                                           st, pr.buf, (int)mode, ch, kz);
+                                                                           st, pr.buf, (int)mode, ch, kz, pr.fs);
 }
 void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
-                    double* y, cudaStream_t s)
+                    double* y, Partials pr, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    ECMG_VARIANT(k_apply, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, y, kz);
+    launch_absmax(g, x, uniform, nullptr, 0, pr, s);
+    ECMG_VARIANT(k_apply, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, y, kz,
+                                                                              pr.fs);
 }
 void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    ECMG_VARIANT(k_apply, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, nullptr, x, y, kz);
+    ECMG_VARIANT(k_apply, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, nullptr, x, y, kz,
+                                                                             nullptr);
 }
 void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
                 Partials pr, cudaStream_t s)

@@ -28,8 +28,9 @@ void launch_pq64(const Grid& g, const Op& op, const double* beta, const int* uni
 void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
                  const float* dinv, const float* pold, float* pnew, float* q, float* e,
                  SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
-// r = b - A x (FP64 arithmetic) on free nodes, 0 on Dirichlet nodes; r stored as double or
-// float; ||r||^2 and r.dinv.r reduced; last block acts by ResMode.
+// r = b - A x on free nodes, 0 on Dirichlet nodes; r stored as double or float; ||r||^2 and
+// r.dinv.r reduced; last block acts by ResMode. A x in FP64 arithmetic, or exactly in fixed
+// point on a level with one beta (two launches: max |x|, then the residual).
 void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const double* dinv, double* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s);
@@ -38,7 +39,7 @@ void launch_res32(const Grid& g, const Op& op, const double* beta, const int* un
                   ResMode mode, CondHandles ch, cudaStream_t s);
 // y = A x with the full matrix (no boundary masking), FP64 or FP32 arithmetic.
 void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
-                    double* y, cudaStream_t s);
+                    double* y, Partials pr, cudaStream_t s);
 void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y,
                     cudaStream_t s);
 
