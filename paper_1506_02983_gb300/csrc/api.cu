@@ -62,6 +62,7 @@ struct ecmg_handle {
     int L = 0;
     Level lv[MAX_LEVELS];
     SolveState* states = nullptr;  // device, one per level
+    KTimer* timers = nullptr;      // device, one per level: the FP32 stencil launches of the solves
     Partials part{nullptr, 0, nullptr};
     double* norm_part = nullptr;   // device, per-block norm partials
     std::vector<void*> allocs;
@@ -233,7 +234,9 @@ void record_setup(Rec& R)
         } else {
             nodal_load(v.g, v.op, v.f, p.g_R ? v.gR : nullptr, v.b, s);
         }
-        jacobi_diag(v.g, v.op, v.beta, v.dinv, mixed ? v.dinv32 : nullptr, mixed ? v.beta32 : nullptr, s);
+        // FP64 diagonal for FP64 JCG and the direct levels, FP32 for the FP32 iteration of MIXED
+        jacobi_diag(v.g, v.op, v.beta, (!mixed || l < 2) ? v.dinv : nullptr, mixed ? v.dinv32 : nullptr,
+                    mixed ? v.beta32 : nullptr, s);
         uniform_check(v.g, v.beta, v.uniform, s);
     }
 }
@@ -296,7 +299,8 @@ void record_level(Rec& R, int l)
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
         auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
-            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, pout, v.q32, v.e32, st, h->part, idx, ch, R.s());
+            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, pout, v.q32, v.e32, st, h->part, idx, ch,
+                            h->timers + l, R.s());
             launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
         };
         auto replace = [&](float* pnew) {
@@ -452,7 +456,7 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
             ck(cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s));
             ck(cudaEventRecord(e0, s));
             switch (which) {
-            case 0: launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, v.pB32, v.q32, v.e32, st, h->part, 1, none, s); break;
+            case 0: launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, v.pB32, v.q32, v.e32, st, h->part, 1, none, nullptr, s); break;
             case 1: launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
             case 2: launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
             case 3: launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
@@ -609,6 +613,12 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
         h->part.max_blocks = maxb;
         h->part.fs = dalloc<FixedScale>(h, 1);
         h->states = dalloc<SolveState>(h, MAX_LEVELS);
+        h->timers = dalloc<KTimer>(h, MAX_LEVELS);
+        {
+            KTimer idle[MAX_LEVELS];
+            for (auto& t : idle) t = KTimer{~0ull, 0ull, 0ull};
+            ck(cudaMemcpyAsync(h->timers, idle, sizeof(idle), cudaMemcpyHostToDevice, h->cap[0]));
+        }
         int* flags = dalloc<int>(h, MAX_LEVELS);
         for (int l = 0; l < h->L; ++l) h->lv[l].uniform = flags + l;
         h->norm_part = dalloc<double>(h, 2048);
@@ -825,6 +835,29 @@ ecmg_status ecmg_get_tiles(ecmg_handle* h, int32_t level, int32_t* ry, int32_t* 
     if (!h->lv[l].r32) return fail(ECMG_ERR_INVALID_ARG, "handle has no FP32 vectors");
     *ry = h->lv[l].k1.ry;
     *kz = h->lv[l].k1.kz;
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_stencil_timer(ecmg_handle* h, int32_t level, int32_t reset, double* ms_total,
+                               int64_t* launches)
+{
+    if (!h || !ms_total || !launches) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    const int l = resolve_level(h, level);
+    if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    KTimer t{};
+    try {
+        ck(cudaMemcpyAsync(&t, h->timers + l, sizeof(t), cudaMemcpyDeviceToHost, h->user_stream));
+        ck(cudaStreamSynchronize(h->user_stream));
+        if (reset) {
+            const KTimer idle{~0ull, 0ull, 0ull};
+            ck(cudaMemcpyAsync(h->timers + l, &idle, sizeof(idle), cudaMemcpyHostToDevice, h->user_stream));
+            ck(cudaStreamSynchronize(h->user_stream));
+        }
+    } catch (CudaFail& f) {
+        return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+    }
+    *ms_total = (double)t.ns * 1e-6;
+    *launches = (int64_t)t.n;
     return ECMG_OK;
 }
 

@@ -115,6 +115,21 @@ struct FixedScale {
     unsigned int arrive;
 };
 
+// Device-side duration of the launches of one kernel on one level, taken inside whatever runs
+// it (a CUDA graph included): the earliest block start of a launch (atomicMin of the global
+// timer) to the end of its last block; the last block adds the difference and rearms t0.
+struct KTimer {
+    unsigned long long t0;   // earliest block start of the running launch (~0 when idle)
+    unsigned long long ns;   // summed launch durations
+    unsigned long long n;    // launches summed
+};
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Launch helper of one reducing kernel: where its per-block partial sums go.
 struct Partials {
     double* buf;         // >= 3 * max_blocks doubles

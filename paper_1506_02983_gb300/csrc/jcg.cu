@@ -669,31 +669,33 @@ __global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, cons
                                                  SolveState* st, double* partials)
 {
     COUNT_LAUNCH();
-    const int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
     const Weights<double> wts(op);
     const bool dx0 = op.bc[0] == 0, dx1 = op.bc[1] == 0, dy0 = op.bc[2] == 0, dy1 = op.bc[3] == 0;
     const bool dz0 = op.bc[4] == 0, dz1 = op.bc[5] == 0;
     double ss = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t % (g.nx + 1));
-        const int64_t rr_ = t / (g.nx + 1);
-        const int j = (int)(rr_ % (g.ny + 1));
-        const int k = (int)(rr_ / (g.ny + 1));
-        if (on_dirichlet(g, op, i, j, k)) continue;
-        const int64_t o = g.off(i, j, k);
-        double f = b[o];
-        const bool near = (dx0 && i <= 1) || (dx1 && i >= g.nx - 1) || (dy0 && j <= 1) || (dy1 && j >= g.ny - 1) ||
-                          (dz0 && k <= 1) || (dz1 && k >= g.nz - 1);
-        if (near) {
-            auto V = [&](int ddx, int ddy, int ddz) -> double {
-                return x[o + (int64_t)ddz * g.plane + (int64_t)ddy * g.pitch + ddx];
-            };
-            auto be = [&](int ex, int ey, int ez) { return beta[g.off(i - 1 + ex, j - 1 + ey, k - 1 + ez)]; };
-            f -= q1_apply<true, ROBIN, CUBE, double>(V, be(0, 0, 0), be(1, 0, 0), be(0, 1, 0), be(1, 1, 0),
-                                                     be(0, 0, 1), be(1, 0, 1), be(0, 1, 1), be(1, 1, 1), i, j, k, g,
-                                                     op, wts);
+    // rows (j, k) spread over the warps of the grid, nodes i of a row over the lanes
+    const int nrows = (g.ny + 1) * (g.nz + 1);
+    const int warps = gridDim.x * (blockDim.x / 32), wid = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    for (int row = wid; row < nrows; row += warps) {
+        const int j = row % (g.ny + 1), k = row / (g.ny + 1);
+        const int64_t orow = g.plane_base(k) + g.in_plane(0, j);
+        for (int i = threadIdx.x & 31; i <= g.nx; i += 32) {
+            if (on_dirichlet(g, op, i, j, k)) continue;
+            const int64_t o = orow + i;
+            double f = b[o];
+            const bool near = (dx0 && i <= 1) || (dx1 && i >= g.nx - 1) || (dy0 && j <= 1) || (dy1 && j >= g.ny - 1) ||
+                              (dz0 && k <= 1) || (dz1 && k >= g.nz - 1);
+            if (near) {
+                auto V = [&](int ddx, int ddy, int ddz) -> double {
+                    return x[o + (int64_t)ddz * g.plane + (int64_t)ddy * g.pitch + ddx];
+                };
+                auto be = [&](int ex, int ey, int ez) { return beta[g.off(i - 1 + ex, j - 1 + ey, k - 1 + ez)]; };
+                f -= q1_apply<true, ROBIN, CUBE, double>(V, be(0, 0, 0), be(1, 0, 0), be(0, 1, 0), be(1, 1, 0),
+                                                         be(0, 0, 1), be(1, 0, 1), be(0, 1, 1), be(1, 1, 1), i, j, k, g,
+                                                         op, wts);
+            }
+            ss = fma(f, f, ss);
         }
-        ss = fma(f, f, ss);
     }
     double v[1] = {ss};
     if (grid_sum<1>(v, partials, &st->arrive)) {

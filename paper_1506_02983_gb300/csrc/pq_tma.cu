@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(NT, RY == 1 ? (ROBIN ? 3 : 4) : 2)
 k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
            const __grid_constant__ CUtensorMap m_dinv, const __grid_constant__ CUtensorMap m_beta,
            const Grid g, const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q,
-           float* __restrict__ e, SolveState* st, double* partials, int pidx, CondHandles ch, int kz)
+           float* __restrict__ e, SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
+           KTimer* tm)
 {
     using S = Shape<RY>;
     COUNT_LAUNCH();
@@ -169,6 +170,7 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
 
     if (st->done) return;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TBX * ty;
+    if (tm && tid == 0) atomicMin(&tm->t0, global_ns());
     const int i0 = rg.ilo + blockIdx.x * TBX, j0 = rg.jlo + blockIdx.y * S::NY;
     const int kb = rg.klo + blockIdx.z * kz;
     const int ke = min(kb + kz, rg.khi + 1);
@@ -349,6 +351,11 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     for (int b = tid; b < nb; b += NT) v[0] += __ldcg(&partials[b]);
     block_sum<1>(v, red);
     if (tid == 0) {
+        if (tm) {
+            tm->ns += global_ns() - tm->t0;
+            tm->n += 1;
+            tm->t0 = ~0ull;
+        }
         st->arrive = 0u;
         const double pq = v[0];
         st->alpha_prev = 0.0;
@@ -424,7 +431,8 @@ cudaError_t prepare_ry()
 
 template <int RY>
 void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, float* pnew,
-               float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, cudaStream_t s)
+               float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm,
+               cudaStream_t s)
 {
     const int v = ry_index(RY);
     const Range rg = k1_range(g, op);
@@ -434,7 +442,7 @@ void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid&
                       : (op.cube ? k_pq32_tma<false, true, RY> : k_pq32_tma<false, false, RY>);
     kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY>(), s>>>(m.r[v], pold_is_b ? m.pB[v] : m.pA[v], m.dinv[v],
                                                                   m.beta[v], g, op, rg, pnew, q, e, st, pr.buf,
-                                                                  pidx, ch, c.kz);
+                                                                  pidx, ch, c.kz, tm);
 }
 
 }  // namespace
@@ -502,10 +510,10 @@ int max_tma_blocks(const Grid& g)
 
 void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op,
                      float* pnew, float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch,
-                     cudaStream_t s)
+                     KTimer* tm, cudaStream_t s)
 {
-    if (c.ry == 1) launch_ry<1>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, s);
-    else launch_ry<2>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, s);
+    if (c.ry == 1) launch_ry<1>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, tm, s);
+    else launch_ry<2>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, tm, s);
 }
 
 unsigned long long launches_pq_tma()

@@ -13,8 +13,15 @@ __device__ unsigned long long g_launches = 0;  // kernel executions of this file
         atomicAdd(&g_launches, 1ull)
 
 constexpr int TPB = 256;
+constexpr int TX = 32, TY = 8;  // node-parallel kernels: 32 x 8 nodes of a plane per block
 
 inline int blocks_for(int64_t n) { return (int)((n + TPB - 1) / TPB); }
+// one thread per point of an (mx+1) x (my+1) x (mz+1) box: x, y tiles and one block row per plane
+inline dim3 grid3(int mx, int my, int mz) { return dim3((mx + TX) / TX, (my + TY) / TY, mz + 1); }
+#define POINT_IJK(MX, MY)                                                            \
+    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y; \
+    const int k = blockIdx.z;                                                       \
+    if (i > (MX) || j > (MY)) return
 
 __device__ __forceinline__ bool on_dirichlet(const Grid& g, const Op& op, int i, int j, int k)
 {
@@ -26,39 +33,24 @@ __device__ __forceinline__ bool on_dirichlet(const Grid& g, const Op& op, int i,
 __global__ void k_pack_nodal(Grid g, const double* __restrict__ dense, double* __restrict__ dst)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % (g.nx + 1));
-    int64_t r = t / (g.nx + 1);
-    int j = (int)(r % (g.ny + 1));
-    int k = (int)(r / (g.ny + 1));
+    POINT_IJK(g.nx, g.ny);
+    const int64_t t = i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);  // dense index
     dst[g.off(i, j, k)] = dense[t];
 }
 
 __global__ void k_unpack_nodal(Grid g, const double* __restrict__ src, double* __restrict__ dense)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % (g.nx + 1));
-    int64_t r = t / (g.nx + 1);
-    int j = (int)(r % (g.ny + 1));
-    int k = (int)(r / (g.ny + 1));
+    POINT_IJK(g.nx, g.ny);
+    const int64_t t = i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);  // dense index
     dense[t] = src[g.off(i, j, k)];
 }
 
 __global__ void k_pack_elements(Grid g, const double* __restrict__ dense, double* __restrict__ dst)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)g.nx * g.ny * g.nz;
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % g.nx);
-    int64_t r = t / g.nx;
-    int j = (int)(r % g.ny);
-    int k = (int)(r / g.ny);
+    POINT_IJK(g.nx - 1, g.ny - 1);
+    const int64_t t = i + (int64_t)g.nx * (j + (int64_t)g.ny * k);  // dense index
     dst[g.off(i, j, k)] = dense[t];
 }
 
@@ -66,13 +58,7 @@ __global__ void k_pack_elements(Grid g, const double* __restrict__ dense, double
 __global__ void k_coarsen_beta(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)gc.nx * gc.ny * gc.nz;
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % gc.nx);
-    int64_t r = t / gc.nx;
-    int j = (int)(r % gc.ny);
-    int k = (int)(r / gc.ny);
+    POINT_IJK(gc.nx - 1, gc.ny - 1);
     double s = 0.0;
     for (int c = 0; c < 8; ++c)
         s += bf[gf.off(2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + (c >> 2))];
@@ -82,13 +68,7 @@ __global__ void k_coarsen_beta(Grid gc, const double* __restrict__ bf, Grid gf, 
 __global__ void k_inject(Grid gc, const double* __restrict__ vf, Grid gf, double* __restrict__ vc)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)(gc.nx + 1) * (gc.ny + 1) * (gc.nz + 1);
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % (gc.nx + 1));
-    int64_t r = t / (gc.nx + 1);
-    int j = (int)(r % (gc.ny + 1));
-    int k = (int)(r / (gc.ny + 1));
+    POINT_IJK(gc.nx, gc.ny);
     vc[gc.off(i, j, k)] = vf[gf.off(2 * i, 2 * j, 2 * k)];
 }
 
@@ -97,13 +77,7 @@ __global__ void k_inject(Grid gc, const double* __restrict__ vf, Grid gf, double
 __global__ void k_restrict(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)(gc.nx + 1) * (gc.ny + 1) * (gc.nz + 1);
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % (gc.nx + 1));
-    int64_t r = t / (gc.nx + 1);
-    int j = (int)(r % (gc.ny + 1));
-    int k = (int)(r / (gc.ny + 1));
+    POINT_IJK(gc.nx, gc.ny);
     double s = 0.0;
     for (int dk = -1; dk <= 1; ++dk)
         for (int dj = -1; dj <= 1; ++dj)
@@ -129,13 +103,7 @@ __global__ void k_nodal_load(Grid g, Op op, const double* __restrict__ f,
                              const double* __restrict__ gR, double* __restrict__ b)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % (g.nx + 1));
-    int64_t r = t / (g.nx + 1);
-    int j = (int)(r % (g.ny + 1));
-    int k = (int)(r / (g.ny + 1));
+    POINT_IJK(g.nx, g.ny);
     const int idx[3] = {i, j, k};
     const int nn[3] = {g.nx, g.ny, g.nz};
     double wa[3][3];
@@ -172,19 +140,10 @@ __global__ void k_nodal_load(Grid g, Op op, const double* __restrict__ f,
 
 // Jacobi diagonal: diag = w0 * (sum of the 8 element betas) + Robin face mass diagonal.
 // Dirichlet nodes get dinv = 0, which also masks them in every JCG kernel.
-__global__ void k_jacobi(Grid g, Op op, const double* __restrict__ beta, double* __restrict__ dinv64,
-                         float* __restrict__ dinv32, float* __restrict__ beta32)
+__global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, double* __restrict__ dinv64)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % (g.nx + 1));
-    int64_t r = t / (g.nx + 1);
-    int j = (int)(r % (g.ny + 1));
-    int k = (int)(r / (g.ny + 1));
-    const int64_t o = g.off(i, j, k);
-    if (beta32 && i < g.nx && j < g.ny && k < g.nz) beta32[o] = (float)beta[o];
+    POINT_IJK(g.nx, g.ny);
     double B = 0.0;
     for (int c = 0; c < 8; ++c)
         B += beta[g.off(i - 1 + (c & 1), j - 1 + ((c >> 1) & 1), k - 1 + (c >> 2))];
@@ -199,22 +158,41 @@ __global__ void k_jacobi(Grid g, Op op, const double* __restrict__ beta, double*
         d += op.alpha[fc] * cnt1(idx[aa], nn[aa], 0) * g.h[aa] / 3.0 *
              cnt1(idx[ab], nn[ab], 0) * g.h[ab] / 3.0;
     }
-    double v = on_dirichlet(g, op, i, j, k) ? 0.0 : 1.0 / d;
-    dinv64[o] = v;
-    if (dinv32) dinv32[o] = (float)v;
+    dinv64[g.off(i, j, k)] = on_dirichlet(g, op, i, j, k) ? 0.0 : 1.0 / d;
+}
+
+// The same diagonal in FP32 arithmetic from the FP32 betas, for the FP32 iteration of MIXED
+// mode: no FP64 division or conversion per node (FP64 runs at 1/64 of the FP32 rate on GB300).
+// Robin terms (boundary nodes only) are formed in FP64 and rounded.
+__global__ void k_jacobi32(Grid g, Op op, const float* __restrict__ beta32, float* __restrict__ dinv32)
+{
+    COUNT_LAUNCH();
+    POINT_IJK(g.nx, g.ny);
+    float B = 0.f;
+    for (int c = 0; c < 8; ++c)
+        B += beta32[g.off(i - 1 + (c & 1), j - 1 + ((c >> 1) & 1), k - 1 + (c >> 2))];
+    float d = __fmul_rn((float)op.w0, B);
+    if (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz) {
+        const int idx[3] = {i, j, k};
+        const int nn[3] = {g.nx, g.ny, g.nz};
+        double dr = 0.0;
+        for (int fc = 0; fc < 6; ++fc) {
+            if (op.alpha[fc] == 0.0) continue;
+            int an = fc / 2;
+            if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
+            int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
+            dr += op.alpha[fc] * cnt1(idx[aa], nn[aa], 0) * g.h[aa] / 3.0 * cnt1(idx[ab], nn[ab], 0) * g.h[ab] / 3.0;
+        }
+        d += (float)dr;
+    }
+    dinv32[g.off(i, j, k)] = on_dirichlet(g, op, i, j, k) ? 0.f : __frcp_rn(d);
 }
 
 // x = g_D on Dirichlet nodes, 0 on free nodes (gD == nullptr: zero everywhere).
 __global__ void k_dirichlet_ext(Grid g, Op op, const double* __restrict__ gD, double* __restrict__ x)
 {
     COUNT_LAUNCH();
-    int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = (int)(t % (g.nx + 1));
-    int64_t r = t / (g.nx + 1);
-    int j = (int)(r % (g.ny + 1));
-    int k = (int)(r / (g.ny + 1));
+    POINT_IJK(g.nx, g.ny);
     const int64_t o = g.off(i, j, k);
     x[o] = (gD && on_dirichlet(g, op, i, j, k)) ? gD[o] : 0.0;
 }
@@ -222,15 +200,8 @@ __global__ void k_dirichlet_ext(Grid g, Op op, const double* __restrict__ gD, do
 __global__ void k_uniform(Grid g, const double* __restrict__ beta, int* flag)
 {
     COUNT_LAUNCH();
-    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-    const double b0 = beta[g.off(0, 0, 0)];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t % g.nx);
-        const int64_t r = t / g.nx;
-        const int j = (int)(r % g.ny);
-        const int k = (int)(r / g.ny);
-        if (beta[g.off(i, j, k)] != b0) *flag = 0;  // every writer stores the same value
-    }
+    POINT_IJK(g.nx - 1, g.ny - 1);
+    if (beta[g.off(i, j, k)] != beta[g.off(0, 0, 0)]) *flag = 0;  // every writer stores the same value
 }
 
 __global__ void k_set_flag(int* flag)
@@ -246,16 +217,12 @@ __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict_
         dst[t] = (float)src[t];
 }
 
-inline int64_t nodes(const Grid& g) { return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
-
 }  // namespace
 
 void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s)
 {
     k_set_flag<<<1, 1, 0, s>>>(flag);
-    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-    int b = blocks_for(n);
-    k_uniform<<<b < 2048 ? b : 2048, TPB, 0, s>>>(g, beta, flag);
+    k_uniform<<<grid3(g.nx - 1, g.ny - 1, g.nz - 1), dim3(TX, TY), 0, s>>>(g, beta, flag);
 }
 
 void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s)
@@ -266,41 +233,45 @@ void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s)
 
 void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s)
 {
-    k_pack_nodal<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, dense, dst);
+    k_pack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, dense, dst);
 }
 void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s)
 {
-    k_unpack_nodal<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, src, dense);
+    k_unpack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, src, dense);
 }
 void pack_elements(const Grid& g, const double* dense, double* dst, cudaStream_t s)
 {
-    k_pack_elements<<<blocks_for((int64_t)g.nx * g.ny * g.nz), TPB, 0, s>>>(g, dense, dst);
+    k_pack_elements<<<grid3(g.nx - 1, g.ny - 1, g.nz - 1), dim3(TX, TY), 0, s>>>(g, dense, dst);
 }
 void coarsen_beta(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s)
 {
-    k_coarsen_beta<<<blocks_for((int64_t)gc.nx * gc.ny * gc.nz), TPB, 0, s>>>(gc, bf, gf, bc);
+    k_coarsen_beta<<<grid3(gc.nx - 1, gc.ny - 1, gc.nz - 1), dim3(TX, TY), 0, s>>>(gc, bf, gf, bc);
 }
 void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, cudaStream_t s)
 {
-    k_inject<<<blocks_for(nodes(gc)), TPB, 0, s>>>(gc, vf, gf, vc);
+    k_inject<<<grid3(gc.nx, gc.ny, gc.nz), dim3(TX, TY), 0, s>>>(gc, vf, gf, vc);
 }
 void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s)
 {
-    k_restrict<<<blocks_for(nodes(gc)), TPB, 0, s>>>(gc, bf, gf, bc);
+    k_restrict<<<grid3(gc.nx, gc.ny, gc.nz), dim3(TX, TY), 0, s>>>(gc, bf, gf, bc);
 }
 void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
                 cudaStream_t s)
 {
-    k_nodal_load<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, f, gR, b);
+    k_nodal_load<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, f, gR, b);
 }
 void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
                  float* beta32, cudaStream_t s)
 {
-    k_jacobi<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, beta, dinv64, dinv32, beta32);
+    if (dinv64) k_jacobi64<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta, dinv64);
+    if (beta32) {
+        convert_f32(beta, beta32, g.total, s);
+        if (dinv32) k_jacobi32<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32);
+    }
 }
 void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x, cudaStream_t s)
 {
-    k_dirichlet_ext<<<blocks_for(nodes(g)), TPB, 0, s>>>(g, op, gD, x);
+    k_dirichlet_ext<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, gD, x);
 }
 
 unsigned long long launches_setup()

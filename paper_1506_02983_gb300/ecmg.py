@@ -71,6 +71,7 @@ _SIGS = {
     "ecmg_set_tiles": (_I32, [_H, _I32, _I32, _I32]),
     "ecmg_get_tiles": (_I32, [_H, _I32, C.POINTER(_I32), C.POINTER(_I32)]),
     "ecmg_autotune": (_I32, [_H, _I32]),
+    "ecmg_stencil_timer": (_I32, [_H, _I32, _I32, C.POINTER(_D), C.POINTER(C.c_int64)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -208,6 +209,13 @@ class Solver:
         ry, kz = C.c_int32(), C.c_int32()
         check(ecmg_get_tiles(self.handle, int(level), C.byref(ry), C.byref(kz)), "ecmg_get_tiles")
         return ry.value, kz.value
+
+    def stencil_timer(self, level=-1, reset=False):
+        """(ms summed over the FP32 stencil launches of a level inside solves, launches)."""
+        ms, n = C.c_double(), C.c_int64()
+        check(ecmg_stencil_timer(self.handle, int(level), int(bool(reset)), C.byref(ms), C.byref(n)),
+              "ecmg_stencil_timer")
+        return ms.value, n.value
 
     def autotune(self, reps=3):
         """Time the candidate stencil tile shapes on every large MIXED level; keep the fastest."""
