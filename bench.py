@@ -44,7 +44,13 @@ def parse():
     ap.add_argument("--cpu-levels", type=int, default=5, help="oracle sample: 8^3 -> 8*2^(L-1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--inner-rtol", type=float, default=1e-3,
+                    help="MIXED: FP32 inner reduction between FP64 residual replacements")
     ap.add_argument("--kernels", default="0,1,2,5,6,7", help="kernels timed alone for the report")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-problem measurement")
+    ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched 64-problem workload (one solve per step; --eager for host loop control)")
     ap.add_argument("--profile-kernel", type=int, default=None,
                     help="profiling run: one MIXED solve, then kernel W of ecmg_time_kernel on the finest level, "
                          "3 launches inside the NVTX range kernel_profile (for ncu -k / --nvtx-include); prints "
@@ -184,8 +190,63 @@ def profile_kernel(args):
     s.close()
 
 
+def bench_batched(args, steps, warmup):
+    """64 independent problems (per-axis sizes from {32, 48, 64, 96, 128} cubic elements of side
+    1/128, lognormal beta clipped to contrast 1e2, f ~ U[-1, 1] per node, g_D = 0), seed 1506,
+    rtol 1e-8, MIXED, one batched solve per step (ecmg_solve_batched)."""
+    import numpy as np
+    import torch
+    from paper_1506_02983_gb300 import ecmg, inputs
+    probs = inputs.batch_problems()
+    dev = []
+    for p in probs:
+        q = dict(p)
+        q["beta"] = torch.as_tensor(p["beta"]).cuda()
+        q["f"] = torch.as_tensor(p["f"]).cuda()
+        dev.append(q)
+    bs = ecmg.BatchSolver(dev, rtol=1e-8, max_iters=args.max_iters, use_graph=0 if args.eager else 1,
+                          inner_rtol=args.inner_rtol)
+    for _ in range(warmup):
+        st, status = bs.solve()
+        assert status == 0, status
+    l0 = ecmg.kernel_launches()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("ecmg_batched_timed")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        st, status = bs.solve()
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ms = e0.elapsed_time(e1) / steps
+    launches = (ecmg.kernel_launches() - l0) // steps
+    dofs = sum(int(np.prod([(v << (p["levels"] - 1)) - 1 for v in p["n0"]])) for p in probs)
+    work = 0  # node-iterations of JCG over all problems and levels
+    for p, s in zip(probs, st):
+        for l in range(p["levels"]):
+            work += s["iters"][l] * int(np.prod([(v << l) + 1 for v in p["n0"]]))
+    bs.close()
+    return {"workload": "64 problems, per-axis N from {32,48,64,96,128} (h = 1/128), lognormal beta (sigma 1, "
+                        "contrast 1e2), f ~ U[-1,1], g_D = 0, rtol 1e-8, MIXED, seed 1506",
+            "value": dofs / (ms * 1e-3) / 1e9, "unit": "Gdof/s", "solve_ms": ms, "finest_free_dofs": dofs,
+            "steps": steps, "warmup": warmup, "gpu_launches": launches,
+            "jcg_node_iterations": work, "max_iters_per_level": [max((s["iters"][l] if l < s["levels"] else 0) for s in st)
+                                                                 for l in range(max(s["levels"] for s in st))],
+            "worst_rel_res_finest": max(s["rel_res"][s["levels"] - 1] for s in st),
+            "replacements": sum(sum(s["updates"]) for s in st), "inner_rtol": args.inner_rtol,
+            "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes"}
+
+
 def main():
     args = parse()
+    if args.batched_only:
+        import torch
+        from paper_1506_02983_gb300 import build
+        build.build()
+        r = bench_batched(args, args.steps, args.warmup)
+        print(json.dumps({"metric": "batched ECMG_jcg solve, aggregate Gdof/s", **r}))
+        return
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_kernel is not None:
@@ -216,7 +277,7 @@ def main():
         return ecmg.Solver(p["n0"], L, p["lo"], p["hi"], p["face_bc"], p["alpha"], d["beta"], d["f"],
                            d["gD"], None, f_mode=ecmg.ECMG_F_LOAD, rtol=args.rtol, precision=precision,
                            max_iters=args.max_iters, use_graph=0 if args.eager else 1,
-                           autotune=1 if precision == ecmg.ECMG_MIXED else 0)
+                           autotune=1 if precision == ecmg.ECMG_MIXED else 0, inner_rtol=args.inner_rtol)
 
     def barrier():
         torch.cuda.synchronize()
@@ -300,6 +361,10 @@ def main():
     err_fp64 = fp64.norms(u_out, u_exact)[0]
     fp64.close()
 
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, args.batched_steps, 2)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, args.cpu_levels)
@@ -346,6 +411,7 @@ def main():
         "e2e": {"value": dofs / (ms_e2e * 1e-3) / 1e9, "unit": "Gdof/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
         "cpu_baseline": cpu,
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(out))

@@ -86,7 +86,7 @@ typedef struct {
     double rtol;            /* relative residual tolerance epsilon of Alg. 4 line 7 [1e-9]  */
     int32_t precision;      /* ECMG_FP64 or ECMG_MIXED                        [ECMG_FP64]   */
     double inner_rtol;      /* MIXED: FP32 inner reduction between FP64 residual
-                               replacements                                  [1e-2]        */
+                               replacements                                  [1e-3]        */
     int32_t max_iters;      /* per-level JCG iteration cap                   [100000]      */
     int32_t use_graph;      /* 1: one CUDA graph per solve with device-side loop control;
                                0: host-driven loop (debugging)               [1]           */
@@ -162,6 +162,29 @@ void ecmg_destroy(ecmg_handle* h);
 const char* ecmg_status_string(ecmg_status s);
 const char* ecmg_last_error(void);
 
+/* ---- batched solves (no counterpart in the paper) ----------------------------------------
+ *
+ * Many independent problems of any sizes, boundary conditions and coefficients solved by
+ * Alg. 4 side by side: every step of the method (level set-up, EXP_finite, the FP64 residual,
+ * each FP32 JCG iteration, the residual replacement, EXP_true) is one kernel launch over all
+ * problems, and the whole solve is one CUDA graph whose loops run while any problem runs.
+ * Levels are aligned at the finest: a problem with fewer levels starts later and every problem
+ * finishes its finest level in the last stage. Precision is MIXED only; the direct solves of
+ * levels 0 and 1 are the same FP32 JCG with FP64 residual replacement, run to dsolve_rtol. */
+
+/* probs: n problems (1..128), each validated as by ecmg_create; their device arrays must stay
+ * valid and unchanged while a solve reads them. opt: shared options (precision must be
+ * ECMG_MIXED). stream: a cudaStream_t. Returns a handle for ecmg_solve_batched,
+ * ecmg_get_level_batched and ecmg_destroy; single-problem calls reject it. */
+ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg_options* opt, void* stream,
+                                ecmg_handle** out);
+/* Solve every problem. u_out: NULL, or n device pointers (each NULL or the finest nodal
+ * solution of that problem, dense layout). stats: NULL or n entries (host). Synchronises the
+ * stream. Returns the worst status over all problems and levels. */
+ecmg_status ecmg_solve_batched(ecmg_handle* h, double* const* u_out, ecmg_stats* stats);
+/* As ecmg_get_level for one problem of a batch (which: U, W, U~ or B). */
+ecmg_status ecmg_get_level_batched(ecmg_handle* h, int32_t problem, int32_t level, int32_t which, double* out);
+
 /* ---- measurement helpers (no counterpart in the paper) --------------------------------- */
 
 /* Total kernel executions of this library in the process so far (counted on the device by
@@ -179,6 +202,14 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
  * iterate); U and W are never changed. Synchronises the stream. */
 ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,
                              double* ms_out, double* bytes_out);
+
+/* Device-side timer of the MIXED FP32 stencil kernel (K1) of one level (-1 = finest): the
+ * summed durations of its launches inside ecmg_solve (graph or eager), each from the earliest
+ * block start (global timer) to the end of its last block, and the number of launches summed.
+ * Launches that find their level finished are not counted. reset != 0 zeroes both after
+ * reading. ms_total, launches: host. Synchronises the stream. */
+ecmg_status ecmg_stencil_timer(ecmg_handle* h, int32_t level, int32_t reset, double* ms_total,
+                               int64_t* launches);
 
 /* ---- tile shapes of the FP32 stencil kernel (no counterpart in the paper) --------------
  *

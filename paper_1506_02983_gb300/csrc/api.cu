@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/ecmg.h"
+#include "batch.cuh"
 #include "ecmg_internal.cuh"
 #include "exp.cuh"
 #include "jcg.cuh"
@@ -25,6 +26,21 @@
 using namespace ecmg;
 
 namespace {
+
+// A batch of independent problems (ecmg_create_batched): one item per (problem, level).
+struct Batch {
+    int n = 0;
+    int Lmax = 0;
+    std::vector<int> L;            // levels of each problem
+    std::vector<int> first;        // item index of (problem, level 0)
+    std::vector<BItem> items;      // host copy of the item table
+    BItem* d_items = nullptr;      // device item table
+    SolveState* states = nullptr;  // device, one per item
+    SolveState* host_states = nullptr;  // pinned
+    BCtl* ctl = nullptr;
+    int robin = 0, cube = 1;       // kernel variants: any Robin face in the batch; all elements cubic
+    int item(int p, int l) const { return first[p] + l; }
+};
 
 thread_local std::string g_last_error;
 
@@ -71,6 +87,7 @@ struct ecmg_handle {
     SolveState* host_states = nullptr;  // pinned
     double* host_norms = nullptr;       // pinned
     int graph_first = -1;               // first level of the recorded graph
+    Batch* batch = nullptr;             // batched handle (ecmg_create_batched), else null
 };
 
 namespace {
@@ -79,6 +96,13 @@ ecmg_status fail(ecmg_status s, const std::string& msg)
 {
     g_last_error = msg;
     return s;
+}
+
+bool op_robin(const Op& op)
+{
+    for (int f = 0; f < 6; ++f)
+        if (op.alpha[f] != 0.0) return true;
+    return false;
 }
 
 Grid make_grid(const ecmg_problem& p, int l)
@@ -421,6 +445,167 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
 
 int resolve_level(ecmg_handle* h, int level) { return level < 0 ? h->L - 1 : level; }
 
+// ---- batched solves ----------------------------------------------------------------------------
+// Block table of one batched launch over the given items in one geometry.
+BLaunch make_launch(const Batch& B, const std::vector<int>& ids, BGeom geo)
+{
+    BLaunch L{};
+    L.n = (int)ids.size();
+    int acc = 0;
+    for (int s = 0; s < L.n; ++s) {
+        L.id[s] = ids[s];
+        L.start[s] = acc;
+        acc += bgeom_blocks(geo, B.items[ids[s]]);
+    }
+    L.start[L.n] = acc;
+    return L;
+}
+
+// Items of the set-up at depth d (d = 0: every problem's finest level).
+std::vector<int> depth_items(const Batch& B, int d)
+{
+    std::vector<int> ids;
+    for (int p = 0; p < B.n; ++p)
+        if (B.L[p] - 1 - d >= 0) ids.push_back(B.item(p, B.L[p] - 1 - d));
+    return ids;
+}
+
+// Items of stage s: problem p works on level s - (Lmax - L_p), levels aligned at the finest.
+std::vector<int> stage_items(const Batch& B, int s, int lmin = 0)
+{
+    std::vector<int> ids;
+    for (int p = 0; p < B.n; ++p) {
+        const int l = s - (B.Lmax - B.L[p]);
+        if (l >= lmin && l < B.L[p]) ids.push_back(B.item(p, l));
+    }
+    return ids;
+}
+
+bool any_state(ecmg_handle* h, const std::vector<int>& ids, bool need_update)
+{
+    Batch& B = *h->batch;
+    ck(cudaMemcpyAsync(B.host_states, B.states, sizeof(SolveState) * B.items.size(), cudaMemcpyDeviceToHost,
+                       h->user_stream));
+    ck(cudaStreamSynchronize(h->user_stream));
+    for (int id : ids) {
+        const SolveState& st = B.host_states[id];
+        if (!st.done && (!need_update || st.need_update)) return true;
+    }
+    return false;
+}
+
+void record_batched(Rec& R)
+{
+    ecmg_handle* h = R.h;
+    Batch& B = *h->batch;
+    const ecmg_options& o = h->opt;
+    const BItem* items = B.d_items;
+    for (int d = 0; d < B.Lmax; ++d) {
+        const std::vector<int> ids = depth_items(B, d);
+        blaunch_setup(items, make_launch(B, ids, BG_NODES), make_launch(B, ids, BG_ELEMS), R.s());
+    }
+    for (int s = 0; s < B.Lmax; ++s) {
+        const std::vector<int> ids = stage_items(B, s), ids2 = stage_items(B, s, 2);
+        if (ids.empty()) continue;
+        blaunch_level_start(items, make_launch(B, ids, BG_ONE), make_launch(B, ids, BG_NODES),
+                            make_launch(B, ids, BG_ROWS), B.robin, B.cube, o.inner_rtol, o.max_iters, R.s());
+        blaunch_guess(items, make_launch(B, ids2, BG_EXPF), make_launch(B, ids, BG_FLAT), o.exp_variant, R.s());
+        const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_FLAT);
+        if (R.graph) {
+            const cudaGraphConditionalHandle loop = R.new_handle();
+            blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, CondHandles{loop, 0, 1}, R.s());
+            R.open(loop, cudaGraphCondTypeWhile);
+            for (int half = 0; half < 2; ++half) {
+                const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
+                blaunch_pq(items, stencil, B.robin, B.cube, half, half ? 0 : 1, R.s());
+                blaunch_update(items, flat, B.ctl, CondHandles{loop, upd, 1}, R.s());
+                R.open(upd, cudaGraphCondTypeIf);
+                blaunch_fold(items, flat, half ? 0 : 1, R.s());
+                blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, CondHandles{loop, 0, 1}, R.s());
+                R.close();
+            }
+            R.close();
+        } else {
+            const CondHandles none{0, 0, 0};
+            blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, none, R.s());
+            int half = 0;
+            while (any_state(h, ids, false)) {
+                blaunch_pq(items, stencil, B.robin, B.cube, half, half ? 0 : 1, R.s());
+                blaunch_update(items, flat, B.ctl, none, R.s());
+                if (any_state(h, ids, true)) {
+                    blaunch_fold(items, flat, half ? 0 : 1, R.s());
+                    blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, none, R.s());
+                }
+                half ^= 1;
+            }
+        }
+        blaunch_exp_true(items, make_launch(B, ids2, BG_EXPT), R.s());
+    }
+}
+
+ecmg_status run_batched(ecmg_handle* h, double* const* u_out, ecmg_stats* stats)
+{
+    Batch& B = *h->batch;
+    try {
+        if (h->opt.use_graph) {
+            if (!h->exec) {
+                Rec R{h, true, 0};
+                ck(cudaStreamBeginCapture(h->cap[0], cudaStreamCaptureModeThreadLocal));
+                try {
+                    record_batched(R);
+                } catch (...) {
+                    cudaGraph_t junk;
+                    cudaStreamEndCapture(h->cap[0], &junk);
+                    if (junk) cudaGraphDestroy(junk);
+                    throw;
+                }
+                ck(cudaStreamEndCapture(h->cap[0], &h->graph));
+                ck(cudaGraphInstantiate(&h->exec, h->graph, 0));
+            }
+            ck(cudaGraphLaunch(h->exec, h->user_stream));
+        } else {
+            Rec R{h, false, 0};
+            record_batched(R);
+        }
+        if (u_out)
+            for (int p = 0; p < B.n; ++p)
+                if (u_out[p]) {
+                    const BItem& it = B.items[B.item(p, B.L[p] - 1)];
+                    unpack_nodal(it.g, it.U, u_out[p], h->user_stream);
+                }
+        ck(cudaGetLastError());
+        ck(cudaMemcpyAsync(B.host_states, B.states, sizeof(SolveState) * B.items.size(), cudaMemcpyDeviceToHost,
+                           h->user_stream));
+        ck(cudaStreamSynchronize(h->user_stream));
+    } catch (CudaFail& f) {
+        return fail(ECMG_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(f.e));
+    }
+    ecmg_status worst = ECMG_OK;
+    for (int p = 0; p < B.n; ++p) {
+        ecmg_stats st;
+        memset(&st, 0, sizeof(st));
+        st.levels = B.L[p];
+        ecmg_status pw = ECMG_OK;
+        for (int l = 0; l < B.L[p]; ++l) {
+            const SolveState& s = B.host_states[B.item(p, l)];
+            st.iters[l] = s.iters;
+            st.updates[l] = s.updates;
+            st.rhs_norm[l] = std::sqrt(s.fh2);
+            st.rel_res[l] = s.fh2 > 0 ? std::sqrt(s.rr_true / s.fh2) : std::sqrt(s.rr_true);
+            ecmg_status ls = ECMG_OK;
+            if (s.status == 3) ls = ECMG_ERR_NO_CONVERGENCE;
+            if (s.status == 4) ls = ECMG_ERR_BREAKDOWN;
+            if (ls == ECMG_ERR_BREAKDOWN || (ls != ECMG_OK && pw == ECMG_OK)) pw = ls;
+        }
+        st.status = pw;
+        if (stats) stats[p] = st;
+        if (pw == ECMG_ERR_BREAKDOWN || (pw != ECMG_OK && worst == ECMG_OK)) worst = pw;
+    }
+    if (worst != ECMG_OK) g_last_error = ecmg_status_string(worst);
+    return worst;
+}
+
+
 // Forget the recorded graph (it holds launch shapes that no longer apply).
 void drop_graph(ecmg_handle* h)
 {
@@ -532,7 +717,7 @@ void ecmg_default_options(ecmg_options* o)
     if (!o) return;
     o->rtol = 1e-9;
     o->precision = ECMG_FP64;
-    o->inner_rtol = 1e-2;
+    o->inner_rtol = 1e-3;
     o->max_iters = 100000;
     o->use_graph = 1;
     o->dsolve_rtol = 1e-14;
@@ -638,7 +823,142 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
 ecmg_status ecmg_solve(ecmg_handle* h, double* u_out, ecmg_stats* stats)
 {
     if (!h) return fail(ECMG_ERR_INVALID_ARG, "null handle");
+    if (h->batch) return fail(ECMG_ERR_INVALID_ARG, "batched handle: use ecmg_solve_batched");
     return run_solve(h, 0, u_out, stats);
+}
+
+ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg_options* opt, void* stream,
+                                ecmg_handle** out)
+{
+    if (!out || !probs || !opt) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (n < 1 || n > BATCH_MAX) return fail(ECMG_ERR_INVALID_ARG, "batch size must be 1..128");
+    if (opt->precision != ECMG_MIXED) return fail(ECMG_ERR_INVALID_ARG, "batched solves run in MIXED precision");
+    for (int p = 0; p < n; ++p) {
+        ecmg_status s = validate(probs + p, opt);
+        if (s != ECMG_OK) return s;
+    }
+    ecmg_handle* h = new ecmg_handle();
+    h->prob = probs[0];
+    h->opt = *opt;
+    h->user_stream = (cudaStream_t)stream;
+    h->L = 0;  // no single-problem levels
+    h->batch = new Batch();
+    Batch& B = *h->batch;
+    B.n = n;
+    try {
+        for (int i = 0; i < 3; ++i) ck(cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
+        int nitems = 0;
+        for (int p = 0; p < n; ++p) {
+            B.L.push_back(probs[p].levels);
+            B.first.push_back(nitems);
+            nitems += probs[p].levels;
+            B.Lmax = std::max(B.Lmax, probs[p].levels);
+        }
+        B.items.resize(nitems);
+        B.states = dalloc<SolveState>(h, nitems);
+        B.ctl = dalloc<BCtl>(h, 1);
+        ck(cudaMallocHost(&B.host_states, sizeof(SolveState) * nitems));
+        // vectors, finest first so that every level can point at its finer neighbour
+        for (int p = 0; p < n; ++p) {
+            const ecmg_problem& pr = probs[p];
+            for (int l = pr.levels - 1; l >= 0; --l) {
+                BItem& it = B.items[B.item(p, l)];
+                it = BItem{};
+                it.g = make_grid(pr, l);
+                it.op = make_op(it.g.h, pr.face_bc, pr.robin_alpha);
+                it.level = l;
+                it.problem = p;
+                it.depth = pr.levels - 1 - l;
+                it.fmode = pr.f_mode;
+                it.kz = std::min(32, it.g.nz + 1);
+                it.rtol = l < 2 ? opt->dsolve_rtol : opt->rtol;
+                const int64_t nv = it.g.total;
+                it.U = dalloc<double>(h, nv);
+                it.W = dalloc<double>(h, nv);
+                it.Ut = dalloc<double>(h, nv);
+                it.b = dalloc<double>(h, nv);
+                it.beta = dalloc<double>(h, nv);
+                it.f = dalloc<double>(h, nv);
+                it.gD = dalloc<double>(h, nv);
+                it.gR = dalloc<double>(h, nv);
+                it.beta32 = dalloc<float>(h, nv);
+                it.dinv32 = dalloc<float>(h, nv);
+                it.r32 = dalloc<float>(h, nv);
+                it.pA32 = dalloc<float>(h, nv);
+                it.pB32 = dalloc<float>(h, nv);
+                it.q32 = dalloc<float>(h, nv);
+                it.e32 = dalloc<float>(h, nv);
+                it.st = B.states + B.item(p, l);
+                it.part = dalloc<double>(h, 2 * (int64_t)bitem_partials(it));
+                if (it.depth == 0) {
+                    it.in_beta = pr.beta;
+                    it.in_f = pr.f;
+                    it.in_gD = pr.g_D;
+                    it.in_gR = pr.g_R;
+                } else {
+                    const BItem& fi = B.items[B.item(p, l + 1)];
+                    it.gf = fi.g;
+                    it.fbeta = fi.beta;
+                    it.ff = fi.f;
+                    it.fgD = fi.gD;
+                    it.fgR = fi.gR;
+                    it.fb = fi.b;
+                }
+                B.robin |= op_robin(it.op);
+                B.cube &= it.op.cube;
+            }
+            for (int l = 2; l < pr.levels; ++l) {
+                BItem& it = B.items[B.item(p, l)];
+                const BItem& i1 = B.items[B.item(p, l - 1)];
+                const BItem& i0 = B.items[B.item(p, l - 2)];
+                it.g1 = i1.g;
+                it.U1 = i1.U;
+                it.g0 = i0.g;
+                it.U0 = i0.U;
+            }
+        }
+        B.d_items = dalloc<BItem>(h, nitems);
+        ck(cudaMemcpyAsync(B.d_items, B.items.data(), sizeof(BItem) * nitems, cudaMemcpyHostToDevice, h->cap[0]));
+        ck(cudaStreamSynchronize(h->cap[0]));
+    } catch (CudaFail& f) {
+        ecmg_destroy(h);
+        if (f.e == cudaErrorMemoryAllocation) return fail(ECMG_ERR_OOM, "device allocation failed");
+        return fail(ECMG_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(f.e));
+    }
+    *out = h;
+    return ECMG_OK;
+}
+
+ecmg_status ecmg_solve_batched(ecmg_handle* h, double* const* u_out, ecmg_stats* stats)
+{
+    if (!h || !h->batch) return fail(ECMG_ERR_INVALID_ARG, "not a batched handle");
+    return run_batched(h, u_out, stats);
+}
+
+ecmg_status ecmg_get_level_batched(ecmg_handle* h, int32_t problem, int32_t level, int32_t which, double* out)
+{
+    if (!h || !h->batch || !out) return fail(ECMG_ERR_INVALID_ARG, "null argument or not a batched handle");
+    Batch& B = *h->batch;
+    if (problem < 0 || problem >= B.n) return fail(ECMG_ERR_INVALID_ARG, "bad problem index");
+    const int l = level < 0 ? B.L[problem] - 1 : level;
+    if (l < 0 || l >= B.L[problem]) return fail(ECMG_ERR_INVALID_ARG, "bad level");
+    const BItem& it = B.items[B.item(problem, l)];
+    const double* src = nullptr;
+    switch (which) {
+    case ECMG_VEC_U: src = it.U; break;
+    case ECMG_VEC_W: src = it.W; break;
+    case ECMG_VEC_UTILDE:
+        if (l < 2) return fail(ECMG_ERR_INVALID_ARG, "U~ exists on levels >= 2 only");
+        src = it.Ut;
+        break;
+    case ECMG_VEC_B: src = it.b; break;
+    default: return fail(ECMG_ERR_INVALID_ARG, "bad vector selector (U, W, U~ or B)");
+    }
+    unpack_nodal(it.g, src, out, h->user_stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
+    return ECMG_OK;
 }
 
 ecmg_status ecmg_solve_from(ecmg_handle* h, int32_t first, double* u_out, ecmg_stats* stats)
@@ -759,6 +1079,10 @@ void ecmg_destroy(ecmg_handle* h)
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->batch) {
+        if (h->batch->host_states) cudaFreeHost(h->batch->host_states);
+        delete h->batch;
+    }
     if (h->host_states) cudaFreeHost(h->host_states);
     if (h->host_norms) cudaFreeHost(h->host_norms);
     for (int i = 0; i < 3; ++i)
@@ -785,7 +1109,7 @@ const char* ecmg_last_error(void) { return g_last_error.c_str(); }
 ecmg_status ecmg_kernel_launches(uint64_t* out)
 {
     if (!out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
-    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma();
+    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_batch();
     return ECMG_OK;
 }
 

@@ -1,0 +1,101 @@
+// batch.cuh -- many independent problems in one launch per step (batch.cu).
+//
+// A batched solve runs Alg. 4 for every problem of the batch side by side. Levels are aligned
+// at the finest: at stage s, a problem with L levels of a batch whose deepest problem has Lmax
+// works on its level s - (Lmax - L), so every problem finishes its finest level at the last
+// stage. Each step of a stage (state set-up, EXP_finite, the FP64 residual, one FP32 JCG
+// iteration, the residual replacement, EXP_true) is ONE kernel launch over the blocks of all
+// problems that take part; a block finds its (problem, level) item from the launch's block
+// offsets and works on that item's grid alone. Reductions are per item (the item's last block
+// advances that item's JCG recurrence); the kernels that steer the loop also count every block
+// of the launch, and the launch's last block sets the CUDA-graph conditions from all items:
+// keep looping while any item runs, replace residuals where any item asks for it.
+#pragma once
+
+#include "ecmg_internal.cuh"
+#include "jcg.cuh"
+
+namespace ecmg {
+
+constexpr int BATCH_MAX = 128;  // problems per batch
+
+// One (problem, level) of a batch.
+struct BItem {
+    Grid g;
+    Op op;
+    Grid g1, g0;          // levels l-1 and l-2 (EXP)
+    Grid gf;              // level l+1 (set-up of a coarser level)
+    int level, problem, depth, fmode;  // depth 0 = the problem's finest level
+    int kz;               // z-march depth of the stencil kernels
+    double rtol;          // relative residual tolerance of this level
+    // vectors of this level (padded layout)
+    double *U, *W, *Ut, *b, *beta, *f, *gD, *gR;
+    float *beta32, *dinv32, *r32, *pA32, *pB32, *q32, *e32;
+    // solutions of levels l-1, l-2 (EXP)
+    const double *U1, *U0;
+    // level l+1 vectors (set-up of a coarser level)
+    const double *fbeta, *ff, *fgD, *fgR, *fb;
+    // the caller's finest arrays (dense layout; depth 0 only; gD, gR may be null)
+    const double *in_beta, *in_f, *in_gD, *in_gR;
+    SolveState* st;
+    double* part;         // per-block partial sums of this item's reductions
+};
+
+// Blocks of one batched launch: slot s covers blocks [start[s], start[s+1]) and works on item
+// id[s].
+struct BLaunch {
+    int n;
+    int id[BATCH_MAX];
+    int start[BATCH_MAX + 1];
+};
+
+// Launch-wide reduction state (device).
+struct BCtl {
+    unsigned int arrive;
+};
+
+// Block shapes of the batched kernels.
+enum BGeom : int {
+    BG_STENCIL = 0,  // 32 x 8 node tiles x kz planes (the z-march kernels)
+    BG_FLAT,         // 4096 consecutive padded elements per block (vector updates)
+    BG_NODES,        // 32 x 8 nodes of one plane per block
+    BG_ELEMS,        // 32 x 8 elements of one slab per block
+    BG_EXPF,         // 128 level-(l-2) elements per block
+    BG_EXPT,         // 128 level-(l-1) elements per block
+    BG_ROWS,         // 32 rows (j, k) per block
+    BG_ONE,          // one block per item
+    BG_COUNT
+};
+constexpr int BFLAT_ELEMS = 4096;
+
+// Blocks one item needs in a geometry (host).
+int bgeom_blocks(BGeom geo, const BItem& it);
+// Most per-block partial pairs any reducing launch needs for this item (host).
+int bitem_partials(const BItem& it);
+
+// Set-up of one depth (finest first): beta (packed or averaged) and its FP32 copy; f, g_D, g_R
+// (packed or injected); the load vector; the FP32 Jacobi diagonal.
+void blaunch_setup(const BItem* items, const BLaunch& nodes, const BLaunch& elems, cudaStream_t s);
+// Start of a level: state reset, Dirichlet extension, ||f_h||^2.
+void blaunch_level_start(const BItem* items, const BLaunch& one, const BLaunch& nodes, const BLaunch& rows,
+                         int robin, int cube, double inner_rtol, int max_iters, cudaStream_t s);
+// EXP_finite for levels >= 2 (x and W), W = x on the direct levels 0 and 1, and zeroed FP32
+// search directions and corrections.
+void blaunch_guess(const BItem* items, const BLaunch& expf, const BLaunch& flat_all, int variant, cudaStream_t s);
+// FP64 residual r = b - A x (stored FP32) with r.z and ||r||^2 per item; mode RES_INIT or
+// RES_REPLACE (items that asked for a replacement only). Sets the loop condition.
+void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube, ResMode mode, BCtl* ctl,
+                 CondHandles ch, cudaStream_t s);
+// One FP32 JCG iteration: K1 (p, q = A p, deferred correction, p.q) and K2 (r, r.z, tests).
+// pin_is_b selects p_old; K2 sets the loop and replacement conditions.
+void blaunch_pq(const BItem* items, const BLaunch& stencil, int robin, int cube, int pin_is_b, int pidx,
+                cudaStream_t s);
+void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s);
+// Fold the FP32 correction into the FP64 iterate for items that asked for a replacement.
+void blaunch_fold(const BItem* items, const BLaunch& flat, int pnew_is_b, cudaStream_t s);
+// EXP_true for levels >= 2.
+void blaunch_exp_true(const BItem* items, const BLaunch& expt, cudaStream_t s);
+
+unsigned long long launches_batch();
+
+}  // namespace ecmg

@@ -12,6 +12,8 @@
 //
 // The operator at a node is q1_apply (stencil_core.cuh).
 #include "jcg.cuh"
+#include "jcg_core.cuh"
+#include "march.cuh"
 #include "stencil_core.cuh"
 
 #include <cmath>
@@ -24,47 +26,10 @@ __device__ unsigned long long g_launches = 0;  // kernel executions of this file
     if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0) \
         atomicAdd(&g_launches, 1ull)
 
-constexpr int BX = 32, BY = 8, NT = BX * BY;
+constexpr int NT = mt::NT;
 constexpr int KZ_TARGET = 64;
 constexpr int UPD_TPB = 256;
 constexpr int UPD_MAX_BLOCKS = 152 * 8;
-
-// ---- compensated FP32 accumulation ------------------------------------------------------
-// Products are split exactly (TwoProduct with an FMA) and summed with TwoSum, so a thread's
-// sum of FP32 products carries about 48 significant bits before it is promoted to FP64 for
-// the block and grid stages. Intrinsics keep the compiler from contracting the steps.
-struct CSum {
-    float s, c;
-};
-__device__ __forceinline__ void csum_add(CSum& a, float x)
-{
-    float t = __fadd_rn(a.s, x);
-    float bp = __fsub_rn(t, a.s);
-    float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-    a.s = t;
-    a.c = __fadd_rn(a.c, e);
-}
-__device__ __forceinline__ void csum_add_prod(CSum& a, float x, float y)
-{
-    float p = __fmul_rn(x, y);
-    float e = __fmaf_rn(x, y, -p);
-    csum_add(a, p);
-    a.c = __fadd_rn(a.c, e);
-}
-__device__ __forceinline__ double csum_value(const CSum& a) { return (double)a.s + (double)a.c; }
-
-// Accumulator selection: FP64 for FP64 data, compensated FP32 for FP32 data.
-template <typename T> struct Acc;
-template <> struct Acc<double> {
-    double v = 0.0;
-    __device__ __forceinline__ void add_prod(double x, double y) { v = fma(x, y, v); }
-    __device__ __forceinline__ double value() const { return v; }
-};
-template <> struct Acc<float> {
-    CSum v{0.f, 0.f};
-    __device__ __forceinline__ void add_prod(float x, float y) { csum_add_prod(v, x, y); }
-    __device__ __forceinline__ double value() const { return csum_value(v); }
-};
 
 // ---- block / grid reductions --------------------------------------------------------------
 template <int NP>
@@ -117,67 +82,12 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NP], double* partials, unsi
     return tid == 0;
 }
 
-// ---- the tiled z-march -------------------------------------------------------------------
-// Each block owns a BX x BY column of nodes over planes [kb, ke). Three node planes of the
-// operand (k-1, k, k+1) and two element slabs of beta (k-1, k) live in shared memory; the
-// operand of a plane is produced by src(offset), so K1 can form p on the fly.
+// ---- the tiled z-march (march.cuh), one tile per block ---------------------------------------
 template <bool ROBIN, bool CUBE, typename VT, typename BT, typename SRC, typename BODY>
 __device__ __forceinline__ void march(const Grid& g, const Op& op, const BT* __restrict__ beta,
                                       int kz, SRC src, BODY body)
 {
-    __shared__ VT sv[3][BY + 2][BX + 2];
-    __shared__ VT sb[2][BY + 1][BX + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
-    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
-    const int kb = blockIdx.z * kz;
-    const int ke = min(kb + kz, g.nz + 1);
-    const Weights<VT> wts(op);
-
-    auto load_plane = [&](int k) {
-        VT(*dst)[BX + 2] = sv[(k + 3) % 3];
-        const int64_t base = g.plane_base(k);
-        for (int c = tid; c < (BX + 2) * (BY + 2); c += NT) {
-            const int ci = c % (BX + 2), cj = c / (BX + 2);
-            const int i = i0 - 1 + ci, j = j0 - 1 + cj;
-            VT v = VT(0);
-            if (i <= g.nx + 1 && j <= g.ny + 1) v = src(base + g.in_plane(i, j));
-            dst[cj][ci] = v;
-        }
-    };
-    auto load_slab = [&](int ez) {
-        VT(*dst)[BX + 1] = sb[(ez + 2) % 2];
-        const int64_t base = g.plane_base(ez);
-        for (int c = tid; c < (BX + 1) * (BY + 1); c += NT) {
-            const int ci = c % (BX + 1), cj = c / (BX + 1);
-            const int ex = i0 - 1 + ci, ey = j0 - 1 + cj;
-            VT v = VT(0);
-            if (ex <= g.nx + 1 && ey <= g.ny + 1) v = (VT)beta[base + g.in_plane(ex, ey)];
-            dst[cj][ci] = v;
-        }
-    };
-
-    load_plane(kb - 1);
-    load_plane(kb);
-    load_slab(kb - 1);
-    for (int k = kb; k < ke; ++k) {
-        load_plane(k + 1);
-        load_slab(k);
-        __syncthreads();
-        const int i = i0 + tx, j = j0 + ty;
-        if (i <= g.nx && j <= g.ny) {
-            const int pm = (k + 2) % 3, p0 = k % 3, pp = (k + 1) % 3;
-            const int s0 = (k + 1) % 2, s1 = k % 2;
-            auto V = [&](int dx, int dy, int dz) -> VT {
-                return sv[dz < 0 ? pm : (dz > 0 ? pp : p0)][ty + 1 + dy][tx + 1 + dx];
-            };
-            const VT xc = V(0, 0, 0);
-            const VT Av = q1_apply<true, ROBIN, CUBE, VT>(V, sb[s0][ty][tx], sb[s0][ty][tx + 1], sb[s0][ty + 1][tx],
-                                                          sb[s0][ty + 1][tx + 1], sb[s1][ty][tx], sb[s1][ty][tx + 1],
-                                                          sb[s1][ty + 1][tx], sb[s1][ty + 1][tx + 1], i, j, k, g, op, wts);
-            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Av, xc);
-        }
-        __syncthreads();
-    }
+    march_tile<ROBIN, CUBE, VT, BT>(g, op, beta, blockIdx.x, blockIdx.y, blockIdx.z, kz, src, body);
 }
 
 // ---- the z-march for a level with one beta everywhere (FP64) ------------------------------
@@ -551,7 +461,7 @@ __global__ void __launch_bounds__(NT) k_pq(const Grid g, const Op op, const T* _
     const T bcg = (T)st->beta;
     const T ap = (T)st->alpha_prev;
     Acc<T> acc;
-    auto src = [&](int64_t o) -> T { return dinv[o] * r[o] + bcg * pold[o]; };
+    const PSource<T> src{dinv, r, pold, bcg};
     auto body = [&](int i, int j, int k, int64_t o, T Av, T pn) {
         const T qv = on_dirichlet(g, op, i, j, k) ? T(0) : Av;
         pnew[o] = pn;
@@ -562,73 +472,10 @@ __global__ void __launch_bounds__(NT) k_pq(const Grid g, const Op op, const T* _
     if constexpr (sizeof(T) == 8) ECMG_FP64_MARCH(T, ROBIN, CUBE, false, src, body);
     else march<ROBIN, CUBE, T, T>(g, op, beta, kz, src, body);
     double v[1] = {acc.value()};
-    if (grid_sum<1>(v, partials, &st->arrive)) {
-        const double pq = v[0];
-        st->alpha_prev = 0.0;  // applied by every block above
-        st->p_latest = pidx;
-        st->pq = pq;
-        if (!(pq > 0.0) || !isfinite(pq)) {
-            st->status = 4;
-            st->done = 1;
-            if (ch.use) cudaGraphSetConditional(ch.loop, 0);
-        } else {
-            st->alpha = st->rho / pq;
-        }
-    }
+    if (grid_sum<1>(v, partials, &st->arrive)) pq_epilogue(st, v[0], pidx, ch);
 }
 
-// ---- residual r = b - A x (FP64 arithmetic) -------------------------------------------------
-__device__ void res_epilogue(SolveState* st, double rr, double rz, int mode, CondHandles ch)
-{
-    switch (mode) {
-    case RES_FH2:
-        st->fh2 = rr;
-        st->thresh2 = st->rtol2 * rr;
-        break;
-    case RES_INIT:
-        st->rr = rr;
-        st->rr_true = rr;
-        st->rr_ref = rr;
-        st->rho = rz;
-        st->beta = 0.0;
-        st->alpha_prev = 0.0;
-        st->need_update = 0;
-        if (!isfinite(rr) || !isfinite(rz)) {
-            st->status = 4;
-            st->done = 1;
-        } else if (rr <= st->thresh2) {
-            st->done = 1;
-        }
-        if (ch.use) cudaGraphSetConditional(ch.loop, st->done ? 0u : 1u);
-        break;
-    case RES_REPLACE:
-        st->updates += 1;
-        st->rr_true = rr;
-        st->alpha_prev = 0.0;
-        st->need_update = 0;
-        if (!isfinite(rr) || !isfinite(rz)) {
-            st->status = 4;
-            st->done = 1;
-        } else if (rr <= st->thresh2) {
-            st->rr = rr;
-            st->done = 1;
-        } else if (st->stop_after_update) {
-            st->rr = rr;
-            st->status = 3;
-            st->done = 1;
-        } else {
-            st->beta = rz / st->rho;
-            st->rho = rz;
-            st->rr = rr;
-            st->rr_ref = rr;
-        }
-        break;
-    default:
-        st->rr_true = rr;
-        break;
-    }
-}
-
+// ---- residual r = b - A x --------------------------------------------------------------------
 template <typename OT, bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const double* __restrict__ beta,
                                             const int* uniform, const double* __restrict__ x,
@@ -659,10 +506,7 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
     if (grid_sum<2>(v, partials, &st->arrive)) res_epilogue(st, v[0], v[1], mode, ch);
 }
 
-// ---- ||f_h||: the free-node right-hand side with the Dirichlet values moved over -------------
-// x holds g_D on Dirichlet nodes and 0 elsewhere, so (A x)_i vanishes at every free node with
-// no Dirichlet neighbour: there f_h,i = b_i. Only the layer next to a Dirichlet face needs the
-// stencil, evaluated here straight from global memory.
+// ---- ||f_h||: the free-node right-hand side with the Dirichlet values moved over (fh_at) -------
 template <bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, const double* __restrict__ beta,
                                                  const double* __restrict__ x, const double* __restrict__ b,
@@ -670,8 +514,6 @@ __global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, cons
 {
     COUNT_LAUNCH();
     const Weights<double> wts(op);
-    const bool dx0 = op.bc[0] == 0, dx1 = op.bc[1] == 0, dy0 = op.bc[2] == 0, dy1 = op.bc[3] == 0;
-    const bool dz0 = op.bc[4] == 0, dz1 = op.bc[5] == 0;
     double ss = 0.0;
     // rows (j, k) spread over the warps of the grid, nodes i of a row over the lanes
     const int nrows = (g.ny + 1) * (g.nz + 1);
@@ -681,19 +523,7 @@ __global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, cons
         const int64_t orow = g.plane_base(k) + g.in_plane(0, j);
         for (int i = threadIdx.x & 31; i <= g.nx; i += 32) {
             if (on_dirichlet(g, op, i, j, k)) continue;
-            const int64_t o = orow + i;
-            double f = b[o];
-            const bool near = (dx0 && i <= 1) || (dx1 && i >= g.nx - 1) || (dy0 && j <= 1) || (dy1 && j >= g.ny - 1) ||
-                              (dz0 && k <= 1) || (dz1 && k >= g.nz - 1);
-            if (near) {
-                auto V = [&](int ddx, int ddy, int ddz) -> double {
-                    return x[o + (int64_t)ddz * g.plane + (int64_t)ddy * g.pitch + ddx];
-                };
-                auto be = [&](int ex, int ey, int ez) { return beta[g.off(i - 1 + ex, j - 1 + ey, k - 1 + ez)]; };
-                f -= q1_apply<true, ROBIN, CUBE, double>(V, be(0, 0, 0), be(1, 0, 0), be(0, 1, 0), be(1, 1, 0),
-                                                         be(0, 0, 1), be(1, 0, 1), be(0, 1, 1), be(1, 1, 1), i, j, k, g,
-                                                         op, wts);
-            }
+            const double f = fh_at<ROBIN, CUBE>(g, op, wts, beta, x, b, orow + i, i, j, k);
             ss = fma(f, f, ss);
         }
     }
@@ -771,34 +601,7 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
     }
     double v[2] = {rz.value(), rr.value()};
     if (grid_sum<2>(v, partials, &st->arrive)) {
-        const double rho_new = v[0], rrv = v[1];
-        st->iters += 1;
-        st->alpha_prev = st->alpha;
-        st->rr = rrv;
-        if (!isfinite(rho_new) || !isfinite(rrv)) {
-            st->status = 4;
-            st->done = 1;
-        } else if (!MIXED) {
-            if (rrv <= st->thresh2) {
-                st->done = 1;
-            } else if (st->iters >= st->max_iters) {
-                st->status = 3;
-                st->done = 1;
-            } else {
-                st->beta = rho_new / st->rho;
-                st->rho = rho_new;
-            }
-        } else {
-            if (rrv <= st->thresh2 || rrv <= st->inner2 * st->rr_ref) {
-                st->need_update = 1;
-            } else if (st->iters >= st->max_iters) {
-                st->need_update = 1;
-                st->stop_after_update = 1;
-            } else {
-                st->beta = rho_new / st->rho;
-                st->rho = rho_new;
-            }
-        }
+        update_epilogue<MIXED>(st, v[0], v[1]);
         if (ch.use) {
             cudaGraphSetConditional(ch.loop, st->done ? 0u : 1u);
             if (MIXED) cudaGraphSetConditional(ch.update, st->need_update ? 1u : 0u);

@@ -2,6 +2,7 @@
 // ghost-padded device layout, beta averaging, injection, load vectors (Sec. 2) and the
 // Jacobi diagonal of JCG. All of it runs once per level per solve; FP64 throughout.
 #include "ecmg_internal.cuh"
+#include "setup_core.cuh"
 
 namespace ecmg {
 
@@ -22,13 +23,6 @@ inline dim3 grid3(int mx, int my, int mz) { return dim3((mx + TX) / TX, (my + TY
     const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y; \
     const int k = blockIdx.z;                                                       \
     if (i > (MX) || j > (MY)) return
-
-__device__ __forceinline__ bool on_dirichlet(const Grid& g, const Op& op, int i, int j, int k)
-{
-    return (i == 0 && op.bc[0] == 0) || (i == g.nx && op.bc[1] == 0) ||
-           (j == 0 && op.bc[2] == 0) || (j == g.ny && op.bc[3] == 0) ||
-           (k == 0 && op.bc[4] == 0) || (k == g.nz && op.bc[5] == 0);
-}
 
 __global__ void k_pack_nodal(Grid g, const double* __restrict__ dense, double* __restrict__ dst)
 {
@@ -54,15 +48,11 @@ __global__ void k_pack_elements(Grid g, const double* __restrict__ dense, double
     dst[g.off(i, j, k)] = dense[t];
 }
 
-// Coarse element = mean of its 8 children, summed x fastest then y then z.
 __global__ void k_coarsen_beta(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
 {
     COUNT_LAUNCH();
     POINT_IJK(gc.nx - 1, gc.ny - 1);
-    double s = 0.0;
-    for (int c = 0; c < 8; ++c)
-        s += bf[gf.off(2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + (c >> 2))];
-    bc[gc.off(i, j, k)] = s / 8.0;
+    bc[gc.off(i, j, k)] = coarse_beta_at(bf, gf, i, j, k);
 }
 
 __global__ void k_inject(Grid gc, const double* __restrict__ vf, Grid gf, double* __restrict__ vc)
@@ -72,70 +62,19 @@ __global__ void k_inject(Grid gc, const double* __restrict__ vf, Grid gf, double
     vc[gc.off(i, j, k)] = vf[gf.off(2 * i, 2 * j, 2 * k)];
 }
 
-// b_c = P^T b_f with P trilinear prolongation: fine node 2I + d contributes with weight
-// prod_a w(d_a), w(0) = 1, w(+-1) = 1/2. Fine ghost nodes hold 0, so no bounds checks.
 __global__ void k_restrict(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
 {
     COUNT_LAUNCH();
     POINT_IJK(gc.nx, gc.ny);
-    double s = 0.0;
-    for (int dk = -1; dk <= 1; ++dk)
-        for (int dj = -1; dj <= 1; ++dj)
-            for (int di = -1; di <= 1; ++di) {
-                double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);
-                s += w * bf[gf.off(2 * i + di, 2 * j + dj, 2 * k + dk)];
-            }
-    bc[gc.off(i, j, k)] = s;
+    bc[gc.off(i, j, k)] = restrict_at(bf, gf, i, j, k);
 }
 
-// Element count along one axis between node index a and a + d (d in -1..1).
-__device__ __forceinline__ int cnt1(int a, int n, int d)
-{
-    if (d < 0) return a >= 1;
-    if (d > 0) return a < n;
-    return (a >= 1) + (a < n);
-}
-
-// b = M f_I + sum over Robin faces of M_F gR_I (consistent mass matrices of Sec. 2). The
-// element mass is a tensor product, so the assembled row is prod_a cnt_a(d_a) m_a(d_a) with
-// m(0) = h/3, m(+-1) = h/6 per element.
 __global__ void k_nodal_load(Grid g, Op op, const double* __restrict__ f,
                              const double* __restrict__ gR, double* __restrict__ b)
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
-    const int idx[3] = {i, j, k};
-    const int nn[3] = {g.nx, g.ny, g.nz};
-    double wa[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int d = -1; d <= 1; ++d)
-            wa[a][d + 1] = cnt1(idx[a], nn[a], d) * g.h[a] * (d ? 1.0 : 2.0) / 6.0;
-    double s = 0.0;
-    for (int dk = -1; dk <= 1; ++dk)
-        for (int dj = -1; dj <= 1; ++dj)
-            for (int di = -1; di <= 1; ++di) {
-                double w = wa[0][di + 1] * wa[1][dj + 1] * wa[2][dk + 1];
-                if (w != 0.0) s += w * f[g.off(i + di, j + dj, k + dk)];
-            }
-    if (gR) {
-        for (int fc = 0; fc < 6; ++fc) {
-            if (op.bc[fc] != 1) continue;
-            int an = fc / 2;
-            if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
-            int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
-            for (int db = -1; db <= 1; ++db)
-                for (int da = -1; da <= 1; ++da) {
-                    double w = cnt1(idx[aa], nn[aa], da) * g.h[aa] * (da ? 1.0 : 2.0) / 6.0 *
-                               cnt1(idx[ab], nn[ab], db) * g.h[ab] * (db ? 1.0 : 2.0) / 6.0;
-                    if (w == 0.0) continue;
-                    int o[3] = {0, 0, 0};
-                    o[aa] = da;
-                    o[ab] = db;
-                    s += w * gR[g.off(i + o[0], j + o[1], k + o[2])];
-                }
-        }
-    }
-    b[g.off(i, j, k)] = s;
+    b[g.off(i, j, k)] = nodal_load_at(g, op, f, gR, i, j, k);
 }
 
 // Jacobi diagonal: diag = w0 * (sum of the 8 element betas) + Robin face mass diagonal.
@@ -168,24 +107,7 @@ __global__ void k_jacobi32(Grid g, Op op, const float* __restrict__ beta32, floa
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
-    float B = 0.f;
-    for (int c = 0; c < 8; ++c)
-        B += beta32[g.off(i - 1 + (c & 1), j - 1 + ((c >> 1) & 1), k - 1 + (c >> 2))];
-    float d = __fmul_rn((float)op.w0, B);
-    if (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz) {
-        const int idx[3] = {i, j, k};
-        const int nn[3] = {g.nx, g.ny, g.nz};
-        double dr = 0.0;
-        for (int fc = 0; fc < 6; ++fc) {
-            if (op.alpha[fc] == 0.0) continue;
-            int an = fc / 2;
-            if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
-            int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
-            dr += op.alpha[fc] * cnt1(idx[aa], nn[aa], 0) * g.h[aa] / 3.0 * cnt1(idx[ab], nn[ab], 0) * g.h[ab] / 3.0;
-        }
-        d += (float)dr;
-    }
-    dinv32[g.off(i, j, k)] = on_dirichlet(g, op, i, j, k) ? 0.f : __frcp_rn(d);
+    dinv32[g.off(i, j, k)] = jacobi32_at(g, op, beta32, i, j, k);
 }
 
 // x = g_D on Dirichlet nodes, 0 on free nodes (gD == nullptr: zero everywhere).

@@ -163,6 +163,29 @@ __device__ __forceinline__ VT q1_apply(VF V, VT b000, VT b100, VT b010, VT b110,
     return Av;
 }
 
+// f_h at the free node (i, j, k) at offset o: b minus A x, where x holds g_D on the Dirichlet
+// nodes and 0 elsewhere, so only nodes next to a Dirichlet face see the lift. Operands come
+// straight from global memory (the lift touches one layer of nodes per Dirichlet face).
+template <bool ROBIN, bool CUBE>
+__device__ __forceinline__ double fh_at(const Grid& g, const Op& op, const Weights<double>& wts,
+                                        const double* __restrict__ beta, const double* __restrict__ x,
+                                        const double* __restrict__ b, int64_t o, int i, int j, int k)
+{
+    double f = b[o];
+    const bool near = (op.bc[0] == 0 && i <= 1) || (op.bc[1] == 0 && i >= g.nx - 1) ||
+                      (op.bc[2] == 0 && j <= 1) || (op.bc[3] == 0 && j >= g.ny - 1) ||
+                      (op.bc[4] == 0 && k <= 1) || (op.bc[5] == 0 && k >= g.nz - 1);
+    if (near) {
+        auto V = [&](int ddx, int ddy, int ddz) -> double {
+            return x[o + (int64_t)ddz * g.plane + (int64_t)ddy * g.pitch + ddx];
+        };
+        auto be = [&](int ex, int ey, int ez) { return beta[g.off(i - 1 + ex, j - 1 + ey, k - 1 + ez)]; };
+        f -= q1_apply<true, ROBIN, CUBE, double>(V, be(0, 0, 0), be(1, 0, 0), be(0, 1, 0), be(1, 1, 0), be(0, 0, 1),
+                                                 be(1, 0, 1), be(0, 1, 1), be(1, 1, 1), i, j, k, g, op, wts);
+    }
+    return f;
+}
+
 __device__ __forceinline__ bool op_has_robin(const Op& op)
 {
     return (op.alpha[0] != 0.0) | (op.alpha[1] != 0.0) | (op.alpha[2] != 0.0) | (op.alpha[3] != 0.0) |

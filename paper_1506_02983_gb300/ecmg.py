@@ -68,6 +68,9 @@ _SIGS = {
     "ecmg_kernel_launches": (_I32, [C.POINTER(C.c_uint64)]),
     "ecmg_error_norms_noalloc": (_I32, [_P, _P, C.c_int64, _P, C.POINTER(_D), C.POINTER(_D)]),
     "ecmg_time_kernel": (_I32, [_H, _I32, _I32, _I32, C.POINTER(_D), C.POINTER(_D)]),
+    "ecmg_create_batched": (_I32, [C.POINTER(ecmg_problem), _I32, C.POINTER(ecmg_options), _P, C.POINTER(_H)]),
+    "ecmg_solve_batched": (_I32, [_H, C.POINTER(C.c_void_p), C.POINTER(ecmg_stats)]),
+    "ecmg_get_level_batched": (_I32, [_H, _I32, _I32, _I32, _P]),
     "ecmg_set_tiles": (_I32, [_H, _I32, _I32, _I32]),
     "ecmg_get_tiles": (_I32, [_H, _I32, C.POINTER(_I32), C.POINTER(_I32)]),
     "ecmg_autotune": (_I32, [_H, _I32]),
@@ -233,6 +236,82 @@ class Solver:
             pass
 
 
+class BatchSolver:
+    """Many independent problems solved together (ecmg_create_batched): one kernel launch per
+    step of Alg. 4 over all problems, one CUDA graph per solve, MIXED precision.
+
+    problems: list of dicts with n0, levels, lo, hi, face_bc, alpha and the device tensors
+    beta, f and optionally gD, gR (as for Solver), plus f_mode. The tensors must outlive the
+    solver."""
+
+    def __init__(self, problems, **options):
+        n = len(problems)
+        arr = (ecmg_problem * n)()
+        self._keep = []
+        self.problems = problems
+        for i, q in enumerate(problems):
+            p = arr[i]
+            p.n0[:] = [int(v) for v in q["n0"]]
+            p.levels = int(q["levels"])
+            p.lo[:] = [float(v) for v in q["lo"]]
+            p.hi[:] = [float(v) for v in q["hi"]]
+            p.face_bc[:] = [int(v) for v in q["face_bc"]]
+            p.robin_alpha[:] = [float(v) for v in q["alpha"]]
+            ts = (q["beta"], q["f"], q.get("gD"), q.get("gR"))
+            for t in ts:
+                if t is not None and (not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64"):
+                    raise ValueError("inputs must be contiguous float64 CUDA tensors")
+            self._keep.append(ts)
+            p.beta, p.f, p.g_D, p.g_R = (None if t is None else t.data_ptr() for t in ts)
+            p.f_mode = int(q.get("f_mode", ECMG_F_NODAL))
+        options.setdefault("precision", ECMG_MIXED)
+        self.options = default_options(**options)
+        self.n = n
+        self._arr = arr
+        h = _H()
+        check(ecmg_create_batched(arr, n, C.byref(self.options), _stream(), C.byref(h)), "ecmg_create_batched")
+        self.handle = h
+
+    def finest_shape(self, i):
+        q = self.problems[i]
+        n = [int(v) << (int(q["levels"]) - 1) for v in q["n0"]]
+        return (n[2] + 1, n[1] + 1, n[0] + 1)
+
+    def solve(self, u_outs=None, raise_on_error=True):
+        """Solve all problems; u_outs: None or a list of finest-level output tensors (or None).
+        Returns (list of per-problem stats dicts, status)."""
+        st = (ecmg_stats * self.n)()
+        ptrs = None
+        if u_outs is not None:
+            ptrs = (C.c_void_p * self.n)(*[None if u is None else u.data_ptr() for u in u_outs])
+        s = ecmg_solve_batched(self.handle, ptrs, st)
+        if raise_on_error:
+            check(s, "ecmg_solve_batched")
+        return [stats_dict(st[i]) for i in range(self.n)], s
+
+    def get(self, problem, which, level=-1):
+        import torch
+        q = self.problems[problem]
+        L = int(q["levels"])
+        l = L - 1 if level < 0 else level
+        n = [int(v) << l for v in q["n0"]]
+        out = torch.empty((n[2] + 1, n[1] + 1, n[0] + 1), dtype=torch.float64, device="cuda")
+        check(ecmg_get_level_batched(self.handle, int(problem), int(level), int(which), _ptr(out)),
+              "ecmg_get_level_batched")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ecmg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kernel_launches() -> int:
     v = C.c_uint64()
     check(ecmg_kernel_launches(C.byref(v)), "ecmg_kernel_launches")
@@ -251,6 +330,7 @@ def solver_from_problem(prob: dict, device="cuda", **options):
     import torch
     t = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64).contiguous().to(device)
     beta, f, gD, gR = t(prob["beta"]), t(prob["f"]), t(prob.get("gD")), t(prob.get("gR"))
+    options.setdefault("rtol", prob.get("rtol", 1e-9))
     s = Solver(prob["n0"], prob["levels"], prob["lo"], prob["hi"], prob["face_bc"], prob["alpha"],
-               beta, f, gD, gR, f_mode=prob.get("f_mode", 0), rtol=prob.get("rtol", 1e-9), **options)
+               beta, f, gD, gR, f_mode=prob.get("f_mode", 0), **options)
     return s

@@ -175,3 +175,34 @@ def random_problem(seed, n0=(2, 3, 2), levels=3, box=(1.0, 1.5, 0.75), face_bc=N
 def random_vector(seed, shape):
     """Seeded uniform [-1, 1] nodal vector (for operator parity checks)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, shape)
+
+
+def coarsest_split(N, min_coarse=4):
+    """Coarsest grid and level count for a finest grid of N = (Nx, Ny, Nz) elements: halve every
+    axis while all are even and every half stays >= min_coarse."""
+    n = [int(v) for v in N]
+    levels = 1
+    while all(v % 2 == 0 and v // 2 >= min_coarse for v in n):
+        n = [v // 2 for v in n]
+        levels += 1
+    return n, levels
+
+
+def batch_problems(count=64, seed=1506, sizes=(32, 48, 64, 96, 128), h=1.0 / 128, rtol=1e-8,
+                   ln_contrast=np.log(10.0)):
+    """Batched workload: `count` independent all-Dirichlet problems (g_D = 0) with cubic elements
+    of side h. Per problem and axis the finest element count is drawn uniformly from `sizes`
+    (box = N h); beta = exp(z) per element with z ~ N(0, 1) clipped to +-ln_contrast (a
+    contrast of at most 1e2); f ~ U[-1, 1] per finest node (nodal data, injected to coarser
+    levels). Levels from coarsest_split (at least 3 for these sizes)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        N = [int(v) for v in rng.choice(sizes, size=3)]
+        n0, levels = coarsest_split(N)
+        p = _base(n0, levels, (0.0, 0.0, 0.0), [v * h for v in N], [DIRICHLET] * 6, [0.0] * 6, rtol)
+        beta = np.exp(np.clip(rng.standard_normal((N[2], N[1], N[0])), -ln_contrast, ln_contrast))
+        f = rng.uniform(-1.0, 1.0, (N[2] + 1, N[1] + 1, N[0] + 1))
+        p.update(beta=beta, f=f, gD=None, gR=None, u_exact=None)
+        out.append(p)
+    return out

@@ -64,3 +64,25 @@ def test_host_side_validation_without_gpu(libpath):
     assert ecmg.ecmg_workspace_bytes(ctypes.byref(p), ctypes.byref(o), ctypes.byref(nbytes)) == 0
     assert nbytes.value > 0
     assert b"singular" in ecmg.ecmg_status_string(ecmg.ECMG_ERR_SINGULAR)
+
+
+def test_batched_validation_without_gpu(libpath):
+    """ecmg_create_batched rejects bad batch sizes and non-MIXED precision before any CUDA call."""
+    from paper_1506_02983_gb300 import ecmg
+    arr = (ecmg.ecmg_problem * 2)()
+    for p in arr:
+        p.n0[:] = [2, 2, 2]
+        p.levels = 3
+        p.lo[:] = [0, 0, 0]
+        p.hi[:] = [1, 1, 1]
+        p.beta = 16
+        p.f = 16
+    o = ecmg.default_options(precision=ecmg.ECMG_MIXED)
+    h = ctypes.c_void_p()
+    assert ecmg.ecmg_create_batched(arr, 0, ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+    assert ecmg.ecmg_create_batched(arr, 129, ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+    o64 = ecmg.default_options(precision=ecmg.ECMG_FP64)
+    assert ecmg.ecmg_create_batched(arr, 2, ctypes.byref(o64), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+    arr[1].levels = 2
+    assert ecmg.ecmg_create_batched(arr, 2, ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+    assert ecmg.ecmg_solve_batched(None, None, None) == ecmg.ECMG_ERR_INVALID_ARG
