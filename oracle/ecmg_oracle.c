@@ -248,6 +248,46 @@ void or_load_nodal(const int32_t n[3], const double h[3], const double* f,
     }
 }
 
+/* (A x) at the single node (i, j, k), straight from the element matrices: beta_e K_e for every
+ * element containing the node, plus alpha_F M_F for every quad of a Robin face containing it
+ * (the full matrix of Sec. 2, no Dirichlet elimination; the row or_assemble_csr builds). */
+double or_apply_at(const int32_t n[3], const double h[3], const double* beta, const int32_t face_bc[6],
+                   const double alpha[6], const double* x, int64_t i, int64_t j, int64_t k)
+{
+    double K[64];
+    or_element_matrix(h[0], h[1], h[2], K);
+    double y = 0.0;
+    for (int r = 0; r < 8; ++r) {
+        int a = r & 1, b = (r >> 1) & 1, c = (r >> 2) & 1;
+        int64_t ex = i - a, ey = j - b, ez = k - c;  /* element with this node at local corner r */
+        if (ex < 0 || ey < 0 || ez < 0 || ex >= n[0] || ey >= n[1] || ez >= n[2]) continue;
+        double be = beta[elem_id(n, ex, ey, ez)];
+        for (int s = 0; s < 8; ++s) {
+            int a2 = s & 1, b2 = (s >> 1) & 1, c2 = (s >> 2) & 1;
+            y += be * K[r * 8 + s] * x[node_id(n, ex + a2, ey + b2, ez + c2)];
+        }
+    }
+    const int64_t F[3] = {i, j, k};
+    for (int f = 0; f < 6; ++f) {
+        if (face_bc[f] != OR_ROBIN || alpha[f] == 0.0) continue;
+        int aa, ab, an;
+        face_axes(f, &aa, &ab, &an);
+        if (F[an] != ((f % 2 == 0) ? 0 : n[an])) continue;
+        double M[16];
+        or_face_mass(h[aa], h[ab], M);
+        for (int r = 0; r < 4; ++r) {
+            int64_t qa = F[aa] - (r & 1), qb = F[ab] - (r >> 1);  /* quad with this node at corner r */
+            if (qa < 0 || qb < 0 || qa >= n[aa] || qb >= n[ab]) continue;
+            for (int s = 0; s < 4; ++s) {
+                int64_t c2[3];
+                c2[an] = F[an]; c2[aa] = qa + (s & 1); c2[ab] = qb + (s >> 1);
+                y += alpha[f] * M[r * 4 + s] * x[node_id(n, c2[0], c2[1], c2[2])];
+            }
+        }
+    }
+    return y;
+}
+
 void or_csr_matvec(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
                    const double* x, double* y)
 {
@@ -502,6 +542,38 @@ void or_serendipity(double xi, double eta, double zeta, double N[20])
  * n: element counts of the target level l (multiples of 4 per axis).
  * U1: FE solution on level l-1 (n/2 elements), U0: on level l-2 (n/4 elements).
  * W: level-l initial guess, all nodes (boundary reset is the caller's job). */
+/* The 20 interpolation values of the level-(l-2) element (ex, ey, ez): 8 corners by eq.
+ * (jiedian), W = (5 U^1 - U^0)/4, and 12 edge midpoints by eq. (zhongdian) along the edge,
+ * W = U^1_mid + (U^1_A - U^0_A + U^1_B - U^0_B)/8. */
+static void ser_values(const int32_t n1[3], const int32_t n0[3], const double* U1, const double* U0,
+                       int64_t ex, int64_t ey, int64_t ez, double Wi[20])
+{
+    for (int m = 0; m < 8; ++m) {
+        int a = SER_NODES[m][0], b = SER_NODES[m][1], c = SER_NODES[m][2];
+        double u1 = U1[node_id(n1, 2 * ex + a / 2, 2 * ey + b / 2, 2 * ez + c / 2)];
+        double u0 = U0[node_id(n0, ex + a / 4, ey + b / 4, ez + c / 4)];
+        Wi[m] = (5.0 * u1 - u0) / 4.0;
+    }
+    for (int m = 8; m < 20; ++m) {
+        int a = SER_NODES[m][0], b = SER_NODES[m][1], c = SER_NODES[m][2];
+        int dir = (m < 12) ? 0 : (m < 16) ? 1 : 2;
+        int A[3] = {a, b, c}, B[3] = {a, b, c};
+        A[dir] = 0; B[dir] = 4;
+        double umid = U1[node_id(n1, 2 * ex + a / 2, 2 * ey + b / 2, 2 * ez + c / 2)];
+        double u1A = U1[node_id(n1, 2 * ex + A[0] / 2, 2 * ey + A[1] / 2, 2 * ez + A[2] / 2)];
+        double u0A = U0[node_id(n0, ex + A[0] / 4, ey + A[1] / 4, ez + A[2] / 4)];
+        double u1B = U1[node_id(n1, 2 * ex + B[0] / 2, 2 * ey + B[1] / 2, 2 * ez + B[2] / 2)];
+        double u0B = U0[node_id(n0, ex + B[0] / 4, ey + B[1] / 4, ez + B[2] / 4)];
+        Wi[m] = umid + (u1A - u0A + u1B - u0B) / 8.0;
+    }
+}
+
+/* EXP_finite (Alg. 4 line 6, Sec. 4.2.2 and 4.3).
+ * n: element counts of the target level l (multiples of 4 per axis).
+ * U1: FE solution on level l-1 (n/2 elements), U0: on level l-2 (n/4 elements).
+ * W: level-l initial guess, all nodes (boundary reset is the caller's job). A node on the
+ * face between two coarse elements is written by both (the values agree); the element with
+ * the larger index writes last. */
 void or_exp_finite(const int32_t n[3], const double* U1, const double* U0, double* W)
 {
     int32_t n1[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
@@ -510,27 +582,7 @@ void or_exp_finite(const int32_t n[3], const double* U1, const double* U0, doubl
         for (int64_t ey = 0; ey < n0[1]; ++ey)
             for (int64_t ex = 0; ex < n0[0]; ++ex) {
                 double Wi[20];
-                /* 8 corners: eq. (jiedian), W = (5 U^1 - U^0)/4 */
-                for (int m = 0; m < 8; ++m) {
-                    int a = SER_NODES[m][0], b = SER_NODES[m][1], c = SER_NODES[m][2];
-                    double u1 = U1[node_id(n1, 2 * ex + a / 2, 2 * ey + b / 2, 2 * ez + c / 2)];
-                    double u0 = U0[node_id(n0, ex + a / 4, ey + b / 4, ez + c / 4)];
-                    Wi[m] = (5.0 * u1 - u0) / 4.0;
-                }
-                /* 12 edge midpoints: eq. (zhongdian) along the edge,
-                 * W = U^1_mid + (U^1_A - U^0_A + U^1_B - U^0_B)/8 */
-                for (int m = 8; m < 20; ++m) {
-                    int a = SER_NODES[m][0], b = SER_NODES[m][1], c = SER_NODES[m][2];
-                    int dir = (m < 12) ? 0 : (m < 16) ? 1 : 2;
-                    int A[3] = {a, b, c}, B[3] = {a, b, c};
-                    A[dir] = 0; B[dir] = 4;
-                    double umid = U1[node_id(n1, 2 * ex + a / 2, 2 * ey + b / 2, 2 * ez + c / 2)];
-                    double u1A = U1[node_id(n1, 2 * ex + A[0] / 2, 2 * ey + A[1] / 2, 2 * ez + A[2] / 2)];
-                    double u0A = U0[node_id(n0, ex + A[0] / 4, ey + A[1] / 4, ez + A[2] / 4)];
-                    double u1B = U1[node_id(n1, 2 * ex + B[0] / 2, 2 * ey + B[1] / 2, 2 * ez + B[2] / 2)];
-                    double u0B = U0[node_id(n0, ex + B[0] / 4, ey + B[1] / 4, ez + B[2] / 4)];
-                    Wi[m] = umid + (u1A - u0A + u1B - u0B) / 8.0;
-                }
+                ser_values(n1, n0, U1, U0, ex, ey, ez, Wi);
                 /* all 125 nodes of the patch by eq. (inter) */
                 for (int c = 0; c <= 4; ++c)
                     for (int b = 0; b <= 4; ++b)
@@ -542,6 +594,26 @@ void or_exp_finite(const int32_t n[3], const double* U1, const double* U0, doubl
                             W[node_id(n, 4 * ex + a, 4 * ey + b, 4 * ez + c)] = s;
                         }
             }
+}
+
+/* EXP_finite at the single level-l node (I, J, K): the value or_exp_finite leaves there. */
+double or_exp_finite_at(const int32_t n[3], const double* U1, const double* U0, int64_t I, int64_t J, int64_t K)
+{
+    int32_t n1[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
+    int32_t n0[3] = {n[0] / 4, n[1] / 4, n[2] / 4};
+    int64_t e[3], F[3] = {I, J, K};
+    int loc[3];
+    for (int a = 0; a < 3; ++a) {
+        e[a] = F[a] / 4;
+        if (e[a] > n0[a] - 1) e[a] = n0[a] - 1;
+        loc[a] = (int)(F[a] - 4 * e[a]);
+    }
+    double Wi[20], N[20];
+    ser_values(n1, n0, U1, U0, e[0], e[1], e[2], Wi);
+    or_serendipity((loc[0] - 2) / 2.0, (loc[1] - 2) / 2.0, (loc[2] - 2) / 2.0, N);
+    double s = 0.0;
+    for (int m = 0; m < 20; ++m) s += N[m] * Wi[m];
+    return s;
 }
 
 /* Variant of EXP_finite from the Remark after the W_35 example (Sec. 4.3): the 6 face
@@ -612,6 +684,44 @@ void or_exp_finite27(const int32_t n[3], const double* U1, const double* U0, dou
             }
 }
 
+/* EXP_true at the level-l node (I, J, K). */
+double or_exp_true_at(const int32_t n[3], const double* U1, const double* U0, int64_t I, int64_t J, int64_t K)
+{
+    int32_t nc[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
+    int64_t F[3] = {I, J, K};
+    int odd[3], nodd = 0;
+    for (int a = 0; a < 3; ++a) { odd[a] = (int)(F[a] & 1); nodd += odd[a]; }
+    double u1 = U1[node_id(n, I, J, K)];
+    if (nodd == 0) {
+        double u0 = U0[node_id(nc, I / 2, J / 2, K / 2)];
+        return (4.0 * u1 - u0) / 3.0;
+    }
+    /* The coarse nodes around (I,J,K) are F_a/2 + {0,1} on odd axes, F_a/2 on even axes. A
+     * diagonal through (I,J,K) pairs each such coarse node with its mirror image; eq.
+     * (chenlin) on that diagonal is u1 + (d(A) + d(B))/6 with d = U^1 - U^0 at coarse nodes.
+     * Average over the 2^(nodd-1) diagonals. */
+    double acc = 0.0;
+    int ndiag = 0;
+    for (int s = 0; s < 8; ++s) {
+        /* corner choice s on the odd axes; skip even-axis bits and mirrored pairs */
+        int ok = 1;
+        for (int a = 0; a < 3; ++a) if (!odd[a] && ((s >> a) & 1)) ok = 0;
+        if (!ok) continue;
+        int first_odd = odd[0] ? 0 : (odd[1] ? 1 : 2);
+        if ((s >> first_odd) & 1) continue; /* each diagonal once */
+        int64_t A[3], B[3];
+        for (int a = 0; a < 3; ++a) {
+            if (!odd[a]) { A[a] = B[a] = F[a] / 2; }
+            else { int bit = (s >> a) & 1; A[a] = F[a] / 2 + bit; B[a] = F[a] / 2 + 1 - bit; }
+        }
+        double dA = U1[node_id(n, 2 * A[0], 2 * A[1], 2 * A[2])] - U0[node_id(nc, A[0], A[1], A[2])];
+        double dB = U1[node_id(n, 2 * B[0], 2 * B[1], 2 * B[2])] - U0[node_id(nc, B[0], B[1], B[2])];
+        acc += u1 + (dA + dB) / 6.0;
+        ++ndiag;
+    }
+    return acc / ndiag;
+}
+
 /* EXP_true (Alg. 4 line 10, Sec. 4.2.1 and the last paragraph of Sec. 4.3).
  * n: element counts of level l (even). U1: level-l solution, U0: level-(l-1) solution.
  * Coarse nodes by eq. (t1); nodes halfway between two coarse nodes by eq. (chenlin); face
@@ -619,44 +729,10 @@ void or_exp_finite27(const int32_t n[3], const double* U1, const double* U0, dou
  * diagonals. */
 void or_exp_true(const int32_t n[3], const double* U1, const double* U0, double* Ut)
 {
-    int32_t nc[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
     for (int64_t K = 0; K <= n[2]; ++K)
         for (int64_t J = 0; J <= n[1]; ++J)
-            for (int64_t I = 0; I <= n[0]; ++I) {
-                int64_t F[3] = {I, J, K};
-                int odd[3], nodd = 0;
-                for (int a = 0; a < 3; ++a) { odd[a] = (int)(F[a] & 1); nodd += odd[a]; }
-                double u1 = U1[node_id(n, I, J, K)];
-                if (nodd == 0) {
-                    double u0 = U0[node_id(nc, I / 2, J / 2, K / 2)];
-                    Ut[node_id(n, I, J, K)] = (4.0 * u1 - u0) / 3.0;
-                    continue;
-                }
-                /* The coarse nodes around (I,J,K) are F_a/2 + {0,1} on odd axes, F_a/2 on even
-                 * axes. A diagonal through (I,J,K) pairs each such coarse node with its mirror
-                 * image; eq. (chenlin) on that diagonal is u1 + (d(A) + d(B))/6 with
-                 * d = U^1 - U^0 at coarse nodes. Average over the 2^(nodd-1) diagonals. */
-                double acc = 0.0;
-                int ndiag = 0;
-                for (int s = 0; s < 8; ++s) {
-                    /* corner choice s on the odd axes; skip even-axis bits and mirrored pairs */
-                    int ok = 1;
-                    for (int a = 0; a < 3; ++a) if (!odd[a] && ((s >> a) & 1)) ok = 0;
-                    if (!ok) continue;
-                    int first_odd = odd[0] ? 0 : (odd[1] ? 1 : 2);
-                    if ((s >> first_odd) & 1) continue; /* each diagonal once */
-                    int64_t A[3], B[3];
-                    for (int a = 0; a < 3; ++a) {
-                        if (!odd[a]) { A[a] = B[a] = F[a] / 2; }
-                        else { int bit = (s >> a) & 1; A[a] = F[a] / 2 + bit; B[a] = F[a] / 2 + 1 - bit; }
-                    }
-                    double dA = U1[node_id(n, 2 * A[0], 2 * A[1], 2 * A[2])] - U0[node_id(nc, A[0], A[1], A[2])];
-                    double dB = U1[node_id(n, 2 * B[0], 2 * B[1], 2 * B[2])] - U0[node_id(nc, B[0], B[1], B[2])];
-                    acc += u1 + (dA + dB) / 6.0;
-                    ++ndiag;
-                }
-                Ut[node_id(n, I, J, K)] = acc / ndiag;
-            }
+            for (int64_t I = 0; I <= n[0]; ++I)
+                Ut[node_id(n, I, J, K)] = or_exp_true_at(n, U1, U0, I, J, K);
 }
 
 /* ----------------------------------------------------------------------------------- */

@@ -59,6 +59,10 @@ void or_load_nodal(const int32_t n[3], const double h[3], const double* f,
                    const int32_t face_bc[6], const double* gR, double* b);
 void or_csr_matvec(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
                    const double* x, double* y);
+/* (A x) at one node (i, j, k) from the element and Robin face matrices (the full matrix of
+ * Sec. 2, no Dirichlet elimination): row (i, j, k) of or_assemble_csr times x. */
+double or_apply_at(const int32_t n[3], const double h[3], const double* beta, const int32_t face_bc[6],
+                   const double alpha[6], const double* x, int64_t i, int64_t j, int64_t k);
 
 /* ---- level transfer --------------------------------------------------------------- */
 void or_coarsen_beta(const int32_t nc[3], const double* beta_fine, double* beta_coarse);
@@ -78,8 +82,12 @@ int or_dsolve_banded(const int32_t n[3], int64_t N, const int64_t* rowptr,
 void or_serendipity(double xi, double eta, double zeta, double N[20]);
 void or_serendipity_nodes(int32_t abc[60]);
 void or_exp_finite(const int32_t n[3], const double* U1, const double* U0, double* W);
+/* EXP_finite at one level-l node (I, J, K): the value or_exp_finite leaves there. */
+double or_exp_finite_at(const int32_t n[3], const double* U1, const double* U0, int64_t I, int64_t J, int64_t K);
 void or_exp_finite27(const int32_t n[3], const double* U1, const double* U0, double* W);
 void or_exp_true(const int32_t n[3], const double* U1, const double* U0, double* Ut);
+/* EXP_true at one level-l node (I, J, K). */
+double or_exp_true_at(const int32_t n[3], const double* U1, const double* U0, int64_t I, int64_t J, int64_t K);
 
 /* ---- the whole method (Alg. 4) ------------------------------------------------------ */
 typedef struct {

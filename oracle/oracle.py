@@ -79,6 +79,12 @@ def lib():
         _lib.or_exp_finite.argtypes = [P, P, P, P]
         _lib.or_exp_finite27.argtypes = [P, P, P, P]
         _lib.or_exp_true.argtypes = [P, P, P, P]
+        _lib.or_apply_at.restype = D
+        _lib.or_apply_at.argtypes = [P, P, P, P, P, P, I64, I64, I64]
+        _lib.or_exp_finite_at.restype = D
+        _lib.or_exp_finite_at.argtypes = [P, P, P, I64, I64, I64]
+        _lib.or_exp_true_at.restype = D
+        _lib.or_exp_true_at.argtypes = [P, P, P, I64, I64, I64]
         _lib.or_ecmg.restype = C.c_int
         _lib.or_ecmg.argtypes = [C.POINTER(_Problem), D, I32, I32, P, P, P, C.POINTER(_Stats)]
         _lib.or_norms.argtypes = [I64, P, P, P, P]
@@ -195,6 +201,29 @@ def restrict_load(nc, b_fine):
 
 
 # ---- solvers ----------------------------------------------------------------------------
+def apply_at(n, h, beta, face_bc, alpha, x, nodes):
+    """(A x) at the given nodes [(i, j, k), ...] from the element matrices (or_apply_at)."""
+    nn, hh, bc, al = _i32(n), _f64(h), _i32(face_bc), _f64(alpha)
+    beta, x = _f64(beta), _f64(x)
+    L = lib()
+    return np.array([L.or_apply_at(_p(nn), _p(hh), _p(beta), _p(bc), _p(al), _p(x), int(i), int(j), int(k))
+                     for i, j, k in nodes])
+
+
+def exp_finite_at(n, U1, U0, nodes):
+    """EXP_finite (Serendipity) of level n at the given nodes (or_exp_finite_at)."""
+    nn, U1, U0 = _i32(n), _f64(U1), _f64(U0)
+    L = lib()
+    return np.array([L.or_exp_finite_at(_p(nn), _p(U1), _p(U0), int(i), int(j), int(k)) for i, j, k in nodes])
+
+
+def exp_true_at(n, U1, U0, nodes):
+    """EXP_true of level n at the given nodes (or_exp_true_at)."""
+    nn, U1, U0 = _i32(n), _f64(U1), _f64(U0)
+    L = lib()
+    return np.array([L.or_exp_true_at(_p(nn), _p(U1), _p(U0), int(i), int(j), int(k)) for i, j, k in nodes])
+
+
 def jcg(A: CSR, mask, b, gext, x0, rtol, max_iters=100000):
     x = _f64(x0).copy()
     it = C.c_int32()
