@@ -206,3 +206,83 @@ def batch_problems(count=64, seed=1506, sizes=(32, 48, 64, 96, 128), h=1.0 / 128
         p.update(beta=beta, f=f, gD=None, gR=None, u_exact=None)
         out.append(p)
     return out
+
+
+def _gauss3():
+    """3-point Gauss-Legendre nodes and weights on [0, 1]."""
+    g, w = np.polynomial.legendre.leggauss(3)
+    return 0.5 * (g + 1.0), 0.5 * w
+
+
+def jump_singular(levels=7, n0=(16, 8, 8), rtol=1e-8, device=None):
+    """Box (0,2)x(0,1)x(0,1), beta = 1 for x < 1 and 100 for x > 1 (element centres), singular
+    manufactured solution u = r^1.5 (r = distance to the origin corner), Robin (alpha = 1) on
+    x = 0 and Dirichlet (g_D = u) elsewhere. Default 16x8x8 -> 1024x512x512 (7 levels).
+
+    u does not carry a continuous flux across x = 1, so the load functional (f_mode 1) is
+        b_i = int f phi_i + int_{x=1} (beta- - beta+) du/dx phi_i dS + int_{x=0} g_R phi_i dS
+    with f = -beta Laplace(u) = -3.75 beta r^-1/2, (beta- - beta+) du/dx = -99 * 1.5 r^-1/2 on
+    x = 1, and g_R = beta du/dn + alpha u = r^1.5 on x = 0 (du/dx = 0 there); every integral by
+    3-point Gauss per element or face quad (no evaluation at r = 0). device: None for numpy,
+    or a torch device to evaluate the (large) arrays there."""
+    if device is None:
+        xp, mk = np, (lambda a: np.asarray(a, dtype=np.float64))
+    else:
+        import torch
+        xp, mk = torch, (lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=device))
+    bc = [ROBIN, DIRICHLET, DIRICHLET, DIRICHLET, DIRICHLET, DIRICHLET]
+    alpha = [1.0, 0.0, 0.0, 0.0, 0.0, 0.0]
+    p = _base(n0, levels, (0, 0, 0), (2, 1, 1), bc, alpha, rtol)
+    p["f_mode"] = 1
+    n = finest(n0, levels)
+    h = [(p["hi"][a] - p["lo"][a]) / n[a] for a in range(3)]
+    g, w = _gauss3()
+    xs = mk(np.arange(n[0] + 1) * h[0])
+    ys = mk(np.arange(n[1] + 1) * h[1])
+    zs = mk(np.arange(n[2] + 1) * h[2])
+    xc = mk((np.arange(n[0]) + 0.5) * h[0])
+    beta_x = xp.where(xc < 1.0, mk(1.0), mk(100.0))                      # (nx,)
+    beta = beta_x.reshape(1, 1, n[0]).expand(n[2], n[1], n[0]).contiguous() if device is not None else \
+        np.broadcast_to(beta_x.reshape(1, 1, n[0]), (n[2], n[1], n[0])).copy()
+    X, Y = xs.reshape(1, -1), ys.reshape(-1, 1)                          # (1, nx+1), (ny+1, 1)
+    b = xp.zeros((n[2] + 1, n[1] + 1, n[0] + 1), dtype=xp.float64) if device is None else \
+        xp.zeros((n[2] + 1, n[1] + 1, n[0] + 1), dtype=xp.float64, device=device)
+    u = b.clone() if device is not None else b.copy()
+    for k in range(n[2] + 1):
+        u[k] = (X * X + Y * Y + zs[k] * zs[k]) ** 0.75
+    # Gauss points of every element along each axis: (n, 3) coordinates and hat values
+    def axis_pts(a):
+        t = mk((np.arange(n[a])[:, None] + g[None, :]) * h[a])           # (n, 3)
+        return t, mk(1.0 - g), mk(g)                                     # left / right hat at the points
+    px, lx, rx = axis_pts(0)
+    py, ly, ry = axis_pts(1)
+    pz, lz, rz = axis_pts(2)
+    wq = mk(w)
+    jac = h[0] * h[1] * h[2]
+    # volume term, one slab of elements at a time: contributions to the 8 corners
+    for k in range(n[2]):
+        # f at (ny, nx, 3z, 3y, 3x) points
+        R2 = (px.reshape(1, n[0], 1, 1, 3) ** 2 + py.reshape(n[1], 1, 1, 3, 1) ** 2
+              + pz[k].reshape(1, 1, 3, 1, 1) ** 2)
+        fv = -3.75 * beta_x.reshape(1, n[0], 1, 1, 1) * R2 ** -0.25
+        wz, wy, wx = wq.reshape(1, 1, 3, 1, 1), wq.reshape(1, 1, 1, 3, 1), wq.reshape(1, 1, 1, 1, 3)
+        fw = fv * (wz * wy * wx) * jac
+        for cz, hz in ((0, lz), (1, rz)):
+            for cy, hy in ((0, ly), (1, ry)):
+                for cx, hx in ((0, lx), (1, rx)):
+                    phi = hz.reshape(1, 1, 3, 1, 1) * hy.reshape(1, 1, 1, 3, 1) * hx.reshape(1, 1, 1, 1, 3)
+                    c = (fw * phi).sum(axis=(2, 3, 4)) if device is None else (fw * phi).sum(dim=(2, 3, 4))
+                    b[k + cz, cy:cy + n[1], cx:cx + n[0]] += c
+    # face terms: (values on the face's (nz, ny) quads at 3x3 points) -> 4 corners
+    def face_add(i_node, xval, coef, power):
+        R2 = xval * xval + py.reshape(1, n[1], 1, 3) ** 2 + pz.reshape(n[2], 1, 3, 1) ** 2
+        fv = coef * R2 ** power * (wq.reshape(1, 1, 3, 1) * wq.reshape(1, 1, 1, 3)) * (h[1] * h[2])
+        for cz, hz in ((0, lz), (1, rz)):
+            for cy, hy in ((0, ly), (1, ry)):
+                phi = hz.reshape(1, 1, 3, 1) * hy.reshape(1, 1, 1, 3)
+                c = (fv * phi).sum(axis=(2, 3)) if device is None else (fv * phi).sum(dim=(2, 3))
+                b[cz:cz + n[2], cy:cy + n[1], i_node] += c
+    face_add(n[0] // 2, 1.0, -99.0 * 1.5, -0.25)    # interface x = 1: (beta- - beta+) du/dx
+    face_add(0, 0.0, 1.0, 0.75)                     # Robin data on x = 0: g_R = r^1.5
+    p.update(beta=beta, f=b, gD=u, gR=None, u_exact=u)
+    return p

@@ -262,3 +262,19 @@ def test_autotuned_solve_matches_oracle(E, oracle_mod):
     ue = np.asarray(p["u_exact"])
     assert np.abs(U - ue).max() == pytest.approx(np.abs(lv[L - 1]["U"] - ue).max(), rel=0.01)
     s.close()
+
+
+def test_mixed_jump_problem_matches_oracle(E, oracle_mod):
+    """Coefficient jump 1 | 100 and a singular solution: MIXED solve against the oracle."""
+    p = inputs.jump_singular(levels=5, n0=(4, 2, 2), rtol=1e-10)
+    L = p["levels"]
+    lv, ost = oracle_mod.ecmg(p, p["rtol"])
+    s = E.solver_from_problem(p, precision=1)
+    st, status = s.solve()
+    assert status == 0, st
+    for l in range(2, L):
+        assert st["rel_res"][l] <= p["rtol"], (l, st["rel_res"])
+        for which, key in ((E.ECMG_VEC_U, "U"), (E.ECMG_VEC_W, "W"), (E.ECMG_VEC_UTILDE, "Ut")):
+            got = _np(s.get(which, l))
+            assert _rel(got, lv[l][key]) <= 1e-7, (l, key, _rel(got, lv[l][key]))
+    s.close()
