@@ -281,8 +281,7 @@ def main():
     def make(precision):
         return ecmg.Solver(p["n0"], L, p["lo"], p["hi"], p["face_bc"], p["alpha"], d["beta"], d["f"],
                            d["gD"], None, f_mode=ecmg.ECMG_F_LOAD, rtol=args.rtol, precision=precision,
-                           max_iters=args.max_iters, use_graph=0 if args.eager else 1,
-                           autotune=1 if precision == ecmg.ECMG_MIXED else 0, inner_rtol=args.inner_rtol)
+                           max_iters=args.max_iters, use_graph=0 if args.eager else 1, inner_rtol=args.inner_rtol)
 
     def barrier():
         torch.cuda.synchronize()
@@ -309,6 +308,10 @@ def main():
 
     mixed = make(ecmg.ECMG_MIXED)
     u_out = torch.empty_like(u_exact)
+    st_mixed, status = mixed.solve(u_out)
+    assert status == 0, st_mixed
+    # tile shapes timed on the set-up levels (the level flags of the set-up pick the kernels' paths)
+    mixed.autotune(3)
     for _ in range(args.warmup):
         st_mixed, status = mixed.solve(u_out)
         assert status == 0, st_mixed
@@ -382,7 +385,8 @@ def main():
     if os.path.exists(tpath):
         try:
             tj = json.load(open(tpath))
-            if tj.get("n") == nf and list(tj.get("tiles", [])) == list(mixed_tiles):
+            if (tj.get("n") == nf and list(tj.get("tiles", [])) == list(mixed_tiles)
+                    and tj.get("algorithmic_bytes_per_launch") == k1_bytes):
                 traffic = tj.get("dram_bytes_per_launch")
         except ValueError:
             pass
@@ -396,7 +400,7 @@ def main():
                    "precision": "MIXED (FP32 JCG, FP64 residual replacement)",
                    "l2": "inputs and finest vectors (>1 GB each) larger than L2", "parallelism": "replicas" if world > 1 else "single GPU",
                    "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes",
-                   "tiles": "FP32 stencil tile shapes autotuned at create (ecmg_autotune)"},
+                   "tiles": "FP32 stencil tile shapes autotuned after the first solve (ecmg_autotune)"},
         "solve_ms_mixed": ms_mixed, "solve_ms_fp64": ms_fp64, "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
         "max_err_mixed": err_mixed, "max_err_fp64": err_fp64,
         "err_ratio_mixed_over_fp64": err_mixed / err_fp64,

@@ -197,7 +197,9 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
  * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true.
  * ms_out: mean duration of one launch (host). bytes_out: the algorithmic bytes one launch
  * must move (each owned input read once, each output written once; host); for kernel 0 the
- * nodes counted are those off the Dirichlet faces, the only ones it visits. Valid after
+ * nodes counted are those off the Dirichlet faces, the only ones it visits, and on a level
+ * with one beta and every face Dirichlet kernels 0 and 1 count no beta and no D^-1 (they read
+ * none). Valid after
  * ecmg_solve; it overwrites the level's work vectors and U~ (kernel 3 uses U~ as its
  * iterate); U and W are never changed. Synchronises the stream. */
 ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,

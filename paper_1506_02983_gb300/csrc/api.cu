@@ -323,9 +323,9 @@ void record_level(Rec& R, int l)
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
         auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
-            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, pout, v.q32, v.e32, st, h->part, idx, ch,
-                            h->timers + l, R.s());
-            launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
+            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, v.uniform, v.beta32, v.dinv32, pout, v.q32, v.e32,
+                            st, h->part, idx, ch, h->timers + l, R.s());
+            launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
         };
         auto replace = [&](float* pnew) {
             launch_fold32(v.g, v.U, v.e32, pnew, st, R.s());
@@ -606,6 +606,18 @@ ecmg_status run_batched(ecmg_handle* h, double* const* u_out, ecmg_stats* stats)
 }
 
 
+// True when the level has one beta (device flag of the last set-up) and every face Dirichlet:
+// the FP32 stencil and update kernels then take their constant-coefficient paths.
+bool constant_coefficient(ecmg_handle* h, const Level& v)
+{
+    for (int f = 0; f < 6; ++f)
+        if (v.op.bc[f] != 0) return false;
+    int flag = 0;
+    ck(cudaMemcpyAsync(&flag, v.uniform, sizeof(int), cudaMemcpyDeviceToHost, h->user_stream));
+    ck(cudaStreamSynchronize(h->user_stream));
+    return flag != 0;
+}
+
 // Forget the recorded graph (it holds launch shapes that no longer apply).
 void drop_graph(ecmg_handle* h)
 {
@@ -641,8 +653,11 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
             ck(cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s));
             ck(cudaEventRecord(e0, s));
             switch (which) {
-            case 0: launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, v.pB32, v.q32, v.e32, st, h->part, 1, none, nullptr, s); break;
-            case 1: launch_update32(v.g, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
+            case 0:
+                launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32, v.e32, st,
+                                h->part, 1, none, nullptr, s);
+                break;
+            case 1: launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
             case 2: launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
             case 3: launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
             case 4: launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, none, s); break;
@@ -1125,9 +1140,17 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
     if (which >= 6 && l < 2) return fail(ECMG_ERR_INVALID_ARG, "EXP kernels need level >= 2");
     const double N = (double)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1);
     const double E = (double)v.g.nx * v.g.ny * v.g.nz;
-    // K1 visits only the nodes off the Dirichlet faces (p = q = 0 there stay untouched)
+    // K1 visits only the nodes off the Dirichlet faces (p = q = 0 there stay untouched). With one
+    // beta on the level and every face Dirichlet (constant coefficient), K1 and K2 read no beta
+    // and no D^-1.
     const double N1 = (double)k1_nodes(v.g, v.op);
-    const double bytes[8] = {28 * N1 + 4 * E, 16 * N, 24 * N + 8 * E, 56 * N + 8 * E,
+    bool cc = false;
+    try {
+        cc = constant_coefficient(h, v);
+    } catch (CudaFail& f) {
+        return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+    }
+    const double bytes[8] = {(cc ? 24 * N1 : 28 * N1 + 4 * E), (cc ? 12 * N : 16 * N), 24 * N + 8 * E, 56 * N + 8 * E,
                              32 * N,         32 * N + 8 * E, 16 * N + 8 * (N / 8 + N / 64), 17 * N};
     *bytes_out = bytes[which];
     try {

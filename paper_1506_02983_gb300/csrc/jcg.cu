@@ -564,10 +564,13 @@ __device__ __forceinline__ float& vget(float4& v, int c) { return c == 0 ? v.x :
 __device__ __forceinline__ double& vget(double2& v, int c) { return c == 0 ? v.x : v.y; }
 
 // Flat over the padded vector, 16-byte vectors (the layout keeps total a multiple of 8).
+// cdiag: when not null and *uniform is set (one beta, every face Dirichlet), D^-1 is the constant
+// *cdiag on every free node (r = 0 on the others), so r.z = cdiag * r.r and D^-1 is not streamed.
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r, const T* __restrict__ q,
                                                     const T* __restrict__ dinv, SolveState* st,
-                                                    double* partials, CondHandles ch)
+                                                    double* partials, CondHandles ch, const int* uniform,
+                                                    const T* cdiag)
 {
     COUNT_LAUNCH();
     if (st->done) {
@@ -586,18 +589,34 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
     const V* __restrict__ qv4 = reinterpret_cast<const V*>(q);
     const V* __restrict__ dv4 = reinterpret_cast<const V*>(dinv);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += stride) {
-        V rr4 = rv4[t];
-        const V q4 = qv4[t], d4 = dv4[t];
+    if (cdiag && *uniform) {
+        const T cd = *cdiag;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += stride) {
+            V rr4 = rv4[t];
+            const V q4 = qv4[t];
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-            const T rv = vget(rr4, c) - a * vget(const_cast<V&>(q4), c);
-            vget(rr4, c) = rv;
-            const T zv = vget(const_cast<V&>(d4), c) * rv;
-            rz.add_prod(rv, zv);
-            rr.add_prod(rv, rv);
+            for (int c = 0; c < W; ++c) {
+                const T rv = vget(rr4, c) - a * vget(const_cast<V&>(q4), c);
+                vget(rr4, c) = rv;
+                rz.add_prod(rv, cd * rv);
+                rr.add_prod(rv, rv);
+            }
+            rv4[t] = rr4;
         }
-        rv4[t] = rr4;
+    } else {
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += stride) {
+            V rr4 = rv4[t];
+            const V q4 = qv4[t], d4 = dv4[t];
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                const T rv = vget(rr4, c) - a * vget(const_cast<V&>(q4), c);
+                vget(rr4, c) = rv;
+                const T zv = vget(const_cast<V&>(d4), c) * rv;
+                rz.add_prod(rv, zv);
+                rr.add_prod(rv, rv);
+            }
+            rv4[t] = rr4;
+        }
     }
     double v[2] = {rz.value(), rr.value()};
     if (grid_sum<2>(v, partials, &st->arrive)) {
@@ -751,12 +770,18 @@ void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv, SolveState* st,
                      Partials pr, CondHandles ch, cudaStream_t s)
 {
-    k_update<double, false><<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, r, q, dinv, st, pr.buf, ch);
+    k_update<double, false><<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, r, q, dinv, st, pr.buf, ch,
+                                                                        nullptr, nullptr);
 }
-void launch_update32(const Grid& g, float* r, const float* q, const float* dinv, SolveState* st,
-                     Partials pr, CondHandles ch, cudaStream_t s)
+void launch_update32(const Grid& g, const Op& op, const int* uniform, float* r, const float* q, const float* dinv,
+                     SolveState* st, Partials pr, CondHandles ch, cudaStream_t s)
 {
-    k_update<float, true><<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, r, q, dinv, st, pr.buf, ch);
+    bool diri = uniform != nullptr;
+    for (int f = 0; f < 6; ++f) diri &= op.bc[f] == 0;
+    // an interior node: free whenever every face is Dirichlet (levels >= 2 have >= 4 elements per axis)
+    const float* cdiag = diri && g.nx >= 2 && g.ny >= 2 && g.nz >= 2 ? dinv + g.off(1, 1, 1) : nullptr;
+    k_update<float, true><<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, r, q, dinv, st, pr.buf, ch, uniform,
+                                                                      cdiag);
 }
 void launch_final64(const Grid& g, double* x, const double* pA, const double* pB, SolveState* st,
                     cudaStream_t s)

@@ -49,7 +49,9 @@ void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x
 // r -= alpha q; z = dinv r; r.z and r.r; last block: convergence / next beta.
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv,
                      SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);
-void launch_update32(const Grid& g, float* r, const float* q, const float* dinv,
+// uniform: the level's device flag; with every face Dirichlet and the flag set, D^-1 is one
+// constant on the free nodes and is not streamed.
+void launch_update32(const Grid& g, const Op& op, const int* uniform, float* r, const float* q, const float* dinv,
                      SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);
 
 // x += alpha_prev p_latest (FP64 JCG exit).

@@ -149,18 +149,24 @@ __device__ __forceinline__ void block_sum(double (&v)[NP], double* sh)
     __syncthreads();
 }
 
-template <bool ROBIN, bool CUBE, int RY>
-__global__ void __launch_bounds__(NT, RY == 1 ? (ROBIN ? 3 : 4) : 2)
-k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
-           const __grid_constant__ CUtensorMap m_dinv, const __grid_constant__ CUtensorMap m_beta,
-           const Grid g, const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q,
-           float* __restrict__ e, SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
-           KTimer* tm)
+// CC: constant coefficient -- one beta on the whole level and every face Dirichlet, so every
+// node the kernel visits is interior with the same diagonal: beta and D^-1 are not streamed
+// (bu and cdinv hold their values; the results are the same bits as with the arrays).
+template <bool ROBIN, bool CUBE, int RY, bool CC>
+__device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMap& m_pold, const CUtensorMap& m_dinv,
+                                        const CUtensorMap& m_beta, const Grid& g, const Op& op, const Range& rg,
+                                        float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e,
+                                        SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
+                                        KTimer* tm, float cdinv, float bu)
 {
     using S = Shape<RY>;
-    COUNT_LAUNCH();
     extern __shared__ __align__(128) unsigned char k1_smem[];
-    Stage<RY>* stage = reinterpret_cast<Stage<RY>*>(k1_smem + ((128u - (smem_u32(k1_smem) & 127u)) & 127u));
+    // the ring of staged boxes: NS stages of NA arrays (r, p_old[, D^-1, beta]). The constant-
+    // coefficient path stages two arrays; holding twice as many planes in flight there measured
+    // slower (the kernel is issue-bound), so both paths keep NSTAGE stages.
+    constexpr int NA = CC ? 2 : 4, NS = NSTAGE;
+    float* ring = reinterpret_cast<float*>(k1_smem + ((128u - (smem_u32(k1_smem) & 127u)) & 127u));
+    auto box = [&](int t, int a) -> float* { return ring + ((t % NS) * NA + a) * S::BOXF_PAD; };
     __shared__ float P[2][S::PY][S::PX];
     __shared__ __align__(8) uint64_t bar[NSTAGE];
     __shared__ double red[32];
@@ -184,7 +190,7 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     const int sh = i0 + XL - 1 - bx;
 
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         bad = 0;
     }
@@ -193,18 +199,19 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     // Stage t holds node plane P0+t (memory plane P0+t+1) and element slab P0+t-1 (memory
     // plane P0+t); row 0 of a box is node row j0-1 (memory row j0).
     auto issue = [&](int t) {
-        Stage<RY>& St = stage[t % NSTAGE];
-        uint64_t* b = &bar[t % NSTAGE];
+        uint64_t* b = &bar[t % NS];
         const int kk = P0 + t;
-        mbar_expect_tx(b, S::STAGE_BYTES);
-        tma_load_3d(St.r, &m_r, bx, j0, kk + 1, b);
-        tma_load_3d(St.pold, &m_pold, bx, j0, kk + 1, b);
-        tma_load_3d(St.dinv, &m_dinv, bx, j0, kk + 1, b);
-        tma_load_3d(St.beta, &m_beta, bx, j0, kk, b);
+        mbar_expect_tx(b, CC ? 2u * S::BOXF * (uint32_t)sizeof(float) : S::STAGE_BYTES);
+        tma_load_3d(box(t, 0), &m_r, bx, j0, kk + 1, b);
+        tma_load_3d(box(t, 1), &m_pold, bx, j0, kk + 1, b);
+        if (!CC) {
+            tma_load_3d(box(t, 2), &m_dinv, bx, j0, kk + 1, b);
+            tma_load_3d(box(t, 3), &m_beta, bx, j0, kk, b);
+        }
     };
     if (tid == 0) {
-        for (int t = 0; t < NSTAGE && t < nplanes; ++t) issue(t);
-        issued_hi = min(NSTAGE, nplanes) - 1;
+        for (int t = 0; t < NS && t < nplanes; ++t) issue(t);
+        issued_hi = min(NS, nplanes) - 1;
     }
 
     // this thread: column i, node rows jt .. jt+RY-1, of which the first nown are in range
@@ -240,43 +247,49 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     auto step = [&](float(&wm)[RY + 2][3], float(&w0)[RY + 2][3], float(&wp)[RY + 2][3],
                     float(&bo)[RY + 1][2], float(&bn)[RY + 1][2]) {
         const int kk = P0 + t;
-        Stage<RY>& St = stage[t % NSTAGE];
+        const float* Sr = box(t, 0);
+        const float* Sp = box(t, 1);
+        const float* Sd = box(t, 2);
+        const float* Sbeta = box(t, 3);
         // prefetch e of the nodes computed at the next step (plane kk), one step ahead
         float e_next[RY];
 #pragma unroll
         for (int r = 0; r < RY; ++r)
             e_next[r] = (ap != 0.f && r < nown && t >= 1) ? e[o + g.plane + r * pitch] : 0.f;
-        if (!mbar_wait(&bar[t % NSTAGE], (uint32_t)((t / NSTAGE) & 1))) bad = 1;
+        if (!mbar_wait(&bar[t % NS], (uint32_t)((t / NS) & 1))) bad = 1;
         t_done = t;
         // form p of plane kk for the tile plus halo
         float* Pk = &P[kk & 1][0][0];
 #pragma unroll
         for (int f = 0; f < S::NFORM; ++f) {
             const int s = sidx[f];
-            if ((f + 1) * NT <= S::NCELL || s >= 0) Pk[tid + f * NT] = fmaf(St.dinv[s], St.r[s], bcg * St.pold[s]);
+            if ((f + 1) * NT <= S::NCELL || s >= 0)
+                Pk[tid + f * NT] = fmaf(CC ? cdinv : Sd[s], Sr[s], bcg * Sp[s]);
         }
         float pown_new[RY];
 #pragma unroll
-        for (int r = 0; r < RY; ++r) pown_new[r] = St.pold[(ty * RY + r + 1) * SX + tx + 1 + sh];
+        for (int r = 0; r < RY; ++r) pown_new[r] = Sp[(ty * RY + r + 1) * SX + tx + 1 + sh];
         __syncthreads();
         if (bad) {
             stop = true;
             return;
         }
-        if (tid == 0 && t >= 1 && t - 1 + NSTAGE < nplanes) {
-            issue(t - 1 + NSTAGE);
-            issued_hi = t - 1 + NSTAGE;
+        if (tid == 0 && t >= 1 && t - 1 + NS < nplanes) {
+            issue(t - 1 + NS);
+            issued_hi = t - 1 + NS;
         }
         const float(*Pp)[S::PX] = P[kk & 1];
 #pragma unroll
         for (int yy = 0; yy < RY + 2; ++yy)
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) wp[yy][dx] = Pp[ty * RY + yy][tx + dx];
-        const float* Sb = St.beta + ty * RY * SX + tx + sh;
+        if (!CC) {
+            const float* Sb = Sbeta + ty * RY * SX + tx + sh;
 #pragma unroll
-        for (int yy = 0; yy < RY + 1; ++yy)
+            for (int yy = 0; yy < RY + 1; ++yy)
 #pragma unroll
-            for (int ex = 0; ex < 2; ++ex) bn[yy][ex] = Sb[yy * SX + ex];
+                for (int ex = 0; ex < 2; ++ex) bn[yy][ex] = Sb[yy * SX + ex];
+        }
 
         if (t >= 2) {
             const int k = kk - 1;
@@ -288,9 +301,12 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
                                       : (dz > 0 ? wp[r + 1 + dy][dx + 1] : w0[r + 1 + dy][dx + 1]);
                     };
                     const float xc = w0[r + 1][1];
-                    const float Av = q1_apply<false, ROBIN, CUBE, float>(
-                        V, bo[r][0], bo[r][1], bo[r + 1][0], bo[r + 1][1], bn[r][0], bn[r][1], bn[r + 1][0],
-                        bn[r + 1][1], i, jt + r, k, g, op, wts);
+                    const float Av =
+                        CC ? q1_apply<false, ROBIN, CUBE, float>(V, bu, bu, bu, bu, bu, bu, bu, bu, i, jt + r, k, g, op,
+                                                                 wts)
+                           : q1_apply<false, ROBIN, CUBE, float>(V, bo[r][0], bo[r][1], bo[r + 1][0], bo[r + 1][1],
+                                                                 bn[r][0], bn[r][1], bn[r + 1][0], bn[r + 1][1], i,
+                                                                 jt + r, k, g, op, wts);
                     const int64_t orr = o + r * pitch;
                     pnew[orr] = xc;
                     q[orr] = Av;
@@ -329,7 +345,7 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
             st->status = 5;
             st->done = 1;
             for (int t = t_done; t <= issued_hi; ++t)
-                (void)mbar_wait(&bar[t % NSTAGE], (uint32_t)((t / NSTAGE) & 1));
+                (void)mbar_wait(&bar[t % NS], (uint32_t)((t / NS) & 1));
         }
         return;
     }
@@ -369,6 +385,26 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
             st->alpha = st->rho / pq;
         }
     }
+}
+
+template <bool ROBIN, bool CUBE, int RY, bool DIRI>
+__global__ void __launch_bounds__(NT, RY == 1 ? (ROBIN ? 3 : 4) : 2)
+k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
+           const __grid_constant__ CUtensorMap m_dinv, const __grid_constant__ CUtensorMap m_beta,
+           const Grid g, const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q,
+           float* __restrict__ e, SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
+           KTimer* tm, const int* __restrict__ uniform, const float* __restrict__ beta32,
+           const float* __restrict__ dinv32)
+{
+    COUNT_LAUNCH();
+    // DIRI: every face Dirichlet (host); *uniform: one beta on the level (device set-up)
+    if (DIRI && *uniform) {
+        k1_body<ROBIN, CUBE, RY, true>(m_r, m_pold, m_dinv, m_beta, g, op, rg, pnew, q, e, st, partials, pidx, ch,
+                                       kz, tm, dinv32[g.off(1, 1, 1)], beta32[g.off(0, 0, 0)]);
+        return;
+    }
+    k1_body<ROBIN, CUBE, RY, false>(m_r, m_pold, m_dinv, m_beta, g, op, rg, pnew, q, e, st, partials, pidx, ch, kz,
+                                    tm, 0.f, 0.f);
 }
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -412,10 +448,10 @@ bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool ROBIN, bool CUBE, int RY>
+template <bool ROBIN, bool CUBE, int RY, bool DIRI = false>
 cudaError_t prepare_one()
 {
-    return cudaFuncSetAttribute(k_pq32_tma<ROBIN, CUBE, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_pq32_tma<ROBIN, CUBE, RY, DIRI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)stage_smem<RY>());
 }
 
@@ -426,23 +462,30 @@ cudaError_t prepare_ry()
     if (e == cudaSuccess) e = prepare_one<false, true, RY>();
     if (e == cudaSuccess) e = prepare_one<true, false, RY>();
     if (e == cudaSuccess) e = prepare_one<true, true, RY>();
+    if (e == cudaSuccess) e = prepare_one<false, false, RY, true>();
+    if (e == cudaSuccess) e = prepare_one<false, true, RY, true>();
     return e;
 }
 
 template <int RY>
-void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, float* pnew,
-               float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm,
-               cudaStream_t s)
+void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, const int* uniform,
+               const float* beta32, const float* dinv32, float* pnew, float* q, float* e, SolveState* st, Partials pr,
+               int pidx, CondHandles ch, KTimer* tm, cudaStream_t s)
 {
     const int v = ry_index(RY);
     const Range rg = k1_range(g, op);
-    bool robin = false;
-    for (int f = 0; f < 6; ++f) robin |= op.alpha[f] != 0.0;
-    auto kern = robin ? (op.cube ? k_pq32_tma<true, true, RY> : k_pq32_tma<true, false, RY>)
-                      : (op.cube ? k_pq32_tma<false, true, RY> : k_pq32_tma<false, false, RY>);
+    bool robin = false, diri = true;
+    for (int f = 0; f < 6; ++f) {
+        robin |= op.alpha[f] != 0.0;
+        diri &= op.bc[f] == 0;
+    }
+    diri &= uniform != nullptr;
+    auto kern = robin  ? (op.cube ? k_pq32_tma<true, true, RY, false> : k_pq32_tma<true, false, RY, false>)
+                : diri ? (op.cube ? k_pq32_tma<false, true, RY, true> : k_pq32_tma<false, false, RY, true>)
+                       : (op.cube ? k_pq32_tma<false, true, RY, false> : k_pq32_tma<false, false, RY, false>);
     kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY>(), s>>>(m.r[v], pold_is_b ? m.pB[v] : m.pA[v], m.dinv[v],
                                                                   m.beta[v], g, op, rg, pnew, q, e, st, pr.buf,
-                                                                  pidx, ch, c.kz, tm);
+                                                                  pidx, ch, c.kz, tm, uniform, beta32, dinv32);
 }
 
 }  // namespace
@@ -509,11 +552,11 @@ int max_tma_blocks(const Grid& g)
 }
 
 void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op,
-                     float* pnew, float* q, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch,
-                     KTimer* tm, cudaStream_t s)
+                     const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
+                     SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s)
 {
-    if (c.ry == 1) launch_ry<1>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, tm, s);
-    else launch_ry<2>(m, pold_is_b, c, g, op, pnew, q, e, st, pr, pidx, ch, tm, s);
+    if (c.ry == 1) launch_ry<1>(m, pold_is_b, c, g, op, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
+    else launch_ry<2>(m, pold_is_b, c, g, op, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
 }
 
 unsigned long long launches_pq_tma()
