@@ -280,6 +280,9 @@ void record_level(Rec& R, int l)
     launch_state_init(st, rtol, o.inner_rtol, o.max_iters, R.s());
     dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s());
     launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s());
+    // constant coefficient: b / c for the exact integer residual, kept in the FP64 r vector,
+    // which the MIXED iteration does not use
+    if (mixed) launch_scale_load(v.g, v.op, v.b, v.r, v.beta, v.uniform, st, R.s());
     if (!direct) {
         const Level& u1 = h->lv[l - 1];
         const Level& u0 = h->lv[l - 2];
@@ -329,12 +332,13 @@ void record_level(Rec& R, int l)
         };
         auto replace = [&](float* pnew) {
             launch_fold32(v.g, v.U, v.e32, pnew, st, R.s());
-            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPLACE, none, R.s());
+            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPLACE, none, R.s(),
+                         v.r);
         };
         if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
             launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT,
-                         CondHandles{loop, 0, 1}, R.s());
+                         CondHandles{loop, 0, 1}, R.s(), v.r);
             R.open(loop, cudaGraphCondTypeWhile);
             for (int half = 0; half < 2; ++half) {
                 const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
@@ -348,7 +352,8 @@ void record_level(Rec& R, int l)
             }
             R.close();
         } else {
-            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT, none, R.s());
+            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT, none, R.s(),
+                         v.r);
             SolveState hs;
             host_state(h, l, &hs);
             int parity = 0;
@@ -647,6 +652,11 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double total = 0.0;
     try {
+        // the fixed-point scale of the level's load (constant-coefficient residual) from its last solve
+        SolveState last;
+        ck(cudaMemcpyAsync(&last, h->states + l, sizeof(last), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        tmpl.bcbits = last.bcbits;
         ck(cudaEventCreate(&e0));
         ck(cudaEventCreate(&e1));
         for (int rep = 0; rep <= reps; ++rep) {
@@ -658,7 +668,10 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
                                 h->part, 1, none, nullptr, s);
                 break;
             case 1: launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
-            case 2: launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s); break;
+            case 2:
+                launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s,
+                             v.r);
+                break;
             case 3: launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
             case 4: launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, none, s); break;
             case 5: launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, s); break;

@@ -106,6 +106,7 @@ struct SolveState {
     int stop_after_update; // MIXED: iteration cap reached, finish after the next replacement
     int p_latest;        // which of the two search-direction buffers holds the newest p
     unsigned int arrive; // block arrival counter of the last-block reductions
+    unsigned long long bcbits;  // MIXED, constant coefficient: bits of max |b / c| (fixed-point scale)
 };
 
 // Fixed-point scale of an iterate: bit pattern of max |x| (nonnegative doubles order like their

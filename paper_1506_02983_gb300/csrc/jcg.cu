@@ -17,6 +17,7 @@
 #include "stencil_core.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 namespace ecmg {
 namespace {
@@ -263,15 +264,27 @@ __device__ __forceinline__ long long s_mid(long long v, bool end)
 // c v with c = 2 (interior) or 1 (end): the centre entry of -D
 __device__ __forceinline__ long long d_mid(long long v, bool end) { return end ? v : v + v; }
 
-template <bool ROBIN, typename SRC, typename BODY>
-__device__ __forceinline__ void march_fixed(const Grid& g, const Op& op, double bu, const FixedFrame& fr, int kz,
-                                            SRC src, BODY body)
+// INT_OUT (cubic elements, no Robin face): body receives the exact integer sum I = I_x + I_y +
+// I_z instead of A x, so that A x = -(beta h / 36) 2^-s I.
+// Shared memory of march_fixed, declared once per kernel (a kernel may call the march with two
+// bodies).
+struct FixedSmem {
+    long long X[3][BY + 2][BX + 2];
+    long long LX[BY + 2][BX];
+    long long LY[BY][BX + 2];
+    long long LZ[BY + 2][BX + 2];
+    long long UZ[BY + 2][BX];
+};
+
+template <bool ROBIN, typename SRC, typename BODY, bool INT_OUT = false>
+__device__ __forceinline__ void march_fixed(FixedSmem& sm, const Grid& g, const Op& op, double bu, const FixedFrame& fr,
+                                            int kz, SRC src, BODY body)
 {
-    __shared__ long long X[3][BY + 2][BX + 2];
-    __shared__ long long LX[BY + 2][BX];
-    __shared__ long long LY[BY][BX + 2];
-    __shared__ long long LZ[BY + 2][BX + 2];
-    __shared__ long long UZ[BY + 2][BX];
+    auto& X = sm.X;
+    auto& LX = sm.LX;
+    auto& LY = sm.LY;
+    auto& LZ = sm.LZ;
+    auto& UZ = sm.UZ;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int kb = blockIdx.z * kz;
@@ -356,32 +369,36 @@ __device__ __forceinline__ void march_fixed(const Grid& g, const Op& op, double 
             const long long Ix = txm + s_mid(tx0, kend) + txp;
             const long long Iy = tym + s_mid(ty0, kend) + typ;
             const long long Iz = UZ[ty][tx] + s_mid(UZ[ty + 1][tx], jend) + UZ[ty + 2][tx];
-            double Av = cx * (double)Ix + cy * (double)Iy + cz * (double)Iz;
-            if (ROBIN && (iend || jend || kend)) {
-                const int pm = (k + 2) % 3, p0 = k % 3, pp = (k + 1) % 3;
-                // S_y S_z X on the node's column (x faces)
-                auto fx = [&](int p) { return X[p][ty][tx + 1] + s_mid(X[p][ty + 1][tx + 1], jend) + X[p][ty + 2][tx + 1]; };
-                // S_x S_z X on the node's row (y faces)
-                auto fy = [&](int p) { return X[p][ty + 1][tx] + s_mid(X[p][ty + 1][tx + 1], iend) + X[p][ty + 1][tx + 2]; };
-                // S_x on row r of the node's plane (z faces)
-                auto fz = [&](int r) { return X[p0][ty + r][tx] + s_mid(X[p0][ty + r][tx + 1], iend) + X[p0][ty + r][tx + 2]; };
-                if (iend) {
-                    const long long I = fx(pm) + s_mid(fx(p0), kend) + fx(pp);
-                    if (i == 0) Av += af[0] * (double)I;
-                    if (i == g.nx) Av += af[1] * (double)I;
+            if constexpr (INT_OUT) {
+                body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Ix + Iy + Iz);
+            } else {
+                double Av = cx * (double)Ix + cy * (double)Iy + cz * (double)Iz;
+                if (ROBIN && (iend || jend || kend)) {
+                    const int pm = (k + 2) % 3, p0 = k % 3, pp = (k + 1) % 3;
+                    // S_y S_z X on the node's column (x faces)
+                    auto fx = [&](int p) { return X[p][ty][tx + 1] + s_mid(X[p][ty + 1][tx + 1], jend) + X[p][ty + 2][tx + 1]; };
+                    // S_x S_z X on the node's row (y faces)
+                    auto fy = [&](int p) { return X[p][ty + 1][tx] + s_mid(X[p][ty + 1][tx + 1], iend) + X[p][ty + 1][tx + 2]; };
+                    // S_x on row r of the node's plane (z faces)
+                    auto fz = [&](int r) { return X[p0][ty + r][tx] + s_mid(X[p0][ty + r][tx + 1], iend) + X[p0][ty + r][tx + 2]; };
+                    if (iend) {
+                        const long long I = fx(pm) + s_mid(fx(p0), kend) + fx(pp);
+                        if (i == 0) Av += af[0] * (double)I;
+                        if (i == g.nx) Av += af[1] * (double)I;
+                    }
+                    if (jend) {
+                        const long long I = fy(pm) + s_mid(fy(p0), kend) + fy(pp);
+                        if (j == 0) Av += af[2] * (double)I;
+                        if (j == g.ny) Av += af[3] * (double)I;
+                    }
+                    if (kend) {
+                        const long long I = fz(0) + s_mid(fz(1), jend) + fz(2);
+                        if (k == 0) Av += af[4] * (double)I;
+                        if (k == g.nz) Av += af[5] * (double)I;
+                    }
                 }
-                if (jend) {
-                    const long long I = fy(pm) + s_mid(fy(p0), kend) + fy(pp);
-                    if (j == 0) Av += af[2] * (double)I;
-                    if (j == g.ny) Av += af[3] * (double)I;
-                }
-                if (kend) {
-                    const long long I = fz(0) + s_mid(fz(1), jend) + fz(2);
-                    if (k == 0) Av += af[4] * (double)I;
-                    if (k == g.nz) Av += af[5] * (double)I;
-                }
+                body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Av, 0.0);
             }
-            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Av, 0.0);
         }
         __syncthreads();  // the Robin rows above read plane k-1, which the next load replaces
         txm = tx0;
@@ -439,6 +456,34 @@ __global__ void __launch_bounds__(UPD_TPB) k_absmax(int64_t n, const double* __r
     }
 }
 
+// Constant coefficient (one beta, every face Dirichlet, cubic elements; the first set by the
+// set-up's device flag): A x = c 2^-s I with c = -beta h / 36 and I the exact integer sum of
+// march_fixed, so with B = b / c on the same fixed-point scale the residual is c 2^-s (B - I),
+// exact in 64-bit integers. bc = b / c once per level, and max |bc| for the scale.
+__global__ void __launch_bounds__(UPD_TPB) k_scale_load(int64_t n, const double* __restrict__ b,
+                                                       double* __restrict__ bc, const double* __restrict__ beta,
+                                                       double h, const int* uniform, SolveState* st)
+{
+    COUNT_LAUNCH();
+    if (!*uniform) return;
+    __shared__ unsigned long long sh[UPD_TPB / 32];
+    const double inv_c = -36.0 / (beta[0] * h);
+    unsigned long long m = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
+        const double v = b[t] * inv_c;
+        bc[t] = v;
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(v)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
+        atomicMax(&st->bcbits, m);
+    }
+}
+
 // Uniform-beta dispatch of the FP64 kernels: *uniform is set per level by the set-up.
 #define ECMG_FP64_MARCH(T, ROBIN, CUBE, FULL, SRC, BODY)                                    \
     do {                                                                                  \
@@ -476,15 +521,46 @@ __global__ void __launch_bounds__(NT) k_pq(const Grid g, const Op op, const T* _
 }
 
 // ---- residual r = b - A x --------------------------------------------------------------------
+// bc: b / c of the constant-coefficient case (k_scale_load), or null when the level can not be
+// one (a Robin face, non-cubic elements, FP64 output): then A x in FP64 or fixed point as below.
 template <typename OT, bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const double* __restrict__ beta,
                                             const int* uniform, const double* __restrict__ x,
                                             const double* __restrict__ b, const OT* __restrict__ dinv,
                                             OT* __restrict__ r, SolveState* st, double* partials, int mode,
-                                            CondHandles ch, int kz, const FixedScale* fs)
+                                            CondHandles ch, int kz, const FixedScale* fs,
+                                            const double* __restrict__ bc)
 {
     COUNT_LAUNCH();
+    __shared__ FixedSmem fsm;
     if (mode == RES_REPLACE && st->done) return;
+    if constexpr (std::is_same<OT, float>::value && CUBE && !ROBIN) {
+        if (bc && *uniform) {
+            // constant coefficient: r = c 2^-s (B - I) exactly, then rounded to FP32 once;
+            // ||r||^2 by compensated FP32 products, r.z = D^-1 r.r (one diagonal)
+            const FixedFrame fr = fixed_frame(max(fs->bits, st->bcbits));
+            const float fscale = (float)(-beta[g.off(0, 0, 0)] * g.h[0] / 36.0 * fr.inv);
+            Acc<float> rr32;
+            auto src = [&](int64_t o) -> double { return x[o]; };
+            auto body = [&](int i, int j, int k, int64_t o, long long I) {
+                float ro = 0.f;
+                if (!on_dirichlet(g, op, i, j, k)) ro = __ll2float_rn(to_fixed(bc[o], fr.s) - I) * fscale;
+                r[o] = ro;
+                rr32.add_prod(ro, ro);
+            };
+            double v[2] = {0.0, 0.0};
+            if (fr.finite) {
+                march_fixed<false, decltype(src), decltype(body), true>(fsm, g, op, beta[g.off(0, 0, 0)], fr, kz,
+                                                                        src, body);
+                v[0] = rr32.value();
+                v[1] = (double)dinv[g.off(1, 1, 1)] * v[0];
+            } else if (threadIdx.x == 0 && threadIdx.y == 0) {
+                v[0] = nan("");  // breakdown: the iterate is not finite
+            }
+            if (grid_sum<2>(v, partials, &st->arrive)) res_epilogue(st, v[0], v[1], mode, ch);
+            return;
+        }
+    }
     double rr = 0.0;
     Acc<OT> rz;  // r.z in the precision of the iteration that uses it (z = D^-1 r rounded)
     auto src = [&](int64_t o) -> double { return x[o]; };
@@ -497,7 +573,7 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
     };
     if (*uniform) {
         const FixedFrame fr = fixed_frame(fs->bits);
-        if (fr.finite) march_fixed<ROBIN>(g, op, beta[g.off(0, 0, 0)], fr, kz, src, body);
+        if (fr.finite) march_fixed<ROBIN>(fsm, g, op, beta[g.off(0, 0, 0)], fr, kz, src, body);
         else if (threadIdx.x == 0 && threadIdx.y == 0) rr = nan("");  // breakdown: the iterate is not finite
     } else {
         march<ROBIN, CUBE, double, double>(g, op, beta, kz, src, body);
@@ -541,13 +617,14 @@ __global__ void __launch_bounds__(NT) k_apply(const Grid g, const Op op, const T
                                               double* __restrict__ y, int kz, const FixedScale* fs)
 {
     COUNT_LAUNCH();
+    __shared__ FixedSmem fsm;
     auto src = [&](int64_t o) -> T { return x[o]; };
     auto body = [&](int, int, int, int64_t o, T Av, T) { y[o] = (double)Av; };
     if constexpr (sizeof(T) == 8) {
         if (*uniform) {
             const FixedFrame fr = fixed_frame(fs->bits);
             auto body64 = [&](int, int, int, int64_t o, double Av, double) { y[o] = fr.finite ? Av : nan(""); };
-            march_fixed<ROBIN>(g, op, beta[g.off(0, 0, 0)], fr, kz, src, body64);
+            march_fixed<ROBIN>(fsm, g, op, beta[g.off(0, 0, 0)], fr, kz, src, body64);
         } else {
             march<ROBIN, CUBE, T, T>(g, op, beta, kz, src, body);
         }
@@ -736,16 +813,32 @@ void launch_res64(const Grid& g, const Op& op, const double* beta, const int* un
     const int kz = stencil_kz(g);
     launch_absmax(g, x, uniform, st, (int)mode, pr, s);
     ECMG_VARIANT(k_res, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
-                                                                            st, pr.buf, (int)mode, ch, kz, pr.fs);
+                                                                            st, pr.buf, (int)mode, ch, kz, pr.fs,
+                                                                            nullptr);
+}
+bool constant_coefficient_shape(const Grid& g, const Op& op)
+{
+    bool diri = true;
+    for (int f = 0; f < 6; ++f) diri &= op.bc[f] == 0;
+    return diri && op.cube && g.nx >= 2 && g.ny >= 2 && g.nz >= 2;
+}
+void launch_scale_load(const Grid& g, const Op& op, const double* b, double* bc, const double* beta,
+                       const int* uniform, SolveState* st, cudaStream_t s)
+{
+    if (!constant_coefficient_shape(g, op)) return;
+    k_scale_load<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, b, bc, beta + g.off(0, 0, 0), g.h[0], uniform,
+                                                            st);
 }
 void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr, ResMode mode,
-                  CondHandles ch, cudaStream_t s)
+                  CondHandles ch, cudaStream_t s, const double* bc)
 {
     const int kz = stencil_kz(g);
     launch_absmax(g, x, uniform, st, (int)mode, pr, s);
+    if (!constant_coefficient_shape(g, op)) bc = nullptr;
     ECMG_VARIANT(k_res, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
-                                                                           st, pr.buf, (int)mode, ch, kz, pr.fs);
+                                                                           st, pr.buf, (int)mode, ch, kz, pr.fs,
+                                                                           bc);
 }
 void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                     double* y, Partials pr, cudaStream_t s)

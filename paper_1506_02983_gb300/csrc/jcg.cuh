@@ -34,9 +34,15 @@ void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
 void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const double* dinv, double* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s);
+// bc: b / c from launch_scale_load (same level), or null. On a constant-coefficient level (one
+// beta, every face Dirichlet, cubic elements) the residual is then exact in 64-bit integers.
 void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr,
-                  ResMode mode, CondHandles ch, cudaStream_t s);
+                  ResMode mode, CondHandles ch, cudaStream_t s, const double* bc = nullptr);
+// bc = b / c (c = -beta h / 36) and max |bc| into the level state, when the level has one beta,
+// every face Dirichlet and cubic elements (a no-op otherwise).
+void launch_scale_load(const Grid& g, const Op& op, const double* b, double* bc, const double* beta,
+                       const int* uniform, SolveState* st, cudaStream_t s);
 // y = A x with the full matrix (no boundary masking), FP64 or FP32 arithmetic.
 void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                     double* y, Partials pr, cudaStream_t s);
