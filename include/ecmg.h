@@ -63,6 +63,12 @@ enum { ECMG_FP64 = 0, ECMG_MIXED = 1 };
 /* EXP_finite variant: the 20-node Serendipity interpolation of Sec. 4.3, or the 27-node
  * tri-quadratic Lagrange variant of the Remark that follows it. */
 enum { ECMG_EXP_SERENDIPITY20 = 0, ECMG_EXP_LAGRANGE27 = 1 };
+/* Smoother of Alg. 4 line 8 (Sec. 3): JCG (ECMG_jcg) or plain CG (ECMG_cg). */
+enum { ECMG_PREC_JACOBI = 0, ECMG_PREC_NONE = 1 };
+/* Steps per level: the relative residual test of Alg. 4 line 7, or the fixed counts
+ * m_j = ceil(m_L beta^(L-j)) of Alg. 3, eq. (ee), with j = 1 .. L the levels above the two
+ * direct ones. */
+enum { ECMG_SCHED_TOLERANCE = 0, ECMG_SCHED_FIXED = 1 };
 /* ecmg_get_level: which vector */
 enum { ECMG_VEC_U = 0, ECMG_VEC_W = 1, ECMG_VEC_UTILDE = 2, ECMG_VEC_B = 3, ECMG_VEC_BETA = 4 };
 
@@ -96,6 +102,13 @@ typedef struct {
     int32_t autotune;       /* MIXED: 1 = ecmg_create times the tile shapes of the FP32
                                stencil kernel on every level of >= 2^18 nodes and keeps the
                                fastest (ecmg_autotune); 0 = built-in shape       [0]       */
+    int32_t preconditioner; /* ECMG_PREC_JACOBI (ECMG_jcg) or ECMG_PREC_NONE (ECMG_cg), on
+                               every level                                   [JACOBI]      */
+    int32_t schedule;       /* ECMG_SCHED_TOLERANCE or ECMG_SCHED_FIXED; with FIXED every
+                               level >= 2 runs exactly m_j steps (rtol and max_iters unused
+                               there)                                        [TOLERANCE]   */
+    int32_t sched_mL;       /* FIXED: m_L, the steps on the finest level, >= 1  [4]         */
+    double sched_beta;      /* FIXED: beta of eq. (ee), 1..64                   [4.0]       */
 } ecmg_options;
 
 /* Per-solve statistics, one entry per level (coarsest first). */

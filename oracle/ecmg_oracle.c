@@ -376,6 +376,17 @@ int or_jcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
            double rtol, int32_t max_iters, int32_t* iters, double* rel_res_true,
            double* rhs_norm)
 {
+    return or_pcg(N, rowptr, col, val, mask, b, gext, x, rtol, max_iters, 1, 0, iters, rel_res_true, rhs_norm);
+}
+
+/* CG (Alg. 4 line 8 for ECMG_cg) or Jacobi-preconditioned CG (ECMG_jcg), textbook form. precond: 1 = Jacobi
+ * (z = D^-1 r), 0 = none (z = r). fixed: 1 = run exactly max_iters iterations with no tolerance
+ * test (the m_j steps of Alg. 3), which then is not a failure. */
+int or_pcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
+           const uint8_t* mask, const double* b, const double* gext, double* x,
+           double rtol, int32_t max_iters, int32_t precond, int32_t fixed, int32_t* iters, double* rel_res_true,
+           double* rhs_norm)
+{
     double* r = (double*)malloc((size_t)N * sizeof(double));
     double* z = (double*)malloc((size_t)N * sizeof(double));
     double* p = (double*)malloc((size_t)N * sizeof(double));
@@ -383,11 +394,11 @@ int or_jcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
     double* dinv = (double*)malloc((size_t)N * sizeof(double));
     int status = 0;
 
-    /* Jacobi preconditioner: the diagonal of A on free nodes */
+    /* Jacobi preconditioner: the diagonal of A on free nodes (identity for plain CG) */
     for (int64_t i = 0; i < N; ++i) {
         double d = 0.0;
         for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) if (col[t] == i) d = val[t];
-        dinv[i] = mask[i] ? 1.0 / d : 0.0;
+        dinv[i] = mask[i] ? (precond ? 1.0 / d : 1.0) : 0.0;
     }
 
     /* ||f_h|| */
@@ -403,11 +414,11 @@ int or_jcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
 
     int32_t k = 0;
     double rr = dot_masked(N, mask, r, r);
-    if (sqrt(rr) > rtol * fh) {
+    if (fixed ? max_iters > 0 : sqrt(rr) > rtol * fh) {
         for (int64_t i = 0; i < N; ++i) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
         double rho = dot_masked(N, mask, r, z);
         for (;;) {
-            if (k >= max_iters) { status = 3; break; }
+            if (k >= max_iters) { status = fixed ? 0 : 3; break; }
             or_csr_matvec(N, rowptr, col, val, p, q);
             for (int64_t i = 0; i < N; ++i) if (!mask[i]) q[i] = 0.0;
             double pq = dot_masked(N, mask, p, q);
@@ -419,7 +430,8 @@ int or_jcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
             }
             ++k;
             rr = dot_masked(N, mask, r, r);
-            if (sqrt(rr) <= rtol * fh) break;
+            if (!fixed && sqrt(rr) <= rtol * fh) break;
+            if (fixed && k >= max_iters) break;
             for (int64_t i = 0; i < N; ++i) z[i] = dinv[i] * r[i];
             double rho_new = dot_masked(N, mask, r, z);
             double beta = rho_new / rho;
@@ -756,6 +768,24 @@ void or_norms(int64_t N, const double* a, const double* b, double* max_abs, doub
 int or_ecmg(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_variant,
             double* U_all, double* W_all, double* Ut_all, or_stats* st)
 {
+    return or_ecmg_ex(p, rtol, max_iters, exp_variant, 1, 0, 0, 0.0, U_all, W_all, Ut_all, st);
+}
+
+/* Number of CG steps on level l (>= 2) of an L-level hierarchy in the fixed schedule of Alg. 3,
+ * eq. (ee): the paper counts the levels above the two direct ones, j = l - 1 = 1 .. L - 2, and
+ * m_j = ceil(m_L beta^(L_p - j)) with L_p = L - 2. */
+int32_t or_schedule_steps(int32_t L, int32_t l, int32_t mL, double beta)
+{
+    return (int32_t)ceil((double)mL * pow(beta, (double)((L - 2) - (l - 1))));
+}
+
+/* Alg. 4 with the choices of Sec. 3: precond 1 = JCG (ECMG_jcg), 0 = CG (ECMG_cg); schedule 0 =
+ * the relative residual test of line 7, 1 = the fixed step counts of Alg. 3 (eq. (ee)) with m_L
+ * and beta. */
+int or_ecmg_ex(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_variant, int32_t precond,
+               int32_t schedule, int32_t mL, double sched_beta, double* U_all, double* W_all, double* Ut_all,
+               or_stats* st)
+{
     const int L = p->levels;
     memset(st, 0, sizeof(*st));
     if (L < 3 || L > 16) { st->status = 1; return 1; }
@@ -846,7 +876,8 @@ int or_ecmg(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_var
             for (int64_t i = 0; i < N; ++i) if (!mask[i]) W[i] = gext[i];
             /* lines 7-9: JCG from W until the relative residual test passes */
             memcpy(U, W, (size_t)N * sizeof(double));
-            int s = or_jcg(N, rowptr, col, val, mask, b, gext, U, rtol, max_iters,
+            const int32_t steps = schedule ? or_schedule_steps(L, l, mL, sched_beta) : max_iters;
+            int s = or_pcg(N, rowptr, col, val, mask, b, gext, U, rtol, steps, precond, schedule,
                            &st->iters[l], &st->rel_res[l], &st->rhs_norm[l]);
             if (s) status = s;
             /* line 10: U~ = EXP_true(u_h, u_2h) */

@@ -74,6 +74,12 @@ int or_jcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
            const uint8_t* mask, const double* b, const double* gext, double* x,
            double rtol, int32_t max_iters, int32_t* iters, double* rel_res_true,
            double* rhs_norm);
+/* CG or Jacobi-preconditioned CG: precond 1 = Jacobi, 0 = none; fixed 1 = exactly max_iters steps
+ * without the tolerance test (Alg. 3). Same outputs as or_jcg. */
+int or_pcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
+           const uint8_t* mask, const double* b, const double* gext, double* x,
+           double rtol, int32_t max_iters, int32_t precond, int32_t fixed, int32_t* iters, double* rel_res_true,
+           double* rhs_norm);
 int or_dsolve_banded(const int32_t n[3], int64_t N, const int64_t* rowptr,
                      const int64_t* col, const double* val, const uint8_t* mask,
                      const double* b, double* x);
@@ -99,6 +105,13 @@ typedef struct {
 
 int or_ecmg(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_variant,
             double* U_all, double* W_all, double* Ut_all, or_stats* st);
+/* or_ecmg with the variants of Sec. 3: precond 1 = JCG (ECMG_jcg), 0 = CG (ECMG_cg); schedule 1 =
+ * the fixed step counts m_j = ceil(m_L beta^(L-j)) of Alg. 3, eq. (ee), instead of the tolerance. */
+int or_ecmg_ex(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_variant, int32_t precond,
+               int32_t schedule, int32_t mL, double sched_beta, double* U_all, double* W_all, double* Ut_all,
+               or_stats* st);
+/* Steps of level l (>= 2) of an L-level hierarchy in that schedule. */
+int32_t or_schedule_steps(int32_t L, int32_t l, int32_t mL, double beta);
 
 /* ---- norms (Sec. 5: max norm and root-mean-square "L2" norm) ------------------------- */
 void or_norms(int64_t N, const double* a, const double* b, double* max_abs, double* rms);

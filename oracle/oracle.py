@@ -85,6 +85,10 @@ def lib():
         _lib.or_exp_finite_at.argtypes = [P, P, P, I64, I64, I64]
         _lib.or_exp_true_at.restype = D
         _lib.or_exp_true_at.argtypes = [P, P, P, I64, I64, I64]
+        _lib.or_ecmg_ex.restype = C.c_int
+        _lib.or_ecmg_ex.argtypes = [C.POINTER(_Problem), D, I32, I32, I32, I32, I32, D, P, P, P, C.POINTER(_Stats)]
+        _lib.or_schedule_steps.restype = I32
+        _lib.or_schedule_steps.argtypes = [I32, I32, I32, D]
         _lib.or_ecmg.restype = C.c_int
         _lib.or_ecmg.argtypes = [C.POINTER(_Problem), D, I32, I32, P, P, P, C.POINTER(_Stats)]
         _lib.or_norms.argtypes = [I64, P, P, P, P]
@@ -201,6 +205,11 @@ def restrict_load(nc, b_fine):
 
 
 # ---- solvers ----------------------------------------------------------------------------
+def schedule_steps(L, l, mL, beta):
+    """CG steps of level l in the fixed schedule of Alg. 3 (eq. (ee))."""
+    return int(lib().or_schedule_steps(int(L), int(l), int(mL), float(beta)))
+
+
 def apply_at(n, h, beta, face_bc, alpha, x, nodes):
     """(A x) at the given nodes [(i, j, k), ...] from the element matrices (or_apply_at)."""
     nn, hh, bc, al = _i32(n), _f64(h), _i32(face_bc), _f64(alpha)
@@ -293,8 +302,11 @@ def norms(a, b=None):
 
 
 # ---- the whole method -------------------------------------------------------------------
-def ecmg(prob, rtol, max_iters=100000, exp_variant=EXP_SERENDIPITY20):
-    """Run Alg. 4 on a problem dict (see ``paper_1506_02983_gb300.inputs``).
+def ecmg(prob, rtol, max_iters=100000, exp_variant=EXP_SERENDIPITY20, precond=1, schedule=0, mL=0,
+         sched_beta=0.0):
+    """Run Alg. 4 on a problem dict (see ``paper_1506_02983_gb300.inputs``). precond 1 = JCG
+    (ECMG_jcg), 0 = plain CG (ECMG_cg); schedule 1 = the fixed step counts of Alg. 3 (eq. (ee),
+    m_j = ceil(mL * sched_beta^(L-j))) instead of the tolerance.
 
     Returns (levels, stats): levels[l] = dict(n=..., U=..., W=..., Ut=...) with nodal arrays
     shaped (nz+1, ny+1, nx+1); stats has per-level iters, rel_res, rhs_norm and status.
@@ -320,8 +332,8 @@ def ecmg(prob, rtol, max_iters=100000, exp_variant=EXP_SERENDIPITY20):
     P.beta, P.f, P.gD, P.gR = _p(beta), _p(f), _p(gD), _p(gR)
     P.f_mode = int(prob.get("f_mode", F_NODAL))
     S = _Stats()
-    lib().or_ecmg(C.byref(P), rtol, max_iters, int(exp_variant), _p(U), _p(W), _p(Ut),
-                  C.byref(S))
+    lib().or_ecmg_ex(C.byref(P), rtol, max_iters, int(exp_variant), int(precond), int(schedule), int(mL),
+                     float(sched_beta), _p(U), _p(W), _p(Ut), C.byref(S))
     out = []
     off = 0
     for l in range(L):

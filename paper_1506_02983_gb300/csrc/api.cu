@@ -154,6 +154,16 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
     if (o->exp_variant != ECMG_EXP_SERENDIPITY20 && o->exp_variant != ECMG_EXP_LAGRANGE27)
         return fail(ECMG_ERR_INVALID_ARG, "bad exp_variant");
     if (o->autotune != 0 && o->autotune != 1) return fail(ECMG_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o->preconditioner != ECMG_PREC_JACOBI && o->preconditioner != ECMG_PREC_NONE)
+        return fail(ECMG_ERR_INVALID_ARG, "bad preconditioner");
+    if (o->schedule != ECMG_SCHED_TOLERANCE && o->schedule != ECMG_SCHED_FIXED)
+        return fail(ECMG_ERR_INVALID_ARG, "bad schedule");
+    if (o->schedule == ECMG_SCHED_FIXED) {
+        if (o->sched_mL < 1 || !(o->sched_beta >= 1.0 && o->sched_beta <= 64.0))
+            return fail(ECMG_ERR_INVALID_ARG, "fixed schedule: sched_mL >= 1 and sched_beta in [1, 64]");
+        if ((double)o->sched_mL * std::pow(o->sched_beta, (double)(p->levels - 3)) > 1e8)
+            return fail(ECMG_ERR_INVALID_ARG, "fixed schedule: more than 1e8 steps on a level");
+    }
     return ECMG_OK;
 }
 
@@ -260,9 +270,17 @@ void record_setup(Rec& R)
         }
         // FP64 diagonal for FP64 JCG and the direct levels, FP32 for the FP32 iteration of MIXED
         jacobi_diag(v.g, v.op, v.beta, (!mixed || l < 2) ? v.dinv : nullptr, mixed ? v.dinv32 : nullptr,
-                    mixed ? v.beta32 : nullptr, s);
+                    mixed ? v.beta32 : nullptr, h->opt.preconditioner == ECMG_PREC_JACOBI, s);
         uniform_check(v.g, v.beta, v.uniform, s);
     }
+}
+
+// Steps of level l (>= 2) of an L-level hierarchy in the fixed schedule of Alg. 3, eq. (ee): the
+// paper numbers the levels above the two direct ones j = l - 1 = 1 .. L - 2 and sets
+// m_j = ceil(m_L beta^(L_p - j)) with L_p = L - 2.
+int schedule_steps(int L, int l, int mL, double beta)
+{
+    return (int)std::ceil((double)mL * std::pow(beta, (double)((L - 2) - (l - 1))));
 }
 
 // ---- one level of Alg. 4 ------------------------------------------------------------------------
@@ -274,10 +292,12 @@ void record_level(Rec& R, int l)
     const ecmg_options& o = h->opt;
     const bool direct = l < 2;
     const bool mixed = o.precision == ECMG_MIXED && !direct;
-    const double rtol = direct ? o.dsolve_rtol : o.rtol;
+    const bool fixed = o.schedule == ECMG_SCHED_FIXED && !direct;
+    const double rtol = direct ? o.dsolve_rtol : (fixed ? 0.0 : o.rtol);
+    const int max_iters = fixed ? schedule_steps(h->L, l, o.sched_mL, o.sched_beta) : o.max_iters;
     CondHandles none{0, 0, 0};
 
-    launch_state_init(st, rtol, o.inner_rtol, o.max_iters, R.s());
+    launch_state_init(st, rtol, o.inner_rtol, max_iters, fixed ? 1 : 0, R.s());
     dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s());
     launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s());
     // constant coefficient: b / c for the exact integer residual, kept in the FP64 r vector,
@@ -513,7 +533,7 @@ void record_batched(Rec& R)
         const std::vector<int> ids = stage_items(B, s), ids2 = stage_items(B, s, 2);
         if (ids.empty()) continue;
         blaunch_level_start(items, make_launch(B, ids, BG_ONE), make_launch(B, ids, BG_NODES),
-                            make_launch(B, ids, BG_ROWS), B.robin, B.cube, o.inner_rtol, o.max_iters, R.s());
+                            make_launch(B, ids, BG_ROWS), B.robin, B.cube, o.inner_rtol, R.s());
         blaunch_guess(items, make_launch(B, ids2, BG_EXPF), make_launch(B, ids, BG_FLAT), o.exp_variant, R.s());
         const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_FLAT);
         if (R.graph) {
@@ -752,6 +772,10 @@ void ecmg_default_options(ecmg_options* o)
     o->exp_variant = ECMG_EXP_SERENDIPITY20;
     o->true_residual = 1;
     o->autotune = 0;
+    o->preconditioner = ECMG_PREC_JACOBI;
+    o->schedule = ECMG_SCHED_TOLERANCE;
+    o->sched_mL = 4;
+    o->sched_beta = 4.0;
 }
 
 ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, uint64_t* bytes)
@@ -900,7 +924,10 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
                 it.depth = pr.levels - 1 - l;
                 it.fmode = pr.f_mode;
                 it.kz = std::min(32, it.g.nz + 1);
-                it.rtol = l < 2 ? opt->dsolve_rtol : opt->rtol;
+                it.fixed = (opt->schedule == ECMG_SCHED_FIXED && l >= 2) ? 1 : 0;
+                it.rtol = l < 2 ? opt->dsolve_rtol : (it.fixed ? 0.0 : opt->rtol);
+                it.max_iters = it.fixed ? schedule_steps(pr.levels, l, opt->sched_mL, opt->sched_beta) : opt->max_iters;
+                it.precond = opt->preconditioner == ECMG_PREC_JACOBI ? 1 : 0;
                 const int64_t nv = it.g.total;
                 it.U = dalloc<double>(h, nv);
                 it.W = dalloc<double>(h, nv);

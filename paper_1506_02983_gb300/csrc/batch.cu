@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) bk_setup_nodes(const BItem* __restrict__ 
         it.gD[o] = it.fgD[of];
         it.gR[o] = it.fgR[of];
     }
-    it.dinv32[o] = jacobi32_at(g, it.op, it.beta32, i, j, k);
+    it.dinv32[o] = jacobi32_at(g, it.op, it.beta32, i, j, k, it.precond);
 }
 
 // The load vector: consistent mass of the nodal data (NODAL), or the caller's finest load
@@ -211,8 +211,7 @@ __global__ void __launch_bounds__(256) bk_setup_load(const BItem* __restrict__ i
 }
 
 // ---- start of a level -------------------------------------------------------------------------
-__global__ void bk_state_init(const BItem* __restrict__ items, const __grid_constant__ BLaunch L, double inner,
-                              int max_iters)
+__global__ void bk_state_init(const BItem* __restrict__ items, const __grid_constant__ BLaunch L, double inner)
 {
     COUNT_LAUNCH();
     if (threadIdx.x != 0) return;
@@ -221,7 +220,8 @@ __global__ void bk_state_init(const BItem* __restrict__ items, const __grid_cons
     SolveState s = {};
     s.rtol2 = it.rtol * it.rtol;
     s.inner2 = inner * inner;
-    s.max_iters = max_iters;
+    s.max_iters = it.max_iters;
+    s.fixed = it.fixed;
     *it.st = s;
 }
 
@@ -491,10 +491,10 @@ void blaunch_setup(const BItem* items, const BLaunch& nodes, const BLaunch& elem
 }
 
 void blaunch_level_start(const BItem* items, const BLaunch& one, const BLaunch& nodes, const BLaunch& rows,
-                         int robin, int cube, double inner_rtol, int max_iters, cudaStream_t s)
+                         int robin, int cube, double inner_rtol, cudaStream_t s)
 {
     if (one.n == 0) return;
-    bk_state_init<<<nblocks(one), 32, 0, s>>>(items, one, inner_rtol, max_iters);
+    bk_state_init<<<nblocks(one), 32, 0, s>>>(items, one, inner_rtol);
     bk_dirichlet_ext<<<nblocks(nodes), dim3(mt::BX, mt::BY), 0, s>>>(items, nodes);
     auto k = robin ? (cube ? bk_fh2<true, true> : bk_fh2<true, false>)
                    : (cube ? bk_fh2<false, true> : bk_fh2<false, false>);

@@ -28,6 +28,9 @@ struct BItem {
     int level, problem, depth, fmode;  // depth 0 = the problem's finest level
     int kz;               // z-march depth of the stencil kernels
     double rtol;          // relative residual tolerance of this level
+    int max_iters;        // step cap (the exact step count when fixed)
+    int fixed;            // 1: exactly max_iters steps (the schedule of Alg. 3)
+    int precond;          // 1: Jacobi (ECMG_jcg), 0: plain CG (ECMG_cg)
     // vectors of this level (padded layout)
     double *U, *W, *Ut, *b, *beta, *f, *gD, *gR;
     float *beta32, *dinv32, *r32, *pA32, *pB32, *q32, *e32;
@@ -78,7 +81,7 @@ int bitem_partials(const BItem& it);
 void blaunch_setup(const BItem* items, const BLaunch& nodes, const BLaunch& elems, cudaStream_t s);
 // Start of a level: state reset, Dirichlet extension, ||f_h||^2.
 void blaunch_level_start(const BItem* items, const BLaunch& one, const BLaunch& nodes, const BLaunch& rows,
-                         int robin, int cube, double inner_rtol, int max_iters, cudaStream_t s);
+                         int robin, int cube, double inner_rtol, cudaStream_t s);
 // EXP_finite for levels >= 2 (x and W), W = x on the direct levels 0 and 1, and zeroed FP32
 // search directions and corrections.
 void blaunch_guess(const BItem* items, const BLaunch& expf, const BLaunch& flat_all, int variant, cudaStream_t s);

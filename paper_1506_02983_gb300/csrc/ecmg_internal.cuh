@@ -107,6 +107,7 @@ struct SolveState {
     int p_latest;        // which of the two search-direction buffers holds the newest p
     unsigned int arrive; // block arrival counter of the last-block reductions
     unsigned long long bcbits;  // MIXED, constant coefficient: bits of max |b / c| (fixed-point scale)
+    int fixed;           // 1: exactly max_iters steps, no tolerance test (the schedule of Alg. 3)
 };
 
 // Fixed-point scale of an iterate: bit pattern of max |x| (nonnegative doubles order like their
@@ -148,7 +149,7 @@ void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc,
 void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
                 cudaStream_t s);
 void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
-                 float* beta32, cudaStream_t s);
+                 float* beta32, int precond, cudaStream_t s);
 void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x,
                          cudaStream_t s);
 void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s);

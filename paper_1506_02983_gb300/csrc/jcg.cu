@@ -730,13 +730,14 @@ __global__ void k_fold32(int64_t n, double* __restrict__ x, float* __restrict__ 
     }
 }
 
-__global__ void k_state_init(SolveState* st, double rtol, double inner, int max_iters)
+__global__ void k_state_init(SolveState* st, double rtol, double inner, int max_iters, int fixed)
 {
     COUNT_LAUNCH();
     SolveState s = {};
     s.rtol2 = rtol * rtol;
     s.inner2 = inner * inner;
     s.max_iters = max_iters;
+    s.fixed = fixed;
     *st = s;
 }
 
@@ -885,9 +886,9 @@ void launch_fold32(const Grid& g, double* x, float* e, const float* p, SolveStat
 {
     k_fold32<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, e, p, st);
 }
-void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, cudaStream_t s)
+void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed, cudaStream_t s)
 {
-    k_state_init<<<1, 1, 0, s>>>(st, rtol, inner_rtol, max_iters);
+    k_state_init<<<1, 1, 0, s>>>(st, rtol, inner_rtol, max_iters, fixed);
 }
 
 unsigned long long launches_jcg()

@@ -66,8 +66,8 @@ void launch_final64(const Grid& g, double* x, const double* pA, const double* pB
 // MIXED: x64 += e + alpha_prev p; e = 0.
 void launch_fold32(const Grid& g, double* x, float* e, const float* p, SolveState* st,
                    cudaStream_t s);
-// Reset the level state before a solve.
-void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters,
+// Reset the level state before a solve; fixed: run exactly max_iters steps (Alg. 3).
+void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed,
                        cudaStream_t s);
 
 int max_stencil_blocks(const Grid& g);

@@ -82,7 +82,7 @@ __device__ __forceinline__ void res_epilogue(SolveState* st, double rr, double r
             st->done = 1;
         } else if (st->stop_after_update) {
             st->rr = rr;
-            st->status = 3;
+            st->status = st->fixed ? 0 : 3;  // the step count of a fixed schedule is the goal
             st->done = 1;
         } else {
             st->beta = rz / st->rho;
@@ -112,7 +112,7 @@ __device__ __forceinline__ void update_epilogue(SolveState* st, double rho_new, 
         if (rrv <= st->thresh2) {
             st->done = 1;
         } else if (st->iters >= st->max_iters) {
-            st->status = 3;
+            st->status = st->fixed ? 0 : 3;  // the step count of a fixed schedule is the goal
             st->done = 1;
         } else {
             st->beta = rho_new / st->rho;

@@ -79,10 +79,14 @@ __global__ void k_nodal_load(Grid g, Op op, const double* __restrict__ f,
 
 // Jacobi diagonal: diag = w0 * (sum of the 8 element betas) + Robin face mass diagonal.
 // Dirichlet nodes get dinv = 0, which also masks them in every JCG kernel.
-__global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, double* __restrict__ dinv64)
+__global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, double* __restrict__ dinv64, int precond)
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
+    if (!precond) {  // plain CG (ECMG_cg): the identity on free nodes
+        dinv64[g.off(i, j, k)] = on_dirichlet(g, op, i, j, k) ? 0.0 : 1.0;
+        return;
+    }
     double B = 0.0;
     for (int c = 0; c < 8; ++c)
         B += beta[g.off(i - 1 + (c & 1), j - 1 + ((c >> 1) & 1), k - 1 + (c >> 2))];
@@ -103,11 +107,11 @@ __global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, doubl
 // The same diagonal in FP32 arithmetic from the FP32 betas, for the FP32 iteration of MIXED
 // mode: no FP64 division or conversion per node (FP64 runs at 1/64 of the FP32 rate on GB300).
 // Robin terms (boundary nodes only) are formed in FP64 and rounded.
-__global__ void k_jacobi32(Grid g, Op op, const float* __restrict__ beta32, float* __restrict__ dinv32)
+__global__ void k_jacobi32(Grid g, Op op, const float* __restrict__ beta32, float* __restrict__ dinv32, int precond)
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
-    dinv32[g.off(i, j, k)] = jacobi32_at(g, op, beta32, i, j, k);
+    dinv32[g.off(i, j, k)] = jacobi32_at(g, op, beta32, i, j, k, precond);
 }
 
 // x = g_D on Dirichlet nodes, 0 on free nodes (gD == nullptr: zero everywhere).
@@ -183,12 +187,12 @@ void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, 
     k_nodal_load<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, f, gR, b);
 }
 void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
-                 float* beta32, cudaStream_t s)
+                 float* beta32, int precond, cudaStream_t s)
 {
-    if (dinv64) k_jacobi64<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta, dinv64);
+    if (dinv64) k_jacobi64<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta, dinv64, precond);
     if (beta32) {
         convert_f32(beta, beta32, g.total, s);
-        if (dinv32) k_jacobi32<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32);
+        if (dinv32) k_jacobi32<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32, precond);
     }
 }
 void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x, cudaStream_t s)

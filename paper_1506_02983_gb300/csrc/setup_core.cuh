@@ -87,9 +87,11 @@ __device__ __forceinline__ double nodal_load_at(const Grid& g, const Op& op, con
 // The same diagonal in FP32 arithmetic from the FP32 betas, for the FP32 iteration of MIXED
 // mode: no FP64 division or conversion per node (FP64 runs at 1/64 of the FP32 rate on GB300).
 // Robin terms (boundary nodes only) are formed in FP64 and rounded.
+// precond 0: the identity on free nodes (plain CG, ECMG_cg).
 __device__ __forceinline__ float jacobi32_at(const Grid& g, const Op& op, const float* __restrict__ beta32, int i, int j,
-                                            int k)
+                                            int k, int precond = 1)
 {
+    if (!precond) return on_dirichlet(g, op, i, j, k) ? 0.f : 1.f;
     float B = 0.f;
     for (int c = 0; c < 8; ++c)
         B += beta32[g.off(i - 1 + (c & 1), j - 1 + ((c >> 1) & 1), k - 1 + (c >> 2))];

@@ -86,3 +86,24 @@ def test_batched_validation_without_gpu(libpath):
     arr[1].levels = 2
     assert ecmg.ecmg_create_batched(arr, 2, ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
     assert ecmg.ecmg_solve_batched(None, None, None) == ecmg.ECMG_ERR_INVALID_ARG
+
+
+def test_solver_variant_options_validation_without_gpu(libpath):
+    """Preconditioner and schedule options are checked before any CUDA call."""
+    from paper_1506_02983_gb300 import ecmg
+    p = ecmg.ecmg_problem()
+    p.n0[:] = [2, 2, 2]
+    p.levels = 4
+    p.lo[:] = [0, 0, 0]
+    p.hi[:] = [1, 1, 1]
+    p.beta = 16
+    p.f = 16
+    h = ctypes.c_void_p()
+    for bad in (dict(preconditioner=2), dict(schedule=3), dict(schedule=1, sched_mL=0),
+                dict(schedule=1, sched_beta=0.5), dict(schedule=1, sched_beta=65.0),
+                dict(schedule=1, sched_mL=2000000, sched_beta=64.0)):
+        o = ecmg.default_options(**bad)
+        assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG, bad
+    o = ecmg.default_options()
+    assert o.preconditioner == ecmg.ECMG_PREC_JACOBI and o.schedule == ecmg.ECMG_SCHED_TOLERANCE
+    assert o.sched_mL == 4 and o.sched_beta == 4.0 and o.inner_rtol == 1e-3

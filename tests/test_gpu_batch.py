@@ -161,3 +161,19 @@ def test_single_problem_calls_reject_a_batched_handle(E):
     out = E.ecmg_get_level_batched(bs.handle, 1, -1, E.ECMG_VEC_U, None)
     assert out == E.ECMG_ERR_INVALID_ARG
     bs.close()
+
+
+def test_batched_ecmg_cg_matches_oracle(E, oracle_mod):
+    """A batch solved with plain CG (ECMG_cg) against the oracle's CG, problem by problem."""
+    probs = _mixed_batch()[:3]
+    dev = [_device(p) for p in probs]
+    bs = E.BatchSolver(dev, rtol=RTOL, preconditioner=E.ECMG_PREC_NONE)
+    stats, status = bs.solve()
+    assert status == 0, stats
+    for i, p in enumerate(probs):
+        lv, ost = oracle_mod.ecmg(p, RTOL, precond=0)
+        L = p["levels"]
+        assert stats[i]["rel_res"][L - 1] <= RTOL
+        U = _np(bs.get(i, E.ECMG_VEC_U))
+        assert _rel(U, lv[L - 1]["U"]) <= 1e-7, (i, _rel(U, lv[L - 1]["U"]))
+    bs.close()

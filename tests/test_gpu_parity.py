@@ -278,3 +278,45 @@ def test_mixed_jump_problem_matches_oracle(E, oracle_mod):
             got = _np(s.get(which, l))
             assert _rel(got, lv[l][key]) <= 1e-7, (l, key, _rel(got, lv[l][key]))
     s.close()
+
+
+@pytest.mark.parametrize("name", ["exp_cube", "random_mixed_bc_0", "problem1_load", "aniso_uniform_robin"])
+def test_fp64_ecmg_cg_matches_oracle(E, oracle_mod, name):
+    """ECMG_cg (plain CG on line 8 of Alg. 4): the FP64 path against the oracle's CG."""
+    p = PROBLEMS[name]()
+    lv, ost = oracle_mod.ecmg(p, p["rtol"], precond=0)
+    assert ost["status"] == 0
+    s = E.solver_from_problem(p, precision=0, preconditioner=E.ECMG_PREC_NONE)
+    st, status = s.solve()
+    assert status == 0, st
+    for l in range(2, p["levels"]):
+        assert abs(st["iters"][l] - ost["iters"][l]) <= 1, (l, st["iters"], ost["iters"])
+        U = _np(s.get(E.ECMG_VEC_U, l))
+        assert _rel(U, lv[l]["U"]) <= 1e-10, (l, _rel(U, lv[l]["U"]))
+    s.close()
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_fixed_schedule_matches_oracle(E, oracle_mod, precond):
+    """Alg. 3's fixed step counts m_j = ceil(m_L beta^(L-j)): exactly m_j steps per level, FP64
+    against the oracle; MIXED takes the same step counts and ends with status OK."""
+    p = PROBLEMS["random_mixed_bc_0"]()
+    L = p["levels"]
+    lv, ost = oracle_mod.ecmg(p, p["rtol"], precond=precond, schedule=1, mL=3, sched_beta=2.5)
+    want = [oracle_mod.schedule_steps(L, l, 3, 2.5) for l in range(2, L)]
+    assert ost["iters"][2:] == want
+    opts = dict(preconditioner=E.ECMG_PREC_JACOBI if precond else E.ECMG_PREC_NONE,
+                schedule=E.ECMG_SCHED_FIXED, sched_mL=3, sched_beta=2.5)
+    s = E.solver_from_problem(p, precision=0, **opts)
+    st, status = s.solve()
+    assert status == 0, st
+    assert st["iters"][2:L] == want, (st["iters"], want)
+    for l in range(2, L):
+        U = _np(s.get(E.ECMG_VEC_U, l))
+        assert _rel(U, lv[l]["U"]) <= 1e-10, (l, _rel(U, lv[l]["U"]))
+    s.close()
+    m = E.solver_from_problem(p, precision=1, **opts)
+    st, status = m.solve()
+    assert status == 0, st
+    assert st["iters"][2:L] == want, (st["iters"], want)
+    m.close()

@@ -60,3 +60,30 @@ def test_problem1_serendipity20_close_to_tables(oracle_mod):
         assert got["WU_L2"] == pytest.approx(want["WU_L2"], rel=0.06)
         assert got["WU_inf"] == pytest.approx(want["WU_inf"], rel=0.30)
         assert abs(got["iters"] - want["iters"]) <= 2
+
+
+@pytest.mark.parametrize("eps_key,eps", [("1e-8", 1e-8), ("1e-9", 1e-9), ("1e-10", 1e-10)])
+def test_problem1_ecmg_cg_reproduces_tables(oracle_mod, eps_key, eps):
+    """ECMG_cg (Alg. 4 with line 8 plain CG, Sec. 3): the printed CG iteration counts on the 32^3
+    and 64^3 grids, to one iteration (same 27-node variant and exact load as above)."""
+    p = inputs.paper_problem1(levels=4, rtol=eps)
+    lv, st = oracle_mod.ecmg(p, eps, exp_variant=1, precond=0)
+    assert st["status"] == 0
+    want = TAB["ecmg_cg_iters"][eps_key]
+    for l, size in ((2, "32"), (3, "64")):
+        assert abs(st["iters"][l] - want[size]) <= 1, (eps_key, size, st["iters"][l], want[size])
+        assert st["rel_res"][l] <= eps
+
+
+def test_fixed_schedule_follows_eq_ee(oracle_mod):
+    """Alg. 3's fixed step counts, eq. (ee): m_j = ceil(m_L beta^(L-j)) on the levels above the two
+    direct ones (j = 1 .. L, finest j = L gets m_L), e.g. m_j = 4 * 4^(L-j)."""
+    assert [oracle_mod.schedule_steps(7, l, 4, 4.0) for l in range(2, 7)] == [1024, 256, 64, 16, 4]
+    assert [oracle_mod.schedule_steps(5, l, 3, 2.5) for l in range(2, 5)] == [19, 8, 3]
+    p = inputs.exp_cube(levels=5, rtol=1e-10)
+    lv, st = oracle_mod.ecmg(p, 1e-10, schedule=1, mL=2, sched_beta=3.0, precond=0)
+    assert st["status"] == 0
+    assert st["iters"][2:] == [18, 6, 2]
+    # more steps shrink the residual (a fixed count, not a tolerance, ends each level)
+    lv2, st2 = oracle_mod.ecmg(p, 1e-10, schedule=1, mL=8, sched_beta=3.0, precond=0)
+    assert st2["rel_res"][4] < st["rel_res"][4]
