@@ -121,6 +121,28 @@ def paper_problem1(levels=7, n0=(8, 8, 8), rtol=1e-9, load="exact"):
     return p
 
 
+def paper_problem2(levels=7, n0=(10, 4, 5), rtol=1e-12, load="exact"):
+    """Problem 2 of Sec. 5: Laplace u = (1 - 2.5 pi^2) e^z sin(3 pi x/2) sin(pi y/2) on [0,1]^3,
+    u = 0 on x = 0 and y = 0, u = sin(3 pi x/2) sin(pi y/2) on z = 0 and e times that on z = 1,
+    du/dn = 0 on x = 1 and y = 1; u = e^z sin(3 pi x/2) sin(pi y/2). Anisotropic elements:
+    coarsest 10 x 4 x 5 (the paper's choice), 7 levels to 640 x 256 x 320.
+    load="exact": f is the load functional int f phi_i (f_mode 1); "nodal": nodal f."""
+    bc = [DIRICHLET, ROBIN, DIRICHLET, ROBIN, DIRICHLET, DIRICHLET]
+    p = _base(n0, levels, (0, 0, 0), (1, 1, 1), bc, [0.0] * 6, rtol)
+    n = finest(n0, levels)
+    x, y, z = _axes(n, p["lo"], p["hi"])
+    u = np.exp(z) * np.sin(1.5 * PI * x) * np.sin(0.5 * PI * y)
+    scale = 2.5 * PI * PI - 1.0
+    if load == "exact":
+        f = separable_load(n, p["lo"], p["hi"], scale, lambda t: np.sin(1.5 * PI * t),
+                           lambda t: np.sin(0.5 * PI * t), np.exp)
+        p["f_mode"] = 1
+    else:
+        f = scale * u
+    p.update(beta=np.ones((n[2], n[1], n[0])), f=f, gD=u, gR=np.zeros_like(u), u_exact=u)
+    return p
+
+
 def variable_box(levels=7, n0=(8, 8, 16), rtol=1e-9):
     """Box (0,1)x(0,1)x(0,2) with beta = 1 + 0.5 sin(2 pi x) cos(2 pi y) sin(pi z) (at element
     centres), u = sin(pi x) sin(pi y) sin(pi z) + x y z, Dirichlet on five faces and Robin

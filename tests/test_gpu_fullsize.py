@@ -197,3 +197,25 @@ def test_jump_singular_full_size_mixed(E, oracle_mod):
     r = _at(b, n, free) - oracle_mod.apply_at(n, h, beta, p["face_bc"], p["alpha"], U, free)
     assert np.abs(r).max() <= p["rtol"] * st["rhs_norm"][L - 1] * 1.0001, np.abs(r).max()
     s.close()
+
+
+def test_problem2_full_size_against_paper(E):
+    """Problem 2 at the paper's finest grid 640 x 256 x 320 (MIXED, eps 1e-12): the errors the
+    paper prints for that row (tables 'table3'/'table4'), ||U-u|| to 2 % and ||W-U|| to 10 %."""
+    import json
+    import os
+    tab = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "problem2_tables.json")))
+    want = tab["rows"]["640x256x320"]
+    p = inputs.paper_problem2(levels=7, rtol=1e-12)
+    s = E.solver_from_problem(p, precision=E.ECMG_MIXED)
+    st, status = s.solve()
+    assert status == 0, st
+    assert st["rel_res"][6] <= 1e-12 * 1.01
+    U = _np(s.get(E.ECMG_VEC_U))
+    W = _np(s.get(E.ECMG_VEC_W))
+    ue = np.asarray(p["u_exact"])
+    e = U - ue
+    assert np.abs(e).max() == pytest.approx(want["U_inf"], rel=0.02)
+    assert np.sqrt(np.mean(e * e)) == pytest.approx(want["U_L2"], rel=0.02)
+    assert np.abs(W - U).max() == pytest.approx(want["WU_inf"], rel=0.10)
+    s.close()

@@ -320,3 +320,22 @@ def test_fixed_schedule_matches_oracle(E, oracle_mod, precond):
     assert status == 0, st
     assert st["iters"][2:L] == want, (st["iters"], want)
     m.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_problem2_anisotropic_matches_oracle(E, oracle_mod, precision):
+    """Problem 2 of Sec. 5 (elements 0.1 x 0.25 x 0.2 on the coarsest grid, Neumann faces,
+    eps 1e-12): FP64 to the method's bar, MIXED to the mixed bar."""
+    p = inputs.paper_problem2(levels=4, rtol=1e-12)
+    L = p["levels"]
+    lv, ost = oracle_mod.ecmg(p, p["rtol"])
+    s = E.solver_from_problem(p, precision=precision)
+    st, status = s.solve()
+    assert status == 0, st
+    for l in range(2, L):
+        assert st["rel_res"][l] <= 1e-12 * 1.01, (l, st["rel_res"])
+        U = _np(s.get(E.ECMG_VEC_U, l))
+        assert _rel(U, lv[l]["U"]) <= (1e-10 if precision == 0 else 1e-9), (l, _rel(U, lv[l]["U"]))
+        if precision == 0:
+            assert abs(st["iters"][l] - ost["iters"][l]) <= 1, (l, st["iters"], ost["iters"])
+    s.close()
