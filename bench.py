@@ -7,7 +7,8 @@ One step = one complete ecmg_solve (level set-up, DSOLVE, EXP_finite / JCG / EXP
 level) in MIXED precision from inputs resident in HBM. value = finest free dofs / step time
 (Gdof/s). The same problem is also solved in plain FP64 (reported beside it, with both
 max-norm errors against the exact solution), end to end through the C ABI from pinned host
-buffers (e2e), and by the CPU oracle on a bounded sample (cpu_baseline).
+buffers (e2e: compact separable inputs assembled on the device; e2e_dense_inputs: the dense
+arrays), and by the CPU oracle on a bounded sample (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun): independent replicas, one per rank, max-over-ranks timing.
@@ -356,10 +357,38 @@ def main():
         mixed.solve(u_out)
         u_host.copy_(u_out, non_blocking=True)
 
-    ms_e2e = timed(e2e_step, args.e2e_steps)
-    h2d = sum(v.numel() * 8 for v in host.values())
+    ms_e2e_dense = timed(e2e_step, args.e2e_steps)
+    h2d_dense = sum(v.numel() * 8 for v in host.values())
     d2h = u_host.numel() * 8
     mixed.close()
+
+    # end to end with compact inputs: f and g_D as separable factors (Gauss samples, nodal
+    # factors), beta as one constant; the load functional and the coarse levels are assembled on
+    # the device inside the solve
+    pc = inputs.cos_cube_compact(levels=L, n0=(n0,) * 3, rtol=args.rtol, with_exact=False)
+    hostc = {k: torch.from_numpy(np.ascontiguousarray(pc[k], dtype=np.float64)).pin_memory() for k in ("f", "gD")}
+    dc = {k: v.to(dev) for k, v in hostc.items()}
+    compact = ecmg.Solver(pc["n0"], L, pc["lo"], pc["hi"], pc["face_bc"], pc["alpha"], None, dc["f"], dc["gD"],
+                          None, f_mode=ecmg.ECMG_F_SEPARABLE, f_terms=pc["f_terms"], gD_terms=pc["gD_terms"],
+                          beta_const=pc["beta_const"], rtol=args.rtol, precision=ecmg.ECMG_MIXED,
+                          max_iters=args.max_iters, use_graph=0 if args.eager else 1, inner_rtol=args.inner_rtol)
+    st_c, status = compact.solve(u_out)
+    assert status == 0, st_c
+    compact.autotune(3)
+
+    def e2e_compact():
+        for k in ("f", "gD"):
+            dc[k].copy_(hostc[k], non_blocking=True)
+        compact.solve(u_out)
+        u_host.copy_(u_out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_compact()
+    ms_e2e = timed(e2e_compact, args.e2e_steps)
+    h2d = sum(v.numel() * 8 for v in hostc.values())
+    st_c, _ = compact.solve(u_out)
+    err_compact = compact.norms(u_out, u_exact)[0]
+    compact.close()
 
     fp64 = make(ecmg.ECMG_FP64)
     st64, status = fp64.solve(u_out)
@@ -419,7 +448,13 @@ def main():
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": dofs / (ms_e2e * 1e-3) / 1e9, "unit": "Gdof/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+                "inputs": "compact: f as one separable term at the 3-point Gauss nodes, g_D as one separable "
+                          "term, beta_const (ECMG_F_SEPARABLE); load assembled on the device; solution read back",
+                "max_err": err_compact, "iters": st_c["iters"]},
+        "e2e_dense_inputs": {"value": dofs / (ms_e2e_dense * 1e-3) / 1e9, "unit": "Gdof/s",
+                             "h2d_bytes_per_step": h2d_dense, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e_dense,
+                             "inputs": "dense beta, load functional and g_D arrays (ECMG_F_LOAD)"},
         "cpu_baseline": cpu,
         "batched": batched,
     }

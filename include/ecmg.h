@@ -58,7 +58,7 @@ typedef enum {
 enum { ECMG_BC_DIRICHLET = 0, ECMG_BC_ROBIN = 1 };
 /* f is nodal values of f (load b = M f_I + sum_F M_F g_R,I per level), or the finest
  * assembled load functional b_i = f(phi_i) of Sec. 2 (coarse loads b_{l-1} = P^T b_l). */
-enum { ECMG_F_NODAL = 0, ECMG_F_LOAD = 1 };
+enum { ECMG_F_NODAL = 0, ECMG_F_LOAD = 1, ECMG_F_SEPARABLE = 2 };
 enum { ECMG_FP64 = 0, ECMG_MIXED = 1 };
 /* EXP_finite variant: the 20-node Serendipity interpolation of Sec. 4.3, or the 27-node
  * tri-quadratic Lagrange variant of the Remark that follows it. */
@@ -84,7 +84,21 @@ typedef struct {
     const double* g_D;      /* device, finest nodes, read on Dirichlet nodes; NULL = 0      */
     const double* g_R;      /* device, finest nodes, read on Robin faces (nodal f_mode only);
                                NULL = 0                                                      */
-    int32_t f_mode;         /* ECMG_F_NODAL or ECMG_F_LOAD                                  */
+    int32_t f_mode;         /* ECMG_F_NODAL, ECMG_F_LOAD or ECMG_F_SEPARABLE                 */
+    /* Compact inputs (single-problem handles; ecmg_create_batched rejects them):
+     * ECMG_F_SEPARABLE: f = sum over f_terms terms of fx(x) fy(y) fz(z); the device array f
+     *   holds every factor at the 3-point Gauss-Legendre nodes of every finest element interval
+     *   [x_e, x_e + h], in the order x_e + h (1 - sqrt(3/5))/2, x_e + h/2, x_e + h (1 + sqrt(3/5))/2:
+     *   f_terms x 3 (nx + ny + nz) doubles, term-major, then x, y, z, interval-major. The library
+     *   assembles the load functional int f phi_i of Sec. 2 from them (the rule is exact for
+     *   factors of degree <= 4) and its exact coarse restrictions P^T b; g_R must be NULL.
+     * gD_terms > 0: g_D = sum over gD_terms terms of gx(x) gy(y) gz(z); the device array g_D holds
+     *   the factors at the finest nodes: gD_terms x ((nx+1) + (ny+1) + (nz+1)) doubles,
+     *   term-major, then x, y, z.
+     * beta == NULL: one beta everywhere, beta_const (> 0). */
+    int32_t f_terms;        /* ECMG_F_SEPARABLE: terms of f, 1..64                           */
+    int32_t gD_terms;       /* 0: g_D nodal (or NULL); 1..64: g_D separable                  */
+    double beta_const;      /* the beta of every element when beta is NULL                  */
 } ecmg_problem;
 
 /* Solver options. ecmg_default_options fills the defaults given in brackets. */

@@ -182,6 +182,50 @@ def load_nodal(n, h, f, face_bc, gR=None):
     return b
 
 
+def gauss3_unit():
+    """3-point Gauss-Legendre rule on [0, 1]: nodes (1 - sqrt(3/5))/2, 1/2, (1 + sqrt(3/5))/2
+    and weights 5/18, 8/18, 5/18 (exact for polynomials of degree <= 5)."""
+    r = np.sqrt(0.6)
+    return np.array([0.5 * (1.0 - r), 0.5, 0.5 * (1.0 + r)]), np.array([5.0, 8.0, 5.0]) / 18.0
+
+
+def load_separable(n, h, terms, samples):
+    """Load functional b_i = int f phi_i of Sec. 2 for f = sum_t fx_t(x) fy_t(y) fz_t(z), given by
+    its factors at the 3-point Gauss nodes of every element interval (the ECMG_F_SEPARABLE
+    layout: term-major, then x (3 per interval), y, z). Written as the definition: on every
+    element, the 27-point tensor Gauss rule of f times each of the element's 8 trilinear hats,
+    added into the hat's node. Exact when the factors have degree <= 4. Shape (nz+1, ny+1, nx+1)."""
+    nx, ny, nz = (int(v) for v in n)
+    s = np.asarray(samples, dtype=np.float64).reshape(int(terms), -1)
+    fx = s[:, :3 * nx].reshape(-1, nx, 3)
+    fy = s[:, 3 * nx:3 * (nx + ny)].reshape(-1, ny, 3)
+    fz = s[:, 3 * (nx + ny):].reshape(-1, nz, 3)
+    # f at the 27 points of every element: F[ez, ey, ex, qz, qy, qx]
+    F = np.einsum("tkc,tjb,tia->kjicba", fz, fy, fx)
+    g, w = gauss3_unit()
+    b = np.zeros((nz + 1, ny + 1, nx + 1))
+    vol = h[0] * h[1] * h[2]
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                # the hat of corner (cx, cy, cz) at the 27 points, times the weights
+                phx = g if cx else 1.0 - g
+                phy = g if cy else 1.0 - g
+                phz = g if cz else 1.0 - g
+                wphi = np.einsum("c,b,a->cba", w * phz, w * phy, w * phx)
+                b[cz:cz + nz, cy:cy + ny, cx:cx + nx] += vol * np.einsum("kjicba,cba->kji", F, wphi)
+    return b
+
+
+def nodal_separable(n, terms, factors):
+    """g(x_i, y_j, z_k) = sum_t gx_t[i] gy_t[j] gz_t[k] from nodal factors (term-major, then x,
+    y, z), shape (nz+1, ny+1, nx+1)."""
+    nx, ny, nz = (int(v) for v in n)
+    s = np.asarray(factors, dtype=np.float64).reshape(int(terms), -1)
+    gx, gy, gz = s[:, :nx + 1], s[:, nx + 1:nx + ny + 2], s[:, nx + ny + 2:]
+    return np.einsum("tk,tj,ti->kji", gz, gy, gx)
+
+
 # ---- level transfer ---------------------------------------------------------------------
 def coarsen_beta(nc, beta_fine):
     out = np.zeros(int(np.prod(nc)))

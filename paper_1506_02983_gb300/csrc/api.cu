@@ -22,6 +22,7 @@
 #include "exp.cuh"
 #include "jcg.cuh"
 #include "pq_tma.cuh"
+#include "separable.cuh"
 
 using namespace ecmg;
 
@@ -66,6 +67,9 @@ struct Level {
     PlaneMaps maps;  // TMA descriptors of the FP32 vectors
     K1Config k1{1, 128};  // tile shape of the FP32 stencil kernel
     int* uniform = nullptr;  // device flag: one beta on the whole level
+    // 1D factors of separable data (ECMG_F_SEPARABLE load, separable g_D); Hg of the finest level
+    // is the caller's array
+    double *Hf = nullptr, *Hg = nullptr;
 };
 
 }  // namespace
@@ -128,9 +132,17 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
         int64_t nf = (int64_t)p->n0[a] << (p->levels - 1);
         if (nf > 16384) return fail(ECMG_ERR_INVALID_ARG, "finest grid too large");
     }
-    if (!p->beta || !p->f) return fail(ECMG_ERR_INVALID_ARG, "beta and f are required");
-    if (p->f_mode != ECMG_F_NODAL && p->f_mode != ECMG_F_LOAD)
+    if (!p->f) return fail(ECMG_ERR_INVALID_ARG, "f is required");
+    if (!p->beta && !(p->beta_const > 0.0 && std::isfinite(p->beta_const)))
+        return fail(ECMG_ERR_INVALID_ARG, "beta is NULL and beta_const is not a finite positive number");
+    if (p->f_mode != ECMG_F_NODAL && p->f_mode != ECMG_F_LOAD && p->f_mode != ECMG_F_SEPARABLE)
         return fail(ECMG_ERR_INVALID_ARG, "bad f_mode");
+    if (p->f_mode == ECMG_F_SEPARABLE) {
+        if (p->f_terms < 1 || p->f_terms > 64) return fail(ECMG_ERR_INVALID_ARG, "f_terms must be 1..64");
+        if (p->g_R) return fail(ECMG_ERR_INVALID_ARG, "ECMG_F_SEPARABLE takes no g_R");
+    }
+    if (p->gD_terms < 0 || p->gD_terms > 64) return fail(ECMG_ERR_INVALID_ARG, "gD_terms must be 0..64");
+    if (p->gD_terms > 0 && !p->g_D) return fail(ECMG_ERR_INVALID_ARG, "gD_terms > 0 needs g_D");
     bool dir = false, alpha = false;
     for (int f = 0; f < 6; ++f) {
         if (p->face_bc[f] != ECMG_BC_DIRICHLET && p->face_bc[f] != ECMG_BC_ROBIN)
@@ -251,21 +263,27 @@ void record_setup(Rec& R)
     for (int l = L - 1; l >= 0; --l) {
         Level& v = h->lv[l];
         if (l == L - 1) {
-            pack_elements(v.g, p.beta, v.beta, s);
-            pack_nodal(v.g, p.f, v.f, s);
-            if (p.g_D) pack_nodal(v.g, p.g_D, v.gD, s);
+            if (p.beta) pack_elements(v.g, p.beta, v.beta, s);
+            else fill_beta(v.g, p.beta_const, v.beta, s);
+            if (p.f_mode == ECMG_F_SEPARABLE) sep_load_finest(v.g, p.f_terms, p.f, v.Hf, v.b, s);
+            else pack_nodal(v.g, p.f, v.f, s);
+            if (p.g_D && p.gD_terms > 0) sep_nodal(v.g, p.gD_terms, p.g_D, v.gD, s);
+            else if (p.g_D) pack_nodal(v.g, p.g_D, v.gD, s);
             if (p.g_R) pack_nodal(v.g, p.g_R, v.gR, s);
         } else {
             Level& u = h->lv[l + 1];
             coarsen_beta(v.g, u.beta, u.g, v.beta, s);
             if (p.f_mode == ECMG_F_LOAD) restrict_load(v.g, u.b, u.g, v.b, s);
+            else if (p.f_mode == ECMG_F_SEPARABLE) sep_coarsen(v.g, u.g, p.f_terms, u.Hf, v.Hf, true, v.b, s);
             else inject_nodal(v.g, u.f, u.g, v.f, s);
-            if (p.g_D) inject_nodal(v.g, u.gD, u.g, v.gD, s);
+            if (p.g_D && p.gD_terms > 0)
+                sep_coarsen(v.g, u.g, p.gD_terms, l + 1 == L - 1 ? p.g_D : u.Hg, v.Hg, false, v.gD, s);
+            else if (p.g_D) inject_nodal(v.g, u.gD, u.g, v.gD, s);
             if (p.g_R) inject_nodal(v.g, u.gR, u.g, v.gR, s);
         }
         if (p.f_mode == ECMG_F_LOAD) {
             if (l == L - 1) ck(cudaMemcpyAsync(v.b, v.f, (size_t)v.g.total * 8, cudaMemcpyDeviceToDevice, s));
-        } else {
+        } else if (p.f_mode == ECMG_F_NODAL) {
             nodal_load(v.g, v.op, v.f, p.g_R ? v.gR : nullptr, v.b, s);
         }
         // FP64 diagonal for FP64 JCG and the direct levels, FP32 for the FP32 iteration of MIXED
@@ -788,6 +806,8 @@ ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, u
     for (int l = 0; l < p->levels; ++l) {
         Grid g = make_grid(*p, l);
         b += level_bytes(g, o->precision == ECMG_MIXED);
+        if (p->f_mode == ECMG_F_SEPARABLE) b += 8ull * (uint64_t)sep_factor_len(g, p->f_terms);
+        if (p->gD_terms > 0 && l < p->levels - 1) b += 8ull * (uint64_t)sep_factor_len(g, p->gD_terms);
         maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
         if (o->precision == ECMG_MIXED) maxb = std::max(maxb, max_tma_blocks(g));
     }
@@ -831,6 +851,8 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
             v.pA = dalloc<double>(h, n);
             v.pB = dalloc<double>(h, n);
             v.q = dalloc<double>(h, n);
+            if (prob->f_mode == ECMG_F_SEPARABLE) v.Hf = dalloc<double>(h, sep_factor_len(v.g, prob->f_terms));
+            if (prob->gD_terms > 0 && l < h->L - 1) v.Hg = dalloc<double>(h, sep_factor_len(v.g, prob->gD_terms));
             if (mixed) {
                 v.beta32 = dalloc<float>(h, n);
                 v.dinv32 = dalloc<float>(h, n);
@@ -889,6 +911,8 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
     for (int p = 0; p < n; ++p) {
         ecmg_status s = validate(probs + p, opt);
         if (s != ECMG_OK) return s;
+        if (probs[p].f_mode == ECMG_F_SEPARABLE || probs[p].gD_terms > 0 || !probs[p].beta)
+            return fail(ECMG_ERR_INVALID_ARG, "batched problems take dense beta, f and g_D");
     }
     ecmg_handle* h = new ecmg_handle();
     h->prob = probs[0];
@@ -1164,7 +1188,7 @@ const char* ecmg_last_error(void) { return g_last_error.c_str(); }
 ecmg_status ecmg_kernel_launches(uint64_t* out)
 {
     if (!out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
-    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_batch();
+    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_batch() + launches_separable();
     return ECMG_OK;
 }
 

@@ -21,7 +21,7 @@ _lib = C.CDLL(LIB_PATH)
 ECMG_OK, ECMG_ERR_INVALID_ARG, ECMG_ERR_SINGULAR, ECMG_ERR_NO_CONVERGENCE = 0, 1, 2, 3
 ECMG_ERR_BREAKDOWN, ECMG_ERR_OOM, ECMG_ERR_CUDA = 4, 5, 6
 ECMG_BC_DIRICHLET, ECMG_BC_ROBIN = 0, 1
-ECMG_F_NODAL, ECMG_F_LOAD = 0, 1
+ECMG_F_NODAL, ECMG_F_LOAD, ECMG_F_SEPARABLE = 0, 1, 2
 ECMG_FP64, ECMG_MIXED = 0, 1
 ECMG_EXP_SERENDIPITY20, ECMG_EXP_LAGRANGE27 = 0, 1
 ECMG_VEC_U, ECMG_VEC_W, ECMG_VEC_UTILDE, ECMG_VEC_B, ECMG_VEC_BETA = 0, 1, 2, 3, 4
@@ -35,7 +35,8 @@ class ecmg_problem(C.Structure):
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("face_bc", C.c_int32 * 6), ("robin_alpha", C.c_double * 6),
                 ("beta", C.c_void_p), ("f", C.c_void_p), ("g_D", C.c_void_p),
-                ("g_R", C.c_void_p), ("f_mode", C.c_int32)]
+                ("g_R", C.c_void_p), ("f_mode", C.c_int32), ("f_terms", C.c_int32), ("gD_terms", C.c_int32),
+                ("beta_const", C.c_double)]
 
 
 class ecmg_options(C.Structure):
@@ -126,10 +127,14 @@ class Solver:
     beta: finest elements (nz, ny, nx) float64 CUDA tensor; f, g_D, g_R: finest nodes
     (nz+1, ny+1, nx+1) float64 CUDA tensors (g_D, g_R optional). The tensors must outlive the
     solver and stay unchanged while a solve reads them.
+
+    Compact inputs: beta=None with beta_const > 0 (one beta everywhere); f_mode=ECMG_F_SEPARABLE
+    with f the Gauss samples of f_terms separable terms (``inputs.separable_samples``); g_D the
+    nodal factors of gD_terms separable terms (``inputs.separable_nodal``).
     """
 
     def __init__(self, n0, levels, lo, hi, face_bc, robin_alpha, beta, f, g_D=None, g_R=None,
-                 f_mode=ECMG_F_NODAL, **options):
+                 f_mode=ECMG_F_NODAL, f_terms=0, gD_terms=0, beta_const=0.0, **options):
         p = ecmg_problem()
         p.n0[:] = [int(v) for v in n0]
         p.levels = int(levels)
@@ -143,6 +148,7 @@ class Solver:
                 raise ValueError("inputs must be contiguous float64 CUDA tensors")
         p.beta, p.f, p.g_D, p.g_R = (None if t is None else t.data_ptr() for t in self._keep)
         p.f_mode = int(f_mode)
+        p.f_terms, p.gD_terms, p.beta_const = int(f_terms), int(gD_terms), float(beta_const)
         self.problem = p
         self.options = default_options(**options)
         self.levels = int(levels)
@@ -333,8 +339,9 @@ def solver_from_problem(prob: dict, device="cuda", **options):
     host arrays to the device)."""
     import torch
     t = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64).contiguous().to(device)
-    beta, f, gD, gR = t(prob["beta"]), t(prob["f"]), t(prob.get("gD")), t(prob.get("gR"))
+    beta, f, gD, gR = t(prob.get("beta")), t(prob["f"]), t(prob.get("gD")), t(prob.get("gR"))
     options.setdefault("rtol", prob.get("rtol", 1e-9))
     s = Solver(prob["n0"], prob["levels"], prob["lo"], prob["hi"], prob["face_bc"], prob["alpha"],
-               beta, f, gD, gR, f_mode=prob.get("f_mode", 0), **options)
+               beta, f, gD, gR, f_mode=prob.get("f_mode", 0), f_terms=prob.get("f_terms", 0),
+               gD_terms=prob.get("gD_terms", 0), beta_const=prob.get("beta_const", 0.0), **options)
     return s

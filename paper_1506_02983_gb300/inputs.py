@@ -10,9 +10,13 @@ Every problem is a dict with keys
     face_bc (6 ints, faces x-,x+,y-,y+,z-,z+; 0 Dirichlet, 1 Robin), alpha (6 floats),
     beta  (finest elements, shape (nz, ny, nx), float64),
     f     (finest nodes, shape (nz+1, ny+1, nx+1)),
-    gD, gR (finest nodes or None), f_mode (0 nodal f, 1 assembled load),
+    gD, gR (finest nodes or None), f_mode (0 nodal f, 1 assembled load, 2 separable f),
     u_exact (finest nodes or None), rtol (relative-residual tolerance of the workload).
 Arrays are C-ordered, so the flat index runs x fastest.
+
+Compact problems (f_mode 2) carry instead: f = the Gauss samples of f_terms separable terms
+(``separable_samples``), beta = None with beta_const, gD = the nodal factors of gD_terms
+separable terms (``separable_nodal``).
 """
 from __future__ import annotations
 
@@ -307,4 +311,84 @@ def jump_singular(levels=7, n0=(16, 8, 8), rtol=1e-8, device=None):
     face_add(n[0] // 2, 1.0, -99.0 * 1.5, -0.25)    # interface x = 1: (beta- - beta+) du/dx
     face_add(0, 0.0, 1.0, 0.75)                     # Robin data on x = 0: g_R = r^1.5
     p.update(beta=beta, f=b, gD=u, gR=None, u_exact=u)
+    return p
+
+
+def gauss3_nodes():
+    """The 3 Gauss-Legendre nodes on [0, 1] in the order the separable layout uses:
+    (1 - sqrt(3/5))/2, 1/2, (1 + sqrt(3/5))/2."""
+    r = np.sqrt(0.6)
+    return np.array([0.5 * (1.0 - r), 0.5, 0.5 * (1.0 + r)])
+
+
+def separable_samples(n, lo, hi, terms):
+    """f = sum_t fx_t(x) fy_t(y) fz_t(z) (terms: list of (fx, fy, fz) callables) sampled at the
+    3 Gauss nodes of every finest element interval: shape (T, 3 (nx + ny + nz)), per term x
+    (interval-major, 3 per interval), then y, then z."""
+    g = gauss3_nodes()
+    rows = []
+    for fac in terms:
+        row = []
+        for a in range(3):
+            h = (hi[a] - lo[a]) / n[a]
+            t = lo[a] + (np.arange(n[a])[:, None] + g[None, :]) * h
+            row.append(np.broadcast_to(np.asarray(fac[a](t), dtype=np.float64), t.shape).ravel())
+        rows.append(np.concatenate(row))
+    return np.stack(rows)
+
+
+def separable_nodal(n, lo, hi, terms):
+    """Nodal factors of g = sum_t gx_t(x) gy_t(y) gz_t(z): shape (T, (nx+1) + (ny+1) + (nz+1)),
+    per term x, then y, then z."""
+    rows = []
+    for fac in terms:
+        row = []
+        for a in range(3):
+            t = lo[a] + np.arange(n[a] + 1) * (hi[a] - lo[a]) / n[a]
+            row.append(np.broadcast_to(np.asarray(fac[a](t), dtype=np.float64), t.shape).ravel())
+        rows.append(np.concatenate(row))
+    return np.stack(rows)
+
+
+def cos_cube_compact(levels=7, n0=(8, 8, 8), rtol=1e-10, with_exact=True):
+    """cos_cube in compact form: f = 3 pi^2 cos(pi x) cos(pi y) cos(pi z) as one separable term
+    (Gauss samples), g_D = u as one separable term, beta_const = 1. O(n) input numbers instead
+    of O(n^3). with_exact=False skips the dense u_exact (the 512^3 array is 1 GiB)."""
+    p = _base(n0, levels, (0, 0, 0), (1, 1, 1), [DIRICHLET] * 6, [0.0] * 6, rtol)
+    n = finest(n0, levels)
+    c = lambda t: np.cos(PI * t)
+    cs = lambda t: (3.0 * PI * PI) * np.cos(PI * t)
+    p.update(f_mode=2, f_terms=1, f=separable_samples(n, p["lo"], p["hi"], [(cs, c, c)]),
+             gD_terms=1, gD=separable_nodal(n, p["lo"], p["hi"], [(c, c, c)]),
+             beta=None, beta_const=1.0, gR=None, u_exact=None)
+    if with_exact:
+        x, y, z = _axes(n, p["lo"], p["hi"])
+        p["u_exact"] = c(x) * c(y) * c(z)
+    return p
+
+
+def random_separable(seed, n0=(3, 2, 2), levels=3, f_terms=3, gD_terms=2, face_bc=None, rtol=1e-10):
+    """Seeded compact problem: a random box, f and g_D sums of products of random polynomials of
+    degree <= 4 in each variable (the 3-point Gauss rule integrates them times a hat exactly),
+    one random beta_const, Dirichlet faces unless face_bc says otherwise (Robin faces take
+    random alpha and homogeneous data)."""
+    rng = np.random.default_rng(seed)
+    hi = tuple(float(v) for v in rng.uniform(0.5, 2.0, 3))
+    lo = tuple(float(v) for v in rng.uniform(-0.5, 0.5, 3))
+    hi = tuple(l + d for l, d in zip(lo, hi))
+    bc = [DIRICHLET] * 6 if face_bc is None else list(face_bc)
+    alpha = [0.0 if b == DIRICHLET else float(rng.uniform(0.5, 2.0)) for b in bc]
+    p = _base(n0, levels, lo, hi, bc, alpha, rtol)
+    n = finest(n0, levels)
+
+    def poly():
+        c = rng.standard_normal(int(rng.integers(1, 6)))
+        return lambda t, c=c: np.polynomial.polynomial.polyval(t, c)
+
+    fterms = [(poly(), poly(), poly()) for _ in range(f_terms)]
+    gterms = [(poly(), poly(), poly()) for _ in range(gD_terms)]
+    p.update(f_mode=2, f_terms=f_terms, f=separable_samples(n, lo, hi, fterms),
+             gD_terms=gD_terms, gD=separable_nodal(n, lo, hi, gterms) if gD_terms else None,
+             beta=None, beta_const=float(rng.uniform(0.5, 3.0)), gR=None, u_exact=None,
+             f_factors=fterms, gD_factors=gterms)
     return p

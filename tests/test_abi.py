@@ -107,3 +107,70 @@ def test_solver_variant_options_validation_without_gpu(libpath):
     o = ecmg.default_options()
     assert o.preconditioner == ecmg.ECMG_PREC_JACOBI and o.schedule == ecmg.ECMG_SCHED_TOLERANCE
     assert o.sched_mL == 4 and o.sched_beta == 4.0 and o.inner_rtol == 1e-3
+
+
+def test_compact_input_validation_without_gpu(libpath):
+    """Separable f, separable g_D and beta_const are checked before any CUDA call; the batched
+    entry point rejects them."""
+    from paper_1506_02983_gb300 import ecmg
+
+    def prob():
+        p = ecmg.ecmg_problem()
+        p.n0[:] = [2, 2, 2]
+        p.levels = 3
+        p.lo[:] = [0, 0, 0]
+        p.hi[:] = [1, 1, 1]
+        p.f = 16
+        p.f_mode = ecmg.ECMG_F_SEPARABLE
+        p.f_terms = 1
+        p.beta_const = 1.0
+        return p
+
+    o = ecmg.default_options()
+    h = ctypes.c_void_p()
+    nbytes = ctypes.c_uint64()
+    good = prob()
+    assert ecmg.ecmg_workspace_bytes(ctypes.byref(good), ctypes.byref(o), ctypes.byref(nbytes)) == 0
+    dense = prob()
+    dense.f_mode, dense.beta = ecmg.ECMG_F_LOAD, 16
+    dense_bytes = ctypes.c_uint64()
+    assert ecmg.ecmg_workspace_bytes(ctypes.byref(dense), ctypes.byref(o), ctypes.byref(dense_bytes)) == 0
+    assert nbytes.value > dense_bytes.value  # the 1D factor arrays of every level
+    bad = []
+    for field, value in (("beta_const", 0.0), ("beta_const", float("inf")), ("f_terms", 0), ("f_terms", 65),
+                         ("g_R", 16), ("gD_terms", 1), ("gD_terms", -1), ("f_mode", 3)):
+        p = prob()
+        setattr(p, field, value)
+        bad.append((field, value, p))
+    for field, value, p in bad:
+        assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG, (field, value)
+    arr = (ecmg.ecmg_problem * 1)(prob())
+    om = ecmg.default_options(precision=ecmg.ECMG_MIXED)
+    assert ecmg.ecmg_create_batched(arr, 1, ctypes.byref(om), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+
+
+def test_problem_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of ecmg_problem and ecmg_options has the C layout (gcc on the header)."""
+    import shutil
+    import subprocess
+    from paper_1506_02983_gb300 import ecmg
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    fields = {"ecmg_problem": [f[0] for f in ecmg.ecmg_problem._fields_],
+              "ecmg_options": [f[0] for f in ecmg.ecmg_options._fields_]}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ecmg.h"', "int main(void) {"]
+    for st, names in fields.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st, st))
+        for n in names:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st, n, st, n))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for st, names in fields.items():
+        cls = getattr(ecmg, st)
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for n in names:
+            assert int(got["%s.%s" % (st, n)]) == getattr(cls, n).offset, (st, n)

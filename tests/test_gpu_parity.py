@@ -339,3 +339,90 @@ def test_problem2_anisotropic_matches_oracle(E, oracle_mod, precision):
         if precision == 0:
             assert abs(st["iters"][l] - ost["iters"][l]) <= 1, (l, st["iters"], ost["iters"])
     s.close()
+
+
+# ---- compact inputs: separable f and g_D, one beta (on-device assembly) ------------------------
+SEPARABLE = {
+    "cos_cube_compact": lambda: inputs.cos_cube_compact(levels=4, n0=(4, 4, 4), rtol=1e-10),
+    "random_separable_dirichlet": lambda: inputs.random_separable(21, n0=(3, 2, 2), levels=4),
+    "random_separable_robin": lambda: inputs.random_separable(22, n0=(2, 3, 2), levels=4, gD_terms=1,
+                                                              face_bc=[0, 1, 1, 0, 1, 0]),
+}
+
+
+def _dense_from_compact(oracle_mod, p):
+    """The same problem with dense inputs, assembled by the oracle from the compact data."""
+    L = p["levels"]
+    n = inputs.finest(p["n0"], L)
+    d = dict(p)
+    d["f"] = oracle_mod.load_separable(n, _level_h(p, L - 1), p["f_terms"], p["f"])
+    d["f_mode"] = 1
+    d["gD"] = oracle_mod.nodal_separable(n, p["gD_terms"], p["gD"]) if p["gD_terms"] else None
+    d["beta"] = np.full((n[2], n[1], n[0]), p["beta_const"])
+    for k in ("f_terms", "gD_terms", "beta_const"):
+        d.pop(k)
+    return d
+
+
+@pytest.mark.parametrize("name", sorted(SEPARABLE))
+def test_separable_setup_matches_oracle(E, oracle_mod, name):
+    """The load assembled on the device from Gauss samples (and its coarse restrictions), beta
+    from beta_const and g_D from its factors equal the oracle's definitions on every level."""
+    import torch
+    p = SEPARABLE[name]()
+    d = _dense_from_compact(oracle_mod, p)
+    s = E.solver_from_problem(p, precision=0)
+    s.solve()
+    L = p["levels"]
+    betas = _oracle_levels(oracle_mod, d)
+    load = np.asarray(d["f"]).ravel()
+    for l in range(L - 1, -1, -1):
+        n = [v << l for v in p["n0"]]
+        if l < L - 1:
+            load = oracle_mod.restrict_load(n, load)
+        b = _np(s.get(E.ECMG_VEC_B, l)).ravel()
+        assert np.abs(b - load).max() <= 1e-13 * np.abs(load).max(), (l, np.abs(b - load).max())
+        assert np.array_equal(_np(s.get(E.ECMG_VEC_BETA, l)).ravel(), betas[l]), l
+        if d["gD"] is not None:
+            step = 1 << (L - 1 - l)
+            g = np.asarray(d["gD"])[::step, ::step, ::step].ravel()
+            dirichlet = oracle_mod.dirichlet_mask(n, p["face_bc"]) == 0
+            U = _np(s.get(E.ECMG_VEC_U, l)).ravel()
+            assert np.abs(U[dirichlet] - g[dirichlet]).max() <= 1e-14 * np.abs(g).max(), l
+    s.close()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("name", sorted(SEPARABLE))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_separable_solve_matches_oracle(E, oracle_mod, name, precision):
+    p = SEPARABLE[name]()
+    d = _dense_from_compact(oracle_mod, p)
+    lv, ost = oracle_mod.ecmg(d, d["rtol"])
+    assert ost["status"] == 0
+    s = E.solver_from_problem(p, precision=precision)
+    st, status = s.solve()
+    assert status == 0, st
+    for l in range(2, p["levels"]):
+        assert st["rel_res"][l] <= p["rtol"] * 1.01, (l, st["rel_res"])
+        U = _np(s.get(E.ECMG_VEC_U, l))
+        assert _rel(U, lv[l]["U"]) <= (1e-10 if precision == 0 else 1e-7), (l, _rel(U, lv[l]["U"]))
+        if precision == 0:
+            assert abs(st["iters"][l] - ost["iters"][l]) <= 1, (l, st["iters"], ost["iters"])
+    s.close()
+
+
+def test_compact_and_dense_inputs_give_the_same_solve(E, oracle_mod):
+    """The compact path changes only how the inputs reach the device: with the oracle's dense
+    assembly of the same data, the FP64 solve agrees to rounding and takes the same steps."""
+    p = inputs.cos_cube_compact(levels=4, n0=(4, 4, 4), rtol=1e-10)
+    d = _dense_from_compact(oracle_mod, p)
+    a = E.solver_from_problem(p, precision=0)
+    b = E.solver_from_problem(d, precision=0)
+    sa, _ = a.solve()
+    sb, _ = b.solve()
+    assert all(abs(x - y) <= 1 for x, y in zip(sa["iters"], sb["iters"])), (sa["iters"], sb["iters"])
+    L = p["levels"]
+    assert _rel(_np(a.get(E.ECMG_VEC_U, L - 1)), _np(b.get(E.ECMG_VEC_U, L - 1))) <= 1e-12
+    a.close()
+    b.close()
