@@ -60,6 +60,8 @@ enum { ECMG_BC_DIRICHLET = 0, ECMG_BC_ROBIN = 1 };
  * assembled load functional b_i = f(phi_i) of Sec. 2 (coarse loads b_{l-1} = P^T b_l). */
 enum { ECMG_F_NODAL = 0, ECMG_F_LOAD = 1, ECMG_F_SEPARABLE = 2 };
 enum { ECMG_FP64 = 0, ECMG_MIXED = 1 };
+/* ecmg_apply_operator only: the FP32 stencil kernel of the MIXED iteration itself (K1). */
+enum { ECMG_APPLY_K1 = 2 };
 /* EXP_finite variant: the 20-node Serendipity interpolation of Sec. 4.3, or the 27-node
  * tri-quadratic Lagrange variant of the Remark that follows it. */
 enum { ECMG_EXP_SERENDIPITY20 = 0, ECMG_EXP_LAGRANGE27 = 1 };
@@ -175,7 +177,11 @@ ecmg_status ecmg_solve_from(ecmg_handle* h, int32_t first, double* u_out, ecmg_s
 /* y = A_l x for level `level` (-1 = finest) with the level's matrix of Sec. 2 (Robin terms
  * included, no boundary elimination): x, y device, dense nodal layout. Valid after the
  * level set-up of an ecmg_solve. precision ECMG_FP64 or ECMG_MIXED (FP32 arithmetic on FP32
- * rounded x). Ordered on the handle's stream. */
+ * rounded x). ECMG_APPLY_K1 (MIXED handles) runs the search-direction kernel of the FP32
+ * iteration (line 8 of Alg. 4 fused with q = A p) with r = 0, p_old = x and beta = 1, so it
+ * forms p = x and q = A p with the level's current tile shape and kernel path; y is q on the
+ * nodes off Dirichlet faces and 0 on them. It overwrites the level's FP32 iteration vectors.
+ * Ordered on the handle's stream. */
 ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision,
                                 const double* x, double* y);
 

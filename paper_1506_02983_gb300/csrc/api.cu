@@ -67,6 +67,7 @@ struct Level {
     PlaneMaps maps;  // TMA descriptors of the FP32 vectors
     K1Config k1{1, 128};  // tile shape of the FP32 stencil kernel
     int* uniform = nullptr;  // device flag: one beta on the whole level
+    bool cc = false;         // the FP32 stencil runs its constant-coefficient kernel (host choice)
     // 1D factors of separable data (ECMG_F_SEPARABLE load, separable g_D); Hg of the finest level
     // is the caller's array
     double *Hf = nullptr, *Hg = nullptr;
@@ -252,6 +253,9 @@ void host_state(ecmg_handle* h, int l, SolveState* out)
     ck(cudaStreamSynchronize(h->user_stream));
 }
 
+bool constant_coefficient(ecmg_handle* h, const Level& v);
+void drop_graph(ecmg_handle* h);
+
 // ---- level set-up (finest to coarsest) -------------------------------------------------------
 void record_setup(Rec& R)
 {
@@ -360,11 +364,15 @@ void record_level(Rec& R, int l)
         if (o.true_residual)
             launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, R.s());
     } else {
+        // eager: the set-up of this solve (or of the last one, for a solve from a finer level)
+        // has run, so the level's flag can be read now; a graph takes the choice made before
+        // its recording
+        if (!R.graph) v.cc = constant_coefficient(h, v);
         ck(cudaMemsetAsync(v.pA32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
         auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
-            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, v.uniform, v.beta32, v.dinv32, pout, v.q32, v.e32,
+            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pout, v.q32, v.e32,
                             st, h->part, idx, ch, h->timers + l, R.s());
             launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
         };
@@ -420,11 +428,19 @@ void record_solve(Rec& R, int first)
     for (int l = first; l < R.h->L; ++l) record_level(R, l);
 }
 
-ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stats)
+ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stats, bool retried = false)
 {
     try {
         if (h->opt.use_graph) {
             if (!h->exec || h->graph_first != first) {
+                // the FP32 stencil path of each level is fixed in the recording: run the set-up
+                // once outside the graph so that the levels' uniform flags are current
+                if (first == 0) {
+                    Rec E{h, false, 0};
+                    record_setup(E);
+                }
+                for (int l = std::max(first, 2); l < h->L; ++l)
+                    h->lv[l].cc = h->opt.precision == ECMG_MIXED && constant_coefficient(h, h->lv[l]);
                 if (h->exec) {
                     cudaGraphExecDestroy(h->exec);
                     h->exec = nullptr;
@@ -461,6 +477,14 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
     } catch (CudaFail& f) {
         return fail(ECMG_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(f.e));
     }
+    // a level whose recorded constant-coefficient path no longer holds (its beta changed under
+    // the graph) computed nothing: record again with the current flags and solve again
+    bool stale = false;
+    for (int l = first; l < h->L; ++l) stale |= h->host_states[l].status == 6;
+    if (stale && !retried) {
+        drop_graph(h);
+        return run_solve(h, first, u_out, stats, true);
+    }
     ecmg_status worst = ECMG_OK;
     ecmg_stats st;
     memset(&st, 0, sizeof(st));
@@ -478,6 +502,7 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
         if (s.status == 3) ls = ECMG_ERR_NO_CONVERGENCE;
         if (s.status == 4) ls = ECMG_ERR_BREAKDOWN;
         if (s.status == 5) ls = ECMG_ERR_CUDA;  // a staged copy of the FP32 stencil never arrived
+        if (s.status == 6) ls = ECMG_ERR_CUDA;  // stale stencil path after a fresh recording (not expected)
         if (ls == ECMG_ERR_BREAKDOWN || (ls != ECMG_OK && worst == ECMG_OK)) worst = ls;
     }
     st.status = worst;
@@ -695,6 +720,7 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
         ck(cudaMemcpyAsync(&last, h->states + l, sizeof(last), cudaMemcpyDeviceToHost, s));
         ck(cudaStreamSynchronize(s));
         tmpl.bcbits = last.bcbits;
+        const bool cc = which == 0 && constant_coefficient(h, v);
         ck(cudaEventCreate(&e0));
         ck(cudaEventCreate(&e1));
         for (int rep = 0; rep <= reps; ++rep) {
@@ -702,7 +728,7 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
             ck(cudaEventRecord(e0, s));
             switch (which) {
             case 0:
-                launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32, v.e32, st,
+                launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, cc, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32, v.e32, st,
                                 h->part, 1, none, nullptr, s);
                 break;
             case 1: launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
@@ -1114,6 +1140,33 @@ ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision
         launch_apply32(v.g, v.op, v.beta32, v.r32, v.q, s);
     } else if (precision == ECMG_FP64) {
         launch_apply64(v.g, v.op, v.beta, v.uniform, v.r, v.q, h->part, s);
+    } else if (precision == ECMG_APPLY_K1) {
+        if (!v.r32) return fail(ECMG_ERR_INVALID_ARG, "handle was created without MIXED precision");
+        // p = D^-1 r + beta p_old with r = 0, beta = 1: p = x; q = A p; alpha_prev = 0: e untouched
+        SolveState* st = h->states + (MAX_LEVELS - 1);
+        SolveState tmpl = {};
+        tmpl.rho = 1.0;
+        tmpl.beta = 1.0;
+        tmpl.alpha = 1.0;
+        tmpl.max_iters = 1 << 30;
+        tmpl.thresh2 = -1.0;
+        tmpl.inner2 = -1.0;
+        const size_t n4 = (size_t)v.g.total * 4;
+        const CondHandles none{0, 0, 0};
+        cudaError_t e = cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(v.r32, 0, n4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(v.q32, 0, n4, s);
+        if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
+        convert_f32(v.r, v.pA32, v.g.total, s);
+        bool cc = false;
+        try {
+            cc = constant_coefficient(h, v);
+        } catch (CudaFail& f) {
+            return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+        }
+        launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, cc, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32, v.e32, st, h->part,
+                        1, none, nullptr, s);
+        convert_f64(v.q32, v.q, v.g.total, s);
     } else {
         return fail(ECMG_ERR_INVALID_ARG, "bad precision");
     }

@@ -100,7 +100,8 @@ struct SolveState {
     int iters;           // JCG iterations done
     int updates;         // MIXED: FP64 residual replacements done
     int max_iters;
-    int status;          // 0 running/ok, 3 no convergence, 4 breakdown
+    int status;          // 0 running/ok, 3 no convergence, 4 breakdown, 5 a staged copy never arrived,
+                         // 6 stale constant-coefficient stencil path (the level computed nothing)
     int done;            // 1 when the level has finished
     int need_update;     // MIXED: 1 when the next step is an FP64 residual replacement
     int stop_after_update; // MIXED: iteration cap reached, finish after the next replacement
@@ -153,6 +154,7 @@ void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64
 void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x,
                          cudaStream_t s);
 void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+void convert_f64(const float* src, double* dst, int64_t n, cudaStream_t s);
 // flag = 1 when every element of the level has the same beta, else 0.
 void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s);
 

@@ -45,19 +45,13 @@ struct Shape {
     static constexpr uint32_t STAGE_BYTES = 4u * BOXF * sizeof(float);
 };
 
-template <int RY>
-struct __align__(128) Stage {
-    float r[Shape<RY>::BOXF_PAD];
-    float pold[Shape<RY>::BOXF_PAD];
-    float dinv[Shape<RY>::BOXF_PAD];
-    float beta[Shape<RY>::BOXF_PAD];
-};
-// Dynamic shared memory of a block: the stage ring plus slack to align it to 128 B (TMA
-// destinations must be 128-byte aligned; the runtime only guarantees 16).
-template <int RY>
+// Dynamic shared memory of a block: the stage ring (NA staged arrays per stage: r, p_old and,
+// on the general path, D^-1 and beta) plus slack to align it to 128 B (TMA destinations must
+// be 128-byte aligned; the runtime only guarantees 16).
+template <int RY, int NA>
 constexpr size_t stage_smem()
 {
-    return NSTAGE * sizeof(Stage<RY>) + 128;
+    return (size_t)NSTAGE * NA * Shape<RY>::BOXF_PAD * sizeof(float) + 128;
 }
 
 // Nodes K1 visits: every node not on a Dirichlet face (those keep p = q = 0).
@@ -149,9 +143,38 @@ __device__ __forceinline__ void block_sum(double (&v)[NP], double* sh)
     __syncthreads();
 }
 
+// Constant-coefficient operator by plane sums. With one beta bu on the level, every node the
+// kernel visits interior, and the 27-point stencil of q1_interior written per plane: for the
+// node column (i, j) and plane z let X(z) be p at the column, Fx(z) and Fy(z) the sums of the
+// differences p - X(z) over the two x and the two y neighbours in that plane, and D(z) the sum
+// of the differences over the four diagonal neighbours. Then, with dm = X(k-1) - X(k) and
+// dp = X(k+1) - X(k),
+//   (A p)(k) = bu [ 4 wf0 Fx(k) + 4 wf1 Fy(k) + 2 we0 (Fy(k-1) + Fy(k+1))
+//                   + 2 we1 (Fx(k-1) + Fx(k+1)) + 2 we2 D(k) + wc (D(k-1) + D(k+1))
+//                   + 4 (wf2 + we0 + we1 + wc) (dm + dp) ],
+// since every neighbour difference splits into an in-plane difference plus dm or dp. The
+// plane sums of a new plane are formed once and reused by the three nodes that need them, so
+// the stencil costs about half the arithmetic of the element form; every term is still a
+// difference of neighbouring values (the FP32 accuracy of the difference form). For cubic
+// elements wf = 0 and we = wc, and Fx + Fy is kept as one sum.
+template <int RY>
+struct PlaneSums {
+    float x[RY], fx[RY], fy[RY], d[RY];
+};
+struct CCWeights {
+    float fx0, fy0, ey, ex, d0, c, z;  // the coefficients above, times bu
+    float e_cube, z_cube;              // cubic elements: 2 wc bu and 12 wc bu
+    __device__ __forceinline__ CCWeights(const Weights<float>& w, float bu)
+        : fx0(4.f * w.wf0 * bu), fy0(4.f * w.wf1 * bu), ey(2.f * w.we0 * bu), ex(2.f * w.we1 * bu),
+          d0(2.f * w.we2 * bu), c(w.wc * bu), z(4.f * (w.wf2 + w.we0 + w.we1 + w.wc) * bu),
+          e_cube(2.f * w.wc * bu), z_cube(12.f * w.wc * bu)
+    {
+    }
+};
+
 // CC: constant coefficient -- one beta on the whole level and every face Dirichlet, so every
 // node the kernel visits is interior with the same diagonal: beta and D^-1 are not streamed
-// (bu and cdinv hold their values; the results are the same bits as with the arrays).
+// (bu and cdinv hold their values) and the operator takes the plane-sum form above.
 template <bool ROBIN, bool CUBE, int RY, bool CC>
 __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMap& m_pold, const CUtensorMap& m_dinv,
                                         const CUtensorMap& m_beta, const Grid& g, const Op& op, const Range& rg,
@@ -233,6 +256,8 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     float wA[RY + 2][3], wB[RY + 2][3], wC[RY + 2][3];  // three planes of the p window, [y][x]
     float bA[RY + 1][2], bB[RY + 1][2];                 // element betas of two slabs, [ey][ex]
     float pown_prev[RY], e_cur[RY];                     // p_old and e of the own nodes, plane k
+    PlaneSums<RY> sA, sB, sC;                           // CC: plane sums of three planes
+    const CCWeights cw(wts, bu);
 #pragma unroll
     for (int r = 0; r < RY; ++r) pown_prev[r] = e_cur[r] = 0.f;
     CSum acc;
@@ -245,7 +270,8 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     // and the slabs (bo, bn) = (kk-2, kk-1). The caller rotates the arrays instead of moving
     // values, so the unrolled loop below needs no register copies.
     auto step = [&](float(&wm)[RY + 2][3], float(&w0)[RY + 2][3], float(&wp)[RY + 2][3],
-                    float(&bo)[RY + 1][2], float(&bn)[RY + 1][2]) {
+                    float(&bo)[RY + 1][2], float(&bn)[RY + 1][2], PlaneSums<RY>& sm, PlaneSums<RY>& s0,
+                    PlaneSums<RY>& sp) {
         const int kk = P0 + t;
         const float* Sr = box(t, 0);
         const float* Sp = box(t, 1);
@@ -279,11 +305,23 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
             issued_hi = t - 1 + NS;
         }
         const float(*Pp)[S::PX] = P[kk & 1];
+        if (CC) {
 #pragma unroll
-        for (int yy = 0; yy < RY + 2; ++yy)
+            for (int r = 0; r < RY; ++r) {
+                const float* c0 = &Pp[ty * RY + r + 1][tx + 1];
+                const float c = c0[0];
+                const float fx = (c0[-1] - c) + (c0[1] - c);
+                const float fy = (c0[-S::PX] - c) + (c0[S::PX] - c);
+                sp.x[r] = c;
+                sp.fx[r] = CUBE ? fx + fy : fx;
+                sp.fy[r] = fy;
+                sp.d[r] = ((c0[-S::PX - 1] - c) + (c0[-S::PX + 1] - c)) + ((c0[S::PX - 1] - c) + (c0[S::PX + 1] - c));
+            }
+        } else {
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) wp[yy][dx] = Pp[ty * RY + yy][tx + dx];
-        if (!CC) {
+            for (int yy = 0; yy < RY + 2; ++yy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) wp[yy][dx] = Pp[ty * RY + yy][tx + dx];
             const float* Sb = Sbeta + ty * RY * SX + tx + sh;
 #pragma unroll
             for (int yy = 0; yy < RY + 1; ++yy)
@@ -300,13 +338,27 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
                         return dz < 0 ? wm[r + 1 + dy][dx + 1]
                                       : (dz > 0 ? wp[r + 1 + dy][dx + 1] : w0[r + 1 + dy][dx + 1]);
                     };
-                    const float xc = w0[r + 1][1];
-                    const float Av =
-                        CC ? q1_apply<false, ROBIN, CUBE, float>(V, bu, bu, bu, bu, bu, bu, bu, bu, i, jt + r, k, g, op,
-                                                                 wts)
-                           : q1_apply<false, ROBIN, CUBE, float>(V, bo[r][0], bo[r][1], bo[r + 1][0], bo[r + 1][1],
+                    float xc, Av;
+                    if (CC) {
+                        xc = s0.x[r];
+                        const float dz = (sm.x[r] - xc) + (sp.x[r] - xc);
+                        if (CUBE) {
+                            Av = fmaf(cw.z_cube, dz,
+                                      fmaf(cw.c, sm.d[r] + sp.d[r], cw.e_cube * ((sm.fx[r] + sp.fx[r]) + s0.d[r])));
+                        } else {
+                            Av = fmaf(cw.z, dz,
+                                      fmaf(cw.c, sm.d[r] + sp.d[r],
+                                           fmaf(cw.d0, s0.d[r],
+                                                fmaf(cw.ex, sm.fx[r] + sp.fx[r],
+                                                     fmaf(cw.ey, sm.fy[r] + sp.fy[r],
+                                                          fmaf(cw.fy0, s0.fy[r], cw.fx0 * s0.fx[r]))))));
+                        }
+                    } else {
+                        xc = w0[r + 1][1];
+                        Av = q1_apply<false, ROBIN, CUBE, float>(V, bo[r][0], bo[r][1], bo[r + 1][0], bo[r + 1][1],
                                                                  bn[r][0], bn[r][1], bn[r + 1][0], bn[r + 1][1], i,
                                                                  jt + r, k, g, op, wts);
+                    }
                     const int64_t orr = o + r * pitch;
                     pnew[orr] = xc;
                     q[orr] = Av;
@@ -325,17 +377,17 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     };
     // period 6 = lcm(3 window planes, 2 beta slabs)
     for (;;) {
-        step(wA, wB, wC, bA, bB);
+        step(wA, wB, wC, bA, bB, sA, sB, sC);
         if (stop) break;
-        step(wB, wC, wA, bB, bA);
+        step(wB, wC, wA, bB, bA, sB, sC, sA);
         if (stop) break;
-        step(wC, wA, wB, bA, bB);
+        step(wC, wA, wB, bA, bB, sC, sA, sB);
         if (stop) break;
-        step(wA, wB, wC, bB, bA);
+        step(wA, wB, wC, bB, bA, sA, sB, sC);
         if (stop) break;
-        step(wB, wC, wA, bA, bB);
+        step(wB, wC, wA, bA, bB, sB, sC, sA);
         if (stop) break;
-        step(wC, wA, wB, bB, bA);
+        step(wC, wA, wB, bB, bA, sC, sA, sB);
         if (stop) break;
     }
 
@@ -387,24 +439,43 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     }
 }
 
-template <bool ROBIN, bool CUBE, int RY, bool DIRI>
+// General path: beta and D^-1 streamed with r and p_old.
+template <bool ROBIN, bool CUBE, int RY>
 __global__ void __launch_bounds__(NT, RY == 1 ? (ROBIN ? 3 : 4) : 2)
 k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
            const __grid_constant__ CUtensorMap m_dinv, const __grid_constant__ CUtensorMap m_beta,
            const Grid g, const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q,
            float* __restrict__ e, SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
-           KTimer* tm, const int* __restrict__ uniform, const float* __restrict__ beta32,
-           const float* __restrict__ dinv32)
+           KTimer* tm)
 {
     COUNT_LAUNCH();
-    // DIRI: every face Dirichlet (host); *uniform: one beta on the level (device set-up)
-    if (DIRI && *uniform) {
-        k1_body<ROBIN, CUBE, RY, true>(m_r, m_pold, m_dinv, m_beta, g, op, rg, pnew, q, e, st, partials, pidx, ch,
-                                       kz, tm, dinv32[g.off(1, 1, 1)], beta32[g.off(0, 0, 0)]);
-        return;
-    }
     k1_body<ROBIN, CUBE, RY, false>(m_r, m_pold, m_dinv, m_beta, g, op, rg, pnew, q, e, st, partials, pidx, ch, kz,
                                     tm, 0.f, 0.f);
+}
+
+// Constant-coefficient path (every face Dirichlet, one beta on the level): r and p_old only,
+// and about half the registers of the general path, so six blocks fit on an SM instead of
+// four. The host picks it from the level's uniform flag after the set-up; should a later
+// set-up clear the flag (new beta data under a recorded graph), the kernel computes nothing
+// and records status 6 so that the host records the solve again with the general path.
+template <bool CUBE, int RY>
+__global__ void __launch_bounds__(NT, RY == 1 ? 6 : 2)
+k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold, const Grid g,
+          const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e,
+          SolveState* st, double* partials, int pidx, CondHandles ch, int kz, KTimer* tm,
+          const int* __restrict__ uniform, const float* __restrict__ beta32, const float* __restrict__ dinv32)
+{
+    COUNT_LAUNCH();
+    if (!*uniform) {
+        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0 && !st->done) {
+            st->status = 6;
+            st->done = 1;
+            if (ch.use) cudaGraphSetConditional(ch.loop, 0);
+        }
+        return;
+    }
+    k1_body<false, CUBE, RY, true>(m_r, m_pold, m_r, m_r, g, op, rg, pnew, q, e, st, partials, pidx, ch, kz, tm,
+                                   dinv32[g.off(1, 1, 1)], beta32[g.off(0, 0, 0)]);
 }
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -448,11 +519,17 @@ bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool ROBIN, bool CUBE, int RY, bool DIRI = false>
+template <bool ROBIN, bool CUBE, int RY>
 cudaError_t prepare_one()
 {
-    return cudaFuncSetAttribute(k_pq32_tma<ROBIN, CUBE, RY, DIRI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stage_smem<RY>());
+    return cudaFuncSetAttribute(k_pq32_tma<ROBIN, CUBE, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem<RY, 4>());
+}
+template <bool CUBE, int RY>
+cudaError_t prepare_cc()
+{
+    return cudaFuncSetAttribute(k_pq32_cc<CUBE, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_smem<RY, 2>());
 }
 
 template <int RY>
@@ -462,30 +539,32 @@ cudaError_t prepare_ry()
     if (e == cudaSuccess) e = prepare_one<false, true, RY>();
     if (e == cudaSuccess) e = prepare_one<true, false, RY>();
     if (e == cudaSuccess) e = prepare_one<true, true, RY>();
-    if (e == cudaSuccess) e = prepare_one<false, false, RY, true>();
-    if (e == cudaSuccess) e = prepare_one<false, true, RY, true>();
+    if (e == cudaSuccess) e = prepare_cc<false, RY>();
+    if (e == cudaSuccess) e = prepare_cc<true, RY>();
     return e;
 }
 
 template <int RY>
-void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, const int* uniform,
-               const float* beta32, const float* dinv32, float* pnew, float* q, float* e, SolveState* st, Partials pr,
-               int pidx, CondHandles ch, KTimer* tm, cudaStream_t s)
+void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
+               const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
+               SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s)
 {
     const int v = ry_index(RY);
     const Range rg = k1_range(g, op);
-    bool robin = false, diri = true;
-    for (int f = 0; f < 6; ++f) {
-        robin |= op.alpha[f] != 0.0;
-        diri &= op.bc[f] == 0;
+    const CUtensorMap& pold = pold_is_b ? m.pB[v] : m.pA[v];
+    if (cc) {
+        auto kern = op.cube ? k_pq32_cc<true, RY> : k_pq32_cc<false, RY>;
+        kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, 2>(), s>>>(m.r[v], pold, g, op, rg, pnew, q, e, st,
+                                                                         pr.buf, pidx, ch, c.kz, tm, uniform, beta32,
+                                                                         dinv32);
+        return;
     }
-    diri &= uniform != nullptr;
-    auto kern = robin  ? (op.cube ? k_pq32_tma<true, true, RY, false> : k_pq32_tma<true, false, RY, false>)
-                : diri ? (op.cube ? k_pq32_tma<false, true, RY, true> : k_pq32_tma<false, false, RY, true>)
-                       : (op.cube ? k_pq32_tma<false, true, RY, false> : k_pq32_tma<false, false, RY, false>);
-    kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY>(), s>>>(m.r[v], pold_is_b ? m.pB[v] : m.pA[v], m.dinv[v],
-                                                                  m.beta[v], g, op, rg, pnew, q, e, st, pr.buf,
-                                                                  pidx, ch, c.kz, tm, uniform, beta32, dinv32);
+    bool robin = false;
+    for (int f = 0; f < 6; ++f) robin |= op.alpha[f] != 0.0;
+    auto kern = robin ? (op.cube ? k_pq32_tma<true, true, RY> : k_pq32_tma<true, false, RY>)
+                      : (op.cube ? k_pq32_tma<false, true, RY> : k_pq32_tma<false, false, RY>);
+    kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, 4>(), s>>>(m.r[v], pold, m.dinv[v], m.beta[v], g, op, rg,
+                                                                     pnew, q, e, st, pr.buf, pidx, ch, c.kz, tm);
 }
 
 }  // namespace
@@ -551,12 +630,13 @@ int max_tma_blocks(const Grid& g)
     return cdiv(g.nx + 1, TBX) * cdiv(g.ny + 1, TBY) * cdiv(g.nz + 1, 4);
 }
 
-void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op,
+void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
                      const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
                      SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s)
 {
-    if (c.ry == 1) launch_ry<1>(m, pold_is_b, c, g, op, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
-    else launch_ry<2>(m, pold_is_b, c, g, op, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
+    if (c.ry == 1)
+        launch_ry<1>(m, pold_is_b, c, g, op, cc, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
+    else launch_ry<2>(m, pold_is_b, c, g, op, cc, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
 }
 
 unsigned long long launches_pq_tma()

@@ -39,10 +39,12 @@ int64_t k1_nodes(const Grid& g, const Op& op);
 int max_tma_blocks(const Grid& g);
 
 // p = D^-1 r + beta p_old (p_old = pA or pB), q = A p, e += alpha_prev p_old, p.q.
-// uniform: the level's device flag (one beta everywhere); with every face Dirichlet and the flag
-// set, beta and D^-1 are constants read once from beta32 and dinv32 instead of streamed.
+// cc: the constant-coefficient kernel (the caller has seen every face Dirichlet and the level's
+// device flag `uniform` set: one beta everywhere); beta and D^-1 are then constants read once
+// from beta32 and dinv32 instead of streamed. If the flag is clear when the kernel runs, it
+// records status 6 (stale path) in st and finishes the level without computing.
 // tm: device timer that accumulates the durations of these launches, or nullptr.
-void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op,
+void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
                      const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
                      SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s);
 

@@ -143,6 +143,13 @@ __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict_
         dst[t] = (float)src[t];
 }
 
+__global__ void k_convert_f64(const float* __restrict__ src, double* __restrict__ dst, int64_t n)
+{
+    COUNT_LAUNCH();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (double)src[t];
+}
+
 }  // namespace
 
 void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s)
@@ -155,6 +162,12 @@ void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s)
 {
     int b = blocks_for(n);
     k_convert_f32<<<b < 4096 ? b : 4096, TPB, 0, s>>>(src, dst, n);
+}
+
+void convert_f64(const float* src, double* dst, int64_t n, cudaStream_t s)
+{
+    int b = blocks_for(n);
+    k_convert_f64<<<b < 4096 ? b : 4096, TPB, 0, s>>>(src, dst, n);
 }
 
 void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s)

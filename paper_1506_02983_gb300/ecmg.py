@@ -23,6 +23,7 @@ ECMG_ERR_BREAKDOWN, ECMG_ERR_OOM, ECMG_ERR_CUDA = 4, 5, 6
 ECMG_BC_DIRICHLET, ECMG_BC_ROBIN = 0, 1
 ECMG_F_NODAL, ECMG_F_LOAD, ECMG_F_SEPARABLE = 0, 1, 2
 ECMG_FP64, ECMG_MIXED = 0, 1
+ECMG_APPLY_K1 = 2  # ecmg_apply_operator: the FP32 search-direction kernel itself
 ECMG_EXP_SERENDIPITY20, ECMG_EXP_LAGRANGE27 = 0, 1
 ECMG_VEC_U, ECMG_VEC_W, ECMG_VEC_UTILDE, ECMG_VEC_B, ECMG_VEC_BETA = 0, 1, 2, 3, 4
 ECMG_PREC_JACOBI, ECMG_PREC_NONE = 0, 1

@@ -426,3 +426,71 @@ def test_compact_and_dense_inputs_give_the_same_solve(E, oracle_mod):
     assert _rel(_np(a.get(E.ECMG_VEC_U, L - 1)), _np(b.get(E.ECMG_VEC_U, L - 1))) <= 1e-12
     a.close()
     b.close()
+
+
+# ---- the FP32 search-direction kernel (K1) itself, on every path and tile shape -----------------
+K1_PROBLEMS = {
+    # one beta, every face Dirichlet: the constant-coefficient path
+    "exp_cube": lambda: inputs.exp_cube(levels=4, rtol=1e-10),
+    "cos_cube_ragged": lambda: inputs.cos_cube(levels=3, n0=(9, 5, 7), rtol=1e-8),
+    # general path: variable beta, Robin faces, non-cubic elements
+    "random_mixed_bc_0": lambda: inputs.random_problem(0, n0=(2, 3, 2), levels=4, rtol=1e-10),
+    "variable_box": lambda: inputs.variable_box(levels=3, n0=(2, 2, 4), rtol=1e-9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(K1_PROBLEMS))
+@pytest.mark.parametrize("tiles", [None, (1, 4), (2, 4), (2, 7)])
+def test_k1_operator_matches_csr(E, oracle_mod, name, tiles):
+    """q = A p from the kernel the MIXED iteration runs (ECMG_APPLY_K1) against the oracle's
+    assembled matrix on the nodes off Dirichlet faces: FP32 bar 1e-5 of max |A x|. Small kz
+    spreads a level over several z-blocks with a ragged last one."""
+    import torch
+    p = K1_PROBLEMS[name]()
+    s = E.solver_from_problem(p, precision=1)
+    s.solve()
+    betas = _oracle_levels(oracle_mod, p)
+    for l in range(2, p["levels"]):
+        if tiles is not None:
+            s.set_tiles(tiles[0], tiles[1], level=l)
+        n = [v << l for v in p["n0"]]
+        A = oracle_mod.assemble(n, _level_h(p, l), betas[l], p["face_bc"], p["alpha"])
+        free = oracle_mod.dirichlet_mask(n, p["face_bc"]) == 1
+        x = inputs.random_vector(300 + l, (n[2] + 1, n[1] + 1, n[0] + 1))
+        want = A.matvec(x.ravel())
+        got = _np(s.apply(torch.tensor(x, device="cuda"), level=l, precision=E.ECMG_APPLY_K1)).ravel()
+        scale = np.abs(want[free]).max()
+        assert np.abs(got[free] - want[free]).max() <= 1e-5 * scale, (l, np.abs(got[free] - want[free]).max() / scale)
+        assert np.all(got[~free] == 0.0)
+    s.close()
+
+
+def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_mod):
+    """A MIXED graph recorded while beta was uniform runs the constant-coefficient stencil
+    kernel; after the caller rewrites beta in place with a variable field, the next solve must
+    notice (the kernel checks the level flag), record again with the general kernel and give
+    the same result as a fresh handle."""
+    import torch
+    p = inputs.exp_cube(levels=4, rtol=1e-10)
+    q = inputs.random_problem(3, n0=(4, 4, 4), levels=4, rtol=1e-10, face_bc=[0] * 6)
+    beta = torch.ones(np.asarray(p["beta"]).shape, dtype=torch.float64, device="cuda")
+    f = torch.tensor(np.asarray(p["f"]), device="cuda")
+    gD = torch.tensor(np.asarray(p["gD"]), device="cuda")
+    s = E.Solver(p["n0"], p["levels"], p["lo"], p["hi"], p["face_bc"], p["alpha"], beta, f, gD, None,
+                 rtol=1e-10, precision=1)
+    st1, status = s.solve()
+    assert status == 0, st1
+    beta.copy_(torch.tensor(np.asarray(q["beta"]), device="cuda"))
+    st2, status = s.solve()
+    assert status == 0, st2
+    U2 = _np(s.get(E.ECMG_VEC_U, -1))
+    d = dict(p, beta=np.asarray(q["beta"]))
+    fresh = E.solver_from_problem(d, precision=1)
+    st3, status = fresh.solve()
+    assert status == 0
+    assert st2["iters"] == st3["iters"], (st2["iters"], st3["iters"])
+    assert np.array_equal(U2, _np(fresh.get(E.ECMG_VEC_U, -1)))
+    lv, ost = oracle_mod.ecmg(d, d["rtol"])
+    assert _rel(U2, lv[-1]["U"]) <= 1e-7
+    s.close()
+    fresh.close()
