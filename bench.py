@@ -56,6 +56,8 @@ def parse():
                     help="profiling run: one MIXED solve, then kernel W of ecmg_time_kernel on the finest level, "
                          "3 launches inside the NVTX range kernel_profile (for ncu -k / --nvtx-include); prints "
                          "one JSON line and exits")
+    ap.add_argument("--profile-tiles", default=None,
+                    help="with --profile-kernel 0: the K1 tile shape ry,kz of the finest level (as autotuned in the bench)")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven level loops instead of one CUDA graph per solve (same kernels); "
                          "ncu cannot profile kernel nodes of graphs that hold conditional nodes")
@@ -187,6 +189,9 @@ def profile_kernel(args):
     p = inputs.cos_cube(levels=args.levels, n0=(args.n0,) * 3, rtol=args.rtol)
     s = ecmg.solver_from_problem(p, precision=ecmg.ECMG_MIXED, max_iters=args.max_iters)
     st, status = s.solve()
+    if args.profile_tiles:
+        ry, kz = (int(v) for v in args.profile_tiles.split(","))
+        s.set_tiles(ry, kz, -1)
     torch.cuda.nvtx.range_push("kernel_profile")
     ms, nb = s.time_kernel(args.profile_kernel, -1, reps=2)
     torch.cuda.nvtx.range_pop()

@@ -887,7 +887,7 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
                 v.pB32 = dalloc<float>(h, n);
                 v.q32 = dalloc<float>(h, n);
                 v.e32 = dalloc<float>(h, n);
-                if (!make_plane_maps(&v.maps, v.r32, v.pA32, v.pB32, v.dinv32, v.beta32, v.g))
+                if (!make_plane_maps(&v.maps, v.r32, v.pA32, v.pB32, v.dinv32, v.beta32, v.e32, v.g))
                     throw CudaFail{cudaErrorNotSupported};
                 v.k1 = k1_default(v.g, v.op);
                 maxb = std::max(maxb, max_tma_blocks(v.g));

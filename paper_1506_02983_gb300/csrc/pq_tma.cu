@@ -1,14 +1,16 @@
 // pq_tma.cu -- K1 of the FP32 JCG iteration with TMA-staged planes.
 //
-// Per block: a TBX x TBY column of nodes over a range of planes. A 4-stage ring of shared
-// memory buffers receives, for every node plane k, boxes of r, p_old, D^-1 (plane k) and beta
+// Per block: a TBX x TBY column of nodes over a range of planes. A ring of shared memory
+// buffers receives, for every node plane k, boxes of r, p_old, D^-1 (plane k) and beta
 // (element slab k-1) by cp.async.bulk.tensor, each stage completing on its own mbarrier.
-// One elected thread issues the copies NSTAGE planes ahead, so HBM latency is hidden behind
+// One elected thread issues the copies several planes ahead, so HBM latency is hidden behind
 // the stencil of the current plane. For each staged plane the block forms the new search
 // direction p = D^-1 r + beta p_old once per node (tile plus halo) into a small plane buffer;
 // every thread then keeps a 3x3x3 window of p and the 2x2x2 element betas of its node in
 // registers while marching in z, so the 27-point stencil reads only 9 new values of p and 4
-// new betas per node from shared memory.
+// new betas per node from shared memory. On a constant-coefficient level (one beta, every face
+// Dirichlet) a kernel of its own stages r and p_old only and keeps three plane sums per node
+// column instead of the window.
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel records ECMG status 5 in the
 // level state, finishes the level, waits (bounded) for its own copies still in flight and
@@ -29,7 +31,9 @@ __device__ unsigned long long g_launches = 0;  // kernel executions of this file
 
 constexpr int TBX = 32, TBY = 8, NT = TBX * TBY;
 constexpr int SX = 40;                     // staged columns: from the 16-byte boundary at or below node i0-1
-constexpr int NSTAGE = 4;
+constexpr int EX = 36;                     // staged columns of e (no halo needed; 16-byte multiple)
+constexpr int NSTAGE = 4;                  // ring stages of the general path (4 staged arrays each)
+constexpr int NSTAGE_CC = 6;               // constant-coefficient path (2 staged arrays each; 4 and 8 measured slower)
 constexpr long long WAIT_LIMIT = 1ll << 22; // polls before a wait is declared lost
 
 // Sizes of a tile whose threads compute RY node rows each.
@@ -42,16 +46,18 @@ struct Shape {
     static constexpr int PX = TBX + 2, PY = NY + 2;       // formed plane of p: tile plus one-node halo
     static constexpr int NCELL = PX * PY;
     static constexpr int NFORM = (NCELL + NT - 1) / NT;   // formed cells per thread (at most)
-    static constexpr uint32_t STAGE_BYTES = 4u * BOXF * sizeof(float);
+    static constexpr int EBOXF = EX * NY;                 // floats of the staged e (own rows only)
+    static constexpr int EBOXF_PAD = (EBOXF + 31) / 32 * 32;
 };
 
 // Dynamic shared memory of a block: the stage ring (NA staged arrays per stage: r, p_old and,
-// on the general path, D^-1 and beta) plus slack to align it to 128 B (TMA destinations must
-// be 128-byte aligned; the runtime only guarantees 16).
+// on the general path, D^-1 and beta; then e of the tile's own rows) plus slack to align it to
+// 128 B (TMA destinations must be 128-byte aligned; the runtime only guarantees 16).
 template <int RY, int NA>
 constexpr size_t stage_smem()
 {
-    return (size_t)NSTAGE * NA * Shape<RY>::BOXF_PAD * sizeof(float) + 128;
+    return (size_t)(NA == 2 ? NSTAGE_CC : NSTAGE) * (NA * Shape<RY>::BOXF_PAD + Shape<RY>::EBOXF_PAD) * sizeof(float) +
+           128;
 }
 
 // Nodes K1 visits: every node not on a Dirichlet face (those keep p = q = 0).
@@ -175,29 +181,39 @@ struct CCWeights {
 // CC: constant coefficient -- one beta on the whole level and every face Dirichlet, so every
 // node the kernel visits is interior with the same diagonal: beta and D^-1 are not streamed
 // (bu and cdinv hold their values) and the operator takes the plane-sum form above.
+// Scalars a K1 block needs before its first plane, loaded together at kernel entry so that the
+// block pays one global-memory round trip for them.
+struct K1Scalars {
+    int done;     // the level has finished: nothing to do
+    float bcg;    // beta of the CG recurrence
+    float ap;     // alpha of the previous step (deferred correction e += ap p_old)
+    float cdinv;  // CC: the constant D^-1
+    float bu;     // CC: the constant beta
+};
+
 template <bool ROBIN, bool CUBE, int RY, bool CC>
 __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMap& m_pold, const CUtensorMap& m_dinv,
-                                        const CUtensorMap& m_beta, const Grid& g, const Op& op, const Range& rg,
-                                        float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e,
-                                        SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
-                                        KTimer* tm, float cdinv, float bu)
+                                        const CUtensorMap& m_beta, const CUtensorMap& m_e, const Grid& g, const Op& op,
+                                        const Range& rg, float* __restrict__ pnew, float* __restrict__ q,
+                                        float* __restrict__ e, SolveState* st, double* partials, int pidx,
+                                        CondHandles ch, int kz, KTimer* tm, const K1Scalars sc)
 {
     using S = Shape<RY>;
     extern __shared__ __align__(128) unsigned char k1_smem[];
-    // the ring of staged boxes: NS stages of NA arrays (r, p_old[, D^-1, beta]). The constant-
-    // coefficient path stages two arrays; holding twice as many planes in flight there measured
-    // slower (the kernel is issue-bound), so both paths keep NSTAGE stages.
-    constexpr int NA = CC ? 2 : 4, NS = NSTAGE;
+    // the ring of staged boxes: NS stages of NA arrays (r, p_old[, D^-1, beta]) and e
+    constexpr int NA = CC ? 2 : 4, NS = CC ? NSTAGE_CC : NSTAGE;
+    constexpr int STAGEF = NA * S::BOXF_PAD + S::EBOXF_PAD;  // floats per stage
     float* ring = reinterpret_cast<float*>(k1_smem + ((128u - (smem_u32(k1_smem) & 127u)) & 127u));
-    auto box = [&](int t, int a) -> float* { return ring + ((t % NS) * NA + a) * S::BOXF_PAD; };
+    // array a (NA = e) of ring slot `slot`
+    auto box = [&](int slot, int a) -> float* { return ring + slot * STAGEF + a * S::BOXF_PAD; };
     __shared__ float P[2][S::PY][S::PX];
-    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    __shared__ __align__(8) uint64_t bar[NS];
     __shared__ double red[32];
     __shared__ int bad;
     __shared__ int issued_hi;              // highest staged plane index issued so far
     __shared__ unsigned int ticket;
 
-    if (st->done) return;
+    if (sc.done) return;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TBX * ty;
     if (tm && tid == 0) atomicMin(&tm->t0, global_ns());
     const int i0 = rg.ilo + blockIdx.x * TBX, j0 = rg.jlo + blockIdx.y * S::NY;
@@ -205,8 +221,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     const int ke = min(kb + kz, rg.khi + 1);
     const int P0 = kb - 1;                 // first staged node plane
     const int nplanes = ke - kb + 2;       // planes kb-1 .. ke
-    const float bcg = (float)st->beta;
-    const float ap = (float)st->alpha_prev;
+    const float bcg = sc.bcg, ap = sc.ap, cdinv = sc.cdinv, bu = sc.bu;
     // Node i sits in column i + XL of the padded layout. The box starts at the 16-byte
     // boundary bx at or below node i0-1's column, and node i0-1 is staged column sh.
     const int bx = (i0 + XL - 1) & ~3;
@@ -219,21 +234,25 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     }
     __syncthreads();
 
-    // Stage t holds node plane P0+t (memory plane P0+t+1) and element slab P0+t-1 (memory
-    // plane P0+t); row 0 of a box is node row j0-1 (memory row j0).
-    auto issue = [&](int t) {
-        uint64_t* b = &bar[t % NS];
+    // Stage t (ring slot t mod NS) holds node plane P0+t (memory plane P0+t+1) and element
+    // slab P0+t-1 (memory plane P0+t); row 0 of a box is node row j0-1 (memory row j0). Its e
+    // box holds the tile's own node rows j0.. of plane P0+t (memory row j0+1); it is staged only
+    // when the deferred correction is live (ap != 0).
+    const uint32_t stage_bytes = (uint32_t)sizeof(float) * (NA * S::BOXF + (ap != 0.f ? S::EBOXF : 0));
+    auto issue = [&](int t, int slot) {
+        uint64_t* b = &bar[slot];
         const int kk = P0 + t;
-        mbar_expect_tx(b, CC ? 2u * S::BOXF * (uint32_t)sizeof(float) : S::STAGE_BYTES);
-        tma_load_3d(box(t, 0), &m_r, bx, j0, kk + 1, b);
-        tma_load_3d(box(t, 1), &m_pold, bx, j0, kk + 1, b);
+        mbar_expect_tx(b, stage_bytes);
+        tma_load_3d(box(slot, 0), &m_r, bx, j0, kk + 1, b);
+        tma_load_3d(box(slot, 1), &m_pold, bx, j0, kk + 1, b);
         if (!CC) {
-            tma_load_3d(box(t, 2), &m_dinv, bx, j0, kk + 1, b);
-            tma_load_3d(box(t, 3), &m_beta, bx, j0, kk, b);
+            tma_load_3d(box(slot, 2), &m_dinv, bx, j0, kk + 1, b);
+            tma_load_3d(box(slot, 3), &m_beta, bx, j0, kk, b);
         }
+        if (ap != 0.f) tma_load_3d(box(slot, NA), &m_e, bx, j0 + 1, kk + 1, b);
     };
     if (tid == 0) {
-        for (int t = 0; t < NS && t < nplanes; ++t) issue(t);
+        for (int t = 0; t < NS && t < nplanes; ++t) issue(t, t);
         issued_hi = min(NS, nplanes) - 1;
     }
 
@@ -263,6 +282,8 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     CSum acc;
     int t_done = -1;                     // last stage waited for
     int t = 0;
+    int slot = 0;                        // ring slot of stage t
+    uint32_t phase = 0;                  // mbarrier phase parity of stage t
     bool stop = false;
 
     // One plane: stage t brings node plane kk = P0 + t into wp and beta slab kk-1 into bn;
@@ -273,17 +294,18 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
                     float(&bo)[RY + 1][2], float(&bn)[RY + 1][2], PlaneSums<RY>& sm, PlaneSums<RY>& s0,
                     PlaneSums<RY>& sp) {
         const int kk = P0 + t;
-        const float* Sr = box(t, 0);
-        const float* Sp = box(t, 1);
-        const float* Sd = box(t, 2);
-        const float* Sbeta = box(t, 3);
-        // prefetch e of the nodes computed at the next step (plane kk), one step ahead
+        const float* Sr = box(slot, 0);
+        const float* Sp = box(slot, 1);
+        const float* Sd = box(slot, 2);
+        const float* Sbeta = box(slot, 3);
+        const float* Se = box(slot, NA);
+        if (!mbar_wait(&bar[slot], phase)) bad = 1;
+        t_done = t;
+        // e of the nodes computed at the next step (plane kk), from this stage: read before the
+        // next step's barrier, after which the slot may be refilled
         float e_next[RY];
 #pragma unroll
-        for (int r = 0; r < RY; ++r)
-            e_next[r] = (ap != 0.f && r < nown && t >= 1) ? e[o + g.plane + r * pitch] : 0.f;
-        if (!mbar_wait(&bar[t % NS], (uint32_t)((t / NS) & 1))) bad = 1;
-        t_done = t;
+        for (int r = 0; r < RY; ++r) e_next[r] = ap != 0.f ? Se[(ty * RY + r) * EX + tx + 1 + sh] : 0.f;
         // form p of plane kk for the tile plus halo
         float* Pk = &P[kk & 1][0][0];
 #pragma unroll
@@ -301,7 +323,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
             return;
         }
         if (tid == 0 && t >= 1 && t - 1 + NS < nplanes) {
-            issue(t - 1 + NS);
+            issue(t - 1 + NS, slot == 0 ? NS - 1 : slot - 1);  // the slot of stage t-1
             issued_hi = t - 1 + NS;
         }
         const float(*Pp)[S::PX] = P[kk & 1];
@@ -373,6 +395,10 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
             e_cur[r] = e_next[r];
         }
         o += g.plane;
+        if (++slot == NS) {
+            slot = 0;
+            phase ^= 1u;
+        }
         if (++t >= nplanes) stop = true;
     };
     // period 6 = lcm(3 window planes, 2 beta slabs)
@@ -444,13 +470,14 @@ template <bool ROBIN, bool CUBE, int RY>
 __global__ void __launch_bounds__(NT, RY == 1 ? (ROBIN ? 3 : 4) : 2)
 k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
            const __grid_constant__ CUtensorMap m_dinv, const __grid_constant__ CUtensorMap m_beta,
-           const Grid g, const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q,
-           float* __restrict__ e, SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
-           KTimer* tm)
+           const __grid_constant__ CUtensorMap m_e, const Grid g, const Op op, const Range rg,
+           float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e, SolveState* st,
+           double* partials, int pidx, CondHandles ch, int kz, KTimer* tm)
 {
     COUNT_LAUNCH();
-    k1_body<ROBIN, CUBE, RY, false>(m_r, m_pold, m_dinv, m_beta, g, op, rg, pnew, q, e, st, partials, pidx, ch, kz,
-                                    tm, 0.f, 0.f);
+    const K1Scalars sc{st->done, (float)st->beta, (float)st->alpha_prev, 0.f, 0.f};
+    k1_body<ROBIN, CUBE, RY, false>(m_r, m_pold, m_dinv, m_beta, m_e, g, op, rg, pnew, q, e, st, partials, pidx, ch,
+                                    kz, tm, sc);
 }
 
 // Constant-coefficient path (every face Dirichlet, one beta on the level): r and p_old only,
@@ -459,23 +486,27 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
 // set-up clear the flag (new beta data under a recorded graph), the kernel computes nothing
 // and records status 6 so that the host records the solve again with the general path.
 template <bool CUBE, int RY>
-__global__ void __launch_bounds__(NT, RY == 1 ? 6 : 2)
-k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold, const Grid g,
-          const Op op, const Range rg, float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e,
-          SolveState* st, double* partials, int pidx, CondHandles ch, int kz, KTimer* tm,
-          const int* __restrict__ uniform, const float* __restrict__ beta32, const float* __restrict__ dinv32)
+__global__ void __launch_bounds__(NT, RY == 1 ? 6 : 3)
+k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
+          const __grid_constant__ CUtensorMap m_e, const Grid g, const Op op, const Range rg,
+          float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e, SolveState* st, double* partials,
+          int pidx, CondHandles ch, int kz, KTimer* tm, const int* __restrict__ uniform,
+          const float* __restrict__ beta32, const float* __restrict__ dinv32)
 {
     COUNT_LAUNCH();
-    if (!*uniform) {
-        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0 && !st->done) {
+    const int uni = *uniform;
+    const K1Scalars sc{st->done, (float)st->beta, (float)st->alpha_prev, dinv32[g.off(1, 1, 1)],
+                       beta32[g.off(0, 0, 0)]};
+    if (!uni) {
+        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0 && !sc.done) {
             st->status = 6;
             st->done = 1;
             if (ch.use) cudaGraphSetConditional(ch.loop, 0);
         }
         return;
     }
-    k1_body<false, CUBE, RY, true>(m_r, m_pold, m_r, m_r, g, op, rg, pnew, q, e, st, partials, pidx, ch, kz, tm,
-                                   dinv32[g.off(1, 1, 1)], beta32[g.off(0, 0, 0)]);
+    k1_body<false, CUBE, RY, true>(m_r, m_pold, m_r, m_r, m_e, g, op, rg, pnew, q, e, st, partials, pidx, ch, kz, tm,
+                                   sc);
 }
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -506,13 +537,13 @@ EncodeTiled encoder()
     return fn;
 }
 
-bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy)
+bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy, int sx = SX)
 {
     EncodeTiled enc = encoder();
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 3), (cuuint64_t)(g.nz + 3)};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
-    const cuuint32_t box[3] = {SX, (cuuint32_t)sy, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)sx, (cuuint32_t)sy, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -554,29 +585,30 @@ void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid&
     const CUtensorMap& pold = pold_is_b ? m.pB[v] : m.pA[v];
     if (cc) {
         auto kern = op.cube ? k_pq32_cc<true, RY> : k_pq32_cc<false, RY>;
-        kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, 2>(), s>>>(m.r[v], pold, g, op, rg, pnew, q, e, st,
-                                                                         pr.buf, pidx, ch, c.kz, tm, uniform, beta32,
-                                                                         dinv32);
+        kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, 2>(), s>>>(m.r[v], pold, m.e[v], g, op, rg, pnew, q, e,
+                                                                         st, pr.buf, pidx, ch, c.kz, tm, uniform,
+                                                                         beta32, dinv32);
         return;
     }
     bool robin = false;
     for (int f = 0; f < 6; ++f) robin |= op.alpha[f] != 0.0;
     auto kern = robin ? (op.cube ? k_pq32_tma<true, true, RY> : k_pq32_tma<true, false, RY>)
                       : (op.cube ? k_pq32_tma<false, true, RY> : k_pq32_tma<false, false, RY>);
-    kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, 4>(), s>>>(m.r[v], pold, m.dinv[v], m.beta[v], g, op, rg,
-                                                                     pnew, q, e, st, pr.buf, pidx, ch, c.kz, tm);
+    kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, 4>(), s>>>(m.r[v], pold, m.dinv[v], m.beta[v], m.e[v], g,
+                                                                     op, rg, pnew, q, e, st, pr.buf, pidx, ch, c.kz,
+                                                                     tm);
 }
 
 }  // namespace
 
 bool make_plane_maps(PlaneMaps* m, const float* r, const float* pA, const float* pB, const float* dinv,
-                     const float* beta, const Grid& g)
+                     const float* beta, const float* e, const Grid& g)
 {
     for (int v = 0; v < K1_NRY; ++v) {
         const int sy = TBY * K1_RY[v] + 2;
         if (!make_plane_map(&m->r[v], r, g, sy) || !make_plane_map(&m->pA[v], pA, g, sy) ||
             !make_plane_map(&m->pB[v], pB, g, sy) || !make_plane_map(&m->dinv[v], dinv, g, sy) ||
-            !make_plane_map(&m->beta[v], beta, g, sy))
+            !make_plane_map(&m->beta[v], beta, g, sy) || !make_plane_map(&m->e[v], e, g, TBY * K1_RY[v], EX))
             return false;
     }
     return true;

@@ -11,9 +11,10 @@ namespace ecmg {
 constexpr int K1_NRY = 2;
 constexpr int K1_RY[K1_NRY] = {1, 2};
 
-// Tensor maps of one level's FP32 vectors; set v stages boxes of 40 x (8*K1_RY[v]+2) x 1.
+// Tensor maps of one level's FP32 vectors; set v stages boxes of 40 x (8*K1_RY[v]+2) x 1
+// (e: 36 x 8*K1_RY[v] x 1, the tile's own rows).
 struct PlaneMaps {
-    CUtensorMap r[K1_NRY], pA[K1_NRY], pB[K1_NRY], dinv[K1_NRY], beta[K1_NRY];
+    CUtensorMap r[K1_NRY], pA[K1_NRY], pB[K1_NRY], dinv[K1_NRY], beta[K1_NRY], e[K1_NRY];
 };
 
 // Tile shape of K1 on one level: ry node rows per thread, kz planes marched per block.
@@ -25,7 +26,7 @@ struct K1Config {
 // Encode the tensor maps of one level. False if the driver entry point is unavailable or an
 // encoding is rejected.
 bool make_plane_maps(PlaneMaps* m, const float* r, const float* pA, const float* pB, const float* dinv,
-                     const float* beta, const Grid& g);
+                     const float* beta, const float* e, const Grid& g);
 
 // Set the shared-memory limit of every K1 instantiation on the current device.
 cudaError_t k1_prepare();
