@@ -480,13 +480,14 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
                                     kz, tm, sc);
 }
 
-// Constant-coefficient path (every face Dirichlet, one beta on the level): r and p_old only,
-// and about half the registers of the general path, so six blocks fit on an SM instead of
-// four. The host picks it from the level's uniform flag after the set-up; should a later
+// Constant-coefficient path (every face Dirichlet, one beta on the level): r, p_old and e only,
+// and about half the registers of the general path, so six blocks fit on an SM instead of four
+// (one node row per thread; four blocks with two rows, which an autotuned 512^3 level
+// prefers). The host picks it from the level's uniform flag after the set-up; should a later
 // set-up clear the flag (new beta data under a recorded graph), the kernel computes nothing
 // and records status 6 so that the host records the solve again with the general path.
 template <bool CUBE, int RY>
-__global__ void __launch_bounds__(NT, RY == 1 ? 6 : 3)
+__global__ void __launch_bounds__(NT, RY == 1 ? 6 : 4)
 k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
           const __grid_constant__ CUtensorMap m_e, const Grid g, const Op op, const Range rg,
           float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e, SolveState* st, double* partials,
