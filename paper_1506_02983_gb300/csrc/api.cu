@@ -22,6 +22,7 @@
 #include "exp.cuh"
 #include "jcg.cuh"
 #include "pq_tma.cuh"
+#include "res_cc.cuh"
 #include "separable.cuh"
 
 using namespace ecmg;
@@ -65,6 +66,7 @@ struct Level {
     float *beta32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *pA32 = nullptr, *pB32 = nullptr,
           *q32 = nullptr, *e32 = nullptr;
     PlaneMaps maps;  // TMA descriptors of the FP32 vectors
+    ResMaps rmaps;   // TMA descriptors of U and of b / c (exact constant-coefficient residual)
     K1Config k1{1, 128};  // tile shape of the FP32 stencil kernel
     int* uniform = nullptr;  // device flag: one beta on the whole level
     bool cc = false;         // the FP32 stencil runs its constant-coefficient kernel (host choice)
@@ -256,6 +258,18 @@ void host_state(ecmg_handle* h, int l, SolveState* out)
 bool constant_coefficient(ecmg_handle* h, const Level& v);
 void drop_graph(ecmg_handle* h);
 
+// FP64 residual of the MIXED iteration into r32: on a constant-coefficient level (the host's
+// choice v.cc, cubic elements) the TMA-staged exact kernel, else the general one.
+void res32(ecmg_handle* h, Level& v, SolveState* st, ResMode mode, CondHandles ch, cudaStream_t s)
+{
+    if (v.cc && v.op.cube) {
+        launch_absmax(v.g, v.U, v.uniform, st, (int)mode, h->part, s);
+        launch_res32_cc(v.rmaps, v.g, v.uniform, v.beta, v.dinv32, v.r32, st, h->part, mode, ch, s);
+    } else {
+        launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, mode, ch, s, v.r);
+    }
+}
+
 // ---- level set-up (finest to coarsest) -------------------------------------------------------
 void record_setup(Rec& R)
 {
@@ -378,13 +392,11 @@ void record_level(Rec& R, int l)
         };
         auto replace = [&](float* pnew) {
             launch_fold32(v.g, v.U, v.e32, pnew, st, R.s());
-            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPLACE, none, R.s(),
-                         v.r);
+            res32(h, v, st, RES_REPLACE, none, R.s());
         };
         if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
-            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT,
-                         CondHandles{loop, 0, 1}, R.s(), v.r);
+            res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s());
             R.open(loop, cudaGraphCondTypeWhile);
             for (int half = 0; half < 2; ++half) {
                 const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
@@ -398,8 +410,7 @@ void record_level(Rec& R, int l)
             }
             R.close();
         } else {
-            launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_INIT, none, R.s(),
-                         v.r);
+            res32(h, v, st, RES_INIT, none, R.s());
             SolveState hs;
             host_state(h, l, &hs);
             int parity = 0;
@@ -720,7 +731,7 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
         ck(cudaMemcpyAsync(&last, h->states + l, sizeof(last), cudaMemcpyDeviceToHost, s));
         ck(cudaStreamSynchronize(s));
         tmpl.bcbits = last.bcbits;
-        const bool cc = which == 0 && constant_coefficient(h, v);
+        const bool cc = (which == 0 || which == 2) && constant_coefficient(h, v);
         ck(cudaEventCreate(&e0));
         ck(cudaEventCreate(&e1));
         for (int rep = 0; rep <= reps; ++rep) {
@@ -732,10 +743,12 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
                                 h->part, 1, none, nullptr, s);
                 break;
             case 1: launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
-            case 2:
-                launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, RES_REPORT, none, s,
-                             v.r);
+            case 2: {
+                Level lv = v;
+                lv.cc = cc;
+                res32(h, lv, st, RES_REPORT, none, s);
                 break;
+            }
             case 3: launch_pq64(v.g, v.op, v.beta, v.uniform, v.r, v.dinv, v.pA, v.pB, v.q, v.Ut, st, h->part, 1, none, s); break;
             case 4: launch_update64(v.g, v.r, v.q, v.dinv, st, h->part, none, s); break;
             case 5: launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, s); break;
@@ -835,7 +848,7 @@ ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, u
         if (p->f_mode == ECMG_F_SEPARABLE) b += 8ull * (uint64_t)sep_factor_len(g, p->f_terms);
         if (p->gD_terms > 0 && l < p->levels - 1) b += 8ull * (uint64_t)sep_factor_len(g, p->gD_terms);
         maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
-        if (o->precision == ECMG_MIXED) maxb = std::max(maxb, max_tma_blocks(g));
+        if (o->precision == ECMG_MIXED) maxb = std::max(maxb, std::max(max_tma_blocks(g), res_cc_blocks(g)));
     }
     b += (uint64_t)maxb * 3 * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
     *bytes = b;
@@ -857,7 +870,10 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
     try {
         for (int i = 0; i < 3; ++i) ck(cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
         const bool mixed = opt->precision == ECMG_MIXED;
-        if (mixed) ck(k1_prepare());
+        if (mixed) {
+            ck(k1_prepare());
+            ck(res_cc_prepare());
+        }
         int maxb = 0;
         for (int l = 0; l < h->L; ++l) {
             Level& v = h->lv[l];
@@ -887,10 +903,11 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
                 v.pB32 = dalloc<float>(h, n);
                 v.q32 = dalloc<float>(h, n);
                 v.e32 = dalloc<float>(h, n);
-                if (!make_plane_maps(&v.maps, v.r32, v.pA32, v.pB32, v.dinv32, v.beta32, v.e32, v.g))
+                if (!make_plane_maps(&v.maps, v.r32, v.pA32, v.pB32, v.dinv32, v.beta32, v.e32, v.g) ||
+                    !make_res_maps(&v.rmaps, v.U, v.r, v.g))
                     throw CudaFail{cudaErrorNotSupported};
                 v.k1 = k1_default(v.g, v.op);
-                maxb = std::max(maxb, max_tma_blocks(v.g));
+                maxb = std::max(maxb, std::max(max_tma_blocks(v.g), res_cc_blocks(v.g)));
             }
             maxb = std::max(maxb, std::max(max_stencil_blocks(v.g), max_stream_blocks()));
         }
@@ -1241,7 +1258,8 @@ const char* ecmg_last_error(void) { return g_last_error.c_str(); }
 ecmg_status ecmg_kernel_launches(uint64_t* out)
 {
     if (!out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
-    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_batch() + launches_separable();
+    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_batch() + launches_separable() +
+           launches_res_cc();
     return ECMG_OK;
 }
 

@@ -1,0 +1,40 @@
+// fixed.cuh -- the fixed-point frame of the exact constant-coefficient operator: an iterate x
+// is written as X 2^-s with 64-bit integers X, s chosen per level from max |x| so that every
+// |X| < 2^53 (jcg.cu, res_cc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ecmg {
+namespace fx {
+
+// Per-level scale: the bit pattern of max |x| (k_absmax), read by every block.
+struct FixedFrame {
+    int s;          // x = X 2^-s
+    double inv;     // 2^-s
+    bool finite;    // false when x holds an Inf or NaN
+};
+__device__ __forceinline__ FixedFrame fixed_frame(unsigned long long bits)
+{
+    FixedFrame f;
+    const int E = (int)((bits >> 52) & 0x7ff);  // biased exponent of max |x|
+    f.finite = E != 0x7ff;
+    f.s = (bits == 0ull || !f.finite) ? 0 : 1075 - E;  // max |x| < 2^(E-1022), so max |X| < 2^53
+    f.inv = ldexp(1.0, -f.s);
+    return f;
+}
+// X = trunc(x 2^s) from the bits of x (integer operations only; |x| <= max |x| keeps the shift
+// non-positive).
+__device__ __forceinline__ long long to_fixed(double x, int s)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const long long m = (b & 0xfffffffffffffll) | 0x10000000000000ll;
+    const int sh = e - 1075 + s;
+    long long v = 0;
+    if (e != 0 && sh > -64) v = sh >= 0 ? (long long)((unsigned long long)m << sh) : (m >> -sh);
+    return b < 0 ? -v : v;
+}
+
+}  // namespace fx
+}  // namespace ecmg

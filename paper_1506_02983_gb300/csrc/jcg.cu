@@ -11,6 +11,7 @@
 // condition of the level's WHILE node, so a level runs with no host round trip.
 //
 // The operator at a node is q1_apply (stencil_core.cuh).
+#include "fixed.cuh"
 #include "jcg.cuh"
 #include "jcg_core.cuh"
 #include "march.cuh"
@@ -21,6 +22,8 @@
 
 namespace ecmg {
 namespace {
+
+using namespace fx;
 
 __device__ unsigned long long g_launches = 0;  // kernel executions of this file
 #define COUNT_LAUNCH()                                                                   \
@@ -229,33 +232,6 @@ __device__ __forceinline__ void march_uniform(const Grid& g, const Op& op, doubl
 // |I| <= 3 * 144 * 2^53 < 2^63, and writing x in fixed point moves each value by less than
 // 2^-53 max |x|, below the rounding error of evaluating the difference form in FP64.
 
-// Per-level scale: the bit pattern of max |x| (k_absmax), read by every block.
-struct FixedFrame {
-    int s;          // x = X 2^-s
-    double inv;     // 2^-s
-    bool finite;    // false when x holds an Inf or NaN
-};
-__device__ __forceinline__ FixedFrame fixed_frame(unsigned long long bits)
-{
-    FixedFrame f;
-    const int E = (int)((bits >> 52) & 0x7ff);  // biased exponent of max |x|
-    f.finite = E != 0x7ff;
-    f.s = (bits == 0ull || !f.finite) ? 0 : 1075 - E;  // max |x| < 2^(E-1022), so max |X| < 2^53
-    f.inv = ldexp(1.0, -f.s);
-    return f;
-}
-// X = trunc(x 2^s) from the bits of x (integer operations only; |x| <= max |x| keeps the shift
-// non-positive).
-__device__ __forceinline__ long long to_fixed(double x, int s)
-{
-    const long long b = __double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff);
-    const long long m = (b & 0xfffffffffffffll) | 0x10000000000000ll;
-    const int sh = e - 1075 + s;
-    long long v = 0;
-    if (e != 0 && sh > -64) v = sh >= 0 ? (long long)((unsigned long long)m << sh) : (m >> -sh);
-    return b < 0 ? -v : v;
-}
 // c v with c = 4 (interior node) or 2 (end node): the centre entry of S
 __device__ __forceinline__ long long s_mid(long long v, bool end)
 {
@@ -801,8 +777,8 @@ void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
                                                                           pnew, q, e, st, pr.buf, pidx, ch, kz);
 }
 // max |x| for the fixed-point evaluation (a no-op on levels with more than one beta)
-inline void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
-                          Partials pr, cudaStream_t s)
+void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
+                   Partials pr, cudaStream_t s)
 {
     k_absmax<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, uniform, st, mode, pr.fs,
                                                         reinterpret_cast<unsigned long long*>(pr.buf));

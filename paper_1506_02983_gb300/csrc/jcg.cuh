@@ -39,6 +39,10 @@ void launch_res64(const Grid& g, const Op& op, const double* beta, const int* un
 void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s, const double* bc = nullptr);
+// max |x| over the level vector into pr.fs (the fixed-point scale of the exact residual) when the
+// level's uniform flag is set; skipped for a replacement (mode RES_REPLACE) of a finished level.
+void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
+                   Partials pr, cudaStream_t s);
 // bc = b / c (c = -beta h / 36) and max |bc| into the level state, when the level has one beta,
 // every face Dirichlet and cubic elements (a no-op otherwise).
 void launch_scale_load(const Grid& g, const Op& op, const double* b, double* bc, const double* beta,

@@ -494,3 +494,26 @@ def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_
     assert _rel(U2, lv[-1]["U"]) <= 1e-7
     s.close()
     fresh.close()
+
+
+@pytest.mark.parametrize("name", ["exp_cube", "cos_cube_cube", "problem1_load", "random_mixed_bc_0"])
+def test_mixed_reported_residual_is_the_true_residual(E, oracle_mod, name):
+    """The residual the MIXED solve reports on every level (from its last FP64 residual
+    evaluation: the exact constant-coefficient kernel on one-beta all-Dirichlet cubes, the
+    general one elsewhere) is ||b - A U|| / ||f_h|| of the returned U, recomputed by the oracle
+    with its assembled matrix; the two differ only by the FP32 rounding of r."""
+    p = inputs.cos_cube(levels=4, n0=(4, 4, 4), rtol=1e-9) if name == "cos_cube_cube" else PROBLEMS[name]()
+    s = E.solver_from_problem(p, precision=1)
+    st, status = s.solve()
+    assert status == 0, st
+    betas = _oracle_levels(oracle_mod, p)
+    for l in range(2, p["levels"]):
+        n = [v << l for v in p["n0"]]
+        A = oracle_mod.assemble(n, _level_h(p, l), betas[l], p["face_bc"], p["alpha"])
+        free = oracle_mod.dirichlet_mask(n, p["face_bc"]) == 1
+        U = _np(s.get(E.ECMG_VEC_U, l)).ravel()
+        b = _np(s.get(E.ECMG_VEC_B, l)).ravel()
+        r = (b - A.matvec(U))[free]
+        rel = np.sqrt(np.dot(r, r)) / st["rhs_norm"][l]
+        assert rel == pytest.approx(st["rel_res"][l], rel=1e-4), (l, rel, st["rel_res"][l])
+    s.close()
