@@ -227,7 +227,8 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
 /* Time one kernel of the solve alone on level `level` (-1 = finest): `reps` launches, each
  * bracketed by CUDA events on the handle's stream, after one untimed launch. which:
  * 0 K1 FP32 (search direction + operator), 1 K2 FP32 (residual update), 2 FP64 residual with
- * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true.
+ * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true, 8 ||f_h||,
+ * 9 MIXED fold of the FP32 correction into the FP64 iterate (applied to U~), 10 max |U|.
  * ms_out: mean duration of one launch (host). bytes_out: the algorithmic bytes one launch
  * must move (each owned input read once, each output written once; host); for kernel 0 the
  * nodes counted are those off the Dirichlet faces, the only ones it visits, and on a level

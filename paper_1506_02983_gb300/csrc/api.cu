@@ -263,7 +263,8 @@ void drop_graph(ecmg_handle* h);
 void res32(ecmg_handle* h, Level& v, SolveState* st, ResMode mode, CondHandles ch, cudaStream_t s)
 {
     if (v.cc && v.op.cube) {
-        launch_absmax(v.g, v.U, v.uniform, st, (int)mode, h->part, s);
+        // a replacement follows the fold, which has taken max |U| already
+        if (mode != RES_REPLACE) launch_absmax(v.g, v.U, v.uniform, st, (int)mode, h->part, s);
         launch_res32_cc(v.rmaps, v.g, v.uniform, v.beta, v.dinv32, v.r32, st, h->part, mode, ch, s);
     } else {
         launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, mode, ch, s, v.r);
@@ -391,7 +392,7 @@ void record_level(Rec& R, int l)
             launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
         };
         auto replace = [&](float* pnew) {
-            launch_fold32(v.g, v.U, v.e32, pnew, st, R.s());
+            launch_fold32(v.g, v.U, v.e32, pnew, v.uniform, st, h->part, R.s());
             res32(h, v, st, RES_REPLACE, none, R.s());
         };
         if (R.graph) {
@@ -758,11 +759,14 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
                 launch_exp_finite(h->opt.exp_variant, v.g, v.op, u1.g, u1.U, u0.g, u0.U, v.r, v.q, s);
                 break;
             }
-            default: {
+            case 7: {
                 const Level& u1 = h->lv[l - 1];
                 launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, s);
                 break;
             }
+            case 8: launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, s); break;
+            case 9: launch_fold32(v.g, v.Ut, v.e32, v.pA32, v.uniform, st, h->part, s); break;
+            default: launch_absmax(v.g, v.U, v.uniform, nullptr, 0, h->part, s); break;
             }
             ck(cudaEventRecord(e1, s));
             ck(cudaEventSynchronize(e1));
@@ -1269,9 +1273,9 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
     if (!h || !ms_out || !bytes_out || reps < 1) return fail(ECMG_ERR_INVALID_ARG, "bad argument");
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
-    if (which < 0 || which > 7) return fail(ECMG_ERR_INVALID_ARG, "bad kernel selector");
+    if (which < 0 || which > 10) return fail(ECMG_ERR_INVALID_ARG, "bad kernel selector");
     Level& v = h->lv[l];
-    if (which <= 2 && !v.r32) return fail(ECMG_ERR_INVALID_ARG, "handle has no FP32 vectors");
+    if ((which <= 2 || which == 9) && !v.r32) return fail(ECMG_ERR_INVALID_ARG, "handle has no FP32 vectors");
     if (which >= 6 && l < 2) return fail(ECMG_ERR_INVALID_ARG, "EXP kernels need level >= 2");
     const double N = (double)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1);
     const double E = (double)v.g.nx * v.g.ny * v.g.nz;
@@ -1285,8 +1289,11 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
     } catch (CudaFail& f) {
         return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
     }
-    const double bytes[8] = {(cc ? 24 * N1 : 28 * N1 + 4 * E), (cc ? 12 * N : 16 * N), 24 * N + 8 * E, 56 * N + 8 * E,
-                             32 * N,         32 * N + 8 * E, 16 * N + 8 * (N / 8 + N / 64), 17 * N};
+    // the constant-coefficient residual (kernel 2) reads x and b / c and writes r: 20 bytes per
+    // node; ||f_h|| (8) reads b; the fold (9) updates x and e and reads p; max |x| (10) reads x
+    const double bytes[11] = {(cc ? 24 * N1 : 28 * N1 + 4 * E), (cc ? 12 * N : 16 * N),
+                              (cc && v.op.cube ? 20 * N : 24 * N + 8 * E), 56 * N + 8 * E, 32 * N, 32 * N + 8 * E,
+                              16 * N + 8 * (N / 8 + N / 64), 17 * N, 8 * N, 28 * N, 8 * N};
     *bytes_out = bytes[which];
     try {
         *ms_out = time_launches(h, l, which, reps);

@@ -46,10 +46,11 @@ struct Grid {
 struct Op {
     double w0, wc, we[3], wf[3];
     int cube;                    // 1 when hx = hy = hz (face weights 0, edge weight = corner weight)
-    float wc32, we32[3], wf32[3];  // the same weights rounded to FP32 on the host
+    float w032, wc32, we32[3], wf32[3];  // the same weights rounded to FP32 on the host
     // Robin: alpha on each face (0 when Dirichlet or Neumann) and the in-face 1D mass entries
     double alpha[6];
     int bc[6];                   // 0 Dirichlet, 1 Robin
+    int robin;                   // 1 when some alpha != 0 (integer test: FP64 compares run at 1/64 rate)
 };
 
 __host__ inline Op make_op(const double h[3], const int bc[6], const double alpha[6])
@@ -70,6 +71,7 @@ __host__ inline Op make_op(const double h[3], const int bc[6], const double alph
     o.wf[1] = K(0, 1, 0);
     o.wf[2] = K(0, 0, 1);
     o.cube = (h[0] == h[1] && h[1] == h[2]) ? 1 : 0;
+    o.w032 = (float)o.w0;
     o.wc32 = (float)o.wc;
     for (int a = 0; a < 3; ++a) {
         o.we32[a] = (float)o.we[a];
@@ -79,6 +81,8 @@ __host__ inline Op make_op(const double h[3], const int bc[6], const double alph
         o.bc[f] = bc[f];
         o.alpha[f] = (bc[f] == 1) ? alpha[f] : 0.0;
     }
+    o.robin = 0;
+    for (int f = 0; f < 6; ++f) o.robin |= o.alpha[f] != 0.0;
     return o;
 }
 

@@ -559,25 +559,69 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
 }
 
 // ---- ||f_h||: the free-node right-hand side with the Dirichlet values moved over (fh_at) -------
+// The free nodes form a box F; the nodes of F one step from a Dirichlet face (the shell) carry
+// the lift b - A g_ext, all others just b. The shell is summed by its own flat loops, one node
+// per thread, so its FP64 stencil never runs in a warp whose other lanes idle (a warp that
+// diverges on the FP64 pipe pays for all 32 lanes); the inner box N streams b alone.
+struct FhBox {
+    int lo[3], hi[3];    // F: free nodes per axis
+    int nlo[3], nhi[3];  // N: no Dirichlet face within one step (nlo > nhi: empty)
+};
+// values of axis a in F but not in N: count, and the idx-th of them
+__device__ __forceinline__ int outer_count(const FhBox& B, int a)
+{
+    return B.nlo[a] > B.nhi[a] ? B.hi[a] - B.lo[a] + 1 : (B.nlo[a] - B.lo[a]) + (B.hi[a] - B.nhi[a]);
+}
+__device__ __forceinline__ int outer_value(const FhBox& B, int a, int idx)
+{
+    if (B.nlo[a] > B.nhi[a]) return B.lo[a] + idx;
+    const int nl = B.nlo[a] - B.lo[a];
+    return idx < nl ? B.lo[a] + idx : B.nhi[a] + 1 + (idx - nl);
+}
+__device__ __forceinline__ int inner_count(const FhBox& B, int a) { return max(B.nhi[a] - B.nlo[a] + 1, 0); }
+
 template <bool ROBIN, bool CUBE>
-__global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, const double* __restrict__ beta,
-                                                 const double* __restrict__ x, const double* __restrict__ b,
-                                                 SolveState* st, double* partials)
+__global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, const FhBox B,
+                                                 const double* __restrict__ beta, const double* __restrict__ x,
+                                                 const double* __restrict__ b, SolveState* st, double* partials)
 {
     COUNT_LAUNCH();
     const Weights<double> wts(op);
     double ss = 0.0;
-    // rows (j, k) spread over the warps of the grid, nodes i of a row over the lanes
-    const int nrows = (g.ny + 1) * (g.nz + 1);
-    const int warps = gridDim.x * (blockDim.x / 32), wid = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    for (int row = wid; row < nrows; row += warps) {
-        const int j = row % (g.ny + 1), k = row / (g.ny + 1);
-        const int64_t orow = g.plane_base(k) + g.in_plane(0, j);
-        for (int i = threadIdx.x & 31; i <= g.nx; i += 32) {
-            if (on_dirichlet(g, op, i, j, k)) continue;
-            const double f = fh_at<ROBIN, CUBE>(g, op, wts, beta, x, b, orow + i, i, j, k);
-            ss = fma(f, f, ss);
-        }
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nFi = B.hi[0] - B.lo[0] + 1, nFj = B.hi[1] - B.lo[1] + 1;
+    const int oi = outer_count(B, 0), oj = outer_count(B, 1), ok = outer_count(B, 2);
+    const int ii = inner_count(B, 0), ij = inner_count(B, 1), ik = inner_count(B, 2);
+    auto shell = [&](int i, int j, int k) {
+        const double f = fh_at<ROBIN, CUBE>(g, op, wts, beta, x, b, g.off(i, j, k), i, j, k);
+        ss = fma(f, f, ss);
+    };
+    // shell 1: planes k of F outside N, every (i, j) of F
+    const int64_t n1 = (int64_t)ok * nFj * nFi;
+    for (int64_t t = tid; t < n1; t += nthreads) {
+        const int i = B.lo[0] + (int)(t % nFi), j = B.lo[1] + (int)((t / nFi) % nFj);
+        shell(i, j, outer_value(B, 2, (int)(t / ((int64_t)nFi * nFj))));
+    }
+    // shell 2: planes of N, rows j of F outside N, every i of F
+    const int64_t n2 = (int64_t)ik * oj * nFi;
+    for (int64_t t = tid; t < n2; t += nthreads) {
+        const int i = B.lo[0] + (int)(t % nFi), j = outer_value(B, 1, (int)((t / nFi) % oj));
+        shell(i, j, B.nlo[2] + (int)(t / ((int64_t)nFi * oj)));
+    }
+    // shell 3: rows of N, nodes i of F outside N
+    const int64_t n3 = (int64_t)ik * ij * oi;
+    for (int64_t t = tid; t < n3; t += nthreads) {
+        const int i = outer_value(B, 0, (int)(t % oi)), j = B.nlo[1] + (int)((t / oi) % ij);
+        shell(i, j, B.nlo[2] + (int)(t / ((int64_t)oi * ij)));
+    }
+    // inner box: rows (j, k) over the warps of the grid, nodes i over the lanes
+    const int64_t nrows = (int64_t)ij * ik;
+    const int64_t warps = nthreads / 32, wid = tid / 32;
+    for (int64_t row = wid; row < nrows; row += warps) {
+        const int j = B.nlo[1] + (int)(row % ij), k = B.nlo[2] + (int)(row / ij);
+        const double* brow = b + g.off(B.nlo[0], j, k);
+        for (int i = threadIdx.x & 31; i < ii; i += 32) ss = fma(brow[i], brow[i], ss);
     }
     double v[1] = {ss};
     if (grid_sum<1>(v, partials, &st->arrive)) {
@@ -693,16 +737,84 @@ __global__ void k_final64(int64_t n, double* __restrict__ x, const double* __res
         x[t] = fma(a, p[t], x[t]);
 }
 
-__global__ void k_fold32(int64_t n, double* __restrict__ x, float* __restrict__ e,
-                         const float* __restrict__ p, const SolveState* st)
+// Exact widening of an FP32 value to FP64 by rebiasing its exponent field (integer operations;
+// the conversion instruction runs on the FP64 pipe, 1/64 of the FP32 rate on GB300). Zeros
+// keep their sign; subnormals, Inf and NaN take the conversion instruction.
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned int b = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+    const unsigned int ex = (b >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// MIXED fold at a residual replacement: x += e + alpha_prev p, e = 0. The FP32 correction is
+// combined in FP32 (one more rounding of an FP32 quantity) and added to x with a single FP64
+// operation. On a level with one beta the block also takes max |x| of the new iterate into
+// fs->bits, the scale of the exact residual that follows (no separate pass over x).
+__global__ void __launch_bounds__(UPD_TPB) k_fold32(int64_t n, double* __restrict__ x, float* __restrict__ e,
+                                                   const float* __restrict__ p, const int* __restrict__ uniform,
+                                                   const SolveState* st, FixedScale* fs,
+                                                   unsigned long long* partials)
 {
     COUNT_LAUNCH();
     if (st->done) return;
-    const double a = st->alpha_prev;
+    const float a = (float)st->alpha_prev;
+    const bool want_max = *uniform != 0;
+    __shared__ unsigned long long sh[UPD_TPB / 32];
+    __shared__ unsigned int ticket;
+    unsigned long long m = 0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
-        x[t] += (double)e[t] + a * (double)p[t];
+    double2* x2 = reinterpret_cast<double2*>(x);
+    float4* e4 = reinterpret_cast<float4*>(e);
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n / 4; t += stride) {
+        const float4 ev = e4[t], pv = p4[t];
+        double2 xa = x2[2 * t], xb = x2[2 * t + 1];
+        xa.x += widen(fmaf(a, pv.x, ev.x));
+        xa.y += widen(fmaf(a, pv.y, ev.y));
+        xb.x += widen(fmaf(a, pv.z, ev.z));
+        xb.y += widen(fmaf(a, pv.w, ev.w));
+        x2[2 * t] = xa;
+        x2[2 * t + 1] = xb;
+        e4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        m = max(m, max(max((unsigned long long)__double_as_longlong(fabs(xa.x)),
+                           (unsigned long long)__double_as_longlong(fabs(xa.y))),
+                       max((unsigned long long)__double_as_longlong(fabs(xb.x)),
+                           (unsigned long long)__double_as_longlong(fabs(xb.y)))));
+    }
+    for (int64_t t = (n / 4) * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
+        x[t] += widen(fmaf(a, p[t], e[t]));
         e[t] = 0.f;
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(x[t])));
+    }
+    if (!want_max) return;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
+        partials[blockIdx.x] = m;
+        __threadfence();
+        ticket = atomicAdd(&fs->arrive, 1u);
+    }
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    m = 0ull;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = max(m, __ldcg(&partials[b]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if (lane == 0) sh[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
+        fs->bits = m;
+        fs->arrive = 0u;
     }
 }
 
@@ -834,8 +946,18 @@ void launch_apply32(const Grid& g, const Op& op, const float* beta, const float*
 void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
                 Partials pr, cudaStream_t s)
 {
+    FhBox B;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        const bool dlo = op.bc[2 * a] == 0, dhi = op.bc[2 * a + 1] == 0;
+        B.lo[a] = dlo ? 1 : 0;
+        B.hi[a] = dhi ? n[a] - 1 : n[a];
+        B.nlo[a] = dlo ? 2 : 0;           // fh_at: within one step of a Dirichlet face
+        B.nhi[a] = dhi ? n[a] - 2 : n[a];
+    }
     (has_robin(op) ? (op.cube ? k_fh2<true, true> : k_fh2<true, false>)
-                   : (op.cube ? k_fh2<false, true> : k_fh2<false, false>))<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g, op, beta, x, b, st, pr.buf);
+                   : (op.cube ? k_fh2<false, true> : k_fh2<false, false>))<<<update_blocks(g.total), UPD_TPB, 0, s>>>(
+        g, op, B, beta, x, b, st, pr.buf);
 }
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv, SolveState* st,
                      Partials pr, CondHandles ch, cudaStream_t s)
@@ -858,9 +980,11 @@ void launch_final64(const Grid& g, double* x, const double* pA, const double* pB
 {
     k_final64<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, pA, pB, st);
 }
-void launch_fold32(const Grid& g, double* x, float* e, const float* p, SolveState* st, cudaStream_t s)
+void launch_fold32(const Grid& g, double* x, float* e, const float* p, const int* uniform, SolveState* st,
+                   Partials pr, cudaStream_t s)
 {
-    k_fold32<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, e, p, st);
+    k_fold32<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, e, p, uniform, st, pr.fs,
+                                                        reinterpret_cast<unsigned long long*>(pr.buf));
 }
 void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed, cudaStream_t s)
 {

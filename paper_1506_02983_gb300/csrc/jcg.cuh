@@ -67,9 +67,10 @@ void launch_update32(const Grid& g, const Op& op, const int* uniform, float* r, 
 // x += alpha_prev p_latest (FP64 JCG exit).
 void launch_final64(const Grid& g, double* x, const double* pA, const double* pB,
                     SolveState* st, cudaStream_t s);
-// MIXED: x64 += e + alpha_prev p; e = 0.
-void launch_fold32(const Grid& g, double* x, float* e, const float* p, SolveState* st,
-                   cudaStream_t s);
+// MIXED: x64 += e + alpha_prev p (combined in FP32, added in FP64); e = 0. With the level's
+// uniform flag set, also max |x| of the new iterate into pr.fs (what launch_absmax computes).
+void launch_fold32(const Grid& g, double* x, float* e, const float* p, const int* uniform, SolveState* st,
+                   Partials pr, cudaStream_t s);
 // Reset the level state before a solve; fixed: run exactly max_iters steps (Alg. 3).
 void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed,
                        cudaStream_t s);

@@ -95,8 +95,8 @@ __device__ __forceinline__ float jacobi32_at(const Grid& g, const Op& op, const 
     float B = 0.f;
     for (int c = 0; c < 8; ++c)
         B += beta32[g.off(i - 1 + (c & 1), j - 1 + ((c >> 1) & 1), k - 1 + (c >> 2))];
-    float d = __fmul_rn((float)op.w0, B);
-    if (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz) {
+    float d = __fmul_rn(op.w032, B);
+    if (op.robin && (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz)) {
         const int idx[3] = {i, j, k};
         const int nn[3] = {g.nx, g.ny, g.nz};
         double dr = 0.0;
