@@ -842,7 +842,9 @@ inline int stencil_kz(const Grid& g)
     const int want_blocks = 152 * 4;
     int gz = (want_blocks + gx * gy - 1) / (gx * gy);
     int kz = (g.nz + 1 + gz - 1) / gz;
-    if (kz < 8) kz = 8;
+    // small levels (the direct solves, the first MIXED levels) are FP64-pipe and latency bound:
+    // spread them over more SMs with short columns
+    if (kz < 2) kz = 2;
     if (kz > KZ_TARGET) kz = KZ_TARGET;
     return kz;
 }

@@ -588,8 +588,9 @@ bool k1_valid(const K1Config& c)
     return (c.ry == 1 || c.ry == 2) && c.kz >= 4 && c.kz <= 1024;
 }
 
-// One node row per thread (measured fastest on cubes of 256^3 and 512^3 nodes), and enough
-// blocks for about three per SM (152 SMs) with at most 128 planes per block.
+// One node row per thread, and enough blocks for about three per SM (152 SMs) with 4 to 128
+// planes per block (small levels are latency bound: short columns spread them over more SMs).
+// Levels of at least 2^18 nodes are autotuned after a solve.
 K1Config k1_default(const Grid& g, const Op& op)
 {
     K1Config c{1, 128};
@@ -597,7 +598,7 @@ K1Config k1_default(const Grid& g, const Op& op)
     const dim3 d = k1_grid(rg, K1Config{c.ry, 1 << 30});
     const int nk = max(rg.khi - rg.klo + 1, 1);
     const int gz = cdiv(152 * 3, (int)(d.x * d.y));
-    c.kz = min(max(cdiv(nk, gz), 8), 128);
+    c.kz = min(max(cdiv(nk, gz), 4), 128);
     return c;
 }
 

@@ -45,7 +45,7 @@ constexpr int XBOX = SX * SY;          // doubles
 constexpr int BBOX = EX * TBY;         // doubles
 constexpr int STAGE = XBOX + BBOX;     // doubles per stage (5504 bytes, a 128-byte multiple)
 constexpr int NS = 4;
-constexpr int KZ = 32;                 // planes per block
+constexpr int KZ_MAX = 32;             // planes per block at most
 static_assert((STAGE * 8) % 128 == 0 && (XBOX * 8) % 128 == 0, "TMA destinations stay 128-byte aligned");
 
 constexpr size_t smem_bytes() { return (size_t)NS * STAGE * sizeof(double) + 128; }
@@ -57,7 +57,7 @@ struct Col {
 
 __global__ void __launch_bounds__(NT, 4)
 k_res_cc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mbc, const Grid g,
-         float* __restrict__ r, SolveState* st, double* partials, int mode, CondHandles ch,
+         float* __restrict__ r, SolveState* st, double* partials, int mode, CondHandles ch, int kz,
          const FixedScale* fs, const int* __restrict__ uniform, const double* __restrict__ beta,
          const float* __restrict__ dinv32)
 {
@@ -96,8 +96,8 @@ k_res_cc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtenso
         double* ring = reinterpret_cast<double*>(rc_smem + ((128u - (smem_u32(rc_smem) & 127u)) & 127u));
         // free nodes 1 .. n-1 on every axis
         const int i0 = 1 + blockIdx.x * TBX, j0 = 1 + blockIdx.y * TBY;
-        const int kb = 1 + blockIdx.z * KZ;
-        const int ke = min(kb + KZ, g.nz);
+        const int kb = 1 + blockIdx.z * kz;
+        const int ke = min(kb + kz, g.nz);
         const int P0 = kb - 1;
         const int nplanes = ke - kb + 2;
         const int bx = (i0 + XL - 1) & ~3;  // 16-byte boundary at or below node i0-1's column
@@ -272,6 +272,14 @@ bool make_map(CUtensorMap* map, const double* base, const Grid& g, int sx, int s
 
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// planes per block: about four blocks per SM (152 SMs), 2 .. KZ_MAX planes
+inline int res_kz(const Grid& g)
+{
+    const int gxy = cdiv(max(g.nx - 1, 1), TBX) * cdiv(max(g.ny - 1, 1), TBY);
+    const int gz = cdiv(152 * 4, gxy);
+    return min(max(cdiv(max(g.nz - 1, 1), gz), 2), KZ_MAX);
+}
+
 }  // namespace
 
 bool make_res_maps(ResMaps* m, const double* x, const double* bc, const Grid& g)
@@ -286,15 +294,16 @@ cudaError_t res_cc_prepare()
 
 int res_cc_blocks(const Grid& g)
 {
-    return cdiv(max(g.nx - 1, 1), TBX) * cdiv(max(g.ny - 1, 1), TBY) * cdiv(max(g.nz - 1, 1), KZ);
+    return cdiv(max(g.nx - 1, 1), TBX) * cdiv(max(g.ny - 1, 1), TBY) * cdiv(max(g.nz - 1, 1), res_kz(g));
 }
 
 void launch_res32_cc(const ResMaps& m, const Grid& g, const int* uniform, const double* beta, const float* dinv32,
                      float* r, SolveState* st, Partials pr, ResMode mode, CondHandles ch, cudaStream_t s)
 {
-    const dim3 grid(cdiv(max(g.nx - 1, 1), TBX), cdiv(max(g.ny - 1, 1), TBY), cdiv(max(g.nz - 1, 1), KZ));
-    k_res_cc<<<grid, dim3(TBX, TBY), smem_bytes(), s>>>(m.x, m.bc, g, r, st, pr.buf, (int)mode, ch, pr.fs, uniform,
-                                                        beta, dinv32);
+    const int kz = res_kz(g);
+    const dim3 grid(cdiv(max(g.nx - 1, 1), TBX), cdiv(max(g.ny - 1, 1), TBY), cdiv(max(g.nz - 1, 1), kz));
+    k_res_cc<<<grid, dim3(TBX, TBY), smem_bytes(), s>>>(m.x, m.bc, g, r, st, pr.buf, (int)mode, ch, kz, pr.fs,
+                                                        uniform, beta, dinv32);
 }
 
 unsigned long long launches_res_cc()
