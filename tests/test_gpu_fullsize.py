@@ -92,6 +92,12 @@ def test_cos_cube_512_mixed_full_size(E, oracle_mod):
     for prec, tol in ((E.ECMG_FP64, 1e-13), (E.ECMG_MIXED, 1e-5)):
         got = _at(_np(s.apply(xt, precision=prec)), n, nodes)
         assert np.abs(got - want).max() <= tol * np.abs(want).max(), (prec, np.abs(got - want).max())
+    # the FP32 stencil kernel of the iteration itself, with the autotuned tile shape: q = A x on
+    # the nodes off the Dirichlet faces, 0 on them
+    got = _at(_np(s.apply(xt, precision=E.ECMG_APPLY_K1)), n, nodes)
+    free = np.array([0 < c[0] < n[0] and 0 < c[1] < n[1] and 0 < c[2] < n[2] for c in nodes])
+    assert np.abs(got[free] - want[free]).max() <= 1e-5 * np.abs(want[free]).max()
+    assert np.all(got[~free] == 0.0)
     del xt
     s.close()
     # the same system in FP64: the same discretisation error to 1 %

@@ -45,8 +45,16 @@ def _oracle_levels(oracle_mod, p):
     return betas
 
 
+def _cube_elements_ragged():
+    """One beta, every face Dirichlet, cubic elements on a box of 5 x 3 x 7 coarse cells: the
+    constant-coefficient kernels with ragged tiles on every axis."""
+    return inputs.random_problem(31, n0=(5, 3, 7), levels=4, box=(1.25, 0.75, 1.75), face_bc=[0] * 6,
+                                 contrast=1.0, rtol=1e-9)
+
+
 PROBLEMS = {
     "exp_cube": lambda: inputs.exp_cube(levels=4, rtol=1e-10),
+    "cube_elements_ragged": _cube_elements_ragged,
     "random_mixed_bc_0": lambda: inputs.random_problem(0, n0=(2, 3, 2), levels=4, rtol=1e-10),
     "random_mixed_bc_1": lambda: inputs.random_problem(1, n0=(3, 2, 2), levels=3, rtol=1e-10),
     "problem1_load": lambda: inputs.paper_problem1(levels=4, rtol=1e-9),
@@ -136,7 +144,7 @@ def test_fp64_solve_matches_oracle(E, oracle_mod, name, variant):
     s.close()
 
 
-@pytest.mark.parametrize("name", ["exp_cube", "problem1_load", "random_mixed_bc_0"])
+@pytest.mark.parametrize("name", ["exp_cube", "cube_elements_ragged", "problem1_load", "random_mixed_bc_0"])
 def test_mixed_solve_reaches_tolerance_and_fp64_accuracy(E, oracle_mod, name):
     p = PROBLEMS[name]()
     lv, ost = oracle_mod.ecmg(p, p["rtol"])
@@ -433,6 +441,7 @@ K1_PROBLEMS = {
     # one beta, every face Dirichlet: the constant-coefficient path
     "exp_cube": lambda: inputs.exp_cube(levels=4, rtol=1e-10),
     "cos_cube_ragged": lambda: inputs.cos_cube(levels=3, n0=(9, 5, 7), rtol=1e-8),
+    "cube_elements_ragged": _cube_elements_ragged,
     # general path: variable beta, Robin faces, non-cubic elements
     "random_mixed_bc_0": lambda: inputs.random_problem(0, n0=(2, 3, 2), levels=4, rtol=1e-10),
     "variable_box": lambda: inputs.variable_box(levels=3, n0=(2, 2, 4), rtol=1e-9),
@@ -496,7 +505,8 @@ def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_
     fresh.close()
 
 
-@pytest.mark.parametrize("name", ["exp_cube", "cos_cube_cube", "problem1_load", "random_mixed_bc_0"])
+@pytest.mark.parametrize("name", ["exp_cube", "cos_cube_cube", "cube_elements_ragged", "problem1_load",
+                                  "random_mixed_bc_0"])
 def test_mixed_reported_residual_is_the_true_residual(E, oracle_mod, name):
     """The residual the MIXED solve reports on every level (from its last FP64 residual
     evaluation: the exact constant-coefficient kernel on one-beta all-Dirichlet cubes, the
