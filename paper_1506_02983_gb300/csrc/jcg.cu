@@ -686,8 +686,9 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
     const V* __restrict__ qv4 = reinterpret_cast<const V*>(q);
     const V* __restrict__ dv4 = reinterpret_cast<const V*>(dinv);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (cdiag && *uniform) {
-        const T cd = *cdiag;
+    const bool cc = cdiag && *uniform;
+    if (cc) {
+        // one diagonal: r.z = D^-1 r.r, formed from ||r||^2 after the reduction
         for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += stride) {
             V rr4 = rv4[t];
             const V q4 = qv4[t];
@@ -695,7 +696,6 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
             for (int c = 0; c < W; ++c) {
                 const T rv = vget(rr4, c) - a * vget(const_cast<V&>(q4), c);
                 vget(rr4, c) = rv;
-                rz.add_prod(rv, cd * rv);
                 rr.add_prod(rv, rv);
             }
             rv4[t] = rr4;
@@ -717,6 +717,7 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
     }
     double v[2] = {rz.value(), rr.value()};
     if (grid_sum<2>(v, partials, &st->arrive)) {
+        if (cc) v[0] = (double)*cdiag * v[1];
         update_epilogue<MIXED>(st, v[0], v[1]);
         if (ch.use) {
             cudaGraphSetConditional(ch.loop, st->done ? 0u : 1u);

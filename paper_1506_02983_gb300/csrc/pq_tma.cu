@@ -605,10 +605,11 @@ K1Config k1_default(const Grid& g, const Op& op)
 int k1_candidates(const Grid& g, K1Config* out, int cap)
 {
     (void)g;
-    const int kzs[4] = {16, 32, 64, 128};
+    // planes per block; the in-between values let a level end close to a whole number of waves
+    const int kzs[8] = {8, 12, 16, 24, 32, 48, 64, 128};
     int n = 0;
     for (int v = 0; v < K1_NRY; ++v)
-        for (int z = 0; z < 4; ++z)
+        for (int z = 0; z < 8; ++z)
             if (n < cap) out[n++] = K1Config{K1_RY[v], kzs[z]};
     return n;
 }

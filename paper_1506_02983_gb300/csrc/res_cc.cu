@@ -55,7 +55,7 @@ struct Col {
     long long x, f, d;
 };
 
-__global__ void __launch_bounds__(NT, 4)
+__global__ void __launch_bounds__(NT, 5)
 k_res_cc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mbc, const Grid g,
          float* __restrict__ r, SolveState* st, double* partials, int mode, CondHandles ch, int kz,
          const FixedScale* fs, const int* __restrict__ uniform, const double* __restrict__ beta,
