@@ -174,47 +174,47 @@ __device__ __forceinline__ void exp_finite_element(const Grid& g, const Op& op, 
     if (nc == 5) zstage(std::integral_constant<int, 4>(), 4);
 }
 
-// EXP_true, for the level-(l-1) element (ex, ey, ez): d = U^l - U^{l-1} at its 8 corners, divided
-// by 3, interpolated trilinearly to the element's 3x3x3 level-l nodes (halves and quarters of
-// corner values) and added to U^l. A thread writes the nodes (2 ex + a, ...), a = 0, 1, plus
-// a = 2 on the last element of an axis.
+// EXP_true, for the level-(l-1) element (ex, ey, ez): d = U^l - U^{l-1} at its 8 corners,
+// interpolated trilinearly to the element's 3x3x3 level-l nodes, divided by 3 and added to U^l.
+// The trilinear interpolant at a node with m midpoint coordinates is the sum of the 2^m
+// nearest corner values divided by 2^m, so the corner differences are summed by sum
+// factorisation (x, then y, then z) and each node takes one FMA with the weight 1/(3 2^m):
+// 28 FP64 operations for the 8 owned nodes instead of 62 with averaged values. A thread
+// writes the nodes (2 ex + a, ...), a = 0, 1, plus a = 2 on the last element of an axis.
 __device__ __forceinline__ void exp_true_element(const Grid& g, const double* __restrict__ U1, const Grid& gc,
                                                  const double* __restrict__ U0, double* __restrict__ Ut, int ex,
                                                  int ey, int ez)
 {
-    double D[3][3][3];  // trilinear interpolant of (U^l - U^{l-1}) / 3 at the 3x3x3 nodes
+    double d[2][2][2];  // [c][b][a]
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int a = 0; a < 2; ++a)
-                D[2 * c][2 * b][2 * a] = (U1[g.off(2 * (ex + a), 2 * (ey + b), 2 * (ez + c))] -
-                                          U0[gc.off(ex + a, ey + b, ez + c)]) * (1.0 / 3.0);  // no FP64 divide
-#pragma unroll
-    for (int c = 0; c < 3; c += 2)
-#pragma unroll
-        for (int b = 0; b < 3; b += 2) D[c][b][1] = 0.5 * (D[c][b][0] + D[c][b][2]);
-#pragma unroll
-    for (int c = 0; c < 3; c += 2)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) D[c][1][a] = 0.5 * (D[c][0][a] + D[c][2][a]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) D[1][b][a] = 0.5 * (D[0][b][a] + D[2][b][a]);
+                d[c][b][a] = U1[g.off(2 * (ex + a), 2 * (ey + b), 2 * (ez + c))] - U0[gc.off(ex + a, ey + b, ez + c)];
+    const double w[4] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 12.0, 1.0 / 24.0};  // 1 / (3 2^m)
     const int na = (ex == gc.nx - 1) ? 3 : 2, nb = (ey == gc.ny - 1) ? 3 : 2, nc = (ez == gc.nz - 1) ? 3 : 2;
+    // level-l node offset a (0, 1 = midpoint, 2) from the corner pair (v0, v1) along one axis
+    auto pick = [](int a, double v0, double v1) { return a == 0 ? v0 : (a == 2 ? v1 : v0 + v1); };
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (c >= nc) break;
+    for (int a = 0; a < 3; ++a) {
+        if (a >= na) break;
+        double X[2][2];  // [c][b]
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) X[c][b] = pick(a, d[c][b][0], d[c][b][1]);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if (b >= nb) break;
-            const int64_t orow = g.off(2 * ex, 2 * ey + b, 2 * ez + c);
+            const double Y0 = pick(b, X[0][0], X[0][1]), Y1 = pick(b, X[1][0], X[1][1]);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (a >= na) break;
-                Ut[orow + a] = U1[orow + a] + D[c][b][a];
+            for (int c = 0; c < 3; ++c) {
+                if (c >= nc) break;
+                const double S = pick(c, Y0, Y1);
+                const int64_t o = g.off(2 * ex + a, 2 * ey + b, 2 * ez + c);
+                Ut[o] = fma(S, w[(a == 1) + (b == 1) + (c == 1)], U1[o]);
             }
         }
     }
