@@ -326,7 +326,11 @@ def main():
             ms = t.item()
         return ms
 
+    torch.cuda.synchronize()
+    t_create = time.perf_counter()
     mixed = make(ecmg.ECMG_MIXED)
+    torch.cuda.synchronize()
+    create_ms = (time.perf_counter() - t_create) * 1e3
     u_out = torch.empty_like(u_exact)
     st_mixed, status = mixed.solve(u_out)
     assert status == 0, st_mixed
@@ -427,6 +431,7 @@ def main():
         cpu = cpu_baseline(args, args.cpu_levels)
 
     dofs = free_dofs(nf) * world
+    node_its = sum(free_dofs(n0 << l) * st_mixed["iters"][l] for l in range(L))
     value = dofs / (ms_mixed * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "k_pq_float_traffic.json")
@@ -460,6 +465,15 @@ def main():
                      "launch_ms_alone_cuda_events": k1_ms, "tiles": {"ry": tiles[0], "kz": tiles[1]},
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy; of measured)"},
         "kernels_alone": kern,
+        # the two ways of counting dofs: finest free dofs per solve (value), and free dofs times
+        # JCG iterations summed over the levels; the byte model charges each node-iteration the
+        # 36 bytes K1 and K2 move on a constant-coefficient level (24 + 12)
+        "node_iterations_per_solve": node_its,
+        "gdofs_node_iterations": node_its * world / (ms_mixed * 1e-3) / 1e9,
+        "byte_model": {"bytes_per_node_iteration": 36, "bytes_per_solve": 36.0 * node_its,
+                       "fraction_of_peak": (36.0 * node_its / (ms_mixed * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None},
+        "roofline_frac_of_spec_8tbs": k1_gbps / 8000.0,
+        "create_ms": create_ms,
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": dofs / (ms_e2e * 1e-3) / 1e9, "unit": "Gdof/s", "h2d_bytes_per_step": h2d,
