@@ -285,9 +285,9 @@ void record_setup(Rec& R)
             if (p.beta) pack_elements(v.g, p.beta, v.beta, s);
             else fill_beta(v.g, p.beta_const, v.beta, s);
             if (p.f_mode == ECMG_F_SEPARABLE) sep_load_finest(v.g, p.f_terms, p.f, v.Hf, v.b, s);
-            else pack_nodal(v.g, p.f, v.f, s);
+            else pack_nodal(v.g, p.f, p.f_mode == ECMG_F_LOAD ? v.b : v.f, s);  // the load is b itself
             if (p.g_D && p.gD_terms > 0) sep_nodal(v.g, p.gD_terms, p.g_D, v.gD, s);
-            else if (p.g_D) pack_nodal(v.g, p.g_D, v.gD, s);
+            else if (p.g_D) pack_dirichlet(v.g, v.op, p.g_D, v.gD, s);
             if (p.g_R) pack_nodal(v.g, p.g_R, v.gR, s);
         } else {
             Level& u = h->lv[l + 1];
@@ -300,15 +300,14 @@ void record_setup(Rec& R)
             else if (p.g_D) inject_nodal(v.g, u.gD, u.g, v.gD, s);
             if (p.g_R) inject_nodal(v.g, u.gR, u.g, v.gR, s);
         }
-        if (p.f_mode == ECMG_F_LOAD) {
-            if (l == L - 1) ck(cudaMemcpyAsync(v.b, v.f, (size_t)v.g.total * 8, cudaMemcpyDeviceToDevice, s));
-        } else if (p.f_mode == ECMG_F_NODAL) {
+        if (p.f_mode == ECMG_F_NODAL) {
             nodal_load(v.g, v.op, v.f, p.g_R ? v.gR : nullptr, v.b, s);
         }
+        uniform_check(v.g, v.beta, v.uniform, s);
         // FP64 diagonal for FP64 JCG and the direct levels, FP32 for the FP32 iteration of MIXED
         jacobi_diag(v.g, v.op, v.beta, (!mixed || l < 2) ? v.dinv : nullptr, mixed ? v.dinv32 : nullptr,
-                    mixed ? v.beta32 : nullptr, h->opt.preconditioner == ECMG_PREC_JACOBI, s);
-        uniform_check(v.g, v.beta, v.uniform, s);
+                    mixed ? v.beta32 : nullptr, h->opt.preconditioner == ECMG_PREC_JACOBI, s,
+                    l >= 2 ? v.uniform : nullptr);
     }
 }
 
@@ -335,7 +334,8 @@ void record_level(Rec& R, int l)
     CondHandles none{0, 0, 0};
 
     launch_state_init(st, rtol, o.inner_rtol, max_iters, fixed ? 1 : 0, R.s());
-    dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s());
+    // levels >= 2: EXP_finite writes every free node below, so only the shell that ||f_h|| reads
+    dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s(), /*shell=*/l >= 2);
     launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s());
     // constant coefficient: b / c for the exact integer residual, kept in the FP64 r vector,
     // which the MIXED iteration does not use

@@ -146,6 +146,8 @@ struct Partials {
 
 // ---- set-up kernels (setup.cu) -------------------------------------------------------
 void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s);
+// pack_nodal on the Dirichlet nodes only (the only nodes where g_D is read)
+void pack_dirichlet(const Grid& g, const Op& op, const double* dense, double* dst, cudaStream_t s);
 void pack_elements(const Grid& g, const double* dense, double* dst, cudaStream_t s);
 void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s);
 void coarsen_beta(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
@@ -153,10 +155,16 @@ void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, 
 void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
 void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
                 cudaStream_t s);
+// D^-1 in FP64 and/or FP32 (beta32 = beta rounded). uniform: the level's flag (uniform_check
+// already run), with which a one-beta all-Dirichlet cube keeps only the D^-1 of node (1, 1, 1)
+// in FP32; nullptr: every node.
 void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
-                 float* beta32, int precond, cudaStream_t s);
-void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x,
-                         cudaStream_t s);
+                 float* beta32, int precond, cudaStream_t s, const int* uniform = nullptr);
+// x = g_D on the Dirichlet nodes (0 when gD is null) and 0 on the free nodes; shell: only the
+// nodes within two steps of a Dirichlet face (enough for ||f_h|| before EXP_finite writes every
+// free node of the level).
+void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x, cudaStream_t s,
+                         bool shell = false);
 void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
 void convert_f64(const float* src, double* dst, int64_t n, cudaStream_t s);
 // flag = 1 when every element of the level has the same beta, else 0.

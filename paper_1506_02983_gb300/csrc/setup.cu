@@ -24,10 +24,12 @@ inline dim3 grid3(int mx, int my, int mz) { return dim3((mx + TX) / TX, (my + TY
     const int k = blockIdx.z;                                                       \
     if (i > (MX) || j > (MY)) return
 
-__global__ void k_pack_nodal(Grid g, const double* __restrict__ dense, double* __restrict__ dst)
+__global__ void k_pack_nodal(Grid g, Op op, const double* __restrict__ dense, double* __restrict__ dst,
+                             int dirichlet_only)
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
+    if (dirichlet_only && !on_dirichlet(g, op, i, j, k)) return;
     const int64_t t = i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);  // dense index
     dst[g.off(i, j, k)] = dense[t];
 }
@@ -107,18 +109,31 @@ __global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, doubl
 // The same diagonal in FP32 arithmetic from the FP32 betas, for the FP32 iteration of MIXED
 // mode: no FP64 division or conversion per node (FP64 runs at 1/64 of the FP32 rate on GB300).
 // Robin terms (boundary nodes only) are formed in FP64 and rounded.
-__global__ void k_jacobi32(Grid g, Op op, const float* __restrict__ beta32, float* __restrict__ dinv32, int precond)
+// uniform: the level's flag, already set by the set-up. On a level with one beta, every face
+// Dirichlet and cubic elements the FP32 iteration reads D^-1 at node (1, 1, 1) only (it is the
+// same on every free node), so the other nodes are skipped.
+__global__ void k_jacobi32(Grid g, Op op, const float* __restrict__ beta32, float* __restrict__ dinv32, int precond,
+                           const int* __restrict__ uniform)
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
+    const bool diri = (op.bc[0] | op.bc[1] | op.bc[2] | op.bc[3] | op.bc[4] | op.bc[5]) == 0;
+    if (uniform && diri && op.cube && *uniform && !(i == 1 && j == 1 && k == 1)) return;
     dinv32[g.off(i, j, k)] = jacobi32_at(g, op, beta32, i, j, k, precond);
 }
 
 // x = g_D on Dirichlet nodes, 0 on free nodes (gD == nullptr: zero everywhere).
-__global__ void k_dirichlet_ext(Grid g, Op op, const double* __restrict__ gD, double* __restrict__ x)
+__global__ void k_dirichlet_ext(Grid g, Op op, const double* __restrict__ gD, double* __restrict__ x, int shell)
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
+    if (shell) {
+        // only nodes within two steps of a Dirichlet face
+        auto near = [](int a, int n, int lo, int hi) { return (lo == 0 && a <= 2) || (hi == 0 && a >= n - 2); };
+        if (!near(i, g.nx, op.bc[0], op.bc[1]) && !near(j, g.ny, op.bc[2], op.bc[3]) &&
+            !near(k, g.nz, op.bc[4], op.bc[5]))
+            return;
+    }
     const int64_t o = g.off(i, j, k);
     x[o] = (gD && on_dirichlet(g, op, i, j, k)) ? gD[o] : 0.0;
 }
@@ -175,7 +190,12 @@ void convert_f64(const float* src, double* dst, int64_t n, cudaStream_t s)
 
 void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s)
 {
-    k_pack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, dense, dst);
+    Op none{};
+    k_pack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, none, dense, dst, 0);
+}
+void pack_dirichlet(const Grid& g, const Op& op, const double* dense, double* dst, cudaStream_t s)
+{
+    k_pack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, dense, dst, 1);
 }
 void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s)
 {
@@ -203,17 +223,18 @@ void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, 
     k_nodal_load<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, f, gR, b);
 }
 void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
-                 float* beta32, int precond, cudaStream_t s)
+                 float* beta32, int precond, cudaStream_t s, const int* uniform)
 {
     if (dinv64) k_jacobi64<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta, dinv64, precond);
     if (beta32) {
         convert_f32(beta, beta32, g.total, s);
-        if (dinv32) k_jacobi32<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32, precond);
+        if (dinv32)
+            k_jacobi32<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32, precond, uniform);
     }
 }
-void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x, cudaStream_t s)
+void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x, cudaStream_t s, bool shell)
 {
-    k_dirichlet_ext<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, gD, x);
+    k_dirichlet_ext<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, gD, x, shell ? 1 : 0);
 }
 
 unsigned long long launches_setup()
