@@ -303,7 +303,8 @@ void record_setup(Rec& R)
         if (p.f_mode == ECMG_F_NODAL) {
             nodal_load(v.g, v.op, v.f, p.g_R ? v.gR : nullptr, v.b, s);
         }
-        uniform_check(v.g, v.beta, v.uniform, s);
+        if (mixed && l >= 2) beta32_uniform(v.g, v.beta, v.beta32, v.uniform, s);
+        else uniform_check(v.g, v.beta, v.uniform, s);
         // FP64 diagonal for FP64 JCG and the direct levels, FP32 for the FP32 iteration of MIXED
         jacobi_diag(v.g, v.op, v.beta, (!mixed || l < 2) ? v.dinv : nullptr, mixed ? v.dinv32 : nullptr,
                     mixed ? v.beta32 : nullptr, h->opt.preconditioner == ECMG_PREC_JACOBI, s,

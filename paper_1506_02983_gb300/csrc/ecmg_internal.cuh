@@ -155,9 +155,9 @@ void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, 
 void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
 void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
                 cudaStream_t s);
-// D^-1 in FP64 and/or FP32 (beta32 = beta rounded). uniform: the level's flag (uniform_check
-// already run), with which a one-beta all-Dirichlet cube keeps only the D^-1 of node (1, 1, 1)
-// in FP32; nullptr: every node.
+// D^-1 in FP64 and/or FP32 (beta32 = beta rounded). uniform: the level's flag, with beta32
+// already converted by beta32_uniform; a one-beta all-Dirichlet cube then keeps only the D^-1
+// of node (1, 1, 1) in FP32. nullptr: beta32 converted here, D^-1 on every node.
 void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
                  float* beta32, int precond, cudaStream_t s, const int* uniform = nullptr);
 // x = g_D on the Dirichlet nodes (0 when gD is null) and 0 on the free nodes; shell: only the
@@ -169,6 +169,8 @@ void convert_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
 void convert_f64(const float* src, double* dst, int64_t n, cudaStream_t s);
 // flag = 1 when every element of the level has the same beta, else 0.
 void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s);
+// beta32 = beta (every padded element) and the flag of uniform_check, in one pass.
+void beta32_uniform(const Grid& g, const double* beta, float* beta32, int* flag, cudaStream_t s);
 
 // Kernel executions counted on the device, per source file (for the benchmark's launch count).
 unsigned long long launches_setup();

@@ -161,6 +161,23 @@ __global__ void k_convert_f32(const double* __restrict__ src, float* __restrict_
         dst[t] = (float)src[t];
 }
 
+// beta32 = beta over the whole padded level (ghost elements included) and, in the same pass,
+// flag = 0 when a real element's beta differs from element (0, 0, 0)'s (bit patterns compared
+// as integers). Row jj, plane kk of the padded layout per thread row.
+__global__ void k_beta32_uniform(Grid g, const double* __restrict__ beta, float* __restrict__ beta32, int* flag)
+{
+    COUNT_LAUNCH();
+    const int ii = blockIdx.x * TX + threadIdx.x, jj = blockIdx.y * TY + threadIdx.y, kk = blockIdx.z;
+    if (ii >= g.pitch || jj >= g.ny + 3) return;
+    const int64_t t = (int64_t)kk * g.plane + (int64_t)jj * g.pitch + ii;
+    const double v = beta[t];
+    beta32[t] = (float)v;
+    const int i = ii - XL, j = jj - 1, k = kk - 1;  // element (i, j, k) sits at its lowest corner node
+    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz &&
+        __double_as_longlong(v) != __double_as_longlong(beta[g.off(0, 0, 0)]))
+        *flag = 0;
+}
+
 __global__ void k_convert_f64(const float* __restrict__ src, double* __restrict__ dst, int64_t n)
 {
     COUNT_LAUNCH();
@@ -169,6 +186,13 @@ __global__ void k_convert_f64(const float* __restrict__ src, double* __restrict_
 }
 
 }  // namespace
+
+void beta32_uniform(const Grid& g, const double* beta, float* beta32, int* flag, cudaStream_t s)
+{
+    k_set_flag<<<1, 1, 0, s>>>(flag);
+    k_beta32_uniform<<<dim3((g.pitch + TX - 1) / TX, (g.ny + 3 + TY - 1) / TY, g.nz + 3), dim3(TX, TY), 0, s>>>(
+        g, beta, beta32, flag);
+}
 
 void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s)
 {
@@ -227,7 +251,7 @@ void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64
 {
     if (dinv64) k_jacobi64<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta, dinv64, precond);
     if (beta32) {
-        convert_f32(beta, beta32, g.total, s);
+        if (!uniform) convert_f32(beta, beta32, g.total, s);  // else beta32_uniform has run
         if (dinv32)
             k_jacobi32<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32, precond, uniform);
     }
