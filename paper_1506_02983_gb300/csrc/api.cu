@@ -594,6 +594,7 @@ void record_batched(Rec& R)
         const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_FLAT);
         if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
+            blaunch_absmax(items, flat, R.s());
             blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, CondHandles{loop, 0, 1}, R.s());
             R.open(loop, cudaGraphCondTypeWhile);
             for (int half = 0; half < 2; ++half) {
@@ -608,6 +609,7 @@ void record_batched(Rec& R)
             R.close();
         } else {
             const CondHandles none{0, 0, 0};
+            blaunch_absmax(items, flat, R.s());
             blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, none, R.s());
             int half = 0;
             while (any_state(h, ids, false)) {

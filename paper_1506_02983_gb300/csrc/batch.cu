@@ -12,6 +12,7 @@
 #include "exp_core.cuh"
 #include "jcg_core.cuh"
 #include "march.cuh"
+#include "march_fx.cuh"
 #include "setup_core.cuh"
 #include "stencil_core.cuh"
 
@@ -68,6 +69,20 @@ __device__ __forceinline__ void bblock_sum(double (&v)[NP], double* sh)
         }
     }
     __syncthreads();
+}
+
+// Max of m over a one-dimensional block into *dst (bit patterns of nonnegative doubles order
+// like the values). Every thread of the block must call it.
+__device__ __forceinline__ void block_max_to(unsigned long long m, unsigned long long* dst)
+{
+    __shared__ unsigned long long sh[32];
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, sh[w]);
+        atomicMax(dst, m);
+    }
 }
 
 // Sum v over the nb blocks of one item (fixed order: deterministic). True in thread 0 of the
@@ -325,17 +340,27 @@ __global__ void __launch_bounds__(mt::NT) bk_res(const BItem* __restrict__ items
         double rr = 0.0;
         Acc<float> rz;
         const double* x = it.U;
-        auto src = [&](int64_t o) -> double { return x[o]; };
-        auto body = [&](int, int, int, int64_t o, double Av, double) {
+        auto body = [&](int, int, int, int64_t o, double Av) {
             const double rv = it.b[o] - Av;
             const float ro = (float)rv;
             it.r32[o] = ro;
             rr = fma(rv, rv, rr);
             rz.add_prod(ro, it.dinv32[o] * ro);
         };
-        march_range<ROBIN, CUBE, double, double>(it.g, it.op, it.beta, rg, bx, by, bz, it.kz, src, body);
+        if constexpr (CUBE && !ROBIN) {
+            // exact integer element sums (march_fx.cuh) on the scale of max |x| (bk_absmax or
+            // bk_fold just before)
+            const fx::FixedFrame fr = fx::fixed_frame(st->xbits);
+            if (fr.finite) march_range_fxv(it.g, it.beta, x, rg, bx, by, bz, it.kz, fr, body);
+            else if (sl.lb == 0 && threadIdx.x == 0 && threadIdx.y == 0) rr = nan("");  // the iterate is not finite
+        } else {
+            auto src = [&](int64_t o) -> double { return x[o]; };
+            auto body6 = [&](int i, int j, int k, int64_t o, double Av, double) { body(i, j, k, o, Av); };
+            march_range<ROBIN, CUBE, double, double>(it.g, it.op, it.beta, rg, bx, by, bz, it.kz, src, body6);
+        }
         double v[2] = {rr, rz.value()};
         if (item_sum<2>(v, it.part, &st->arrive, sl.lb, sl.nb)) {
+            st->xbits = 0ull;  // every block has read the scale; the next fold or bk_absmax takes it anew
             res_epilogue(st, v[0], v[1], mode, CondHandles{0, 0, 0});
             if (item_arrives(ctl, L.n)) batch_conditions(items, L, CondHandles{ch.loop, 0, ch.use ? 1 : 0});
         }
@@ -430,14 +455,34 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_fold(const BItem* __restrict__ it
     const BItem& it = items[sl.item];
     const SolveState* st = it.st;
     if (st->done || !st->need_update) return;
-    const double a = st->alpha_prev;
+    const float a = (float)st->alpha_prev;
     const float* __restrict__ p = pnew_is_b ? it.pB32 : it.pA32;
     const int64_t base = (int64_t)sl.lb * BFLAT_ELEMS;
     const int64_t end = min(base + BFLAT_ELEMS, it.g.total);
+    unsigned long long m = 0ull;
     for (int64_t t = base + threadIdx.x; t < end; t += FLAT_TPB) {
-        it.U[t] += (double)it.e32[t] + a * (double)p[t];
+        // the FP32 correction combined in FP32, added with one FP64 operation (jcg.cu k_fold32)
+        const double xn = it.U[t] + fx::widen(fmaf(a, p[t], it.e32[t]));
+        it.U[t] = xn;
         it.e32[t] = 0.f;
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(xn)));
     }
+    block_max_to(m, &it.st->xbits);  // the scale of the exact residual that follows
+}
+
+// max |x| of each item's iterate into its state (the scale of the initial exact residual).
+__global__ void __launch_bounds__(FLAT_TPB) bk_absmax(const BItem* __restrict__ items, const __grid_constant__ BLaunch L)
+{
+    COUNT_LAUNCH();
+    const Slot sl = find_slot(L);
+    const BItem& it = items[sl.item];
+    if (it.st->done) return;
+    const int64_t base = (int64_t)sl.lb * BFLAT_ELEMS;
+    const int64_t end = min(base + BFLAT_ELEMS, it.g.total);
+    unsigned long long m = 0ull;
+    for (int64_t t = base + threadIdx.x; t < end; t += FLAT_TPB)
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(it.U[t])));
+    block_max_to(m, &it.st->xbits);
 }
 
 // EXP_true for levels >= 2.
@@ -529,6 +574,11 @@ void blaunch_pq(const BItem* items, const BLaunch& stencil, int robin, int cube,
 void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s)
 {
     bk_update<<<nblocks(flat), FLAT_TPB, 0, s>>>(items, flat, ctl, ch);
+}
+
+void blaunch_absmax(const BItem* items, const BLaunch& flat, cudaStream_t s)
+{
+    bk_absmax<<<nblocks(flat), FLAT_TPB, 0, s>>>(items, flat);
 }
 
 void blaunch_fold(const BItem* items, const BLaunch& flat, int pnew_is_b, cudaStream_t s)

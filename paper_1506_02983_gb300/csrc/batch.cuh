@@ -86,7 +86,10 @@ void blaunch_level_start(const BItem* items, const BLaunch& one, const BLaunch& 
 // search directions and corrections.
 void blaunch_guess(const BItem* items, const BLaunch& expf, const BLaunch& flat_all, int variant, cudaStream_t s);
 // FP64 residual r = b - A x (stored FP32) with r.z and ||r||^2 per item; mode RES_INIT or
-// RES_REPLACE (items that asked for a replacement only). Sets the loop condition.
+// RES_REPLACE (items that asked for a replacement only). Sets the loop condition. With cubic
+// elements and no Robin term, A x is exact in fixed point up to the products with beta
+// (march_fx.cuh), on the scale of max |x| that blaunch_absmax (before RES_INIT) or
+// blaunch_fold (before RES_REPLACE) left in the item's state.
 void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube, ResMode mode, BCtl* ctl,
                  CondHandles ch, cudaStream_t s);
 // One FP32 JCG iteration: K1 (p, q = A p, deferred correction, p.q) and K2 (r, r.z, tests).
@@ -94,8 +97,11 @@ void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube
 void blaunch_pq(const BItem* items, const BLaunch& stencil, int robin, int cube, int pin_is_b, int pidx,
                 cudaStream_t s);
 void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s);
-// Fold the FP32 correction into the FP64 iterate for items that asked for a replacement.
+// Fold the FP32 correction into the FP64 iterate for items that asked for a replacement, and
+// take max |x| of the new iterate into the item's state (the scale of the exact residual).
 void blaunch_fold(const BItem* items, const BLaunch& flat, int pnew_is_b, cudaStream_t s);
+// max |x| of each running item's iterate into its state, before an initial residual.
+void blaunch_absmax(const BItem* items, const BLaunch& flat, cudaStream_t s);
 // EXP_true for levels >= 2.
 void blaunch_exp_true(const BItem* items, const BLaunch& expt, cudaStream_t s);
 

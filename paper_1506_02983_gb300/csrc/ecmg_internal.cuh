@@ -112,6 +112,7 @@ struct SolveState {
     int p_latest;        // which of the two search-direction buffers holds the newest p
     unsigned int arrive; // block arrival counter of the last-block reductions
     unsigned long long bcbits;  // MIXED, constant coefficient: bits of max |b / c| (fixed-point scale)
+    unsigned long long xbits;   // batched MIXED: bits of max |x| for the next exact residual (0 = not taken)
     int fixed;           // 1: exactly max_iters steps, no tolerance test (the schedule of Alg. 3)
 };
 

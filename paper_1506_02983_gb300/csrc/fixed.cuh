@@ -36,5 +36,19 @@ __device__ __forceinline__ long long to_fixed(double x, int s)
     return b < 0 ? -v : v;
 }
 
+// Exact widening of an FP32 value to FP64 by rebiasing its exponent field (integer operations;
+// the conversion instruction runs on the FP64 pipe, 1/64 of the FP32 rate on GB300). Zeros
+// keep their sign; subnormals, Inf and NaN take the conversion instruction.
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned int b = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+    const unsigned int ex = (b >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
 }  // namespace fx
 }  // namespace ecmg

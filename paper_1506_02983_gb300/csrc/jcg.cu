@@ -738,20 +738,6 @@ __global__ void k_final64(int64_t n, double* __restrict__ x, const double* __res
         x[t] = fma(a, p[t], x[t]);
 }
 
-// Exact widening of an FP32 value to FP64 by rebiasing its exponent field (integer operations;
-// the conversion instruction runs on the FP64 pipe, 1/64 of the FP32 rate on GB300). Zeros
-// keep their sign; subnormals, Inf and NaN take the conversion instruction.
-__device__ __forceinline__ double widen(float f)
-{
-    const unsigned int b = __float_as_uint(f);
-    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
-    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
-    const unsigned int ex = (b >> 23) & 0xffu;
-    if (ex == 0u || ex == 0xffu) return (double)f;
-    return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 896u) << 52) |
-                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
-}
-
 // MIXED fold at a residual replacement: x += e + alpha_prev p, e = 0. The FP32 correction is
 // combined in FP32 (one more rounding of an FP32 quantity) and added to x with a single FP64
 // operation. On a level with one beta the block also takes max |x| of the new iterate into

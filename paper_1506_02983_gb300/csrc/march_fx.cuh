@@ -1,0 +1,119 @@
+// march_fx.cuh -- the operator of a level with cubic elements and variable beta, exact in
+// fixed point up to the products with beta (batch.cu, jcg.cu).
+//
+// For a cube element of side h the element matrix is beta_e h times the unit-cube matrix:
+// 1/3 on the diagonal, 0 between two nodes on an element edge, -1/12 between two nodes on a
+// face diagonal or on the body diagonal. Every row sums to zero, so at node i
+//     (A x)_i = -(h / 12) sum_e beta_e I_e,   I_e = sum_{j far from i in e} (x_j - x_i),
+// the inner sum running over the three face-diagonal nodes and the body-diagonal node of
+// element e. With the iterate in fixed point, x = X 2^-s (64-bit X, the scale of fixed.cuh),
+// each I_e is an exact integer sum and only the eight products beta_e I_e and their sum are
+// FP64 operations -- about a third of the FP64 work of the difference form (FP64 runs at
+// 1/64 of the FP32 rate on GB300). Elements outside the box carry beta = 0 in the padded
+// layout, so nodes on a Neumann face need no special case; Robin terms are not included.
+#pragma once
+
+#include "fixed.cuh"
+#include "march.cuh"
+
+namespace ecmg {
+
+// The z-march of march_range (march.cuh) with the operand staged as fixed-point integers:
+// body(i, j, k, offset, A x) for every node of the range. x: the level vector (FP64, padded).
+template <typename BODY>
+__device__ __forceinline__ void march_range_fxv(const Grid& g, const double* __restrict__ beta,
+                                                const double* __restrict__ x, const NodeRange& rg, int bx, int by,
+                                                int bz, int kz, const fx::FixedFrame& fr, BODY body)
+{
+    constexpr int NT = mt::NT;
+    constexpr int PC = (BX + 2) * (BY + 2), SC = (BX + 1) * (BY + 1);  // plane and slab cells
+    constexpr int NP = (PC + NT - 1) / NT, NS = (SC + NT - 1) / NT;    // cells per thread
+    __shared__ long long sv[3][BY + 2][BX + 2];
+    __shared__ double sb[2][BY + 1][BX + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int i0 = rg.ilo + bx * BX, j0 = rg.jlo + by * BY;
+    const int kb = rg.klo + bz * kz;
+    const int ke = min(kb + kz, rg.khi + 1);
+    const double cA = -g.h[0] / 12.0 * fr.inv;  // A x = cA sum_e beta_e I_e
+
+    int pofs[NP], sofs[NS];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+        const int cell = tid + c * NT;
+        const int i = i0 - 1 + cell % (BX + 2), j = j0 - 1 + cell / (BX + 2);
+        pofs[c] = (cell < PC && i <= g.nx + 1 && j <= g.ny + 1) ? g.in_plane(i, j) : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < NS; ++c) {
+        const int cell = tid + c * NT;
+        const int ex = i0 - 1 + cell % (BX + 1), ey = j0 - 1 + cell / (BX + 1);
+        sofs[c] = (cell < SC && ex <= g.nx + 1 && ey <= g.ny + 1) ? g.in_plane(ex, ey) : -1;
+    }
+    double rp[NP], rb[NS];
+    auto fetch_plane = [&](int k) {
+        const int64_t base = g.plane_base(k);
+#pragma unroll
+        for (int c = 0; c < NP; ++c)
+            if (pofs[c] >= 0) rp[c] = x[base + pofs[c]];
+    };
+    auto fetch_slab = [&](int ez) {
+        const int64_t base = g.plane_base(ez);
+#pragma unroll
+        for (int c = 0; c < NS; ++c)
+            if (sofs[c] >= 0) rb[c] = beta[base + sofs[c]];
+    };
+    auto store_plane = [&](int k) {
+        long long* dst = &sv[(k + 3) % 3][0][0];
+#pragma unroll
+        for (int c = 0; c < NP; ++c)
+            if (tid + c * NT < PC) dst[tid + c * NT] = pofs[c] >= 0 ? fx::to_fixed(rp[c], fr.s) : 0ll;
+    };
+    auto store_slab = [&](int ez) {
+        double* dst = &sb[(ez + 2) % 2][0][0];
+#pragma unroll
+        for (int c = 0; c < NS; ++c)
+            if (tid + c * NT < SC) dst[tid + c * NT] = sofs[c] >= 0 ? rb[c] : 0.0;
+    };
+
+    fetch_plane(kb - 1);
+    store_plane(kb - 1);
+    fetch_plane(kb);
+    store_plane(kb);
+    fetch_slab(kb - 1);
+    store_slab(kb - 1);
+    if (kb < ke) {
+        fetch_plane(kb + 1);
+        fetch_slab(kb);
+    }
+    for (int k = kb; k < ke; ++k) {
+        store_plane(k + 1);
+        store_slab(k);
+        if (k + 1 < ke) {
+            fetch_plane(k + 2);
+            fetch_slab(k + 1);
+        }
+        __syncthreads();
+        const int i = i0 + tx, j = j0 + ty;
+        if (i <= rg.ihi && j <= rg.jhi) {
+            const int pl[3] = {(k + 2) % 3, k % 3, (k + 1) % 3};  // planes k-1, k, k+1
+            auto X = [&](int dx, int dy, int dz) -> long long { return sv[pl[dz + 1]][ty + 1 + dy][tx + 1 + dx]; };
+            const long long x4 = 4 * X(0, 0, 0);
+            double S = 0.0;
+#pragma unroll
+            for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+                for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+                    for (int ex = 0; ex < 2; ++ex) {
+                        // element (i-1+ex, j-1+ey, k-1+ez); its other nodes lie towards (ox, oy, oz)
+                        const int ox = ex ? 1 : -1, oy = ey ? 1 : -1, oz = ez ? 1 : -1;
+                        const long long I = (X(ox, oy, 0) + X(ox, 0, oz)) + (X(0, oy, oz) + X(ox, oy, oz)) - x4;
+                        S = fma(sb[ez ? k % 2 : (k + 1) % 2][ty + ey][tx + ex], (double)I, S);
+                    }
+            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), cA * S);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace ecmg
