@@ -15,6 +15,7 @@
 #include "jcg.cuh"
 #include "jcg_core.cuh"
 #include "march.cuh"
+#include "march_fx.cuh"
 #include "stencil_core.cuh"
 
 #include <cmath>
@@ -385,14 +386,14 @@ __device__ __forceinline__ void march_fixed(FixedSmem& sm, const Grid& g, const 
 }
 
 // max |x| over a level vector into fs->bits (bit patterns of nonnegative doubles order like the
-// values; any Inf or NaN gives exponent 0x7ff). Skipped when the level has more than one beta,
-// or when a residual replacement is not going to run.
+// values; any Inf or NaN gives exponent 0x7ff). Skipped when no fixed-point operator follows
+// (more than one beta, and not `always`), or when a residual replacement is not going to run.
 __global__ void __launch_bounds__(UPD_TPB) k_absmax(int64_t n, const double* __restrict__ x, const int* uniform,
-                                                   const SolveState* st, int mode, FixedScale* fs,
+                                                   int always, const SolveState* st, int mode, FixedScale* fs,
                                                    unsigned long long* partials)
 {
     COUNT_LAUNCH();
-    if (!*uniform) return;
+    if (!always && !*uniform) return;
     if (st && mode == RES_REPLACE && st->done) return;
     __shared__ unsigned long long sh[UPD_TPB / 32];
     __shared__ unsigned int ticket;
@@ -547,10 +548,17 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
         rr = fma(rv, rv, rr);
         rz.add_prod(ro, dinv[o] * ro);
     };
-    if (*uniform) {
+    if (*uniform || (CUBE && !ROBIN)) {
         const FixedFrame fr = fixed_frame(fs->bits);
-        if (fr.finite) march_fixed<ROBIN>(fsm, g, op, beta[g.off(0, 0, 0)], fr, kz, src, body);
-        else if (threadIdx.x == 0 && threadIdx.y == 0) rr = nan("");  // breakdown: the iterate is not finite
+        if (!fr.finite) {
+            if (threadIdx.x == 0 && threadIdx.y == 0) rr = nan("");  // breakdown: the iterate is not finite
+        } else if (*uniform) {
+            march_fixed<ROBIN>(fsm, g, op, beta[g.off(0, 0, 0)], fr, kz, src, body);
+        } else if constexpr (CUBE && !ROBIN) {
+            // variable beta on cubic elements: integer element sums (march_fx.cuh)
+            auto body5 = [&](int i, int j, int k, int64_t o, double Av) { body(i, j, k, o, Av, 0.0); };
+            march_range_fxv(g, beta, x, all_nodes(g), blockIdx.x, blockIdx.y, blockIdx.z, kz, fr, body5);
+        }
     } else {
         march<ROBIN, CUBE, double, double>(g, op, beta, kz, src, body);
     }
@@ -879,9 +887,9 @@ void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
 }
 // max |x| for the fixed-point evaluation (a no-op on levels with more than one beta)
 void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
-                   Partials pr, cudaStream_t s)
+                   Partials pr, cudaStream_t s, bool always)
 {
-    k_absmax<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, uniform, st, mode, pr.fs,
+    k_absmax<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, uniform, always ? 1 : 0, st, mode, pr.fs,
                                                         reinterpret_cast<unsigned long long*>(pr.buf));
 }
 void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
@@ -889,7 +897,7 @@ void launch_res64(const Grid& g, const Op& op, const double* beta, const int* un
                   CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    launch_absmax(g, x, uniform, st, (int)mode, pr, s);
+    launch_absmax(g, x, uniform, st, (int)mode, pr, s, op.cube && !has_robin(op));
     ECMG_VARIANT(k_res, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
                                                                             st, pr.buf, (int)mode, ch, kz, pr.fs,
                                                                             nullptr);
@@ -912,7 +920,7 @@ void launch_res32(const Grid& g, const Op& op, const double* beta, const int* un
                   CondHandles ch, cudaStream_t s, const double* bc)
 {
     const int kz = stencil_kz(g);
-    launch_absmax(g, x, uniform, st, (int)mode, pr, s);
+    launch_absmax(g, x, uniform, st, (int)mode, pr, s, op.cube && !has_robin(op));
     if (!constant_coefficient_shape(g, op)) bc = nullptr;
     ECMG_VARIANT(k_res, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
                                                                            st, pr.buf, (int)mode, ch, kz, pr.fs,

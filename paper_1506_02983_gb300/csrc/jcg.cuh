@@ -29,8 +29,9 @@ void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
                  const float* dinv, const float* pold, float* pnew, float* q, float* e,
                  SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
 // r = b - A x on free nodes, 0 on Dirichlet nodes; r stored as double or float; ||r||^2 and
-// r.dinv.r reduced; last block acts by ResMode. A x in FP64 arithmetic, or exactly in fixed
-// point on a level with one beta (two launches: max |x|, then the residual).
+// r.dinv.r reduced; last block acts by ResMode. A x exactly in fixed point on a level with one
+// beta, in fixed point up to the beta products with variable beta on cubic elements without
+// Robin terms (march_fx.cuh), else in FP64 arithmetic (two launches: max |x|, then the residual).
 void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const double* dinv, double* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s);
@@ -40,9 +41,10 @@ void launch_res32(const Grid& g, const Op& op, const double* beta, const int* un
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s, const double* bc = nullptr);
 // max |x| over the level vector into pr.fs (the fixed-point scale of the exact residual) when the
-// level's uniform flag is set; skipped for a replacement (mode RES_REPLACE) of a finished level.
+// level's uniform flag is set, or always with `always` (variable beta on cubic elements without
+// Robin terms); skipped for a replacement (mode RES_REPLACE) of a finished level.
 void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
-                   Partials pr, cudaStream_t s);
+                   Partials pr, cudaStream_t s, bool always = false);
 // bc = b / c (c = -beta h / 36) and max |bc| into the level state, when the level has one beta,
 // every face Dirichlet and cubic elements (a no-op otherwise).
 void launch_scale_load(const Grid& g, const Op& op, const double* b, double* bc, const double* beta,

@@ -55,6 +55,12 @@ def _cube_elements_ragged():
 PROBLEMS = {
     "exp_cube": lambda: inputs.exp_cube(levels=4, rtol=1e-10),
     "cube_elements_ragged": _cube_elements_ragged,
+    # variable beta on cubic elements without Robin terms (the fixed-point element sums), one
+    # with every face Dirichlet and one with Neumann faces (free boundary nodes)
+    "random_cube_dirichlet": lambda: inputs.random_problem(51, n0=(3, 2, 4), levels=4, box=(0.75, 0.5, 1.0),
+                                                           face_bc=[0] * 6, rtol=1e-10),
+    "random_cube_neumann": lambda: inputs.random_problem(52, n0=(2, 3, 2), levels=4, box=(0.5, 0.75, 0.5),
+                                                         face_bc=[0, 1, 1, 0, 1, 0], alpha=[0.0] * 6, rtol=1e-10),
     "random_mixed_bc_0": lambda: inputs.random_problem(0, n0=(2, 3, 2), levels=4, rtol=1e-10),
     "random_mixed_bc_1": lambda: inputs.random_problem(1, n0=(3, 2, 2), levels=3, rtol=1e-10),
     "problem1_load": lambda: inputs.paper_problem1(levels=4, rtol=1e-9),
@@ -144,7 +150,8 @@ def test_fp64_solve_matches_oracle(E, oracle_mod, name, variant):
     s.close()
 
 
-@pytest.mark.parametrize("name", ["exp_cube", "cube_elements_ragged", "problem1_load", "random_mixed_bc_0"])
+@pytest.mark.parametrize("name", ["exp_cube", "cube_elements_ragged", "random_cube_dirichlet", "random_cube_neumann",
+                                  "problem1_load", "random_mixed_bc_0"])
 def test_mixed_solve_reaches_tolerance_and_fp64_accuracy(E, oracle_mod, name):
     p = PROBLEMS[name]()
     lv, ost = oracle_mod.ecmg(p, p["rtol"])
@@ -505,8 +512,8 @@ def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_
     fresh.close()
 
 
-@pytest.mark.parametrize("name", ["exp_cube", "cos_cube_cube", "cube_elements_ragged", "problem1_load",
-                                  "random_mixed_bc_0"])
+@pytest.mark.parametrize("name", ["exp_cube", "cos_cube_cube", "cube_elements_ragged", "random_cube_dirichlet",
+                                  "random_cube_neumann", "problem1_load", "random_mixed_bc_0"])
 def test_mixed_reported_residual_is_the_true_residual(E, oracle_mod, name):
     """The residual the MIXED solve reports on every level (from its last FP64 residual
     evaluation: the exact constant-coefficient kernel on one-beta all-Dirichlet cubes, the
