@@ -52,10 +52,10 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=3)
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched 64-problem workload (one solve per step; --eager for host loop control)")
-    ap.add_argument("--profile-kernel", type=int, default=None,
-                    help="profiling run: one MIXED solve, then kernel W of ecmg_time_kernel on the finest level, "
-                         "3 launches inside the NVTX range kernel_profile (for ncu -k / --nvtx-include); prints "
-                         "one JSON line and exits")
+    ap.add_argument("--profile-kernel", default=None,
+                    help="profiling run: one MIXED solve, then kernel W (or a comma list) of ecmg_time_kernel on "
+                         "the finest level, 3 launches each inside the NVTX range kernel_profile (for ncu -k / "
+                         "--nvtx-include); prints one JSON line per kernel and exits")
     ap.add_argument("--profile-tiles", default=None,
                     help="with --profile-kernel 0: the K1 tile shape ry,kz of the finest level (as autotuned in the bench)")
     ap.add_argument("--eager", action="store_true",
@@ -206,12 +206,13 @@ def profile_kernel(args):
     if args.profile_tiles:
         ry, kz = (int(v) for v in args.profile_tiles.split(","))
         s.set_tiles(ry, kz, -1)
-    torch.cuda.nvtx.range_push("kernel_profile")
-    ms, nb = s.time_kernel(args.profile_kernel, -1, reps=2)
-    torch.cuda.nvtx.range_pop()
     ry, kz = s.get_tiles(-1)
-    print(json.dumps({"kernel": args.profile_kernel, "n": args.n0 << (args.levels - 1), "ms": ms,
-                      "algorithmic_bytes": nb, "GBps": nb / ms / 1e6, "tiles": [ry, kz], "solve_status": status}))
+    for w in [int(v) for v in str(args.profile_kernel).split(",")]:
+        torch.cuda.nvtx.range_push("kernel_profile")
+        ms, nb = s.time_kernel(w, -1, reps=2)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"kernel": w, "n": args.n0 << (args.levels - 1), "ms": ms, "algorithmic_bytes": nb,
+                          "GBps": nb / ms / 1e6, "tiles": [ry, kz], "solve_status": status}))
     s.close()
 
 

@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_fold(const BItem* __restrict__ it
         const double xn = it.U[t] + fx::widen(fmaf(a, p[t], it.e32[t]));
         it.U[t] = xn;
         it.e32[t] = 0.f;
-        m = max(m, (unsigned long long)__double_as_longlong(fabs(xn)));
+        m = max(m, fx::abs_bits(xn));
     }
     block_max_to(m, &it.st->xbits);  // the scale of the exact residual that follows
 }
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_absmax(const BItem* __restrict__ 
     const int64_t end = min(base + BFLAT_ELEMS, it.g.total);
     unsigned long long m = 0ull;
     for (int64_t t = base + threadIdx.x; t < end; t += FLAT_TPB)
-        m = max(m, (unsigned long long)__double_as_longlong(fabs(it.U[t])));
+        m = max(m, fx::abs_bits(it.U[t]));
     block_max_to(m, &it.st->xbits);
 }
 

@@ -50,5 +50,13 @@ __device__ __forceinline__ double widen(float f)
                                             ((unsigned long long)(b & 0x7fffffu) << 29)));
 }
 
+// Bit pattern of |x| as an unsigned integer (sign bit cleared with an integer AND: fabs on a
+// double would take an FP64-pipe instruction). Patterns of nonnegative doubles order like the
+// values, Inf and NaN above every finite value.
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
 }  // namespace fx
 }  // namespace ecmg

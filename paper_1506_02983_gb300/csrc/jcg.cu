@@ -402,11 +402,11 @@ __global__ void __launch_bounds__(UPD_TPB) k_absmax(int64_t n, const double* __r
     const double2* x2 = reinterpret_cast<const double2*>(x);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n / 2; t += stride) {
         const double2 v = x2[t];
-        m = max(m, (unsigned long long)__double_as_longlong(fabs(v.x)));
-        m = max(m, (unsigned long long)__double_as_longlong(fabs(v.y)));
+        m = max(m, fx::abs_bits(v.x));
+        m = max(m, fx::abs_bits(v.y));
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
-        m = max(m, (unsigned long long)__double_as_longlong(fabs(x[n - 1])));
+        m = max(m, fx::abs_bits(x[n - 1]));
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) sh[warp] = m;
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(UPD_TPB) k_scale_load(int64_t n, const double*
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
         const double v = b[t] * inv_c;
         bc[t] = v;
-        m = max(m, (unsigned long long)__double_as_longlong(fabs(v)));
+        m = max(m, fx::abs_bits(v));
     }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
@@ -776,15 +776,15 @@ __global__ void __launch_bounds__(UPD_TPB) k_fold32(int64_t n, double* __restric
         x2[2 * t] = xa;
         x2[2 * t + 1] = xb;
         e4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        m = max(m, max(max((unsigned long long)__double_as_longlong(fabs(xa.x)),
-                           (unsigned long long)__double_as_longlong(fabs(xa.y))),
-                       max((unsigned long long)__double_as_longlong(fabs(xb.x)),
-                           (unsigned long long)__double_as_longlong(fabs(xb.y)))));
+        m = max(m, max(max(fx::abs_bits(xa.x),
+                           fx::abs_bits(xa.y)),
+                       max(fx::abs_bits(xb.x),
+                           fx::abs_bits(xb.y))));
     }
     for (int64_t t = (n / 4) * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
         x[t] += widen(fmaf(a, p[t], e[t]));
         e[t] = 0.f;
-        m = max(m, (unsigned long long)__double_as_longlong(fabs(x[t])));
+        m = max(m, fx::abs_bits(x[t]));
     }
     if (!want_max) return;
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
