@@ -877,14 +877,6 @@ void launch_pq64(const Grid& g, const Op& op, const double* beta, const int* uni
     ECMG_VARIANT(k_pq, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, r, dinv, pold,
                                                                            pnew, q, x, st, pr.buf, pidx, ch, kz);
 }
-void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r, const float* dinv,
-                 const float* pold, float* pnew, float* q, float* e, SolveState* st, Partials pr,
-                 int pidx, CondHandles ch, cudaStream_t s)
-{
-    const int kz = stencil_kz(g);
-    ECMG_VARIANT(k_pq, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, nullptr, r, dinv, pold,
-                                                                          pnew, q, e, st, pr.buf, pidx, ch, kz);
-}
 // max |x| for the fixed-point evaluation (a no-op on levels with more than one beta)
 void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
                    Partials pr, cudaStream_t s, bool always)

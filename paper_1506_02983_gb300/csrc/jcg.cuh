@@ -25,9 +25,6 @@ struct CondHandles {
 void launch_pq64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* r,
                  const double* dinv, const double* pold, double* pnew, double* q, double* x,
                  SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
-void launch_pq32(const Grid& g, const Op& op, const float* beta, const float* r,
-                 const float* dinv, const float* pold, float* pnew, float* q, float* e,
-                 SolveState* st, Partials pr, int pnew_index, CondHandles ch, cudaStream_t s);
 // r = b - A x on free nodes, 0 on Dirichlet nodes; r stored as double or float; ||r||^2 and
 // r.dinv.r reduced; last block acts by ResMode. A x exactly in fixed point on a level with one
 // beta, in fixed point up to the beta products with variable beta on cubic elements without

@@ -51,4 +51,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 }
 
 }  // namespace tma
+
+struct Grid;
+// Tiled tensor map of one level vector (FP64 or FP32) in the padded layout (tma_map.cu): the
+// whole padded box, boxes of sx x sy x 1 elements, out-of-bounds reads filled with zeros.
+// False if the driver entry point is unavailable or the encoding is rejected.
+bool encode_level_map(CUtensorMap* map, bool fp64, const void* base, const Grid& g, int sx, int sy);
+
 }  // namespace ecmg
