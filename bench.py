@@ -56,6 +56,10 @@ def parse():
                     help="profiling run: one MIXED solve, then kernel W (or a comma list) of ecmg_time_kernel on "
                          "the finest level, 3 launches each inside the NVTX range kernel_profile (for ncu -k / "
                          "--nvtx-include); prints one JSON line per kernel and exits")
+    ap.add_argument("--profile-workload", default="cos_cube", choices=["cos_cube", "jump"],
+                    help="with --profile-kernel: cos_cube (one beta, all Dirichlet: the constant-coefficient "
+                         "kernels) or the coefficient-jump box (16x8x8 coarsest, beta 1 | 100, Robin face: the "
+                         "general kernels)")
     ap.add_argument("--profile-tiles", default=None,
                     help="with --profile-kernel 0: the K1 tile shape ry,kz of the finest level (as autotuned in the bench)")
     ap.add_argument("--eager", action="store_true",
@@ -200,7 +204,12 @@ def profile_kernel(args):
     from paper_1506_02983_gb300 import build, inputs
     build.build()
     from paper_1506_02983_gb300 import ecmg
-    p = inputs.cos_cube(levels=args.levels, n0=(args.n0,) * 3, rtol=args.rtol)
+    if args.profile_workload == "jump":
+        p = inputs.jump_singular(levels=args.levels, rtol=1e-8, device="cuda")
+        nfin = 16 << (args.levels - 1)
+    else:
+        p = inputs.cos_cube(levels=args.levels, n0=(args.n0,) * 3, rtol=args.rtol)
+        nfin = args.n0 << (args.levels - 1)
     s = ecmg.solver_from_problem(p, precision=ecmg.ECMG_MIXED, max_iters=args.max_iters)
     st, status = s.solve()
     if args.profile_tiles:
@@ -211,7 +220,7 @@ def profile_kernel(args):
         torch.cuda.nvtx.range_push("kernel_profile")
         ms, nb = s.time_kernel(w, -1, reps=2)
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"kernel": w, "n": args.n0 << (args.levels - 1), "ms": ms, "algorithmic_bytes": nb,
+        print(json.dumps({"kernel": w, "workload": args.profile_workload, "n": nfin, "ms": ms, "algorithmic_bytes": nb,
                           "GBps": nb / ms / 1e6, "tiles": [ry, kz], "solve_status": status}))
     s.close()
 

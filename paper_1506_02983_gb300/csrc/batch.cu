@@ -347,11 +347,11 @@ __global__ void __launch_bounds__(mt::NT) bk_res(const BItem* __restrict__ items
             rr = fma(rv, rv, rr);
             rz.add_prod(ro, it.dinv32[o] * ro);
         };
-        if constexpr (CUBE && !ROBIN) {
+        if constexpr (CUBE) {
             // exact integer element sums (march_fx.cuh) on the scale of max |x| (bk_absmax or
             // bk_fold just before)
             const fx::FixedFrame fr = fx::fixed_frame(st->xbits);
-            if (fr.finite) march_range_fxv(it.g, it.beta, x, rg, bx, by, bz, it.kz, fr, body);
+            if (fr.finite) march_range_fxv<ROBIN>(it.g, it.beta, x, rg, bx, by, bz, it.kz, fr, it.op, body);
             else if (sl.lb == 0 && threadIdx.x == 0 && threadIdx.y == 0) rr = nan("");  // the iterate is not finite
         } else {
             auto src = [&](int64_t o) -> double { return x[o]; };

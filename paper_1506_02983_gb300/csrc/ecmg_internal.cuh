@@ -51,6 +51,11 @@ struct Op {
     double alpha[6];
     int bc[6];                   // 0 Dirichlet, 1 Robin
     int robin;                   // 1 when some alpha != 0 (integer test: FP64 compares run at 1/64 rate)
+    int robin_mask;              // bit f set when face f has alpha != 0
+    // alpha_F h_a h_b / 36 per face (a, b its in-face axes): the Robin face-mass weight of the
+    // level, times small integer multiplicities at each node (host-rounded to FP32 as well)
+    double rw64[6];
+    float rw32[6];
 };
 
 __host__ inline Op make_op(const double h[3], const int bc[6], const double alpha[6])
@@ -82,7 +87,14 @@ __host__ inline Op make_op(const double h[3], const int bc[6], const double alph
         o.alpha[f] = (bc[f] == 1) ? alpha[f] : 0.0;
     }
     o.robin = 0;
-    for (int f = 0; f < 6; ++f) o.robin |= o.alpha[f] != 0.0;
+    o.robin_mask = 0;
+    for (int f = 0; f < 6; ++f) {
+        o.robin |= o.alpha[f] != 0.0;
+        if (o.alpha[f] != 0.0) o.robin_mask |= 1 << f;
+        const int an = f / 2, aa = an == 0 ? 1 : 0, ab = an == 2 ? 1 : 2;
+        o.rw64[f] = o.alpha[f] * h[aa] * h[ab] / 36.0;
+        o.rw32[f] = (float)o.rw64[f];
+    }
     return o;
 }
 

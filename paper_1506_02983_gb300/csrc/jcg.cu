@@ -548,16 +548,16 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
         rr = fma(rv, rv, rr);
         rz.add_prod(ro, dinv[o] * ro);
     };
-    if (*uniform || (CUBE && !ROBIN)) {
+    if (*uniform || CUBE) {
         const FixedFrame fr = fixed_frame(fs->bits);
         if (!fr.finite) {
             if (threadIdx.x == 0 && threadIdx.y == 0) rr = nan("");  // breakdown: the iterate is not finite
         } else if (*uniform) {
             march_fixed<ROBIN>(fsm, g, op, beta[g.off(0, 0, 0)], fr, kz, src, body);
-        } else if constexpr (CUBE && !ROBIN) {
+        } else if constexpr (CUBE) {
             // variable beta on cubic elements: integer element sums (march_fx.cuh)
             auto body5 = [&](int i, int j, int k, int64_t o, double Av) { body(i, j, k, o, Av, 0.0); };
-            march_range_fxv(g, beta, x, all_nodes(g), blockIdx.x, blockIdx.y, blockIdx.z, kz, fr, body5);
+            march_range_fxv<ROBIN>(g, beta, x, all_nodes(g), blockIdx.x, blockIdx.y, blockIdx.z, kz, fr, op, body5);
         }
     } else {
         march<ROBIN, CUBE, double, double>(g, op, beta, kz, src, body);
@@ -889,7 +889,7 @@ void launch_res64(const Grid& g, const Op& op, const double* beta, const int* un
                   CondHandles ch, cudaStream_t s)
 {
     const int kz = stencil_kz(g);
-    launch_absmax(g, x, uniform, st, (int)mode, pr, s, op.cube && !has_robin(op));
+    launch_absmax(g, x, uniform, st, (int)mode, pr, s, op.cube != 0);
     ECMG_VARIANT(k_res, double)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
                                                                             st, pr.buf, (int)mode, ch, kz, pr.fs,
                                                                             nullptr);
@@ -912,7 +912,7 @@ void launch_res32(const Grid& g, const Op& op, const double* beta, const int* un
                   CondHandles ch, cudaStream_t s, const double* bc)
 {
     const int kz = stencil_kz(g);
-    launch_absmax(g, x, uniform, st, (int)mode, pr, s, op.cube && !has_robin(op));
+    launch_absmax(g, x, uniform, st, (int)mode, pr, s, op.cube != 0);
     if (!constant_coefficient_shape(g, op)) bc = nullptr;
     ECMG_VARIANT(k_res, float)<<<stencil_grid(g, kz), dim3(BX, BY), 0, s>>>(g, op, beta, uniform, x, b, dinv, r,
                                                                            st, pr.buf, (int)mode, ch, kz, pr.fs,

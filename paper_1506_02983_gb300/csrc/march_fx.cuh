@@ -10,7 +10,9 @@
 // each I_e is an exact integer sum and only the eight products beta_e I_e and their sum are
 // FP64 operations -- about a third of the FP64 work of the difference form (FP64 runs at
 // 1/64 of the FP32 rate on GB300). Elements outside the box carry beta = 0 in the padded
-// layout, so nodes on a Neumann face need no special case; Robin terms are not included.
+// layout, so nodes on a Neumann face need no special case. A Robin face F adds
+// alpha_F (h^2 / 36) (S (x) S) x on its nodes, S = [1 4 1] ([2 1] at a face edge): again an
+// exact integer sum of the face neighbours (ghost nodes hold 0) times one FP64 weight.
 #pragma once
 
 #include "fixed.cuh"
@@ -20,11 +22,13 @@ namespace ecmg {
 
 // The z-march of march_range (march.cuh) with the operand staged as fixed-point integers:
 // body(i, j, k, offset, A x) for every node of the range. x: the level vector (FP64, padded).
-template <typename BODY>
+template <bool ROBIN, typename BODY>
 __device__ __forceinline__ void march_range_fxv(const Grid& g, const double* __restrict__ beta,
                                                 const double* __restrict__ x, const NodeRange& rg, int bx, int by,
-                                                int bz, int kz, const fx::FixedFrame& fr, BODY body)
+                                                int bz, int kz, const fx::FixedFrame& fr, const Op& op, BODY body)
 {
+    const int op_robin_mask = op.robin_mask;
+    const double* rw = op.rw64;
     constexpr int NT = mt::NT;
     constexpr int PC = (BX + 2) * (BY + 2), SC = (BX + 1) * (BY + 1);  // plane and slab cells
     constexpr int NP = (PC + NT - 1) / NT, NS = (SC + NT - 1) / NT;    // cells per thread
@@ -110,7 +114,43 @@ __device__ __forceinline__ void march_range_fxv(const Grid& g, const double* __r
                         const long long I = (X(ox, oy, 0) + X(ox, 0, oz)) + (X(0, oy, oz) + X(ox, oy, oz)) - x4;
                         S = fma(sb[ez ? k % 2 : (k + 1) % 2][ty + ey][tx + ex], (double)I, S);
                     }
-            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), cA * S);
+            double Av = cA * S;
+            if (ROBIN && (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz)) {
+                // S_a S_b X over the face through the node, in-face axes (a, b); the centre
+                // weight is 2 at the face's edge (end of that axis) and 4 inside
+                const long long sx0 = (i == 0 || i == g.nx) ? 2 : 4, sy0 = (j == 0 || j == g.ny) ? 2 : 4,
+                                sz0 = (k == 0 || k == g.nz) ? 2 : 4;
+                auto face = [&](int an) -> long long {
+                    long long I = 0;
+#pragma unroll
+                    for (int u = -1; u <= 1; ++u)
+#pragma unroll
+                        for (int v = -1; v <= 1; ++v) {
+                            long long w;
+                            long long xv;
+                            if (an == 0) {
+                                w = (u ? 1 : sy0) * (v ? 1 : sz0);
+                                xv = X(0, u, v);
+                            } else if (an == 1) {
+                                w = (u ? 1 : sx0) * (v ? 1 : sz0);
+                                xv = X(u, 0, v);
+                            } else {
+                                w = (u ? 1 : sx0) * (v ? 1 : sy0);
+                                xv = X(u, v, 0);
+                            }
+                            I += w * xv;
+                        }
+                    return I;
+                };
+                const int pos[3] = {i, j, k}, nn[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    const int an = f / 2;
+                    if (((op_robin_mask >> f) & 1) && pos[an] == ((f & 1) ? nn[an] : 0))
+                        Av = fma(rw[f] * fr.inv, (double)face(an), Av);
+                }
+            }
+            body(i, j, k, g.plane_base(k) + g.in_plane(i, j), Av);
         }
         __syncthreads();
     }

@@ -96,12 +96,12 @@ __global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, doubl
     const int idx[3] = {i, j, k};
     const int nn[3] = {g.nx, g.ny, g.nz};
     for (int fc = 0; fc < 6; ++fc) {
-        if (op.alpha[fc] == 0.0) continue;
+        if (!((op.robin_mask >> fc) & 1)) continue;
         int an = fc / 2;
         if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
         int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
-        d += op.alpha[fc] * cnt1(idx[aa], nn[aa], 0) * g.h[aa] / 3.0 *
-             cnt1(idx[ab], nn[ab], 0) * g.h[ab] / 3.0;
+        // alpha h_a h_b / 9 per shared face quad pair: the diagonal of the face mass matrix
+        d += op.rw64[fc] * (double)(4 * cnt1(idx[aa], nn[aa], 0) * cnt1(idx[ab], nn[ab], 0));
     }
     dinv64[g.off(i, j, k)] = on_dirichlet(g, op, i, j, k) ? 0.0 : 1.0 / d;
 }

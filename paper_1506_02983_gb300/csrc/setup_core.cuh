@@ -99,15 +99,14 @@ __device__ __forceinline__ float jacobi32_at(const Grid& g, const Op& op, const 
     if (op.robin && (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz)) {
         const int idx[3] = {i, j, k};
         const int nn[3] = {g.nx, g.ny, g.nz};
-        double dr = 0.0;
         for (int fc = 0; fc < 6; ++fc) {
-            if (op.alpha[fc] == 0.0) continue;
+            if (!((op.robin_mask >> fc) & 1)) continue;
             int an = fc / 2;
             if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
             int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
-            dr += op.alpha[fc] * cnt1(idx[aa], nn[aa], 0) * g.h[aa] / 3.0 * cnt1(idx[ab], nn[ab], 0) * g.h[ab] / 3.0;
+            // alpha h_a h_b / 9 per shared face quad pair, in FP32 (host-rounded weight)
+            d += op.rw32[fc] * (float)(4 * cnt1(idx[aa], nn[aa], 0) * cnt1(idx[ab], nn[ab], 0));
         }
-        d += (float)dr;
     }
     return on_dirichlet(g, op, i, j, k) ? 0.f : __frcp_rn(d);
 }

@@ -81,8 +81,19 @@ __device__ __forceinline__ int elems_between(int a, int n, int d)
     return d < 0 ? (a >= 1) : d > 0 ? (a < n) : (a >= 1) + (a < n);
 }
 
+// Robin face-mass weight alpha_F h_a h_b / 36 of face f in the arithmetic type (rounded on the
+// host: no FP64 instruction in an FP32 kernel, and no FP64 divide anywhere).
+template <typename VT>
+__device__ __forceinline__ VT robin_weight(const Op& op, int f);
+template <>
+__device__ __forceinline__ double robin_weight<double>(const Op& op, int f) { return op.rw64[f]; }
+template <>
+__device__ __forceinline__ float robin_weight<float>(const Op& op, int f) { return op.rw32[f]; }
+
 // alpha_F times the face mass matrix, summed over every Robin face through the node (the
-// Gamma_R part of the bilinear form of Sec. 2). Fully unrolled: offsets are compile-time.
+// Gamma_R part of the bilinear form of Sec. 2): the face mass entry between the node and its
+// in-face neighbour (da, db) is alpha_F h_a h_b / 36 times the number of face quads they share
+// times 2 per axis with da = 0 (resp. db = 0). Fully unrolled: offsets are compile-time.
 template <typename VT, typename VF>
 __device__ __forceinline__ VT q1_robin(VF V, int i, int j, int k, const Grid& g, const Op& op)
 {
@@ -92,22 +103,23 @@ __device__ __forceinline__ VT q1_robin(VF V, int i, int j, int k, const Grid& g,
         const int an = f / 2;
         const int ia = an == 0 ? i : an == 1 ? j : k;
         const int na = an == 0 ? g.nx : an == 1 ? g.ny : g.nz;
-        if (op.alpha[f] == 0.0 || ia != ((f & 1) ? na : 0)) continue;
+        if (!((op.robin_mask >> f) & 1) || ia != ((f & 1) ? na : 0)) continue;
         // in-face axes a < b
         const int aa = an == 0 ? 1 : 0, ab = an == 2 ? 1 : 2;
         const int ja = aa == 0 ? i : j, jb = ab == 1 ? j : k;
         const int nA = aa == 0 ? g.nx : g.ny, nB = ab == 1 ? g.ny : g.nz;
+        const VT rw = robin_weight<VT>(op, f);
 #pragma unroll
         for (int db = -1; db <= 1; ++db)
 #pragma unroll
             for (int da = -1; da <= 1; ++da) {
                 const int c = elems_between(ja, nA, da) * elems_between(jb, nB, db);
                 if (!c) continue;
-                const double w = op.alpha[f] * c * g.h[aa] * (da ? 1.0 : 2.0) / 6.0 * g.h[ab] * (db ? 1.0 : 2.0) / 6.0;
+                const VT w = rw * (VT)(c * (da ? 1 : 2) * (db ? 1 : 2));
                 const int dx = aa == 0 ? da : 0;
                 const int dy = aa == 1 ? da : (ab == 1 ? db : 0);
                 const int dz = ab == 2 ? db : 0;
-                acc += (VT)w * V(dx, dy, dz);
+                acc += w * V(dx, dy, dz);
             }
     }
     return acc;
@@ -124,21 +136,22 @@ __device__ __forceinline__ VT q1_robin_rolled(VF V, int i, int j, int k, const G
         const int an = f / 2;
         const int ia = an == 0 ? i : an == 1 ? j : k;
         const int na = an == 0 ? g.nx : an == 1 ? g.ny : g.nz;
-        if (op.alpha[f] == 0.0 || ia != ((f & 1) ? na : 0)) continue;
+        if (!((op.robin_mask >> f) & 1) || ia != ((f & 1) ? na : 0)) continue;
         const int aa = an == 0 ? 1 : 0, ab = an == 2 ? 1 : 2;
         const int ja = aa == 0 ? i : j, jb = ab == 1 ? j : k;
         const int nA = aa == 0 ? g.nx : g.ny, nB = ab == 1 ? g.ny : g.nz;
+        const VT rw = robin_weight<VT>(op, f);
 #pragma unroll 1
         for (int db = -1; db <= 1; ++db)
 #pragma unroll 1
             for (int da = -1; da <= 1; ++da) {
                 const int c = elems_between(ja, nA, da) * elems_between(jb, nB, db);
                 if (!c) continue;
-                const double w = op.alpha[f] * c * g.h[aa] * (da ? 1.0 : 2.0) / 6.0 * g.h[ab] * (db ? 1.0 : 2.0) / 6.0;
+                const VT w = rw * (VT)(c * (da ? 1 : 2) * (db ? 1 : 2));
                 const int dx = aa == 0 ? da : 0;
                 const int dy = aa == 1 ? da : (ab == 1 ? db : 0);
                 const int dz = ab == 2 ? db : 0;
-                acc += (VT)w * V(dx, dy, dz);
+                acc += w * V(dx, dy, dz);
             }
     }
     return acc;
@@ -186,10 +199,6 @@ __device__ __forceinline__ double fh_at(const Grid& g, const Op& op, const Weigh
     return f;
 }
 
-__device__ __forceinline__ bool op_has_robin(const Op& op)
-{
-    return (op.alpha[0] != 0.0) | (op.alpha[1] != 0.0) | (op.alpha[2] != 0.0) | (op.alpha[3] != 0.0) |
-           (op.alpha[4] != 0.0) | (op.alpha[5] != 0.0);
-}
+__device__ __forceinline__ bool op_has_robin(const Op& op) { return op.robin != 0; }
 
 }  // namespace ecmg

@@ -513,7 +513,7 @@ def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_
 
 
 @pytest.mark.parametrize("name", ["exp_cube", "cos_cube_cube", "cube_elements_ragged", "random_cube_dirichlet",
-                                  "random_cube_neumann", "problem1_load", "random_mixed_bc_0"])
+                                  "random_cube_neumann", "variable_box", "problem1_load", "random_mixed_bc_0"])
 def test_mixed_reported_residual_is_the_true_residual(E, oracle_mod, name):
     """The residual the MIXED solve reports on every level (from its last FP64 residual
     evaluation: the exact constant-coefficient kernel on one-beta all-Dirichlet cubes, the
