@@ -72,6 +72,17 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over the ranks of the job (every rank gets it); value itself at N = 1."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -328,13 +339,7 @@ def main():
             fn()
         e1.record()
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = t.item()
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
 
     torch.cuda.synchronize()
     t_create = time.perf_counter()
