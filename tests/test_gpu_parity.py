@@ -534,3 +534,39 @@ def test_mixed_reported_residual_is_the_true_residual(E, oracle_mod, name):
         rel = np.sqrt(np.dot(r, r)) / st["rhs_norm"][l]
         assert rel == pytest.approx(st["rel_res"][l], rel=1e-4), (l, rel, st["rel_res"][l])
     s.close()
+
+
+def _random_case(seed):
+    """Seeded random problem of random shape: coarsest 1..3 elements per axis, 3 or 4 levels,
+    cubic or stretched elements, one or many betas, random face types and Robin alphas."""
+    rng = np.random.default_rng(seed)
+    n0 = tuple(int(v) for v in rng.integers(1, 4, 3))
+    levels = int(rng.integers(3, 5))
+    if rng.random() < 0.5:
+        h0 = float(rng.uniform(0.2, 0.5))
+        box = tuple(h0 * v for v in n0)  # cubic elements
+    else:
+        box = tuple(float(v) for v in rng.uniform(0.5, 1.5, 3))
+    contrast = 1.0 if rng.random() < 0.4 else 10.0
+    return inputs.random_problem(int(seed), n0=n0, levels=levels, box=box, contrast=contrast, rtol=1e-10)
+
+
+@pytest.mark.parametrize("seed", range(200, 216))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_random_problems_match_oracle(E, oracle_mod, seed, precision):
+    """Randomised parity sweep over shapes, boundary types and coefficient fields: FP64 to the
+    method's bar (1e-10, iterations +-1), MIXED to the mixed bar (residual test met, U within
+    1e-7 of the oracle's)."""
+    p = _random_case(seed)
+    lv, ost = oracle_mod.ecmg(p, p["rtol"])
+    assert ost["status"] == 0
+    s = E.solver_from_problem(p, precision=precision)
+    st, status = s.solve()
+    assert status == 0, (p["n0"], p["levels"], p["face_bc"], st)
+    for l in range(2, p["levels"]):
+        U = _np(s.get(E.ECMG_VEC_U, l))
+        assert _rel(U, lv[l]["U"]) <= (1e-10 if precision == 0 else 1e-7), (l, _rel(U, lv[l]["U"]))
+        assert st["rel_res"][l] <= p["rtol"] * 1.01, (l, st["rel_res"])
+        if precision == 0:
+            assert abs(st["iters"][l] - ost["iters"][l]) <= 1, (l, st["iters"], ost["iters"])
+    s.close()
