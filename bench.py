@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--max-iters", type=int, default=20000)
     ap.add_argument("--inner-rtol", type=float, default=1e-3,
                     help="MIXED: FP32 inner reduction between FP64 residual replacements")
-    ap.add_argument("--kernels", default="0,1,2,5,6,7", help="kernels timed alone for the report")
+    ap.add_argument("--kernels", default="0,1,2,5,6,7,11", help="kernels timed alone for the report")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-problem measurement")
     ap.add_argument("--batched-steps", type=int, default=3)
     ap.add_argument("--batched-only", action="store_true",
@@ -62,6 +62,10 @@ def parse():
                          "general kernels)")
     ap.add_argument("--profile-tiles", default=None,
                     help="with --profile-kernel 0: the K1 tile shape ry,kz of the finest level (as autotuned in the bench)")
+    ap.add_argument("--cg-form", default="two", choices=["two", "single"],
+                    help="MIXED step of the headline solve: two-pass (K1 + K2) or single-pass (one kernel)")
+    ap.add_argument("--no-compare-form", action="store_true",
+                    help="skip timing the other MIXED step form beside the headline one")
     ap.add_argument("--eager", action="store_true",
                     help="host-driven level loops instead of one CUDA graph per solve (same kernels); "
                          "ncu cannot profile kernel nodes of graphs that hold conditional nodes")
@@ -177,6 +181,8 @@ def arm_config(args, world):
             "l2": "inputs and finest vectors (>1 GB each) larger than L2",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes",
+            "mixed_step": ("single-pass (one kernel per JCG step, ECMG_CG_SINGLE_PASS)" if args.cg_form == "single"
+                           else "two-pass (K1 + K2 per JCG step)"),
             "tiles": "FP32 stencil tile shapes autotuned after the first solve (ecmg_autotune)"}
 
 
@@ -221,7 +227,8 @@ def profile_kernel(args):
     else:
         p = inputs.cos_cube(levels=args.levels, n0=(args.n0,) * 3, rtol=args.rtol)
         nfin = args.n0 << (args.levels - 1)
-    s = ecmg.solver_from_problem(p, precision=ecmg.ECMG_MIXED, max_iters=args.max_iters)
+    s = ecmg.solver_from_problem(p, precision=ecmg.ECMG_MIXED, max_iters=args.max_iters,
+                                 cg_form=ecmg.ECMG_CG_SINGLE_PASS if args.cg_form == "single" else ecmg.ECMG_CG_TWO_PASS)
     st, status = s.solve()
     if args.profile_tiles:
         ry, kz = (int(v) for v in args.profile_tiles.split(","))
@@ -319,10 +326,14 @@ def main():
     u_exact = torch.from_numpy(np.ascontiguousarray(p["u_exact"])).to(dev)
     del p["beta"], p["f"], p["gD"]
 
-    def make(precision):
+    single = args.cg_form == "single"
+    form = {True: ecmg.ECMG_CG_SINGLE_PASS, False: ecmg.ECMG_CG_TWO_PASS}
+
+    def make(precision, single_pass=single):
         return ecmg.Solver(p["n0"], L, p["lo"], p["hi"], p["face_bc"], p["alpha"], d["beta"], d["f"],
                            d["gD"], None, f_mode=ecmg.ECMG_F_LOAD, rtol=args.rtol, precision=precision,
-                           max_iters=args.max_iters, use_graph=0 if args.eager else 1, inner_rtol=args.inner_rtol)
+                           max_iters=args.max_iters, use_graph=0 if args.eager else 1, inner_rtol=args.inner_rtol,
+                           cg_form=form[single_pass] if precision == ecmg.ECMG_MIXED else ecmg.ECMG_CG_TWO_PASS)
 
     def barrier():
         torch.cuda.synchronize()
@@ -375,13 +386,14 @@ def main():
     hbm_peak = pk.get("hbm_gbs")
     kern = {}
     names = {0: "k_pq<float> (K1 FP32)", 1: "k_update<float> (K2 FP32)", 2: "k_res<float> (FP64 residual)",
-             5: "k_res<double>", 6: "k_exp_finite", 7: "k_exp_true"}
+             5: "k_res<double>", 6: "k_exp_finite", 7: "k_exp_true", 11: "k_step32 (single-pass FP32 step)"}
+    step_kernel = 11 if single else 0
     for w in [int(x) for x in args.kernels.split(",") if x != ""]:
-        if w in (3, 4):
+        if w in (3, 4) or (single and w in (0, 1)) or (w == 11 and not single):
             continue
         ms, nb = mixed.time_kernel(w, -1, reps=10)
         kern[names.get(w, str(w))] = {"ms": ms, "algorithmic_bytes": nb, "GBps": nb / ms / 1e6}
-    k1_ms, k1_bytes = mixed.time_kernel(0, -1, reps=20)
+    k1_ms, k1_bytes = mixed.time_kernel(step_kernel, -1, reps=20)
     k1_live_ms = k1_live_total_ms / max(k1_live_n, 1)
     tiles = mixed.get_tiles(-1)
     mixed_tiles = tiles
@@ -428,6 +440,27 @@ def main():
     err_compact = compact.norms(u_out, u_exact)[0]
     compact.close()
 
+    # the other MIXED step form on the same problem, for comparison (same warm-up and timing)
+    other = None
+    if not args.no_compare_form:
+        alt = make(ecmg.ECMG_MIXED, single_pass=not single)
+        st_alt, status = alt.solve(u_out)
+        assert status == 0, st_alt
+        alt.autotune(3)
+        for _ in range(args.warmup):
+            alt.solve(u_out)
+        alt.stencil_timer(-1, reset=True)
+        ms_alt = timed(lambda: alt.solve(u_out), args.steps)
+        alt_total, alt_n = alt.stencil_timer(-1, reset=True)
+        st_alt, _ = alt.solve(u_out)
+        other = {"mixed_step": "two-pass" if single else "single-pass", "ms_per_step": ms_alt,
+                 "value": free_dofs(nf) * world / (ms_alt * 1e-3) / 1e9, "unit": "Gdof/s",
+                 "iters": st_alt["iters"], "updates": st_alt["updates"], "rel_res": st_alt["rel_res"],
+                 "max_err": alt.norms(u_out, u_exact)[0], "tiles_finest": list(alt.get_tiles(-1)),
+                 "finest_step_kernel_ms": alt_total / max(alt_n, 1),
+                 "finest_step_kernels": alt_n / max(args.steps, 1)}
+        alt.close()
+
     fp64 = make(ecmg.ECMG_FP64)
     st64, status = fp64.solve(u_out)
     assert status == 0, st64
@@ -459,6 +492,7 @@ def main():
         except ValueError:
             pass
     k1_gbps = k1_bytes / k1_live_ms / 1e6
+    bpni = 32.0 if single else 36.0
     out = {
         "metric": METRIC, "value": value, "unit": "Gdof/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
@@ -469,8 +503,10 @@ def main():
         "err_ratio_mixed_over_fp64": err_mixed / err_fp64,
         "iters_mixed": st_mixed["iters"], "updates_mixed": st_mixed["updates"], "iters_fp64": st64["iters"],
         "rel_res_mixed": st_mixed["rel_res"], "gdofs_fp64": dofs / (ms_fp64 * 1e-3) / 1e9,
-        "roofline": {"kernel": "K1 (k_pq32_cc on this one-beta all-Dirichlet level: FP32 search direction + "
-                               "27-point operator), finest level",
+        "roofline": {"kernel": ("single-pass step (k_step32_cc on this one-beta all-Dirichlet level: residual "
+                                "update, search direction, 27-point operator and the dots in one pass)" if single else
+                                "K1 (k_pq32_cc on this one-beta all-Dirichlet level: FP32 search direction + "
+                                "27-point operator)") + ", finest level",
                      "bound": "hbm", "achieved": k1_gbps, "peak": hbm_peak, "unit": "GB/s",
                      "frac": (k1_gbps / hbm_peak) if hbm_peak else None, "traffic": traffic,
                      "algorithmic_bytes_per_launch": k1_bytes,
@@ -482,11 +518,13 @@ def main():
         "kernels_alone": kern,
         # the two ways of counting dofs: finest free dofs per solve (value), and free dofs times
         # JCG iterations summed over the levels; the byte model charges each node-iteration the
-        # 36 bytes K1 and K2 move on a constant-coefficient level (24 + 12)
+        # bytes the step moves on a constant-coefficient level: 36 for K1 and K2 (24 + 12), 32
+        # for the single-pass kernel
         "node_iterations_per_solve": node_its,
         "gdofs_node_iterations": node_its * world / (ms_mixed * 1e-3) / 1e9,
-        "byte_model": {"bytes_per_node_iteration": 36, "bytes_per_solve": 36.0 * node_its,
-                       "fraction_of_peak": (36.0 * node_its / (ms_mixed * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None},
+        "byte_model": {"bytes_per_node_iteration": bpni, "bytes_per_solve": bpni * node_its,
+                       "fraction_of_peak": (bpni * node_its / (ms_mixed * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None},
+        "other_mixed_step_form": other,
         "roofline_frac_of_spec_8tbs": k1_gbps / 8000.0,
         "create_ms": create_ms,
         "clocks": clk,

@@ -71,6 +71,14 @@ enum { ECMG_PREC_JACOBI = 0, ECMG_PREC_NONE = 1 };
  * m_j = ceil(m_L beta^(L-j)) of Alg. 3, eq. (ee), with j = 1 .. L the levels above the two
  * direct ones. */
 enum { ECMG_SCHED_TOLERANCE = 0, ECMG_SCHED_FIXED = 1 };
+/* Form of one FP32 step of the MIXED iteration (the recurrence of Alg. 4 line 8 is the same):
+ * TWO_PASS runs the search-direction/stencil kernel (p, q = A p, p.q) and then the residual
+ * kernel (r -= alpha q, r.z, r.r); SINGLE_PASS does both in one kernel per step: the residual
+ * update of the previous step is applied while its tiles are staged, and the next r.z and r.r
+ * are obtained from the dots of the same pass by expanding (r - alpha q).D^-1(r - alpha q) and
+ * (r - alpha q).(r - alpha q). Equal to TWO_PASS in exact arithmetic; the FP64 residual
+ * replacements bound the difference in floating point. Needs two more FP32 vectors per level. */
+enum { ECMG_CG_TWO_PASS = 0, ECMG_CG_SINGLE_PASS = 1 };
 /* ecmg_get_level: which vector */
 enum { ECMG_VEC_U = 0, ECMG_VEC_W = 1, ECMG_VEC_UTILDE = 2, ECMG_VEC_B = 3, ECMG_VEC_BETA = 4 };
 
@@ -125,6 +133,9 @@ typedef struct {
                                there)                                        [TOLERANCE]   */
     int32_t sched_mL;       /* FIXED: m_L, the steps on the finest level, >= 1  [4]         */
     double sched_beta;      /* FIXED: beta of eq. (ee), 1..64                   [4.0]       */
+    int32_t cg_form;        /* MIXED: ECMG_CG_TWO_PASS or ECMG_CG_SINGLE_PASS on the
+                               single-problem path (ecmg_create_batched rejects
+                               SINGLE_PASS)                                  [TWO_PASS]    */
 } ecmg_options;
 
 /* Per-solve statistics, one entry per level (coarsest first). */
@@ -228,7 +239,8 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
  * bracketed by CUDA events on the handle's stream, after one untimed launch. which:
  * 0 K1 FP32 (search direction + operator), 1 K2 FP32 (residual update), 2 FP64 residual with
  * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true, 8 ||f_h||,
- * 9 MIXED fold of the FP32 correction into the FP64 iterate (applied to U~), 10 max |U|.
+ * 9 MIXED fold of the FP32 correction into the FP64 iterate (applied to U~), 10 max |U|,
+ * 11 the single-pass FP32 step (handles created with ECMG_CG_SINGLE_PASS).
  * ms_out: mean duration of one launch (host). bytes_out: the algorithmic bytes one launch
  * must move (each owned input read once, each output written once; host); for kernel 0 the
  * nodes counted are those off the Dirichlet faces, the only ones it visits, and on a level

@@ -27,7 +27,7 @@
  * orders 3 and 4 of W-U and U~-u, and the 1D formulas (sifen1)/(sifen2).
  * Parity is pinned for every function in this file.
  *
- * Readings of places where the paper is silent (listed again in the design doc):
+ * Readings of places where the paper is silent:
  *   - "P_1" in Sec. 2 is the trilinear Q1 space on hexahedra (27-point stencil).
  *   - beta is one value per element; a coarse element takes the mean of its 8 children.
  *   - the load of the nodal mode is M f_I + sum_F M_F gR_I (consistent mass matrices applied
@@ -442,6 +442,91 @@ int or_pcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
     *iters = k;
 
     /* true residual on exit */
+    or_csr_matvec(N, rowptr, col, val, x, q);
+    double tr = 0.0;
+    for (int64_t i = 0; i < N; ++i) if (mask[i]) { double t = b[i] - q[i]; tr += t * t; }
+    *rel_res_true = (fh > 0.0) ? sqrt(tr) / fh : sqrt(tr);
+
+    free(r); free(z); free(p); free(q); free(dinv);
+    return status;
+}
+
+/* The same Jacobi-preconditioned CG (Alg. 4, line 8) arranged in one pass over the vectors per
+ * step, as the library's ECMG_CG_SINGLE_PASS form runs it. Step k first completes the previous
+ * step, x_k = x_{k-1} + alpha_{k-1} p_{k-1} and r_k = r_{k-1} - alpha_{k-1} q_{k-1}, then forms
+ * z_k = D^-1 r_k, p_k = z_k + beta_k p_{k-1} and q_k = A p_k, and takes every dot it needs from
+ * these vectors: alpha_k = (r_k.z_k) / (p_k.q_k), and the quantities of r_{k+1} = r_k - alpha_k q_k
+ * by expanding the products,
+ *     r_{k+1}.z_{k+1} = r_k.z_k - 2 alpha_k z_k.q_k + alpha_k^2 q_k.D^-1 q_k,
+ *     ||r_{k+1}||^2   = r_k.r_k - 2 alpha_k r_k.q_k + alpha_k^2 q_k.q_k,
+ * so beta_{k+1} = r_{k+1}.z_{k+1} / r_k.z_k and the stopping test on ||r_{k+1}|| need no second
+ * pass. In exact arithmetic every iterate equals that of or_pcg. On exit the pending step is
+ * applied to x. Same outputs as or_pcg (tolerance schedule). */
+int or_pcg_single_pass(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
+                       const uint8_t* mask, const double* b, const double* gext, double* x, double rtol,
+                       int32_t max_iters, int32_t precond, int32_t* iters, double* rel_res_true,
+                       double* rhs_norm)
+{
+    double* r = (double*)malloc((size_t)N * sizeof(double));
+    double* z = (double*)malloc((size_t)N * sizeof(double));
+    double* p = (double*)calloc((size_t)N, sizeof(double));
+    double* q = (double*)calloc((size_t)N, sizeof(double));
+    double* dinv = (double*)malloc((size_t)N * sizeof(double));
+    int status = 0;
+
+    for (int64_t i = 0; i < N; ++i) {
+        double d = 0.0;
+        for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) if (col[t] == i) d = val[t];
+        dinv[i] = mask[i] ? (precond ? 1.0 / d : 1.0) : 0.0;
+    }
+
+    or_csr_matvec(N, rowptr, col, val, gext, q);
+    double fh2 = 0.0;
+    for (int64_t i = 0; i < N; ++i) if (mask[i]) { double t = b[i] - q[i]; fh2 += t * t; }
+    double fh = sqrt(fh2);
+    *rhs_norm = fh;
+
+    or_csr_matvec(N, rowptr, col, val, x, q);
+    for (int64_t i = 0; i < N; ++i) { r[i] = mask[i] ? b[i] - q[i] : 0.0; q[i] = 0.0; }
+
+    int32_t k = 0;
+    double alpha_prev = 0.0, beta = 0.0;  /* the pending step and the next direction's coefficient */
+    double rr = dot_masked(N, mask, r, r);
+    if (sqrt(rr) > rtol * fh) {
+        for (;;) {
+            if (k >= max_iters) { status = 3; break; }
+            for (int64_t i = 0; i < N; ++i) {
+                x[i] += alpha_prev * p[i];
+                r[i] -= alpha_prev * q[i];
+                z[i] = dinv[i] * r[i];
+                p[i] = z[i] + beta * p[i];
+            }
+            or_csr_matvec(N, rowptr, col, val, p, q);
+            for (int64_t i = 0; i < N; ++i) if (!mask[i]) q[i] = 0.0;
+            double pq = 0.0, rz = 0.0, zq = 0.0, qdq = 0.0, rr_k = 0.0, rq = 0.0, qq = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                if (!mask[i]) continue;
+                pq += p[i] * q[i];
+                rz += r[i] * z[i];
+                zq += z[i] * q[i];
+                qdq += q[i] * dinv[i] * q[i];
+                rr_k += r[i] * r[i];
+                rq += r[i] * q[i];
+                qq += q[i] * q[i];
+            }
+            if (!(pq > 0.0) || !isfinite(pq)) { status = 4; alpha_prev = 0.0; break; }
+            const double alpha = rz / pq;
+            ++k;
+            const double rz_next = rz - 2.0 * alpha * zq + alpha * alpha * qdq;
+            const double rr_next = rr_k - 2.0 * alpha * rq + alpha * alpha * qq;
+            alpha_prev = alpha;
+            if (sqrt(fmax(rr_next, 0.0)) <= rtol * fh) break;
+            beta = rz_next / rz;
+        }
+        for (int64_t i = 0; i < N; ++i) x[i] += alpha_prev * p[i];
+    }
+    *iters = k;
+
     or_csr_matvec(N, rowptr, col, val, x, q);
     double tr = 0.0;
     for (int64_t i = 0; i < N; ++i) if (mask[i]) { double t = b[i] - q[i]; tr += t * t; }

@@ -80,6 +80,12 @@ int or_pcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
            const uint8_t* mask, const double* b, const double* gext, double* x,
            double rtol, int32_t max_iters, int32_t precond, int32_t fixed, int32_t* iters, double* rel_res_true,
            double* rhs_norm);
+/* JCG (or CG, precond = 0) in the single-pass arrangement: the same iterates as or_pcg in exact
+ * arithmetic, the next r.z and ||r|| by expansion of r - alpha q. Same outputs as or_jcg. */
+int or_pcg_single_pass(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
+                       const uint8_t* mask, const double* b, const double* gext, double* x, double rtol,
+                       int32_t max_iters, int32_t precond, int32_t* iters, double* rel_res_true,
+                       double* rhs_norm);
 int or_dsolve_banded(const int32_t n[3], int64_t N, const int64_t* rowptr,
                      const int64_t* col, const double* val, const uint8_t* mask,
                      const double* b, double* x);

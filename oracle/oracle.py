@@ -72,6 +72,10 @@ def lib():
         _lib.or_restrict_load.argtypes = [P, P, P]
         _lib.or_jcg.restype = C.c_int
         _lib.or_jcg.argtypes = [I64, P, P, P, P, P, P, P, D, I32, P, P, P]
+        _lib.or_pcg.restype = C.c_int
+        _lib.or_pcg.argtypes = [I64, P, P, P, P, P, P, P, D, I32, I32, I32, P, P, P]
+        _lib.or_pcg_single_pass.restype = C.c_int
+        _lib.or_pcg_single_pass.argtypes = [I64, P, P, P, P, P, P, P, D, I32, I32, P, P, P]
         _lib.or_dsolve_banded.restype = C.c_int
         _lib.or_dsolve_banded.argtypes = [P, I64, P, P, P, P, P, P]
         _lib.or_serendipity.argtypes = [D, D, D, P]
@@ -287,6 +291,28 @@ def jcg(A: CSR, mask, b, gext, x0, rtol, max_iters=100000):
     g = _f64(gext)
     st = lib().or_jcg(A.N, _p(A.rowptr), _p(A.col), _p(A.val), _p(m), _p(b), _p(g), _p(x),
                       rtol, max_iters, C.byref(it), C.byref(rr), C.byref(fh))
+    return x, dict(status=st, iters=it.value, rel_res=rr.value, rhs_norm=fh.value)
+
+
+def pcg(A: CSR, mask, b, gext, x0, rtol, max_iters=100000, precond=1, fixed=0):
+    """Textbook JCG / CG (or_pcg); fixed=1 runs exactly max_iters steps."""
+    x = _f64(x0).copy()
+    it, rr, fh = C.c_int32(), C.c_double(), C.c_double()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    b, g = _f64(b), _f64(gext)
+    st = lib().or_pcg(A.N, _p(A.rowptr), _p(A.col), _p(A.val), _p(m), _p(b), _p(g), _p(x), rtol, max_iters,
+                      precond, fixed, C.byref(it), C.byref(rr), C.byref(fh))
+    return x, dict(status=st, iters=it.value, rel_res=rr.value, rhs_norm=fh.value)
+
+
+def pcg_single_pass(A: CSR, mask, b, gext, x0, rtol, max_iters=100000, precond=1):
+    """The same iteration in the single-pass arrangement (or_pcg_single_pass)."""
+    x = _f64(x0).copy()
+    it, rr, fh = C.c_int32(), C.c_double(), C.c_double()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    b, g = _f64(b), _f64(gext)
+    st = lib().or_pcg_single_pass(A.N, _p(A.rowptr), _p(A.col), _p(A.val), _p(m), _p(b), _p(g), _p(x), rtol,
+                                  max_iters, precond, C.byref(it), C.byref(rr), C.byref(fh))
     return x, dict(status=st, iters=it.value, rel_res=rr.value, rhs_norm=fh.value)
 
 

@@ -65,6 +65,7 @@ struct Level {
     // FP32 vectors (mixed precision)
     float *beta32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *pA32 = nullptr, *pB32 = nullptr,
           *q32 = nullptr, *e32 = nullptr;
+    float *r32B = nullptr, *q32B = nullptr;  // single-pass form: second r and q buffers
     PlaneMaps maps;  // TMA descriptors of the FP32 vectors
     ResMaps rmaps;   // TMA descriptors of U and of b / c (exact constant-coefficient residual)
     K1Config k1{1, 128};  // tile shape of the FP32 stencil kernel
@@ -173,6 +174,8 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
         return fail(ECMG_ERR_INVALID_ARG, "bad preconditioner");
     if (o->schedule != ECMG_SCHED_TOLERANCE && o->schedule != ECMG_SCHED_FIXED)
         return fail(ECMG_ERR_INVALID_ARG, "bad schedule");
+    if (o->cg_form != ECMG_CG_TWO_PASS && o->cg_form != ECMG_CG_SINGLE_PASS)
+        return fail(ECMG_ERR_INVALID_ARG, "bad cg_form");
     if (o->schedule == ECMG_SCHED_FIXED) {
         if (o->sched_mL < 1 || !(o->sched_beta >= 1.0 && o->sched_beta <= 64.0))
             return fail(ECMG_ERR_INVALID_ARG, "fixed schedule: sched_mL >= 1 and sched_beta in [1, 64]");
@@ -182,13 +185,20 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
     return ECMG_OK;
 }
 
-// Byte count of the per-level vectors (the same arithmetic allocate() performs).
-uint64_t level_bytes(const Grid& g, bool mixed)
+// Byte count of the per-level vectors (the same arithmetic ecmg_create performs).
+uint64_t level_bytes(const Grid& g, bool mixed, bool single_pass)
 {
     const uint64_t n = (uint64_t)g.total;
     uint64_t b = n * 8ull * 14ull;  // U W Ut b beta dinv f gD gR r pA pB q (+1 spare alignment)
-    if (mixed) b += n * 4ull * 7ull;
+    if (mixed) b += n * 4ull * (single_pass ? 9ull : 7ull);
     return b;
+}
+
+// Partial sums per block of the reducing kernels: 3 (FP64 and residual kernels), 7 (the
+// single-pass step on the general path); rounded up to 8.
+int partials_per_block(const ecmg_options& o)
+{
+    return (o.precision == ECMG_MIXED && o.cg_form == ECMG_CG_SINGLE_PASS) ? 8 : 3;
 }
 
 template <typename T>
@@ -258,16 +268,19 @@ void host_state(ecmg_handle* h, int l, SolveState* out)
 bool constant_coefficient(ecmg_handle* h, const Level& v);
 void drop_graph(ecmg_handle* h);
 
-// FP64 residual of the MIXED iteration into r32: on a constant-coefficient level (the host's
-// choice v.cc, cubic elements) the TMA-staged exact kernel, else the general one.
-void res32(ecmg_handle* h, Level& v, SolveState* st, ResMode mode, CondHandles ch, cudaStream_t s)
+// FP64 residual of the MIXED iteration into r32 (or, in the single-pass form, into the residual
+// buffer the next step reads): on a constant-coefficient level (the host's choice v.cc, cubic
+// elements) the TMA-staged exact kernel, else the general one.
+void res32(ecmg_handle* h, Level& v, SolveState* st, ResMode mode, CondHandles ch, cudaStream_t s,
+           float* rdst = nullptr)
 {
+    float* r = rdst ? rdst : v.r32;
     if (v.cc && v.op.cube) {
         // a replacement follows the fold, which has taken max |U| already
         if (mode != RES_REPLACE) launch_absmax(v.g, v.U, v.uniform, st, (int)mode, h->part, s);
-        launch_res32_cc(v.rmaps, v.g, v.uniform, v.beta, v.dinv32, v.r32, st, h->part, mode, ch, s);
+        launch_res32_cc(v.rmaps, v.g, v.uniform, v.beta, v.dinv32, r, st, h->part, mode, ch, s);
     } else {
-        launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, v.r32, st, h->part, mode, ch, s, v.r);
+        launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, r, st, h->part, mode, ch, s, v.r);
     }
 }
 
@@ -387,6 +400,53 @@ void record_level(Rec& R, int l)
         ck(cudaMemsetAsync(v.pA32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
+        if (v.r32B) {
+            // Single-pass form: step `half` reads (r, q, p) of set A (half 0) or B (half 1) and
+            // writes the other set; the residual of the initial state and of a replacement goes
+            // to the r buffer the next step reads. r and q keep 0 on the nodes no step visits.
+            float* rbuf[2] = {v.r32, v.r32B};
+            float* qbuf[2] = {v.q32, v.q32B};
+            float* pbuf[2] = {v.pA32, v.pB32};
+            auto sp_step = [&](CondHandles ch, int half) {
+                const int o = half ^ 1;
+                launch_step32(v.maps, half, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pbuf[o], qbuf[o],
+                              rbuf[o], v.e32, st, h->part, o, ch, h->timers + l, R.s());
+            };
+            auto sp_replace = [&](int half) {
+                const int o = half ^ 1;
+                launch_fold32(v.g, v.U, v.e32, pbuf[o], v.uniform, st, h->part, R.s());
+                res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[o]);
+            };
+            if (R.graph) {
+                const cudaGraphConditionalHandle loop = R.new_handle();
+                res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s(), rbuf[0]);
+                R.open(loop, cudaGraphCondTypeWhile);
+                for (int half = 0; half < 2; ++half) {
+                    const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
+                    sp_step(CondHandles{loop, upd, 1}, half);
+                    R.open(upd, cudaGraphCondTypeIf);
+                    sp_replace(half);
+                    R.close();
+                }
+                R.close();
+            } else {
+                res32(h, v, st, RES_INIT, none, R.s(), rbuf[0]);
+                SolveState hs;
+                host_state(h, l, &hs);
+                int half = 0;
+                while (!hs.done) {
+                    sp_step(none, half);
+                    host_state(h, l, &hs);
+                    if (hs.need_update && !hs.done) {
+                        sp_replace(half);
+                        host_state(h, l, &hs);
+                    }
+                    half ^= 1;
+                }
+            }
+            if (!direct) launch_exp_true(v.g, v.U, h->lv[l - 1].g, h->lv[l - 1].U, v.Ut, R.s());
+            return;
+        }
         auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
             launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pout, v.q32, v.e32,
                             st, h->part, idx, ch, h->timers + l, R.s());
@@ -735,7 +795,7 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
         ck(cudaMemcpyAsync(&last, h->states + l, sizeof(last), cudaMemcpyDeviceToHost, s));
         ck(cudaStreamSynchronize(s));
         tmpl.bcbits = last.bcbits;
-        const bool cc = (which == 0 || which == 2) && constant_coefficient(h, v);
+        const bool cc = (which == 0 || which == 2 || which == 11) && constant_coefficient(h, v);
         ck(cudaEventCreate(&e0));
         ck(cudaEventCreate(&e1));
         for (int rep = 0; rep <= reps; ++rep) {
@@ -769,6 +829,10 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
             }
             case 8: launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, s); break;
             case 9: launch_fold32(v.g, v.Ut, v.e32, v.pA32, v.uniform, st, h->part, s); break;
+            case 11:
+                launch_step32(v.maps, 0, v.k1, v.g, v.op, cc, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32B, v.r32B,
+                              v.e32, st, h->part, 1, none, nullptr, s);
+                break;
             default: launch_absmax(v.g, v.U, v.uniform, nullptr, 0, h->part, s); break;
             }
             ck(cudaEventRecord(e1, s));
@@ -805,10 +869,11 @@ void autotune(ecmg_handle* h, int reps)
         const int n = k1_candidates(v.g, cand, 32);
         const K1Config start = v.k1;
         K1Config best = start;
-        double best_ms = time_launches(h, l, 0, reps);
+        const int which = v.r32B ? 11 : 0;  // the step kernel the solve runs
+        double best_ms = time_launches(h, l, which, reps);
         for (int c = 0; c < n; ++c) {
             v.k1 = cand[c];
-            const double ms = time_launches(h, l, 0, reps);
+            const double ms = time_launches(h, l, which, reps);
             if (ms < best_ms) {
                 best_ms = ms;
                 best = cand[c];
@@ -840,6 +905,7 @@ void ecmg_default_options(ecmg_options* o)
     o->schedule = ECMG_SCHED_TOLERANCE;
     o->sched_mL = 4;
     o->sched_beta = 4.0;
+    o->cg_form = ECMG_CG_TWO_PASS;
 }
 
 ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, uint64_t* bytes)
@@ -851,13 +917,13 @@ ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, u
     int maxb = 0;
     for (int l = 0; l < p->levels; ++l) {
         Grid g = make_grid(*p, l);
-        b += level_bytes(g, o->precision == ECMG_MIXED);
+        b += level_bytes(g, o->precision == ECMG_MIXED, o->cg_form == ECMG_CG_SINGLE_PASS && l >= 2);
         if (p->f_mode == ECMG_F_SEPARABLE) b += 8ull * (uint64_t)sep_factor_len(g, p->f_terms);
         if (p->gD_terms > 0 && l < p->levels - 1) b += 8ull * (uint64_t)sep_factor_len(g, p->gD_terms);
         maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
         if (o->precision == ECMG_MIXED) maxb = std::max(maxb, std::max(max_tma_blocks(g), res_cc_blocks(g)));
     }
-    b += (uint64_t)maxb * 3 * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
+    b += (uint64_t)maxb * partials_per_block(*o) * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
     *bytes = b;
     return ECMG_OK;
 }
@@ -913,12 +979,17 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
                 if (!make_plane_maps(&v.maps, v.r32, v.pA32, v.pB32, v.dinv32, v.beta32, v.e32, v.g) ||
                     !make_res_maps(&v.rmaps, v.U, v.r, v.g))
                     throw CudaFail{cudaErrorNotSupported};
+                if (opt->cg_form == ECMG_CG_SINGLE_PASS && l >= 2) {
+                    v.r32B = dalloc<float>(h, n);
+                    v.q32B = dalloc<float>(h, n);
+                    if (!make_plane_maps_sp(&v.maps, v.r32B, v.q32, v.q32B, v.g)) throw CudaFail{cudaErrorNotSupported};
+                }
                 v.k1 = k1_default(v.g, v.op);
                 maxb = std::max(maxb, std::max(max_tma_blocks(v.g), res_cc_blocks(v.g)));
             }
             maxb = std::max(maxb, std::max(max_stencil_blocks(v.g), max_stream_blocks()));
         }
-        h->part.buf = dalloc<double>(h, (int64_t)maxb * 3);
+        h->part.buf = dalloc<double>(h, (int64_t)maxb * partials_per_block(*opt));
         h->part.max_blocks = maxb;
         h->part.fs = dalloc<FixedScale>(h, 1);
         h->states = dalloc<SolveState>(h, MAX_LEVELS);
@@ -958,6 +1029,7 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
     *out = nullptr;
     if (n < 1 || n > BATCH_MAX) return fail(ECMG_ERR_INVALID_ARG, "batch size must be 1..128");
     if (opt->precision != ECMG_MIXED) return fail(ECMG_ERR_INVALID_ARG, "batched solves run in MIXED precision");
+    if (opt->cg_form != ECMG_CG_TWO_PASS) return fail(ECMG_ERR_INVALID_ARG, "batched solves run the two-pass step");
     for (int p = 0; p < n; ++p) {
         ecmg_status s = validate(probs + p, opt);
         if (s != ECMG_OK) return s;
@@ -1265,8 +1337,8 @@ const char* ecmg_last_error(void) { return g_last_error.c_str(); }
 ecmg_status ecmg_kernel_launches(uint64_t* out)
 {
     if (!out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
-    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_batch() + launches_separable() +
-           launches_res_cc();
+    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_pq_sp() + launches_batch() +
+           launches_separable() + launches_res_cc();
     return ECMG_OK;
 }
 
@@ -1276,8 +1348,9 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
     if (!h || !ms_out || !bytes_out || reps < 1) return fail(ECMG_ERR_INVALID_ARG, "bad argument");
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
-    if (which < 0 || which > 10) return fail(ECMG_ERR_INVALID_ARG, "bad kernel selector");
+    if (which < 0 || which > 11) return fail(ECMG_ERR_INVALID_ARG, "bad kernel selector");
     Level& v = h->lv[l];
+    if (which == 11 && !v.r32B) return fail(ECMG_ERR_INVALID_ARG, "level has no single-pass buffers");
     if ((which <= 2 || which == 9) && !v.r32) return fail(ECMG_ERR_INVALID_ARG, "handle has no FP32 vectors");
     if (which >= 6 && l < 2) return fail(ECMG_ERR_INVALID_ARG, "EXP kernels need level >= 2");
     const double N = (double)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1);
@@ -1293,10 +1366,12 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
         return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
     }
     // the constant-coefficient residual (kernel 2) reads x and b / c and writes r: 20 bytes per
-    // node; ||f_h|| (8) reads b; the fold (9) updates x and e and reads p; max |x| (10) reads x
-    const double bytes[11] = {(cc ? 24 * N1 : 28 * N1 + 4 * E), (cc ? 12 * N : 16 * N),
+    // node; ||f_h|| (8) reads b; the fold (9) updates x and e and reads p; max |x| (10) reads x;
+    // the single-pass step (11) moves r, q, p and e in and out (and D^-1, beta in)
+    const double bytes[12] = {(cc ? 24 * N1 : 28 * N1 + 4 * E), (cc ? 12 * N : 16 * N),
                               (cc && v.op.cube ? 20 * N : 24 * N + 8 * E), 56 * N + 8 * E, 32 * N, 32 * N + 8 * E,
-                              16 * N + 8 * (N / 8 + N / 64), 17 * N, 8 * N, 28 * N, 8 * N};
+                              16 * N + 8 * (N / 8 + N / 64), 17 * N, 8 * N, 28 * N, 8 * N,
+                              (cc ? 32 * N1 : 36 * N1 + 4 * E)};
     *bytes_out = bytes[which];
     try {
         *ms_out = time_launches(h, l, which, reps);

@@ -12,9 +12,11 @@ constexpr int K1_NRY = 2;
 constexpr int K1_RY[K1_NRY] = {1, 2};
 
 // Tensor maps of one level's FP32 vectors; set v stages boxes of 40 x (8*K1_RY[v]+2) x 1
-// (e: 36 x 8*K1_RY[v] x 1, the tile's own rows).
+// (e: 36 x 8*K1_RY[v] x 1, the tile's own rows). r is the first residual buffer; rB, qA and qB
+// (the second residual buffer and the two q buffers) are encoded for single-pass levels only.
 struct PlaneMaps {
     CUtensorMap r[K1_NRY], pA[K1_NRY], pB[K1_NRY], dinv[K1_NRY], beta[K1_NRY], e[K1_NRY];
+    CUtensorMap rB[K1_NRY], qA[K1_NRY], qB[K1_NRY];
 };
 
 // Tile shape of K1 on one level: ry node rows per thread, kz planes marched per block.
@@ -28,7 +30,10 @@ struct K1Config {
 bool make_plane_maps(PlaneMaps* m, const float* r, const float* pA, const float* pB, const float* dinv,
                      const float* beta, const float* e, const Grid& g);
 
-// Set the shared-memory limit of every K1 instantiation on the current device.
+// The single-pass buffers of a level: second residual buffer and the two q buffers.
+bool make_plane_maps_sp(PlaneMaps* m, const float* rB, const float* qA, const float* qB, const Grid& g);
+
+// Set the shared-memory limit of every K1 instantiation (both forms) on the current device.
 cudaError_t k1_prepare();
 // Heuristic tile shape, the candidate shapes an autotuner may try, and validity.
 K1Config k1_default(const Grid& g, const Op& op);
@@ -49,6 +54,18 @@ void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const
                      const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
                      SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s);
 
+// Single-pass step (ECMG_CG_SINGLE_PASS): with (r_in, q_in, p_old) the buffers A (in_b = 0) or
+// B (in_b = 1) and the outputs the other three: r = r_in - alpha_prev q_in, e += alpha_prev p_old,
+// p = D^-1 r + beta p_old, q = A p; stores r, p, q; the last block sets alpha, the expanded
+// next r.z and r.r, the test of update_epilogue and the loop's conditions (loop, update).
+// cc as for launch_pq32_tma.
+void launch_step32(const PlaneMaps& m, int in_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
+                   const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* qnew,
+                   float* rnew, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm,
+                   cudaStream_t s);
+cudaError_t k1_sp_prepare();
+
 unsigned long long launches_pq_tma();
+unsigned long long launches_pq_sp();
 
 }  // namespace ecmg

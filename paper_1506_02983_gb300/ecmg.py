@@ -28,6 +28,7 @@ ECMG_EXP_SERENDIPITY20, ECMG_EXP_LAGRANGE27 = 0, 1
 ECMG_VEC_U, ECMG_VEC_W, ECMG_VEC_UTILDE, ECMG_VEC_B, ECMG_VEC_BETA = 0, 1, 2, 3, 4
 ECMG_PREC_JACOBI, ECMG_PREC_NONE = 0, 1
 ECMG_SCHED_TOLERANCE, ECMG_SCHED_FIXED = 0, 1
+ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS = 0, 1
 ECMG_NOALLOC_MAX_ELEMS = 536870912  # include/ecmg.h
 
 
@@ -45,7 +46,7 @@ class ecmg_options(C.Structure):
                 ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("dsolve_rtol", C.c_double),
                 ("exp_variant", C.c_int32), ("true_residual", C.c_int32), ("autotune", C.c_int32),
                 ("preconditioner", C.c_int32), ("schedule", C.c_int32), ("sched_mL", C.c_int32),
-                ("sched_beta", C.c_double)]
+                ("sched_beta", C.c_double), ("cg_form", C.c_int32)]
 
 
 class ecmg_stats(C.Structure):

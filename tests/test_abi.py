@@ -104,9 +104,16 @@ def test_solver_variant_options_validation_without_gpu(libpath):
                 dict(schedule=1, sched_mL=2000000, sched_beta=64.0)):
         o = ecmg.default_options(**bad)
         assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG, bad
+    o = ecmg.default_options(cg_form=2)
+    assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+    # the batched entry point runs the two-pass step only
+    o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=ecmg.ECMG_CG_SINGLE_PASS)
+    assert ecmg.ecmg_create_batched(ctypes.byref(p), 1, ctypes.byref(o), None, ctypes.byref(h)) == \
+        ecmg.ECMG_ERR_INVALID_ARG
     o = ecmg.default_options()
     assert o.preconditioner == ecmg.ECMG_PREC_JACOBI and o.schedule == ecmg.ECMG_SCHED_TOLERANCE
     assert o.sched_mL == 4 and o.sched_beta == 4.0 and o.inner_rtol == 1e-3
+    assert o.cg_form == ecmg.ECMG_CG_TWO_PASS
 
 
 def test_compact_input_validation_without_gpu(libpath):

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (derived in the design doc):
+Tolerances, from the arithmetic of each path:
   - set-up vectors and the FP64 operator: rounding-order differences only, 1e-13 relative;
   - FP32 operator: difference form on FP32-rounded data, 1e-5 of max |A x|;
   - FP64 solves: the method's own bar, 1e-10 relative in max norm and JCG iteration counts

@@ -77,3 +77,35 @@ def test_fe_solution_is_second_order(oracle_mod):
         errs.append(np.abs(x - p["u_exact"].ravel()).max())
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(orders - 2.0) < 0.05), orders
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("precond", [1, 0])
+def test_single_pass_jcg_has_the_iterates_of_textbook_jcg(oracle_mod, seed, precond):
+    """The single-pass arrangement reaches, after every step count k, the iterate the textbook
+    recurrence reaches after k steps (exact arithmetic makes them equal; FP64 keeps them within
+    1e-10 over these short runs): a dropped or mis-signed term in the expanded r.z or ||r||
+    changes beta from the second step on and fails this at once."""
+    p = inputs.random_problem(seed, n0=(4, 3, 5), levels=1)
+    n, A, b, mask, gext = _level_system(oracle_mod, p)
+    for k in (1, 2, 3, 5, 8, 13):
+        x_ref, st_ref = oracle_mod.pcg(A, mask, b, gext, gext, rtol=1e-30, max_iters=k, precond=precond, fixed=1)
+        x_sp, st_sp = oracle_mod.pcg_single_pass(A, mask, b, gext, gext, rtol=1e-30, max_iters=k, precond=precond)
+        assert st_ref["iters"] == st_sp["iters"] == k
+        assert st_sp["status"] == 3
+        assert np.abs(x_sp - x_ref).max() <= 1e-10 * np.abs(x_ref).max(), k
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_single_pass_jcg_converges_like_textbook_jcg(oracle_mod, seed):
+    """To a tolerance: the same step count (within one, the test reading the expanded norm
+    instead of the recursively updated residual), the true residual below the tolerance, and the
+    dense solution."""
+    p = inputs.random_problem(seed, n0=(3, 4, 2), levels=1)
+    n, A, b, mask, gext = _level_system(oracle_mod, p)
+    x_ref = _dense_solution(A, b, mask, gext)
+    x_cg, st = oracle_mod.jcg(A, mask, b, gext, gext, rtol=1e-12)
+    x_sp, st_sp = oracle_mod.pcg_single_pass(A, mask, b, gext, gext, rtol=1e-12)
+    assert st_sp["status"] == 0 and abs(st_sp["iters"] - st["iters"]) <= 1
+    assert st_sp["rel_res"] <= 1e-12 * 1.01
+    assert np.abs(x_sp - x_ref).max() <= 1e-9 * np.abs(x_ref).max()
