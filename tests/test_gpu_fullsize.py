@@ -109,6 +109,16 @@ def test_cos_cube_512_mixed_full_size(E, oracle_mod):
     for l in range(2, L):
         assert abs(st64["iters"][l] - st["iters"][l]) <= max(2, 0.1 * st64["iters"][l]), (st64["iters"], st["iters"])
     s64.close()
+    # the single-pass MIXED step (ECMG_CG_SINGLE_PASS) on the same workload: the residual test on
+    # every level, the same error to 1 %, and the two-pass step counts within 10 %
+    sp = E.solver_from_problem(p, precision=E.ECMG_MIXED, autotune=1, cg_form=E.ECMG_CG_SINGLE_PASS)
+    st_sp, status = sp.solve()
+    assert status == 0, st_sp
+    for l in range(2, L):
+        assert st_sp["rel_res"][l] <= p["rtol"] * 1.0001, (l, st_sp["rel_res"])
+        assert abs(st_sp["iters"][l] - st["iters"][l]) <= max(2, 0.1 * st["iters"][l]), (st_sp["iters"], st["iters"])
+    assert _max_err(_np(sp.get(E.ECMG_VEC_U)), ue) == pytest.approx(e64, rel=0.01)
+    sp.close()
 
 
 def test_variable_box_full_size_fp64(E, oracle_mod):
@@ -200,6 +210,29 @@ def test_jump_singular_full_size_mixed(E, oracle_mod):
     U = _np(s.get(E.ECMG_VEC_U)).ravel()
     b = _np(s.get(E.ECMG_VEC_B)).ravel()
     free = [t for t in nodes if t[0] < n[0] and all(0 < t[a] < n[a] for a in (1, 2))]
+    r = _at(b, n, free) - oracle_mod.apply_at(n, h, beta, p["face_bc"], p["alpha"], U, free)
+    assert np.abs(r).max() <= p["rtol"] * st["rhs_norm"][L - 1] * 1.0001, np.abs(r).max()
+    s.close()
+
+
+def test_jump_singular_full_size_single_pass(E, oracle_mod):
+    """Configuration 5 with the single-pass MIXED step on its general path (variable beta, a
+    Robin face): the residual test on every level, and b - A U recomputed by the oracle at
+    sampled free nodes within the test."""
+    p = inputs.jump_singular(levels=7, rtol=1e-8, device="cuda")
+    L = p["levels"]
+    s = E.solver_from_problem(p, precision=E.ECMG_MIXED, autotune=1, cg_form=E.ECMG_CG_SINGLE_PASS)
+    st, status = s.solve()
+    assert status == 0, st
+    for l in range(2, L):
+        assert st["rel_res"][l] <= p["rtol"] * 1.0001, (l, st["rel_res"])
+    assert (s.get(E.ECMG_VEC_U) - p["u_exact"]).abs().max().item() < 1e-3
+    n = [v << (L - 1) for v in p["n0"]]
+    h = [(p["hi"][a] - p["lo"][a]) / n[a] for a in range(3)]
+    beta = p["beta"].cpu().numpy().ravel()
+    U = _np(s.get(E.ECMG_VEC_U)).ravel()
+    b = _np(s.get(E.ECMG_VEC_B)).ravel()
+    free = [t for t in _sample_nodes(n, 300, 6) if t[0] < n[0] and all(0 < t[a] < n[a] for a in (1, 2))]
     r = _at(b, n, free) - oracle_mod.apply_at(n, h, beta, p["face_bc"], p["alpha"], U, free)
     assert np.abs(r).max() <= p["rtol"] * st["rhs_norm"][L - 1] * 1.0001, np.abs(r).max()
     s.close()
