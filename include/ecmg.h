@@ -39,6 +39,7 @@
 #ifndef ECMG_H
 #define ECMG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -147,6 +148,12 @@ typedef struct {
                             /* else the recursive one)                                      */
     double rhs_norm[16];    /* ||f_h||_2, the free-node right-hand side with g_D moved over */
     int32_t status;         /* ecmg_status of the solve                                     */
+    double seconds[16];     /* single-problem solves: device time of each level (its DSOLVE or
+                               EXP_finite, JCG and EXP_true), from the GPU's global timer at
+                               the level's first and the next level's first kernel; 0 for
+                               levels a solve did not run and for batched solves             */
+    double setup_seconds;   /* device time of the level set-up of all levels (0 when a solve
+                               starts above level 0, or batched)                             */
 } ecmg_stats;
 
 typedef struct ecmg_handle ecmg_handle;
@@ -160,6 +167,21 @@ void ecmg_default_options(ecmg_options* opt);
  * Dirichlet and every Robin alpha is 0, ECMG_ERR_OOM when allocation fails. */
 ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void* stream,
                         ecmg_handle** out);
+
+/* Device memory from the caller: alloc returns `bytes` of device memory usable on `stream`
+ * (NULL when it cannot), free gives back a block alloc returned, with the same size. `ctx`
+ * is passed through unchanged. A framework that owns device memory (a caching allocator)
+ * supplies both, so that the workspace counts against its pools. */
+typedef void* (*ecmg_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*ecmg_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+/* As ecmg_create, with every device allocation of the handle's workspace made through
+ * alloc and released through free (in ecmg_destroy, after the stream has synchronised; also
+ * when creation fails part way). alloc and free must both be given; ECMG_ERR_INVALID_ARG
+ * otherwise. A NULL from alloc fails creation with ECMG_ERR_OOM. Pinned host buffers of the
+ * handle still come from the CUDA runtime. */
+ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_options* opt, void* stream,
+                                       ecmg_alloc_fn alloc, ecmg_free_fn free, void* ctx, ecmg_handle** out);
 
 /* Run Alg. 4: level set-up from the current input arrays (beta averaging, loads, Jacobi
  * diagonals), DSOLVE on levels 0 and 1, then for each finer level EXP_finite, JCG and

@@ -89,7 +89,12 @@ struct ecmg_handle {
     KTimer* timers = nullptr;      // device, one per level: the FP32 stencil launches of the solves
     Partials part{nullptr, 0, nullptr};
     double* norm_part = nullptr;   // device, per-block norm partials
-    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> allocs;  // device workspace blocks and their sizes
+    ecmg_alloc_fn alloc_fn = nullptr;              // caller's allocator (ecmg_create_with_allocator)
+    ecmg_free_fn free_fn = nullptr;
+    void* alloc_ctx = nullptr;
+    unsigned long long* stamps = nullptr;       // device: global timer at the set-up, at each level's start, at the end
+    unsigned long long* host_stamps = nullptr;  // pinned copy
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     SolveState* host_states = nullptr;  // pinned
@@ -205,9 +210,16 @@ template <typename T>
 T* dalloc(ecmg_handle* h, int64_t n)
 {
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, (size_t)n * sizeof(T));
-    if (e != cudaSuccess) throw CudaFail{e};
-    h->allocs.push_back(p);
+    const size_t bytes = (size_t)n * sizeof(T);
+    if (bytes == 0) return nullptr;
+    if (h->alloc_fn) {
+        p = h->alloc_fn(bytes, (void*)h->user_stream, h->alloc_ctx);
+        if (!p) throw CudaFail{cudaErrorMemoryAllocation};
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) throw CudaFail{e};
+    }
+    h->allocs.emplace_back(p, bytes);
     ck(cudaMemsetAsync(p, 0, (size_t)n * sizeof(T), h->cap[0]));
     return (T*)p;
 }
@@ -400,92 +412,55 @@ void record_level(Rec& R, int l)
         ck(cudaMemsetAsync(v.pA32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
-        if (v.r32B) {
-            // Single-pass form: step `half` reads (r, q, p) of set A (half 0) or B (half 1) and
-            // writes the other set; the residual of the initial state and of a replacement goes
-            // to the r buffer the next step reads. r and q keep 0 on the nodes no step visits.
-            float* rbuf[2] = {v.r32, v.r32B};
-            float* qbuf[2] = {v.q32, v.q32B};
-            float* pbuf[2] = {v.pA32, v.pB32};
-            auto sp_step = [&](CondHandles ch, int half) {
-                const int o = half ^ 1;
+        // Step `half` of the loop body reads the buffers of set A (half 0) or B (half 1) and
+        // writes the other set: p in both forms, r and q too in the single-pass form (which
+        // keeps 0 in them on the nodes no step visits). The residual of the initial state and
+        // of a replacement goes to the r buffer the next step reads.
+        const bool single = v.r32B != nullptr;
+        float* rbuf[2] = {v.r32, single ? v.r32B : v.r32};
+        float* qbuf[2] = {v.q32, single ? v.q32B : v.q32};
+        float* pbuf[2] = {v.pA32, v.pB32};
+        auto step = [&](CondHandles ch, int half) {
+            const int o = half ^ 1;
+            if (single) {
                 launch_step32(v.maps, half, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pbuf[o], qbuf[o],
                               rbuf[o], v.e32, st, h->part, o, ch, h->timers + l, R.s());
-            };
-            auto sp_replace = [&](int half) {
-                const int o = half ^ 1;
-                launch_fold32(v.g, v.U, v.e32, pbuf[o], v.uniform, st, h->part, R.s());
-                res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[o]);
-            };
-            if (R.graph) {
-                const cudaGraphConditionalHandle loop = R.new_handle();
-                res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s(), rbuf[0]);
-                R.open(loop, cudaGraphCondTypeWhile);
-                for (int half = 0; half < 2; ++half) {
-                    const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
-                    sp_step(CondHandles{loop, upd, 1}, half);
-                    R.open(upd, cudaGraphCondTypeIf);
-                    sp_replace(half);
-                    R.close();
-                }
-                R.close();
             } else {
-                res32(h, v, st, RES_INIT, none, R.s(), rbuf[0]);
-                SolveState hs;
-                host_state(h, l, &hs);
-                int half = 0;
-                while (!hs.done) {
-                    sp_step(none, half);
-                    host_state(h, l, &hs);
-                    if (hs.need_update && !hs.done) {
-                        sp_replace(half);
-                        host_state(h, l, &hs);
-                    }
-                    half ^= 1;
-                }
+                launch_pq32_tma(v.maps, half, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pbuf[o], v.q32,
+                                v.e32, st, h->part, o, ch, h->timers + l, R.s());
+                launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
             }
-            if (!direct) launch_exp_true(v.g, v.U, h->lv[l - 1].g, h->lv[l - 1].U, v.Ut, R.s());
-            return;
-        }
-        auto step = [&](CondHandles ch, const float* pin, float* pout, int idx) {
-            launch_pq32_tma(v.maps, pin == v.pB32, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pout, v.q32, v.e32,
-                            st, h->part, idx, ch, h->timers + l, R.s());
-            launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
         };
-        auto replace = [&](float* pnew) {
-            launch_fold32(v.g, v.U, v.e32, pnew, v.uniform, st, h->part, R.s());
-            res32(h, v, st, RES_REPLACE, none, R.s());
+        auto replace = [&](int half) {
+            const int o = half ^ 1;
+            launch_fold32(v.g, v.U, v.e32, pbuf[o], v.uniform, st, h->part, R.s());
+            res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[o]);
         };
         if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
-            res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s());
+            res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s(), rbuf[0]);
             R.open(loop, cudaGraphCondTypeWhile);
             for (int half = 0; half < 2; ++half) {
                 const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
-                const CondHandles ch{loop, upd, 1};
-                float* pin = half ? v.pB32 : v.pA32;
-                float* pout = half ? v.pA32 : v.pB32;
-                step(ch, pin, pout, half ? 0 : 1);
+                step(CondHandles{loop, upd, 1}, half);
                 R.open(upd, cudaGraphCondTypeIf);
-                replace(pout);
+                replace(half);
                 R.close();
             }
             R.close();
         } else {
-            res32(h, v, st, RES_INIT, none, R.s());
+            res32(h, v, st, RES_INIT, none, R.s(), rbuf[0]);
             SolveState hs;
             host_state(h, l, &hs);
-            int parity = 0;
+            int half = 0;
             while (!hs.done) {
-                float* pin = parity ? v.pB32 : v.pA32;
-                float* pout = parity ? v.pA32 : v.pB32;
-                step(none, pin, pout, parity ? 0 : 1);
+                step(none, half);
                 host_state(h, l, &hs);
                 if (hs.need_update && !hs.done) {
-                    replace(pout);
+                    replace(half);
                     host_state(h, l, &hs);
                 }
-                parity ^= 1;
+                half ^= 1;
             }
         }
     }
@@ -495,10 +470,20 @@ void record_level(Rec& R, int l)
     }
 }
 
+// The whole solve from level `first`, with a global-timer stamp before the set-up, before each
+// level and at the end (the per-level seconds of ecmg_stats).
 void record_solve(Rec& R, int first)
 {
-    if (first == 0) record_setup(R);
-    for (int l = first; l < R.h->L; ++l) record_level(R, l);
+    ecmg_handle* h = R.h;
+    if (first == 0) {
+        launch_stamp(h->stamps, R.s());
+        record_setup(R);
+    }
+    for (int l = first; l < h->L; ++l) {
+        launch_stamp(h->stamps + 1 + l, R.s());
+        record_level(R, l);
+    }
+    launch_stamp(h->stamps + 1 + h->L, R.s());
 }
 
 ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stats, bool retried = false)
@@ -546,6 +531,8 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
         ck(cudaGetLastError());
         ck(cudaMemcpyAsync(h->host_states, h->states, sizeof(SolveState) * h->L, cudaMemcpyDeviceToHost,
                            h->user_stream));
+        ck(cudaMemcpyAsync(h->host_stamps, h->stamps, sizeof(unsigned long long) * (h->L + 2),
+                           cudaMemcpyDeviceToHost, h->user_stream));
         ck(cudaStreamSynchronize(h->user_stream));
     } catch (CudaFail& f) {
         return fail(ECMG_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(f.e));
@@ -562,9 +549,12 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
     ecmg_stats st;
     memset(&st, 0, sizeof(st));
     st.levels = h->L;
+    const unsigned long long* t = h->host_stamps;
+    if (first == 0) st.setup_seconds = 1e-9 * (double)(t[1] - t[0]);
     for (int l = 0; l < h->L; ++l) {
         const SolveState& s = h->host_states[l];
         if (l < first) continue;
+        st.seconds[l] = 1e-9 * (double)(t[2 + l] - t[1 + l]);
         st.iters[l] = s.iters;
         st.updates[l] = s.updates;
         st.rhs_norm[l] = std::sqrt(s.fh2);
@@ -931,11 +921,21 @@ ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, u
 ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void* stream,
                         ecmg_handle** out)
 {
+    return ecmg_create_with_allocator(prob, opt, stream, nullptr, nullptr, nullptr, out);
+}
+
+ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_options* opt, void* stream,
+                                       ecmg_alloc_fn alloc, ecmg_free_fn free_fn, void* ctx, ecmg_handle** out)
+{
     if (!out) return fail(ECMG_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(ECMG_ERR_INVALID_ARG, "alloc and free go together");
     ecmg_status s = validate(prob, opt);
     if (s != ECMG_OK) return s;
     ecmg_handle* h = new ecmg_handle();
+    h->alloc_fn = alloc;
+    h->free_fn = free_fn;
+    h->alloc_ctx = ctx;
     h->prob = *prob;
     h->opt = *opt;
     h->user_stream = (cudaStream_t)stream;
@@ -1004,6 +1004,8 @@ ecmg_status ecmg_create(const ecmg_problem* prob, const ecmg_options* opt, void*
         h->norm_part = dalloc<double>(h, 2048);
         ck(cudaMallocHost(&h->host_states, sizeof(SolveState) * MAX_LEVELS));
         ck(cudaMallocHost(&h->host_norms, sizeof(double) * 2048));
+        h->stamps = dalloc<unsigned long long>(h, MAX_LEVELS + 2);
+        ck(cudaMallocHost(&h->host_stamps, sizeof(unsigned long long) * (MAX_LEVELS + 2)));
         ck(cudaStreamSynchronize(h->cap[0]));
         if (mixed && opt->autotune) autotune(h, 3);
     } catch (CudaFail& f) {
@@ -1306,13 +1308,17 @@ void ecmg_destroy(ecmg_handle* h)
     cudaStreamSynchronize(h->user_stream);
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    for (void* p : h->allocs) cudaFree(p);
+    for (auto& a : h->allocs) {
+        if (h->free_fn) h->free_fn(a.first, a.second, (void*)h->user_stream, h->alloc_ctx);
+        else cudaFree(a.first);
+    }
     if (h->batch) {
         if (h->batch->host_states) cudaFreeHost(h->batch->host_states);
         delete h->batch;
     }
     if (h->host_states) cudaFreeHost(h->host_states);
     if (h->host_norms) cudaFreeHost(h->host_norms);
+    if (h->host_stamps) cudaFreeHost(h->host_stamps);
     for (int i = 0; i < 3; ++i)
         if (h->cap[i]) cudaStreamDestroy(h->cap[i]);
     delete h;

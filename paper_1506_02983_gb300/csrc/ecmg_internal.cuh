@@ -185,6 +185,9 @@ void uniform_check(const Grid& g, const double* beta, int* flag, cudaStream_t s)
 // beta32 = beta (every padded element) and the flag of uniform_check, in one pass.
 void beta32_uniform(const Grid& g, const double* beta, float* beta32, int* flag, cudaStream_t s);
 
+// One thread writes the GPU's global timer (ns) into *t (device).
+void launch_stamp(unsigned long long* t, cudaStream_t s);
+
 // Kernel executions counted on the device, per source file (for the benchmark's launch count).
 unsigned long long launches_setup();
 unsigned long long launches_jcg();

@@ -28,6 +28,8 @@
 #include "tma.cuh"
 
 namespace ecmg {
+// Internal linkage on purpose: each translation unit that includes the body (the two-pass and
+// the single-pass kernels) compiles its own copy, and no device symbol crosses units.
 namespace {
 
 using namespace tma;

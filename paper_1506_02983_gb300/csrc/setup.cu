@@ -13,6 +13,13 @@ __device__ unsigned long long g_launches = 0;  // kernel executions of this file
     if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0) \
         atomicAdd(&g_launches, 1ull)
 
+// The GPU's global timer (ns) into *t: the time stamps of the per-level solve times.
+__global__ void k_stamp(unsigned long long* t)
+{
+    COUNT_LAUNCH();
+    *t = global_ns();
+}
+
 constexpr int TPB = 256;
 constexpr int TX = 32, TY = 8;  // node-parallel kernels: 32 x 8 nodes of a plane per block
 
@@ -260,6 +267,8 @@ void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* 
 {
     k_dirichlet_ext<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, gD, x, shell ? 1 : 0);
 }
+
+void launch_stamp(unsigned long long* t, cudaStream_t s) { k_stamp<<<1, 1, 0, s>>>(t); }
 
 unsigned long long launches_setup()
 {

@@ -52,14 +52,19 @@ class ecmg_options(C.Structure):
 class ecmg_stats(C.Structure):
     _fields_ = [("levels", C.c_int32), ("iters", C.c_int32 * 16), ("updates", C.c_int32 * 16),
                 ("rel_res", C.c_double * 16), ("rhs_norm", C.c_double * 16),
-                ("status", C.c_int32)]
+                ("status", C.c_int32), ("seconds", C.c_double * 16), ("setup_seconds", C.c_double)]
 
 
 _P, _I32, _D = C.c_void_p, C.c_int32, C.c_double
 _H = C.c_void_p
+# caller-supplied device allocator (ecmg_create_with_allocator)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 _SIGS = {
     "ecmg_default_options": (None, [C.POINTER(ecmg_options)]),
     "ecmg_create": (_I32, [C.POINTER(ecmg_problem), C.POINTER(ecmg_options), _P, C.POINTER(_H)]),
+    "ecmg_create_with_allocator": (_I32, [C.POINTER(ecmg_problem), C.POINTER(ecmg_options), _P, ALLOC_FN, FREE_FN,
+                                          _P, C.POINTER(_H)]),
     "ecmg_solve": (_I32, [_H, _P, C.POINTER(ecmg_stats)]),
     "ecmg_solve_from": (_I32, [_H, _I32, _P, C.POINTER(ecmg_stats)]),
     "ecmg_extrapolate": (_I32, [_H, _I32, _P]),
@@ -118,6 +123,25 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def torch_allocator():
+    """(alloc, free) callbacks for ecmg_create_with_allocator that take device memory from
+    PyTorch's caching allocator on the current device. Keep the returned pair alive as long as
+    the handle."""
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream) if stream else None)
+        except RuntimeError:
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
 def _stream():
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -136,7 +160,7 @@ class Solver:
     """
 
     def __init__(self, n0, levels, lo, hi, face_bc, robin_alpha, beta, f, g_D=None, g_R=None,
-                 f_mode=ECMG_F_NODAL, f_terms=0, gD_terms=0, beta_const=0.0, **options):
+                 f_mode=ECMG_F_NODAL, f_terms=0, gD_terms=0, beta_const=0.0, torch_memory=False, **options):
         p = ecmg_problem()
         p.n0[:] = [int(v) for v in n0]
         p.levels = int(levels)
@@ -156,7 +180,13 @@ class Solver:
         self.levels = int(levels)
         self.n0 = [int(v) for v in n0]
         h = _H()
-        check(ecmg_create(C.byref(p), C.byref(self.options), _stream(), C.byref(h)), "ecmg_create")
+        if torch_memory:
+            # the workspace comes from PyTorch's caching allocator (counted in its statistics)
+            self._allocator = torch_allocator()
+            check(ecmg_create_with_allocator(C.byref(p), C.byref(self.options), _stream(), *self._allocator, None,
+                                             C.byref(h)), "ecmg_create_with_allocator")
+        else:
+            check(ecmg_create(C.byref(p), C.byref(self.options), _stream(), C.byref(h)), "ecmg_create")
         self.handle = h
 
     def level_shape(self, level=-1):
@@ -333,7 +363,8 @@ def kernel_launches() -> int:
 def stats_dict(st: ecmg_stats) -> dict:
     L = st.levels
     return dict(levels=L, iters=list(st.iters[:L]), updates=list(st.updates[:L]),
-                rel_res=list(st.rel_res[:L]), rhs_norm=list(st.rhs_norm[:L]), status=st.status)
+                rel_res=list(st.rel_res[:L]), rhs_norm=list(st.rhs_norm[:L]), status=st.status,
+                seconds=list(st.seconds[:L]), setup_seconds=st.setup_seconds)
 
 
 def solver_from_problem(prob: dict, device="cuda", **options):

@@ -181,3 +181,26 @@ def test_problem_struct_layout_matches_header(tmp_path):
         assert int(got[st]) == ctypes.sizeof(cls), st
         for n in names:
             assert int(got["%s.%s" % (st, n)]) == getattr(cls, n).offset, (st, n)
+
+
+def test_create_with_allocator_validation_without_gpu(libpath):
+    """alloc and free come together; the problem is validated before any allocation."""
+    from paper_1506_02983_gb300 import ecmg
+    p = ecmg.ecmg_problem()
+    p.n0[:] = [2, 2, 2]
+    p.levels = 3
+    p.lo[:] = [0, 0, 0]
+    p.hi[:] = [1, 1, 1]
+    p.beta = 16
+    p.f = 16
+    o = ecmg.default_options()
+    h = ctypes.c_void_p()
+    calls = []
+    alloc = ecmg.ALLOC_FN(lambda n, s, c: calls.append(n) or None)
+    free = ecmg.FREE_FN(lambda ptr, n, s, c: calls.append(-n))
+    assert ecmg.ecmg_create_with_allocator(ctypes.byref(p), ctypes.byref(o), None, alloc, ecmg.FREE_FN(), None,
+                                           ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+    p.levels = 2  # invalid: at least 3 levels
+    assert ecmg.ecmg_create_with_allocator(ctypes.byref(p), ctypes.byref(o), None, alloc, free, None,
+                                           ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
+    assert calls == [] and not h.value

@@ -1,0 +1,73 @@
+"""C-ABI services around the solve, on the GPU: per-level device times in ecmg_stats, and the
+workspace taken from a caller-supplied allocator (PyTorch's caching allocator)."""
+import numpy as np
+import pytest
+
+from paper_1506_02983_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_02983_gb300 import build
+    build.build()
+    from paper_1506_02983_gb300 import ecmg
+    return ecmg
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_level_seconds_add_up_to_the_solve(E, precision, use_graph):
+    import torch
+    p = inputs.cos_cube(levels=5, n0=(4, 4, 4), rtol=1e-10)
+    s = E.solver_from_problem(p, precision=precision, use_graph=use_graph)
+    s.solve()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st, status = s.solve()
+    e1.record()
+    torch.cuda.synchronize()
+    assert status == 0
+    total = e0.elapsed_time(e1) * 1e-3
+    assert st["setup_seconds"] > 0 and all(t > 0 for t in st["seconds"]), st["seconds"]
+    inside = st["setup_seconds"] + sum(st["seconds"])
+    assert inside <= total * 1.02 + 1e-5, (inside, total)
+    if use_graph:
+        assert inside >= 0.5 * total, (inside, total)
+    # a solve from level 2 times levels 2.. only
+    st2 = s.solve_from(2)
+    assert st2["setup_seconds"] == 0 and st2["seconds"][:2] == [0.0, 0.0] and all(t > 0 for t in st2["seconds"][2:])
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_workspace_from_the_torch_caching_allocator(E, precision):
+    """Every device block of the handle comes from PyTorch's allocator (its statistics grow by at
+    least ecmg_workspace_bytes) and goes back at destroy; the solve is the same bit for bit."""
+    import ctypes
+    import torch
+    p = inputs.exp_cube(levels=4, rtol=1e-10)
+    ref = E.solver_from_problem(p, precision=precision)
+    st_ref, _ = ref.solve()
+    U_ref = ref.get(E.ECMG_VEC_U).cpu().numpy()
+    ref.close()
+    t = lambda a: torch.as_tensor(np.asarray(a), dtype=torch.float64).contiguous().cuda()
+    beta, f, gD = t(p["beta"]), t(p["f"]), t(p["gD"])
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    s = E.Solver(p["n0"], p["levels"], p["lo"], p["hi"], p["face_bc"], p["alpha"], beta, f, gD, None,
+                 rtol=1e-10, precision=precision, torch_memory=True)
+    grown = torch.cuda.memory_allocated() - before
+    nbytes = ctypes.c_uint64()
+    assert E.ecmg_workspace_bytes(ctypes.byref(s.problem), ctypes.byref(s.options), ctypes.byref(nbytes)) == 0
+    assert grown >= nbytes.value * 0.85, (grown, nbytes.value)  # the estimate rounds up
+    st, status = s.solve()
+    assert status == 0 and st["iters"] == st_ref["iters"]
+    assert np.array_equal(s.get(E.ECMG_VEC_U).cpu().numpy(), U_ref)
+    s.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
