@@ -64,6 +64,8 @@ def parse():
                     help="with --profile-kernel 0: the K1 tile shape ry,kz of the finest level (as autotuned in the bench)")
     ap.add_argument("--cg-form", default="two", choices=["two", "single"],
                     help="MIXED step of the headline solve: two-pass (K1 + K2) or single-pass (one kernel)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the two other paper-scale workloads (variable-beta box in FP64, jump case MIXED)")
     ap.add_argument("--no-compare-form", action="store_true",
                     help="skip timing the other MIXED step form beside the headline one")
     ap.add_argument("--eager", action="store_true",
@@ -241,6 +243,77 @@ def profile_kernel(args):
         print(json.dumps({"kernel": w, "workload": args.profile_workload, "n": nfin, "ms": ms, "algorithmic_bytes": nb,
                           "GBps": nb / ms / 1e6, "tiles": [ry, kz], "solve_status": status}))
     s.close()
+
+
+def bench_extra(args, world):
+    """The two other paper-scale single-GPU workloads, one solve each after a warm-up solve:
+    the variable-beta box (512 x 512 x 1024 elements, Robin on z = 0) in FP64 and the jump case
+    (1024 x 512 x 512, beta 1 | 100, singular u, Robin on x = 0) in MIXED, with the general
+    FP32 stencil kernel's own device timer for its roofline."""
+    import numpy as np
+    import torch
+    from paper_1506_02983_gb300 import ecmg, inputs
+    pk = peaks().get("hbm_gbs")
+    out = {}
+
+    def timed_solve(s, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            st, status = s.solve()
+        e1.record()
+        torch.cuda.synchronize()
+        assert status == 0, st
+        return e0.elapsed_time(e1) / steps, st
+
+    p = inputs.variable_box(levels=7, rtol=1e-9)
+    n = inputs.finest(p["n0"], p["levels"])
+    free = (n[0] - 1) * (n[1] - 1) * n[2]  # Dirichlet on five faces, Robin on z = 0
+    ue = torch.from_numpy(np.ascontiguousarray(p.pop("u_exact"))).cuda()
+    wl = ("box (0,1)x(0,1)x(0,2), 8x8x16 -> 512x512x1024 elements (7 levels), beta = 1 + 0.5 sin(2 pi x) "
+          "cos(2 pi y) sin(pi z), Dirichlet on five faces, Robin alpha = 1 on z = 0, rtol 1e-9")
+    for name, precision, steps in (("variable_box_fp64", ecmg.ECMG_FP64, 1), ("variable_box_mixed", ecmg.ECMG_MIXED, 2)):
+        s = ecmg.solver_from_problem(p, precision=precision, autotune=1 if precision == ecmg.ECMG_MIXED else 0)
+        u = torch.empty_like(ue)
+        s.solve(u)
+        ms, st = timed_solve(s, steps)
+        s.solve(u)
+        out[name] = {
+            "workload": wl + (", FP64" if precision == ecmg.ECMG_FP64 else ", MIXED"),
+            "ms_per_solve": ms, "value": free / (ms * 1e-3) / 1e9, "unit": "Gdof/s (finest free dofs / solve time)",
+            "finest_free_dofs": free, "iters": st["iters"], "level_seconds": st["seconds"],
+            "setup_seconds": st["setup_seconds"], "max_err": (u - ue).abs().max().item()}
+        s.close()
+        del u
+    del p, ue
+
+    p = inputs.jump_singular(levels=7, rtol=1e-8, device="cuda")
+    n = inputs.finest(p["n0"], p["levels"])
+    free = n[0] * (n[1] - 1) * (n[2] - 1)  # Robin on x = 0, Dirichlet elsewhere
+    s = ecmg.solver_from_problem(p, precision=ecmg.ECMG_MIXED, autotune=1)
+    s.solve()
+    s.stencil_timer(-1, reset=True)
+    ms, st = timed_solve(s, 2)
+    k1_total, k1_n = s.stencil_timer(-1, reset=True)
+    k1_ms_alone, k1_bytes = s.time_kernel(0, -1, reps=10)
+    k1_live = k1_total / max(k1_n, 1)
+    gbps = k1_bytes / k1_live / 1e6
+    out["jump_mixed"] = {
+        "workload": "box (0,2)x(0,1)x(0,1), 16x8x8 -> 1024x512x512 elements (7 levels), beta 1 for x < 1 and 100 "
+                    "for x > 1, u = r^1.5, Robin alpha = 1 on x = 0, Dirichlet elsewhere, rtol 1e-8, MIXED",
+        "ms_per_solve": ms, "value": free / (ms * 1e-3) / 1e9, "unit": "Gdof/s (finest free dofs / solve time)",
+        "finest_free_dofs": free, "iters": st["iters"], "updates": st["updates"], "level_seconds": st["seconds"],
+        "setup_seconds": st["setup_seconds"],
+        "stencil_roofline": {"kernel": "K1 general path (k_pq32_tma: variable beta, a Robin face), finest level",
+                             "bound": "hbm", "achieved": gbps, "peak": pk, "unit": "GB/s",
+                             "frac": gbps / pk if pk else None, "algorithmic_bytes_per_launch": k1_bytes,
+                             "launch_ms": k1_live, "launches_timed": k1_n, "launch_ms_alone_cuda_events": k1_ms_alone,
+                             "tiles": list(s.get_tiles(-1))}}
+    s.close()
+    del p
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_batched(args, steps, warmup):
@@ -473,6 +546,7 @@ def main():
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, args.batched_steps, 2)
+    extra = None if args.no_extra else bench_extra(args, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -539,6 +613,7 @@ def main():
                              "inputs": "dense beta, load functional and g_D arrays (ECMG_F_LOAD)"},
         "cpu_baseline": cpu,
         "batched": batched,
+        "paper_scale_workloads": extra,
     }
     if rank == 0:
         print(json.dumps(out))
