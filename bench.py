@@ -245,11 +245,11 @@ def profile_kernel(args):
     s.close()
 
 
-def bench_extra(args, world):
-    """The two other paper-scale single-GPU workloads, one solve each after a warm-up solve:
-    the variable-beta box (512 x 512 x 1024 elements, Robin on z = 0) in FP64 and the jump case
-    (1024 x 512 x 512, beta 1 | 100, singular u, Robin on x = 0) in MIXED, with the general
-    FP32 stencil kernel's own device timer for its roofline."""
+def bench_extra():
+    """The two other paper-scale single-GPU workloads, timed after a warm-up solve: the
+    variable-beta box (512 x 512 x 1024 elements, Robin on z = 0) in FP64 and in MIXED, and the
+    jump case (1024 x 512 x 512, beta 1 | 100, singular u, Robin on x = 0) in MIXED, with the
+    general FP32 stencil kernel's own device timer for its roofline."""
     import numpy as np
     import torch
     from paper_1506_02983_gb300 import ecmg, inputs
@@ -546,7 +546,7 @@ def main():
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, args.batched_steps, 2)
-    extra = None if args.no_extra else bench_extra(args, world)
+    extra = None if args.no_extra else bench_extra()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
