@@ -15,8 +15,12 @@
  * order Richardson-extrapolated solution (EXP_true, Sec. 4.2.1 and 4.3).
  *
  * Memory and ownership
- *   - Every pointer argument documented as "device" is a CUDA device pointer on the current
- *     device; "host" pointers are ordinary host memory. Inputs are read, never written.
+ *   - Every pointer argument documented as "device" is read or written by the library's
+ *     kernels: device memory of the current device, managed memory, or page-locked host memory
+ *     (cudaHostAlloc, cudaHostRegister; a GB300 reaches it over its coherent chip-to-chip link,
+ *     so a solve can take its inputs from, and write its solution to, pinned host buffers with
+ *     no separate copy). Any other pointer is refused with ECMG_ERR_INVALID_ARG before a kernel
+ *     touches it. "host" pointers are ordinary host memory. Inputs are read, never written.
  *   - The caller owns every array it passes. ecmg_create records the problem description and
  *     the input pointers; the input arrays must stay valid and unchanged until the last
  *     ecmg_solve on the handle has completed (ecmg_solve reads them on the device).

@@ -111,6 +111,58 @@ ecmg_status fail(ecmg_status s, const std::string& msg)
     return s;
 }
 
+// The library's kernels read and write caller arrays through the pointers they are given:
+// device memory of the current device, managed memory and page-locked host memory
+// (cudaHostAlloc / cudaHostRegister, which a GB300 reaches over its coherent chip-to-chip link)
+// qualify, and *dev receives the address the kernels use. Any other pointer (pageable host
+// memory, another device's memory, an invalid address) would fault the GPU, so it is refused.
+bool kernel_accessible(const void* p, const void** dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return false;
+    switch (a.type) {
+    case cudaMemoryTypeDevice:
+        if (a.device != cur) return false;
+        *dev = p;
+        return true;
+    case cudaMemoryTypeManaged:
+        *dev = p;
+        return true;
+    case cudaMemoryTypeHost:
+        if (!a.devicePointer) return false;
+        *dev = a.devicePointer;
+        return true;
+    default:
+        return false;
+    }
+}
+
+// The input arrays of a problem, each replaced by the address the kernels use; false if one of
+// them is not reachable by the kernels.
+bool resolve_inputs(ecmg_problem* p)
+{
+    for (const double** q : {&p->beta, &p->f, &p->g_D, &p->g_R}) {
+        if (!*q) continue;
+        const void* d = nullptr;
+        if (!kernel_accessible(*q, &d)) return false;
+        *q = static_cast<const double*>(d);
+    }
+    return true;
+}
+
+// An output (or input) array of a call, as the address the kernels use; null if not reachable.
+template <typename T>
+T* resolve_array(T* p)
+{
+    const void* d = nullptr;
+    return kernel_accessible(p, &d) ? static_cast<T*>(const_cast<void*>(d)) : nullptr;
+}
+
 bool op_robin(const Op& op)
 {
     for (int f = 0; f < 6; ++f)
@@ -488,6 +540,8 @@ void record_solve(Rec& R, int first)
 
 ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stats, bool retried = false)
 {
+    if (u_out && !(u_out = resolve_array(u_out)))
+        return fail(ECMG_ERR_INVALID_ARG, "u_out must be device memory of the current device or page-locked host memory");
     try {
         if (h->opt.use_graph) {
             if (!h->exec || h->graph_first != first) {
@@ -679,6 +733,15 @@ void record_batched(Rec& R)
 ecmg_status run_batched(ecmg_handle* h, double* const* u_out, ecmg_stats* stats)
 {
     Batch& B = *h->batch;
+    std::vector<double*> outs;
+    if (u_out) {
+        for (int p = 0; p < B.n; ++p) {
+            outs.push_back(u_out[p] ? resolve_array(u_out[p]) : nullptr);
+            if (u_out[p] && !outs.back())
+                return fail(ECMG_ERR_INVALID_ARG,
+                            "u_out entries must be device memory of the current device or page-locked host memory");
+        }
+    }
     try {
         if (h->opt.use_graph) {
             if (!h->exec) {
@@ -700,12 +763,11 @@ ecmg_status run_batched(ecmg_handle* h, double* const* u_out, ecmg_stats* stats)
             Rec R{h, false, 0};
             record_batched(R);
         }
-        if (u_out)
-            for (int p = 0; p < B.n; ++p)
-                if (u_out[p]) {
-                    const BItem& it = B.items[B.item(p, B.L[p] - 1)];
-                    unpack_nodal(it.g, it.U, u_out[p], h->user_stream);
-                }
+        for (int p = 0; p < (int)outs.size(); ++p)
+            if (outs[p]) {
+                const BItem& it = B.items[B.item(p, B.L[p] - 1)];
+                unpack_nodal(it.g, it.U, outs[p], h->user_stream);
+            }
         ck(cudaGetLastError());
         ck(cudaMemcpyAsync(B.host_states, B.states, sizeof(SolveState) * B.items.size(), cudaMemcpyDeviceToHost,
                            h->user_stream));
@@ -932,11 +994,14 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
     if ((alloc == nullptr) != (free_fn == nullptr)) return fail(ECMG_ERR_INVALID_ARG, "alloc and free go together");
     ecmg_status s = validate(prob, opt);
     if (s != ECMG_OK) return s;
+    ecmg_problem pr = *prob;
+    if (!resolve_inputs(&pr))
+        return fail(ECMG_ERR_INVALID_ARG, "inputs must be device memory of the current device or page-locked host memory");
     ecmg_handle* h = new ecmg_handle();
     h->alloc_fn = alloc;
     h->free_fn = free_fn;
     h->alloc_ctx = ctx;
-    h->prob = *prob;
+    h->prob = pr;
     h->opt = *opt;
     h->user_stream = (cudaStream_t)stream;
     h->L = prob->levels;
@@ -1038,6 +1103,11 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
         if (probs[p].f_mode == ECMG_F_SEPARABLE || probs[p].gD_terms > 0 || !probs[p].beta)
             return fail(ECMG_ERR_INVALID_ARG, "batched problems take dense beta, f and g_D");
     }
+    std::vector<ecmg_problem> resolved(probs, probs + n);
+    for (auto& q : resolved)
+        if (!resolve_inputs(&q))
+            return fail(ECMG_ERR_INVALID_ARG, "inputs must be device memory of the current device or page-locked host memory");
+    probs = resolved.data();
     ecmg_handle* h = new ecmg_handle();
     h->prob = probs[0];
     h->opt = *opt;
@@ -1179,6 +1249,8 @@ ecmg_status ecmg_extrapolate(ecmg_handle* h, int32_t level, double* u_tilde_out)
 ecmg_status ecmg_get_level(ecmg_handle* h, int32_t level, int32_t which, double* out)
 {
     if (!h || !out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    if (!(out = resolve_array(out)))
+        return fail(ECMG_ERR_INVALID_ARG, "out must be device memory of the current device or page-locked host memory");
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
     Level& v = h->lv[l];
@@ -1200,7 +1272,7 @@ ecmg_status ecmg_get_level(ecmg_handle* h, int32_t level, int32_t which, double*
             for (int j = 0; j < v.g.ny; ++j) {
                 cudaError_t e = cudaMemcpyAsync(out + (size_t)v.g.nx * (j + (size_t)v.g.ny * k),
                                                 src + v.g.off(0, j, k), (size_t)v.g.nx * 8,
-                                                cudaMemcpyDeviceToDevice, h->user_stream);
+                                                cudaMemcpyDefault, h->user_stream);
                 if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
             }
         return ECMG_OK;
@@ -1214,6 +1286,7 @@ ecmg_status ecmg_get_level(ecmg_handle* h, int32_t level, int32_t which, double*
 ecmg_status ecmg_set_level(ecmg_handle* h, int32_t level, const double* in)
 {
     if (!h || !in) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    if (!(in = resolve_array(in))) return fail(ECMG_ERR_INVALID_ARG, "arrays must be device memory of the current device or page-locked host memory");
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
     pack_nodal(h->lv[l].g, in, h->lv[l].U, h->user_stream);
@@ -1226,6 +1299,7 @@ ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision
                                 double* y)
 {
     if (!h || !x || !y) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    if (!(x = resolve_array(x)) || !(y = resolve_array(y))) return fail(ECMG_ERR_INVALID_ARG, "arrays must be device memory of the current device or page-locked host memory");
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
     Level& v = h->lv[l];
@@ -1278,6 +1352,7 @@ ecmg_status ecmg_error_norms(ecmg_handle* h, int32_t level, const double* a, con
                              double* max_abs, double* rms)
 {
     if (!h || !a || !max_abs || !rms) return fail(ECMG_ERR_INVALID_ARG, "null argument");
+    if (!(a = resolve_array(a)) || (b && !(b = resolve_array(b)))) return fail(ECMG_ERR_INVALID_ARG, "arrays must be device memory of the current device or page-locked host memory");
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
     Level& v = h->lv[l];

@@ -170,8 +170,9 @@ class Solver:
         p.robin_alpha[:] = [float(v) for v in robin_alpha]
         self._keep = (beta, f, g_D, g_R)
         for t in self._keep:
-            if t is not None and (not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64"):
-                raise ValueError("inputs must be contiguous float64 CUDA tensors")
+            if t is not None and (not (t.is_cuda or t.is_pinned()) or not t.is_contiguous()
+                                  or str(t.dtype) != "torch.float64"):
+                raise ValueError("inputs must be contiguous float64 CUDA or pinned host tensors")
         p.beta, p.f, p.g_D, p.g_R = (None if t is None else t.data_ptr() for t in self._keep)
         p.f_mode = int(f_mode)
         p.f_terms, p.gD_terms, p.beta_const = int(f_terms), int(gD_terms), float(beta_const)

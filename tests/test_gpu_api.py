@@ -71,3 +71,45 @@ def test_workspace_from_the_torch_caching_allocator(E, precision):
     s.close()
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == before
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pinned_host_inputs_and_output(E, precision):
+    """Inputs in page-locked host memory are read, and the solution written, by the kernels
+    directly; the solve is the same bit for bit as with device arrays. Pageable host memory is
+    refused before any kernel runs."""
+    import ctypes
+    import torch
+    p = inputs.exp_cube(levels=4, rtol=1e-10)
+    ref = E.solver_from_problem(p, precision=precision)
+    u_dev = torch.empty(ref.level_shape(), dtype=torch.float64, device="cuda")
+    st_ref, _ = ref.solve(u_dev)
+    ref.close()
+    pin = lambda a: torch.as_tensor(np.asarray(a), dtype=torch.float64).contiguous().pin_memory()
+    beta, f, gD = pin(p["beta"]), pin(p["f"]), pin(p["gD"])
+    s = E.Solver(p["n0"], p["levels"], p["lo"], p["hi"], p["face_bc"], p["alpha"], beta, f, gD, None,
+                 rtol=1e-10, precision=precision)
+    u_host = torch.empty(s.level_shape(), dtype=torch.float64).pin_memory()
+    st, status = s.solve(u_host)
+    assert status == 0 and st["iters"] == st_ref["iters"]
+    assert torch.equal(u_host, u_dev.cpu())
+    # pageable host memory: refused, no kernel launched, the handle stays usable
+    pageable = torch.empty(s.level_shape(), dtype=torch.float64)
+    st2 = E.ecmg_stats()
+    assert E.ecmg_solve(s.handle, ctypes.c_void_p(pageable.data_ptr()), ctypes.byref(st2)) == E.ECMG_ERR_INVALID_ARG
+    st3, status = s.solve(u_host)
+    assert status == 0 and torch.equal(u_host, u_dev.cpu())
+    s.close()
+    # and at create
+    bad = torch.as_tensor(np.asarray(p["f"]), dtype=torch.float64).contiguous()
+    pr = E.ecmg_problem()
+    pr.n0[:] = p["n0"]
+    pr.levels = p["levels"]
+    pr.lo[:] = p["lo"]
+    pr.hi[:] = p["hi"]
+    pr.face_bc[:] = p["face_bc"]
+    pr.robin_alpha[:] = p["alpha"]
+    pr.beta, pr.f, pr.g_D = beta.data_ptr(), bad.data_ptr(), gD.data_ptr()
+    o = E.default_options(rtol=1e-10)
+    h = ctypes.c_void_p()
+    assert E.ecmg_create(ctypes.byref(pr), ctypes.byref(o), None, ctypes.byref(h)) == E.ECMG_ERR_INVALID_ARG
