@@ -576,6 +576,7 @@ def main():
         "max_err_mixed": err_mixed, "max_err_fp64": err_fp64,
         "err_ratio_mixed_over_fp64": err_mixed / err_fp64,
         "iters_mixed": st_mixed["iters"], "updates_mixed": st_mixed["updates"], "iters_fp64": st64["iters"],
+        "level_seconds_mixed": st_mixed["seconds"], "setup_seconds_mixed": st_mixed["setup_seconds"],
         "rel_res_mixed": st_mixed["rel_res"], "gdofs_fp64": dofs / (ms_fp64 * 1e-3) / 1e9,
         "roofline": {"kernel": ("single-pass step (k_step32_cc on this one-beta all-Dirichlet level: residual "
                                 "update, search direction, 27-point operator and the dots in one pass)" if single else
