@@ -530,6 +530,7 @@ def main():
                  "value": free_dofs(nf) * world / (ms_alt * 1e-3) / 1e9, "unit": "Gdof/s",
                  "iters": st_alt["iters"], "updates": st_alt["updates"], "rel_res": st_alt["rel_res"],
                  "max_err": alt.norms(u_out, u_exact)[0], "tiles_finest": list(alt.get_tiles(-1)),
+                 "level_seconds": st_alt["seconds"], "setup_seconds": st_alt["setup_seconds"],
                  "finest_step_kernel_ms": alt_total / max(alt_n, 1),
                  "finest_step_kernels": alt_n / max(args.steps, 1)}
         alt.close()
