@@ -62,8 +62,9 @@ def parse():
                          "general kernels)")
     ap.add_argument("--profile-tiles", default=None,
                     help="with --profile-kernel 0: the K1 tile shape ry,kz of the finest level (as autotuned in the bench)")
-    ap.add_argument("--cg-form", default="two", choices=["two", "single"],
-                    help="MIXED step of the headline solve: two-pass (K1 + K2) or single-pass (one kernel)")
+    ap.add_argument("--cg-form", default="auto", choices=["auto", "two", "single"],
+                    help="MIXED step of the headline solve: the library default (single pass below 2^22 nodes, "
+                         "two passes above), two-pass (K1 + K2) or single-pass (one kernel) on every level")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the two other paper-scale workloads (variable-beta box in FP64, jump case MIXED)")
     ap.add_argument("--no-compare-form", action="store_true",
@@ -183,8 +184,10 @@ def arm_config(args, world):
             "l2": "inputs and finest vectors (>1 GB each) larger than L2",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes",
-            "mixed_step": ("single-pass (one kernel per JCG step, ECMG_CG_SINGLE_PASS)" if args.cg_form == "single"
-                           else "two-pass (K1 + K2 per JCG step)"),
+            "mixed_step": {"single": "single-pass (one kernel per JCG step, ECMG_CG_SINGLE_PASS)",
+                           "two": "two-pass (K1 + K2 per JCG step, ECMG_CG_TWO_PASS)",
+                           "auto": "ECMG_CG_AUTO (the default): single-pass below 2^22 nodes, two-pass above"}[
+                               args.cg_form],
             "tiles": "FP32 stencil tile shapes autotuned after the first solve (ecmg_autotune)"}
 
 
@@ -230,7 +233,8 @@ def profile_kernel(args):
         p = inputs.cos_cube(levels=args.levels, n0=(args.n0,) * 3, rtol=args.rtol)
         nfin = args.n0 << (args.levels - 1)
     s = ecmg.solver_from_problem(p, precision=ecmg.ECMG_MIXED, max_iters=args.max_iters,
-                                 cg_form=ecmg.ECMG_CG_SINGLE_PASS if args.cg_form == "single" else ecmg.ECMG_CG_TWO_PASS)
+                                 cg_form={"auto": ecmg.ECMG_CG_AUTO, "two": ecmg.ECMG_CG_TWO_PASS,
+                                          "single": ecmg.ECMG_CG_SINGLE_PASS}[args.cg_form])
     st, status = s.solve()
     if args.profile_tiles:
         ry, kz = (int(v) for v in args.profile_tiles.split(","))
@@ -400,13 +404,19 @@ def main():
     del p["beta"], p["f"], p["gD"]
 
     single = args.cg_form == "single"
-    form = {True: ecmg.ECMG_CG_SINGLE_PASS, False: ecmg.ECMG_CG_TWO_PASS}
+    form = {"auto": ecmg.ECMG_CG_AUTO, "two": ecmg.ECMG_CG_TWO_PASS, "single": ecmg.ECMG_CG_SINGLE_PASS}
+    other_form = "two" if args.cg_form != "two" else "auto"
 
-    def make(precision, single_pass=single):
+    def sp_level(l):
+        """Whether level l runs the single-pass step in the headline form."""
+        n = (n0 << l) + 1
+        return l >= 2 and (single or (args.cg_form == "auto" and n ** 3 < ecmg.ECMG_AUTO_SINGLE_PASS_NODES))
+
+    def make(precision, cg_form=args.cg_form):
         return ecmg.Solver(p["n0"], L, p["lo"], p["hi"], p["face_bc"], p["alpha"], d["beta"], d["f"],
                            d["gD"], None, f_mode=ecmg.ECMG_F_LOAD, rtol=args.rtol, precision=precision,
                            max_iters=args.max_iters, use_graph=0 if args.eager else 1, inner_rtol=args.inner_rtol,
-                           cg_form=form[single_pass] if precision == ecmg.ECMG_MIXED else ecmg.ECMG_CG_TWO_PASS)
+                           cg_form=form[cg_form] if precision == ecmg.ECMG_MIXED else ecmg.ECMG_CG_TWO_PASS)
 
     def barrier():
         torch.cuda.synchronize()
@@ -516,7 +526,7 @@ def main():
     # the other MIXED step form on the same problem, for comparison (same warm-up and timing)
     other = None
     if not args.no_compare_form:
-        alt = make(ecmg.ECMG_MIXED, single_pass=not single)
+        alt = make(ecmg.ECMG_MIXED, cg_form=other_form)
         st_alt, status = alt.solve(u_out)
         assert status == 0, st_alt
         alt.autotune(3)
@@ -526,7 +536,7 @@ def main():
         ms_alt = timed(lambda: alt.solve(u_out), args.steps)
         alt_total, alt_n = alt.stencil_timer(-1, reset=True)
         st_alt, _ = alt.solve(u_out)
-        other = {"mixed_step": "two-pass" if single else "single-pass", "ms_per_step": ms_alt,
+        other = {"mixed_step": {"two": "two-pass", "auto": "auto"}[other_form], "ms_per_step": ms_alt,
                  "value": free_dofs(nf) * world / (ms_alt * 1e-3) / 1e9, "unit": "Gdof/s",
                  "iters": st_alt["iters"], "updates": st_alt["updates"], "rel_res": st_alt["rel_res"],
                  "max_err": alt.norms(u_out, u_exact)[0], "tiles_finest": list(alt.get_tiles(-1)),
@@ -567,7 +577,9 @@ def main():
         except ValueError:
             pass
     k1_gbps = k1_bytes / k1_live_ms / 1e6
-    bpni = 32.0 if single else 36.0
+    # bytes per node-iteration of the step each level runs: 32 single-pass, 36 two-pass
+    node_bytes = sum(free_dofs(n0 << l) * st_mixed["iters"][l] * (32.0 if sp_level(l) else 36.0) for l in range(L))
+    bpni = node_bytes / max(node_its, 1)
     out = {
         "metric": METRIC, "value": value, "unit": "Gdof/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
@@ -595,7 +607,7 @@ def main():
         # the two ways of counting dofs: finest free dofs per solve (value), and free dofs times
         # JCG iterations summed over the levels; the byte model charges each node-iteration the
         # bytes the step moves on a constant-coefficient level: 36 for K1 and K2 (24 + 12), 32
-        # for the single-pass kernel
+        # for the single-pass kernel (bytes_per_node_iteration is their iteration-weighted mean)
         "node_iterations_per_solve": node_its,
         "gdofs_node_iterations": node_its * world / (ms_mixed * 1e-3) / 1e9,
         "byte_model": {"bytes_per_node_iteration": bpni, "bytes_per_solve": bpni * node_its,

@@ -83,7 +83,12 @@ enum { ECMG_SCHED_TOLERANCE = 0, ECMG_SCHED_FIXED = 1 };
  * are obtained from the dots of the same pass by expanding (r - alpha q).D^-1(r - alpha q) and
  * (r - alpha q).(r - alpha q). Equal to TWO_PASS in exact arithmetic; the FP64 residual
  * replacements bound the difference in floating point. Needs two more FP32 vectors per level. */
-enum { ECMG_CG_TWO_PASS = 0, ECMG_CG_SINGLE_PASS = 1 };
+enum { ECMG_CG_TWO_PASS = 0, ECMG_CG_SINGLE_PASS = 1, ECMG_CG_AUTO = 2 };
+/* ECMG_CG_AUTO: SINGLE_PASS on the levels of fewer than ECMG_AUTO_SINGLE_PASS_NODES nodes, where
+ * a step's time is mostly launch and reduction latency and one kernel per step saves a launch,
+ * TWO_PASS on the larger ones, where both forms stream at their bandwidth and take the same
+ * time per step. */
+#define ECMG_AUTO_SINGLE_PASS_NODES (1 << 22)
 /* ecmg_get_level: which vector */
 enum { ECMG_VEC_U = 0, ECMG_VEC_W = 1, ECMG_VEC_UTILDE = 2, ECMG_VEC_B = 3, ECMG_VEC_BETA = 4 };
 
@@ -138,9 +143,9 @@ typedef struct {
                                there)                                        [TOLERANCE]   */
     int32_t sched_mL;       /* FIXED: m_L, the steps on the finest level, >= 1  [4]         */
     double sched_beta;      /* FIXED: beta of eq. (ee), 1..64                   [4.0]       */
-    int32_t cg_form;        /* MIXED: ECMG_CG_TWO_PASS or ECMG_CG_SINGLE_PASS on the
-                               single-problem path (ecmg_create_batched rejects
-                               SINGLE_PASS)                                  [TWO_PASS]    */
+    int32_t cg_form;        /* MIXED: ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS or ECMG_CG_AUTO on
+                               the single-problem path (batched handles run TWO_PASS for
+                               AUTO and reject SINGLE_PASS)                  [AUTO]        */
 } ecmg_options;
 
 /* Per-solve statistics, one entry per level (coarsest first). */

@@ -231,7 +231,7 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
         return fail(ECMG_ERR_INVALID_ARG, "bad preconditioner");
     if (o->schedule != ECMG_SCHED_TOLERANCE && o->schedule != ECMG_SCHED_FIXED)
         return fail(ECMG_ERR_INVALID_ARG, "bad schedule");
-    if (o->cg_form != ECMG_CG_TWO_PASS && o->cg_form != ECMG_CG_SINGLE_PASS)
+    if (o->cg_form != ECMG_CG_TWO_PASS && o->cg_form != ECMG_CG_SINGLE_PASS && o->cg_form != ECMG_CG_AUTO)
         return fail(ECMG_ERR_INVALID_ARG, "bad cg_form");
     if (o->schedule == ECMG_SCHED_FIXED) {
         if (o->sched_mL < 1 || !(o->sched_beta >= 1.0 && o->sched_beta <= 64.0))
@@ -255,7 +255,17 @@ uint64_t level_bytes(const Grid& g, bool mixed, bool single_pass)
 // single-pass step on the general path); rounded up to 8.
 int partials_per_block(const ecmg_options& o)
 {
-    return (o.precision == ECMG_MIXED && o.cg_form == ECMG_CG_SINGLE_PASS) ? 8 : 3;
+    return (o.precision == ECMG_MIXED && o.cg_form != ECMG_CG_TWO_PASS) ? 8 : 3;
+}
+
+// Whether MIXED level l (>= 2) runs the single-pass step: always, never, or (AUTO) on levels
+// of fewer than ECMG_AUTO_SINGLE_PASS_NODES nodes.
+bool single_pass_level(const ecmg_options& o, const Grid& g, int l)
+{
+    if (o.precision != ECMG_MIXED || l < 2) return false;
+    if (o.cg_form == ECMG_CG_SINGLE_PASS) return true;
+    if (o.cg_form != ECMG_CG_AUTO) return false;
+    return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1) < (int64_t)ECMG_AUTO_SINGLE_PASS_NODES;
 }
 
 template <typename T>
@@ -957,7 +967,7 @@ void ecmg_default_options(ecmg_options* o)
     o->schedule = ECMG_SCHED_TOLERANCE;
     o->sched_mL = 4;
     o->sched_beta = 4.0;
-    o->cg_form = ECMG_CG_TWO_PASS;
+    o->cg_form = ECMG_CG_AUTO;
 }
 
 ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, uint64_t* bytes)
@@ -969,7 +979,7 @@ ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, u
     int maxb = 0;
     for (int l = 0; l < p->levels; ++l) {
         Grid g = make_grid(*p, l);
-        b += level_bytes(g, o->precision == ECMG_MIXED, o->cg_form == ECMG_CG_SINGLE_PASS && l >= 2);
+        b += level_bytes(g, o->precision == ECMG_MIXED, single_pass_level(*o, g, l));
         if (p->f_mode == ECMG_F_SEPARABLE) b += 8ull * (uint64_t)sep_factor_len(g, p->f_terms);
         if (p->gD_terms > 0 && l < p->levels - 1) b += 8ull * (uint64_t)sep_factor_len(g, p->gD_terms);
         maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
@@ -1044,7 +1054,7 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
                 if (!make_plane_maps(&v.maps, v.r32, v.pA32, v.pB32, v.dinv32, v.beta32, v.e32, v.g) ||
                     !make_res_maps(&v.rmaps, v.U, v.r, v.g))
                     throw CudaFail{cudaErrorNotSupported};
-                if (opt->cg_form == ECMG_CG_SINGLE_PASS && l >= 2) {
+                if (single_pass_level(*opt, v.g, l)) {
                     v.r32B = dalloc<float>(h, n);
                     v.q32B = dalloc<float>(h, n);
                     if (!make_plane_maps_sp(&v.maps, v.r32B, v.q32, v.q32B, v.g)) throw CudaFail{cudaErrorNotSupported};
@@ -1096,7 +1106,8 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
     *out = nullptr;
     if (n < 1 || n > BATCH_MAX) return fail(ECMG_ERR_INVALID_ARG, "batch size must be 1..128");
     if (opt->precision != ECMG_MIXED) return fail(ECMG_ERR_INVALID_ARG, "batched solves run in MIXED precision");
-    if (opt->cg_form != ECMG_CG_TWO_PASS) return fail(ECMG_ERR_INVALID_ARG, "batched solves run the two-pass step");
+    if (opt->cg_form == ECMG_CG_SINGLE_PASS)
+        return fail(ECMG_ERR_INVALID_ARG, "batched solves run the two-pass step");
     for (int p = 0; p < n; ++p) {
         ecmg_status s = validate(probs + p, opt);
         if (s != ECMG_OK) return s;

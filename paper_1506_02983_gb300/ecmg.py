@@ -28,8 +28,9 @@ ECMG_EXP_SERENDIPITY20, ECMG_EXP_LAGRANGE27 = 0, 1
 ECMG_VEC_U, ECMG_VEC_W, ECMG_VEC_UTILDE, ECMG_VEC_B, ECMG_VEC_BETA = 0, 1, 2, 3, 4
 ECMG_PREC_JACOBI, ECMG_PREC_NONE = 0, 1
 ECMG_SCHED_TOLERANCE, ECMG_SCHED_FIXED = 0, 1
-ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS = 0, 1
+ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS, ECMG_CG_AUTO = 0, 1, 2
 ECMG_NOALLOC_MAX_ELEMS = 536870912  # include/ecmg.h
+ECMG_AUTO_SINGLE_PASS_NODES = 1 << 22  # include/ecmg.h
 
 
 class ecmg_problem(C.Structure):

@@ -104,7 +104,7 @@ def test_solver_variant_options_validation_without_gpu(libpath):
                 dict(schedule=1, sched_mL=2000000, sched_beta=64.0)):
         o = ecmg.default_options(**bad)
         assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG, bad
-    o = ecmg.default_options(cg_form=2)
+    o = ecmg.default_options(cg_form=3)
     assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
     # the batched entry point runs the two-pass step only
     o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=ecmg.ECMG_CG_SINGLE_PASS)
@@ -113,7 +113,7 @@ def test_solver_variant_options_validation_without_gpu(libpath):
     o = ecmg.default_options()
     assert o.preconditioner == ecmg.ECMG_PREC_JACOBI and o.schedule == ecmg.ECMG_SCHED_TOLERANCE
     assert o.sched_mL == 4 and o.sched_beta == 4.0 and o.inner_rtol == 1e-3
-    assert o.cg_form == ecmg.ECMG_CG_TWO_PASS
+    assert o.cg_form == ecmg.ECMG_CG_AUTO
 
 
 def test_compact_input_validation_without_gpu(libpath):
@@ -204,3 +204,21 @@ def test_create_with_allocator_validation_without_gpu(libpath):
     assert ecmg.ecmg_create_with_allocator(ctypes.byref(p), ctypes.byref(o), None, alloc, free, None,
                                            ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
     assert calls == [] and not h.value
+
+
+def test_binding_constants_match_the_header():
+    """Every enum value and #define constant of include/ecmg.h that the binding names has the
+    header's value."""
+    import re
+    from paper_1506_02983_gb300 import ecmg
+    text = open(os.path.join(ROOT, "include", "ecmg.h")).read()
+    consts = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", text):
+        for name, val in re.findall(r"(ECMG_\w+)\s*=\s*(\d+)", body):
+            consts[name] = int(val)
+    for name, expr in re.findall(r"#define\s+(ECMG_\w+)\s+\(?([0-9 <<]+)\)?", text):
+        consts[name] = eval(expr)
+    named = {k: v for k, v in consts.items() if hasattr(ecmg, k)}
+    assert len(named) >= 20, sorted(named)
+    for k, v in named.items():
+        assert getattr(ecmg, k) == v, (k, getattr(ecmg, k), v)

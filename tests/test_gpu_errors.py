@@ -31,7 +31,7 @@ def _rel(a, b):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_iteration_cap_reports_no_convergence(E, precision):
     p = inputs.exp_cube(levels=4, rtol=1e-12)
-    s = E.solver_from_problem(p, precision=precision, max_iters=2)
+    s = E.solver_from_problem(p, precision=precision, max_iters=2, cg_form=0)
     st, status = s.solve(raise_on_error=False)
     assert status == E.ECMG_ERR_NO_CONVERGENCE, st
     assert st["status"] == E.ECMG_ERR_NO_CONVERGENCE
@@ -53,13 +53,13 @@ def test_non_finite_load_reports_breakdown_and_the_handle_recovers(E, precision)
     good = f.clone()
     f[10, 11, 12] = float("nan")
     s = E.Solver(p["n0"], p["levels"], p["lo"], p["hi"], p["face_bc"], p["alpha"], beta, f, gD, None,
-                 rtol=1e-10, precision=precision)
+                 rtol=1e-10, precision=precision, cg_form=0)
     st, status = s.solve(raise_on_error=False)
     assert status == E.ECMG_ERR_BREAKDOWN, st
     f.copy_(good)
     st, status = s.solve(raise_on_error=False)
     assert status == E.ECMG_OK, st
-    fresh = E.solver_from_problem(p, precision=precision)
+    fresh = E.solver_from_problem(p, precision=precision, cg_form=0)
     st2, _ = fresh.solve()
     assert st["iters"] == st2["iters"]
     assert np.array_equal(_np(s.get(E.ECMG_VEC_U, -1)), _np(fresh.get(E.ECMG_VEC_U, -1)))

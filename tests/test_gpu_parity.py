@@ -152,10 +152,11 @@ def test_fp64_solve_matches_oracle(E, oracle_mod, name, variant):
 
 @pytest.mark.parametrize("name", ["exp_cube", "cube_elements_ragged", "random_cube_dirichlet", "random_cube_neumann",
                                   "problem1_load", "random_mixed_bc_0"])
-def test_mixed_solve_reaches_tolerance_and_fp64_accuracy(E, oracle_mod, name):
+@pytest.mark.parametrize("cg_form", [0, 2])  # two-pass step, and the default (single pass on these small levels)
+def test_mixed_solve_reaches_tolerance_and_fp64_accuracy(E, oracle_mod, name, cg_form):
     p = PROBLEMS[name]()
     lv, ost = oracle_mod.ecmg(p, p["rtol"])
-    s = E.solver_from_problem(p, precision=1)
+    s = E.solver_from_problem(p, precision=1, cg_form=cg_form)
     gst, status = s.solve()
     assert status == 0, gst
     L = p["levels"]
@@ -180,12 +181,13 @@ def test_mixed_solve_reaches_tolerance_and_fp64_accuracy(E, oracle_mod, name):
     s.close()
 
 
-def test_graph_and_eager_paths_agree_bitwise(E):
+@pytest.mark.parametrize("cg_form", [0, 2])
+def test_graph_and_eager_paths_agree_bitwise(E, cg_form):
     p = PROBLEMS["random_mixed_bc_0"]()
     outs = []
     for use_graph in (1, 0):
         for precision in (0, 1):
-            s = E.solver_from_problem(p, precision=precision, use_graph=use_graph)
+            s = E.solver_from_problem(p, precision=precision, use_graph=use_graph, cg_form=cg_form)
             st, status = s.solve()
             assert status == 0
             outs.append((precision, _np(s.get(E.ECMG_VEC_U)), st["iters"]))
@@ -218,13 +220,14 @@ TILE_PROBLEMS = {
 
 
 @pytest.mark.parametrize("name", sorted(TILE_PROBLEMS))
-def test_mixed_tile_shapes_agree(E, oracle_mod, name):
+@pytest.mark.parametrize("cg_form", [0, 2])
+def test_mixed_tile_shapes_agree(E, oracle_mod, name, cg_form):
     """Every FP32 stencil tile shape gives the same mixed solve (up to the order of the p.q
     partial sums), within the mixed bar of the oracle."""
     p = TILE_PROBLEMS[name]()
     L = p["levels"]
     lv, ost = oracle_mod.ecmg(p, p["rtol"])
-    s = E.solver_from_problem(p, precision=1)
+    s = E.solver_from_problem(p, precision=1, cg_form=cg_form)
     ref, status = s.solve()
     assert status == 0, ref
     U_ref = _np(s.get(E.ECMG_VEC_U))
@@ -481,7 +484,8 @@ def test_k1_operator_matches_csr(E, oracle_mod, name, tiles):
     s.close()
 
 
-def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_mod):
+@pytest.mark.parametrize("cg_form", [0, 2])
+def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_mod, cg_form):
     """A MIXED graph recorded while beta was uniform runs the constant-coefficient stencil
     kernel; after the caller rewrites beta in place with a variable field, the next solve must
     notice (the kernel checks the level flag), record again with the general kernel and give
@@ -493,7 +497,7 @@ def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_
     f = torch.tensor(np.asarray(p["f"]), device="cuda")
     gD = torch.tensor(np.asarray(p["gD"]), device="cuda")
     s = E.Solver(p["n0"], p["levels"], p["lo"], p["hi"], p["face_bc"], p["alpha"], beta, f, gD, None,
-                 rtol=1e-10, precision=1)
+                 rtol=1e-10, precision=1, cg_form=cg_form)
     st1, status = s.solve()
     assert status == 0, st1
     beta.copy_(torch.tensor(np.asarray(q["beta"]), device="cuda"))
@@ -501,7 +505,7 @@ def test_beta_change_under_a_recorded_graph_switches_the_stencil_path(E, oracle_
     assert status == 0, st2
     U2 = _np(s.get(E.ECMG_VEC_U, -1))
     d = dict(p, beta=np.asarray(q["beta"]))
-    fresh = E.solver_from_problem(d, precision=1)
+    fresh = E.solver_from_problem(d, precision=1, cg_form=cg_form)
     st3, status = fresh.solve()
     assert status == 0
     assert st2["iters"] == st3["iters"], (st2["iters"], st3["iters"])
@@ -560,7 +564,8 @@ def test_random_problems_match_oracle(E, oracle_mod, seed, precision):
     p = _random_case(seed)
     lv, ost = oracle_mod.ecmg(p, p["rtol"])
     assert ost["status"] == 0
-    s = E.solver_from_problem(p, precision=precision)
+    # MIXED: the two-pass step here (the single-pass sweep is in test_gpu_single_pass.py)
+    s = E.solver_from_problem(p, precision=precision, cg_form=0)
     st, status = s.solve()
     assert status == 0, (p["n0"], p["levels"], p["face_bc"], st)
     for l in range(2, p["levels"]):

@@ -41,7 +41,7 @@ def test_single_pass_matches_oracle(E, oracle_mod, name):
     s = E.solver_from_problem(p, precision=1, cg_form=E.ECMG_CG_SINGLE_PASS)
     st, status = s.solve()
     assert status == 0, st
-    t = E.solver_from_problem(p, precision=1)
+    t = E.solver_from_problem(p, precision=1, cg_form=E.ECMG_CG_TWO_PASS)
     two, status = t.solve()
     assert status == 0
     _check(E, oracle_mod, p, s, st, two)
@@ -101,7 +101,7 @@ def test_single_pass_plain_cg_and_fixed_schedule(E, oracle_mod, precond):
     f = E.solver_from_problem(p, precision=1, cg_form=E.ECMG_CG_SINGLE_PASS, schedule=E.ECMG_SCHED_FIXED,
                               sched_mL=3, sched_beta=2.0, preconditioner=0 if precond else 1)
     t = E.solver_from_problem(p, precision=1, schedule=E.ECMG_SCHED_FIXED, sched_mL=3, sched_beta=2.0,
-                              preconditioner=0 if precond else 1)
+                              preconditioner=0 if precond else 1, cg_form=E.ECMG_CG_TWO_PASS)
     sf, status = f.solve()
     assert status == 0
     tf, _ = t.solve()
@@ -180,8 +180,36 @@ def test_single_pass_kernel_timer_and_bytes(E):
     ms1, nb1 = s.time_kernel(0, level=-1, reps=3)
     assert ms > 0 and nb == pytest.approx(nb1 * 32 / 24)  # 8 words per node against K1's 6
     s.close()
-    t = E.solver_from_problem(p, precision=1)
+    t = E.solver_from_problem(p, precision=1, cg_form=E.ECMG_CG_TWO_PASS)
     t.solve()
     with pytest.raises(E.EcmgError):
         t.time_kernel(11, level=-1, reps=1)
+    t.close()
+
+
+def test_auto_form_picks_single_pass_on_small_levels(E, oracle_mod):
+    """ECMG_CG_AUTO (the default): the single-pass step on levels of fewer than 2^22 nodes, the
+    two-pass step above; the solve meets the residual test and equals a two-pass solve's error."""
+    p = inputs.cos_cube(levels=6, n0=(8, 8, 8), rtol=1e-10)  # 256^3 finest: 16.8 M nodes
+    ue = np.asarray(p["u_exact"])
+    s = E.solver_from_problem(p, precision=1)
+    assert s.options.cg_form == E.ECMG_CG_AUTO
+    st, status = s.solve()
+    assert status == 0, st
+    for l in range(2, p["levels"]):
+        assert st["rel_res"][l] <= p["rtol"] * 1.0001, (l, st["rel_res"])
+    for l in range(2, 5):  # 32^3 .. 128^3: single-pass buffers exist
+        ms, nb = s.time_kernel(11, level=l, reps=1)
+        assert ms > 0
+    with pytest.raises(E.EcmgError):  # 256^3: two-pass
+        s.time_kernel(11, level=5, reps=1)
+    t = E.solver_from_problem(p, precision=1, cg_form=E.ECMG_CG_TWO_PASS)
+    st2, status = t.solve()
+    assert status == 0
+    e_auto = np.abs(_np(s.get(E.ECMG_VEC_U)) - ue).max()
+    e_two = np.abs(_np(t.get(E.ECMG_VEC_U)) - ue).max()
+    assert e_auto == pytest.approx(e_two, rel=1e-6)
+    for l in range(2, p["levels"]):
+        assert abs(st["iters"][l] - st2["iters"][l]) <= max(2, st2["iters"][l] // 10), (st["iters"], st2["iters"])
+    s.close()
     t.close()
