@@ -222,3 +222,36 @@ def test_binding_constants_match_the_header():
     assert len(named) >= 20, sorted(named)
     for k, v in named.items():
         assert getattr(ecmg, k) == v, (k, getattr(ecmg, k), v)
+
+
+def test_workspace_of_the_step_forms_without_gpu(libpath):
+    """Host logic of the MIXED step form: the single-pass form adds a second FP32 r and q on
+    every level >= 2, ECMG_CG_AUTO only on the levels of fewer than 2^22 nodes, and both widen
+    the per-block partials from 3 to 8 doubles (ecmg_workspace_bytes, no CUDA call)."""
+    from paper_1506_02983_gb300 import ecmg
+    p = ecmg.ecmg_problem()
+    p.n0[:] = [8, 8, 8]
+    p.levels = 7
+    p.lo[:] = [0, 0, 0]
+    p.hi[:] = [1, 1, 1]
+    p.beta = 16
+    p.f = 16
+
+    def ws(form):
+        o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=form)
+        n = ctypes.c_uint64()
+        assert ecmg.ecmg_workspace_bytes(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == 0
+        return n.value
+
+    def total(l):  # padded nodes of level l (ghost layers and the 16-byte left pad)
+        nx = 8 << l
+        pitch = (nx + 1 + 4 + 2 + 7) // 8 * 8
+        return pitch * (nx + 3) * (nx + 3)
+
+    two, single, auto = ws(ecmg.ECMG_CG_TWO_PASS), ws(ecmg.ECMG_CG_SINGLE_PASS), ws(ecmg.ECMG_CG_AUTO)
+    small = [l for l in range(2, 7) if ((8 << l) + 1) ** 3 < ecmg.ECMG_AUTO_SINGLE_PASS_NODES]
+    assert small == [2, 3, 4]
+    # the partials (3 -> 8 doubles per block) are the same for both forms that use them
+    assert single - auto == sum(8 * total(l) for l in range(2, 7) if l not in small)
+    extra = single - two - sum(8 * total(l) for l in range(2, 7))
+    assert extra > 0 and extra % (5 * 8) == 0  # 5 more doubles per block of the largest grid
