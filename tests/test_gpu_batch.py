@@ -71,7 +71,8 @@ def test_batched_solve_matches_oracle(E, oracle_mod):
     assert status == 0, stats
     for i, p in enumerate(probs):
         lv, ost = oracle_mod.ecmg(p, RTOL)
-        single = E.solver_from_problem(p, precision=1, rtol=RTOL)
+        # the batched handle runs the two-pass step, so the single-problem one does here too
+        single = E.solver_from_problem(p, precision=1, rtol=RTOL, cg_form=E.ECMG_CG_TWO_PASS)
         sst, sstatus = single.solve()
         assert sstatus == 0
         single.close()
