@@ -151,9 +151,12 @@ def _stream():
 class Solver:
     """One ECMG_jcg problem on the current CUDA device (torch tensors in, torch tensors out).
 
-    beta: finest elements (nz, ny, nx) float64 CUDA tensor; f, g_D, g_R: finest nodes
-    (nz+1, ny+1, nx+1) float64 CUDA tensors (g_D, g_R optional). The tensors must outlive the
-    solver and stay unchanged while a solve reads them.
+    beta: finest elements (nz, ny, nx) float64 tensor; f, g_D, g_R: finest nodes
+    (nz+1, ny+1, nx+1) float64 tensors (g_D, g_R optional); each on the current CUDA device or
+    in pinned host memory (the kernels then read it over the host link). The tensors must
+    outlive the solver and stay unchanged while a solve reads them. Options are the fields of
+    ecmg_options as keywords; torch_memory=True takes the workspace from PyTorch's caching
+    allocator.
 
     Compact inputs: beta=None with beta_const > 0 (one beta everywhere); f_mode=ECMG_F_SEPARABLE
     with f the Gauss samples of f_terms separable terms (``inputs.separable_samples``); g_D the
