@@ -255,3 +255,17 @@ def test_workspace_of_the_step_forms_without_gpu(libpath):
     assert single - auto == sum(8 * total(l) for l in range(2, 7) if l not in small)
     extra = single - two - sum(8 * total(l) for l in range(2, 7))
     assert extra > 0 and extra % (5 * 8) == 0  # 5 more doubles per block of the largest grid
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """The binding has no fallback: imported from a tree where libecmg.so was never built, it
+    raises ImportError instead of running anything on the CPU."""
+    import importlib.util
+    import shutil
+    pkg = tmp_path / "pkg"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_1506_02983_gb300", "ecmg.py"), pkg / "ecmg.py")
+    spec = importlib.util.spec_from_file_location("ecmg_unbuilt", pkg / "ecmg.py")
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError, match="no fallback"):
+        spec.loader.exec_module(mod)
