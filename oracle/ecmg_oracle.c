@@ -836,15 +836,21 @@ void or_exp_true(const int32_t n[3], const double* U1, const double* U0, double*
 /* Alg. 4: the whole ECMG_jcg method                                                    */
 /* ----------------------------------------------------------------------------------- */
 
+/* The max norm and the "L2" norm of the tables of Sec. 5: max |a - b| and the root mean
+ * square sqrt(sum (a - b)^2 / N) over all N nodes. A NaN difference makes the max NaN (an
+ * error norm must not report a finite value for a vector that holds a NaN); the sum carries
+ * it into the RMS by itself. */
 void or_norms(int64_t N, const double* a, const double* b, double* max_abs, double* rms)
 {
     double m = 0.0, s = 0.0;
+    int nan_seen = 0;
     for (int64_t i = 0; i < N; ++i) {
         double d = a[i] - (b ? b[i] : 0.0);
-        if (fabs(d) > m) m = fabs(d);
+        if (isnan(d)) nan_seen = 1;
+        else if (fabs(d) > m) m = fabs(d);
         s += d * d;
     }
-    *max_abs = m;
+    *max_abs = nan_seen ? NAN : m;
     *rms = sqrt(s / (double)N);
 }
 
