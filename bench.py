@@ -143,11 +143,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(loaded)}
 
 
+FALLBACK_HBM_GBS = 6800.0  # one earlier copy measurement on a GB300, used when no measured file exists
+
+
 def peaks():
+    """The measured peaks (MEASURED_PEAKS.json), or the fallback HBM copy rate, with its source."""
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        if d.get("hbm_gbs"):
+            d["source"] = "MEASURED_PEAKS.json hbm_gbs (copy; of measured)"
+            return d
     except (OSError, ValueError):
-        return {}
+        pass
+    return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback 6800 GB/s (no MEASURED_PEAKS.json; of fallback)"}
 
 
 def free_dofs(n):
@@ -209,10 +217,19 @@ def run_reference(args):
     dt = (time.perf_counter() - t0) / steps
     nf = args.n0 << (levels - 1)
     v = free_dofs(nf) / dt / 1e9
+    # the same workload as the GPU arm, as a bounded sample: what this arm runs is stated in
+    # config (the FP64 oracle on one core, the hierarchy cut at nf^3)
+    cfg = arm_config(args, world)
+    for k in ("loop_control", "mixed_step", "tiles", "l2"):
+        cfg.pop(k, None)
+    cfg.update(precision="FP64 (the plain C oracle: CSR assembly, banded Cholesky, JCG, EXP_finite, EXP_true)",
+               parallelism="one host core",
+               sample="each step solves the same problem cut to %d^3 (%d levels) instead of %d^3" % (
+                   nf, levels, args.n0 << (args.levels - 1)))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gdof/s", "n_gpus": args.gpus,
            "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": arm_config(args, world),
+           "config": cfg,
            "cpu_baseline": {"value": v, "unit": "Gdof/s", "cores": 1, "kind": "oracle",
                             "sample": "each step: the plain C FP64 oracle (CSR assembly, banded Cholesky, JCG) on the "
                                       "same cos_cube problem cut to %d^3 (%d levels), rtol %g; value = free dofs of "
@@ -461,8 +478,22 @@ def main():
     # (earliest block start to end of last block per launch; CUDA events cannot sit inside the
     # conditional-node bodies of the solve graph)
     k1_live_total_ms, k1_live_n = mixed.stencil_timer(-1, reset=True)
-    st_mixed, _ = mixed.solve(u_out)
+    st_mixed, status = mixed.solve(u_out)
+    assert status == 0, st_mixed
     err_mixed = mixed.norms(u_out, u_exact)[0]
+    # the error columns of the tables of Sec. 5 on the finest level (max and RMS norms over all
+    # nodes), and r_h = ||W - U||_2 / ||U - u||_2
+    e_u = mixed.norms(u_out, u_exact)
+    w_fin = mixed.get(ecmg.ECMG_VEC_W)
+    e_w = mixed.norms(w_fin, u_out)
+    del w_fin
+    ut_fin = mixed.extrapolate()
+    e_t = mixed.norms(ut_fin, u_exact)
+    del ut_fin
+    table_norms = {"level": "%d^3" % nf, "U_minus_u": {"max": e_u[0], "rms": e_u[1]},
+                   "Utilde_minus_u": {"max": e_t[0], "rms": e_t[1]}, "W_minus_U": {"max": e_w[0], "rms": e_w[1]},
+                   "r_h": e_w[1] / e_u[1] if e_u[1] else None,
+                   "note": "MIXED solution; Utilde = EXP_true, W = EXP_finite guess; rms = sqrt(sum e^2 / nodes)"}
 
     # kernels alone (finest level), for the roofline
     pk = peaks()
@@ -588,6 +619,7 @@ def main():
         "solve_ms_mixed": ms_mixed, "solve_ms_fp64": ms_fp64, "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
         "max_err_mixed": err_mixed, "max_err_fp64": err_fp64,
         "err_ratio_mixed_over_fp64": err_mixed / err_fp64,
+        "table_norms_finest": table_norms,
         "iters_mixed": st_mixed["iters"], "updates_mixed": st_mixed["updates"], "iters_fp64": st64["iters"],
         "level_seconds_mixed": st_mixed["seconds"], "setup_seconds_mixed": st_mixed["setup_seconds"],
         "rel_res_mixed": st_mixed["rel_res"], "gdofs_fp64": dofs / (ms_fp64 * 1e-3) / 1e9,
@@ -602,7 +634,7 @@ def main():
                      "timing": "device global timer per launch inside the timed solves (earliest block start to "
                                "end of last block), averaged over the launches of the finest level",
                      "launch_ms_alone_cuda_events": k1_ms, "tiles": {"ry": tiles[0], "kz": tiles[1]},
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy; of measured)"},
+                     "peak_source": pk["source"]},
         "kernels_alone": kern,
         # the two ways of counting dofs: finest free dofs per solve (value), and free dofs times
         # JCG iterations summed over the levels; the byte model charges each node-iteration the

@@ -229,7 +229,8 @@ ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision
 
 /* Error norms between two device vectors of one level (dense nodal layout): max |a - b| and
  * root-mean-square over all nodes (the max and "L2" norms of the tables of Sec. 5).
- * b may be NULL (norms of a). Results on the host; synchronises the stream. */
+ * b may be NULL (norms of a). A NaN anywhere in a - b makes both results NaN (an error norm
+ * never hides one). Results on the host; synchronises the stream. */
 ecmg_status ecmg_error_norms(ecmg_handle* h, int32_t level, const double* a, const double* b,
                              double* max_abs, double* rms);
 
@@ -302,7 +303,7 @@ ecmg_status ecmg_set_tiles(ecmg_handle* h, int32_t level, int32_t ry, int32_t kz
 /* Read the shape of one level into *ry, *kz (host). */
 ecmg_status ecmg_get_tiles(ecmg_handle* h, int32_t level, int32_t* ry, int32_t* kz);
 /* Autotuner: on every MIXED level of at least 2^18 nodes, time each candidate shape (ry in
- * {1, 2} x kz in {16, 32, 64, 128}) and the current one with `reps` launches each (CUDA
+ * {1, 2} x kz in {8, 12, 16, 24, 32, 48, 64, 128}) and the current one with `reps` launches each (CUDA
  * events on the handle's stream) and keep the fastest. Overwrites the level's work vectors;
  * call it before a solve or between solves. Synchronises the stream. */
 ecmg_status ecmg_autotune(ecmg_handle* h, int32_t reps);
@@ -322,7 +323,11 @@ ecmg_status ecmg_autotune(ecmg_handle* h, int32_t reps);
  * device work. stream: a cudaStream_t (NULL = default stream), synchronised before return.
  * max_abs, rms: host outputs.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. Every call overwrites
+ * that device current and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not reset the device (cudaDeviceReset) after it. a and b are checked
+ * with cudaPointerGetAttributes first: device memory of the current device, managed memory or
+ * page-locked host memory; anything else returns ECMG_ERR_INVALID_ARG and leaves the outputs
+ * unwritten. A NaN anywhere in a - b makes both outputs NaN. Every call overwrites
  * the whole part of the array it reads, so nothing has to start at zero, but all calls share
  * the one array: calls that overlap on the GPU (different streams, or different host threads
  * on one device) race and may return wrong norms. */

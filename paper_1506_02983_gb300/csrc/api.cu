@@ -1377,7 +1377,8 @@ ecmg_status ecmg_error_norms(ecmg_handle* h, int32_t level, const double* a, con
         ck(cudaStreamSynchronize(s));
         double mx = 0.0, ss = 0.0;
         for (int i = 0; i < nb; ++i) {
-            mx = std::max(mx, h->host_norms[2 * i]);
+            const double m = h->host_norms[2 * i];
+            mx = (std::isnan(m) || std::isnan(mx)) ? m + mx : std::max(mx, m);  // keeps a NaN
             ss += h->host_norms[2 * i + 1];
         }
         *max_abs = mx;

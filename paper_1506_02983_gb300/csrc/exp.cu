@@ -62,13 +62,17 @@ __global__ void __launch_bounds__(128) k_exp_true(Grid g, const double* __restri
     exp_true_element(g, U1, gc, U0, Ut, ex, ey, ez);
 }
 
-// Per-block max |a-b| and sum (a-b)^2 over the owned nodes of a level.
+// Per-block max |a-b| and sum (a-b)^2 over the owned nodes of a level. The max is taken over
+// the bit patterns of |a-b| as unsigned integers: for non-negative doubles that order is the
+// numeric one, and every NaN (sign cleared) sorts above +inf, so a NaN anywhere in a - b makes
+// the max NaN instead of dropping out as it would with fmax (an error norm must not hide one).
 __global__ void k_norms(Grid g, const double* __restrict__ a, const double* __restrict__ b,
                         double* __restrict__ part)
 {
     COUNT_LAUNCH();
     const int64_t n = (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-    double mx = 0.0, ss = 0.0;
+    unsigned long long mx = 0ull;
+    double ss = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int I = (int)(t % (g.nx + 1));
@@ -77,12 +81,13 @@ __global__ void k_norms(Grid g, const double* __restrict__ a, const double* __re
         const int K = (int)(rr / (g.ny + 1));
         const int64_t o = g.off(I, J, K);
         const double d = a[o] - (b ? b[o] : 0.0);
-        mx = fmax(mx, fabs(d));
+        mx = max(mx, (unsigned long long)__double_as_longlong(fabs(d)));
         ss = fma(d, d, ss);
     }
-    __shared__ double smx[TPB / 32], sss[TPB / 32];
+    __shared__ unsigned long long smx[TPB / 32];
+    __shared__ double sss[TPB / 32];
     for (int o = 16; o > 0; o >>= 1) {
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
         ss += __shfl_down_sync(0xffffffffu, ss, o);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -93,10 +98,10 @@ __global__ void k_norms(Grid g, const double* __restrict__ a, const double* __re
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w2 = 1; w2 < TPB / 32; ++w2) {
-            mx = fmax(mx, smx[w2]);
+            mx = max(mx, smx[w2]);
             ss += sss[w2];
         }
-        part[2 * blockIdx.x] = mx;
+        part[2 * blockIdx.x] = __longlong_as_double((long long)mx);
         part[2 * blockIdx.x + 1] = ss;
     }
 }

@@ -29,15 +29,22 @@ static_assert((int64_t)NA_MAX_BLOCKS * NA_PER_BLOCK == ECMG_NOALLOC_MAX_ELEMS, "
 // 2 * 32768 + 2 doubles = 512 KiB + 16 B per device.
 static __device__ __align__(256) double g_noalloc_scratch[2 * NA_MAX_BLOCKS + 2];
 
-// Device address of g_noalloc_scratch per device, looked up once per device.
+// Device address of g_noalloc_scratch per device, looked up once per device. The address
+// belongs to the device's primary context: after cudaDeviceReset (which destroys that context
+// and unloads the module) it would be stale, so resetting a device after the first call on it
+// is not supported.
 std::mutex g_lookup_mutex;
 double* g_scratch_ptr[256] = {};
 
-__device__ __forceinline__ void block_max_sum(double& mx, double& ss)
+// The max is taken over the bit patterns of |a-b| as unsigned integers: for non-negative
+// doubles that order is the numeric one and every NaN (sign cleared) sorts above +inf, so a NaN
+// anywhere in a - b makes max_abs NaN instead of dropping out as it would with fmax.
+__device__ __forceinline__ void block_max_sum(unsigned long long& mx, double& ss)
 {
-    __shared__ double smx[32], sss[32];
+    __shared__ unsigned long long smx[32];
+    __shared__ double sss[32];
     for (int o = 16; o > 0; o >>= 1) {
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
         ss += __shfl_down_sync(0xffffffffu, ss, o);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -47,13 +54,18 @@ __device__ __forceinline__ void block_max_sum(double& mx, double& ss)
     }
     __syncthreads();
     if (warp == 0) {
-        mx = lane < nw ? smx[lane] : 0.0;
+        mx = lane < nw ? smx[lane] : 0ull;
         ss = lane < nw ? sss[lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) {
-            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
             ss += __shfl_down_sync(0xffffffffu, ss, o);
         }
     }
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double d)
+{
+    return (unsigned long long)__double_as_longlong(fabs(d));
 }
 
 // One partial pair per block of NA_PER_BLOCK consecutive elements.
@@ -61,18 +73,19 @@ __global__ void __launch_bounds__(NA_TPB) k_noalloc_partials(const double* __res
                                                             int64_t n, double* __restrict__ scratch)
 {
     const int64_t base = (int64_t)blockIdx.x * NA_PER_BLOCK + threadIdx.x;
-    double mx = 0.0, ss = 0.0;
+    unsigned long long mx = 0ull;
+    double ss = 0.0;
     for (int it = 0; it < NA_ITEMS; ++it) {
         const int64_t t = base + (int64_t)it * NA_TPB;
         if (t < n) {
             const double d = a[t] - (b ? b[t] : 0.0);
-            mx = fmax(mx, fabs(d));
+            mx = max(mx, abs_bits(d));
             ss = fma(d, d, ss);
         }
     }
     block_max_sum(mx, ss);
     if (threadIdx.x == 0) {
-        scratch[2 * blockIdx.x] = mx;
+        scratch[2 * blockIdx.x] = __longlong_as_double((long long)mx);
         scratch[2 * blockIdx.x + 1] = ss;
     }
 }
@@ -80,24 +93,53 @@ __global__ void __launch_bounds__(NA_TPB) k_noalloc_partials(const double* __res
 // Fixed-order reduction of the nb partial pairs into the final pair (deterministic).
 __global__ void __launch_bounds__(1024) k_noalloc_final(int nb, double* __restrict__ scratch)
 {
-    double mx = 0.0, ss = 0.0;
+    unsigned long long mx = 0ull;
+    double ss = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        mx = fmax(mx, scratch[2 * b]);
+        mx = max(mx, abs_bits(scratch[2 * b]));
         ss += scratch[2 * b + 1];
     }
     block_max_sum(mx, ss);
     if (threadIdx.x == 0) {
-        scratch[NA_RESULT] = mx;
+        scratch[NA_RESULT] = __longlong_as_double((long long)mx);
         scratch[NA_RESULT + 1] = ss;
+    }
+}
+
+// The kernels read a and b through the pointers they are given, so those must be reachable
+// from the current device: its own device memory, managed memory, or page-locked host memory
+// (then the mapped device address is used). Pageable host memory or another device's memory
+// would make the kernel fault, so such pointers are refused before any launch. The check is
+// cudaPointerGetAttributes, which allocates nothing.
+bool device_readable(const double* p, int dev, const double** out)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the (non-sticky) error an unknown pointer leaves behind
+        return false;
+    }
+    switch (at.type) {
+    case cudaMemoryTypeDevice:
+        if (at.device != dev) return false;
+        *out = p;
+        return true;
+    case cudaMemoryTypeManaged:
+        *out = p;
+        return true;
+    case cudaMemoryTypeHost:
+        if (!at.devicePointer) return false;
+        *out = static_cast<const double*>(at.devicePointer);
+        return true;
+    default:
+        return false;
     }
 }
 
 // Set-up, once per device, with that device current: the host-side symbol is only a stand-in,
 // so the kernels get the array's device address from cudaGetSymbolAddress.
-ecmg_status scratch_address(double** out)
+ecmg_status scratch_address(int dev, double** out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return ECMG_ERR_CUDA;
+    if (dev < 0 || dev >= 256) return ECMG_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_lookup_mutex);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
@@ -115,8 +157,11 @@ extern "C" ecmg_status ecmg_error_norms_noalloc(const double* a, const double* b
 {
     if (!a || !max_abs || !rms || n < 1) return ECMG_ERR_INVALID_ARG;
     if (n > ECMG_NOALLOC_MAX_ELEMS) return ECMG_ERR_INVALID_ARG;  // beyond the fixed scratch
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ECMG_ERR_CUDA;
+    if (!device_readable(a, dev, &a) || (b && !device_readable(b, dev, &b))) return ECMG_ERR_INVALID_ARG;
     double* scratch = nullptr;
-    const ecmg_status st = scratch_address(&scratch);
+    const ecmg_status st = scratch_address(dev, &scratch);
     if (st != ECMG_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nb = (int)((n + NA_PER_BLOCK - 1) / NA_PER_BLOCK);

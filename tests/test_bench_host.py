@@ -79,3 +79,6 @@ def test_reference_arm_prints_the_contract_line(monkeypatch):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+    # the line states what this arm ran: the FP64 oracle on a cut of the workload
+    assert d["config"]["precision"].startswith("FP64")
+    assert "cut to" in d["config"]["sample"]

@@ -99,12 +99,32 @@ def test_cos_cube_512_mixed_full_size(E, oracle_mod):
     assert np.abs(got[free] - want[free]).max() <= 1e-5 * np.abs(want[free]).max()
     assert np.all(got[~free] == 0.0)
     del xt
+    # b - A U recomputed by the oracle at sampled free nodes: every component of a residual with
+    # ||r||_2 <= rtol ||f_h||_2 is at most that
+    b = _np(s.get(E.ECMG_VEC_B)).ravel()
+    fnodes = [t for t in _sample_nodes(n, 420, 3) if all(0 < t[a] < n[a] for a in range(3))]
+    assert len(fnodes) >= 300
+    r = _at(b, n, fnodes) - oracle_mod.apply_at(n, h, np.ones(n[0] * n[1] * n[2]), p["face_bc"], p["alpha"],
+                                                U[L - 1].ravel(), fnodes)
+    assert np.abs(r).max() <= p["rtol"] * st["rhs_norm"][L - 1] * 1.0001, np.abs(r).max()
+    # the error norms of the library (max and RMS over all 513^3 nodes) against numpy
+    Ud = s.get(E.ECMG_VEC_U)
+    ued = torch.tensor(ue, device="cuda")
+    mx, rms = s.norms(Ud, ued)
+    d = U[L - 1] - ue
+    assert mx == np.abs(d).max()
+    assert rms == pytest.approx(float(np.sqrt(np.mean(d * d))), rel=1e-12)
+    del Ud, ued, d
     s.close()
-    # the same system in FP64: the same discretisation error to 1 %
+    # the same system in FP64: the same discretisation error to 1 %, and the same solution node
+    # by node to well below that error
     s64 = E.solver_from_problem(p, precision=E.ECMG_FP64)
     st64, status = s64.solve()
     assert status == 0
-    e64 = _max_err(_np(s64.get(E.ECMG_VEC_U)), ue)
+    U64 = _np(s64.get(E.ECMG_VEC_U))
+    e64 = _max_err(U64, ue)
+    assert np.abs(U[L - 1] - U64).max() <= 1e-7 * np.abs(U64).max(), np.abs(U[L - 1] - U64).max()
+    del U64
     assert err[L - 1] == pytest.approx(e64, rel=0.01)
     for l in range(2, L):
         assert abs(st64["iters"][l] - st["iters"][l]) <= max(2, 0.1 * st64["iters"][l]), (st64["iters"], st["iters"])
