@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE: used by the tests, by ``__graft_entry__.smoke()`` and by the CPU-baseline
 leg of ``bench.py`` only. It shares no code with the CUDA path; it receives the same seeded
-inputs (from ``paper_1506_02983_gb300.inputs``, which holds none of the method's arithmetic)
-and computes everything itself, in FP64, on one host core.
+inputs (from ``paper_1506_02983_gb300.inputs``, which holds none of the solver's arithmetic;
+the LOAD-mode functionals it evaluates are pinned to ``load_functional`` here) and computes
+everything itself, in FP64, on one host core.
 """
 from __future__ import annotations
 
@@ -191,6 +192,57 @@ def gauss3_unit():
     and weights 5/18, 8/18, 5/18 (exact for polynomials of degree <= 5)."""
     r = np.sqrt(0.6)
     return np.array([0.5 * (1.0 - r), 0.5, 0.5 * (1.0 + r)]), np.array([5.0, 8.0, 5.0]) / 18.0
+
+
+def load_functional(n, lo, hi, f, q=6, faces=()):
+    """Load functional of the weak form of Sec. 2 on the uniform grid of n = (nx, ny, nz)
+    elements of the box [lo, hi]:  b_i = int_Omega f phi_i dx + sum over `faces` of
+    int_F g phi_i dS,  written as the definition, element by element: on every element a q-point
+    tensor Gauss-Legendre rule of f times each of the element's 8 trilinear hats, added into that
+    hat's node; on every quad of a face likewise with q x q points and the quad's 4 bilinear
+    hats. f(x, y, z) and g(x, y, z) take broadcastable coordinate arrays (points are interior to
+    the elements and quads, so piecewise data may switch on element boundaries). faces: triples
+    (axis, node index along that axis, g). Shape (nz+1, ny+1, nx+1)."""
+    n = [int(v) for v in n]
+    nx, ny, nz = n
+    h = [(hi[a] - lo[a]) / n[a] for a in range(3)]
+    t, w = np.polynomial.legendre.leggauss(int(q))
+    t, w = 0.5 * (t + 1.0), 0.5 * w
+    hat = {0: 1.0 - t, 1: t}  # the left and right hat of an interval at its points
+    # the Gauss points of every element interval along each axis, shape (n_a, q)
+    P = [lo[a] + (np.arange(n[a])[:, None] + t[None, :]) * h[a] for a in range(3)]
+    b = np.zeros((nz + 1, ny + 1, nx + 1))
+    vol = h[0] * h[1] * h[2]
+    for ez in range(nz):
+        X = P[0].reshape(1, nx, 1, 1, q)
+        Y = P[1].reshape(ny, 1, 1, q, 1)
+        Z = P[2][ez].reshape(1, 1, q, 1, 1)
+        F = np.broadcast_to(f(X, Y, Z), (ny, nx, q, q, q))  # F[ey, ex, qz, qy, qx]
+        for cz in (0, 1):
+            for cy in (0, 1):
+                for cx in (0, 1):
+                    wphi = np.einsum("c,b,a->cba", w * hat[cz], w * hat[cy], w * hat[cx])
+                    b[ez + cz, cy:cy + ny, cx:cx + nx] += vol * np.einsum("jicba,cba->ji", F, wphi)
+    for axis, idx, g in faces:
+        a1, a2 = [a for a in range(3) if a != axis]  # the face's two axes, a1 < a2
+        c = lo[axis] + idx * h[axis]
+        pts = [None, None, None]
+        pts[axis] = np.full((1, 1, 1, 1), c)
+        pts[a1] = P[a1].reshape(1, n[a1], 1, q)
+        pts[a2] = P[a2].reshape(n[a2], 1, q, 1)
+        G = np.broadcast_to(g(*pts), (n[a2], n[a1], q, q))  # G[e2, e1, q2, q1]
+        area = h[a1] * h[a2]
+        for c2 in (0, 1):
+            for c1 in (0, 1):
+                wphi = np.outer(w * hat[c2], w * hat[c1])
+                v = area * np.einsum("jiba,ba->ji", G, wphi)
+                if axis == 0:
+                    b[c2:c2 + nz, c1:c1 + ny, idx] += v
+                elif axis == 1:
+                    b[c2:c2 + nz, idx, c1:c1 + nx] += v
+                else:
+                    b[idx, c2:c2 + ny, c1:c1 + nx] += v
+    return b
 
 
 def load_separable(n, h, terms, samples):

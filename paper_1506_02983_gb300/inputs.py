@@ -1,9 +1,13 @@
 """Seeded synthetic problem generators for eq. (bvp): -div(beta grad u) = f on a box.
 
-This module holds none of the method's arithmetic: it only evaluates problem data
-(coefficient beta per element, nodal f, Dirichlet data g_D, Robin data g_R, boundary types)
-for manufactured solutions and for seeded random problems. Both the CUDA path and the CPU
-oracle receive exactly these arrays.
+This module holds none of the solver's arithmetic (no operator, no JCG, no extrapolation). It
+evaluates problem data -- coefficient beta per element, nodal f, Dirichlet data g_D, Robin data
+g_R, boundary types -- for manufactured solutions and for seeded random problems, and, for the
+problems given in LOAD mode, the input functional b_i = int f phi_i (+ face terms) of the weak
+form of Sec. 2 by Gauss quadrature (hat_integrals_1d / separable_load for separable f, the
+per-element rule of jump_singular). That functional is an input of the library's LOAD mode; the
+oracle's own per-element definition (oracle.load_functional) pins it. Both the CUDA path and
+the CPU oracle receive exactly these arrays.
 
 Every problem is a dict with keys
     n0 (3 ints, coarsest elements per axis), levels, lo, hi (box corners),
