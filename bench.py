@@ -352,7 +352,7 @@ def bench_batched(args, steps, warmup):
         q["f"] = torch.as_tensor(p["f"]).cuda()
         dev.append(q)
     bs = ecmg.BatchSolver(dev, rtol=1e-8, max_iters=args.max_iters, use_graph=0 if args.eager else 1,
-                          inner_rtol=args.inner_rtol)
+                          inner_rtol=args.inner_rtol, autotune=1)
     for _ in range(warmup):
         st, status = bs.solve()
         assert status == 0, status
@@ -368,6 +368,11 @@ def bench_batched(args, steps, warmup):
     torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1) / steps
     launches = (ecmg.kernel_launches() - l0) // steps
+    # the FP32 stencil (K1) and residual (K2) launches of the last stage alone (every problem's
+    # finest level), CUDA events around each launch
+    k1_ms, k1_bytes = bs.time_kernel(0, reps=10)
+    k2_ms, k2_bytes = bs.time_kernel(1, reps=10)
+    pk = peaks()
     dofs = sum(int(np.prod([(v << (p["levels"] - 1)) - 1 for v in p["n0"]])) for p in probs)
     work = 0  # node-iterations of JCG over all problems and levels
     for p, s in zip(probs, st):
@@ -382,7 +387,15 @@ def bench_batched(args, steps, warmup):
                                                                  for l in range(max(s["levels"] for s in st))],
             "worst_rel_res_finest": max(s["rel_res"][s["levels"] - 1] for s in st),
             "replacements": sum(sum(s["updates"]) for s in st), "inner_rtol": args.inner_rtol,
-            "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes"}
+            "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes",
+            "tiles": "batched FP32 stencil tile shapes autotuned at creation (per stage, per size class)",
+            "roofline": {"kernel": "batched K1 (bk_pq_tma: TMA-staged FP32 stencil, variable beta) over the 64 "
+                                   "finest levels, alone", "bound": "hbm",
+                         "achieved": k1_bytes / k1_ms / 1e6, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": k1_bytes / k1_ms / 1e6 / pk["hbm_gbs"], "algorithmic_bytes_per_launch": k1_bytes,
+                         "launch_ms": k1_ms, "peak_source": pk["source"]},
+            "k2_alone": {"kernel": "batched K2 (bk_update) over the 64 finest levels", "ms": k2_ms,
+                         "algorithmic_bytes": k2_bytes, "GBps": k2_bytes / k2_ms / 1e6}}
 
 
 def main():

@@ -279,7 +279,11 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
  * with one beta and every face Dirichlet kernels 0 and 1 count no beta and no D^-1 (they read
  * none). Valid after
  * ecmg_solve; it overwrites the level's work vectors and U~ (kernel 3 uses U~ as its
- * iterate); U and W are never changed. Synchronises the stream. */
+ * iterate); U and W are never changed. Synchronises the stream.
+ * Batched handles: `level` is a stage of the batched solve (-1 = the last, where every problem
+ * works on its finest level) and which is 0 (the batched K1 over every item of the stage) or 1
+ * (the batched K2); bytes_out sums the items' algorithmic bytes. The launches overwrite the
+ * items' work vectors and states, which the next ecmg_solve_batched sets up afresh. */
 ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,
                              double* ms_out, double* bytes_out);
 
@@ -305,7 +309,11 @@ ecmg_status ecmg_get_tiles(ecmg_handle* h, int32_t level, int32_t* ry, int32_t* 
 /* Autotuner: on every MIXED level of at least 2^18 nodes, time each candidate shape (ry in
  * {1, 2} x kz in {8, 12, 16, 24, 32, 48, 64, 128}) and the current one with `reps` launches each (CUDA
  * events on the handle's stream) and keep the fastest. Overwrites the level's work vectors;
- * call it before a solve or between solves. Synchronises the stream. */
+ * call it before a solve or between solves. Synchronises the stream.
+ * Batched handles (also run at ecmg_create_batched when options.autotune = 1): for every stage,
+ * the stage's whole K1 launch is timed for ry in {1, 2} x kz in {4, 8, 16, 32, 64} applied to all
+ * of its items, then the kz of each size class of items (the same power of two of z nodes) is
+ * varied with the others fixed; the fastest shapes are kept. */
 ecmg_status ecmg_autotune(ecmg_handle* h, int32_t reps);
 
 /* ---- error norms without device allocation (no counterpart in the paper) ---------------

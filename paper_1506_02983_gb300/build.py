@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libecmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["setup.cu", "jcg.cu", "pq_tma.cu", "pq_sp.cu", "exp.cu", "api.cu", "norms_noalloc.cu", "batch.cu", "separable.cu", "res_cc.cu", "tma_map.cu"]
+SOURCES = ["setup.cu", "jcg.cu", "pq_tma.cu", "pq_sp.cu", "exp.cu", "api.cu", "norms_noalloc.cu", "batch.cu", "batch_tma.cu", "separable.cu", "res_cc.cu", "tma_map.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -41,6 +41,8 @@ struct Batch {
     SolveState* host_states = nullptr;  // pinned
     BCtl* ctl = nullptr;
     int robin = 0, cube = 1;       // kernel variants: any Robin face in the batch; all elements cubic
+    PlaneMaps* d_maps = nullptr;   // device, the tensor maps of every item's FP32 vectors
+    std::vector<int> stage_ry;     // node rows per thread of the TMA-staged K1 at each stage
     int item(int p, int l) const { return first[p] + l; }
 };
 
@@ -656,6 +658,22 @@ BLaunch make_launch(const Batch& B, const std::vector<int>& ids, BGeom geo)
     return L;
 }
 
+// Block table of one batched launch of the TMA-staged K1 (ry node rows per thread, each item's
+// own planes per block).
+BLaunch make_launch_k1(const Batch& B, const std::vector<int>& ids, int ry)
+{
+    BLaunch L{};
+    L.n = (int)ids.size();
+    int acc = 0;
+    for (int s = 0; s < L.n; ++s) {
+        L.id[s] = ids[s];
+        L.start[s] = acc;
+        acc += bk1_blocks(B.items[ids[s]], ry);
+    }
+    L.start[L.n] = acc;
+    return L;
+}
+
 // Items of the set-up at depth d (d = 0: every problem's finest level).
 std::vector<int> depth_items(const Batch& B, int d)
 {
@@ -706,6 +724,8 @@ void record_batched(Rec& R)
                             make_launch(B, ids, BG_ROWS), B.robin, B.cube, o.inner_rtol, R.s());
         blaunch_guess(items, make_launch(B, ids2, BG_EXPF), make_launch(B, ids, BG_FLAT), o.exp_variant, R.s());
         const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_FLAT);
+        const int ry = B.stage_ry[s];
+        const BLaunch k1 = make_launch_k1(B, ids, ry);
         if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
             blaunch_absmax(items, flat, R.s());
@@ -713,7 +733,7 @@ void record_batched(Rec& R)
             R.open(loop, cudaGraphCondTypeWhile);
             for (int half = 0; half < 2; ++half) {
                 const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
-                blaunch_pq(items, stencil, B.robin, B.cube, half, half ? 0 : 1, R.s());
+                blaunch_pq_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, half ? 0 : 1, R.s());
                 blaunch_update(items, flat, B.ctl, CondHandles{loop, upd, 1}, R.s());
                 R.open(upd, cudaGraphCondTypeIf);
                 blaunch_fold(items, flat, half ? 0 : 1, R.s());
@@ -727,7 +747,7 @@ void record_batched(Rec& R)
             blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, none, R.s());
             int half = 0;
             while (any_state(h, ids, false)) {
-                blaunch_pq(items, stencil, B.robin, B.cube, half, half ? 0 : 1, R.s());
+                blaunch_pq_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, half ? 0 : 1, R.s());
                 blaunch_update(items, flat, B.ctl, none, R.s());
                 if (any_state(h, ids, true)) {
                     blaunch_fold(items, flat, half ? 0 : 1, R.s());
@@ -920,8 +940,127 @@ constexpr int64_t AUTOTUNE_MIN_NODES = 1 << 18;
 // Time every candidate tile shape of the FP32 stencil kernel on each MIXED level that is large
 // enough, and keep the fastest (ties keep the earlier candidate, so the choice is repeatable
 // when timings agree).
+// ---- batched K1 tile shapes ------------------------------------------------------------------
+// Mean milliseconds of `reps` launches of the batched K1 (which 0) or K2 (which 1) over the items
+// `ids` (CUDA events on the handle's stream, one untimed launch first). Before every launch each
+// item's state is set to a running step with a tiny non-zero deferred step, so that K1 stages
+// and writes e as inside a solve; no solve state survives (the next solve starts afresh).
+double time_batch_launch(ecmg_handle* h, const std::vector<int>& ids, int which, int ry, int reps)
+{
+    Batch& B = *h->batch;
+    cudaStream_t s = h->user_stream;
+    SolveState tmpl = {};
+    tmpl.rho = 1.0;
+    tmpl.beta = 0.5;
+    tmpl.alpha = 1e-30;
+    tmpl.alpha_prev = 1e-30;
+    tmpl.max_iters = 1 << 30;
+    tmpl.thresh2 = -1.0;
+    tmpl.inner2 = -1.0;
+    const size_t ni = B.items.size();
+    const BLaunch k1 = make_launch_k1(B, ids, ry), flat = make_launch(B, ids, BG_FLAT);
+    const CondHandles none{0, 0, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double total = 0.0;
+    try {
+        ck(cudaEventCreate(&e0));
+        ck(cudaEventCreate(&e1));
+        for (int rep = 0; rep <= reps; ++rep) {
+            ck(cudaStreamSynchronize(s));  // the pinned staging array is refilled below
+            for (size_t i = 0; i < ni; ++i) B.host_states[i] = tmpl;
+            ck(cudaMemcpyAsync(B.states, B.host_states, sizeof(SolveState) * ni, cudaMemcpyHostToDevice, s));
+            ck(cudaEventRecord(e0, s));
+            if (which == 0) blaunch_pq_tma(B.d_items, B.d_maps, k1, ry, B.robin, B.cube, 0, 1, s);
+            else blaunch_update(B.d_items, flat, B.ctl, none, s);
+            ck(cudaEventRecord(e1, s));
+            ck(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) total += ms;
+        }
+        ck(cudaGetLastError());
+    } catch (CudaFail&) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return total / reps;
+}
+
+void upload_items(ecmg_handle* h)
+{
+    Batch& B = *h->batch;
+    ck(cudaMemcpyAsync(B.d_items, B.items.data(), sizeof(BItem) * B.items.size(), cudaMemcpyHostToDevice,
+                       h->user_stream));
+    ck(cudaStreamSynchronize(h->user_stream));
+}
+
+// Autotuner of the batched K1: per stage, first one shape for every item (ry in {1, 2} x planes
+// per block in {4, 8, 16, 32, 64}), timed as the stage's whole launch; then, with the others
+// fixed, the planes per block of each size class (items whose z extent has the same power of
+// two), again by the time of the whole launch.
+void batch_autotune(ecmg_handle* h, int reps)
+{
+    Batch& B = *h->batch;
+    const int kzs[5] = {4, 8, 16, 32, 64};
+    for (int s = 0; s < B.Lmax; ++s) {
+        const std::vector<int> ids = stage_items(B, s);
+        if (ids.empty()) continue;
+        auto set_kz = [&](const std::vector<int>& which, int kz) {
+            for (int id : which) B.items[id].k1kz = kz;
+        };
+        int best_ry = B.stage_ry[s], best_kz = B.items[ids[0]].k1kz;
+        double best = 1e300;
+        for (int ry = 1; ry <= 2; ++ry)
+            for (int kz : kzs) {
+                set_kz(ids, kz);
+                upload_items(h);
+                const double ms = time_batch_launch(h, ids, 0, ry, reps);
+                if (ms < best) {
+                    best = ms;
+                    best_ry = ry;
+                    best_kz = kz;
+                }
+            }
+        B.stage_ry[s] = best_ry;
+        set_kz(ids, best_kz);
+        std::vector<std::vector<int>> classes(32);
+        for (int id : ids) {
+            int c = 0;
+            while ((1 << c) < B.items[id].g.nz + 1) ++c;
+            classes[c].push_back(id);
+        }
+        int nclass = 0;
+        for (const auto& c : classes) nclass += c.empty() ? 0 : 1;
+        if (nclass > 1)
+            for (const auto& c : classes) {
+                if (c.empty()) continue;
+                int ckz = best_kz;
+                for (int kz : kzs) {
+                    if (kz == best_kz) continue;
+                    set_kz(c, kz);
+                    upload_items(h);
+                    const double ms = time_batch_launch(h, ids, 0, best_ry, reps);
+                    if (ms < best) {
+                        best = ms;
+                        ckz = kz;
+                    }
+                }
+                set_kz(c, ckz);
+            }
+        upload_items(h);
+    }
+    drop_graph(h);
+}
+
 void autotune(ecmg_handle* h, int reps)
 {
+    if (h->batch) {
+        batch_autotune(h, reps);
+        return;
+    }
     bool changed = false;
     for (int l = 2; l < h->L; ++l) {
         Level& v = h->lv[l];
@@ -1153,6 +1292,7 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
                 it.depth = pr.levels - 1 - l;
                 it.fmode = pr.f_mode;
                 it.kz = std::min(32, it.g.nz + 1);
+                it.k1kz = 16;
                 it.fixed = (opt->schedule == ECMG_SCHED_FIXED && l >= 2) ? 1 : 0;
                 it.rtol = l < 2 ? opt->dsolve_rtol : (it.fixed ? 0.0 : opt->rtol);
                 it.max_iters = it.fixed ? schedule_steps(pr.levels, l, opt->sched_mL, opt->sched_beta) : opt->max_iters;
@@ -1202,9 +1342,21 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
                 it.U0 = i0.U;
             }
         }
+        // tensor maps of every item's FP32 vectors for the TMA-staged K1
+        std::vector<PlaneMaps> maps(nitems);
+        for (int i = 0; i < nitems; ++i) {
+            const BItem& it = B.items[i];
+            if (!make_plane_maps(&maps[i], it.r32, it.pA32, it.pB32, it.dinv32, it.beta32, it.e32, it.g))
+                throw CudaFail{cudaErrorInvalidValue};
+        }
+        B.d_maps = dalloc<PlaneMaps>(h, nitems);
+        ck(cudaMemcpyAsync(B.d_maps, maps.data(), sizeof(PlaneMaps) * nitems, cudaMemcpyHostToDevice, h->cap[0]));
+        B.stage_ry.assign(B.Lmax, 1);
+        ck(bk1_prepare());
         B.d_items = dalloc<BItem>(h, nitems);
         ck(cudaMemcpyAsync(B.d_items, B.items.data(), sizeof(BItem) * nitems, cudaMemcpyHostToDevice, h->cap[0]));
         ck(cudaStreamSynchronize(h->cap[0]));
+        if (opt->autotune) batch_autotune(h, 3);
     } catch (CudaFail& f) {
         ecmg_destroy(h);
         if (f.e == cudaErrorMemoryAllocation) return fail(ECMG_ERR_OOM, "device allocation failed");
@@ -1430,7 +1582,7 @@ const char* ecmg_last_error(void) { return g_last_error.c_str(); }
 ecmg_status ecmg_kernel_launches(uint64_t* out)
 {
     if (!out) return fail(ECMG_ERR_INVALID_ARG, "null argument");
-    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_pq_sp() + launches_batch() +
+    *out = launches_setup() + launches_jcg() + launches_exp() + launches_pq_tma() + launches_pq_sp() + launches_batch() + launches_batch_tma() +
            launches_separable() + launches_res_cc();
     return ECMG_OK;
 }
@@ -1439,6 +1591,29 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
                              double* ms_out, double* bytes_out)
 {
     if (!h || !ms_out || !bytes_out || reps < 1) return fail(ECMG_ERR_INVALID_ARG, "bad argument");
+    if (h->batch) {
+        // batched handle: `level` is a stage (-1 = the last), the kernel its K1 (0) or K2 (1)
+        // launch over every item of the stage
+        Batch& B = *h->batch;
+        const int s = level < 0 ? B.Lmax - 1 : level;
+        if (s < 0 || s >= B.Lmax) return fail(ECMG_ERR_INVALID_ARG, "bad stage");
+        if (which != 0 && which != 1) return fail(ECMG_ERR_INVALID_ARG, "batched handles time kernels 0 and 1");
+        const std::vector<int> ids = stage_items(B, s);
+        double bytes = 0.0;
+        for (int id : ids) {
+            const BItem& it = B.items[id];
+            const double N = (double)(it.g.nx + 1) * (it.g.ny + 1) * (it.g.nz + 1);
+            const double E = (double)it.g.nx * it.g.ny * it.g.nz;
+            bytes += which == 0 ? 28.0 * (double)bk1_nodes(it) + 4.0 * E : 16.0 * N;
+        }
+        *bytes_out = bytes;
+        try {
+            *ms_out = time_batch_launch(h, ids, which, B.stage_ry[s], reps);
+        } catch (CudaFail& f) {
+            return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+        }
+        return ECMG_OK;
+    }
     const int l = resolve_level(h, level);
     if (l < 0 || l >= h->L) return fail(ECMG_ERR_INVALID_ARG, "bad level");
     if (which < 0 || which > 11) return fail(ECMG_ERR_INVALID_ARG, "bad kernel selector");

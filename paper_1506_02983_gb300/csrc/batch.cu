@@ -369,40 +369,6 @@ __global__ void __launch_bounds__(mt::NT) bk_res(const BItem* __restrict__ items
     }
 }
 
-// K1: p = D^-1 r + beta p_old on the fly, q = A p, e += alpha_prev p_old, p.q.
-template <bool ROBIN, bool CUBE>
-__global__ void __launch_bounds__(mt::NT) bk_pq(const BItem* __restrict__ items, const __grid_constant__ BLaunch L,
-                                               int pin_is_b, int pidx)
-{
-    COUNT_LAUNCH();
-    const Slot sl = find_slot(L);
-    const BItem& it = items[sl.item];
-    SolveState* st = it.st;
-    if (st->done) return;
-    const NodeRange rg = free_nodes(it.g, it.op);
-    int bx, by, bz;
-    tile_of(it, rg, sl.lb, bx, by, bz);
-    const float bcg = (float)st->beta;
-    const float ap = (float)st->alpha_prev;
-    const float* __restrict__ pold = pin_is_b ? it.pB32 : it.pA32;
-    float* __restrict__ pnew = pin_is_b ? it.pA32 : it.pB32;
-    const float* __restrict__ r = it.r32;
-    const float* __restrict__ dinv = it.dinv32;
-    float* __restrict__ q = it.q32;
-    float* __restrict__ e = it.e32;
-    Acc<float> acc;
-    const PSource<float> src{dinv, r, pold, bcg};
-    auto body = [&](int, int, int, int64_t o, float Av, float pn) {
-        pnew[o] = pn;
-        q[o] = Av;
-        if (ap != 0.f) e[o] += ap * pold[o];
-        acc.add_prod(pn, Av);
-    };
-    march_range<ROBIN, CUBE, float, float>(it.g, it.op, it.beta32, rg, bx, by, bz, it.kz, src, body);
-    double v[1] = {acc.value()};
-    if (item_sum<1>(v, it.part, &st->arrive, sl.lb, sl.nb)) pq_epilogue(st, v[0], pidx, CondHandles{0, 0, 0});
-}
-
 // K2: r -= alpha q; z = D^-1 r; r.z and r.r (compensated FP32); the item's tests.
 __global__ void __launch_bounds__(FLAT_TPB) bk_update(const BItem* __restrict__ items, const __grid_constant__ BLaunch L,
                                                      BCtl* ctl, CondHandles ch)
@@ -522,7 +488,7 @@ int bgeom_blocks(BGeom geo, const BItem& it)
 
 int bitem_partials(const BItem& it)
 {
-    int m = 0;
+    int m = bk1_max_blocks(it);
     for (BGeom geo : {BG_STENCIL, BG_FLAT, BG_ROWS}) m = std::max(m, bgeom_blocks(geo, it));
     return m;
 }
@@ -561,14 +527,6 @@ void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube
     auto k = robin ? (cube ? bk_res<true, true> : bk_res<true, false>)
                    : (cube ? bk_res<false, true> : bk_res<false, false>);
     k<<<nblocks(stencil), dim3(mt::BX, mt::BY), 0, s>>>(items, stencil, (int)mode, ctl, ch);
-}
-
-void blaunch_pq(const BItem* items, const BLaunch& stencil, int robin, int cube, int pin_is_b, int pidx,
-                cudaStream_t s)
-{
-    auto k = robin ? (cube ? bk_pq<true, true> : bk_pq<true, false>)
-                   : (cube ? bk_pq<false, true> : bk_pq<false, false>);
-    k<<<nblocks(stencil), dim3(mt::BX, mt::BY), 0, s>>>(items, stencil, pin_is_b, pidx);
 }
 
 void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s)

@@ -14,6 +14,7 @@
 
 #include "ecmg_internal.cuh"
 #include "jcg.cuh"
+#include "pq_tma.cuh"
 
 namespace ecmg {
 
@@ -26,7 +27,8 @@ struct BItem {
     Grid g1, g0;          // levels l-1 and l-2 (EXP)
     Grid gf;              // level l+1 (set-up of a coarser level)
     int level, problem, depth, fmode;  // depth 0 = the problem's finest level
-    int kz;               // z-march depth of the stencil kernels
+    int kz;               // z-march depth of the register-prefetched stencil kernels
+    int k1kz;             // planes per block of the TMA-staged FP32 stencil kernel (K1)
     double rtol;          // relative residual tolerance of this level
     int max_iters;        // step cap (the exact step count when fixed)
     int fixed;            // 1: exactly max_iters steps (the schedule of Alg. 3)
@@ -92,10 +94,8 @@ void blaunch_guess(const BItem* items, const BLaunch& expf, const BLaunch& flat_
 // blaunch_fold (before RES_REPLACE) left in the item's state.
 void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube, ResMode mode, BCtl* ctl,
                  CondHandles ch, cudaStream_t s);
-// One FP32 JCG iteration: K1 (p, q = A p, deferred correction, p.q) and K2 (r, r.z, tests).
-// pin_is_b selects p_old; K2 sets the loop and replacement conditions.
-void blaunch_pq(const BItem* items, const BLaunch& stencil, int robin, int cube, int pin_is_b, int pidx,
-                cudaStream_t s);
+// K2 of one FP32 JCG iteration (after K1, blaunch_pq_tma): r -= alpha q, r.z, r.r and the
+// item's tests; sets the loop and replacement conditions.
 void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s);
 // Fold the FP32 correction into the FP64 iterate for items that asked for a replacement, and
 // take max |x| of the new iterate into the item's state (the scale of the exact residual).
@@ -105,6 +105,19 @@ void blaunch_absmax(const BItem* items, const BLaunch& flat, cudaStream_t s);
 // EXP_true for levels >= 2.
 void blaunch_exp_true(const BItem* items, const BLaunch& expt, cudaStream_t s);
 
+// TMA-staged K1 (batch_tma.cu): p = D^-1 r + beta p_old, q = A p, e += alpha_prev p_old and
+// the item's p.q, one launch over the items of L with tiles of 32 x 8 ry nodes and k1kz planes;
+// maps: the items' tensor maps (device array indexed like items).
+void blaunch_pq_tma(const BItem* items, const PlaneMaps* maps, const BLaunch& L, int ry, int robin, int cube,
+                    int pin_is_b, int pidx, cudaStream_t s);
+// Blocks of one item in that launch, the most any tile shape needs, and the nodes it computes.
+int bk1_blocks(const BItem& it, int ry);
+int bk1_max_blocks(const BItem& it);
+int64_t bk1_nodes(const BItem& it);
+// Shared-memory limits of the batched K1 instantiations on the current device.
+cudaError_t bk1_prepare();
+
 unsigned long long launches_batch();
+unsigned long long launches_batch_tma();
 
 }  // namespace ecmg

@@ -83,7 +83,7 @@ constexpr size_t stage_smem()
 struct Range {
     int ilo, ihi, jlo, jhi, klo, khi;
 };
-inline Range k1_range(const Grid& g, const Op& op)
+__host__ __device__ inline Range k1_range(const Grid& g, const Op& op)
 {
     return Range{op.bc[0] == 0 ? 1 : 0, op.bc[1] == 0 ? g.nx - 1 : g.nx,
                  op.bc[2] == 0 ? 1 : 0, op.bc[3] == 0 ? g.ny - 1 : g.ny,
@@ -170,6 +170,21 @@ struct CCWeights {
 // CC: constant coefficient -- one beta on the whole level and every face Dirichlet, so every
 // node the kernel visits is interior with the same diagonal: beta and D^-1 are not streamed
 // (bu and cdinv hold their values) and the operator takes the plane-sum form above.
+// Where a block sits: its tile (bx, by, bz) in the level's tile grid, and its index among the
+// nb blocks whose partial sums the last of them reduces. The single-problem kernels take both
+// from blockIdx and gridDim (k1_block_of_grid); a batched launch decodes them from the block
+// range of the block's (problem, level) item.
+struct K1Block {
+    int bx, by, bz;
+    int bid, nb;
+};
+__device__ __forceinline__ K1Block k1_block_of_grid()
+{
+    return K1Block{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                   (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)),
+                   (int)(gridDim.x * gridDim.y * gridDim.z)};
+}
+
 // Scalars a K1 block needs before its first plane, loaded together at kernel entry so that the
 // block pays one global-memory round trip for them.
 struct K1Scalars {
@@ -229,7 +244,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
                                         const Grid& g, const Op& op, const Range& rg, float* __restrict__ pnew,
                                         float* __restrict__ q, float* __restrict__ rnew, float* __restrict__ e,
                                         SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
-                                        KTimer* tm, const K1Scalars sc)
+                                        KTimer* tm, const K1Scalars sc, const K1Block kb)
 {
     using S = Shape<RY>;
     extern __shared__ __align__(128) unsigned char k1_smem[];
@@ -251,7 +266,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
 
     if (sc.done) {
         // single pass: no residual kernel follows, so the loop's conditions are cleared here
-        if (SP && ch.use && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) {
+        if (SP && ch.use && kb.bid == 0 && (threadIdx.x | threadIdx.y) == 0) {
             cudaGraphSetConditional(ch.loop, 0);
             cudaGraphSetConditional(ch.update, 0);
         }
@@ -259,11 +274,11 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     }
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TBX * ty;
     if (tm && tid == 0) atomicMin(&tm->t0, global_ns());
-    const int i0 = rg.ilo + blockIdx.x * TBX, j0 = rg.jlo + blockIdx.y * S::NY;
-    const int kb = rg.klo + blockIdx.z * kz;
-    const int ke = min(kb + kz, rg.khi + 1);
-    const int P0 = kb - 1;                 // first staged node plane
-    const int nplanes = ke - kb + 2;       // planes kb-1 .. ke
+    const int i0 = rg.ilo + kb.bx * TBX, j0 = rg.jlo + kb.by * S::NY;
+    const int k0 = rg.klo + kb.bz * kz;
+    const int ke = min(k0 + kz, rg.khi + 1);
+    const int P0 = k0 - 1;                 // first staged node plane
+    const int nplanes = ke - k0 + 2;       // planes k0-1 .. ke
     const float bcg = sc.bcg, ap = sc.ap, cdinv = sc.cdinv, bu = sc.bu;
     // Node i sits in column i + XL of the padded layout. The box starts at the 16-byte
     // boundary bx at or below node i0-1's column, and node i0-1 is staged column sh.
@@ -307,7 +322,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     const Weights<float> wts(op);
     const int pitch = g.pitch;
 
-    // offset of the thread's first node on the plane computed next (plane kb at step t = 2)
+    // offset of the thread's first node on the plane computed next (plane k0 at step t = 2)
     int64_t o = g.plane_base(P0 - 1) + g.in_plane(min(i, g.nx + 1), min(jt, g.ny + 1));
     // the cells of the formed plane this thread fills, as staged offsets
     int sidx[S::NFORM];
@@ -523,8 +538,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
             v[6] = a_qzq.value();
         }
     }
-    const int nb = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nb = kb.nb, bid = kb.bid;
     block_sum<NP>(v, red);
     if (tid == 0) {
 #pragma unroll

@@ -29,7 +29,7 @@ k_step32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CU
     COUNT_LAUNCH();
     const K1Scalars sc{st->done, (float)st->beta, (float)st->alpha_prev, 0.f, 0.f};
     k1_body<ROBIN, CUBE, RY, false, true>(m_r, m_pold, m_dinv, m_beta, m_qold, m_e, g, op, rg, pnew, q, rnew, e, st,
-                                          partials, pidx, ch, kz, tm, sc);
+                                          partials, pidx, ch, kz, tm, sc, k1_block_of_grid());
 }
 
 // Constant-coefficient path (every face Dirichlet, one beta on the level); a stale host choice
@@ -61,7 +61,7 @@ k_step32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUt
         return;
     }
     k1_body<false, CUBE, RY, true, true>(m_r, m_pold, m_r, m_r, m_qold, m_e, g, op, rg, pnew, q, rnew, e, st,
-                                         partials, pidx, ch, kz, tm, sc);
+                                         partials, pidx, ch, kz, tm, sc, k1_block_of_grid());
 }
 
 template <bool ROBIN, bool CUBE, int RY>

@@ -26,7 +26,7 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
     COUNT_LAUNCH();
     const K1Scalars sc{st->done, (float)st->beta, (float)st->alpha_prev, 0.f, 0.f};
     k1_body<ROBIN, CUBE, RY, false, false>(m_r, m_pold, m_dinv, m_beta, m_r, m_e, g, op, rg, pnew, q, nullptr, e, st,
-                                           partials, pidx, ch, kz, tm, sc);
+                                           partials, pidx, ch, kz, tm, sc, k1_block_of_grid());
 }
 
 // Constant-coefficient path (every face Dirichlet, one beta on the level): r, p_old and e only,
@@ -56,7 +56,7 @@ k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUten
         return;
     }
     k1_body<false, CUBE, RY, true, false>(m_r, m_pold, m_r, m_r, m_r, m_e, g, op, rg, pnew, q, nullptr, e, st, partials,
-                                          pidx, ch, kz, tm, sc);
+                                          pidx, ch, kz, tm, sc, k1_block_of_grid());
 }
 
 bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy, int sx = SX)

@@ -336,6 +336,18 @@ class BatchSolver:
             check(s, "ecmg_solve_batched")
         return [stats_dict(st[i]) for i in range(self.n)], s
 
+    def time_kernel(self, which, stage=-1, reps=5):
+        """Mean ms of one launch of the stage's batched K1 (0) or K2 (1) alone, and its
+        algorithmic bytes."""
+        ms, nb = C.c_double(), C.c_double()
+        check(ecmg_time_kernel(self.handle, int(stage), int(which), int(reps), C.byref(ms), C.byref(nb)),
+              "ecmg_time_kernel")
+        return ms.value, nb.value
+
+    def autotune(self, reps=3):
+        """Time the batched stencil tile shapes of every stage; keep the fastest."""
+        check(ecmg_autotune(self.handle, int(reps)), "ecmg_autotune")
+
     def get(self, problem, which, level=-1):
         import torch
         q = self.problems[problem]

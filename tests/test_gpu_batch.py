@@ -178,3 +178,40 @@ def test_batched_ecmg_cg_matches_oracle(E, oracle_mod):
         U = _np(bs.get(i, E.ECMG_VEC_U))
         assert _rel(U, lv[L - 1]["U"]) <= 1e-7, (i, _rel(U, lv[L - 1]["U"]))
     bs.close()
+
+
+def test_batched_autotuned_tiles_match_the_oracle(E, oracle_mod):
+    """The autotuner of the batched FP32 stencil (per stage: rows per thread and planes per
+    block, then planes per block of each size class) changes only launch geometry and the order
+    of the partial sums: the MIXED bar against the oracle still holds and the step counts stay
+    within 2 of the untuned batch."""
+    import ctypes
+    probs = _mixed_batch()
+    dev = [_device(p) for p in probs]
+    plain = E.BatchSolver(dev, rtol=RTOL)
+    st0, status = plain.solve()
+    assert status == 0
+    plain.close()
+    bs = E.BatchSolver(dev, rtol=RTOL, autotune=1)
+    stats, status = bs.solve()
+    assert status == 0, stats
+    for i, p in enumerate(probs):
+        lv, ost = oracle_mod.ecmg(p, RTOL)
+        L = p["levels"]
+        for l in range(2, L):
+            assert stats[i]["rel_res"][l] <= RTOL
+            assert abs(stats[i]["iters"][l] - st0[i]["iters"][l]) <= 2, (i, l, stats[i]["iters"], st0[i]["iters"])
+        U = _np(bs.get(i, E.ECMG_VEC_U))
+        assert _rel(U, lv[L - 1]["U"]) <= 1e-7, (i, _rel(U, lv[L - 1]["U"]))
+    # the stage kernels timed alone through the C ABI (level = stage): K1 and K2 of the last stage
+    for which in (0, 1):
+        ms, nb = ctypes.c_double(), ctypes.c_double()
+        assert E.ecmg_time_kernel(bs.handle, -1, which, 2, ctypes.byref(ms), ctypes.byref(nb)) == E.ECMG_OK
+        assert ms.value > 0.0 and nb.value > 0.0
+    ms, nb = ctypes.c_double(), ctypes.c_double()
+    assert E.ecmg_time_kernel(bs.handle, -1, 5, 2, ctypes.byref(ms), ctypes.byref(nb)) == E.ECMG_ERR_INVALID_ARG
+    # and the batch solves again to the same result after the timing launches
+    again, status = bs.solve()
+    assert status == 0
+    assert [s["iters"] for s in again] == [s["iters"] for s in stats]
+    bs.close()
