@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-levels", type=int, default=5, help="oracle sample: 8^3 -> 8*2^(L-1)")
+    ap.add_argument("--cpu-levels", type=int, default=5, help="oracle sample, one thread: 8^3 -> 8*2^(L-1)")
+    ap.add_argument("--cpu-levels-omp", type=int, default=6,
+                    help="oracle sample, OpenMP build on every host core: 8^3 -> 8*2^(L-1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iters", type=int, default=20000)
     ap.add_argument("--inner-rtol", type=float, default=1e-3,
@@ -50,12 +52,19 @@ def parse():
     ap.add_argument("--kernels", default="0,1,2,5,6,7,11", help="kernels timed alone for the report")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-problem measurement")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--batched-form", default="two", choices=["two", "single"],
+                    help="MIXED step of the batched workload: two-pass (K1 + K2, the batched default) or the "
+                         "single-pass step on every level")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched 64-problem workload (one solve per step; --eager for host loop control)")
     ap.add_argument("--profile-kernel", default=None,
                     help="profiling run: one MIXED solve, then kernel W (or a comma list) of ecmg_time_kernel on "
                          "the finest level, 3 launches each inside the NVTX range kernel_profile (for ncu -k / "
                          "--nvtx-include); prints one JSON line per kernel and exits")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="profiling run: one batched solve of the 64-problem workload, then its last stage's K1, "
+                         "K2 and FP64 residual alone (ecmg_time_kernel 0, 1, 2), 2 launches each inside the NVTX "
+                         "range kernel_profile; prints one JSON line per kernel and exits")
     ap.add_argument("--profile-workload", default="cos_cube", choices=["cos_cube", "jump"],
                     help="with --profile-kernel: cos_cube (one beta, all Dirichlet: the constant-coefficient "
                          "kernels) or the coefficient-jump box (16x8x8 coarsest, beta 1 | 100, Robin face: the "
@@ -162,24 +171,66 @@ def free_dofs(n):
     return (n - 1) ** 3
 
 
-def cpu_baseline(args, levels, min_seconds=10.0, max_runs=4):
-    """The oracle as it stands, one host core, on cos_cube up to 8*2^(levels-1); repeated until
-    about min_seconds of CPU work (a bounded sample of the benchmark workload)."""
+def host_cpu():
+    """(logical cores, CPU model) of this host, from os.cpu_count and lscpu (or /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def cpu_baseline(args, levels_one=5, levels_omp=6, min_seconds=10.0, max_runs=4):
+    """The oracle as it stands on the host cores, two legs on the benchmark problem cut to a
+    bounded sample: the one-thread build up to 8*2^(levels_one-1) (repeated until about
+    min_seconds of work), and the OpenMP build on every host core up to 8*2^(levels_omp-1) (one
+    run). Each leg reports finest free dofs / wall time, and the set-up (CSR assembly, loads) and
+    solve seconds apart. The headline value is the all-core leg."""
     import oracle
     from paper_1506_02983_gb300 import inputs
     oracle.build()
-    p = inputs.cos_cube(levels=levels, n0=(args.n0,) * 3, rtol=args.rtol)
-    runs, total = 0, 0.0
-    while runs < max_runs and (runs == 0 or total < min_seconds):
-        t0 = time.perf_counter()
-        oracle.ecmg(p, p["rtol"])
-        total += time.perf_counter() - t0
-        runs += 1
-    dt = total / runs
-    nf = args.n0 << (levels - 1)
-    return dict(value=free_dofs(nf) / dt / 1e9, unit="Gdof/s", cores=1, kind="oracle",
-                sample="oracle ECMG_jcg FP64 on the same problem up to %d^3 (%d levels), %d runs, %.1f s each, "
-                       "finest free dofs / wall time" % (nf, levels, runs, dt), seconds=total)
+    oracle.build_omp()
+    nproc, model = host_cpu()
+    legs = []
+    for levels, threads, runs_max in ((levels_one, None, max_runs), (levels_omp, nproc, 1)):
+        p = inputs.cos_cube(levels=levels, n0=(args.n0,) * 3, rtol=args.rtol)
+        runs, total, asm, sol, used = 0, 0.0, 0.0, 0.0, 1
+        while runs < runs_max and (runs == 0 or total < min_seconds):
+            t0 = time.perf_counter()
+            _, st = oracle.ecmg(p, p["rtol"], threads=threads)
+            total += time.perf_counter() - t0
+            asm += st["seconds_assembly"]
+            sol += st["seconds_solve"]
+            used = st["threads"]
+            runs += 1
+        nf = args.n0 << (levels - 1)
+        dt = total / runs
+        legs.append(dict(value=free_dofs(nf) / dt / 1e9, unit="Gdof/s", cores=used, finest="%d^3" % nf,
+                         levels=levels, runs=runs, seconds_per_run=dt, seconds_assembly=asm / runs,
+                         seconds_solve=sol / runs, iters=st["iters"],
+                         build="one thread" if threads is None else "OpenMP (CSR products, vector updates)"))
+        del p
+    main = legs[1]
+    return dict(value=main["value"], unit="Gdof/s", cores=main["cores"], kind="oracle",
+                sample="oracle ECMG_jcg FP64 (OpenMP build, %d threads) on the same problem cut to %s (%d levels), "
+                       "one run of %.1f s (set-up %.1f s, solve %.1f s); finest free dofs / wall time"
+                       % (main["cores"], main["finest"], main["levels"], main["seconds_per_run"],
+                          main["seconds_assembly"], main["seconds_solve"]),
+                host={"nproc": nproc, "cpu_model": model}, legs=legs)
 
 
 def arm_config(args, world):
@@ -204,16 +255,24 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     steps, warm = args.steps, args.warmup
-    levels = min(args.cpu_levels, 4) if steps + warm > 4 else args.cpu_levels
+    # each step a bounded sample: the hierarchy cut at 128^3 (64^3 for long runs), so that the
+    # whole run ends within a few minutes
+    levels = min(args.cpu_levels, 4) if steps + warm > 30 else args.cpu_levels
     import oracle
     from paper_1506_02983_gb300 import inputs
-    oracle.build()
+    oracle.build_omp()
+    nproc, model = host_cpu()
     p = inputs.cos_cube(levels=levels, n0=(args.n0,) * 3, rtol=args.rtol)
     for _ in range(warm):
-        oracle.ecmg(p, p["rtol"])
+        oracle.ecmg(p, p["rtol"], threads=nproc)
     t0 = time.perf_counter()
+    asm = sol = 0.0
+    used = 1
     for _ in range(steps):
-        oracle.ecmg(p, p["rtol"])
+        _, st = oracle.ecmg(p, p["rtol"], threads=nproc)
+        asm += st["seconds_assembly"]
+        sol += st["seconds_solve"]
+        used = st["threads"]
     dt = (time.perf_counter() - t0) / steps
     nf = args.n0 << (levels - 1)
     v = free_dofs(nf) / dt / 1e9
@@ -223,17 +282,19 @@ def run_reference(args):
     for k in ("loop_control", "mixed_step", "tiles", "l2"):
         cfg.pop(k, None)
     cfg.update(precision="FP64 (the plain C oracle: CSR assembly, banded Cholesky, JCG, EXP_finite, EXP_true)",
-               parallelism="one host core",
+               parallelism="OpenMP build of the oracle on %d host cores (%s)" % (used, model),
                sample="each step solves the same problem cut to %d^3 (%d levels) instead of %d^3" % (
                    nf, levels, args.n0 << (args.levels - 1)))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gdof/s", "n_gpus": args.gpus,
            "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg,
-           "cpu_baseline": {"value": v, "unit": "Gdof/s", "cores": 1, "kind": "oracle",
-                            "sample": "each step: the plain C FP64 oracle (CSR assembly, banded Cholesky, JCG) on the "
-                                      "same cos_cube problem cut to %d^3 (%d levels), rtol %g; value = free dofs of "
-                                      "that finest level / step time" % (nf, levels, args.rtol)},
+           "cpu_baseline": {"value": v, "unit": "Gdof/s", "cores": used, "kind": "oracle",
+                            "sample": "each step: the plain C FP64 oracle (CSR assembly, banded Cholesky, JCG; OpenMP "
+                                      "build) on the same cos_cube problem cut to %d^3 (%d levels), rtol %g; value = "
+                                      "free dofs of that finest level / step time; set-up %.2f s and solve %.2f s "
+                                      "per step" % (nf, levels, args.rtol, asm / steps, sol / steps),
+                            "host": {"nproc": nproc, "cpu_model": model}},
            "e2e": {"value": v, "unit": "Gdof/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -264,6 +325,28 @@ def profile_kernel(args):
         print(json.dumps({"kernel": w, "workload": args.profile_workload, "n": nfin, "ms": ms, "algorithmic_bytes": nb,
                           "GBps": nb / ms / 1e6, "tiles": [ry, kz], "solve_status": status}))
     s.close()
+
+
+def profile_batched(args):
+    import torch
+    from paper_1506_02983_gb300 import build, inputs
+    build.build()
+    from paper_1506_02983_gb300 import ecmg
+    dev = []
+    for p in inputs.batch_problems():
+        q = dict(p)
+        q["beta"] = torch.as_tensor(p["beta"]).cuda()
+        q["f"] = torch.as_tensor(p["f"]).cuda()
+        dev.append(q)
+    bs = ecmg.BatchSolver(dev, rtol=1e-8, max_iters=args.max_iters, autotune=1)
+    st, status = bs.solve()
+    for w in (0, 1, 2):
+        torch.cuda.nvtx.range_push("kernel_profile")
+        ms, nb = bs.time_kernel(w, -1, reps=2)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"batched_kernel": w, "ms": ms, "algorithmic_bytes": nb, "GBps": nb / ms / 1e6,
+                          "solve_status": status}))
+    bs.close()
 
 
 def bench_extra():
@@ -352,7 +435,8 @@ def bench_batched(args, steps, warmup):
         q["f"] = torch.as_tensor(p["f"]).cuda()
         dev.append(q)
     bs = ecmg.BatchSolver(dev, rtol=1e-8, max_iters=args.max_iters, use_graph=0 if args.eager else 1,
-                          inner_rtol=args.inner_rtol, autotune=1)
+                          inner_rtol=args.inner_rtol, autotune=1,
+                          cg_form=ecmg.ECMG_CG_TWO_PASS if args.batched_form == "two" else ecmg.ECMG_CG_SINGLE_PASS)
     for _ in range(warmup):
         st, status = bs.solve()
         assert status == 0, status
@@ -370,8 +454,12 @@ def bench_batched(args, steps, warmup):
     launches = (ecmg.kernel_launches() - l0) // steps
     # the FP32 stencil (K1) and residual (K2) launches of the last stage alone (every problem's
     # finest level), CUDA events around each launch
-    k1_ms, k1_bytes = bs.time_kernel(0, reps=10)
-    k2_ms, k2_bytes = bs.time_kernel(1, reps=10)
+    two_pass = args.batched_form == "two"
+    if two_pass:
+        k1_ms, k1_bytes = bs.time_kernel(0, reps=10)
+        k2_ms, k2_bytes = bs.time_kernel(1, reps=10)
+    else:
+        k1_ms, k1_bytes = bs.time_kernel(11, reps=10)
     pk = peaks()
     dofs = sum(int(np.prod([(v << (p["levels"] - 1)) - 1 for v in p["n0"]])) for p in probs)
     work = 0  # node-iterations of JCG over all problems and levels
@@ -389,13 +477,16 @@ def bench_batched(args, steps, warmup):
             "replacements": sum(sum(s["updates"]) for s in st), "inner_rtol": args.inner_rtol,
             "loop_control": "host (eager)" if args.eager else "CUDA graph, conditional nodes",
             "tiles": "batched FP32 stencil tile shapes autotuned at creation (per stage, per size class)",
-            "roofline": {"kernel": "batched K1 (bk_pq_tma: TMA-staged FP32 stencil, variable beta) over the 64 "
-                                   "finest levels, alone", "bound": "hbm",
+            "mixed_step": "two-pass (K1 + K2)" if two_pass else "single-pass (one kernel per JCG step)",
+            "roofline": {"kernel": ("batched K1 (bk_pq_tma: TMA-staged FP32 stencil, variable beta)" if two_pass else
+                                    "batched single-pass step (bk_step_tma: TMA-staged FP32 residual update, search "
+                                    "direction, stencil and dots, variable beta)") + " over the 64 finest levels, alone",
+                         "bound": "hbm",
                          "achieved": k1_bytes / k1_ms / 1e6, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": k1_bytes / k1_ms / 1e6 / pk["hbm_gbs"], "algorithmic_bytes_per_launch": k1_bytes,
                          "launch_ms": k1_ms, "peak_source": pk["source"]},
-            "k2_alone": {"kernel": "batched K2 (bk_update) over the 64 finest levels", "ms": k2_ms,
-                         "algorithmic_bytes": k2_bytes, "GBps": k2_bytes / k2_ms / 1e6}}
+            "k2_alone": ({"kernel": "batched K2 (bk_update) over the 64 finest levels", "ms": k2_ms,
+                          "algorithmic_bytes": k2_bytes, "GBps": k2_bytes / k2_ms / 1e6} if two_pass else None)}
 
 
 def main():
@@ -411,6 +502,8 @@ def main():
         return run_reference(args)
     if args.profile_kernel is not None:
         return profile_kernel(args)
+    if args.profile_batched:
+        return profile_batched(args)
     import numpy as np
     import torch
 
@@ -605,7 +698,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, args.cpu_levels)
+        cpu = cpu_baseline(args, args.cpu_levels, args.cpu_levels_omp)
 
     dofs = free_dofs(nf) * world
     node_its = sum(free_dofs(n0 << l) * st_mixed["iters"][l] for l in range(L))

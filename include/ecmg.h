@@ -62,8 +62,10 @@ typedef enum {
 
 enum { ECMG_BC_DIRICHLET = 0, ECMG_BC_ROBIN = 1 };
 /* f is nodal values of f (load b = M f_I + sum_F M_F g_R,I per level), or the finest
- * assembled load functional b_i = f(phi_i) of Sec. 2 (coarse loads b_{l-1} = P^T b_l). */
-enum { ECMG_F_NODAL = 0, ECMG_F_LOAD = 1, ECMG_F_SEPARABLE = 2 };
+ * assembled load functional b_i = f(phi_i) of Sec. 2 (coarse loads b_{l-1} = P^T b_l), or f as
+ * separable terms (ECMG_F_SEPARABLE, below), or f at the points of the 3x3x3 Gauss rule of every
+ * finest element (ECMG_F_GAUSS, below). */
+enum { ECMG_F_NODAL = 0, ECMG_F_LOAD = 1, ECMG_F_SEPARABLE = 2, ECMG_F_GAUSS = 3 };
 enum { ECMG_FP64 = 0, ECMG_MIXED = 1 };
 /* ecmg_apply_operator only: the FP32 stencil kernel of the MIXED iteration itself (K1). */
 enum { ECMG_APPLY_K1 = 2 };
@@ -100,18 +102,26 @@ typedef struct {
     int32_t face_bc[6];     /* faces x-,x+,y-,y+,z-,z+: ECMG_BC_DIRICHLET or ECMG_BC_ROBIN  */
     double robin_alpha[6];  /* alpha on each Robin face (>= 0); ignored on Dirichlet faces  */
     const double* beta;     /* device, finest elements, > 0 (dense element layout)          */
-    const double* f;        /* device, finest nodes: f values or load functional (f_mode)   */
+    const double* f;        /* device: f values or load functional at the finest nodes, or
+                               the compact forms below (f_mode)                             */
     const double* g_D;      /* device, finest nodes, read on Dirichlet nodes; NULL = 0      */
-    const double* g_R;      /* device, finest nodes, read on Robin faces (nodal f_mode only);
-                               NULL = 0                                                      */
-    int32_t f_mode;         /* ECMG_F_NODAL, ECMG_F_LOAD or ECMG_F_SEPARABLE                 */
-    /* Compact inputs (single-problem handles; ecmg_create_batched rejects them):
+    const double* g_R;      /* device, finest nodes, read on Robin faces (ECMG_F_NODAL and
+                               ECMG_F_GAUSS only); NULL = 0                                   */
+    int32_t f_mode;         /* ECMG_F_NODAL, ECMG_F_LOAD, ECMG_F_SEPARABLE or ECMG_F_GAUSS   */
+    /* Compact inputs (single-problem and batched handles):
      * ECMG_F_SEPARABLE: f = sum over f_terms terms of fx(x) fy(y) fz(z); the device array f
      *   holds every factor at the 3-point Gauss-Legendre nodes of every finest element interval
      *   [x_e, x_e + h], in the order x_e + h (1 - sqrt(3/5))/2, x_e + h/2, x_e + h (1 + sqrt(3/5))/2:
      *   f_terms x 3 (nx + ny + nz) doubles, term-major, then x, y, z, interval-major. The library
      *   assembles the load functional int f phi_i of Sec. 2 from them (the rule is exact for
      *   factors of degree <= 4) and its exact coarse restrictions P^T b; g_R must be NULL.
+     * ECMG_F_GAUSS: the device array f holds f at the 27 points of the 3-point Gauss-Legendre rule
+     *   of every finest element: 27 nx ny nz doubles, elements x fastest (index ex + nx (ey + ny ez)),
+     *   then the points qx fastest, qy, qz, each axis in the order above (x_e + h (1 - sqrt(3/5))/2,
+     *   x_e + h/2, x_e + h (1 + sqrt(3/5))/2). The library assembles the load functional int f phi_i
+     *   of Sec. 2 with that rule on every element (plus the face mass of the nodal g_R on Robin faces)
+     *   and its coarse restrictions P^T b; f may be any function (singular ones included, since no
+     *   point lies on an element's boundary).
      * gD_terms > 0: g_D = sum over gD_terms terms of gx(x) gy(y) gz(z); the device array g_D holds
      *   the factors at the finest nodes: gD_terms x ((nx+1) + (ny+1) + (nz+1)) doubles,
      *   term-major, then x, y, z.
@@ -143,9 +153,8 @@ typedef struct {
                                there)                                        [TOLERANCE]   */
     int32_t sched_mL;       /* FIXED: m_L, the steps on the finest level, >= 1  [4]         */
     double sched_beta;      /* FIXED: beta of eq. (ee), 1..64                   [4.0]       */
-    int32_t cg_form;        /* MIXED: ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS or ECMG_CG_AUTO on
-                               the single-problem path (batched handles run TWO_PASS for
-                               AUTO and reject SINGLE_PASS)                  [AUTO]        */
+    int32_t cg_form;        /* MIXED: ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS or ECMG_CG_AUTO (batched
+                               handles run TWO_PASS for AUTO)                   [AUTO]     */
 } ecmg_options;
 
 /* Per-solve statistics, one entry per level (coarsest first). */
@@ -281,8 +290,10 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
  * ecmg_solve; it overwrites the level's work vectors and U~ (kernel 3 uses U~ as its
  * iterate); U and W are never changed. Synchronises the stream.
  * Batched handles: `level` is a stage of the batched solve (-1 = the last, where every problem
- * works on its finest level) and which is 0 (the batched K1 over every item of the stage) or 1
- * (the batched K2); bytes_out sums the items' algorithmic bytes. The launches overwrite the
+ * works on its finest level) and which is 0 (the batched K1 over every item of the stage), 1 (the
+ * batched K2), 2 (the batched FP64 residual with its max |x| pass) or 11 (the batched single-pass
+ * step, on batches created with ECMG_CG_SINGLE_PASS); bytes_out sums the items' algorithmic
+ * bytes. The launches overwrite the
  * items' work vectors and states, which the next ecmg_solve_batched sets up afresh. */
 ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32_t reps,
                              double* ms_out, double* bytes_out);

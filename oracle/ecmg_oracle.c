@@ -45,6 +45,28 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int32_t or_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+static double wall_seconds(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 /* ----------------------------------------------------------------------------------- */
 /* indexing                                                                            */
@@ -291,6 +313,7 @@ double or_apply_at(const int32_t n[3], const double h[3], const double* beta, co
 void or_csr_matvec(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
                    const double* x, double* y)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < N; ++r) {
         double s = 0.0;
         for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) s += val[q] * x[col[q]];
@@ -395,6 +418,7 @@ int or_pcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
     int status = 0;
 
     /* Jacobi preconditioner: the diagonal of A on free nodes (identity for plain CG) */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         double d = 0.0;
         for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) if (col[t] == i) d = val[t];
@@ -410,20 +434,24 @@ int or_pcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
 
     /* r = b - A x on free nodes */
     or_csr_matvec(N, rowptr, col, val, x, q);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) r[i] = mask[i] ? b[i] - q[i] : 0.0;
 
     int32_t k = 0;
     double rr = dot_masked(N, mask, r, r);
     if (fixed ? max_iters > 0 : sqrt(rr) > rtol * fh) {
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
         double rho = dot_masked(N, mask, r, z);
         for (;;) {
             if (k >= max_iters) { status = fixed ? 0 : 3; break; }
             or_csr_matvec(N, rowptr, col, val, p, q);
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < N; ++i) if (!mask[i]) q[i] = 0.0;
             double pq = dot_masked(N, mask, p, q);
             if (!(pq > 0.0) || !isfinite(pq)) { status = 4; break; }
             double alpha = rho / pq;
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < N; ++i) {
                 x[i] += alpha * p[i];
                 r[i] -= alpha * q[i];
@@ -432,9 +460,11 @@ int or_pcg(int64_t N, const int64_t* rowptr, const int64_t* col, const double* v
             rr = dot_masked(N, mask, r, r);
             if (!fixed && sqrt(rr) <= rtol * fh) break;
             if (fixed && k >= max_iters) break;
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < N; ++i) z[i] = dinv[i] * r[i];
             double rho_new = dot_masked(N, mask, r, z);
             double beta = rho_new / rho;
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
             rho = rho_new;
         }
@@ -896,6 +926,7 @@ int or_ecmg_ex(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_
     }
     memset(W_all, 0, (size_t)off[L] * sizeof(double));
     memset(Ut_all, 0, (size_t)off[L] * sizeof(double));
+    double t0 = wall_seconds();
 
     /* per-level data, finest first: beta by averaging, f / gD / gR by injection (or the load
      * functional by restriction in the load mode) */
@@ -923,8 +954,10 @@ int or_ecmg_ex(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_
         }
     }
 
+    st->seconds_assembly = wall_seconds() - t0;  /* per-level data (coarse beta, loads, g_D) */
     int status = 0;
     for (int l = 0; l < L && !status; ++l) {
+        const double ta = wall_seconds();
         const int32_t* n = nl[l];
         int64_t N = num_nodes(n);
         double h[3];
@@ -940,6 +973,8 @@ int or_ecmg_ex(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_
         else or_load_nodal(n, h, fl[l], p->face_bc, gRl[l], b);
         or_dirichlet_mask(n, p->face_bc, mask);
         for (int64_t i = 0; i < N; ++i) if (!mask[i]) gext[i] = gDl[l][i];
+        const double tb = wall_seconds();
+        st->seconds_assembly += tb - ta;
 
         double* U = U_all + off[l];
         if (l < 2) {
@@ -974,6 +1009,7 @@ int or_ecmg_ex(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_
             /* line 10: U~ = EXP_true(u_h, u_2h) */
             or_exp_true(n, U, U_all + off[l - 1], Ut_all + off[l]);
         }
+        st->seconds_solve += wall_seconds() - tb;
         free(rowptr); free(col); free(val); free(b); free(gext); free(mask);
     }
     for (int l = 0; l < L; ++l) { free(beta[l]); free(fl[l]); free(gDl[l]); free(gRl[l]); }

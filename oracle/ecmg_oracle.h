@@ -107,7 +107,15 @@ typedef struct {
     double rel_res[16];    /* true ||b - A u|| / ||f_h|| on exit, per level               */
     double rhs_norm[16];   /* ||f_h|| (lifted free-node load) per level                   */
     int32_t status;        /* 0 ok, 1 invalid input, 2 singular, 3 no convergence         */
+    double seconds_assembly; /* wall time of the set-up: level data, CSR assembly, loads   */
+    double seconds_solve;    /* wall time of DSOLVE, EXP_finite, JCG and EXP_true          */
 } or_stats;
+
+/* Threads for the loops that may run in parallel (CSR matrix-vector products and the
+ * element-wise vector updates of JCG; every row and element is computed exactly as with one
+ * thread, and the dot products stay sequential, so the results do not depend on the thread
+ * count). Returns the threads that will be used: 1 unless built with OpenMP. */
+int32_t or_set_threads(int32_t n);
 
 int or_ecmg(const or_problem* p, double rtol, int32_t max_iters, int32_t exp_variant,
             double* U_all, double* W_all, double* Ut_all, or_stats* st);

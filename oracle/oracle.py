@@ -18,24 +18,37 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ecmg_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 
 DIRICHLET, ROBIN = 0, 1
 F_NODAL, F_LOAD = 0, 1
 EXP_SERENDIPITY20, EXP_LAGRANGE27 = 0, 1
 
 
+def _compile(target: str, extra: list, force: bool) -> str:
+    os.makedirs(os.path.dirname(target), exist_ok=True)
+    hdr = os.path.join(_HERE, "ecmg_oracle.h")
+    if force or not os.path.exists(target) or os.path.getmtime(target) < max(os.path.getmtime(_SRC),
+                                                                             os.path.getmtime(hdr)):
+        tmp = target + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, target)
+    return target
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into ``oracle/_build/liboracle.so``.
+    """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` (one thread).
 
     ``-ffp-contract=off`` keeps x86 and Arm hosts bit-identical (no fused multiply-add).
     """
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    return _compile(_LIB, [], force)
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source with OpenMP (``liboracle_omp.so``): the CSR products and the element-wise
+    vector updates of JCG run on several threads, with results equal to the one-thread build."""
+    return _compile(_LIB_OMP, ["-fopenmp"], force)
 
 
 class _Problem(C.Structure):
@@ -48,7 +61,8 @@ class _Problem(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("iters", C.c_int32 * 16), ("rel_res", C.c_double * 16),
-                ("rhs_norm", C.c_double * 16), ("status", C.c_int32)]
+                ("rhs_norm", C.c_double * 16), ("status", C.c_int32),
+                ("seconds_assembly", C.c_double), ("seconds_solve", C.c_double)]
 
 
 _lib = None
@@ -57,46 +71,65 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        D, I64, I32 = C.c_double, C.c_int64, C.c_int32
-        P = C.c_void_p
-        _lib.or_assemble_csr.restype = I64
-        _lib.or_assemble_csr.argtypes = [P, P, P, P, P, P, P, P]
-        _lib.or_element_matrix.argtypes = [D, D, D, P]
-        _lib.or_element_mass.argtypes = [D, D, D, P]
-        _lib.or_face_mass.argtypes = [D, D, P]
-        _lib.or_dirichlet_mask.argtypes = [P, P, P]
-        _lib.or_load_nodal.argtypes = [P, P, P, P, P, P]
-        _lib.or_csr_matvec.argtypes = [I64, P, P, P, P, P]
-        _lib.or_coarsen_beta.argtypes = [P, P, P]
-        _lib.or_inject.argtypes = [P, P, P]
-        _lib.or_restrict_load.argtypes = [P, P, P]
-        _lib.or_jcg.restype = C.c_int
-        _lib.or_jcg.argtypes = [I64, P, P, P, P, P, P, P, D, I32, P, P, P]
-        _lib.or_pcg.restype = C.c_int
-        _lib.or_pcg.argtypes = [I64, P, P, P, P, P, P, P, D, I32, I32, I32, P, P, P]
-        _lib.or_pcg_single_pass.restype = C.c_int
-        _lib.or_pcg_single_pass.argtypes = [I64, P, P, P, P, P, P, P, D, I32, I32, P, P, P]
-        _lib.or_dsolve_banded.restype = C.c_int
-        _lib.or_dsolve_banded.argtypes = [P, I64, P, P, P, P, P, P]
-        _lib.or_serendipity.argtypes = [D, D, D, P]
-        _lib.or_serendipity_nodes.argtypes = [P]
-        _lib.or_exp_finite.argtypes = [P, P, P, P]
-        _lib.or_exp_finite27.argtypes = [P, P, P, P]
-        _lib.or_exp_true.argtypes = [P, P, P, P]
-        _lib.or_apply_at.restype = D
-        _lib.or_apply_at.argtypes = [P, P, P, P, P, P, I64, I64, I64]
-        _lib.or_exp_finite_at.restype = D
-        _lib.or_exp_finite_at.argtypes = [P, P, P, I64, I64, I64]
-        _lib.or_exp_true_at.restype = D
-        _lib.or_exp_true_at.argtypes = [P, P, P, I64, I64, I64]
-        _lib.or_ecmg_ex.restype = C.c_int
-        _lib.or_ecmg_ex.argtypes = [C.POINTER(_Problem), D, I32, I32, I32, I32, I32, D, P, P, P, C.POINTER(_Stats)]
-        _lib.or_schedule_steps.restype = I32
-        _lib.or_schedule_steps.argtypes = [I32, I32, I32, D]
-        _lib.or_ecmg.restype = C.c_int
-        _lib.or_ecmg.argtypes = [C.POINTER(_Problem), D, I32, I32, P, P, P, C.POINTER(_Stats)]
-        _lib.or_norms.argtypes = [I64, P, P, P, P]
+        _lib = _load(build())
+    return _lib
+
+
+_lib_omp = None
+
+
+def lib_omp():
+    """The OpenMP build (see build_omp)."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _load(build_omp())
+    return _lib_omp
+
+
+def _load(path):
+    """Load one build of the oracle and declare its entry points."""
+    _lib = C.CDLL(path)
+    D, I64, I32 = C.c_double, C.c_int64, C.c_int32
+    P = C.c_void_p
+    _lib.or_assemble_csr.restype = I64
+    _lib.or_assemble_csr.argtypes = [P, P, P, P, P, P, P, P]
+    _lib.or_element_matrix.argtypes = [D, D, D, P]
+    _lib.or_element_mass.argtypes = [D, D, D, P]
+    _lib.or_face_mass.argtypes = [D, D, P]
+    _lib.or_dirichlet_mask.argtypes = [P, P, P]
+    _lib.or_load_nodal.argtypes = [P, P, P, P, P, P]
+    _lib.or_csr_matvec.argtypes = [I64, P, P, P, P, P]
+    _lib.or_coarsen_beta.argtypes = [P, P, P]
+    _lib.or_inject.argtypes = [P, P, P]
+    _lib.or_restrict_load.argtypes = [P, P, P]
+    _lib.or_jcg.restype = C.c_int
+    _lib.or_jcg.argtypes = [I64, P, P, P, P, P, P, P, D, I32, P, P, P]
+    _lib.or_set_threads.restype = I32
+    _lib.or_set_threads.argtypes = [I32]
+    _lib.or_pcg.restype = C.c_int
+    _lib.or_pcg.argtypes = [I64, P, P, P, P, P, P, P, D, I32, I32, I32, P, P, P]
+    _lib.or_pcg_single_pass.restype = C.c_int
+    _lib.or_pcg_single_pass.argtypes = [I64, P, P, P, P, P, P, P, D, I32, I32, P, P, P]
+    _lib.or_dsolve_banded.restype = C.c_int
+    _lib.or_dsolve_banded.argtypes = [P, I64, P, P, P, P, P, P]
+    _lib.or_serendipity.argtypes = [D, D, D, P]
+    _lib.or_serendipity_nodes.argtypes = [P]
+    _lib.or_exp_finite.argtypes = [P, P, P, P]
+    _lib.or_exp_finite27.argtypes = [P, P, P, P]
+    _lib.or_exp_true.argtypes = [P, P, P, P]
+    _lib.or_apply_at.restype = D
+    _lib.or_apply_at.argtypes = [P, P, P, P, P, P, I64, I64, I64]
+    _lib.or_exp_finite_at.restype = D
+    _lib.or_exp_finite_at.argtypes = [P, P, P, I64, I64, I64]
+    _lib.or_exp_true_at.restype = D
+    _lib.or_exp_true_at.argtypes = [P, P, P, I64, I64, I64]
+    _lib.or_ecmg_ex.restype = C.c_int
+    _lib.or_ecmg_ex.argtypes = [C.POINTER(_Problem), D, I32, I32, I32, I32, I32, D, P, P, P, C.POINTER(_Stats)]
+    _lib.or_schedule_steps.restype = I32
+    _lib.or_schedule_steps.argtypes = [I32, I32, I32, D]
+    _lib.or_ecmg.restype = C.c_int
+    _lib.or_ecmg.argtypes = [C.POINTER(_Problem), D, I32, I32, P, P, P, C.POINTER(_Stats)]
+    _lib.or_norms.argtypes = [I64, P, P, P, P]
     return _lib
 
 
@@ -242,6 +275,28 @@ def load_functional(n, lo, hi, f, q=6, faces=()):
                     b[c2:c2 + nz, idx, c1:c1 + nx] += v
                 else:
                     b[idx, c2:c2 + ny, c1:c1 + nx] += v
+    return b
+
+
+def load_gauss(n, h, samples):
+    """Load functional b_i = int f phi_i of Sec. 2 with f given at the 27 points of the 3-point
+    Gauss-Legendre rule of every element (the ECMG_F_GAUSS layout: elements x fastest, then the
+    points qx fastest, qy, qz). Written as the definition: on every element the rule's weights
+    times f times each of the element's 8 trilinear hats at the points, added into the hat's
+    node. Shape (nz+1, ny+1, nx+1)."""
+    nx, ny, nz = (int(v) for v in n)
+    F = np.asarray(samples, dtype=np.float64).reshape(nz, ny, nx, 3, 3, 3)  # [ez, ey, ex, qz, qy, qx]
+    g, w = gauss3_unit()
+    b = np.zeros((nz + 1, ny + 1, nx + 1))
+    vol = h[0] * h[1] * h[2]
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                phx = g if cx else 1.0 - g
+                phy = g if cy else 1.0 - g
+                phz = g if cz else 1.0 - g
+                wphi = np.einsum("c,b,a->cba", w * phz, w * phy, w * phx)
+                b[cz:cz + nz, cy:cy + ny, cx:cx + nx] += vol * np.einsum("kjicba,cba->kji", F, wphi)
     return b
 
 
@@ -425,13 +480,16 @@ def norms(a, b=None):
 
 # ---- the whole method -------------------------------------------------------------------
 def ecmg(prob, rtol, max_iters=100000, exp_variant=EXP_SERENDIPITY20, precond=1, schedule=0, mL=0,
-         sched_beta=0.0):
+         sched_beta=0.0, threads=None):
     """Run Alg. 4 on a problem dict (see ``paper_1506_02983_gb300.inputs``). precond 1 = JCG
     (ECMG_jcg), 0 = plain CG (ECMG_cg); schedule 1 = the fixed step counts of Alg. 3 (eq. (ee),
-    m_j = ceil(mL * sched_beta^(L-j))) instead of the tolerance.
+    m_j = ceil(mL * sched_beta^(L-j))) instead of the tolerance. threads: None runs the one-thread
+    build; a number runs the OpenMP build on that many threads (0: its default).
 
     Returns (levels, stats): levels[l] = dict(n=..., U=..., W=..., Ut=...) with nodal arrays
-    shaped (nz+1, ny+1, nx+1); stats has per-level iters, rel_res, rhs_norm and status.
+    shaped (nz+1, ny+1, nx+1); stats has per-level iters, rel_res, rhs_norm and status, the
+    wall seconds of the set-up (seconds_assembly) and of the solves (seconds_solve), and the
+    threads used.
     """
     L = int(prob["levels"])
     n0 = [int(v) for v in prob["n0"]]
@@ -454,8 +512,10 @@ def ecmg(prob, rtol, max_iters=100000, exp_variant=EXP_SERENDIPITY20, precond=1,
     P.beta, P.f, P.gD, P.gR = _p(beta), _p(f), _p(gD), _p(gR)
     P.f_mode = int(prob.get("f_mode", F_NODAL))
     S = _Stats()
-    lib().or_ecmg_ex(C.byref(P), rtol, max_iters, int(exp_variant), int(precond), int(schedule), int(mL),
-                     float(sched_beta), _p(U), _p(W), _p(Ut), C.byref(S))
+    lb = lib() if threads is None else lib_omp()
+    used = lb.or_set_threads(int(threads or 0))
+    lb.or_ecmg_ex(C.byref(P), rtol, max_iters, int(exp_variant), int(precond), int(schedule), int(mL),
+                  float(sched_beta), _p(U), _p(W), _p(Ut), C.byref(S))
     out = []
     off = 0
     for l in range(L):
@@ -465,5 +525,6 @@ def ecmg(prob, rtol, max_iters=100000, exp_variant=EXP_SERENDIPITY20, precond=1,
         out.append(dict(n=n, U=U[sl].reshape(shp), W=W[sl].reshape(shp), Ut=Ut[sl].reshape(shp)))
         off += sizes[l]
     stats = dict(iters=list(S.iters[:L]), rel_res=list(S.rel_res[:L]),
-                 rhs_norm=list(S.rhs_norm[:L]), status=S.status)
+                 rhs_norm=list(S.rhs_norm[:L]), status=S.status, seconds_assembly=S.seconds_assembly,
+                 seconds_solve=S.seconds_solve, threads=used)
     return out, stats

@@ -42,6 +42,9 @@ struct Batch {
     BCtl* ctl = nullptr;
     int robin = 0, cube = 1;       // kernel variants: any Robin face in the batch; all elements cubic
     PlaneMaps* d_maps = nullptr;   // device, the tensor maps of every item's FP32 vectors
+    std::vector<ecmg_problem> probs;  // the problems (device input pointers resolved)
+    std::vector<double*> Hf;       // per problem: 1D hat integrals of separable f (else null)
+    bool sp = false;               // FP32 steps in the single-pass form (one kernel per step)
     std::vector<int> stage_ry;     // node rows per thread of the TMA-staged K1 at each stage
     int item(int p, int l) const { return first[p] + l; }
 };
@@ -198,7 +201,8 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
     if (!p->f) return fail(ECMG_ERR_INVALID_ARG, "f is required");
     if (!p->beta && !(p->beta_const > 0.0 && std::isfinite(p->beta_const)))
         return fail(ECMG_ERR_INVALID_ARG, "beta is NULL and beta_const is not a finite positive number");
-    if (p->f_mode != ECMG_F_NODAL && p->f_mode != ECMG_F_LOAD && p->f_mode != ECMG_F_SEPARABLE)
+    if (p->f_mode != ECMG_F_NODAL && p->f_mode != ECMG_F_LOAD && p->f_mode != ECMG_F_SEPARABLE &&
+        p->f_mode != ECMG_F_GAUSS)
         return fail(ECMG_ERR_INVALID_ARG, "bad f_mode");
     if (p->f_mode == ECMG_F_SEPARABLE) {
         if (p->f_terms < 1 || p->f_terms > 64) return fail(ECMG_ERR_INVALID_ARG, "f_terms must be 1..64");
@@ -373,15 +377,16 @@ void record_setup(Rec& R)
         if (l == L - 1) {
             if (p.beta) pack_elements(v.g, p.beta, v.beta, s);
             else fill_beta(v.g, p.beta_const, v.beta, s);
+            if (p.g_R) pack_nodal(v.g, p.g_R, v.gR, s);
             if (p.f_mode == ECMG_F_SEPARABLE) sep_load_finest(v.g, p.f_terms, p.f, v.Hf, v.b, s);
+            else if (p.f_mode == ECMG_F_GAUSS) gauss_load(v.g, v.op, p.f, p.g_R ? v.gR : nullptr, v.b, s);
             else pack_nodal(v.g, p.f, p.f_mode == ECMG_F_LOAD ? v.b : v.f, s);  // the load is b itself
             if (p.g_D && p.gD_terms > 0) sep_nodal(v.g, p.gD_terms, p.g_D, v.gD, s);
             else if (p.g_D) pack_dirichlet(v.g, v.op, p.g_D, v.gD, s);
-            if (p.g_R) pack_nodal(v.g, p.g_R, v.gR, s);
         } else {
             Level& u = h->lv[l + 1];
             coarsen_beta(v.g, u.beta, u.g, v.beta, s);
-            if (p.f_mode == ECMG_F_LOAD) restrict_load(v.g, u.b, u.g, v.b, s);
+            if (p.f_mode == ECMG_F_LOAD || p.f_mode == ECMG_F_GAUSS) restrict_load(v.g, u.b, u.g, v.b, s);
             else if (p.f_mode == ECMG_F_SEPARABLE) sep_coarsen(v.g, u.g, p.f_terms, u.Hf, v.Hf, true, v.b, s);
             else inject_nodal(v.g, u.f, u.g, v.f, s);
             if (p.g_D && p.gD_terms > 0)
@@ -713,6 +718,14 @@ void record_batched(Rec& R)
     Batch& B = *h->batch;
     const ecmg_options& o = h->opt;
     const BItem* items = B.d_items;
+    // compact inputs: beta, the load and g_D of the finest level assembled per problem first
+    for (int p = 0; p < B.n; ++p) {
+        const ecmg_problem& pr = B.probs[p];
+        const BItem& it = B.items[B.item(p, B.L[p] - 1)];
+        if (!pr.beta) fill_beta(it.g, pr.beta_const, it.beta, R.s());
+        if (pr.f_mode == ECMG_F_SEPARABLE) sep_load_finest(it.g, pr.f_terms, pr.f, B.Hf[p], it.b, R.s());
+        if (pr.gD_terms > 0) sep_nodal(it.g, pr.gD_terms, pr.g_D, it.gD, R.s());
+    }
     for (int d = 0; d < B.Lmax; ++d) {
         const std::vector<int> ids = depth_items(B, d);
         blaunch_setup(items, make_launch(B, ids, BG_NODES), make_launch(B, ids, BG_ELEMS), R.s());
@@ -723,10 +736,45 @@ void record_batched(Rec& R)
         blaunch_level_start(items, make_launch(B, ids, BG_ONE), make_launch(B, ids, BG_NODES),
                             make_launch(B, ids, BG_ROWS), B.robin, B.cube, o.inner_rtol, R.s());
         blaunch_guess(items, make_launch(B, ids2, BG_EXPF), make_launch(B, ids, BG_FLAT), o.exp_variant, R.s());
-        const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_FLAT);
+        const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_SPAN);
         const int ry = B.stage_ry[s];
         const BLaunch k1 = make_launch_k1(B, ids, ry);
-        if (R.graph) {
+        if (B.sp) {
+            // single-pass steps: step `half` reads buffer set `half` (A: r32, q32, pA32; B: r32B,
+            // q32B, pB32) and writes the other; a replacement folds the other set's p and writes
+            // its residual there, where the next step reads it
+            if (R.graph) {
+                const cudaGraphConditionalHandle loop = R.new_handle();
+                blaunch_absmax(items, flat, R.s());
+                blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, CondHandles{loop, 0, 1}, R.s(), 0);
+                R.open(loop, cudaGraphCondTypeWhile);
+                for (int half = 0; half < 2; ++half) {
+                    const int o = half ^ 1;
+                    const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
+                    blaunch_step_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, o, B.ctl, CondHandles{loop, upd, 1},
+                                     R.s());
+                    R.open(upd, cudaGraphCondTypeIf);
+                    blaunch_fold(items, flat, o, R.s());
+                    blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, CondHandles{loop, 0, 1}, R.s(), o);
+                    R.close();
+                }
+                R.close();
+            } else {
+                const CondHandles none{0, 0, 0};
+                blaunch_absmax(items, flat, R.s());
+                blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, none, R.s(), 0);
+                int half = 0;
+                while (any_state(h, ids, false)) {
+                    const int o = half ^ 1;
+                    blaunch_step_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, o, B.ctl, none, R.s());
+                    if (any_state(h, ids, true)) {
+                        blaunch_fold(items, flat, o, R.s());
+                        blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, none, R.s(), o);
+                    }
+                    half = o;
+                }
+            }
+        } else if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
             blaunch_absmax(items, flat, R.s());
             blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, CondHandles{loop, 0, 1}, R.s());
@@ -958,7 +1006,7 @@ double time_batch_launch(ecmg_handle* h, const std::vector<int>& ids, int which,
     tmpl.thresh2 = -1.0;
     tmpl.inner2 = -1.0;
     const size_t ni = B.items.size();
-    const BLaunch k1 = make_launch_k1(B, ids, ry), flat = make_launch(B, ids, BG_FLAT);
+    const BLaunch k1 = make_launch_k1(B, ids, ry), flat = make_launch(B, ids, BG_SPAN);
     const CondHandles none{0, 0, 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double total = 0.0;
@@ -971,7 +1019,12 @@ double time_batch_launch(ecmg_handle* h, const std::vector<int>& ids, int which,
             ck(cudaMemcpyAsync(B.states, B.host_states, sizeof(SolveState) * ni, cudaMemcpyHostToDevice, s));
             ck(cudaEventRecord(e0, s));
             if (which == 0) blaunch_pq_tma(B.d_items, B.d_maps, k1, ry, B.robin, B.cube, 0, 1, s);
-            else blaunch_update(B.d_items, flat, B.ctl, none, s);
+            else if (which == 11) blaunch_step_tma(B.d_items, B.d_maps, k1, ry, B.robin, B.cube, 0, 1, B.ctl, none, s);
+            else if (which == 2) {
+                // the FP64 residual of every item (its max |x| first), into r, reported only
+                blaunch_absmax(B.d_items, flat, s);
+                blaunch_res(B.d_items, make_launch(B, ids, BG_STENCIL), B.robin, B.cube, RES_REPORT, B.ctl, none, s);
+            } else blaunch_update(B.d_items, flat, B.ctl, none, s);
             ck(cudaEventRecord(e1, s));
             ck(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -1017,7 +1070,7 @@ void batch_autotune(ecmg_handle* h, int reps)
             for (int kz : kzs) {
                 set_kz(ids, kz);
                 upload_items(h);
-                const double ms = time_batch_launch(h, ids, 0, ry, reps);
+                const double ms = time_batch_launch(h, ids, B.sp ? 11 : 0, ry, reps);
                 if (ms < best) {
                     best = ms;
                     best_ry = ry;
@@ -1042,7 +1095,7 @@ void batch_autotune(ecmg_handle* h, int reps)
                     if (kz == best_kz) continue;
                     set_kz(c, kz);
                     upload_items(h);
-                    const double ms = time_batch_launch(h, ids, 0, best_ry, reps);
+                    const double ms = time_batch_launch(h, ids, B.sp ? 11 : 0, best_ry, reps);
                     if (ms < best) {
                         best = ms;
                         ckz = kz;
@@ -1245,13 +1298,9 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
     *out = nullptr;
     if (n < 1 || n > BATCH_MAX) return fail(ECMG_ERR_INVALID_ARG, "batch size must be 1..128");
     if (opt->precision != ECMG_MIXED) return fail(ECMG_ERR_INVALID_ARG, "batched solves run in MIXED precision");
-    if (opt->cg_form == ECMG_CG_SINGLE_PASS)
-        return fail(ECMG_ERR_INVALID_ARG, "batched solves run the two-pass step");
     for (int p = 0; p < n; ++p) {
         ecmg_status s = validate(probs + p, opt);
         if (s != ECMG_OK) return s;
-        if (probs[p].f_mode == ECMG_F_SEPARABLE || probs[p].gD_terms > 0 || !probs[p].beta)
-            return fail(ECMG_ERR_INVALID_ARG, "batched problems take dense beta, f and g_D");
     }
     std::vector<ecmg_problem> resolved(probs, probs + n);
     for (auto& q : resolved)
@@ -1266,6 +1315,9 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
     h->batch = new Batch();
     Batch& B = *h->batch;
     B.n = n;
+    B.sp = opt->cg_form == ECMG_CG_SINGLE_PASS;
+    B.probs.assign(probs, probs + n);
+    B.Hf.assign(n, nullptr);
     try {
         for (int i = 0; i < 3; ++i) ck(cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
         int nitems = 0;
@@ -1290,7 +1342,15 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
                 it.level = l;
                 it.problem = p;
                 it.depth = pr.levels - 1 - l;
-                it.fmode = pr.f_mode;
+                // separable f: the finest load is assembled before the batched set-up, and the
+                // coarse ones are its restrictions, as for a given load functional
+                it.fmode = pr.f_mode == ECMG_F_SEPARABLE ? ECMG_F_LOAD : pr.f_mode;
+                if (it.depth == 0) {
+                    it.pre_beta = pr.beta ? 0 : 1;
+                    it.pre_load = pr.f_mode == ECMG_F_SEPARABLE ? 1 : 0;
+                    it.pre_gD = pr.gD_terms > 0 ? 1 : 0;
+                    if (pr.f_mode == ECMG_F_SEPARABLE) B.Hf[p] = dalloc<double>(h, sep_factor_len(it.g, pr.f_terms));
+                }
                 it.kz = std::min(32, it.g.nz + 1);
                 it.k1kz = 16;
                 it.fixed = (opt->schedule == ECMG_SCHED_FIXED && l >= 2) ? 1 : 0;
@@ -1313,8 +1373,13 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
                 it.pB32 = dalloc<float>(h, nv);
                 it.q32 = dalloc<float>(h, nv);
                 it.e32 = dalloc<float>(h, nv);
+                if (B.sp) {
+                    it.r32B = dalloc<float>(h, nv);
+                    it.q32B = dalloc<float>(h, nv);
+                }
                 it.st = B.states + B.item(p, l);
-                it.part = dalloc<double>(h, 2 * (int64_t)bitem_partials(it));
+                // 7 sums per block in the single-pass step on the general path
+                it.part = dalloc<double>(h, (B.sp ? 8 : 2) * (int64_t)bitem_partials(it));
                 if (it.depth == 0) {
                     it.in_beta = pr.beta;
                     it.in_f = pr.f;
@@ -1347,6 +1412,8 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
         for (int i = 0; i < nitems; ++i) {
             const BItem& it = B.items[i];
             if (!make_plane_maps(&maps[i], it.r32, it.pA32, it.pB32, it.dinv32, it.beta32, it.e32, it.g))
+                throw CudaFail{cudaErrorInvalidValue};
+            if (B.sp && !make_plane_maps_sp(&maps[i], it.r32B, it.q32, it.q32B, it.g))
                 throw CudaFail{cudaErrorInvalidValue};
         }
         B.d_maps = dalloc<PlaneMaps>(h, nitems);
@@ -1597,14 +1664,22 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
         Batch& B = *h->batch;
         const int s = level < 0 ? B.Lmax - 1 : level;
         if (s < 0 || s >= B.Lmax) return fail(ECMG_ERR_INVALID_ARG, "bad stage");
-        if (which != 0 && which != 1) return fail(ECMG_ERR_INVALID_ARG, "batched handles time kernels 0 and 1");
+        if (which != 0 && which != 1 && which != 2 && which != 11)
+            return fail(ECMG_ERR_INVALID_ARG, "batched handles time kernels 0, 1, 2 and 11");
+        if (which != 2 && (which == 11) != B.sp)
+            return fail(ECMG_ERR_INVALID_ARG, "kernel 11 on single-pass batches, 0 and 1 on two-pass ones");
         const std::vector<int> ids = stage_items(B, s);
         double bytes = 0.0;
         for (int id : ids) {
             const BItem& it = B.items[id];
             const double N = (double)(it.g.nx + 1) * (it.g.ny + 1) * (it.g.nz + 1);
             const double E = (double)it.g.nx * it.g.ny * it.g.nz;
-            bytes += which == 0 ? 28.0 * (double)bk1_nodes(it) + 4.0 * E : 16.0 * N;
+            // K1 28 N_f + 4 E; K2 16 N; the residual reads x, b, beta, D^-1 and writes r (24 N + 8 E,
+            // its max |x| pass 8 N more); the single-pass step 36 N_f + 4 E
+            bytes += which == 0    ? 28.0 * (double)bk1_nodes(it) + 4.0 * E
+                     : which == 1  ? 16.0 * N
+                     : which == 2  ? 32.0 * N + 8.0 * E
+                                   : 36.0 * (double)bk1_nodes(it) + 4.0 * E;
         }
         *bytes_out = bytes;
         try {

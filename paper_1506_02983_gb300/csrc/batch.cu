@@ -48,6 +48,19 @@ __device__ __forceinline__ Slot find_slot(const BLaunch& L)
     return Slot{L.id[lo], b - L.start[lo], L.start[lo + 1] - L.start[lo]};
 }
 
+// Element range [base, end) of a BG_SPAN block: chunk c of node plane k's span.
+struct SpanRange {
+    int64_t base, end;
+};
+__device__ __forceinline__ SpanRange span_of(const Grid& g, int lb)
+{
+    const int nv = span_v4(g);
+    const int nch = (nv + SPAN_CHUNK_V4 - 1) / SPAN_CHUNK_V4;
+    const int k = lb / nch, c = lb - k * nch;
+    const int64_t p0 = g.off(0, 0, k);
+    return SpanRange{p0 + 4 * (int64_t)c * SPAN_CHUNK_V4, p0 + 4 * (int64_t)min((c + 1) * SPAN_CHUNK_V4, nv)};
+}
+
 // ---- reductions --------------------------------------------------------------------------------
 template <int NP>
 __device__ __forceinline__ void bblock_sum(double (&v)[NP], double* sh)
@@ -180,8 +193,10 @@ __global__ void __launch_bounds__(256) bk_setup_beta(const BItem* __restrict__ i
     int i, j, k;
     if (!elem_of(it.g, sl.lb, i, j, k)) return;
     const int64_t o = it.g.off(i, j, k);
-    const double v = it.depth == 0 ? it.in_beta[i + (int64_t)it.g.nx * (j + (int64_t)it.g.ny * k)]
-                                   : coarse_beta_at(it.fbeta, it.gf, i, j, k);
+    double v;
+    if (it.depth > 0) v = coarse_beta_at(it.fbeta, it.gf, i, j, k);
+    else if (it.pre_beta) v = it.beta[o];  // one beta, filled before
+    else v = it.in_beta[i + (int64_t)it.g.nx * (j + (int64_t)it.g.ny * k)];
     it.beta[o] = v;
     it.beta32[o] = (float)v;
 }
@@ -199,8 +214,9 @@ __global__ void __launch_bounds__(256) bk_setup_nodes(const BItem* __restrict__ 
     const int64_t o = g.off(i, j, k);
     if (it.depth == 0) {
         const int64_t t = i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);
-        it.f[o] = it.in_f[t];
-        it.gD[o] = it.in_gD ? it.in_gD[t] : 0.0;
+        // Gauss-point f is read by the load kernel; a prefilled load needs no f
+        if (it.fmode != ECMG_F_GAUSS && !it.pre_load) it.f[o] = it.in_f[t];
+        if (!it.pre_gD) it.gD[o] = it.in_gD ? it.in_gD[t] : 0.0;
         it.gR[o] = it.in_gR ? it.in_gR[t] : 0.0;
     } else {
         const int64_t of = it.gf.off(2 * i, 2 * j, 2 * k);
@@ -222,7 +238,10 @@ __global__ void __launch_bounds__(256) bk_setup_load(const BItem* __restrict__ i
     if (!node_of(it.g, sl.lb, i, j, k)) return;
     const int64_t o = it.g.off(i, j, k);
     if (it.fmode == ECMG_F_NODAL) it.b[o] = nodal_load_at(it.g, it.op, it.f, it.gR, i, j, k);
-    else it.b[o] = it.depth == 0 ? it.f[o] : restrict_at(it.fb, it.gf, i, j, k);
+    else if (it.depth > 0) it.b[o] = restrict_at(it.fb, it.gf, i, j, k);
+    else if (it.pre_load) return;  // assembled before from separable f
+    else if (it.fmode == ECMG_F_GAUSS) it.b[o] = gauss_load_at(it.g, it.op, it.in_f, it.in_gR ? it.gR : nullptr, i, j, k);
+    else it.b[o] = it.f[o];
 }
 
 // ---- start of a level -------------------------------------------------------------------------
@@ -308,6 +327,11 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_flat_init(const BItem* __restrict
         it.pA32[t] = 0.f;
         it.pB32[t] = 0.f;
         it.e32[t] = 0.f;
+        if (it.q32B) {
+            it.q32[t] = 0.f;
+            it.q32B[t] = 0.f;
+            it.r32B[t] = 0.f;
+        }
         if (it.level < 2) it.W[t] = it.U[t];
     }
 }
@@ -326,7 +350,7 @@ __device__ __forceinline__ void tile_of(const BItem& it, const NodeRange& rg, in
 // r = b - A x (FP64), stored FP32; ||r||^2 and the compensated FP32 r.z.
 template <bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(mt::NT) bk_res(const BItem* __restrict__ items, const __grid_constant__ BLaunch L,
-                                                int mode, BCtl* ctl, CondHandles ch)
+                                                int mode, BCtl* ctl, CondHandles ch, int r_to_b)
 {
     COUNT_LAUNCH();
     const Slot sl = find_slot(L);
@@ -340,10 +364,11 @@ __global__ void __launch_bounds__(mt::NT) bk_res(const BItem* __restrict__ items
         double rr = 0.0;
         Acc<float> rz;
         const double* x = it.U;
+        float* __restrict__ r32 = r_to_b ? it.r32B : it.r32;
         auto body = [&](int, int, int, int64_t o, double Av) {
             const double rv = it.b[o] - Av;
             const float ro = (float)rv;
-            it.r32[o] = ro;
+            r32[o] = ro;
             rr = fma(rv, rv, rr);
             rz.add_prod(ro, it.dinv32[o] * ro);
         };
@@ -380,8 +405,8 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_update(const BItem* __restrict__ 
     if (block_flag(!st->done)) {
         const float a = (float)st->alpha;
         Acc<float> rz, rr;
-        const int64_t base = (int64_t)sl.lb * BFLAT_ELEMS;
-        const int64_t end = min(base + BFLAT_ELEMS, it.g.total);  // total is a multiple of 8
+        const SpanRange sr = span_of(it.g, sl.lb);
+        const int64_t base = sr.base, end = sr.end;  // multiples of 4
         float4* __restrict__ r4 = reinterpret_cast<float4*>(it.r32);
         const float4* __restrict__ q4 = reinterpret_cast<const float4*>(it.q32);
         const float4* __restrict__ d4 = reinterpret_cast<const float4*>(it.dinv32);
@@ -423,8 +448,8 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_fold(const BItem* __restrict__ it
     if (st->done || !st->need_update) return;
     const float a = (float)st->alpha_prev;
     const float* __restrict__ p = pnew_is_b ? it.pB32 : it.pA32;
-    const int64_t base = (int64_t)sl.lb * BFLAT_ELEMS;
-    const int64_t end = min(base + BFLAT_ELEMS, it.g.total);
+    const SpanRange sr = span_of(it.g, sl.lb);
+    const int64_t base = sr.base, end = sr.end;
     unsigned long long m = 0ull;
     for (int64_t t = base + threadIdx.x; t < end; t += FLAT_TPB) {
         // the FP32 correction combined in FP32, added with one FP64 operation (jcg.cu k_fold32)
@@ -443,8 +468,8 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_absmax(const BItem* __restrict__ 
     const Slot sl = find_slot(L);
     const BItem& it = items[sl.item];
     if (it.st->done) return;
-    const int64_t base = (int64_t)sl.lb * BFLAT_ELEMS;
-    const int64_t end = min(base + BFLAT_ELEMS, it.g.total);
+    const SpanRange sr = span_of(it.g, sl.lb);
+    const int64_t base = sr.base, end = sr.end;
     unsigned long long m = 0ull;
     for (int64_t t = base + threadIdx.x; t < end; t += FLAT_TPB)
         m = max(m, fx::abs_bits(it.U[t]));
@@ -477,6 +502,7 @@ int bgeom_blocks(BGeom geo, const BItem& it)
         return range_tiles_x(rg) * range_tiles_y(rg) * range_tiles_z(rg, it.kz);
     }
     case BG_FLAT: return cdiv(g.total, BFLAT_ELEMS);
+    case BG_SPAN: return (g.nz + 1) * cdiv(span_v4(g), SPAN_CHUNK_V4);
     case BG_NODES: return cdiv(g.nx + 1, mt::BX) * cdiv(g.ny + 1, mt::BY) * (g.nz + 1);
     case BG_ELEMS: return cdiv(g.nx, mt::BX) * cdiv(g.ny, mt::BY) * g.nz;
     case BG_EXPF: return cdiv((int64_t)it.g0.nx * it.g0.ny * it.g0.nz, EXP_TPB);
@@ -489,7 +515,7 @@ int bgeom_blocks(BGeom geo, const BItem& it)
 int bitem_partials(const BItem& it)
 {
     int m = bk1_max_blocks(it);
-    for (BGeom geo : {BG_STENCIL, BG_FLAT, BG_ROWS}) m = std::max(m, bgeom_blocks(geo, it));
+    for (BGeom geo : {BG_STENCIL, BG_FLAT, BG_SPAN, BG_ROWS}) m = std::max(m, bgeom_blocks(geo, it));
     return m;
 }
 
@@ -522,11 +548,11 @@ void blaunch_guess(const BItem* items, const BLaunch& expf, const BLaunch& flat_
 }
 
 void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube, ResMode mode, BCtl* ctl,
-                 CondHandles ch, cudaStream_t s)
+                 CondHandles ch, cudaStream_t s, int r_to_b)
 {
     auto k = robin ? (cube ? bk_res<true, true> : bk_res<true, false>)
                    : (cube ? bk_res<false, true> : bk_res<false, false>);
-    k<<<nblocks(stencil), dim3(mt::BX, mt::BY), 0, s>>>(items, stencil, (int)mode, ctl, ch);
+    k<<<nblocks(stencil), dim3(mt::BX, mt::BY), 0, s>>>(items, stencil, (int)mode, ctl, ch, r_to_b);
 }
 
 void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s)

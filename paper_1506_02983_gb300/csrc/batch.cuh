@@ -27,6 +27,9 @@ struct BItem {
     Grid g1, g0;          // levels l-1 and l-2 (EXP)
     Grid gf;              // level l+1 (set-up of a coarser level)
     int level, problem, depth, fmode;  // depth 0 = the problem's finest level
+    // depth 0 of a problem with compact inputs: beta, the load b and g_D already assembled on the
+    // device from them (separable f or g_D, one beta) before the batched set-up, which keeps them
+    int pre_beta, pre_load, pre_gD;
     int kz;               // z-march depth of the register-prefetched stencil kernels
     int k1kz;             // planes per block of the TMA-staged FP32 stencil kernel (K1)
     double rtol;          // relative residual tolerance of this level
@@ -36,6 +39,7 @@ struct BItem {
     // vectors of this level (padded layout)
     double *U, *W, *Ut, *b, *beta, *f, *gD, *gR;
     float *beta32, *dinv32, *r32, *pA32, *pB32, *q32, *e32;
+    float *r32B, *q32B;   // single-pass step: the second residual and q buffers
     // solutions of levels l-1, l-2 (EXP)
     const double *U1, *U0;
     // level l+1 vectors (set-up of a coarser level)
@@ -62,7 +66,8 @@ struct BCtl {
 // Block shapes of the batched kernels.
 enum BGeom : int {
     BG_STENCIL = 0,  // 32 x 8 node tiles x kz planes (the z-march kernels)
-    BG_FLAT,         // 4096 consecutive padded elements per block (vector updates)
+    BG_FLAT,         // 4096 consecutive padded elements per block (whole-vector initialisation)
+    BG_SPAN,         // up to 4096 elements of one node plane's span (0,0,k)..(nx,ny,k) per block (updates)
     BG_NODES,        // 32 x 8 nodes of one plane per block
     BG_ELEMS,        // 32 x 8 elements of one slab per block
     BG_EXPF,         // 128 level-(l-2) elements per block
@@ -72,6 +77,13 @@ enum BGeom : int {
     BG_COUNT
 };
 constexpr int BFLAT_ELEMS = 4096;
+
+// The owned nodes of node plane k lie in the span from node (0, 0, k) to node (nx, ny, k) of the
+// padded layout (rows of pitch elements: the ghost rows and planes around it are skipped, the row
+// padding in between is not). In 4-element vectors, rounded up (the span starts 16-byte
+// aligned; the last vector ends inside row ny's padding).
+__host__ __device__ inline int span_v4(const Grid& g) { return (int)(((int64_t)g.ny * g.pitch + g.nx + 1 + 3) / 4); }
+constexpr int SPAN_CHUNK_V4 = 1024;  // vectors per BG_SPAN block
 
 // Blocks one item needs in a geometry (host).
 int bgeom_blocks(BGeom geo, const BItem& it);
@@ -87,13 +99,14 @@ void blaunch_level_start(const BItem* items, const BLaunch& one, const BLaunch& 
 // EXP_finite for levels >= 2 (x and W), W = x on the direct levels 0 and 1, and zeroed FP32
 // search directions and corrections.
 void blaunch_guess(const BItem* items, const BLaunch& expf, const BLaunch& flat_all, int variant, cudaStream_t s);
-// FP64 residual r = b - A x (stored FP32) with r.z and ||r||^2 per item; mode RES_INIT or
+// FP64 residual r = b - A x (stored FP32 into r32, or r32B with r_to_b) with r.z and ||r||^2 per
+// item; mode RES_INIT or
 // RES_REPLACE (items that asked for a replacement only). Sets the loop condition. With cubic
 // elements and no Robin term, A x is exact in fixed point up to the products with beta
 // (march_fx.cuh), on the scale of max |x| that blaunch_absmax (before RES_INIT) or
 // blaunch_fold (before RES_REPLACE) left in the item's state.
 void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube, ResMode mode, BCtl* ctl,
-                 CondHandles ch, cudaStream_t s);
+                 CondHandles ch, cudaStream_t s, int r_to_b = 0);
 // K2 of one FP32 JCG iteration (after K1, blaunch_pq_tma): r -= alpha q, r.z, r.r and the
 // item's tests; sets the loop and replacement conditions.
 void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s);
@@ -110,6 +123,10 @@ void blaunch_exp_true(const BItem* items, const BLaunch& expt, cudaStream_t s);
 // maps: the items' tensor maps (device array indexed like items).
 void blaunch_pq_tma(const BItem* items, const PlaneMaps* maps, const BLaunch& L, int ry, int robin, int cube,
                     int pin_is_b, int pidx, cudaStream_t s);
+// The single-pass step over the items of L (buffer set in_b read, the other written), which
+// also sets the loop and replacement conditions from all items (ctl: the launch-wide counter).
+void blaunch_step_tma(const BItem* items, const PlaneMaps* maps, const BLaunch& L, int ry, int robin, int cube,
+                      int in_b, int pidx, BCtl* ctl, CondHandles ch, cudaStream_t s);
 // Blocks of one item in that launch, the most any tile shape needs, and the nodes it computes.
 int bk1_blocks(const BItem& it, int ry);
 int bk1_max_blocks(const BItem& it);

@@ -168,6 +168,9 @@ void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, 
 void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
 void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
                 cudaStream_t s);
+// b = int f phi_i by the 3x3x3 Gauss rule per element from f at the rule's points (f27, the
+// ECMG_F_GAUSS layout), plus M_F gR_I on Robin faces when gR is given.
+void gauss_load(const Grid& g, const Op& op, const double* f27, const double* gR, double* b, cudaStream_t s);
 // D^-1 in FP64 and/or FP32 (beta32 = beta rounded). uniform: the level's flag, with beta32
 // already converted by beta32_uniform; a one-beta all-Dirichlet cube then keeps only the D^-1
 // of node (1, 1, 1) in FP32. nullptr: beta32 converted here, D^-1 on every node.

@@ -86,6 +86,14 @@ __global__ void k_nodal_load(Grid g, Op op, const double* __restrict__ f,
     b[g.off(i, j, k)] = nodal_load_at(g, op, f, gR, i, j, k);
 }
 
+__global__ void k_gauss_load(Grid g, Op op, const double* __restrict__ f27, const double* __restrict__ gR,
+                             double* __restrict__ b)
+{
+    COUNT_LAUNCH();
+    POINT_IJK(g.nx, g.ny);
+    b[g.off(i, j, k)] = gauss_load_at(g, op, f27, gR, i, j, k);
+}
+
 // Jacobi diagonal: diag = w0 * (sum of the 8 element betas) + Robin face mass diagonal.
 // Dirichlet nodes get dinv = 0, which also masks them in every JCG kernel.
 __global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, double* __restrict__ dinv64, int precond)
@@ -252,6 +260,10 @@ void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, 
                 cudaStream_t s)
 {
     k_nodal_load<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, f, gR, b);
+}
+void gauss_load(const Grid& g, const Op& op, const double* f27, const double* gR, double* b, cudaStream_t s)
+{
+    k_gauss_load<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, f27, gR, b);
 }
 void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64, float* dinv32,
                  float* beta32, int precond, cudaStream_t s, const int* uniform)

@@ -40,6 +40,34 @@ __device__ __forceinline__ int cnt1(int a, int n, int d)
     return (a >= 1) + (a < n);
 }
 
+// sum over the Robin faces through node (i, j, k) of (M_F gR_I)_i, the consistent face mass of
+// the nodal interpolant of g_R (the face term of the load of Sec. 2): a tensor product of the 1D
+// masses m(0) = h/3, m(+-1) = h/6 per element over the face's two axes.
+__device__ __forceinline__ double robin_load_at(const Grid& g, const Op& op, const double* __restrict__ gR, int i,
+                                                int j, int k)
+{
+    const int idx[3] = {i, j, k};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    double s = 0.0;
+    for (int fc = 0; fc < 6; ++fc) {
+        if (op.bc[fc] != 1) continue;
+        const int an = fc / 2;
+        if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
+        const int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
+        for (int db = -1; db <= 1; ++db)
+            for (int da = -1; da <= 1; ++da) {
+                const double w = cnt1(idx[aa], nn[aa], da) * (g.h[aa] * (da ? (1.0 / 6.0) : (1.0 / 3.0))) *
+                                 (cnt1(idx[ab], nn[ab], db) * (g.h[ab] * (db ? (1.0 / 6.0) : (1.0 / 3.0))));
+                if (w == 0.0) continue;
+                int o[3] = {0, 0, 0};
+                o[aa] = da;
+                o[ab] = db;
+                s += w * gR[g.off(i + o[0], j + o[1], k + o[2])];
+            }
+    }
+    return s;
+}
+
 // b_i = (M f_I + sum over Robin faces of M_F gR_I)_i with the consistent mass matrices of
 // Sec. 2. The element mass is a tensor product, so the assembled row is
 // prod_a cnt_a(d_a) m_a(d_a), m(0) = h/3 and m(+-1) = h/6 per element, and the sum over the
@@ -64,23 +92,57 @@ __device__ __forceinline__ double nodal_load_at(const Grid& g, const Op& op, con
         }
         s = fma(wa[2][dk + 1], sz, s);
     }
-    if (gR) {
-        for (int fc = 0; fc < 6; ++fc) {
-            if (op.bc[fc] != 1) continue;
-            int an = fc / 2;
-            if (idx[an] != ((fc & 1) ? nn[an] : 0)) continue;
-            int aa = (an == 0) ? 1 : 0, ab = (an == 2) ? 1 : 2;
-            for (int db = -1; db <= 1; ++db)
-                for (int da = -1; da <= 1; ++da) {
-                    double w = wa[aa][da + 1] * wa[ab][db + 1];
-                    if (w == 0.0) continue;
-                    int o[3] = {0, 0, 0};
-                    o[aa] = da;
-                    o[ab] = db;
-                    s += w * gR[g.off(i + o[0], j + o[1], k + o[2])];
+    if (gR) s += robin_load_at(g, op, gR, i, j, k);
+    return s;
+}
+
+// The 3-point Gauss-Legendre rule on [0, 1]: nodes (1 -+ sqrt(3/5)) / 2 and 1/2, weights 5/18,
+// 8/18, 5/18; the layout of f at the rule's points (ECMG_F_GAUSS) takes the nodes in this order.
+constexpr double GAUSS3_OFF = 0.38729833462074168852;  // sqrt(3/5) / 2
+__device__ __forceinline__ double gauss3_node(int q) { return q == 0 ? 0.5 - GAUSS3_OFF : (q == 1 ? 0.5 : 0.5 + GAUSS3_OFF); }
+__device__ __forceinline__ double gauss3_weight(int q) { return q == 1 ? 8.0 / 18.0 : 5.0 / 18.0; }
+
+// b_i = int f phi_i of the weak form of Sec. 2 by the 3x3x3 Gauss rule on every element around
+// node i, with f given at the rule's points of every element of the level (f27: 27 values per
+// element, elements x fastest, then the points qx fastest, qy, qz), plus the Robin face terms of
+// nodal_load_at. On an element where the node is corner (cx, cy, cz), its hat at point q is
+// prod_a (c_a ? t_qa : 1 - t_qa); the sum runs over the points axis by axis.
+__device__ __forceinline__ double gauss_load_at(const Grid& g, const Op& op, const double* __restrict__ f27,
+                                                const double* __restrict__ gR, int i, int j, int k)
+{
+    const double vol = g.h[0] * g.h[1] * g.h[2];
+    double s = 0.0;
+    for (int dz = 0; dz < 2; ++dz) {
+        const int ez = k - 1 + dz;
+        if (ez < 0 || ez >= g.nz) continue;
+        for (int dy = 0; dy < 2; ++dy) {
+            const int ey = j - 1 + dy;
+            if (ey < 0 || ey >= g.ny) continue;
+            for (int dx = 0; dx < 2; ++dx) {
+                const int ex = i - 1 + dx;
+                if (ex < 0 || ex >= g.nx) continue;
+                // the node is corner (1 - dx, 1 - dy, 1 - dz) of this element
+                const double* fe = f27 + 27 * (ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez));
+                double sz = 0.0;
+                for (int qz = 0; qz < 3; ++qz) {
+                    double sy = 0.0;
+                    for (int qy = 0; qy < 3; ++qy) {
+                        double sx = 0.0;
+                        for (int qx = 0; qx < 3; ++qx) {
+                            const double t = gauss3_node(qx);
+                            sx = fma(gauss3_weight(qx) * (dx ? 1.0 - t : t), fe[qx + 3 * qy + 9 * qz], sx);
+                        }
+                        const double t = gauss3_node(qy);
+                        sy = fma(gauss3_weight(qy) * (dy ? 1.0 - t : t), sx, sy);
+                    }
+                    const double t = gauss3_node(qz);
+                    sz = fma(gauss3_weight(qz) * (dz ? 1.0 - t : t), sy, sz);
                 }
+                s = fma(vol, sz, s);
+            }
         }
     }
+    if (gR) s += robin_load_at(g, op, gR, i, j, k);
     return s;
 }
 

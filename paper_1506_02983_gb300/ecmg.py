@@ -21,7 +21,7 @@ _lib = C.CDLL(LIB_PATH)
 ECMG_OK, ECMG_ERR_INVALID_ARG, ECMG_ERR_SINGULAR, ECMG_ERR_NO_CONVERGENCE = 0, 1, 2, 3
 ECMG_ERR_BREAKDOWN, ECMG_ERR_OOM, ECMG_ERR_CUDA = 4, 5, 6
 ECMG_BC_DIRICHLET, ECMG_BC_ROBIN = 0, 1
-ECMG_F_NODAL, ECMG_F_LOAD, ECMG_F_SEPARABLE = 0, 1, 2
+ECMG_F_NODAL, ECMG_F_LOAD, ECMG_F_SEPARABLE, ECMG_F_GAUSS = 0, 1, 2, 3
 ECMG_FP64, ECMG_MIXED = 0, 1
 ECMG_APPLY_K1 = 2  # ecmg_apply_operator: the FP32 search-direction kernel itself
 ECMG_EXP_SERENDIPITY20, ECMG_EXP_LAGRANGE27 = 0, 1
@@ -288,8 +288,8 @@ class BatchSolver:
     step of Alg. 4 over all problems, one CUDA graph per solve, MIXED precision.
 
     problems: list of dicts with n0, levels, lo, hi, face_bc, alpha and the device tensors
-    beta, f and optionally gD, gR (as for Solver), plus f_mode. The tensors must outlive the
-    solver."""
+    beta, f and optionally gD, gR (as for Solver), plus f_mode and, for compact inputs, f_terms,
+    gD_terms and beta_const (beta None). The tensors must outlive the solver."""
 
     def __init__(self, problems, **options):
         n = len(problems)
@@ -304,13 +304,15 @@ class BatchSolver:
             p.hi[:] = [float(v) for v in q["hi"]]
             p.face_bc[:] = [int(v) for v in q["face_bc"]]
             p.robin_alpha[:] = [float(v) for v in q["alpha"]]
-            ts = (q["beta"], q["f"], q.get("gD"), q.get("gR"))
+            ts = (q.get("beta"), q["f"], q.get("gD"), q.get("gR"))
             for t in ts:
                 if t is not None and (not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64"):
                     raise ValueError("inputs must be contiguous float64 CUDA tensors")
             self._keep.append(ts)
             p.beta, p.f, p.g_D, p.g_R = (None if t is None else t.data_ptr() for t in ts)
             p.f_mode = int(q.get("f_mode", ECMG_F_NODAL))
+            p.f_terms, p.gD_terms = int(q.get("f_terms", 0)), int(q.get("gD_terms", 0))
+            p.beta_const = float(q.get("beta_const", 0.0))
         options.setdefault("precision", ECMG_MIXED)
         self.options = default_options(**options)
         self.n = n

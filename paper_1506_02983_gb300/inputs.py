@@ -341,6 +341,42 @@ def separable_samples(n, lo, hi, terms):
     return np.stack(rows)
 
 
+def gauss_samples(n, lo, hi, f):
+    """f(x, y, z) (broadcasting callable) at the 27 points of the 3-point Gauss-Legendre rule of
+    every element of the uniform grid n on [lo, hi], in the ECMG_F_GAUSS layout: shape
+    (nz, ny, nx, 3, 3, 3), elements x fastest, then the points qx fastest, qy, qz."""
+    g = gauss3_nodes()
+    pts = [lo[a] + (np.arange(n[a])[:, None] + g[None, :]) * (hi[a] - lo[a]) / n[a] for a in range(3)]
+    X = pts[0].reshape(1, 1, n[0], 1, 1, 3)
+    Y = pts[1].reshape(1, n[1], 1, 1, 3, 1)
+    Z = pts[2].reshape(n[2], 1, 1, 3, 1, 1)
+    return np.array(np.broadcast_to(f(X, Y, Z), (n[2], n[1], n[0], 3, 3, 3)), dtype=np.float64)
+
+
+def exp_cube_gauss(levels=4, n0=(4, 4, 4), rtol=1e-10):
+    """exp_cube with f = -Laplace(u) = -3 e^{x+y+z} given at the Gauss points of every finest
+    element (f_mode 3)."""
+    p = exp_cube(levels=levels, n0=n0, rtol=rtol)
+    n = finest(n0, levels)
+    p["f"] = gauss_samples(n, p["lo"], p["hi"], lambda x, y, z: -3.0 * np.exp(x + y + z))
+    p["f_mode"] = 3
+    return p
+
+
+def random_gauss(seed, n0=(2, 3, 2), levels=3, face_bc=None):
+    """A seeded random problem (lognormal beta, random boundary types, Robin alphas and data) with
+    f a random trigonometric function given at the Gauss points of every finest element (f_mode 3)
+    and nodal g_R on its Robin faces."""
+    rng = np.random.default_rng(seed)
+    p = random_problem(seed, n0=n0, levels=levels, face_bc=face_bc)
+    n = finest(n0, levels)
+    a, b, c, d = rng.uniform(0.5, 3.0, 4)
+    p["f"] = gauss_samples(n, p["lo"], p["hi"],
+                           lambda x, y, z: d * np.sin(a * x + 0.3) * np.cos(b * y - 0.2) + np.exp(-c * z))
+    p["f_mode"] = 3
+    return p
+
+
 def separable_nodal(n, lo, hi, terms):
     """Nodal factors of g = sum_t gx_t(x) gy_t(y) gz_t(z): shape (T, (nx+1) + (ny+1) + (nz+1)),
     per term x, then y, then z."""

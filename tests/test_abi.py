@@ -106,8 +106,8 @@ def test_solver_variant_options_validation_without_gpu(libpath):
         assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG, bad
     o = ecmg.default_options(cg_form=3)
     assert ecmg.ecmg_create(ctypes.byref(p), ctypes.byref(o), None, ctypes.byref(h)) == ecmg.ECMG_ERR_INVALID_ARG
-    # the batched entry point runs the two-pass step only
-    o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=ecmg.ECMG_CG_SINGLE_PASS)
+    # the batched entry point takes a bad step form as an invalid argument too
+    o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=3)
     assert ecmg.ecmg_create_batched(ctypes.byref(p), 1, ctypes.byref(o), None, ctypes.byref(h)) == \
         ecmg.ECMG_ERR_INVALID_ARG
     o = ecmg.default_options()

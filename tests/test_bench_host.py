@@ -76,9 +76,26 @@ def test_reference_arm_prints_the_contract_line(monkeypatch):
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "Gdof/s"
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["host"]["nproc"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
     # the line states what this arm ran: the FP64 oracle on a cut of the workload
     assert d["config"]["precision"].startswith("FP64")
     assert "cut to" in d["config"]["sample"]
+
+
+def test_cpu_baseline_legs(monkeypatch):
+    """The CPU baseline times the one-thread oracle and the OpenMP build on every host core,
+    each with its set-up and solve seconds, and records the host's cores and CPU model."""
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()
+    cb = bench.cpu_baseline(args, 3, 4, min_seconds=0.0, max_runs=1)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
+    assert cb["host"]["nproc"] >= 1 and isinstance(cb["host"]["cpu_model"], str)
+    one, omp = cb["legs"]
+    assert one["cores"] == 1 and omp["cores"] >= 1
+    assert one["finest"] == "32^3" and omp["finest"] == "64^3"
+    for leg in (one, omp):
+        assert leg["seconds_assembly"] > 0 and leg["seconds_solve"] > 0

@@ -63,16 +63,18 @@ def _iter_bound(p, l, fp64_iters):
     return max(3 * fp64_iters + 2, 4 * n)
 
 
-def test_batched_solve_matches_oracle(E, oracle_mod):
+@pytest.mark.parametrize("cg_form", [2, 1])  # the default (two-pass: K1 + K2), and the single-pass step
+def test_batched_solve_matches_oracle(E, oracle_mod, cg_form):
     probs = _mixed_batch()
     dev = [_device(p) for p in probs]
-    bs = E.BatchSolver(dev, rtol=RTOL)
+    bs = E.BatchSolver(dev, rtol=RTOL, cg_form=cg_form)
     stats, status = bs.solve()
     assert status == 0, stats
     for i, p in enumerate(probs):
         lv, ost = oracle_mod.ecmg(p, RTOL)
-        # the batched handle runs the two-pass step, so the single-problem one does here too
-        single = E.solver_from_problem(p, precision=1, rtol=RTOL, cg_form=E.ECMG_CG_TWO_PASS)
+        # the single-problem solve with the same step form on every level
+        single = E.solver_from_problem(p, precision=1, rtol=RTOL,
+                                       cg_form=E.ECMG_CG_SINGLE_PASS if cg_form == 1 else E.ECMG_CG_TWO_PASS)
         sst, sstatus = single.solve()
         assert sstatus == 0
         single.close()
@@ -204,14 +206,27 @@ def test_batched_autotuned_tiles_match_the_oracle(E, oracle_mod):
         U = _np(bs.get(i, E.ECMG_VEC_U))
         assert _rel(U, lv[L - 1]["U"]) <= 1e-7, (i, _rel(U, lv[L - 1]["U"]))
     # the stage kernels timed alone through the C ABI (level = stage): K1 and K2 of the last stage
+    # (the default step form of a batch is the two-pass step: kernels 0 and 1)
+    ms, nb = ctypes.c_double(), ctypes.c_double()
     for which in (0, 1):
-        ms, nb = ctypes.c_double(), ctypes.c_double()
         assert E.ecmg_time_kernel(bs.handle, -1, which, 2, ctypes.byref(ms), ctypes.byref(nb)) == E.ECMG_OK
         assert ms.value > 0.0 and nb.value > 0.0
-    ms, nb = ctypes.c_double(), ctypes.c_double()
-    assert E.ecmg_time_kernel(bs.handle, -1, 5, 2, ctypes.byref(ms), ctypes.byref(nb)) == E.ECMG_ERR_INVALID_ARG
+    for which in (11, 5):
+        assert E.ecmg_time_kernel(bs.handle, -1, which, 2, ctypes.byref(ms), ctypes.byref(nb)) == E.ECMG_ERR_INVALID_ARG
     # and the batch solves again to the same result after the timing launches
     again, status = bs.solve()
     assert status == 0
     assert [s["iters"] for s in again] == [s["iters"] for s in stats]
     bs.close()
+    # a single-pass batch (autotuned on its own step kernel) times that kernel, 11
+    one = E.BatchSolver(dev, rtol=RTOL, cg_form=E.ECMG_CG_SINGLE_PASS, autotune=1)
+    assert E.ecmg_time_kernel(one.handle, -1, 11, 2, ctypes.byref(ms), ctypes.byref(nb)) == E.ECMG_OK
+    assert ms.value > 0.0 and nb.value > 0.0
+    for which in (0, 1):
+        assert E.ecmg_time_kernel(one.handle, -1, which, 2, ctypes.byref(ms), ctypes.byref(nb)) == E.ECMG_ERR_INVALID_ARG
+    st1, status = one.solve()
+    assert status == 0
+    for i, p in enumerate(probs):
+        for l in range(2, p["levels"]):
+            assert st1[i]["rel_res"][l] <= RTOL
+    one.close()

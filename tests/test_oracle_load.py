@@ -125,3 +125,19 @@ def test_jump_generator_load_equals_the_oracle_definition(oracle_mod):
     want = oracle_mod.load_functional(n, p["lo"], p["hi"], f, q=3, faces=[(0, n[0] // 2, g_int), (0, 0, g_rob)])
     got = np.asarray(p["f"])
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * np.abs(want).max())
+
+
+def test_gauss_point_load_equals_the_functional_with_the_same_rule(oracle_mod):
+    """oracle.load_gauss (f given at the Gauss points, ECMG_F_GAUSS) is int f phi_i by the 3-point
+    rule: equal to load_functional with q = 3 on a smooth and on a discontinuous f, and the hat
+    volumes for constant f."""
+    n, lo, hi = (5, 3, 4), (0.0, -1.0, 0.5), (2.0, 0.5, 1.0)
+    h = [(hi[a] - lo[a]) / n[a] for a in range(3)]
+    for f in (lambda x, y, z: np.exp(x - 2 * y) * np.cos(3 * z),
+              lambda x, y, z: np.where(x < 1.0, 1.0, 100.0) * (x * x + y * y + z * z) ** -0.25):
+        got = oracle_mod.load_gauss(n, h, inputs.gauss_samples(n, lo, hi, f))
+        want = oracle_mod.load_functional(n, lo, hi, f, q=3)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-14 * np.abs(want).max())
+    one = oracle_mod.load_gauss(n, h, np.ones((n[2], n[1], n[0], 3, 3, 3)))
+    assert one.sum() == pytest.approx(np.prod([hi[a] - lo[a] for a in range(3)]), rel=1e-14)
+    assert one[0, 0, 0] == pytest.approx(h[0] * h[1] * h[2] / 8.0, rel=1e-14)

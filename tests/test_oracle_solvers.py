@@ -109,3 +109,18 @@ def test_single_pass_jcg_converges_like_textbook_jcg(oracle_mod, seed):
     assert st_sp["status"] == 0 and abs(st_sp["iters"] - st["iters"]) <= 1
     assert st_sp["rel_res"] <= 1e-12 * 1.01
     assert np.abs(x_sp - x_ref).max() <= 1e-9 * np.abs(x_ref).max()
+
+
+def test_openmp_build_gives_the_one_thread_results(oracle_mod):
+    """The OpenMP build parallelises only the CSR rows and the element-wise vector updates (dot
+    products stay sequential), so every level's solution is bit-identical to the one-thread
+    build's; both report the set-up and solve seconds."""
+    p = inputs.cos_cube(levels=4, n0=(4, 4, 4), rtol=1e-10)
+    a, sa = oracle_mod.ecmg(p, p["rtol"])
+    b, sb = oracle_mod.ecmg(p, p["rtol"], threads=4)
+    assert sa["threads"] == 1 and sb["threads"] >= 1
+    assert sa["iters"] == sb["iters"]
+    for x, y in zip(a, b):
+        assert np.array_equal(x["U"], y["U"]) and np.array_equal(x["Ut"], y["Ut"])
+    for s in (sa, sb):
+        assert s["seconds_assembly"] > 0.0 and s["seconds_solve"] > 0.0
