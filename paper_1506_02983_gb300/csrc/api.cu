@@ -1351,7 +1351,7 @@ ecmg_status ecmg_create_batched(const ecmg_problem* probs, int32_t n, const ecmg
                     it.pre_gD = pr.gD_terms > 0 ? 1 : 0;
                     if (pr.f_mode == ECMG_F_SEPARABLE) B.Hf[p] = dalloc<double>(h, sep_factor_len(it.g, pr.f_terms));
                 }
-                it.kz = std::min(32, it.g.nz + 1);
+                it.kz = std::min(8, it.g.nz + 1);  // short columns: a replacement often runs on one item alone
                 it.k1kz = 16;
                 it.fixed = (opt->schedule == ECMG_SCHED_FIXED && l >= 2) ? 1 : 0;
                 it.rtol = l < 2 ? opt->dsolve_rtol : (it.fixed ? 0.0 : opt->rtol);

@@ -48,17 +48,27 @@ __device__ __forceinline__ Slot find_slot(const BLaunch& L)
     return Slot{L.id[lo], b - L.start[lo], L.start[lo + 1] - L.start[lo]};
 }
 
-// Element range [base, end) of a BG_SPAN block: chunk c of node plane k's span.
+// Work of a BG_SPAN block: node planes k0 .. k1-1, in each the vectors [v0, v1) of the plane's
+// span (4-element vectors from node (0, 0, k)).
 struct SpanRange {
-    int64_t base, end;
+    int k0, k1, v0, v1;
 };
 __device__ __forceinline__ SpanRange span_of(const Grid& g, int lb)
 {
-    const int nv = span_v4(g);
-    const int nch = (nv + SPAN_CHUNK_V4 - 1) / SPAN_CHUNK_V4;
-    const int k = lb / nch, c = lb - k * nch;
-    const int64_t p0 = g.off(0, 0, k);
-    return SpanRange{p0 + 4 * (int64_t)c * SPAN_CHUNK_V4, p0 + 4 * (int64_t)min((c + 1) * SPAN_CHUNK_V4, nv)};
+    const int nv = span_v4(g), ppb = span_planes_per_block(g), cpp = span_chunks_per_plane(g);
+    if (cpp == 1) return SpanRange{lb * ppb, min((lb + 1) * ppb, g.nz + 1), 0, nv};
+    const int k = lb / cpp, c = lb - k * cpp;
+    return SpanRange{k, k + 1, c * SPAN_BLOCK_V4, min((c + 1) * SPAN_BLOCK_V4, nv)};
+}
+// Calls f(t) for the 4-element vector index t (from the start of the level vector) of every
+// vector of the block's range, the threads of a one-dimensional block striding over it.
+template <typename F>
+__device__ __forceinline__ void span_for(const Grid& g, const SpanRange& sr, F f)
+{
+    for (int k = sr.k0; k < sr.k1; ++k) {
+        const int64_t p4 = g.off(0, 0, k) / 4;
+        for (int v = sr.v0 + (int)threadIdx.x; v < sr.v1; v += (int)blockDim.x) f(p4 + v);
+    }
 }
 
 // ---- reductions --------------------------------------------------------------------------------
@@ -406,11 +416,10 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_update(const BItem* __restrict__ 
         const float a = (float)st->alpha;
         Acc<float> rz, rr;
         const SpanRange sr = span_of(it.g, sl.lb);
-        const int64_t base = sr.base, end = sr.end;  // multiples of 4
         float4* __restrict__ r4 = reinterpret_cast<float4*>(it.r32);
         const float4* __restrict__ q4 = reinterpret_cast<const float4*>(it.q32);
         const float4* __restrict__ d4 = reinterpret_cast<const float4*>(it.dinv32);
-        for (int64_t t = base / 4 + threadIdx.x; t < end / 4; t += FLAT_TPB) {
+        span_for(it.g, sr, [&](int64_t t) {
             float4 rv = r4[t];
             const float4 qv = q4[t], dv = d4[t];
             rv.x -= a * qv.x;
@@ -426,7 +435,7 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_update(const BItem* __restrict__ 
             rr.add_prod(rv.z, rv.z);
             rr.add_prod(rv.w, rv.w);
             r4[t] = rv;
-        }
+        });
         double v[2] = {rz.value(), rr.value()};
         if (item_sum<2>(v, it.part, &st->arrive, sl.lb, sl.nb)) {
             update_epilogue<true>(st, v[0], v[1]);
@@ -449,15 +458,18 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_fold(const BItem* __restrict__ it
     const float a = (float)st->alpha_prev;
     const float* __restrict__ p = pnew_is_b ? it.pB32 : it.pA32;
     const SpanRange sr = span_of(it.g, sl.lb);
-    const int64_t base = sr.base, end = sr.end;
     unsigned long long m = 0ull;
-    for (int64_t t = base + threadIdx.x; t < end; t += FLAT_TPB) {
-        // the FP32 correction combined in FP32, added with one FP64 operation (jcg.cu k_fold32)
-        const double xn = it.U[t] + fx::widen(fmaf(a, p[t], it.e32[t]));
-        it.U[t] = xn;
-        it.e32[t] = 0.f;
-        m = max(m, fx::abs_bits(xn));
-    }
+    span_for(it.g, sr, [&](int64_t t4) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t t = 4 * t4 + c;
+            // the FP32 correction combined in FP32, added with one FP64 operation (jcg.cu k_fold32)
+            const double xn = it.U[t] + fx::widen(fmaf(a, p[t], it.e32[t]));
+            it.U[t] = xn;
+            it.e32[t] = 0.f;
+            m = max(m, fx::abs_bits(xn));
+        }
+    });
     block_max_to(m, &it.st->xbits);  // the scale of the exact residual that follows
 }
 
@@ -469,10 +481,11 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_absmax(const BItem* __restrict__ 
     const BItem& it = items[sl.item];
     if (it.st->done) return;
     const SpanRange sr = span_of(it.g, sl.lb);
-    const int64_t base = sr.base, end = sr.end;
     unsigned long long m = 0ull;
-    for (int64_t t = base + threadIdx.x; t < end; t += FLAT_TPB)
-        m = max(m, fx::abs_bits(it.U[t]));
+    span_for(it.g, sr, [&](int64_t t4) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) m = max(m, fx::abs_bits(it.U[4 * t4 + c]));
+    });
     block_max_to(m, &it.st->xbits);
 }
 
@@ -502,7 +515,9 @@ int bgeom_blocks(BGeom geo, const BItem& it)
         return range_tiles_x(rg) * range_tiles_y(rg) * range_tiles_z(rg, it.kz);
     }
     case BG_FLAT: return cdiv(g.total, BFLAT_ELEMS);
-    case BG_SPAN: return (g.nz + 1) * cdiv(span_v4(g), SPAN_CHUNK_V4);
+    case BG_SPAN:
+        return span_chunks_per_plane(g) == 1 ? cdiv(g.nz + 1, span_planes_per_block(g))
+                                             : (g.nz + 1) * span_chunks_per_plane(g);
     case BG_NODES: return cdiv(g.nx + 1, mt::BX) * cdiv(g.ny + 1, mt::BY) * (g.nz + 1);
     case BG_ELEMS: return cdiv(g.nx, mt::BX) * cdiv(g.ny, mt::BY) * g.nz;
     case BG_EXPF: return cdiv((int64_t)it.g0.nx * it.g0.ny * it.g0.nz, EXP_TPB);

@@ -67,7 +67,7 @@ struct BCtl {
 enum BGeom : int {
     BG_STENCIL = 0,  // 32 x 8 node tiles x kz planes (the z-march kernels)
     BG_FLAT,         // 4096 consecutive padded elements per block (whole-vector initialisation)
-    BG_SPAN,         // up to 4096 elements of one node plane's span (0,0,k)..(nx,ny,k) per block (updates)
+    BG_SPAN,         // node plane spans (0,0,k)..(nx,ny,k): whole planes, or chunks of one, per block (updates)
     BG_NODES,        // 32 x 8 nodes of one plane per block
     BG_ELEMS,        // 32 x 8 elements of one slab per block
     BG_EXPF,         // 128 level-(l-2) elements per block
@@ -83,7 +83,20 @@ constexpr int BFLAT_ELEMS = 4096;
 // padding in between is not). In 4-element vectors, rounded up (the span starts 16-byte
 // aligned; the last vector ends inside row ny's padding).
 __host__ __device__ inline int span_v4(const Grid& g) { return (int)(((int64_t)g.ny * g.pitch + g.nx + 1 + 3) / 4); }
-constexpr int SPAN_CHUNK_V4 = 1024;  // vectors per BG_SPAN block
+// A BG_SPAN block covers about SPAN_BLOCK_V4 vectors: several whole planes of a small level, or
+// a chunk of one plane of a large one, so that every block has enough work to pay for its
+// reduction.
+constexpr int SPAN_BLOCK_V4 = 4096;
+__host__ __device__ inline int span_planes_per_block(const Grid& g)
+{
+    const int v = span_v4(g);
+    return v >= SPAN_BLOCK_V4 ? 1 : SPAN_BLOCK_V4 / v;
+}
+__host__ __device__ inline int span_chunks_per_plane(const Grid& g)
+{
+    const int v = span_v4(g);
+    return v <= SPAN_BLOCK_V4 ? 1 : (v + SPAN_BLOCK_V4 - 1) / SPAN_BLOCK_V4;
+}
 
 // Blocks one item needs in a geometry (host).
 int bgeom_blocks(BGeom geo, const BItem& it);
