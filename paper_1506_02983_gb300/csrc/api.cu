@@ -736,7 +736,8 @@ void record_batched(Rec& R)
         blaunch_level_start(items, make_launch(B, ids, BG_ONE), make_launch(B, ids, BG_NODES),
                             make_launch(B, ids, BG_ROWS), B.robin, B.cube, o.inner_rtol, R.s());
         blaunch_guess(items, make_launch(B, ids2, BG_EXPF), make_launch(B, ids, BG_FLAT), o.exp_variant, R.s());
-        const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_SPAN);
+        const BLaunch stencil = make_launch(B, ids, BG_STENCIL), flat = make_launch(B, ids, BG_SPAN),
+                      fine = make_launch(B, ids, BG_SPAN_FINE);
         const int ry = B.stage_ry[s];
         const BLaunch k1 = make_launch_k1(B, ids, ry);
         if (B.sp) {
@@ -745,7 +746,7 @@ void record_batched(Rec& R)
             // its residual there, where the next step reads it
             if (R.graph) {
                 const cudaGraphConditionalHandle loop = R.new_handle();
-                blaunch_absmax(items, flat, R.s());
+                blaunch_absmax(items, fine, R.s());
                 blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, CondHandles{loop, 0, 1}, R.s(), 0);
                 R.open(loop, cudaGraphCondTypeWhile);
                 for (int half = 0; half < 2; ++half) {
@@ -754,21 +755,21 @@ void record_batched(Rec& R)
                     blaunch_step_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, o, B.ctl, CondHandles{loop, upd, 1},
                                      R.s());
                     R.open(upd, cudaGraphCondTypeIf);
-                    blaunch_fold(items, flat, o, R.s());
+                    blaunch_fold(items, fine, o, R.s());
                     blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, CondHandles{loop, 0, 1}, R.s(), o);
                     R.close();
                 }
                 R.close();
             } else {
                 const CondHandles none{0, 0, 0};
-                blaunch_absmax(items, flat, R.s());
+                blaunch_absmax(items, fine, R.s());
                 blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, none, R.s(), 0);
                 int half = 0;
                 while (any_state(h, ids, false)) {
                     const int o = half ^ 1;
                     blaunch_step_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, o, B.ctl, none, R.s());
                     if (any_state(h, ids, true)) {
-                        blaunch_fold(items, flat, o, R.s());
+                        blaunch_fold(items, fine, o, R.s());
                         blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, none, R.s(), o);
                     }
                     half = o;
@@ -776,7 +777,7 @@ void record_batched(Rec& R)
             }
         } else if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
-            blaunch_absmax(items, flat, R.s());
+            blaunch_absmax(items, fine, R.s());
             blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, CondHandles{loop, 0, 1}, R.s());
             R.open(loop, cudaGraphCondTypeWhile);
             for (int half = 0; half < 2; ++half) {
@@ -784,21 +785,21 @@ void record_batched(Rec& R)
                 blaunch_pq_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, half ? 0 : 1, R.s());
                 blaunch_update(items, flat, B.ctl, CondHandles{loop, upd, 1}, R.s());
                 R.open(upd, cudaGraphCondTypeIf);
-                blaunch_fold(items, flat, half ? 0 : 1, R.s());
+                blaunch_fold(items, fine, half ? 0 : 1, R.s());
                 blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, CondHandles{loop, 0, 1}, R.s());
                 R.close();
             }
             R.close();
         } else {
             const CondHandles none{0, 0, 0};
-            blaunch_absmax(items, flat, R.s());
+            blaunch_absmax(items, fine, R.s());
             blaunch_res(items, stencil, B.robin, B.cube, RES_INIT, B.ctl, none, R.s());
             int half = 0;
             while (any_state(h, ids, false)) {
                 blaunch_pq_tma(items, B.d_maps, k1, ry, B.robin, B.cube, half, half ? 0 : 1, R.s());
                 blaunch_update(items, flat, B.ctl, none, R.s());
                 if (any_state(h, ids, true)) {
-                    blaunch_fold(items, flat, half ? 0 : 1, R.s());
+                    blaunch_fold(items, fine, half ? 0 : 1, R.s());
                     blaunch_res(items, stencil, B.robin, B.cube, RES_REPLACE, B.ctl, none, R.s());
                 }
                 half ^= 1;
@@ -1006,7 +1007,8 @@ double time_batch_launch(ecmg_handle* h, const std::vector<int>& ids, int which,
     tmpl.thresh2 = -1.0;
     tmpl.inner2 = -1.0;
     const size_t ni = B.items.size();
-    const BLaunch k1 = make_launch_k1(B, ids, ry), flat = make_launch(B, ids, BG_SPAN);
+    const BLaunch k1 = make_launch_k1(B, ids, ry), flat = make_launch(B, ids, BG_SPAN),
+                  fine = make_launch(B, ids, BG_SPAN_FINE);
     const CondHandles none{0, 0, 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double total = 0.0;
@@ -1022,7 +1024,7 @@ double time_batch_launch(ecmg_handle* h, const std::vector<int>& ids, int which,
             else if (which == 11) blaunch_step_tma(B.d_items, B.d_maps, k1, ry, B.robin, B.cube, 0, 1, B.ctl, none, s);
             else if (which == 2) {
                 // the FP64 residual of every item (its max |x| first), into r, reported only
-                blaunch_absmax(B.d_items, flat, s);
+                blaunch_absmax(B.d_items, fine, s);
                 blaunch_res(B.d_items, make_launch(B, ids, BG_STENCIL), B.robin, B.cube, RES_REPORT, B.ctl, none, s);
             } else blaunch_update(B.d_items, flat, B.ctl, none, s);
             ck(cudaEventRecord(e1, s));

@@ -60,6 +60,13 @@ __device__ __forceinline__ SpanRange span_of(const Grid& g, int lb)
     const int k = lb / cpp, c = lb - k * cpp;
     return SpanRange{k, k + 1, c * SPAN_BLOCK_V4, min((c + 1) * SPAN_BLOCK_V4, nv)};
 }
+// The same for a BG_SPAN_FINE block: chunk c of at most SPAN_FINE_V4 vectors of plane k.
+__device__ __forceinline__ SpanRange span_fine_of(const Grid& g, int lb)
+{
+    const int nv = span_v4(g), cpp = (nv + SPAN_FINE_V4 - 1) / SPAN_FINE_V4;
+    const int k = lb / cpp, c = lb - k * cpp;
+    return SpanRange{k, k + 1, c * SPAN_FINE_V4, min((c + 1) * SPAN_FINE_V4, nv)};
+}
 // Calls f(t) for the 4-element vector index t (from the start of the level vector) of every
 // vector of the block's range, the threads of a one-dimensional block striding over it.
 template <typename F>
@@ -457,7 +464,7 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_fold(const BItem* __restrict__ it
     if (st->done || !st->need_update) return;
     const float a = (float)st->alpha_prev;
     const float* __restrict__ p = pnew_is_b ? it.pB32 : it.pA32;
-    const SpanRange sr = span_of(it.g, sl.lb);
+    const SpanRange sr = span_fine_of(it.g, sl.lb);
     unsigned long long m = 0ull;
     span_for(it.g, sr, [&](int64_t t4) {
 #pragma unroll
@@ -480,7 +487,7 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_absmax(const BItem* __restrict__ 
     const Slot sl = find_slot(L);
     const BItem& it = items[sl.item];
     if (it.st->done) return;
-    const SpanRange sr = span_of(it.g, sl.lb);
+    const SpanRange sr = span_fine_of(it.g, sl.lb);
     unsigned long long m = 0ull;
     span_for(it.g, sr, [&](int64_t t4) {
 #pragma unroll
@@ -518,6 +525,7 @@ int bgeom_blocks(BGeom geo, const BItem& it)
     case BG_SPAN:
         return span_chunks_per_plane(g) == 1 ? cdiv(g.nz + 1, span_planes_per_block(g))
                                              : (g.nz + 1) * span_chunks_per_plane(g);
+    case BG_SPAN_FINE: return (g.nz + 1) * cdiv(span_v4(g), SPAN_FINE_V4);
     case BG_NODES: return cdiv(g.nx + 1, mt::BX) * cdiv(g.ny + 1, mt::BY) * (g.nz + 1);
     case BG_ELEMS: return cdiv(g.nx, mt::BX) * cdiv(g.ny, mt::BY) * g.nz;
     case BG_EXPF: return cdiv((int64_t)it.g0.nx * it.g0.ny * it.g0.nz, EXP_TPB);
@@ -530,7 +538,7 @@ int bgeom_blocks(BGeom geo, const BItem& it)
 int bitem_partials(const BItem& it)
 {
     int m = bk1_max_blocks(it);
-    for (BGeom geo : {BG_STENCIL, BG_FLAT, BG_SPAN, BG_ROWS}) m = std::max(m, bgeom_blocks(geo, it));
+    for (BGeom geo : {BG_STENCIL, BG_FLAT, BG_SPAN, BG_SPAN_FINE, BG_ROWS}) m = std::max(m, bgeom_blocks(geo, it));
     return m;
 }
 

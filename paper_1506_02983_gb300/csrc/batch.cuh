@@ -67,7 +67,8 @@ struct BCtl {
 enum BGeom : int {
     BG_STENCIL = 0,  // 32 x 8 node tiles x kz planes (the z-march kernels)
     BG_FLAT,         // 4096 consecutive padded elements per block (whole-vector initialisation)
-    BG_SPAN,         // node plane spans (0,0,k)..(nx,ny,k): whole planes, or chunks of one, per block (updates)
+    BG_SPAN,         // node plane spans (0,0,k)..(nx,ny,k): whole planes, or chunks of one, per block (K2)
+    BG_SPAN_FINE,    // one chunk of at most 1024 vectors of one plane span per block (fold, max |x|)
     BG_NODES,        // 32 x 8 nodes of one plane per block
     BG_ELEMS,        // 32 x 8 elements of one slab per block
     BG_EXPF,         // 128 level-(l-2) elements per block
@@ -87,6 +88,9 @@ __host__ __device__ inline int span_v4(const Grid& g) { return (int)(((int64_t)g
 // a chunk of one plane of a large one, so that every block has enough work to pay for its
 // reduction.
 constexpr int SPAN_BLOCK_V4 = 4096;
+// The fold and max |x| of a replacement usually run on one problem alone: their blocks take
+// chunks of at most SPAN_FINE_V4 vectors of one plane, for more blocks on one problem.
+constexpr int SPAN_FINE_V4 = 1024;
 __host__ __device__ inline int span_planes_per_block(const Grid& g)
 {
     const int v = span_v4(g);
@@ -125,9 +129,11 @@ void blaunch_res(const BItem* items, const BLaunch& stencil, int robin, int cube
 void blaunch_update(const BItem* items, const BLaunch& flat, BCtl* ctl, CondHandles ch, cudaStream_t s);
 // Fold the FP32 correction into the FP64 iterate for items that asked for a replacement, and
 // take max |x| of the new iterate into the item's state (the scale of the exact residual).
-void blaunch_fold(const BItem* items, const BLaunch& flat, int pnew_is_b, cudaStream_t s);
-// max |x| of each running item's iterate into its state, before an initial residual.
-void blaunch_absmax(const BItem* items, const BLaunch& flat, cudaStream_t s);
+// fine: a BG_SPAN_FINE launch.
+void blaunch_fold(const BItem* items, const BLaunch& fine, int pnew_is_b, cudaStream_t s);
+// max |x| of each running item's iterate into its state, before an initial residual (fine: a
+// BG_SPAN_FINE launch).
+void blaunch_absmax(const BItem* items, const BLaunch& fine, cudaStream_t s);
 // EXP_true for levels >= 2.
 void blaunch_exp_true(const BItem* items, const BLaunch& expt, cudaStream_t s);
 
