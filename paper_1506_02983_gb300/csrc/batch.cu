@@ -57,8 +57,9 @@ __device__ __forceinline__ SpanRange span_of(const Grid& g, int lb)
 {
     const int nv = span_v4(g), ppb = span_planes_per_block(g), cpp = span_chunks_per_plane(g);
     if (cpp == 1) return SpanRange{lb * ppb, min((lb + 1) * ppb, g.nz + 1), 0, nv};
-    const int k = lb / cpp, c = lb - k * cpp;
-    return SpanRange{k, k + 1, c * SPAN_BLOCK_V4, min((c + 1) * SPAN_BLOCK_V4, nv)};
+    // a large plane in cpp chunks of (nearly) equal length
+    const int k = lb / cpp, c = lb - k * cpp, len = (nv + cpp - 1) / cpp;
+    return SpanRange{k, k + 1, c * len, min((c + 1) * len, nv)};
 }
 // The same for a BG_SPAN_FINE block: chunk c of at most SPAN_FINE_V4 vectors of plane k.
 __device__ __forceinline__ SpanRange span_fine_of(const Grid& g, int lb)
