@@ -563,6 +563,8 @@ def main():
     mixed = make(ecmg.ECMG_MIXED)
     torch.cuda.synchronize()
     create_ms = (time.perf_counter() - t_create) * 1e3
+    # slots of the ring of search directions on the two-pass levels (ECMG_RING_AUTO resolved)
+    ring_slots = mixed.ring_slots()
     u_out = torch.empty_like(u_exact)
     st_mixed, status = mixed.solve(u_out)
     assert status == 0, st_mixed
@@ -574,7 +576,8 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ecmg.kernel_launches()
-    mixed.stencil_timer(-1, reset=True)
+    for l in range(L):
+        mixed.stencil_timer(l, reset=True)
     torch.cuda.nvtx.range_push("ecmg_mixed_timed")
     ms_mixed = timed(lambda: mixed.solve(u_out), args.steps)
     torch.cuda.nvtx.range_pop()
@@ -583,7 +586,14 @@ def main():
     # K1 launches of the finest level inside the timed solves: the kernel's own device timer
     # (earliest block start to end of last block per launch; CUDA events cannot sit inside the
     # conditional-node bodies of the solve graph)
-    k1_live_total_ms, k1_live_n = mixed.stencil_timer(-1, reset=True)
+    k1_live_total_ms, k1_live_n = mixed.stencil_timer(-1)
+    # the FP32 step kernel's own device time per level and solve (K1, or the single-pass step),
+    # beside the level's device time: on the small levels the rest is launch, conditional-node
+    # and reduction latency
+    step_kernel_ms = []
+    for l in range(L):
+        t_ms, n_l = mixed.stencil_timer(l, reset=True)
+        step_kernel_ms.append({"ms_per_solve": t_ms / args.steps, "launches_per_solve": n_l / args.steps})
     st_mixed, status = mixed.solve(u_out)
     assert status == 0, st_mixed
     err_mixed = mixed.norms(u_out, u_exact)[0]
@@ -714,8 +724,12 @@ def main():
         except ValueError:
             pass
     k1_gbps = k1_bytes / k1_live_ms / 1e6
-    # bytes per node-iteration of the step each level runs: 32 single-pass, 36 two-pass
-    node_bytes = sum(free_dofs(n0 << l) * st_mixed["iters"][l] * (32.0 if sp_level(l) else 36.0) for l in range(L))
+    # bytes per node-iteration of the step each level runs: 32 single-pass; two-pass 36 with the
+    # correction vector (K1 24, K2 12), and with a ring of R search directions 28 (K1 16, K2 12)
+    # + 4 (each direction read back once) + 8 / (R - 2) (e written and read once per full ring)
+    two_pass_bytes = 36.0 if ring_slots == 0 else 32.0 + 8.0 / (ring_slots - 2)
+    node_bytes = sum(free_dofs(n0 << l) * st_mixed["iters"][l] * (32.0 if sp_level(l) else two_pass_bytes)
+                     for l in range(L))
     bpni = node_bytes / max(node_its, 1)
     out = {
         "metric": METRIC, "value": value, "unit": "Gdof/s", "n_gpus": world, "steps": args.steps,
@@ -726,8 +740,10 @@ def main():
         "max_err_mixed": err_mixed, "max_err_fp64": err_fp64,
         "err_ratio_mixed_over_fp64": err_mixed / err_fp64,
         "table_norms_finest": table_norms,
-        "iters_mixed": st_mixed["iters"], "updates_mixed": st_mixed["updates"], "iters_fp64": st64["iters"],
+        "iters_mixed": st_mixed["iters"], "updates_mixed": st_mixed["updates"],
+        "ring_slots_mixed": ring_slots, "iters_fp64": st64["iters"],
         "level_seconds_mixed": st_mixed["seconds"], "setup_seconds_mixed": st_mixed["setup_seconds"],
+        "step_kernel_per_level_mixed": step_kernel_ms,
         "rel_res_mixed": st_mixed["rel_res"], "gdofs_fp64": dofs / (ms_fp64 * 1e-3) / 1e9,
         "roofline": {"kernel": ("single-pass step (k_step32_cc on this one-beta all-Dirichlet level: residual "
                                 "update, search direction, 27-point operator and the dots in one pass)" if single else
@@ -744,8 +760,9 @@ def main():
         "kernels_alone": kern,
         # the two ways of counting dofs: finest free dofs per solve (value), and free dofs times
         # JCG iterations summed over the levels; the byte model charges each node-iteration the
-        # bytes the step moves on a constant-coefficient level: 36 for K1 and K2 (24 + 12), 32
-        # for the single-pass kernel (bytes_per_node_iteration is their iteration-weighted mean)
+        # bytes the step moves on a constant-coefficient level: about 32 for K1 and K2 with the
+        # ring of search directions (36 without), 32 for the single-pass kernel
+        # (bytes_per_node_iteration is their iteration-weighted mean)
         "node_iterations_per_solve": node_its,
         "gdofs_node_iterations": node_its * world / (ms_mixed * 1e-3) / 1e9,
         "byte_model": {"bytes_per_node_iteration": bpni, "bytes_per_solve": bpni * node_its,

@@ -91,6 +91,10 @@ enum { ECMG_CG_TWO_PASS = 0, ECMG_CG_SINGLE_PASS = 1, ECMG_CG_AUTO = 2 };
  * TWO_PASS on the larger ones, where both forms stream at their bandwidth and take the same
  * time per step. */
 #define ECMG_AUTO_SINGLE_PASS_NODES (1 << 22)
+
+/* ecmg_options.ring_slots: slots chosen by ecmg_create from the workspace and the device memory:
+ * 64, 8..63 or 0. */
+#define ECMG_RING_AUTO (-1)
 /* ecmg_get_level: which vector */
 enum { ECMG_VEC_U = 0, ECMG_VEC_W = 1, ECMG_VEC_UTILDE = 2, ECMG_VEC_B = 3, ECMG_VEC_BETA = 4 };
 
@@ -155,6 +159,19 @@ typedef struct {
     double sched_beta;      /* FIXED: beta of eq. (ee), 1..64                   [4.0]       */
     int32_t cg_form;        /* MIXED: ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS or ECMG_CG_AUTO (batched
                                handles run TWO_PASS for AUTO)                   [AUTO]     */
+    int32_t ring_slots;     /* MIXED two-pass levels of single-problem handles: ECMG_RING_AUTO, 0, or
+                               4..64 slots of a ring of FP32 search directions. Without a ring every
+                               FP32 step adds alpha_k p_k to a correction vector e (4 bytes read
+                               and 4 written per node); with one, the step only stores p_k, and
+                               e += alpha_k p_k runs over all pending directions at once when
+                               ring_slots - 2 are pending, and at a residual replacement, as the
+                               same FP32 fused multiply-adds in the same order: the solve is
+                               bit-identical to the one without a ring. Costs 4 ring_slots bytes
+                               per stored node of each such level. 0: no ring. ECMG_RING_AUTO: 64
+                               slots when the handle's workspace with them stays within 3/4 of the
+                               current device's memory, else the most slots (at least 8) that do,
+                               else 0; the choice depends only on the problem's sizes, the options
+                               and the device's total memory                     [AUTO]      */
 } ecmg_options;
 
 /* Per-solve statistics, one entry per level (coarsest first). */
@@ -280,7 +297,8 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
  * bracketed by CUDA events on the handle's stream, after one untimed launch. which:
  * 0 K1 FP32 (search direction + operator), 1 K2 FP32 (residual update), 2 FP64 residual with
  * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true, 8 ||f_h||,
- * 9 MIXED fold of the FP32 correction into the FP64 iterate (applied to U~), 10 max |U|,
+ * 9 MIXED fold of the FP32 correction into the FP64 iterate (applied to U~; on a level with a
+ * ring of search directions the fold of ring_slots - 2 pending directions), 10 max |U|,
  * 11 the single-pass FP32 step (handles created with ECMG_CG_SINGLE_PASS).
  * ms_out: mean duration of one launch (host). bytes_out: the algorithmic bytes one launch
  * must move (each owned input read once, each output written once; host); for kernel 0 the

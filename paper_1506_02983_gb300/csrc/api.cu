@@ -71,6 +71,10 @@ struct Level {
     float *beta32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *pA32 = nullptr, *pB32 = nullptr,
           *q32 = nullptr, *e32 = nullptr;
     float *r32B = nullptr, *q32B = nullptr;  // single-pass form: second r and q buffers
+    // two-pass form with a ring of search directions: R stored directions and their steps alpha
+    float* ring = nullptr;
+    double* ring_alpha = nullptr;
+    int R = 0;
     PlaneMaps maps;  // TMA descriptors of the FP32 vectors
     ResMaps rmaps;   // TMA descriptors of U and of b / c (exact constant-coefficient residual)
     K1Config k1{1, 128};  // tile shape of the FP32 stencil kernel
@@ -239,6 +243,8 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
         return fail(ECMG_ERR_INVALID_ARG, "bad schedule");
     if (o->cg_form != ECMG_CG_TWO_PASS && o->cg_form != ECMG_CG_SINGLE_PASS && o->cg_form != ECMG_CG_AUTO)
         return fail(ECMG_ERR_INVALID_ARG, "bad cg_form");
+    if (o->ring_slots != ECMG_RING_AUTO && o->ring_slots != 0 && (o->ring_slots < 4 || o->ring_slots > 64))
+        return fail(ECMG_ERR_INVALID_ARG, "ring_slots must be ECMG_RING_AUTO, 0 or in [4, 64]");
     if (o->schedule == ECMG_SCHED_FIXED) {
         if (o->sched_mL < 1 || !(o->sched_beta >= 1.0 && o->sched_beta <= 64.0))
             return fail(ECMG_ERR_INVALID_ARG, "fixed schedule: sched_mL >= 1 and sched_beta in [1, 64]");
@@ -249,11 +255,12 @@ ecmg_status validate(const ecmg_problem* p, const ecmg_options* o)
 }
 
 // Byte count of the per-level vectors (the same arithmetic ecmg_create performs).
-uint64_t level_bytes(const Grid& g, bool mixed, bool single_pass)
+uint64_t level_bytes(const Grid& g, bool mixed, bool single_pass, int ring_slots)
 {
     const uint64_t n = (uint64_t)g.total;
     uint64_t b = n * 8ull * 14ull;  // U W Ut b beta dinv f gD gR r pA pB q (+1 spare alignment)
     if (mixed) b += n * 4ull * (single_pass ? 9ull : 7ull);
+    if (ring_slots) b += (n * 4ull + 8ull) * (uint64_t)ring_slots;
     return b;
 }
 
@@ -272,6 +279,20 @@ bool single_pass_level(const ecmg_options& o, const Grid& g, int l)
     if (o.cg_form == ECMG_CG_SINGLE_PASS) return true;
     if (o.cg_form != ECMG_CG_AUTO) return false;
     return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1) < (int64_t)ECMG_AUTO_SINGLE_PASS_NODES;
+}
+
+// Slots of the ring of search directions on level l: the MIXED two-pass levels (>= 2) of a
+// single-problem handle with every face Dirichlet, when the option asks for one. A solve uses the
+// ring on such a level when it also has one beta: the constant-coefficient FP32 stencil kernel is
+// bound by DRAM bandwidth, so the correction-vector bytes it no longer moves are time saved; the
+// general kernel (beta and D^-1 streamed, Robin terms) runs below the bandwidth bound, and there
+// the directions the ring reads back at a replacement would cost more than they save.
+int ring_slots_level(const ecmg_problem& p, const ecmg_options& o, const Grid& g, int l)
+{
+    if (o.precision != ECMG_MIXED || l < 2 || single_pass_level(o, g, l)) return 0;
+    for (int f = 0; f < 6; ++f)
+        if (p.face_bc[f] != ECMG_BC_DIRICHLET) return 0;
+    return o.ring_slots;
 }
 
 template <typename T>
@@ -427,8 +448,13 @@ void record_level(Rec& R, int l)
     const double rtol = direct ? o.dsolve_rtol : (fixed ? 0.0 : o.rtol);
     const int max_iters = fixed ? schedule_steps(h->L, l, o.sched_mL, o.sched_beta) : o.max_iters;
     CondHandles none{0, 0, 0};
+    // eager: the set-up of this solve (or of the last one, for a solve from a finer level) has
+    // run, so the level's flag can be read now; a graph takes the choice made before its recording
+    if (mixed && !R.graph) v.cc = constant_coefficient(h, v);
+    // the ring of search directions runs with the constant-coefficient stencil kernel only
+    const bool ring_on = mixed && v.ring && v.cc;
 
-    launch_state_init(st, rtol, o.inner_rtol, max_iters, fixed ? 1 : 0, R.s());
+    launch_state_init(st, rtol, o.inner_rtol, max_iters, fixed ? 1 : 0, R.s(), ring_on ? v.R : 0);
     // levels >= 2: EXP_finite writes every free node below, so only the shell that ||f_h|| reads
     dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s(), /*shell=*/l >= 2);
     launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s());
@@ -474,13 +500,13 @@ void record_level(Rec& R, int l)
         if (o.true_residual)
             launch_res64(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv, v.r, st, h->part, RES_REPORT, none, R.s());
     } else {
-        // eager: the set-up of this solve (or of the last one, for a solve from a finer level)
-        // has run, so the level's flag can be read now; a graph takes the choice made before
-        // its recording
-        if (!R.graph) v.cc = constant_coefficient(h, v);
         ck(cudaMemsetAsync(v.pA32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.pB32, 0, (size_t)v.g.total * 4, R.s()));
         ck(cudaMemsetAsync(v.e32, 0, (size_t)v.g.total * 4, R.s()));
+        // ring: slot 0 holds the zero direction the first step reads (its beta is 0 as well)
+        if (ring_on) ck(cudaMemsetAsync(v.ring, 0, (size_t)v.g.total * 4, R.s()));
+        const RingArgs ring{v.ring, v.ring_alpha, v.R};
+        const RingArgs* rp = ring_on ? &ring : nullptr;
         // Step `half` of the loop body reads the buffers of set A (half 0) or B (half 1) and
         // writes the other set: p in both forms, r and q too in the single-pass form (which
         // keeps 0 in them on the nodes no step visits). The residual of the initial state and
@@ -496,13 +522,15 @@ void record_level(Rec& R, int l)
                               rbuf[o], v.e32, st, h->part, o, ch, h->timers + l, R.s());
             } else {
                 launch_pq32_tma(v.maps, half, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pbuf[o], v.q32,
-                                v.e32, st, h->part, o, ch, h->timers + l, R.s());
-                launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s());
+                                v.e32, st, h->part, o, ch, h->timers + l, R.s(), rp);
+                launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, ch, R.s(),
+                                rp, v.e32);
             }
         };
         auto replace = [&](int half) {
             const int o = half ^ 1;
-            launch_fold32(v.g, v.U, v.e32, pbuf[o], v.uniform, st, h->part, R.s());
+            if (ring_on) launch_fold_ring(v.g, v.U, ring, v.e32, v.uniform, st, h->part, R.s());
+            else launch_fold32(v.g, v.U, v.e32, pbuf[o], v.uniform, st, h->part, R.s());
             res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[o]);
         };
         if (R.graph) {
@@ -926,7 +954,15 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
         ck(cudaMemcpyAsync(&last, h->states + l, sizeof(last), cudaMemcpyDeviceToHost, s));
         ck(cudaStreamSynchronize(s));
         tmpl.bcbits = last.bcbits;
-        const bool cc = (which == 0 || which == 2 || which == 11) && constant_coefficient(h, v);
+        const bool cc = (which == 0 || which == 2 || which == 9 || which == 11) && constant_coefficient(h, v);
+        // a level that runs the ring: K1 reads p_old from slot 0 and writes slot 1; the fold adds
+        // the largest pending set a solve can hold
+        const bool ring_on = v.ring && cc && (which == 0 || which == 9);
+        if (ring_on) {
+            tmpl.pring = v.R;
+            tmpl.pend = which == 9 ? ring_cap(v.R) : 0;
+        }
+        const RingArgs ring{v.ring, v.ring_alpha, v.R};
         ck(cudaEventCreate(&e0));
         ck(cudaEventCreate(&e1));
         for (int rep = 0; rep <= reps; ++rep) {
@@ -935,7 +971,7 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
             switch (which) {
             case 0:
                 launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, cc, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32, v.e32, st,
-                                h->part, 1, none, nullptr, s);
+                                h->part, 1, none, nullptr, s, ring_on ? &ring : nullptr);
                 break;
             case 1: launch_update32(v.g, v.op, v.uniform, v.r32, v.q32, v.dinv32, st, h->part, none, s); break;
             case 2: {
@@ -959,7 +995,10 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
                 break;
             }
             case 8: launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, s); break;
-            case 9: launch_fold32(v.g, v.Ut, v.e32, v.pA32, v.uniform, st, h->part, s); break;
+            case 9:
+                if (ring_on) launch_fold_ring(v.g, v.Ut, ring, v.e32, v.uniform, st, h->part, s);
+                else launch_fold32(v.g, v.Ut, v.e32, v.pA32, v.uniform, st, h->part, s);
+                break;
             case 11:
                 launch_step32(v.maps, 0, v.k1, v.g, v.op, cc, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32B, v.r32B,
                               v.e32, st, h->part, 1, none, nullptr, s);
@@ -1162,25 +1201,64 @@ void ecmg_default_options(ecmg_options* o)
     o->sched_mL = 4;
     o->sched_beta = 4.0;
     o->cg_form = ECMG_CG_AUTO;
+    o->ring_slots = ECMG_RING_AUTO;
 }
+
+namespace {
+
+// Bytes of a single-problem handle's workspace (the arithmetic of ecmg_create's allocations),
+// with o.ring_slots already a slot count.
+uint64_t workspace_of(const ecmg_problem* p, const ecmg_options& o)
+{
+    uint64_t b = 0;
+    int maxb = 0;
+    for (int l = 0; l < p->levels; ++l) {
+        Grid g = make_grid(*p, l);
+        b += level_bytes(g, o.precision == ECMG_MIXED, single_pass_level(o, g, l), ring_slots_level(*p, o, g, l));
+        if (p->f_mode == ECMG_F_SEPARABLE) b += 8ull * (uint64_t)sep_factor_len(g, p->f_terms);
+        if (p->gD_terms > 0 && l < p->levels - 1) b += 8ull * (uint64_t)sep_factor_len(g, p->gD_terms);
+        maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
+        if (o.precision == ECMG_MIXED) maxb = std::max(maxb, std::max(max_tma_blocks(g), res_cc_blocks(g)));
+    }
+    return b + (uint64_t)maxb * partials_per_block(o) * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
+}
+
+// The slot count of ring_slots: ECMG_RING_AUTO takes 64 when the workspace with them stays
+// within 3/4 of the current device's total memory, else the most slots (>= 8) that do, else 0
+// (also when no device answers). A ring of R slots moves 4 + 8 / (R - 2) bytes per node and step
+// for the correction (the directions read once, e read and written once per R - 2 steps) against
+// 8 without a ring; 8 slots keep most of that gain.
+int resolve_ring_slots(const ecmg_problem* p, const ecmg_options& o)
+{
+    if (o.ring_slots != ECMG_RING_AUTO) return o.ring_slots;
+    ecmg_options z = o;
+    z.ring_slots = 0;
+    const uint64_t base = workspace_of(p, z);
+    z.ring_slots = 1;
+    const uint64_t per_slot = workspace_of(p, z) - base;
+    if (per_slot == 0) return 0;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const uint64_t budget = (uint64_t)prop.totalGlobalMem / 4 * 3;
+    if (budget <= base) return 0;
+    const uint64_t r = std::min<uint64_t>(64, (budget - base) / per_slot);
+    return r >= 8 ? (int)r : 0;
+}
+
+}  // namespace
 
 ecmg_status ecmg_workspace_bytes(const ecmg_problem* p, const ecmg_options* o, uint64_t* bytes)
 {
     ecmg_status s = validate(p, o);
     if (s != ECMG_OK) return s;
     if (!bytes) return fail(ECMG_ERR_INVALID_ARG, "bytes is null");
-    uint64_t b = 0;
-    int maxb = 0;
-    for (int l = 0; l < p->levels; ++l) {
-        Grid g = make_grid(*p, l);
-        b += level_bytes(g, o->precision == ECMG_MIXED, single_pass_level(*o, g, l));
-        if (p->f_mode == ECMG_F_SEPARABLE) b += 8ull * (uint64_t)sep_factor_len(g, p->f_terms);
-        if (p->gD_terms > 0 && l < p->levels - 1) b += 8ull * (uint64_t)sep_factor_len(g, p->gD_terms);
-        maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
-        if (o->precision == ECMG_MIXED) maxb = std::max(maxb, std::max(max_tma_blocks(g), res_cc_blocks(g)));
-    }
-    b += (uint64_t)maxb * partials_per_block(*o) * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
-    *bytes = b;
+    ecmg_options r = *o;
+    r.ring_slots = resolve_ring_slots(p, *o);
+    *bytes = workspace_of(p, r);
     return ECMG_OK;
 }
 
@@ -1207,6 +1285,7 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
     h->alloc_ctx = ctx;
     h->prob = pr;
     h->opt = *opt;
+    h->opt.ring_slots = resolve_ring_slots(&pr, *opt);
     h->user_stream = (cudaStream_t)stream;
     h->L = prob->levels;
     try {
@@ -1252,6 +1331,12 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
                     v.r32B = dalloc<float>(h, n);
                     v.q32B = dalloc<float>(h, n);
                     if (!make_plane_maps_sp(&v.maps, v.r32B, v.q32, v.q32B, v.g)) throw CudaFail{cudaErrorNotSupported};
+                }
+                if (const int R = ring_slots_level(h->prob, h->opt, v.g, l)) {
+                    v.R = R;
+                    v.ring = dalloc<float>(h, n * R);
+                    v.ring_alpha = dalloc<double>(h, R);
+                    if (!make_ring_maps(&v.maps, v.ring, R, v.g)) throw CudaFail{cudaErrorNotSupported};
                 }
                 v.k1 = k1_default(v.g, v.op);
                 maxb = std::max(maxb, std::max(max_tma_blocks(v.g), res_cc_blocks(v.g)));
@@ -1547,6 +1632,14 @@ ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision
     } else if (precision == ECMG_APPLY_K1) {
         if (!v.r32) return fail(ECMG_ERR_INVALID_ARG, "handle was created without MIXED precision");
         // p = D^-1 r + beta p_old with r = 0, beta = 1: p = x; q = A p; alpha_prev = 0: e untouched
+        bool cc = false;
+        try {
+            cc = constant_coefficient(h, v);
+        } catch (CudaFail& f) {
+            return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
+        }
+        // a level that runs the ring runs K1's ring form: p_old from slot 0, p into slot 1
+        const bool ring_on = v.ring && cc;
         SolveState* st = h->states + (MAX_LEVELS - 1);
         SolveState tmpl = {};
         tmpl.rho = 1.0;
@@ -1555,21 +1648,17 @@ ecmg_status ecmg_apply_operator(ecmg_handle* h, int32_t level, int32_t precision
         tmpl.max_iters = 1 << 30;
         tmpl.thresh2 = -1.0;
         tmpl.inner2 = -1.0;
+        if (ring_on) tmpl.pring = v.R;
         const size_t n4 = (size_t)v.g.total * 4;
         const CondHandles none{0, 0, 0};
         cudaError_t e = cudaMemcpyAsync(st, &tmpl, sizeof(tmpl), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(v.r32, 0, n4, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(v.q32, 0, n4, s);
         if (e != cudaSuccess) return fail(ECMG_ERR_CUDA, cudaGetErrorString(e));
-        convert_f32(v.r, v.pA32, v.g.total, s);
-        bool cc = false;
-        try {
-            cc = constant_coefficient(h, v);
-        } catch (CudaFail& f) {
-            return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
-        }
+        convert_f32(v.r, ring_on ? v.ring : v.pA32, v.g.total, s);
+        const RingArgs ring{v.ring, v.ring_alpha, v.R};
         launch_pq32_tma(v.maps, 0, v.k1, v.g, v.op, cc, v.uniform, v.beta32, v.dinv32, v.pB32, v.q32, v.e32, st, h->part,
-                        1, none, nullptr, s);
+                        1, none, nullptr, s, ring_on ? &ring : nullptr);
         convert_f64(v.q32, v.q, v.g.total, s);
     } else {
         return fail(ECMG_ERR_INVALID_ARG, "bad precision");
@@ -1713,9 +1802,14 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
     // the constant-coefficient residual (kernel 2) reads x and b / c and writes r: 20 bytes per
     // node; ||f_h|| (8) reads b; the fold (9) updates x and e and reads p; max |x| (10) reads x;
     // the single-pass step (11) moves r, q, p and e in and out (and D^-1, beta in)
-    const double bytes[12] = {(cc ? 24 * N1 : 28 * N1 + 4 * E), (cc ? 12 * N : 16 * N),
+    // with a ring of search directions K1 moves no correction vector (8 bytes fewer per node) and
+    // the fold reads ring_slots - 2 directions instead of e and p and writes no e
+    const bool ring_on = v.ring && cc;
+    const double e1 = ring_on ? 0.0 : 8.0;
+    const double bytes[12] = {(cc ? 16 + e1 : 20 + e1) * N1 + (cc ? 0.0 : 4 * E), (cc ? 12 * N : 16 * N),
                               (cc && v.op.cube ? 20 * N : 24 * N + 8 * E), 56 * N + 8 * E, 32 * N, 32 * N + 8 * E,
-                              16 * N + 8 * (N / 8 + N / 64), 17 * N, 8 * N, 28 * N, 8 * N,
+                              16 * N + 8 * (N / 8 + N / 64), 17 * N, 8 * N,
+                              ring_on ? (16.0 + 4.0 * ring_cap(v.R)) * N : 28 * N, 8 * N,
                               (cc ? 32 * N1 : 36 * N1 + 4 * E)};
     *bytes_out = bytes[which];
     try {

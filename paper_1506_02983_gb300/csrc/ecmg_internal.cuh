@@ -126,6 +126,29 @@ struct SolveState {
     unsigned long long bcbits;  // MIXED, constant coefficient: bits of max |b / c| (fixed-point scale)
     unsigned long long xbits;   // batched MIXED: bits of max |x| for the next exact residual (0 = not taken)
     int fixed;           // 1: exactly max_iters steps, no tolerance test (the schedule of Alg. 3)
+    // MIXED two-pass levels with a ring of search directions: the FP32 correction of the iterate,
+    // sum of alpha_k p_k since the last replacement, is formed from the stored directions (at a
+    // replacement, or into the correction vector when the ring fills) instead of being
+    // accumulated in a vector by every step
+    int pj;              // ring slot of the newest search direction
+    int pbase;           // ring slot of the oldest direction not yet added
+    int pend;            // directions not yet added
+    int pring;           // ring slots (0: no ring on this level)
+    int espill;          // 1 when the correction vector holds directions added from a full ring
+};
+// When this many directions are pending in a ring of pring slots, K2 adds them to the
+// correction vector (the next step must not overwrite a pending direction).
+__host__ __device__ inline int ring_cap(int pring) { return pring - 2; }
+
+// The ring of search directions of a two-pass MIXED level: R FP32 level vectors back to back,
+// the step alpha of the direction in each slot, and R. With a ring, K1 reads p_old from slot
+// st->pj, writes p to the next slot and records its alpha there, and moves no correction
+// vector; K2 adds a full ring to the correction vector e, and the fold of a replacement adds e
+// (when it holds anything) and the pending alpha p.
+struct RingArgs {
+    float* base;
+    double* alpha;
+    int R;
 };
 
 // Fixed-point scale of an iterate: bit pattern of max |x| (nonnegative doubles order like their

@@ -661,6 +661,49 @@ __global__ void __launch_bounds__(NT) k_apply(const Grid g, const Op op, const T
     }
 }
 
+// ---- ring of search directions (MIXED two-pass levels) -----------------------------------------
+constexpr int RING_MAX = 64;
+
+// The pending directions of a level's ring in shared memory, oldest first: their slots and their
+// steps alpha rounded to FP32 (the rounding the correction vector's e += alpha p applies). Every
+// thread of the block calls it; a barrier follows inside.
+__device__ __forceinline__ void ring_pending(const SolveState* st, const double* __restrict__ alpha, int R,
+                                             int* sslot, float* sa)
+{
+    const int pend = st->pend, pbase = st->pbase;
+    for (int t = threadIdx.x; t < pend; t += blockDim.x) {
+        const int slot = (pbase + t) % R;
+        sslot[t] = slot;
+        sa[t] = (float)alpha[slot];
+    }
+    __syncthreads();
+}
+
+// acc, then acc = fmaf(alpha_u, p_u, acc) over the pending directions u = 0 .. pend-1 at float4
+// index t of level vectors of length n: the fused multiply-adds the correction vector performs,
+// in its order. Four directions' loads are issued before their sums.
+__device__ __forceinline__ float4 ring_chain(float4 acc, const float* __restrict__ ring, int64_t n, const int* sslot,
+                                             const float* sa, int pend, int64_t t)
+{
+    auto dir = [&](int u) { return __ldcs(reinterpret_cast<const float4*>(ring + (int64_t)sslot[u] * n) + t); };
+    auto step = [&](float a, const float4 pv) {
+        acc.x = fmaf(a, pv.x, acc.x);
+        acc.y = fmaf(a, pv.y, acc.y);
+        acc.z = fmaf(a, pv.z, acc.z);
+        acc.w = fmaf(a, pv.w, acc.w);
+    };
+    int u = 0;
+    for (; u + 4 <= pend; u += 4) {
+        const float4 p0 = dir(u), p1 = dir(u + 1), p2 = dir(u + 2), p3 = dir(u + 3);
+        step(sa[u], p0);
+        step(sa[u + 1], p1);
+        step(sa[u + 2], p2);
+        step(sa[u + 3], p3);
+    }
+    for (; u < pend; ++u) step(sa[u], dir(u));
+    return acc;
+}
+
 // ---- K2: residual update and stopping test ----------------------------------------------------
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
@@ -671,11 +714,14 @@ __device__ __forceinline__ double& vget(double2& v, int c) { return c == 0 ? v.x
 // Flat over the padded vector, 16-byte vectors (the layout keeps total a multiple of 8).
 // cdiag: when not null and *uniform is set (one beta, every face Dirichlet), D^-1 is the constant
 // *cdiag on every free node (r = 0 on the others), so r.z = cdiag * r.r and D^-1 is not streamed.
+// MIXED with a ring of search directions (ring.base not null): when the ring is full (ring_cap
+// directions pending after this step's K1), the blocks also add the pending alpha p to the
+// correction vector e, oldest first, and the last block empties the ring.
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r, const T* __restrict__ q,
                                                     const T* __restrict__ dinv, SolveState* st,
                                                     double* partials, CondHandles ch, const int* uniform,
-                                                    const T* cdiag)
+                                                    const T* cdiag, const RingArgs ring, float* __restrict__ e)
 {
     COUNT_LAUNCH();
     if (st->done) {
@@ -695,6 +741,17 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
     const V* __restrict__ dv4 = reinterpret_cast<const V*>(dinv);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool cc = cdiag && *uniform;
+    const bool spill = MIXED && ring.base && st->pend >= ring_cap(st->pring);
+    if (spill) {
+        __shared__ int sslot[RING_MAX];
+        __shared__ float sa[RING_MAX];
+        ring_pending(st, ring.alpha, ring.R, sslot, sa);
+        const int pend = st->pend;
+        const bool es = st->espill != 0;
+        float4* e4 = reinterpret_cast<float4*>(e);
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n / 4; t += stride)
+            e4[t] = ring_chain(es ? e4[t] : make_float4(0.f, 0.f, 0.f, 0.f), ring.base, n, sslot, sa, pend, t);
+    }
     if (cc) {
         // one diagonal: r.z = D^-1 r.r, formed from ||r||^2 after the reduction
         for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += stride) {
@@ -726,6 +783,11 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
     double v[2] = {rz.value(), rr.value()};
     if (grid_sum<2>(v, partials, &st->arrive)) {
         if (cc) v[0] = (double)*cdiag * v[1];
+        if (spill) {  // every block has read the pending set above
+            st->pbase = (st->pj + 1) % st->pring;
+            st->pend = 0;
+            st->espill = 1;
+        }
         update_epilogue<MIXED>(st, v[0], v[1]);
         if (ch.use) {
             cudaGraphSetConditional(ch.loop, st->done ? 0u : 1u);
@@ -813,7 +875,7 @@ __global__ void __launch_bounds__(UPD_TPB) k_fold32(int64_t n, double* __restric
     }
 }
 
-__global__ void k_state_init(SolveState* st, double rtol, double inner, int max_iters, int fixed)
+__global__ void k_state_init(SolveState* st, double rtol, double inner, int max_iters, int fixed, int pring)
 {
     COUNT_LAUNCH();
     SolveState s = {};
@@ -821,7 +883,76 @@ __global__ void k_state_init(SolveState* st, double rtol, double inner, int max_
     s.inner2 = inner * inner;
     s.max_iters = max_iters;
     s.fixed = fixed;
+    s.pring = pring;  // pj = 0: slot 0 holds the zero direction p_{-1}
     *st = s;
+}
+
+// MIXED with a ring of search directions: x64 += e + the pending alpha p, formed in FP32 oldest
+// first (e only when a full ring was added to it since the last replacement; e is then zeroed):
+// the same fused multiply-adds, in the same order, as the correction vector of the form without
+// a ring, added with one FP64 operation. With the level's uniform flag set, also max |x| of the
+// new iterate into fs (as k_fold32).
+__global__ void __launch_bounds__(UPD_TPB) k_fold_ring(int64_t n, double* __restrict__ x, const float* __restrict__ ring,
+                                                      const double* __restrict__ alpha, int R, float* __restrict__ e,
+                                                      const int* __restrict__ uniform, const SolveState* st,
+                                                      FixedScale* fs, unsigned long long* partials)
+{
+    COUNT_LAUNCH();
+    if (st->done) return;
+    __shared__ float sa[RING_MAX];
+    __shared__ int sslot[RING_MAX];
+    __shared__ unsigned long long sh[UPD_TPB / 32];
+    __shared__ unsigned int ticket;
+    ring_pending(st, alpha, R, sslot, sa);
+    const int pend = st->pend;
+    const bool es = st->espill != 0;
+    const bool want_max = *uniform != 0;
+    unsigned long long m = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double2* x2 = reinterpret_cast<double2*>(x);
+    float4* e4 = reinterpret_cast<float4*>(e);
+    // n, a level's stored length, is a multiple of 8 (rows are padded to 8 elements): no tail
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n / 4; t += stride) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (es) {
+            acc = e4[t];
+            e4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        acc = ring_chain(acc, ring, n, sslot, sa, pend, t);
+        double2 xa = x2[2 * t], xb = x2[2 * t + 1];
+        xa.x += widen(acc.x);
+        xa.y += widen(acc.y);
+        xb.x += widen(acc.z);
+        xb.y += widen(acc.w);
+        x2[2 * t] = xa;
+        x2[2 * t + 1] = xb;
+        m = max(m, max(max(fx::abs_bits(xa.x), fx::abs_bits(xa.y)), max(fx::abs_bits(xb.x), fx::abs_bits(xb.y))));
+    }
+    if (!want_max) return;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
+        partials[blockIdx.x] = m;
+        __threadfence();
+        ticket = atomicAdd(&fs->arrive, 1u);
+    }
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    m = 0ull;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = max(m, __ldcg(&partials[b]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if (lane == 0) sh[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
+        fs->bits = m;
+        fs->arrive = 0u;
+    }
 }
 
 inline bool has_robin(const Op& op)
@@ -952,17 +1083,19 @@ void launch_update64(const Grid& g, double* r, const double* q, const double* di
                      Partials pr, CondHandles ch, cudaStream_t s)
 {
     k_update<double, false><<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, r, q, dinv, st, pr.buf, ch,
-                                                                        nullptr, nullptr);
+                                                                        nullptr, nullptr,
+                                                                        RingArgs{nullptr, nullptr, 0}, nullptr);
 }
 void launch_update32(const Grid& g, const Op& op, const int* uniform, float* r, const float* q, const float* dinv,
-                     SolveState* st, Partials pr, CondHandles ch, cudaStream_t s)
+                     SolveState* st, Partials pr, CondHandles ch, cudaStream_t s, const RingArgs* ring, float* e)
 {
     bool diri = uniform != nullptr;
     for (int f = 0; f < 6; ++f) diri &= op.bc[f] == 0;
     // an interior node: free whenever every face is Dirichlet (levels >= 2 have >= 4 elements per axis)
     const float* cdiag = diri && g.nx >= 2 && g.ny >= 2 && g.nz >= 2 ? dinv + g.off(1, 1, 1) : nullptr;
+    const RingArgs rg = ring ? *ring : RingArgs{nullptr, nullptr, 0};
     k_update<float, true><<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, r, q, dinv, st, pr.buf, ch, uniform,
-                                                                      cdiag);
+                                                                      cdiag, rg, e);
 }
 void launch_final64(const Grid& g, double* x, const double* pA, const double* pB, SolveState* st,
                     cudaStream_t s)
@@ -975,9 +1108,16 @@ void launch_fold32(const Grid& g, double* x, float* e, const float* p, const int
     k_fold32<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, e, p, uniform, st, pr.fs,
                                                         reinterpret_cast<unsigned long long*>(pr.buf));
 }
-void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed, cudaStream_t s)
+void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed, cudaStream_t s,
+                       int pring)
 {
-    k_state_init<<<1, 1, 0, s>>>(st, rtol, inner_rtol, max_iters, fixed);
+    k_state_init<<<1, 1, 0, s>>>(st, rtol, inner_rtol, max_iters, fixed, pring);
+}
+void launch_fold_ring(const Grid& g, double* x, const RingArgs& ring, float* e, const int* uniform, SolveState* st,
+                      Partials pr, cudaStream_t s)
+{
+    k_fold_ring<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, ring.base, ring.alpha, ring.R, e, uniform, st,
+                                                           pr.fs, reinterpret_cast<unsigned long long*>(pr.buf));
 }
 
 unsigned long long launches_jcg()

@@ -59,9 +59,11 @@ void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv,
                      SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);
 // uniform: the level's device flag; with every face Dirichlet and the flag set, D^-1 is one
-// constant on the free nodes and is not streamed.
+// constant on the free nodes and is not streamed. ring: the level's ring of search directions
+// (or nullptr); when it is full this step also adds the pending alpha p to the correction vector e.
 void launch_update32(const Grid& g, const Op& op, const int* uniform, float* r, const float* q, const float* dinv,
-                     SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);
+                     SolveState* st, Partials pr, CondHandles ch, cudaStream_t s, const RingArgs* ring = nullptr,
+                     float* e = nullptr);
 
 // x += alpha_prev p_latest (FP64 JCG exit).
 void launch_final64(const Grid& g, double* x, const double* pA, const double* pB,
@@ -70,9 +72,15 @@ void launch_final64(const Grid& g, double* x, const double* pA, const double* pB
 // uniform flag set, also max |x| of the new iterate into pr.fs (what launch_absmax computes).
 void launch_fold32(const Grid& g, double* x, float* e, const float* p, const int* uniform, SolveState* st,
                    Partials pr, cudaStream_t s);
-// Reset the level state before a solve; fixed: run exactly max_iters steps (Alg. 3).
+// Reset the level state before a solve; fixed: run exactly max_iters steps (Alg. 3); pring: the
+// slots of the level's ring of search directions (0: none).
 void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed,
-                       cudaStream_t s);
+                       cudaStream_t s, int pring = 0);
+// MIXED with a ring of search directions: x64 += e + the pending alpha p (FP32 sum, one FP64 add;
+// e only when a full ring was added to it, and then e = 0); with the level's uniform flag set,
+// also max |x| of the new iterate into pr.fs.
+void launch_fold_ring(const Grid& g, double* x, const RingArgs& ring, float* e, const int* uniform, SolveState* st,
+                      Partials pr, cudaStream_t s);
 
 int max_stencil_blocks(const Grid& g);
 int max_stream_blocks();

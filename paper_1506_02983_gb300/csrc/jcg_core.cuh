@@ -61,6 +61,11 @@ __device__ __forceinline__ void res_epilogue(SolveState* st, double rr, double r
         st->beta = 0.0;
         st->alpha_prev = 0.0;
         st->need_update = 0;
+        if (st->pring) {  // the ring starts empty after the newest (zero) direction
+            st->pbase = (st->pj + 1) % st->pring;
+            st->pend = 0;
+            st->espill = 0;
+        }
         if (!isfinite(rr) || !isfinite(rz)) {
             st->status = 4;
             st->done = 1;
@@ -74,6 +79,11 @@ __device__ __forceinline__ void res_epilogue(SolveState* st, double rr, double r
         st->rr_true = rr;
         st->alpha_prev = 0.0;
         st->need_update = 0;
+        if (st->pring) {  // the fold before this residual added every pending direction and e
+            st->pbase = (st->pj + 1) % st->pring;
+            st->pend = 0;
+            st->espill = 0;
+        }
         if (!isfinite(rr) || !isfinite(rz)) {
             st->status = 4;
             st->done = 1;

@@ -193,6 +193,7 @@ struct K1Scalars {
     float ap;     // alpha of the previous step (deferred correction e += ap p_old)
     float cdinv;  // CC: the constant D^-1
     float bu;     // CC: the constant beta
+    int pw = -1;  // ring slot of p_old (ring of search directions; -1: p_old is its own vector)
 };
 
 // Last block of a single-pass step. alpha comes from the measured r.z (this step's r) and p.q;
@@ -244,7 +245,8 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
                                         const Grid& g, const Op& op, const Range& rg, float* __restrict__ pnew,
                                         float* __restrict__ q, float* __restrict__ rnew, float* __restrict__ e,
                                         SolveState* st, double* partials, int pidx, CondHandles ch, int kz,
-                                        KTimer* tm, const K1Scalars sc, const K1Block kb)
+                                        KTimer* tm, const K1Scalars sc, const K1Block kb,
+                                        double* ring_alpha = nullptr, int ring_R = 0)
 {
     using S = Shape<RY>;
     extern __shared__ __align__(128) unsigned char k1_smem[];
@@ -303,7 +305,8 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
         const int kk = P0 + t;
         mbar_expect_tx(b, stage_bytes);
         tma_load_3d(box(slot, 0), &m_r, bx, j0, kk + 1, b);
-        tma_load_3d(box(slot, 1), &m_pold, bx, j0, kk + 1, b);
+        if (sc.pw >= 0) tma_load_4d(box(slot, 1), &m_pold, bx, j0, kk + 1, sc.pw, b);
+        else tma_load_3d(box(slot, 1), &m_pold, bx, j0, kk + 1, b);
         if (!CC) {
             tma_load_3d(box(slot, 2), &m_dinv, bx, j0, kk + 1, b);
             tma_load_3d(box(slot, 3), &m_beta, bx, j0, kk, b);
@@ -579,6 +582,13 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
             if (ch.use) cudaGraphSetConditional(ch.loop, 0);
         } else {
             st->alpha = st->rho / pq;
+            if (ring_alpha) {
+                // the new direction is pending in the next ring slot with its step alpha
+                const int jn = (sc.pw + 1) % ring_R;
+                ring_alpha[jn] = st->alpha;
+                st->pj = jn;
+                st->pend += 1;
+            }
         }
     }
 }

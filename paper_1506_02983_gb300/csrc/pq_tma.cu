@@ -14,6 +14,18 @@ __device__ unsigned long long g_launches = 0;  // kernel executions of this file
     if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0) \
         atomicAdd(&g_launches, 1ull)
 
+// With a ring of search directions (ring.base not null; m_pold is then the ring's 4D map): p_old
+// from slot st->pj, p into the next slot, no deferred correction (ap = 0: e is neither read nor
+// written; K2 and the fold of a replacement add the pending alpha p from the ring).
+__device__ __forceinline__ float* ring_scalars(K1Scalars& sc, float* pnew, const SolveState* st, const Grid& g,
+                                               const RingArgs& ring)
+{
+    if (!ring.base) return pnew;
+    sc.pw = st->pj;
+    sc.ap = 0.f;
+    return ring.base + (int64_t)((sc.pw + 1) % ring.R) * g.total;
+}
+
 // General path: beta and D^-1 streamed with r and p_old.
 template <bool ROBIN, bool CUBE, int RY>
 __global__ void __launch_bounds__(NT, RY == 1 ? (ROBIN ? 3 : 4) : 2)
@@ -41,12 +53,12 @@ k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUten
           const __grid_constant__ CUtensorMap m_e, const Grid g, const Op op, const Range rg,
           float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e, SolveState* st, double* partials,
           int pidx, CondHandles ch, int kz, KTimer* tm, const int* __restrict__ uniform,
-          const float* __restrict__ beta32, const float* __restrict__ dinv32)
+          const float* __restrict__ beta32, const float* __restrict__ dinv32, const RingArgs ring)
 {
     COUNT_LAUNCH();
     const int uni = *uniform;
-    const K1Scalars sc{st->done, (float)st->beta, (float)st->alpha_prev, dinv32[g.off(1, 1, 1)],
-                       beta32[g.off(0, 0, 0)]};
+    K1Scalars sc{st->done, (float)st->beta, (float)st->alpha_prev, dinv32[g.off(1, 1, 1)], beta32[g.off(0, 0, 0)]};
+    pnew = ring_scalars(sc, pnew, st, g, ring);
     if (!uni) {
         if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0 && !sc.done) {
             st->status = 6;
@@ -56,7 +68,7 @@ k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUten
         return;
     }
     k1_body<false, CUBE, RY, true, false>(m_r, m_pold, m_r, m_r, m_r, m_e, g, op, rg, pnew, q, nullptr, e, st, partials,
-                                          pidx, ch, kz, tm, sc, k1_block_of_grid());
+                                          pidx, ch, kz, tm, sc, k1_block_of_grid(), ring.alpha, ring.R);
 }
 
 bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy, int sx = SX)
@@ -92,15 +104,18 @@ cudaError_t prepare_ry()
 template <int RY>
 void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
                const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
-               SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s)
+               SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s,
+               const RingArgs* ring)
 {
     const int v = ry_index(RY);
     const Range rg = k1_range(g, op);
     const CUtensorMap& pold = pold_is_b ? m.pB[v] : m.pA[v];
     if (cc) {
+        const RingArgs ra = ring ? *ring : RingArgs{nullptr, nullptr, 0};
         auto kern = op.cube ? k_pq32_cc<true, RY> : k_pq32_cc<false, RY>;
         kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, true, false>(), s>>>(
-            m.r[v], pold, m.e[v], g, op, rg, pnew, q, e, st, pr.buf, pidx, ch, c.kz, tm, uniform, beta32, dinv32);
+            m.r[v], ring ? m.ring[v] : pold, m.e[v], g, op, rg, pnew, q, e, st, pr.buf, pidx, ch, c.kz, tm, uniform,
+            beta32, dinv32, ra);
         return;
     }
     bool robin = false;
@@ -123,6 +138,13 @@ bool make_plane_maps(PlaneMaps* m, const float* r, const float* pA, const float*
             !make_plane_map(&m->beta[v], beta, g, sy) || !make_plane_map(&m->e[v], e, g, TBY * K1_RY[v], EX))
             return false;
     }
+    return true;
+}
+
+bool make_ring_maps(PlaneMaps* m, const float* ring, int R, const Grid& g)
+{
+    for (int v = 0; v < K1_NRY; ++v)
+        if (!encode_ring_map(&m->ring[v], ring, g, R, SX, TBY * K1_RY[v] + 2)) return false;
     return true;
 }
 
@@ -190,11 +212,12 @@ int max_tma_blocks(const Grid& g)
 
 void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
                      const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
-                     SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s)
+                     SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s,
+                     const RingArgs* ring)
 {
     if (c.ry == 1)
-        launch_ry<1>(m, pold_is_b, c, g, op, cc, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
-    else launch_ry<2>(m, pold_is_b, c, g, op, cc, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s);
+        launch_ry<1>(m, pold_is_b, c, g, op, cc, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s, ring);
+    else launch_ry<2>(m, pold_is_b, c, g, op, cc, uniform, beta32, dinv32, pnew, q, e, st, pr, pidx, ch, tm, s, ring);
 }
 
 unsigned long long launches_pq_tma()

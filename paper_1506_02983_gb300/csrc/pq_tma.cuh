@@ -17,7 +17,9 @@ constexpr int K1_RY[K1_NRY] = {1, 2};
 struct PlaneMaps {
     CUtensorMap r[K1_NRY], pA[K1_NRY], pB[K1_NRY], dinv[K1_NRY], beta[K1_NRY], e[K1_NRY];
     CUtensorMap rB[K1_NRY], qA[K1_NRY], qB[K1_NRY];
+    CUtensorMap ring[K1_NRY];  // 4D: the ring of search directions (two-pass MIXED levels)
 };
+
 
 // Tile shape of K1 on one level: ry node rows per thread, kz planes marched per block.
 struct K1Config {
@@ -32,6 +34,8 @@ bool make_plane_maps(PlaneMaps* m, const float* r, const float* pA, const float*
 
 // The single-pass buffers of a level: second residual buffer and the two q buffers.
 bool make_plane_maps_sp(PlaneMaps* m, const float* rB, const float* qA, const float* qB, const Grid& g);
+// The 4D maps of a level's ring of R search directions.
+bool make_ring_maps(PlaneMaps* m, const float* ring, int R, const Grid& g);
 
 // Set the shared-memory limit of every K1 instantiation (both forms) on the current device.
 cudaError_t k1_prepare();
@@ -50,9 +54,13 @@ int max_tma_blocks(const Grid& g);
 // from beta32 and dinv32 instead of streamed. If the flag is clear when the kernel runs, it
 // records status 6 (stale path) in st and finishes the level without computing.
 // tm: device timer that accumulates the durations of these launches, or nullptr.
+// ring: the level's ring of search directions, or nullptr (pold_is_b, pnew and e are then used);
+// the constant-coefficient kernel only (cc true): the general kernel takes no ring, and a caller
+// passes one only with cc.
 void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
                      const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* q, float* e,
-                     SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s);
+                     SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm, cudaStream_t s,
+                     const RingArgs* ring = nullptr);
 
 // Single-pass step (ECMG_CG_SINGLE_PASS): with (r_in, q_in, p_old) the buffers A (in_b = 0) or
 // B (in_b = 1) and the outputs the other three: r = r_in - alpha_prev q_in, e += alpha_prev p_old,

@@ -50,6 +50,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// 4D box load: (x, y, z) in one level vector, w the vector of a ring of them.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
 }  // namespace tma
 
 struct Grid;
@@ -57,5 +68,8 @@ struct Grid;
 // whole padded box, boxes of sx x sy x 1 elements, out-of-bounds reads filled with zeros.
 // False if the driver entry point is unavailable or the encoding is rejected.
 bool encode_level_map(CUtensorMap* map, bool fp64, const void* base, const Grid& g, int sx, int sy);
+// The same for a ring of nvec FP32 level vectors stored back to back (vector w at base + w
+// total): a 4D map whose fourth coordinate picks the vector.
+bool encode_ring_map(CUtensorMap* map, const float* base, const Grid& g, int nvec, int sx, int sy);
 
 }  // namespace ecmg

@@ -31,6 +31,7 @@ ECMG_SCHED_TOLERANCE, ECMG_SCHED_FIXED = 0, 1
 ECMG_CG_TWO_PASS, ECMG_CG_SINGLE_PASS, ECMG_CG_AUTO = 0, 1, 2
 ECMG_NOALLOC_MAX_ELEMS = 536870912  # include/ecmg.h
 ECMG_AUTO_SINGLE_PASS_NODES = 1 << 22  # include/ecmg.h
+ECMG_RING_AUTO = -1
 
 
 class ecmg_problem(C.Structure):
@@ -47,7 +48,8 @@ class ecmg_options(C.Structure):
                 ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("dsolve_rtol", C.c_double),
                 ("exp_variant", C.c_int32), ("true_residual", C.c_int32), ("autotune", C.c_int32),
                 ("preconditioner", C.c_int32), ("schedule", C.c_int32), ("sched_mL", C.c_int32),
-                ("sched_beta", C.c_double), ("cg_form", C.c_int32)]
+                ("sched_beta", C.c_double), ("cg_form", C.c_int32),
+                ("ring_slots", C.c_int32)]
 
 
 class ecmg_stats(C.Structure):
@@ -193,6 +195,24 @@ class Solver:
         else:
             check(ecmg_create(C.byref(p), C.byref(self.options), _stream(), C.byref(h)), "ecmg_create")
         self.handle = h
+
+    def workspace_bytes(self, **override):
+        """ecmg_workspace_bytes of this solver's problem and options (keywords override options)."""
+        o = ecmg_options.from_buffer_copy(self.options)
+        for k, v in override.items():
+            setattr(o, k, v)
+        n = C.c_uint64()
+        check(ecmg_workspace_bytes(C.byref(self.problem), C.byref(o), C.byref(n)), "ecmg_workspace_bytes")
+        return n.value
+
+    def ring_slots(self):
+        """The slots of the ring of search directions ecmg_create gave the two-pass levels
+        (ECMG_RING_AUTO resolved), from the workspace byte counts; 0 when no level has one."""
+        if self.options.ring_slots != ECMG_RING_AUTO:
+            return int(self.options.ring_slots)
+        base = self.workspace_bytes(ring_slots=0)
+        per_slot = (self.workspace_bytes(ring_slots=4) - base) // 4
+        return 0 if per_slot == 0 else (self.workspace_bytes() - base) // per_slot
 
     def level_shape(self, level=-1):
         l = self.levels - 1 if level < 0 else level

@@ -237,8 +237,8 @@ def test_workspace_of_the_step_forms_without_gpu(libpath):
     p.beta = 16
     p.f = 16
 
-    def ws(form):
-        o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=form)
+    def ws(form, ring_slots=0):
+        o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=form, ring_slots=ring_slots)
         n = ctypes.c_uint64()
         assert ecmg.ecmg_workspace_bytes(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == 0
         return n.value
@@ -255,6 +255,19 @@ def test_workspace_of_the_step_forms_without_gpu(libpath):
     assert single - auto == sum(8 * total(l) for l in range(2, 7) if l not in small)
     extra = single - two - sum(8 * total(l) for l in range(2, 7))
     assert extra > 0 and extra % (5 * 8) == 0  # 5 more doubles per block of the largest grid
+    # the ring of search directions: 4 bytes per stored node and 8 bytes of alpha per slot on
+    # every two-pass level >= 2, nothing on single-pass levels
+    for slots in (4, 34, 64):
+        assert ws(ecmg.ECMG_CG_TWO_PASS, slots) - two == sum((4 * total(l) + 8) * slots for l in range(2, 7))
+        assert ws(ecmg.ECMG_CG_AUTO, slots) - auto == sum((4 * total(l) + 8) * slots for l in (5, 6))
+        assert ws(ecmg.ECMG_CG_SINGLE_PASS, slots) == single
+    o = ecmg.default_options()
+    assert o.ring_slots == ecmg.ECMG_RING_AUTO
+    for bad in (1, 3, 65, -2):
+        o = ecmg.default_options(precision=ecmg.ECMG_MIXED, ring_slots=bad)
+        n = ctypes.c_uint64()
+        assert ecmg.ecmg_workspace_bytes(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == \
+            ecmg.ECMG_ERR_INVALID_ARG, bad
 
 
 def test_binding_fails_loudly_without_the_library(tmp_path):
@@ -269,3 +282,26 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError, match="no fallback"):
         spec.loader.exec_module(mod)
+
+
+def test_ring_auto_resolves_to_none_without_a_device(libpath):
+    """ECMG_RING_AUTO sizes the ring from the device's memory; with no device it keeps the
+    correction vector (0 slots)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present (tests/test_gpu_ring.py covers the choice there)")
+    from paper_1506_02983_gb300 import ecmg
+    p = ecmg.ecmg_problem()
+    p.n0[:] = [8, 8, 8]
+    p.levels = 6
+    p.lo[:] = [0, 0, 0]
+    p.hi[:] = [1, 1, 1]
+    p.beta = 16
+    p.f = 16
+    n = {}
+    for slots in (ecmg.ECMG_RING_AUTO, 0):
+        o = ecmg.default_options(precision=ecmg.ECMG_MIXED, cg_form=ecmg.ECMG_CG_TWO_PASS, ring_slots=slots)
+        b = ctypes.c_uint64()
+        assert ecmg.ecmg_workspace_bytes(ctypes.byref(p), ctypes.byref(o), ctypes.byref(b)) == 0
+        n[slots] = b.value
+    assert n[ecmg.ECMG_RING_AUTO] == n[0]

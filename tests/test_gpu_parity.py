@@ -460,13 +460,15 @@ K1_PROBLEMS = {
 
 @pytest.mark.parametrize("name", sorted(K1_PROBLEMS))
 @pytest.mark.parametrize("tiles", [None, (1, 4), (2, 4), (2, 7)])
-def test_k1_operator_matches_csr(E, oracle_mod, name, tiles):
+@pytest.mark.parametrize("cg_form", [2, 0])  # default (single-pass levels), two-pass (ring form of K1)
+def test_k1_operator_matches_csr(E, oracle_mod, name, tiles, cg_form):
     """q = A p from the kernel the MIXED iteration runs (ECMG_APPLY_K1) against the oracle's
     assembled matrix on the nodes off Dirichlet faces: FP32 bar 1e-5 of max |A x|. Small kz
-    spreads a level over several z-blocks with a ragged last one."""
+    spreads a level over several z-blocks with a ragged last one. On two-pass levels the kernel
+    reads p_old from the level's ring of search directions (4D tensor map)."""
     import torch
     p = K1_PROBLEMS[name]()
-    s = E.solver_from_problem(p, precision=1)
+    s = E.solver_from_problem(p, precision=1, cg_form=cg_form)
     s.solve()
     betas = _oracle_levels(oracle_mod, p)
     for l in range(2, p["levels"]):
