@@ -21,6 +21,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "jcg.cuh"
 #include "jcg_core.cuh"
 #include "pq_tma.cuh"
@@ -113,6 +115,15 @@ struct KSum {
         const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
         s = t;
         c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    // plain FP32 term (TwoSum only)
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        s = t;
+        c = __fadd_rn(c, err);
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
@@ -354,18 +365,24 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     // One plane: stage t brings node plane kk = P0 + t into wp and beta slab kk-1 into bn;
     // then node plane kk-1 is computed from the window (wm, w0, wp) = planes (kk-2, kk-1, kk)
     // and the slabs (bo, bn) = (kk-2, kk-1). The caller rotates the arrays instead of moving
-    // values, so the unrolled loop below needs no register copies.
-    auto step = [&](float(&wm)[RY + 2][3], float(&w0)[RY + 2][3], float(&wp)[RY + 2][3],
+    // values, so the unrolled loop below needs no register copies. Jc is the step's position
+    // J = t mod 6 in that loop: with a 6-stage ring (the two-pass constant-coefficient path) the
+    // ring slot is J and the formed-plane buffer J mod 2, both known at compile time, so every
+    // shared-memory address below is a register plus a constant.
+    auto step = [&](auto Jc, float(&wm)[RY + 2][3], float(&w0)[RY + 2][3], float(&wp)[RY + 2][3],
                     float(&bo)[RY + 1][2], float(&bn)[RY + 1][2], PlaneSums<RY>& sm, PlaneSums<RY>& s0,
                     PlaneSums<RY>& sp) {
+        constexpr int J = decltype(Jc)::value;
+        constexpr bool FS = NS == 6;
+        const int cs = FS ? J : slot;
         const int kk = P0 + t;
-        const float* Sr = box(slot, 0);
-        const float* Sp = box(slot, 1);
-        const float* Sd = box(slot, 2);
-        const float* Sbeta = box(slot, 3);
-        const float* Sq = box(slot, AQ);
-        const float* Se = box(slot, NA);
-        if (!mbar_wait(&bar[slot], phase)) bad = 1;
+        const float* Sr = box(cs, 0);
+        const float* Sp = box(cs, 1);
+        const float* Sd = box(cs, 2);
+        const float* Sbeta = box(cs, 3);
+        const float* Sq = box(cs, AQ);
+        const float* Se = box(cs, NA);
+        if (!mbar_wait(&bar[cs], phase)) bad = 1;
         t_done = t;
         // e of the nodes computed at the next step (plane kk), from this stage: read before the
         // next step's barrier, after which the slot may be refilled
@@ -373,7 +390,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
 #pragma unroll
         for (int r = 0; r < RY; ++r) e_next[r] = ap != 0.f ? Se[(ty * RY + r) * EX + tx + 1 + sh] : 0.f;
         // form p of plane kk for the tile plus halo
-        float* Pk = &P[kk & 1][0][0];
+        float* Pk = &P[FS ? (J & 1) : (kk & 1)][0][0];
 #pragma unroll
         for (int f = 0; f < S::NFORM; ++f) {
             const int s = sidx[f];
@@ -387,7 +404,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int so = (ty * RY + r + 1) * SX + tx + 1 + sh;
-            pown_new[r] = Sp[so];
+            pown_new[r] = ap != 0.f ? Sp[so] : 0.f;  // only the correction e += ap p_old reads it
             if (SP) {
                 float rv = Sr[so];
                 if (ap != 0.f) rv = fmaf(-ap, Sq[so], rv);  // as the formed value of this node
@@ -401,10 +418,10 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
             return;
         }
         if (tid == 0 && t >= 1 && t - 1 + NS < nplanes) {
-            issue(t - 1 + NS, slot == 0 ? NS - 1 : slot - 1);  // the slot of stage t-1
+            issue(t - 1 + NS, FS ? (J + NS - 1) % NS : (slot == 0 ? NS - 1 : slot - 1));  // the slot of stage t-1
             issued_hi = t - 1 + NS;
         }
-        const float(*Pp)[S::PX] = P[kk & 1];
+        const float(*Pp)[S::PX] = P[FS ? (J & 1) : (kk & 1)];
         if (CC) {
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
@@ -431,6 +448,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
 
         if (t >= 2) {
             const int k = kk - 1;
+            float pq_plane = 0.f;  // two-pass: p.q of this plane's own nodes, one TwoSum per plane
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 if (r < nown) {
@@ -463,7 +481,8 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
                     pnew[orr] = xc;
                     q[orr] = Av;
                     if (ap != 0.f) e[orr] = fmaf(ap, pown_prev[r], e_cur[r]);
-                    acc.add_prod(xc, Av);
+                    if (SP) acc.add_prod(xc, Av);
+                    else pq_plane = fmaf(xc, Av, pq_plane);
                     if (SP) {
                         const float rc = r_cur[r];
                         rnew[orr] = rc;
@@ -479,6 +498,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
                     }
                 }
             }
+            if (!SP) acc.add(pq_plane);
         }
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
@@ -497,18 +517,19 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
         if (++t >= nplanes) stop = true;
     };
     // period 6 = lcm(3 window planes, 2 beta slabs)
+    using std::integral_constant;
     for (;;) {
-        step(wA, wB, wC, bA, bB, sA, sB, sC);
+        step(integral_constant<int, 0>{}, wA, wB, wC, bA, bB, sA, sB, sC);
         if (stop) break;
-        step(wB, wC, wA, bB, bA, sB, sC, sA);
+        step(integral_constant<int, 1>{}, wB, wC, wA, bB, bA, sB, sC, sA);
         if (stop) break;
-        step(wC, wA, wB, bA, bB, sC, sA, sB);
+        step(integral_constant<int, 2>{}, wC, wA, wB, bA, bB, sC, sA, sB);
         if (stop) break;
-        step(wA, wB, wC, bB, bA, sA, sB, sC);
+        step(integral_constant<int, 3>{}, wA, wB, wC, bB, bA, sA, sB, sC);
         if (stop) break;
-        step(wB, wC, wA, bA, bB, sB, sC, sA);
+        step(integral_constant<int, 4>{}, wB, wC, wA, bA, bB, sB, sC, sA);
         if (stop) break;
-        step(wC, wA, wB, bB, bA, sC, sA, sB);
+        step(integral_constant<int, 5>{}, wC, wA, wB, bB, bA, sC, sA, sB);
         if (stop) break;
     }
 
