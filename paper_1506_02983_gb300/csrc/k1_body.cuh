@@ -71,13 +71,13 @@ constexpr int k1_stages()
 }
 
 // Dynamic shared memory of a block: the stage ring (the staged arrays, then e of the tile's
-// own rows) plus slack to align it to 128 B (TMA destinations must be 128-byte aligned; the
-// runtime only guarantees 16).
-template <int RY, bool CC, bool SP>
+// own rows unless NOE: the kernels of a ring of search directions move no e) plus slack to
+// align it to 128 B (TMA destinations must be 128-byte aligned; the runtime only guarantees 16).
+template <int RY, bool CC, bool SP, bool NOE = false>
 constexpr size_t stage_smem()
 {
-    return (size_t)k1_stages<CC, SP>() * (k1_arrays<CC, SP>() * Shape<RY>::BOXF_PAD + Shape<RY>::EBOXF_PAD) *
-               sizeof(float) +
+    return (size_t)k1_stages<CC, SP>() *
+               (k1_arrays<CC, SP>() * Shape<RY>::BOXF_PAD + (NOE ? 0 : Shape<RY>::EBOXF_PAD)) * sizeof(float) +
            128;
 }
 
@@ -250,7 +250,7 @@ __device__ __forceinline__ void sp_epilogue(SolveState* st, double pq, double rz
 // and also sums r.r, r.q, q.q (and, on the general path, r.D^-1 r, D^-1 r.q, q.D^-1 q) for
 // sp_epilogue. The old r and q come from one buffer of a pair and the new ones go to the
 // other, since neighbouring blocks read the old values in their halo.
-template <bool ROBIN, bool CUBE, int RY, bool CC, bool SP>
+template <bool ROBIN, bool CUBE, int RY, bool CC, bool SP, bool NOE = false>
 __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMap& m_pold, const CUtensorMap& m_dinv,
                                         const CUtensorMap& m_beta, const CUtensorMap& m_qold, const CUtensorMap& m_e,
                                         const Grid& g, const Op& op, const Range& rg, float* __restrict__ pnew,
@@ -266,7 +266,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     constexpr int NB = CC ? 2 : 4;                           // arrays staged at every step
     constexpr int AQ = NB;                                   // array index of q_old
     constexpr int NP = SP ? (CC ? 4 : 7) : 1;                // block sums
-    constexpr int STAGEF = NA * S::BOXF_PAD + S::EBOXF_PAD;  // floats per stage
+    constexpr int STAGEF = NA * S::BOXF_PAD + (NOE ? 0 : S::EBOXF_PAD);  // floats per stage
     float* ring = reinterpret_cast<float*>(k1_smem + ((128u - (smem_u32(k1_smem) & 127u)) & 127u));
     // array a (NA = e) of ring slot `slot`
     auto box = [&](int slot, int a) -> float* { return ring + slot * STAGEF + a * S::BOXF_PAD; };
@@ -292,7 +292,8 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     const int ke = min(k0 + kz, rg.khi + 1);
     const int P0 = k0 - 1;                 // first staged node plane
     const int nplanes = ke - k0 + 2;       // planes k0-1 .. ke
-    const float bcg = sc.bcg, ap = sc.ap, cdinv = sc.cdinv, bu = sc.bu;
+    // NOE: no e box in the stages, so no deferred correction (the caller passes ap = 0)
+    const float bcg = sc.bcg, ap = NOE ? 0.f : sc.ap, cdinv = sc.cdinv, bu = sc.bu;
     // Node i sits in column i + XL of the padded layout. The box starts at the 16-byte
     // boundary bx at or below node i0-1's column, and node i0-1 is staged column sh.
     const int bx = (i0 + XL - 1) & ~3;

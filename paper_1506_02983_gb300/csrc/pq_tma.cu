@@ -47,8 +47,10 @@ k_pq32_tma(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUte
 // prefers). The host picks it from the level's uniform flag after the set-up; should a later
 // set-up clear the flag (new beta data under a recorded graph), the kernel computes nothing
 // and records status 6 so that the host records the solve again with the general path.
-template <bool CUBE, int RY>
-__global__ void __launch_bounds__(NT, RY == 1 ? 6 : 4)
+// RING: the ring form (p_old from the ring, no e): its stages hold no e box, so on cubic elements
+// five blocks of two-row tiles fit an SM by shared memory and by registers.
+template <bool CUBE, int RY, bool RING>
+__global__ void __launch_bounds__(NT, RY == 1 ? 6 : (RING && CUBE ? 5 : 4))
 k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUtensorMap m_pold,
           const __grid_constant__ CUtensorMap m_e, const Grid g, const Op op, const Range rg,
           float* __restrict__ pnew, float* __restrict__ q, float* __restrict__ e, SolveState* st, double* partials,
@@ -67,8 +69,8 @@ k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUten
         }
         return;
     }
-    k1_body<false, CUBE, RY, true, false>(m_r, m_pold, m_r, m_r, m_r, m_e, g, op, rg, pnew, q, nullptr, e, st, partials,
-                                          pidx, ch, kz, tm, sc, k1_block_of_grid(), ring.alpha, ring.R);
+    k1_body<false, CUBE, RY, true, false, RING>(m_r, m_pold, m_r, m_r, m_r, m_e, g, op, rg, pnew, q, nullptr, e, st,
+                                                partials, pidx, ch, kz, tm, sc, k1_block_of_grid(), ring.alpha, ring.R);
 }
 
 bool make_plane_map(CUtensorMap* map, const float* base, const Grid& g, int sy, int sx = SX)
@@ -85,8 +87,12 @@ cudaError_t prepare_one()
 template <bool CUBE, int RY>
 cudaError_t prepare_cc()
 {
-    return cudaFuncSetAttribute(k_pq32_cc<CUBE, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stage_smem<RY, true, false>());
+    cudaError_t e = cudaFuncSetAttribute(k_pq32_cc<CUBE, RY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)stage_smem<RY, true, false>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pq32_cc<CUBE, RY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stage_smem<RY, true, false, true>());
+    return e;
 }
 
 template <int RY>
@@ -111,11 +117,17 @@ void launch_ry(const PlaneMaps& m, int pold_is_b, const K1Config& c, const Grid&
     const Range rg = k1_range(g, op);
     const CUtensorMap& pold = pold_is_b ? m.pB[v] : m.pA[v];
     if (cc) {
-        const RingArgs ra = ring ? *ring : RingArgs{nullptr, nullptr, 0};
-        auto kern = op.cube ? k_pq32_cc<true, RY> : k_pq32_cc<false, RY>;
-        kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, true, false>(), s>>>(
-            m.r[v], ring ? m.ring[v] : pold, m.e[v], g, op, rg, pnew, q, e, st, pr.buf, pidx, ch, c.kz, tm, uniform,
-            beta32, dinv32, ra);
+        if (ring) {
+            auto kern = op.cube ? k_pq32_cc<true, RY, true> : k_pq32_cc<false, RY, true>;
+            kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, true, false, true>(), s>>>(
+                m.r[v], m.ring[v], m.e[v], g, op, rg, pnew, q, e, st, pr.buf, pidx, ch, c.kz, tm, uniform, beta32,
+                dinv32, *ring);
+        } else {
+            auto kern = op.cube ? k_pq32_cc<true, RY, false> : k_pq32_cc<false, RY, false>;
+            kern<<<k1_grid(rg, c), dim3(TBX, TBY), stage_smem<RY, true, false>(), s>>>(
+                m.r[v], pold, m.e[v], g, op, rg, pnew, q, e, st, pr.buf, pidx, ch, c.kz, tm, uniform, beta32, dinv32,
+                RingArgs{nullptr, nullptr, 0});
+        }
         return;
     }
     bool robin = false;
