@@ -296,7 +296,9 @@ ecmg_status ecmg_kernel_launches(uint64_t* out);
 /* Time one kernel of the solve alone on level `level` (-1 = finest): `reps` launches, each
  * bracketed by CUDA events on the handle's stream, after one untimed launch. which:
  * 0 K1 FP32 (search direction + operator), 1 K2 FP32 (residual update), 2 FP64 residual with
- * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true, 8 ||f_h||,
+ * FP32 output, 3 K1 FP64, 4 K2 FP64, 5 FP64 residual, 6 EXP_finite, 7 EXP_true, 8 ||f_h|| (on a
+ * MIXED level with one beta, every face Dirichlet and cubic elements also b / c for the exact
+ * residual, as the solve runs it),
  * 9 MIXED fold of the FP32 correction into the FP64 iterate (applied to U~; on a level with a
  * ring of search directions the fold of ring_slots - 2 pending directions), 10 max |U|,
  * 11 the single-pass FP32 step (handles created with ECMG_CG_SINGLE_PASS).

@@ -457,10 +457,9 @@ void record_level(Rec& R, int l)
     launch_state_init(st, rtol, o.inner_rtol, max_iters, fixed ? 1 : 0, R.s(), ring_on ? v.R : 0);
     // levels >= 2: EXP_finite writes every free node below, so only the shell that ||f_h|| reads
     dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s(), /*shell=*/l >= 2);
-    launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s());
-    // constant coefficient: b / c for the exact integer residual, kept in the FP64 r vector,
-    // which the MIXED iteration does not use
-    if (mixed) launch_scale_load(v.g, v.op, v.b, v.r, v.beta, v.uniform, st, R.s());
+    // MIXED: also b / c and its max on a constant-coefficient level, the exact residual's load
+    // and scale, kept in the FP64 r vector, which the MIXED iteration does not use
+    launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s(), mixed ? v.uniform : nullptr, mixed ? v.r : nullptr);
     if (!direct) {
         const Level& u1 = h->lv[l - 1];
         const Level& u0 = h->lv[l - 2];
@@ -994,7 +993,9 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
                 launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, s);
                 break;
             }
-            case 8: launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, s); break;
+            case 8:  // as a MIXED solve runs it: with b / c on a constant-coefficient level
+                launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, s, v.r32 ? v.uniform : nullptr, v.r32 ? v.r : nullptr);
+                break;
             case 9:
                 if (ring_on) launch_fold_ring(v.g, v.Ut, ring, v.e32, v.uniform, st, h->part, s);
                 else launch_fold32(v.g, v.Ut, v.e32, v.pA32, v.uniform, st, h->part, s);
@@ -1800,7 +1801,8 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
         return fail(ECMG_ERR_CUDA, cudaGetErrorString(f.e));
     }
     // the constant-coefficient residual (kernel 2) reads x and b / c and writes r: 20 bytes per
-    // node; ||f_h|| (8) reads b; the fold (9) updates x and e and reads p; max |x| (10) reads x;
+    // node; ||f_h|| (8) reads b (and on a MIXED one-beta cube writes b / c on the nodes off the
+    // faces); the fold (9) updates x and e and reads p; max |x| (10) reads x;
     // the single-pass step (11) moves r, q, p and e in and out (and D^-1, beta in)
     // with a ring of search directions K1 moves no correction vector (8 bytes fewer per node) and
     // the fold reads ring_slots - 2 directions instead of e and p and writes no e
@@ -1808,7 +1810,7 @@ ecmg_status ecmg_time_kernel(ecmg_handle* h, int32_t level, int32_t which, int32
     const double e1 = ring_on ? 0.0 : 8.0;
     const double bytes[12] = {(cc ? 16 + e1 : 20 + e1) * N1 + (cc ? 0.0 : 4 * E), (cc ? 12 * N : 16 * N),
                               (cc && v.op.cube ? 20 * N : 24 * N + 8 * E), 56 * N + 8 * E, 32 * N, 32 * N + 8 * E,
-                              16 * N + 8 * (N / 8 + N / 64), 17 * N, 8 * N,
+                              16 * N + 8 * (N / 8 + N / 64), 17 * N, (v.r32 && cc && v.op.cube) ? 8 * N + 8 * N1 : 8 * N,
                               ring_on ? (16.0 + 4.0 * ring_cap(v.R)) * N : 28 * N, 8 * N,
                               (cc ? 32 * N1 : 36 * N1 + 4 * E)};
     *bytes_out = bytes[which];

@@ -123,7 +123,8 @@ struct SolveState {
     int stop_after_update; // MIXED: iteration cap reached, finish after the next replacement
     int p_latest;        // which of the two search-direction buffers holds the newest p
     unsigned int arrive; // block arrival counter of the last-block reductions
-    unsigned long long bcbits;  // MIXED, constant coefficient: bits of max |b / c| (fixed-point scale)
+    unsigned long long bcbits;  // MIXED, constant coefficient: bits of max |b / c| over the free nodes
+                                // (fixed-point scale; c = -beta h / 36)
     unsigned long long xbits;   // batched MIXED: bits of max |x| for the next exact residual (0 = not taken)
     int fixed;           // 1: exactly max_iters steps, no tolerance test (the schedule of Alg. 3)
     // MIXED two-pass levels with a ring of search directions: the FP32 correction of the iterate,

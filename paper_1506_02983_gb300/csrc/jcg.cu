@@ -436,29 +436,11 @@ __global__ void __launch_bounds__(UPD_TPB) k_absmax(int64_t n, const double* __r
 // Constant coefficient (one beta, every face Dirichlet, cubic elements; the first set by the
 // set-up's device flag): A x = c 2^-s I with c = -beta h / 36 and I the exact integer sum of
 // march_fixed, so with B = b / c on the same fixed-point scale the residual is c 2^-s (B - I),
-// exact in 64-bit integers. bc = b / c once per level, and max |bc| for the scale.
-__global__ void __launch_bounds__(UPD_TPB) k_scale_load(int64_t n, const double* __restrict__ b,
-                                                       double* __restrict__ bc, const double* __restrict__ beta,
-                                                       double h, const int* uniform, SolveState* st)
+// exact in 64-bit integers. ||f_h|| (k_fh2), which reads b anyway, stores bc = b / c with this
+// reciprocal on the free nodes and takes max |bc| for the scale.
+__device__ __forceinline__ double inv_c_of(const double* __restrict__ beta, const Grid& g)
 {
-    COUNT_LAUNCH();
-    if (!*uniform) return;
-    __shared__ unsigned long long sh[UPD_TPB / 32];
-    const double inv_c = -36.0 / (beta[0] * h);
-    unsigned long long m = 0ull;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
-        const double v = b[t] * inv_c;
-        bc[t] = v;
-        m = max(m, fx::abs_bits(v));
-    }
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < UPD_TPB / 32; ++w) m = max(m, sh[w]);
-        atomicMax(&st->bcbits, m);
-    }
+    return -36.0 / (beta[g.off(0, 0, 0)] * g.h[0]);
 }
 
 // Uniform-beta dispatch of the FP64 kernels: *uniform is set per level by the set-up.
@@ -498,7 +480,7 @@ __global__ void __launch_bounds__(NT) k_pq(const Grid g, const Op op, const T* _
 }
 
 // ---- residual r = b - A x --------------------------------------------------------------------
-// bc: b / c of the constant-coefficient case (k_scale_load), or null when the level can not be
+// bc: b / c of the constant-coefficient case (from k_fh2), or null when the level can not be
 // one (a Robin face, non-cubic elements, FP64 output): then A x in FP64 or fixed point as below.
 template <typename OT, bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const double* __restrict__ beta,
@@ -588,22 +570,36 @@ __device__ __forceinline__ int outer_value(const FhBox& B, int a, int idx)
 }
 __device__ __forceinline__ int inner_count(const FhBox& B, int a) { return max(B.nhi[a] - B.nlo[a] + 1, 0); }
 
+// bc: on a MIXED level that may be a constant-coefficient one, the vector that receives b / c;
+// with the level's uniform flag set the kernel stores it on the free nodes (the only ones the
+// residual reads) and takes max |b / c| into st->bcbits (the exact residual's scale).
 template <bool ROBIN, bool CUBE>
 __global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, const FhBox B,
                                                  const double* __restrict__ beta, const double* __restrict__ x,
-                                                 const double* __restrict__ b, SolveState* st, double* partials)
+                                                 const double* __restrict__ b, SolveState* st, double* partials,
+                                                 const int* __restrict__ uniform, double* __restrict__ bc)
 {
     COUNT_LAUNCH();
     const Weights<double> wts(op);
     double ss = 0.0;
+    // max |b / c| as integer bits (the order of non-negative doubles, NaN above +inf)
+    const bool bmax = bc && *uniform;
+    const double inv_c = bmax ? inv_c_of(beta, g) : 0.0;
+    unsigned long long mb = 0ull;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int nFi = B.hi[0] - B.lo[0] + 1, nFj = B.hi[1] - B.lo[1] + 1;
     const int oi = outer_count(B, 0), oj = outer_count(B, 1), ok = outer_count(B, 2);
     const int ii = inner_count(B, 0), ij = inner_count(B, 1), ik = inner_count(B, 2);
     auto shell = [&](int i, int j, int k) {
-        const double f = fh_at<ROBIN, CUBE>(g, op, wts, beta, x, b, g.off(i, j, k), i, j, k);
+        const int64_t o = g.off(i, j, k);
+        const double f = fh_at<ROBIN, CUBE>(g, op, wts, beta, x, b, o, i, j, k);
         ss = fma(f, f, ss);
+        if (bmax) {
+            const double v = b[o] * inv_c;
+            bc[o] = v;
+            mb = max(mb, fx::abs_bits(v));
+        }
     };
     // shell 1: planes k of F outside N, every (i, j) of F
     const int64_t n1 = (int64_t)ok * nFj * nFi;
@@ -628,8 +624,27 @@ __global__ void __launch_bounds__(UPD_TPB) k_fh2(const Grid g, const Op op, cons
     const int64_t warps = nthreads / 32, wid = tid / 32;
     for (int64_t row = wid; row < nrows; row += warps) {
         const int j = B.nlo[1] + (int)(row % ij), k = B.nlo[2] + (int)(row / ij);
-        const double* brow = b + g.off(B.nlo[0], j, k);
-        for (int i = threadIdx.x & 31; i < ii; i += 32) ss = fma(brow[i], brow[i], ss);
+        const int64_t orow = g.off(B.nlo[0], j, k);
+        const double* brow = b + orow;
+        for (int i = threadIdx.x & 31; i < ii; i += 32) {
+            const double bv = brow[i];
+            ss = fma(bv, bv, ss);
+            if (bmax) {
+                const double v = bv * inv_c;
+                bc[orow + i] = v;
+                mb = max(mb, fx::abs_bits(v));
+            }
+        }
+    }
+    if (bmax) {
+        __shared__ unsigned long long shm[UPD_TPB / 32];
+        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_down_sync(0xffffffffu, mb, o));
+        if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mb;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < UPD_TPB / 32; ++w) mb = max(mb, shm[w]);
+            atomicMax(&st->bcbits, mb);  // before this block's arrival in grid_sum
+        }
     }
     double v[1] = {ss};
     if (grid_sum<1>(v, partials, &st->arrive)) {
@@ -1031,13 +1046,6 @@ bool constant_coefficient_shape(const Grid& g, const Op& op)
     for (int f = 0; f < 6; ++f) diri &= op.bc[f] == 0;
     return diri && op.cube && g.nx >= 2 && g.ny >= 2 && g.nz >= 2;
 }
-void launch_scale_load(const Grid& g, const Op& op, const double* b, double* bc, const double* beta,
-                       const int* uniform, SolveState* st, cudaStream_t s)
-{
-    if (!constant_coefficient_shape(g, op)) return;
-    k_scale_load<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, b, bc, beta + g.off(0, 0, 0), g.h[0], uniform,
-                                                            st);
-}
 void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr, ResMode mode,
                   CondHandles ch, cudaStream_t s, const double* bc)
@@ -1064,7 +1072,7 @@ void launch_apply32(const Grid& g, const Op& op, const float* beta, const float*
                                                                              nullptr);
 }
 void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
-                Partials pr, cudaStream_t s)
+                Partials pr, cudaStream_t s, const int* uniform, double* bc)
 {
     FhBox B;
     const int n[3] = {g.nx, g.ny, g.nz};
@@ -1077,7 +1085,7 @@ void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x
     }
     (has_robin(op) ? (op.cube ? k_fh2<true, true> : k_fh2<true, false>)
                    : (op.cube ? k_fh2<false, true> : k_fh2<false, false>))<<<update_blocks(g.total), UPD_TPB, 0, s>>>(
-        g, op, B, beta, x, b, st, pr.buf);
+        g, op, B, beta, x, b, st, pr.buf, uniform, uniform && constant_coefficient_shape(g, op) ? bc : nullptr);
 }
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv, SolveState* st,
                      Partials pr, CondHandles ch, cudaStream_t s)

@@ -32,8 +32,8 @@ void launch_pq64(const Grid& g, const Op& op, const double* beta, const int* uni
 void launch_res64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const double* dinv, double* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s);
-// bc: b / c from launch_scale_load (same level), or null. On a constant-coefficient level (one
-// beta, every face Dirichlet, cubic elements) the residual is then exact in 64-bit integers.
+// bc: b / c from launch_fh2 (same level), or null. On a constant-coefficient level (one beta,
+// every face Dirichlet, cubic elements) the residual is then exact in 64-bit integers.
 void launch_res32(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                   const double* b, const float* dinv, float* r, SolveState* st, Partials pr,
                   ResMode mode, CondHandles ch, cudaStream_t s, const double* bc = nullptr);
@@ -42,19 +42,19 @@ void launch_res32(const Grid& g, const Op& op, const double* beta, const int* un
 // Robin terms); skipped for a replacement (mode RES_REPLACE) of a finished level.
 void launch_absmax(const Grid& g, const double* x, const int* uniform, const SolveState* st, int mode,
                    Partials pr, cudaStream_t s, bool always = false);
-// bc = b / c (c = -beta h / 36) and max |bc| into the level state, when the level has one beta,
-// every face Dirichlet and cubic elements (a no-op otherwise).
-void launch_scale_load(const Grid& g, const Op& op, const double* b, double* bc, const double* beta,
-                       const int* uniform, SolveState* st, cudaStream_t s);
 // y = A x with the full matrix (no boundary masking), FP64 or FP32 arithmetic.
 void launch_apply64(const Grid& g, const Op& op, const double* beta, const int* uniform, const double* x,
                     double* y, Partials pr, cudaStream_t s);
 void launch_apply32(const Grid& g, const Op& op, const float* beta, const float* x, double* y,
                     cudaStream_t s);
 
-// ||f_h||^2 into the level state (x = Dirichlet extension), and the stopping threshold.
+// ||f_h||^2 into the level state (x = Dirichlet extension), and the stopping threshold. On a
+// MIXED level (uniform: the level's flag, bc: a level vector, else both null) that turns out to
+// be a constant-coefficient one (one beta, every face Dirichlet, cubic elements), also
+// bc = b / c (c = -beta h / 36) on the free nodes and max |bc| into st->bcbits: the exact
+// residual's load and scale.
 void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
-                Partials pr, cudaStream_t s);
+                Partials pr, cudaStream_t s, const int* uniform = nullptr, double* bc = nullptr);
 // r -= alpha q; z = dinv r; r.z and r.r; last block: convergence / next beta.
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv,
                      SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);

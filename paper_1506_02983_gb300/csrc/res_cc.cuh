@@ -8,7 +8,7 @@
 namespace ecmg {
 
 // Tensor maps of a level's FP64 iterate U and of b / c (the level's FP64 r vector after
-// launch_scale_load).
+// launch_fh2 on a MIXED level).
 struct ResMaps {
     CUtensorMap x, bc;
 };
@@ -22,7 +22,7 @@ int res_cc_blocks(const Grid& g);
 // elements (r on the Dirichlet nodes is not written and stays 0), exactly in fixed point and
 // rounded once to FP32; ||r||^2 and r.z reduced, the last block acts by `mode` (RES_INIT,
 // RES_REPLACE or RES_REPORT). Needs the level's max |x| in pr.fs (launch_absmax, same
-// stream) and max |b / c| in st->bcbits (launch_scale_load). If the level's uniform flag is
+// stream) and max |b / c| in st->bcbits (launch_fh2). If the level's uniform flag is
 // clear when the kernel runs, it records status 6 and finishes the level without computing.
 void launch_res32_cc(const ResMaps& m, const Grid& g, const int* uniform, const double* beta, const float* dinv32,
                      float* r, SolveState* st, Partials pr, ResMode mode, CondHandles ch, cudaStream_t s);
