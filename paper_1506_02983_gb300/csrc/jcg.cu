@@ -984,8 +984,8 @@ inline int stencil_kz(const Grid& g)
     int gz = (want_blocks + gx * gy - 1) / (gx * gy);
     int kz = (g.nz + 1 + gz - 1) / gz;
     // small levels (the direct solves, the first MIXED levels) are FP64-pipe and latency bound:
-    // spread them over more SMs with short columns
-    if (kz < 2) kz = 2;
+    // spread them over more SMs with short columns, down to one plane per block
+    if (kz < 1) kz = 1;
     if (kz > KZ_TARGET) kz = KZ_TARGET;
     return kz;
 }
