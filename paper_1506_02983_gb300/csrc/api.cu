@@ -260,7 +260,7 @@ uint64_t level_bytes(const Grid& g, bool mixed, bool single_pass, int ring_slots
     const uint64_t n = (uint64_t)g.total;
     uint64_t b = n * 8ull * 14ull;  // U W Ut b beta dinv f gD gR r pA pB q (+1 spare alignment)
     if (mixed) b += n * 4ull * (single_pass ? 9ull : 7ull);
-    if (ring_slots) b += (n * 4ull + 8ull) * (uint64_t)ring_slots;
+    if (ring_slots) b += ((uint64_t)ring_stride((int64_t)n) * 4ull + 8ull) * (uint64_t)ring_slots;
     return b;
 }
 
@@ -1335,7 +1335,7 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
                 }
                 if (const int R = ring_slots_level(h->prob, h->opt, v.g, l)) {
                     v.R = R;
-                    v.ring = dalloc<float>(h, n * R);
+                    v.ring = dalloc<float>(h, ring_stride(n) * R);
                     v.ring_alpha = dalloc<double>(h, R);
                     if (!make_ring_maps(&v.maps, v.ring, R, v.g)) throw CudaFail{cudaErrorNotSupported};
                 }

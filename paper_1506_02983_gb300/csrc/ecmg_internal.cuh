@@ -141,6 +141,11 @@ struct SolveState {
 // correction vector (the next step must not overwrite a pending direction).
 __host__ __device__ inline int ring_cap(int pring) { return pring - 2; }
 
+// Elements from one slot of a ring of search directions to the next: the level's stored length
+// rounded up to 64 (256 bytes), so that every slot, like a vector of its own, starts on a DRAM
+// burst boundary (at 32-byte alignment the fold's reads of 62 slots fetched 13 % more than they used).
+__host__ __device__ inline int64_t ring_stride(int64_t total) { return (total + 63) / 64 * 64; }
+
 // The ring of search directions of a two-pass MIXED level: R FP32 level vectors back to back,
 // the step alpha of the direction in each slot, and R. With a ring, K1 reads p_old from slot
 // st->pj, writes p to the next slot and records its alpha there, and moves no correction

@@ -695,12 +695,12 @@ __device__ __forceinline__ void ring_pending(const SolveState* st, const double*
 }
 
 // acc, then acc = fmaf(alpha_u, p_u, acc) over the pending directions u = 0 .. pend-1 at float4
-// index t of level vectors of length n: the fused multiply-adds the correction vector performs,
-// in its order. Four directions' loads are issued before their sums.
-__device__ __forceinline__ float4 ring_chain(float4 acc, const float* __restrict__ ring, int64_t n, const int* sslot,
-                                             const float* sa, int pend, int64_t t)
+// index t of the ring's slots (stride elements apart): the fused multiply-adds the correction
+// vector performs, in its order. Four directions' loads are issued before their sums.
+__device__ __forceinline__ float4 ring_chain(float4 acc, const float* __restrict__ ring, int64_t stride,
+                                             const int* sslot, const float* sa, int pend, int64_t t)
 {
-    auto dir = [&](int u) { return __ldcs(reinterpret_cast<const float4*>(ring + (int64_t)sslot[u] * n) + t); };
+    auto dir = [&](int u) { return __ldcs(reinterpret_cast<const float4*>(ring + (int64_t)sslot[u] * stride) + t); };
     auto step = [&](float a, const float4 pv) {
         acc.x = fmaf(a, pv.x, acc.x);
         acc.y = fmaf(a, pv.y, acc.y);
@@ -765,7 +765,8 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
         const bool es = st->espill != 0;
         float4* e4 = reinterpret_cast<float4*>(e);
         for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n / 4; t += stride)
-            e4[t] = ring_chain(es ? e4[t] : make_float4(0.f, 0.f, 0.f, 0.f), ring.base, n, sslot, sa, pend, t);
+            e4[t] = ring_chain(es ? e4[t] : make_float4(0.f, 0.f, 0.f, 0.f), ring.base, ring_stride(n), sslot, sa,
+                               pend, t);
     }
     if (cc) {
         // one diagonal: r.z = D^-1 r.r, formed from ||r||^2 after the reduction
@@ -933,7 +934,7 @@ __global__ void __launch_bounds__(UPD_TPB) k_fold_ring(int64_t n, double* __rest
             acc = e4[t];
             e4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        acc = ring_chain(acc, ring, n, sslot, sa, pend, t);
+        acc = ring_chain(acc, ring, ring_stride(n), sslot, sa, pend, t);
         double2 xa = x2[2 * t], xb = x2[2 * t + 1];
         xa.x += widen(acc.x);
         xa.y += widen(acc.y);

@@ -23,7 +23,7 @@ __device__ __forceinline__ float* ring_scalars(K1Scalars& sc, float* pnew, const
     if (!ring.base) return pnew;
     sc.pw = st->pj;
     sc.ap = 0.f;
-    return ring.base + (int64_t)((sc.pw + 1) % ring.R) * g.total;
+    return ring.base + (int64_t)((sc.pw + 1) % ring.R) * ring_stride(g.total);
 }
 
 // General path: beta and D^-1 streamed with r and p_old.

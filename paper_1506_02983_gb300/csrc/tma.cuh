@@ -69,7 +69,7 @@ struct Grid;
 // False if the driver entry point is unavailable or the encoding is rejected.
 bool encode_level_map(CUtensorMap* map, bool fp64, const void* base, const Grid& g, int sx, int sy);
 // The same for a ring of nvec FP32 level vectors stored back to back (vector w at base + w
-// total): a 4D map whose fourth coordinate picks the vector.
+// ring_stride(total)): a 4D map whose fourth coordinate picks the vector.
 bool encode_ring_map(CUtensorMap* map, const float* base, const Grid& g, int nvec, int sx, int sy);
 
 }  // namespace ecmg

@@ -50,7 +50,8 @@ bool encode_ring_map(CUtensorMap* map, const float* base, const Grid& g, int nve
     if (!enc) return false;
     const cuuint64_t es = 4;
     const cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 3), (cuuint64_t)(g.nz + 3), (cuuint64_t)nvec};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.plane * es, (cuuint64_t)g.total * es};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.plane * es,
+                                   (cuuint64_t)ring_stride(g.total) * es};
     const cuuint32_t box[4] = {(cuuint32_t)sx, (cuuint32_t)sy, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, estr,

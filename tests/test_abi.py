@@ -255,11 +255,14 @@ def test_workspace_of_the_step_forms_without_gpu(libpath):
     assert single - auto == sum(8 * total(l) for l in range(2, 7) if l not in small)
     extra = single - two - sum(8 * total(l) for l in range(2, 7))
     assert extra > 0 and extra % (5 * 8) == 0  # 5 more doubles per block of the largest grid
-    # the ring of search directions: 4 bytes per stored node and 8 bytes of alpha per slot on
-    # every two-pass level >= 2, nothing on single-pass levels
+    # the ring of search directions: 4 bytes per stored node (slots 256-byte aligned) and 8 bytes
+    # of alpha per slot on every two-pass level >= 2, nothing on single-pass levels
+    def slot(l):
+        return 4 * ((total(l) + 63) // 64 * 64) + 8
+
     for slots in (4, 34, 64):
-        assert ws(ecmg.ECMG_CG_TWO_PASS, slots) - two == sum((4 * total(l) + 8) * slots for l in range(2, 7))
-        assert ws(ecmg.ECMG_CG_AUTO, slots) - auto == sum((4 * total(l) + 8) * slots for l in (5, 6))
+        assert ws(ecmg.ECMG_CG_TWO_PASS, slots) - two == sum(slot(l) * slots for l in range(2, 7))
+        assert ws(ecmg.ECMG_CG_AUTO, slots) - auto == sum(slot(l) * slots for l in (5, 6))
         assert ws(ecmg.ECMG_CG_SINGLE_PASS, slots) == single
     o = ecmg.default_options()
     assert o.ring_slots == ecmg.ECMG_RING_AUTO
