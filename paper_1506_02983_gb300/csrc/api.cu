@@ -273,6 +273,9 @@ int partials_per_block(const ecmg_options& o)
 
 // Whether MIXED level l (>= 2) runs the single-pass step: always, never, or (AUTO) on levels
 // of fewer than ECMG_AUTO_SINGLE_PASS_NODES nodes.
+// FP32 steps per replacement check in the loop body of a level with a ring of search directions.
+constexpr int RING_STEPS = 4;
+
 bool single_pass_level(const ecmg_options& o, const Grid& g, int l)
 {
     if (o.precision != ECMG_MIXED || l < 2) return false;
@@ -532,7 +535,20 @@ void record_level(Rec& R, int l)
             else launch_fold32(v.g, v.U, v.e32, pbuf[o], v.uniform, st, h->part, R.s());
             res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[o]);
         };
-        if (R.graph) {
+        if (R.graph && ring_on) {
+            // with the ring every step reads and writes the same buffers, so one replacement
+            // check serves RING_STEPS steps: a step after the one that asks for a replacement
+            // finds need_update set and returns at once (K1 and K2 both)
+            const cudaGraphConditionalHandle loop = R.new_handle();
+            res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s(), rbuf[0]);
+            R.open(loop, cudaGraphCondTypeWhile);
+            const cudaGraphConditionalHandle upd = R.new_handle();  // on the loop body
+            for (int k = 0; k < RING_STEPS; ++k) step(CondHandles{loop, upd, 1}, 0);
+            R.open(upd, cudaGraphCondTypeIf);
+            replace(0);
+            R.close();
+            R.close();
+        } else if (R.graph) {
             const cudaGraphConditionalHandle loop = R.new_handle();
             res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s(), rbuf[0]);
             R.open(loop, cudaGraphCondTypeWhile);

@@ -746,6 +746,9 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
         }
         return;
     }
+    // a step behind one that asked for a replacement (levels with a ring, whose loop body checks
+    // once per several steps): nothing to do, and the conditions stay as that step set them
+    if (MIXED && ring.base && st->need_update) return;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::n;
     const T a = (T)st->alpha;

@@ -59,7 +59,9 @@ k_pq32_cc(const __grid_constant__ CUtensorMap m_r, const __grid_constant__ CUten
 {
     COUNT_LAUNCH();
     const int uni = *uniform;
-    K1Scalars sc{st->done, (float)st->beta, (float)st->alpha_prev, dinv32[g.off(1, 1, 1)], beta32[g.off(0, 0, 0)]};
+    // ring form: a step behind one that asked for a replacement does nothing until it has run
+    K1Scalars sc{RING ? (st->done | st->need_update) : st->done, (float)st->beta, (float)st->alpha_prev,
+                 dinv32[g.off(1, 1, 1)], beta32[g.off(0, 0, 0)]};
     pnew = ring_scalars(sc, pnew, st, g, ring);
     if (!uni) {
         if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0 && !sc.done) {
