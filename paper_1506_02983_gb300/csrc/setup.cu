@@ -71,11 +71,41 @@ __global__ void k_inject(Grid gc, const double* __restrict__ vf, Grid gf, double
     vc[gc.off(i, j, k)] = vf[gf.off(2 * i, 2 * j, 2 * k)];
 }
 
-__global__ void k_restrict(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
+// P^T b with the weights (1/2, 1, 1/2) of the trilinear prolongation per axis, summed axis by
+// axis: per fine plane a block stages the 65 x 17 fine values under its 32 x 8 coarse nodes,
+// sums them along x and then y in shared memory, and forms each coarse value from the sums of
+// three consecutive fine planes. 14.5 FP64 operations per coarse node instead of the 27 of the
+// full weighted sum (restrict_at); the same weights, summed in another order.
+constexpr int RKZ = 8;  // coarse planes per block
+__global__ void __launch_bounds__(TX * TY) k_restrict(Grid gc, const double* __restrict__ bf, Grid gf,
+                                                      double* __restrict__ bc)
 {
     COUNT_LAUNCH();
-    POINT_IJK(gc.nx, gc.ny);
-    bc[gc.off(i, j, k)] = restrict_at(bf, gf, i, j, k);
+    constexpr int SR = 2 * TY + 1, SCOL = 2 * TX + 1;  // staged fine rows and columns
+    __shared__ double S[SR][SCOL];
+    __shared__ double T[SR][TX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int I0 = blockIdx.x * TX, J0 = blockIdx.y * TY, K0 = blockIdx.z * RKZ;
+    const int K1 = min(K0 + RKZ, gc.nz + 1);  // coarse planes [K0, K1)
+    const int I = I0 + tx, J = J0 + ty;
+    const bool own = I <= gc.nx && J <= gc.ny;
+    double t2m = 0.0, t2c = 0.0;  // the y, x sums of fine planes kf - 2 and kf - 1
+    for (int kf = 2 * K0 - 1; kf <= 2 * K1 - 1; ++kf) {
+        const int64_t pb = gf.plane_base(kf);
+        for (int c = tid; c < SR * SCOL; c += TX * TY) {
+            const int r = c / SCOL, col = c % SCOL;
+            const int jf = 2 * J0 - 1 + r, ifn = 2 * I0 - 1 + col;
+            S[r][col] = (jf <= gf.ny + 1 && ifn <= gf.nx + 1) ? bf[pb + gf.in_plane(ifn, jf)] : 0.0;
+        }
+        __syncthreads();
+        for (int r = ty; r < SR; r += TY) T[r][tx] = S[r][2 * tx + 1] + 0.5 * (S[r][2 * tx] + S[r][2 * tx + 2]);
+        __syncthreads();
+        const double t2 = T[2 * ty + 1][tx] + 0.5 * (T[2 * ty][tx] + T[2 * ty + 2][tx]);
+        // fine plane 2K + 1 closes coarse plane K
+        if (kf > 2 * K0 && (kf & 1) && own) bc[gc.off(I, J, (kf - 1) / 2)] = t2c + 0.5 * (t2m + t2);
+        t2m = t2c;
+        t2c = t2;
+    }
 }
 
 __global__ void k_nodal_load(Grid g, Op op, const double* __restrict__ f,
@@ -254,7 +284,8 @@ void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, 
 }
 void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s)
 {
-    k_restrict<<<grid3(gc.nx, gc.ny, gc.nz), dim3(TX, TY), 0, s>>>(gc, bf, gf, bc);
+    const dim3 grid((gc.nx + TX) / TX, (gc.ny + TY) / TY, (gc.nz + RKZ) / RKZ);
+    k_restrict<<<grid, dim3(TX, TY), 0, s>>>(gc, bf, gf, bc);
 }
 void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,
                 cudaStream_t s)
