@@ -300,15 +300,48 @@ __global__ void __launch_bounds__(256) bk_fh2(const BItem* __restrict__ items, c
     const Weights<double> wts(it.op);
     const int nrows = (g.ny + 1) * (g.nz + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Op& op = it.op;
+    // nodes i that need the FP64 stencil of the Dirichlet lift in a row away from the y and z
+    // faces: the free nodes within one step of a Dirichlet x face (fh_at is b elsewhere)
+    const int xlo = op.bc[0] == 0 ? 2 : 0, xhi = op.bc[1] == 0 ? g.nx - 2 : g.nx;
+    constexpr int R = ROWS_PER_BLOCK / 8;  // rows of a warp
     double ss = 0.0;
-    for (int r = 0; r < ROWS_PER_BLOCK / 8; ++r) {
-        const int row = sl.lb * ROWS_PER_BLOCK + warp * (ROWS_PER_BLOCK / 8) + r;
+    for (int r = 0; r < R; ++r) {
+        const int row = sl.lb * ROWS_PER_BLOCK + warp * R + r;
         if (row >= nrows) break;
         const int j = row % (g.ny + 1), k = row / (g.ny + 1);
         const int64_t orow = g.plane_base(k) + g.in_plane(0, j);
-        for (int i = lane; i <= g.nx; i += 32) {
-            if (on_dirichlet(g, it.op, i, j, k)) continue;
-            const double f = fh_at<ROBIN, CUBE>(g, it.op, wts, it.beta, it.U, it.b, orow + i, i, j, k);
+        const bool near_yz = (op.bc[2] == 0 && j <= 1) || (op.bc[3] == 0 && j >= g.ny - 1) ||
+                             (op.bc[4] == 0 && k <= 1) || (op.bc[5] == 0 && k >= g.nz - 1);
+        if (near_yz) {  // every free node of the row needs the stencil: no lane idles
+            for (int i = lane; i <= g.nx; i += 32) {
+                if (on_dirichlet(g, op, i, j, k)) continue;
+                const double f = fh_at<ROBIN, CUBE>(g, op, wts, it.beta, it.U, it.b, orow + i, i, j, k);
+                ss = fma(f, f, ss);
+            }
+        } else {  // the inner run streams b; its x ends follow below, all rows of the warp at once
+            for (int i = xlo + lane; i <= xhi; i += 32) {
+                const double f = it.b[orow + i];
+                ss = fma(f, f, ss);
+            }
+        }
+    }
+    // the free nodes next to a Dirichlet x face in the warp's rows away from the y and z faces:
+    // up to two per face and row, one lane each (a single pass of the FP64 stencil per warp)
+    if (xlo > 0 || xhi < g.nx) {
+        const int per = (xlo > 0 ? 1 : 0) + (xhi < g.nx ? 1 : 0);  // x-shell nodes per row
+        for (int u = lane; u < R * per; u += 32) {
+            const int row = sl.lb * ROWS_PER_BLOCK + warp * R + u / per;
+            if (row >= nrows) continue;
+            const int j = row % (g.ny + 1), k = row / (g.ny + 1);
+            const bool near_yz = (op.bc[2] == 0 && j <= 1) || (op.bc[3] == 0 && j >= g.ny - 1) ||
+                                 (op.bc[4] == 0 && k <= 1) || (op.bc[5] == 0 && k >= g.nz - 1);
+            if (near_yz) continue;
+            if (per == 2 && u % per == 1 && g.nx - 1 <= 1) continue;  // the node i = 1 counted once
+            const int i = (xlo > 0 && u % per == 0) ? 1 : g.nx - 1;
+            if (i < 0 || i > g.nx || on_dirichlet(g, op, i, j, k)) continue;
+            const double f = fh_at<ROBIN, CUBE>(g, op, wts, it.beta, it.U, it.b,
+                                                g.plane_base(k) + g.in_plane(i, j), i, j, k);
             ss = fma(f, f, ss);
         }
     }
