@@ -666,7 +666,8 @@ def main():
         e2e_compact()
     ms_e2e = timed(e2e_compact, args.e2e_steps)
     h2d = sum(v.numel() * 8 for v in hostc.values())
-    st_c, _ = compact.solve(u_out)
+    st_c, status = compact.solve(u_out)
+    assert status == 0, st_c
     err_compact = compact.norms(u_out, u_exact)[0]
     compact.close()
 
@@ -682,7 +683,8 @@ def main():
         alt.stencil_timer(-1, reset=True)
         ms_alt = timed(lambda: alt.solve(u_out), args.steps)
         alt_total, alt_n = alt.stencil_timer(-1, reset=True)
-        st_alt, _ = alt.solve(u_out)
+        st_alt, status = alt.solve(u_out)
+        assert status == 0, st_alt
         other = {"mixed_step": {"two": "two-pass", "auto": "auto"}[other_form], "ms_per_step": ms_alt,
                  "value": free_dofs(nf) * world / (ms_alt * 1e-3) / 1e9, "unit": "Gdof/s",
                  "iters": st_alt["iters"], "updates": st_alt["updates"], "rel_res": st_alt["rel_res"],
