@@ -31,12 +31,10 @@ inline dim3 grid3(int mx, int my, int mz) { return dim3((mx + TX) / TX, (my + TY
     const int k = blockIdx.z;                                                       \
     if (i > (MX) || j > (MY)) return
 
-__global__ void k_pack_nodal(Grid g, Op op, const double* __restrict__ dense, double* __restrict__ dst,
-                             int dirichlet_only)
+__global__ void k_pack_nodal(Grid g, const double* __restrict__ dense, double* __restrict__ dst)
 {
     COUNT_LAUNCH();
     POINT_IJK(g.nx, g.ny);
-    if (dirichlet_only && !on_dirichlet(g, op, i, j, k)) return;
     const int64_t t = i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);  // dense index
     dst[g.off(i, j, k)] = dense[t];
 }
@@ -157,30 +155,60 @@ __global__ void k_jacobi64(Grid g, Op op, const double* __restrict__ beta, doubl
 // uniform: the level's flag, already set by the set-up. On a level with one beta, every face
 // Dirichlet and cubic elements the FP32 iteration reads D^-1 at node (1, 1, 1) only (it is the
 // same on every free node), so the other nodes are skipped.
+// Kernels that may find nothing to do on most nodes (a one-beta cube keeps a single FP32 D^-1;
+// the Dirichlet shell is a thin layer) walk ZT planes per block, so that a grid of empty blocks
+// does not cost a block launch per node row and plane.
+constexpr int ZT = 16;
+inline dim3 grid3z(int mx, int my, int mz) { return dim3((mx + TX) / TX, (my + TY) / TY, (mz + ZT) / ZT); }
+
+// g_D on the Dirichlet nodes only: a block walks ZT planes of its node columns; a column off
+// the Dirichlet x and y faces holds Dirichlet nodes only on the z faces.
+__global__ void k_pack_dirichlet(Grid g, Op op, const double* __restrict__ dense, double* __restrict__ dst)
+{
+    COUNT_LAUNCH();
+    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const bool column = (i == 0 && op.bc[0] == 0) || (i == g.nx && op.bc[1] == 0) || (j == 0 && op.bc[2] == 0) ||
+                        (j == g.ny && op.bc[3] == 0);
+    const int k1 = min((int)(blockIdx.z + 1) * ZT, g.nz + 1);
+    for (int k = blockIdx.z * ZT; k < k1; ++k) {
+        if (!column && !((k == 0 && op.bc[4] == 0) || (k == g.nz && op.bc[5] == 0))) continue;
+        const int64_t t = i + (int64_t)(g.nx + 1) * (j + (int64_t)(g.ny + 1) * k);  // dense index
+        dst[g.off(i, j, k)] = dense[t];
+    }
+}
+
 __global__ void k_jacobi32(Grid g, Op op, const float* __restrict__ beta32, float* __restrict__ dinv32, int precond,
                            const int* __restrict__ uniform)
 {
     COUNT_LAUNCH();
-    POINT_IJK(g.nx, g.ny);
+    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
     const bool diri = (op.bc[0] | op.bc[1] | op.bc[2] | op.bc[3] | op.bc[4] | op.bc[5]) == 0;
-    if (uniform && diri && op.cube && *uniform && !(i == 1 && j == 1 && k == 1)) return;
-    dinv32[g.off(i, j, k)] = jacobi32_at(g, op, beta32, i, j, k, precond);
+    const bool one = uniform && diri && op.cube && *uniform;  // only node (1, 1, 1) is read
+    if (one && !(i == 1 && j == 1)) return;
+    const int k1 = min((int)(blockIdx.z + 1) * ZT, g.nz + 1);
+    for (int k = blockIdx.z * ZT; k < k1; ++k) {
+        if (one && k != 1) continue;
+        dinv32[g.off(i, j, k)] = jacobi32_at(g, op, beta32, i, j, k, precond);
+    }
 }
 
 // x = g_D on Dirichlet nodes, 0 on free nodes (gD == nullptr: zero everywhere).
 __global__ void k_dirichlet_ext(Grid g, Op op, const double* __restrict__ gD, double* __restrict__ x, int shell)
 {
     COUNT_LAUNCH();
-    POINT_IJK(g.nx, g.ny);
-    if (shell) {
-        // only nodes within two steps of a Dirichlet face
-        auto near = [](int a, int n, int lo, int hi) { return (lo == 0 && a <= 2) || (hi == 0 && a >= n - 2); };
-        if (!near(i, g.nx, op.bc[0], op.bc[1]) && !near(j, g.ny, op.bc[2], op.bc[3]) &&
-            !near(k, g.nz, op.bc[4], op.bc[5]))
-            return;
+    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    // shell: only nodes within two steps of a Dirichlet face
+    auto near = [](int a, int n, int lo, int hi) { return (lo == 0 && a <= 2) || (hi == 0 && a >= n - 2); };
+    const bool column = !shell || near(i, g.nx, op.bc[0], op.bc[1]) || near(j, g.ny, op.bc[2], op.bc[3]);
+    const int k1 = min((int)(blockIdx.z + 1) * ZT, g.nz + 1);
+    for (int k = blockIdx.z * ZT; k < k1; ++k) {
+        if (!column && !near(k, g.nz, op.bc[4], op.bc[5])) continue;
+        const int64_t o = g.off(i, j, k);
+        x[o] = (gD && on_dirichlet(g, op, i, j, k)) ? gD[o] : 0.0;
     }
-    const int64_t o = g.off(i, j, k);
-    x[o] = (gD && on_dirichlet(g, op, i, j, k)) ? gD[o] : 0.0;
 }
 
 __global__ void k_uniform(Grid g, const double* __restrict__ beta, int* flag)
@@ -259,12 +287,11 @@ void convert_f64(const float* src, double* dst, int64_t n, cudaStream_t s)
 
 void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s)
 {
-    Op none{};
-    k_pack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, none, dense, dst, 0);
+    k_pack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, dense, dst);
 }
 void pack_dirichlet(const Grid& g, const Op& op, const double* dense, double* dst, cudaStream_t s)
 {
-    k_pack_nodal<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, dense, dst, 1);
+    k_pack_dirichlet<<<grid3z(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, dense, dst);
 }
 void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s)
 {
@@ -303,12 +330,12 @@ void jacobi_diag(const Grid& g, const Op& op, const double* beta, double* dinv64
     if (beta32) {
         if (!uniform) convert_f32(beta, beta32, g.total, s);  // else beta32_uniform has run
         if (dinv32)
-            k_jacobi32<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32, precond, uniform);
+            k_jacobi32<<<grid3z(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, beta32, dinv32, precond, uniform);
     }
 }
 void dirichlet_extension(const Grid& g, const Op& op, const double* gD, double* x, cudaStream_t s, bool shell)
 {
-    k_dirichlet_ext<<<grid3(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, gD, x, shell ? 1 : 0);
+    k_dirichlet_ext<<<grid3z(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, gD, x, shell ? 1 : 0);
 }
 
 void launch_stamp(unsigned long long* t, cudaStream_t s) { k_stamp<<<1, 1, 0, s>>>(t); }
