@@ -396,10 +396,14 @@ void record_setup(Rec& R)
     cudaStream_t s = R.s();
     const bool mixed = h->opt.precision == ECMG_MIXED;
     const int L = h->L;
+    // MIXED with a dense beta: the finest beta, its FP32 copy, the uniform flag and the beta of the
+    // level below in one pass over the caller's array (16-byte pairs: the array must be aligned)
+    const bool fused_beta = mixed && p.beta && L >= 3 && reinterpret_cast<uintptr_t>(p.beta) % 16 == 0;
     for (int l = L - 1; l >= 0; --l) {
         Level& v = h->lv[l];
         if (l == L - 1) {
-            if (p.beta) pack_elements(v.g, p.beta, v.beta, s);
+            if (fused_beta) beta_finest(v.g, h->lv[L - 2].g, p.beta, v.beta, v.beta32, v.uniform, h->lv[L - 2].beta, s);
+            else if (p.beta) pack_elements(v.g, p.beta, v.beta, s);
             else fill_beta(v.g, p.beta_const, v.beta, s);
             if (p.g_R) pack_nodal(v.g, p.g_R, v.gR, s);
             if (p.f_mode == ECMG_F_SEPARABLE) sep_load_finest(v.g, p.f_terms, p.f, v.Hf, v.b, s);
@@ -409,7 +413,7 @@ void record_setup(Rec& R)
             else if (p.g_D) pack_dirichlet(v.g, v.op, p.g_D, v.gD, s);
         } else {
             Level& u = h->lv[l + 1];
-            coarsen_beta(v.g, u.beta, u.g, v.beta, s);
+            if (!(fused_beta && l == L - 2)) coarsen_beta(v.g, u.beta, u.g, v.beta, s);
             if (p.f_mode == ECMG_F_LOAD || p.f_mode == ECMG_F_GAUSS) restrict_load(v.g, u.b, u.g, v.b, s);
             else if (p.f_mode == ECMG_F_SEPARABLE) sep_coarsen(v.g, u.g, p.f_terms, u.Hf, v.Hf, true, v.b, s);
             else inject_nodal(v.g, u.f, u.g, v.f, s);
@@ -421,8 +425,11 @@ void record_setup(Rec& R)
         if (p.f_mode == ECMG_F_NODAL) {
             nodal_load(v.g, v.op, v.f, p.g_R ? v.gR : nullptr, v.b, s);
         }
-        if (mixed && l >= 2) beta32_uniform(v.g, v.beta, v.beta32, v.uniform, s);
-        else uniform_check(v.g, v.beta, v.uniform, s);
+        if (mixed && l >= 2) {
+            if (!(fused_beta && l == L - 1)) beta32_uniform(v.g, v.beta, v.beta32, v.uniform, s);
+        } else {
+            uniform_check(v.g, v.beta, v.uniform, s);
+        }
         // FP64 diagonal for FP64 JCG and the direct levels, FP32 for the FP32 iteration of MIXED
         jacobi_diag(v.g, v.op, v.beta, (!mixed || l < 2) ? v.dinv : nullptr, mixed ? v.dinv32 : nullptr,
                     mixed ? v.beta32 : nullptr, h->opt.preconditioner == ECMG_PREC_JACOBI, s,

@@ -193,6 +193,11 @@ void pack_dirichlet(const Grid& g, const Op& op, const double* dense, double* ds
 void pack_elements(const Grid& g, const double* dense, double* dst, cudaStream_t s);
 void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s);
 void coarsen_beta(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
+// The finest beta from the caller's dense array in one pass: packed (beta), in FP32 (beta32, the
+// elements only), the uniform flag (as beta32_uniform) and the beta of the level below (bc, as
+// coarsen_beta).
+void beta_finest(const Grid& g, const Grid& gc, const double* dense, double* beta, float* beta32, int* flag,
+                 double* bc, cudaStream_t s);
 void inject_nodal(const Grid& gc, const double* vf, const Grid& gf, double* vc, cudaStream_t s);
 void restrict_load(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
 void nodal_load(const Grid& g, const Op& op, const double* f, const double* gR, double* b,

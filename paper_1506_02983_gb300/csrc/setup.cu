@@ -55,6 +55,39 @@ __global__ void k_pack_elements(Grid g, const double* __restrict__ dense, double
     dst[g.off(i, j, k)] = dense[t];
 }
 
+// The finest level's beta in one pass over the caller's dense array, one thread per element of
+// the level below: its eight fine elements are packed into the padded FP64 layout and into FP32,
+// compared with element (0, 0, 0) for the uniform flag (bit patterns), and averaged for the
+// coarse beta in the order of coarse_beta_at. Fine rows are even in length, so every access is
+// an aligned pair.
+__global__ void k_beta_finest(Grid g, Grid gc, const double* __restrict__ dense, double* __restrict__ beta,
+                              float* __restrict__ beta32, int* flag, double* __restrict__ bc)
+{
+    COUNT_LAUNCH();
+    POINT_IJK(gc.nx - 1, gc.ny - 1);
+    const long long ref = __double_as_longlong(dense[0]);
+    double2 v[4];  // rows (b, c) = (0, 0), (1, 0), (0, 1), (1, 1): elements 2i and 2i + 1
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int fj = 2 * j + (r & 1), fk = 2 * k + (r >> 1);
+        const int64_t t = 2 * i + (int64_t)g.nx * (fj + (int64_t)g.ny * fk);  // dense index, even
+        v[r] = *reinterpret_cast<const double2*>(dense + t);
+    }
+    bool same = true;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t o = g.off(2 * i, 2 * j + (r & 1), 2 * k + (r >> 1));  // even: a 16-byte pair
+        *reinterpret_cast<double2*>(beta + o) = v[r];
+        *reinterpret_cast<float2*>(beta32 + o) = make_float2((float)v[r].x, (float)v[r].y);
+        same = same && __double_as_longlong(v[r].x) == ref && __double_as_longlong(v[r].y) == ref;
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sum += (c & 1) ? v[c >> 1].y : v[c >> 1].x;
+    bc[gc.off(i, j, k)] = sum / 8.0;
+    if (!same) *flag = 0;
+}
+
 __global__ void k_coarsen_beta(Grid gc, const double* __restrict__ bf, Grid gf, double* __restrict__ bc)
 {
     COUNT_LAUNCH();
@@ -300,6 +333,12 @@ void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t 
 void pack_elements(const Grid& g, const double* dense, double* dst, cudaStream_t s)
 {
     k_pack_elements<<<grid3(g.nx - 1, g.ny - 1, g.nz - 1), dim3(TX, TY), 0, s>>>(g, dense, dst);
+}
+void beta_finest(const Grid& g, const Grid& gc, const double* dense, double* beta, float* beta32, int* flag,
+                 double* bc, cudaStream_t s)
+{
+    k_set_flag<<<1, 1, 0, s>>>(flag);
+    k_beta_finest<<<grid3(gc.nx - 1, gc.ny - 1, gc.nz - 1), dim3(TX, TY), 0, s>>>(g, gc, dense, beta, beta32, flag, bc);
 }
 void coarsen_beta(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s)
 {

@@ -577,3 +577,30 @@ def test_random_problems_match_oracle(E, oracle_mod, seed, precision):
         if precision == 0:
             assert abs(st["iters"][l] - ost["iters"][l]) <= 1, (l, st["iters"], ost["iters"])
     s.close()
+
+
+@pytest.mark.parametrize("name", ["random_cube_dirichlet", "random_mixed_bc_0"])
+def test_dense_beta_read_in_one_pass_or_unaligned_gives_the_same_solve(E, name):
+    """A MIXED solve reads a 16-byte aligned dense beta in one pass (packing, FP32 copy, uniform
+    test and the coarsening of the level below); a beta array that starts 8 bytes into its
+    allocation takes the separate passes. Both give the same beta on every level and the same
+    solve, bit for bit."""
+    import torch
+    p = PROBLEMS[name]()
+    t = lambda a: None if a is None else torch.as_tensor(np.asarray(a), dtype=torch.float64).contiguous().cuda()
+    beta = t(p["beta"])
+    buf = torch.empty(beta.numel() + 1, dtype=torch.float64, device="cuda")
+    shifted = buf[1:]
+    shifted.copy_(beta.ravel())
+    assert beta.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    out = []
+    for b in (beta, shifted):
+        s = E.Solver(p["n0"], p["levels"], p["lo"], p["hi"], p["face_bc"], p["alpha"], b, t(p["f"]), t(p.get("gD")),
+                     t(p.get("gR")), f_mode=p.get("f_mode", 0), rtol=p["rtol"], precision=1)
+        st, status = s.solve()
+        assert status == 0, st
+        out.append(([_np(s.get(E.ECMG_VEC_BETA, l)) for l in range(p["levels"])], _np(s.get(E.ECMG_VEC_U)), st["iters"]))
+        s.close()
+    for l in range(p["levels"]):
+        assert np.array_equal(out[0][0][l], out[1][0][l]), l
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
