@@ -338,7 +338,7 @@ ecmg_status ecmg_set_tiles(ecmg_handle* h, int32_t level, int32_t ry, int32_t kz
 /* Read the shape of one level into *ry, *kz (host). */
 ecmg_status ecmg_get_tiles(ecmg_handle* h, int32_t level, int32_t* ry, int32_t* kz);
 /* Autotuner: on every MIXED level of at least 2^18 nodes, time each candidate shape (ry in
- * {1, 2} x kz in {8, 12, 16, 24, 32, 48, 64, 128}) and the current one with `reps` launches each (CUDA
+ * {1, 2} x kz in {8, 10, 12, 14, 16, 20, 24, 32, 48, 64, 128}) and the current one with `reps` launches each (CUDA
  * events on the handle's stream) and keep the fastest. Overwrites the level's work vectors;
  * call it before a solve or between solves. Synchronises the stream.
  * Batched handles (also run at ecmg_create_batched when options.autotune = 1): for every stage,

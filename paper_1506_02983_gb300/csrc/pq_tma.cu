@@ -204,10 +204,11 @@ int k1_candidates(const Grid& g, K1Config* out, int cap)
 {
     (void)g;
     // planes per block; the in-between values let a level end close to a whole number of waves
-    const int kzs[8] = {8, 12, 16, 24, 32, 48, 64, 128};
+    constexpr int NKZ = 11;
+    const int kzs[NKZ] = {8, 10, 12, 14, 16, 20, 24, 32, 48, 64, 128};
     int n = 0;
     for (int v = 0; v < K1_NRY; ++v)
-        for (int z = 0; z < 8; ++z)
+        for (int z = 0; z < NKZ; ++z)
             if (n < cap) out[n++] = K1Config{K1_RY[v], kzs[z]};
     return n;
 }
