@@ -375,14 +375,16 @@ void drop_graph(ecmg_handle* h);
 // FP64 residual of the MIXED iteration into r32 (or, in the single-pass form, into the residual
 // buffer the next step reads): on a constant-coefficient level (the host's choice v.cc, cubic
 // elements) the TMA-staged exact kernel, else the general one.
+// r_b: the single-pass buffer pair taken from the level state (constant-coefficient cubes): the
+// residual goes to rdst or r_b, whichever st->p_latest names.
 void res32(ecmg_handle* h, Level& v, SolveState* st, ResMode mode, CondHandles ch, cudaStream_t s,
-           float* rdst = nullptr)
+           float* rdst = nullptr, float* r_b = nullptr)
 {
     float* r = rdst ? rdst : v.r32;
     if (v.cc && v.op.cube) {
         // a replacement follows the fold, which has taken max |U| already
         if (mode != RES_REPLACE) launch_absmax(v.g, v.U, v.uniform, st, (int)mode, h->part, s);
-        launch_res32_cc(v.rmaps, v.g, v.uniform, v.beta, v.dinv32, r, st, h->part, mode, ch, s);
+        launch_res32_cc(v.rmaps, v.g, v.uniform, v.beta, v.dinv32, r, st, h->part, mode, ch, s, r_b);
     } else {
         launch_res32(v.g, v.op, v.beta, v.uniform, v.U, v.b, v.dinv32, r, st, h->part, mode, ch, s, v.r);
     }
@@ -524,11 +526,16 @@ void record_level(Rec& R, int l)
         float* rbuf[2] = {v.r32, single ? v.r32B : v.r32};
         float* qbuf[2] = {v.q32, single ? v.q32B : v.q32};
         float* pbuf[2] = {v.pA32, v.pB32};
+        // single pass on a constant-coefficient cube: the step picks its buffer set from the level
+        // state, so the loop body needs no fixed alternation and can check for a replacement once
+        // per several steps (a step behind the one that asked returns at once)
+        const bool pf = single && v.cc && v.op.cube;
+        SpSets sets{{v.pA32, v.pB32}, {v.q32, v.q32B}, {v.r32, v.r32B}};
         auto step = [&](CondHandles ch, int half) {
             const int o = half ^ 1;
             if (single) {
                 launch_step32(v.maps, half, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pbuf[o], qbuf[o],
-                              rbuf[o], v.e32, st, h->part, o, ch, h->timers + l, R.s());
+                              rbuf[o], v.e32, st, h->part, o, ch, h->timers + l, R.s(), pf ? &sets : nullptr);
             } else {
                 launch_pq32_tma(v.maps, half, v.k1, v.g, v.op, v.cc, v.uniform, v.beta32, v.dinv32, pbuf[o], v.q32,
                                 v.e32, st, h->part, o, ch, h->timers + l, R.s(), rp);
@@ -539,13 +546,15 @@ void record_level(Rec& R, int l)
         auto replace = [&](int half) {
             const int o = half ^ 1;
             if (ring_on) launch_fold_ring(v.g, v.U, ring, v.e32, v.uniform, st, h->part, R.s());
+            else if (pf) launch_fold32(v.g, v.U, v.e32, pbuf[0], v.uniform, st, h->part, R.s(), pbuf[1]);
             else launch_fold32(v.g, v.U, v.e32, pbuf[o], v.uniform, st, h->part, R.s());
-            res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[o]);
+            if (pf) res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[0], rbuf[1]);
+            else res32(h, v, st, RES_REPLACE, none, R.s(), rbuf[o]);
         };
-        if (R.graph && ring_on) {
-            // with the ring every step reads and writes the same buffers, so one replacement
-            // check serves RING_STEPS steps: a step after the one that asks for a replacement
-            // finds need_update set and returns at once (K1 and K2 both)
+        if (R.graph && (ring_on || pf)) {
+            // with the ring every step reads and writes the same buffers (with pf the buffers come
+            // from the level state), so one replacement check serves RING_STEPS steps: a step
+            // after the one that asks for a replacement finds need_update set and returns at once
             const cudaGraphConditionalHandle loop = R.new_handle();
             res32(h, v, st, RES_INIT, CondHandles{loop, 0, 1}, R.s(), rbuf[0]);
             R.open(loop, cudaGraphCondTypeWhile);

@@ -832,12 +832,13 @@ __global__ void k_final64(int64_t n, double* __restrict__ x, const double* __res
 // operation. On a level with one beta the block also takes max |x| of the new iterate into
 // fs->bits, the scale of the exact residual that follows (no separate pass over x).
 __global__ void __launch_bounds__(UPD_TPB) k_fold32(int64_t n, double* __restrict__ x, float* __restrict__ e,
-                                                   const float* __restrict__ p, const int* __restrict__ uniform,
-                                                   const SolveState* st, FixedScale* fs,
-                                                   unsigned long long* partials)
+                                                   const float* __restrict__ pa, const float* __restrict__ pb,
+                                                   const int* __restrict__ uniform, const SolveState* st,
+                                                   FixedScale* fs, unsigned long long* partials)
 {
     COUNT_LAUNCH();
     if (st->done) return;
+    const float* __restrict__ p = (pb && st->p_latest) ? pb : pa;  // pb: the newest p of the pair
     const float a = (float)st->alpha_prev;
     const bool want_max = *uniform != 0;
     __shared__ unsigned long long sh[UPD_TPB / 32];
@@ -1115,9 +1116,9 @@ void launch_final64(const Grid& g, double* x, const double* pA, const double* pB
     k_final64<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, pA, pB, st);
 }
 void launch_fold32(const Grid& g, double* x, float* e, const float* p, const int* uniform, SolveState* st,
-                   Partials pr, cudaStream_t s)
+                   Partials pr, cudaStream_t s, const float* p_b)
 {
-    k_fold32<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, e, p, uniform, st, pr.fs,
+    k_fold32<<<update_blocks(g.total), UPD_TPB, 0, s>>>(g.total, x, e, p, p_b, uniform, st, pr.fs,
                                                         reinterpret_cast<unsigned long long*>(pr.buf));
 }
 void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed, cudaStream_t s,

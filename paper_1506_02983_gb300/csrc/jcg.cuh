@@ -70,8 +70,10 @@ void launch_final64(const Grid& g, double* x, const double* pA, const double* pB
                     SolveState* st, cudaStream_t s);
 // MIXED: x64 += e + alpha_prev p (combined in FP32, added in FP64); e = 0. With the level's
 // uniform flag set, also max |x| of the new iterate into pr.fs (what launch_absmax computes).
+// p_b: with the single-pass buffer pairs taken from the level state, the other p of the pair; the
+// fold then takes the newest one (st->p_latest).
 void launch_fold32(const Grid& g, double* x, float* e, const float* p, const int* uniform, SolveState* st,
-                   Partials pr, cudaStream_t s);
+                   Partials pr, cudaStream_t s, const float* p_b = nullptr);
 // Reset the level state before a solve; fixed: run exactly max_iters steps (Alg. 3); pring: the
 // slots of the level's ring of search directions (0: none).
 void launch_state_init(SolveState* st, double rtol, double inner_rtol, int max_iters, int fixed,

@@ -205,6 +205,7 @@ struct K1Scalars {
     float cdinv;  // CC: the constant D^-1
     float bu;     // CC: the constant beta
     int pw = -1;  // ring slot of p_old (ring of search directions; -1: p_old is its own vector)
+    int skip = 0; // a step behind one that asked for a replacement: return, conditions untouched
 };
 
 // Last block of a single-pass step. alpha comes from the measured r.z (this step's r) and p.q;
@@ -277,6 +278,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     __shared__ int issued_hi;              // highest staged plane index issued so far
     __shared__ unsigned int ticket;
 
+    if (sc.skip) return;
     if (sc.done) {
         // single pass: no residual kernel follows, so the loop's conditions are cleared here
         if (SP && ch.use && kb.bid == 0 && (threadIdx.x | threadIdx.y) == 0) {

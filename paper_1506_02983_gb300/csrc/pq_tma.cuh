@@ -67,10 +67,17 @@ void launch_pq32_tma(const PlaneMaps& m, int pold_is_b, const K1Config& c, const
 // p = D^-1 r + beta p_old, q = A p; stores r, p, q; the last block sets alpha, the expanded
 // next r.z and r.r, the test of update_epilogue and the loop's conditions (loop, update).
 // cc as for launch_pq32_tma.
+// sets: with a one-beta, all-Dirichlet level (cc) the buffer sets may instead be taken from the
+// level state: the step reads set st->p_latest and writes the other (in_b, pnew, qnew, rnew and
+// pidx are then unused), and a step that finds a replacement requested returns at once, so that
+// several steps can share one replacement check.
+struct SpSets {
+    float *p[2], *q[2], *r[2];
+};
 void launch_step32(const PlaneMaps& m, int in_b, const K1Config& c, const Grid& g, const Op& op, bool cc,
                    const int* uniform, const float* beta32, const float* dinv32, float* pnew, float* qnew,
                    float* rnew, float* e, SolveState* st, Partials pr, int pidx, CondHandles ch, KTimer* tm,
-                   cudaStream_t s);
+                   cudaStream_t s, const SpSets* sets = nullptr);
 cudaError_t k1_sp_prepare();
 
 unsigned long long launches_pq_tma();

@@ -57,11 +57,13 @@ struct Col {
 
 __global__ void __launch_bounds__(NT, 5)
 k_res_cc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mbc, const Grid g,
-         float* __restrict__ r, SolveState* st, double* partials, int mode, CondHandles ch, int kz,
-         const FixedScale* fs, const int* __restrict__ uniform, const double* __restrict__ beta,
+         float* __restrict__ ra, float* __restrict__ rb, SolveState* st, double* partials, int mode, CondHandles ch,
+         int kz, const FixedScale* fs, const int* __restrict__ uniform, const double* __restrict__ beta,
          const float* __restrict__ dinv32)
 {
     COUNT_LAUNCH();
+    // rb: the single-pass buffer pair from the level state: r goes where the next step reads it
+    float* __restrict__ r = (rb && st->p_latest) ? rb : ra;
     extern __shared__ __align__(128) unsigned char rc_smem[];
     __shared__ long long P[2][PY][PX];
     __shared__ __align__(8) uint64_t bar[NS];
@@ -272,11 +274,11 @@ int res_cc_blocks(const Grid& g)
 }
 
 void launch_res32_cc(const ResMaps& m, const Grid& g, const int* uniform, const double* beta, const float* dinv32,
-                     float* r, SolveState* st, Partials pr, ResMode mode, CondHandles ch, cudaStream_t s)
+                     float* r, SolveState* st, Partials pr, ResMode mode, CondHandles ch, cudaStream_t s, float* r_b)
 {
     const int kz = res_kz(g);
     const dim3 grid(cdiv(max(g.nx - 1, 1), TBX), cdiv(max(g.ny - 1, 1), TBY), cdiv(max(g.nz - 1, 1), kz));
-    k_res_cc<<<grid, dim3(TBX, TBY), smem_bytes(), s>>>(m.x, m.bc, g, r, st, pr.buf, (int)mode, ch, kz, pr.fs,
+    k_res_cc<<<grid, dim3(TBX, TBY), smem_bytes(), s>>>(m.x, m.bc, g, r, r_b, st, pr.buf, (int)mode, ch, kz, pr.fs,
                                                         uniform, beta, dinv32);
 }
 

@@ -24,8 +24,11 @@ int res_cc_blocks(const Grid& g);
 // RES_REPLACE or RES_REPORT). Needs the level's max |x| in pr.fs (launch_absmax, same
 // stream) and max |b / c| in st->bcbits (launch_fh2). If the level's uniform flag is
 // clear when the kernel runs, it records status 6 and finishes the level without computing.
+// r_b: with the single-pass buffer pair taken from the level state, the other r of the pair; the
+// residual then goes to r_b when st->p_latest is 1 (the buffer the next step reads).
 void launch_res32_cc(const ResMaps& m, const Grid& g, const int* uniform, const double* beta, const float* dinv32,
-                     float* r, SolveState* st, Partials pr, ResMode mode, CondHandles ch, cudaStream_t s);
+                     float* r, SolveState* st, Partials pr, ResMode mode, CondHandles ch, cudaStream_t s,
+                     float* r_b = nullptr);
 
 unsigned long long launches_res_cc();
 
