@@ -125,25 +125,56 @@ struct KSum {
         s = t;
         c = __fadd_rn(c, err);
     }
+    // another compensated pair (s2, c2): TwoSum of the leading parts, and the compensations and
+    // the rounding error of that sum added in FP32
+    __device__ __forceinline__ void merge(float s2, float c2)
+    {
+        const float t = __fadd_rn(s, s2);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(c2, err));
+    }
+    __device__ __forceinline__ void merge(float2 p) { merge(p.x, p.y); }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Block sums of NP compensated pairs, in FP32 arithmetic throughout (this part's FP64 pipe runs
+// at a small fraction of its FP32 rate, and an FP64 tree here held every block for microseconds):
+// the lanes of each warp merge their pairs by shuffles, then warp 0 merges the eight warps' pairs,
+// eight lanes per sum. Sum c goes to out[c]; every thread may read out after the return.
 template <int NP>
-__device__ __forceinline__ void block_sum(double (&v)[NP], double* sh)
+__device__ __forceinline__ void block_merge(KSum (&k)[NP], float2* sh, float2* out)
 {
+    constexpr int NW = NT / 32;
+    static_assert(NW == 8, "warp 0 merges the warps' pairs in groups of eight lanes");
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int c = 0; c < NP; ++c)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, k[c].s, o);
+            const float c2 = __shfl_down_sync(0xffffffffu, k[c].c, o);
+            k[c].merge(s2, c2);
+        }
     if (lane == 0)
-        for (int c = 0; c < NP; ++c) sh[c * 32 + warp] = v[c];
+#pragma unroll
+        for (int c = 0; c < NP; ++c) sh[c * NW + warp] = make_float2(k[c].s, k[c].c);
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) {
-            v[c] = (lane < nw) ? sh[c * 32 + lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        for (int c0 = 0; c0 < NP; c0 += 4) {
+            const int c = c0 + (lane >> 3);
+            KSum m;
+            if (c < NP) m.merge(sh[c * NW + (lane & 7)]);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const float s2 = __shfl_down_sync(0xffffffffu, m.s, o, 8);
+                const float c2 = __shfl_down_sync(0xffffffffu, m.c, o, 8);
+                m.merge(s2, c2);
+            }
+            if ((lane & 7) == 0 && c < NP) out[c] = make_float2(m.s, m.c);
         }
     }
     __syncthreads();
@@ -273,7 +304,7 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     auto box = [&](int slot, int a) -> float* { return ring + slot * STAGEF + a * S::BOXF_PAD; };
     __shared__ float P[2][S::PY][S::PX];
     __shared__ __align__(8) uint64_t bar[NS];
-    __shared__ double red[32 * NP];
+    __shared__ float2 red[8 * NP], red_out[NP];
     __shared__ int bad;
     __shared__ int issued_hi;              // highest staged plane index issued so far
     __shared__ unsigned int ticket;
@@ -552,24 +583,27 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     }
 
     // grid reduction of p.q (and the single-pass sums), last block advances the recurrence;
-    // partials holds sum c of block b at c * nb + b
-    double v[NP];
-    v[0] = acc.value();
+    // partials holds the compensated pair of sum c of block b at c * nb + b (a float2 per double
+    // slot), and the last block merges them in the same FP32 arithmetic before the one widening
+    // to FP64 of each sum
+    KSum kv[NP];
+    kv[0] = acc;
     if constexpr (SP) {
-        v[1] = a_rr.value();
-        v[2] = a_rq.value();
-        v[3] = a_qq.value();
+        kv[1] = a_rr;
+        kv[2] = a_rq;
+        kv[3] = a_qq;
         if constexpr (!CC) {
-            v[4] = a_rz.value();
-            v[5] = a_zq.value();
-            v[6] = a_qzq.value();
+            kv[4] = a_rz;
+            kv[5] = a_zq;
+            kv[6] = a_qzq;
         }
     }
     const int nb = kb.nb, bid = kb.bid;
-    block_sum<NP>(v, red);
+    float2* pp = reinterpret_cast<float2*>(partials);
+    block_merge<NP>(kv, red, red_out);
     if (tid == 0) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) partials[c * nb + bid] = v[c];
+        for (int c = 0; c < NP; ++c) pp[c * nb + bid] = red_out[c];
         __threadfence();
         ticket = atomicAdd(&st->arrive, 1u);
     }
@@ -577,12 +611,15 @@ __device__ __forceinline__ void k1_body(const CUtensorMap& m_r, const CUtensorMa
     if (ticket != (unsigned int)(nb - 1)) return;
     __threadfence();
 #pragma unroll
-    for (int c = 0; c < NP; ++c) v[c] = 0.0;
+    for (int c = 0; c < NP; ++c) kv[c] = KSum{};
     for (int b = tid; b < nb; b += NT)
 #pragma unroll
-        for (int c = 0; c < NP; ++c) v[c] += __ldcg(&partials[c * nb + b]);
-    block_sum<NP>(v, red);
+        for (int c = 0; c < NP; ++c) kv[c].merge(__ldcg(&pp[c * nb + b]));
+    block_merge<NP>(kv, red, red_out);
     if (tid == 0) {
+        double v[NP];
+#pragma unroll
+        for (int c = 0; c < NP; ++c) v[c] = (double)red_out[c].x + (double)red_out[c].y;
         if (tm) {
             tm->ns += global_ns() - tm->t0;
             tm->n += 1;
