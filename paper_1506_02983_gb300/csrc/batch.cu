@@ -142,6 +142,38 @@ __device__ bool item_sum(double (&v)[NP], double* partials, unsigned int* arrive
     return tid == 0;
 }
 
+// The same over compensated FP32 pairs of 256-thread blocks, merged in FP32 (block_merge) and
+// widened to FP64 once per total (out); partials hold a float2 per double slot.
+template <int NP>
+__device__ bool item_merge(CSum (&v)[NP], double* partials, unsigned int* arrive, int lb, int nb, double (&out)[NP])
+{
+    __shared__ float2 sh[NP * 8], tot[NP];
+    __shared__ unsigned int ticket;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    float2* pp = reinterpret_cast<float2*>(partials);
+    block_merge<NP>(v, sh, tot);
+    if (tid == 0) {
+        for (int c = 0; c < NP; ++c) pp[lb * NP + c] = tot[c];
+        __threadfence();
+        ticket = atomicAdd(arrive, 1u);
+    }
+    __syncthreads();
+    if (ticket != (unsigned int)(nb - 1)) return false;
+    __threadfence();
+    for (int c = 0; c < NP; ++c) v[c] = CSum{0.f, 0.f};
+    for (int b = tid; b < nb; b += FLAT_TPB)
+#pragma unroll
+        for (int c = 0; c < NP; ++c) {
+            const float2 p = __ldcg(&pp[b * NP + c]);
+            twosum_merge(v[c].s, v[c].c, p.x, p.y);
+        }
+    block_merge<NP>(v, sh, tot);
+    if (tid != 0) return false;
+    *arrive = 0u;
+    for (int c = 0; c < NP; ++c) out[c] = (double)tot[c].x + (double)tot[c].y;
+    return true;
+}
+
 // Launch-wide arrival, one per item: the item's last block after its epilogue, or block 0 of an
 // item that had nothing to do. True in the thread that brings the count to the number of items
 // of the launch -- every item epilogue of the launch is then written.
@@ -477,8 +509,9 @@ __global__ void __launch_bounds__(FLAT_TPB) bk_update(const BItem* __restrict__ 
             rr.add_prod(rv.w, rv.w);
             r4[t] = rv;
         });
-        double v[2] = {rz.value(), rr.value()};
-        if (item_sum<2>(v, it.part, &st->arrive, sl.lb, sl.nb)) {
+        CSum pr[2] = {rz.v, rr.v};
+        double v[2];
+        if (item_merge<2>(pr, it.part, &st->arrive, sl.lb, sl.nb, v)) {
             update_epilogue<true>(st, v[0], v[1]);
             if (item_arrives(ctl, L.n)) batch_conditions(items, L, CondHandles{ch.loop, ch.update, ch.use ? 2 : 0});
         }

@@ -87,6 +87,42 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NP], double* partials, unsi
     return tid == 0;
 }
 
+// Sum compensated FP32 pairs over a 1D grid of 256-thread blocks in FP32 arithmetic: each block
+// merges its threads' pairs (block_merge) into partials (a float2 per double slot), the last
+// block to arrive merges the blocks' pairs the same way, and each total is widened to FP64 once.
+// Returns true in thread 0 of the last block, which then holds the totals in out.
+template <int NP>
+__device__ __forceinline__ bool grid_merge(CSum (&v)[NP], double* partials, unsigned int* arrive,
+                                           double (&out)[NP])
+{
+    __shared__ float2 sh[NP * 8], tot[NP];
+    __shared__ unsigned int ticket;
+    const int tid = threadIdx.x;
+    const int nb = gridDim.x;
+    float2* pp = reinterpret_cast<float2*>(partials);
+    block_merge<NP>(v, sh, tot);
+    if (tid == 0) {
+        for (int c = 0; c < NP; ++c) pp[blockIdx.x * NP + c] = tot[c];
+        __threadfence();
+        ticket = atomicAdd(arrive, 1u);
+    }
+    __syncthreads();
+    if (ticket != (unsigned int)(nb - 1)) return false;
+    __threadfence();
+    for (int c = 0; c < NP; ++c) v[c] = CSum{0.f, 0.f};
+    for (int b = tid; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NP; ++c) {
+            const float2 p = __ldcg(&pp[b * NP + c]);
+            twosum_merge(v[c].s, v[c].c, p.x, p.y);
+        }
+    block_merge<NP>(v, sh, tot);
+    if (tid != 0) return false;
+    *arrive = 0u;
+    for (int c = 0; c < NP; ++c) out[c] = (double)tot[c].x + (double)tot[c].y;
+    return true;
+}
+
 // ---- the tiled z-march (march.cuh), one tile per block ---------------------------------------
 template <bool ROBIN, bool CUBE, typename VT, typename BT, typename SRC, typename BODY>
 __device__ __forceinline__ void march(const Grid& g, const Op& op, const BT* __restrict__ beta,
@@ -799,8 +835,17 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
             rv4[t] = rr4;
         }
     }
-    double v[2] = {rz.value(), rr.value()};
-    if (grid_sum<2>(v, partials, &st->arrive)) {
+    double v[2];
+    bool last;
+    if constexpr (sizeof(T) == 4) {
+        CSum pr[2] = {rz.v, rr.v};  // FP32 data: the pairs merged in FP32 (grid_merge)
+        last = grid_merge<2>(pr, partials, &st->arrive, v);
+    } else {
+        v[0] = rz.value();
+        v[1] = rr.value();
+        last = grid_sum<2>(v, partials, &st->arrive);
+    }
+    if (last) {
         if (cc) v[0] = (double)*cdiag * v[1];
         if (spill) {  // every block has read the pending set above
             st->pbase = (st->pj + 1) % st->pring;

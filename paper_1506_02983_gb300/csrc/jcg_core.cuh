@@ -10,8 +10,9 @@ namespace ecmg {
 
 // ---- compensated FP32 accumulation ------------------------------------------------------
 // Products are split exactly (TwoProduct with an FMA) and summed with TwoSum, so a thread's
-// sum of FP32 products carries about 48 significant bits before it is promoted to FP64 for
-// the block and grid stages. Intrinsics keep the compiler from contracting the steps.
+// sum of FP32 products carries about 48 significant bits; the block and grid stages merge such
+// pairs the same way (block_merge) and widen each total to FP64 once. Intrinsics keep the
+// compiler from contracting the steps.
 struct CSum {
     float s, c;
 };
@@ -31,6 +32,62 @@ __device__ __forceinline__ void csum_add_prod(CSum& a, float x, float y)
     a.c = __fadd_rn(a.c, e);
 }
 __device__ __forceinline__ double csum_value(const CSum& a) { return (double)a.s + (double)a.c; }
+
+// Merge the compensated pair (s2, c2) into (s, c): TwoSum of the leading parts, and the
+// compensations and the rounding error of that sum added in FP32.
+__device__ __forceinline__ void twosum_merge(float& s, float& c, float s2, float c2)
+{
+    const float t = __fadd_rn(s, s2);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, err));
+}
+
+// Block sums of NP compensated pairs (any type with float members s and c) of a 256-thread
+// block, in FP32 arithmetic throughout: this part's FP64 pipe runs at a small fraction of its
+// FP32 rate, and an FP64 tree here held every block for microseconds. The lanes of each warp
+// merge their pairs by shuffles, then warp 0 merges the eight warps' pairs, eight lanes per sum.
+// Sum c goes to out[c]; sh holds 8 NP pairs. Every thread may read out after the return.
+template <int NP, typename P>
+__device__ __forceinline__ void block_merge(P (&k)[NP], float2* sh, float2* out)
+{
+    constexpr int NW = 8;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int c = 0; c < NP; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, k[c].s, o);
+            const float c2 = __shfl_down_sync(0xffffffffu, k[c].c, o);
+            twosum_merge(k[c].s, k[c].c, s2, c2);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NP; ++c) sh[c * NW + warp] = make_float2(k[c].s, k[c].c);
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int c0 = 0; c0 < NP; c0 += 4) {
+            const int c = c0 + (lane >> 3);
+            float ms = 0.f, mc = 0.f;
+            if (c < NP) {
+                const float2 p = sh[c * NW + (lane & 7)];
+                ms = p.x;
+                mc = p.y;
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const float s2 = __shfl_down_sync(0xffffffffu, ms, o, 8);
+                const float c2 = __shfl_down_sync(0xffffffffu, mc, o, 8);
+                twosum_merge(ms, mc, s2, c2);
+            }
+            if ((lane & 7) == 0 && c < NP) out[c] = make_float2(ms, mc);
+        }
+    }
+    __syncthreads();
+}
 
 // Accumulator selection: FP64 for FP64 data, compensated FP32 for FP32 data.
 template <typename T> struct Acc;

@@ -103,7 +103,8 @@ inline dim3 k1_grid(const Range& rg, const K1Config& c)
 
 inline int ry_index(int ry) { return ry == 1 ? 0 : 1; }
 
-// compensated FP32 accumulation (TwoProduct + TwoSum), promoted to FP64 per thread
+// compensated FP32 accumulation (TwoProduct + TwoSum); the block and grid stages merge the
+// pairs in FP32 (block_merge) and widen each total to FP64 once
 struct KSum {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add_prod(float x, float y)
@@ -125,60 +126,10 @@ struct KSum {
         s = t;
         c = __fadd_rn(c, err);
     }
-    // another compensated pair (s2, c2): TwoSum of the leading parts, and the compensations and
-    // the rounding error of that sum added in FP32
-    __device__ __forceinline__ void merge(float s2, float c2)
-    {
-        const float t = __fadd_rn(s, s2);
-        const float bp = __fsub_rn(t, s);
-        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
-        s = t;
-        c = __fadd_rn(c, __fadd_rn(c2, err));
-    }
-    __device__ __forceinline__ void merge(float2 p) { merge(p.x, p.y); }
+    __device__ __forceinline__ void merge(float2 p) { twosum_merge(s, c, p.x, p.y); }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
-
-// Block sums of NP compensated pairs, in FP32 arithmetic throughout (this part's FP64 pipe runs
-// at a small fraction of its FP32 rate, and an FP64 tree here held every block for microseconds):
-// the lanes of each warp merge their pairs by shuffles, then warp 0 merges the eight warps' pairs,
-// eight lanes per sum. Sum c goes to out[c]; every thread may read out after the return.
-template <int NP>
-__device__ __forceinline__ void block_merge(KSum (&k)[NP], float2* sh, float2* out)
-{
-    constexpr int NW = NT / 32;
-    static_assert(NW == 8, "warp 0 merges the warps' pairs in groups of eight lanes");
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int c = 0; c < NP; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float s2 = __shfl_down_sync(0xffffffffu, k[c].s, o);
-            const float c2 = __shfl_down_sync(0xffffffffu, k[c].c, o);
-            k[c].merge(s2, c2);
-        }
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < NP; ++c) sh[c * NW + warp] = make_float2(k[c].s, k[c].c);
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int c0 = 0; c0 < NP; c0 += 4) {
-            const int c = c0 + (lane >> 3);
-            KSum m;
-            if (c < NP) m.merge(sh[c * NW + (lane & 7)]);
-#pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
-                const float s2 = __shfl_down_sync(0xffffffffu, m.s, o, 8);
-                const float c2 = __shfl_down_sync(0xffffffffu, m.c, o, 8);
-                m.merge(s2, c2);
-            }
-            if ((lane & 7) == 0 && c < NP) out[c] = make_float2(m.s, m.c);
-        }
-    }
-    __syncthreads();
-}
+static_assert(NT == 256, "block_merge takes 256-thread blocks");
 
 // Constant-coefficient operator by plane sums. With one beta bu on the level, every node the
 // kernel visits interior, and the 27-point stencil of q1_interior written per plane: for the
