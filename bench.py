@@ -627,6 +627,7 @@ def main():
     k1_live_ms = k1_live_total_ms / max(k1_live_n, 1)
     tiles = mixed.get_tiles(-1)
     mixed_tiles = tiles
+    level_tiles = {l: mixed.get_tiles(l) for l in range(2, L)}
 
     # end to end through the C ABI from pinned host buffers
     u_host = torch.empty(u_exact.shape, dtype=torch.float64).pin_memory()
@@ -654,7 +655,8 @@ def main():
                           max_iters=args.max_iters, use_graph=0 if args.eager else 1, inner_rtol=args.inner_rtol)
     st_c, status = compact.solve(u_out)
     assert status == 0, st_c
-    compact.autotune(3)
+    for l in range(2, L):  # same level sizes and kernels as the dense-input handle: its tuned shapes
+        compact.set_tiles(*level_tiles[l], level=l)
 
     def e2e_compact():
         for k in ("f", "gD"):

@@ -337,10 +337,12 @@ ecmg_status ecmg_stencil_timer(ecmg_handle* h, int32_t level, int32_t reset, dou
 ecmg_status ecmg_set_tiles(ecmg_handle* h, int32_t level, int32_t ry, int32_t kz);
 /* Read the shape of one level into *ry, *kz (host). */
 ecmg_status ecmg_get_tiles(ecmg_handle* h, int32_t level, int32_t* ry, int32_t* kz);
-/* Autotuner: on every MIXED level of at least 2^18 nodes, time each candidate shape (ry in
- * {1, 2} x kz in {8, 10, 12, 14, 16, 20, 24, 32, 48, 64, 128}) and the current one with `reps` launches each (CUDA
- * events on the handle's stream) and keep the fastest. Overwrites the level's work vectors;
- * call it before a solve or between solves. Synchronises the stream.
+/* Autotuner: on every MIXED level of at least 2^18 nodes, try each candidate shape (ry in
+ * {1, 2} x kz in {4, 6, 8, 10, 12, 14, 16, 20, 24, 32, 48, 64, 128}) and the current one: each
+ * shape is set on all those levels at once and the whole solve runs `reps` times (level times from
+ * device time stamps, so each level is timed as the solve runs it); every level keeps its fastest
+ * shape. Costs 27 x reps solves. Overwrites every level's vectors (the solution included); call it
+ * before a solve or between solves. Synchronises the stream.
  * Batched handles (also run at ecmg_create_batched when options.autotune = 1): for every stage,
  * the stage's whole K1 launch is timed for ry in {1, 2} x kz in {4, 8, 16, 32, 64} applied to all
  * of its items, then the kz of each size class of items (the same power of two of z nodes) is

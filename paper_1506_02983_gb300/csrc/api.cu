@@ -1182,35 +1182,70 @@ void batch_autotune(ecmg_handle* h, int reps)
     drop_graph(h);
 }
 
+// Tile shape of the FP32 stencil kernel (K1, or the single-pass step) per level: every candidate
+// shape is set on all tuned levels at once (their kernels do not interact), the whole solve runs
+// `reps` times, and each level keeps the shape of its shortest level time (device time stamps).
+// Inside the solve a level's kernels meet the cache state the kernels before them leave (K1
+// after K2 or after a replacement), which a kernel timed alone does not: alone, the 256^3 level
+// of the cos_cube benchmark preferred 128 planes per block, inside the solve 16 (16.6 against
+// 15.3 ms).
 void autotune(ecmg_handle* h, int reps)
 {
     if (h->batch) {
         batch_autotune(h, reps);
         return;
     }
-    bool changed = false;
+    // the tuned levels: MIXED levels of at least AUTOTUNE_MIN_NODES nodes
+    std::vector<int> lv;
     for (int l = 2; l < h->L; ++l) {
-        Level& v = h->lv[l];
-        if (!v.r32) continue;
-        if ((int64_t)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1) < AUTOTUNE_MIN_NODES) continue;
-        K1Config cand[32];
-        const int n = k1_candidates(v.g, cand, 32);
-        const K1Config start = v.k1;
-        K1Config best = start;
-        const int which = v.r32B ? 11 : 0;  // the step kernel the solve runs
-        double best_ms = time_launches(h, l, which, reps);
-        for (int c = 0; c < n; ++c) {
-            v.k1 = cand[c];
-            const double ms = time_launches(h, l, which, reps);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = cand[c];
+        const Level& v = h->lv[l];
+        if (v.r32 && (int64_t)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1) >= AUTOTUNE_MIN_NODES) lv.push_back(l);
+    }
+    if (lv.empty()) return;
+    const int nl = (int)lv.size();
+    // level seconds of the fastest of `reps` whole solves with the shapes now set (device time
+    // stamps) and the levels' iteration counts; false when a solve did not succeed
+    std::vector<double> t(nl);
+    std::vector<int> it(nl);
+    auto measure = [&]() -> bool {
+        drop_graph(h);
+        std::fill(t.begin(), t.end(), INFINITY);
+        for (int r = 0; r < reps; ++r) {
+            ecmg_stats st;
+            if (run_solve(h, 0, nullptr, &st) != ECMG_OK) return false;
+            for (int i = 0; i < nl; ++i) {
+                t[i] = std::min(t[i], st.seconds[lv[i]]);
+                it[i] = st.iters[lv[i]];
             }
         }
-        v.k1 = best;
-        changed |= best.ry != start.ry || best.kz != start.kz;
+        return true;
+    };
+    std::vector<K1Config> best(nl);
+    std::vector<double> best_t(nl, INFINITY);
+    std::vector<int> it0(nl, 0);
+    for (int i = 0; i < nl; ++i) best[i] = h->lv[lv[i]].k1;
+    if (measure()) {
+        best_t = t;
+        it0 = it;
     }
-    if (changed) drop_graph(h);
+    K1Config cand[32];
+    const int n = k1_candidates(h->lv[lv[0]].g, cand, 32);
+    for (int c = 0; c < n; ++c) {
+        for (int i = 0; i < nl; ++i) h->lv[lv[i]].k1 = cand[c];
+        if (!measure()) continue;
+        for (int i = 0; i < nl; ++i) {
+            // a shape sums p.q in another order, which can move a level's iteration count by a
+            // step: compare per iteration, at the starting shape's count
+            const double ti = (it[i] > 0 && it0[i] > 0) ? t[i] * it0[i] / it[i] : t[i];
+            if (ti < best_t[i]) {
+                best_t[i] = ti;
+                best[i] = cand[c];
+            }
+        }
+    }
+    for (int i = 0; i < nl; ++i) h->lv[lv[i]].k1 = best[i];
+    drop_graph(h);
+    g_last_error.clear();
 }
 
 }  // namespace

@@ -87,22 +87,22 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NP], double* partials, unsi
     return tid == 0;
 }
 
-// Sum compensated FP32 pairs over a 1D grid of 256-thread blocks in FP32 arithmetic: each block
+// Sum compensated FP32 pairs over a grid of 256-thread blocks in FP32 arithmetic: each block
 // merges its threads' pairs (block_merge) into partials (a float2 per double slot), the last
 // block to arrive merges the blocks' pairs the same way, and each total is widened to FP64 once.
-// Returns true in thread 0 of the last block, which then holds the totals in out.
+// Returns true in thread 0 of the last block, which then holds the totals in out. bid and nb: the
+// block's index in the grid and the grid's size (the caller's layout, 1D or 3D).
 template <int NP>
 __device__ __forceinline__ bool grid_merge(CSum (&v)[NP], double* partials, unsigned int* arrive,
-                                           double (&out)[NP])
+                                           double (&out)[NP], int bid, int nb)
 {
     __shared__ float2 sh[NP * 8], tot[NP];
     __shared__ unsigned int ticket;
-    const int tid = threadIdx.x;
-    const int nb = gridDim.x;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     float2* pp = reinterpret_cast<float2*>(partials);
     block_merge<NP>(v, sh, tot);
     if (tid == 0) {
-        for (int c = 0; c < NP; ++c) pp[blockIdx.x * NP + c] = tot[c];
+        for (int c = 0; c < NP; ++c) pp[bid * NP + c] = tot[c];
         __threadfence();
         ticket = atomicAdd(arrive, 1u);
     }
@@ -110,7 +110,7 @@ __device__ __forceinline__ bool grid_merge(CSum (&v)[NP], double* partials, unsi
     if (ticket != (unsigned int)(nb - 1)) return false;
     __threadfence();
     for (int c = 0; c < NP; ++c) v[c] = CSum{0.f, 0.f};
-    for (int b = tid; b < nb; b += blockDim.x)
+    for (int b = tid; b < nb; b += 256)
 #pragma unroll
         for (int c = 0; c < NP; ++c) {
             const float2 p = __ldcg(&pp[b * NP + c]);
@@ -543,16 +543,19 @@ __global__ void __launch_bounds__(NT) k_res(const Grid g, const Op op, const dou
                 r[o] = ro;
                 rr32.add_prod(ro, ro);
             };
-            double v[2] = {0.0, 0.0};
+            CSum pr[1] = {CSum{0.f, 0.f}};
             if (fr.finite) {
                 march_fixed<false, decltype(src), decltype(body), true>(fsm, g, op, beta[g.off(0, 0, 0)], fr, kz,
                                                                         src, body);
-                v[0] = rr32.value();
-                v[1] = (double)dinv[g.off(1, 1, 1)] * v[0];
+                pr[0] = rr32.v;
             } else if (threadIdx.x == 0 && threadIdx.y == 0) {
-                v[0] = nan("");  // breakdown: the iterate is not finite
+                pr[0].s = __int_as_float(0x7fc00000);  // NaN: breakdown, the iterate is not finite
             }
-            if (grid_sum<2>(v, partials, &st->arrive)) res_epilogue(st, v[0], v[1], mode, ch);
+            double v[1];
+            const int nb = gridDim.x * gridDim.y * gridDim.z;
+            const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+            if (grid_merge<1>(pr, partials, &st->arrive, v, bid, nb))
+                res_epilogue(st, v[0], (double)dinv[g.off(1, 1, 1)] * v[0], mode, ch);
             return;
         }
     }
@@ -839,7 +842,7 @@ __global__ void __launch_bounds__(UPD_TPB) k_update(int64_t n, T* __restrict__ r
     bool last;
     if constexpr (sizeof(T) == 4) {
         CSum pr[2] = {rz.v, rr.v};  // FP32 data: the pairs merged in FP32 (grid_merge)
-        last = grid_merge<2>(pr, partials, &st->arrive, v);
+        last = grid_merge<2>(pr, partials, &st->arrive, v, (int)blockIdx.x, (int)gridDim.x);
     } else {
         v[0] = rz.value();
         v[1] = rr.value();

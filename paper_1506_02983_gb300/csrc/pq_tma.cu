@@ -204,8 +204,8 @@ int k1_candidates(const Grid& g, K1Config* out, int cap)
 {
     (void)g;
     // planes per block; the in-between values let a level end close to a whole number of waves
-    constexpr int NKZ = 11;
-    const int kzs[NKZ] = {8, 10, 12, 14, 16, 20, 24, 32, 48, 64, 128};
+    constexpr int NKZ = 13;
+    const int kzs[NKZ] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 32, 48, 64, 128};
     int n = 0;
     for (int v = 0; v < K1_NRY; ++v)
         for (int z = 0; z < NKZ; ++z)

@@ -67,7 +67,7 @@ k_res_cc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtenso
     extern __shared__ __align__(128) unsigned char rc_smem[];
     __shared__ long long P[2][PY][PX];
     __shared__ __align__(8) uint64_t bar[NS];
-    __shared__ double red[2][32];
+    __shared__ float2 red[8], red_out[1];
     __shared__ int bad;
     __shared__ int issued_hi;
     __shared__ unsigned int ticket;
@@ -210,32 +210,30 @@ k_res_cc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtenso
         }
     }
 
-    // ||r||^2 (compensated FP32 products, FP64 across threads) and r.z = D^-1 r.r
-    double v0 = fr.finite ? rr.value() : (tid == 0 && first_block ? nan("") : 0.0);
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int w = 16; w > 0; w >>= 1) v0 += __shfl_down_sync(0xffffffffu, v0, w);
-    if (lane == 0) red[0][warp] = v0;
-    __syncthreads();
+    // ||r||^2: compensated FP32 products, merged in FP32 pairs over the block and the grid
+    // (block_merge; partials hold a float2 per double slot) and widened to FP64 once; r.z = D^-1 r.r
+    CSum pr[1] = {rr.v};
+    if (!fr.finite) pr[0] = CSum{(tid == 0 && first_block) ? __int_as_float(0x7fc00000) : 0.f, 0.f};  // NaN
     const int nb = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    float2* pp = reinterpret_cast<float2*>(partials);
+    block_merge<1>(pr, red, red_out);
     if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < NT / 32; ++w) s += red[0][w];
-        partials[bid] = s;
+        pp[bid] = red_out[0];
         __threadfence();
         ticket = atomicAdd(&st->arrive, 1u);
     }
     __syncthreads();
     if (ticket != (unsigned int)(nb - 1)) return;
     __threadfence();
-    double v = 0.0;
-    for (int b = tid; b < nb; b += NT) v += __ldcg(&partials[b]);
-    for (int w = 16; w > 0; w >>= 1) v += __shfl_down_sync(0xffffffffu, v, w);
-    if (lane == 0) red[1][warp] = v;
-    __syncthreads();
+    pr[0] = CSum{0.f, 0.f};
+    for (int b = tid; b < nb; b += NT) {
+        const float2 p = __ldcg(&pp[b]);
+        twosum_merge(pr[0].s, pr[0].c, p.x, p.y);
+    }
+    block_merge<1>(pr, red, red_out);
     if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < NT / 32; ++w) s += red[1][w];
+        const double s = (double)red_out[0].x + (double)red_out[0].y;
         st->arrive = 0u;
         res_epilogue(st, s, (double)dd * s, mode, ch);
     }
