@@ -110,6 +110,12 @@ struct ecmg_handle {
     double* host_norms = nullptr;       // pinned
     int graph_first = -1;               // first level of the recorded graph
     Batch* batch = nullptr;             // batched handle (ecmg_create_batched), else null
+    // the starts of levels >= 2 (state, Dirichlet shell, ||f_h||) on a second stream while the
+    // coarser levels solve: the stream, its partials, one event per level it completes
+    cudaStream_t side = nullptr;
+    Partials part_side{nullptr, 0, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_level[MAX_LEVELS] = {};
 };
 
 namespace {
@@ -448,9 +454,13 @@ int schedule_steps(int L, int l, int mL, double beta)
 }
 
 // ---- one level of Alg. 4 ------------------------------------------------------------------------
-void record_level(Rec& R, int l)
+// The start of level l: its state, the Dirichlet extension and ||f_h|| (Alg. 4 line 7's
+// threshold). It needs only the set-up (b, beta, g_D of the level), not the coarser solutions,
+// so after a full set-up the starts of the large levels run on a second stream while the small
+// levels solve (record_solve); pr: the partials of the ||f_h|| reduction on that stream,
+// fh_blocks: a cap on the blocks of that pass (0: none).
+void level_start(ecmg_handle* h, bool graph, int l, cudaStream_t s, Partials pr, int fh_blocks = 0)
 {
-    ecmg_handle* h = R.h;
     Level& v = h->lv[l];
     SolveState* st = h->states + l;
     const ecmg_options& o = h->opt;
@@ -459,19 +469,33 @@ void record_level(Rec& R, int l)
     const bool fixed = o.schedule == ECMG_SCHED_FIXED && !direct;
     const double rtol = direct ? o.dsolve_rtol : (fixed ? 0.0 : o.rtol);
     const int max_iters = fixed ? schedule_steps(h->L, l, o.sched_mL, o.sched_beta) : o.max_iters;
-    CondHandles none{0, 0, 0};
     // eager: the set-up of this solve (or of the last one, for a solve from a finer level) has
     // run, so the level's flag can be read now; a graph takes the choice made before its recording
-    if (mixed && !R.graph) v.cc = constant_coefficient(h, v);
+    if (mixed && !graph) v.cc = constant_coefficient(h, v);
     // the ring of search directions runs with the constant-coefficient stencil kernel only
     const bool ring_on = mixed && v.ring && v.cc;
-
-    launch_state_init(st, rtol, o.inner_rtol, max_iters, fixed ? 1 : 0, R.s(), ring_on ? v.R : 0);
+    launch_state_init(st, rtol, o.inner_rtol, max_iters, fixed ? 1 : 0, s, ring_on ? v.R : 0);
     // levels >= 2: EXP_finite writes every free node below, so only the shell that ||f_h|| reads
-    dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, R.s(), /*shell=*/l >= 2);
+    dirichlet_extension(v.g, v.op, h->prob.g_D ? v.gD : nullptr, v.U, s, /*shell=*/l >= 2);
     // MIXED: also b / c and its max on a constant-coefficient level, the exact residual's load
     // and scale, kept in the FP64 r vector, which the MIXED iteration does not use
-    launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, h->part, R.s(), mixed ? v.uniform : nullptr, mixed ? v.r : nullptr);
+    launch_fh2(v.g, v.op, v.beta, v.U, v.b, st, pr, s, mixed ? v.uniform : nullptr, mixed ? v.r : nullptr,
+               fh_blocks);
+}
+
+// started: level_start has run for this level (on the side stream, joined before this call)
+void record_level(Rec& R, int l, bool started = false)
+{
+    ecmg_handle* h = R.h;
+    Level& v = h->lv[l];
+    SolveState* st = h->states + l;
+    const ecmg_options& o = h->opt;
+    const bool direct = l < 2;
+    const bool mixed = o.precision == ECMG_MIXED && !direct;
+    CondHandles none{0, 0, 0};
+    if (!started) level_start(h, R.graph, l, R.s(), h->part);
+    else if (mixed && !R.graph) v.cc = constant_coefficient(h, v);
+    const bool ring_on = mixed && v.ring && v.cc;
     if (!direct) {
         const Level& u1 = h->lv[l - 1];
         const Level& u0 = h->lv[l - 2];
@@ -598,18 +622,50 @@ void record_level(Rec& R, int l)
     }
 }
 
+// Levels whose start goes to the side stream, and the blocks of its ||f_h|| pass (two per SM:
+// enough warps for the FP64 pipe, room on every SM for the small levels' blocks).
+constexpr int64_t SIDE_START_NODES = 1 << 22;
+constexpr int SIDE_FH_BLOCKS = 2 * 152;
+
 // The whole solve from level `first`, with a global-timer stamp before the set-up, before each
 // level and at the end (the per-level seconds of ecmg_stats).
 void record_solve(Rec& R, int first)
 {
     ecmg_handle* h = R.h;
+    // After a full set-up the starts of the levels of at least SIDE_START_NODES nodes depend on
+    // nothing the coarser solves write. They are issued before level 2 (after the two direct
+    // levels, whose FP64 kernels they would slow) and, in a graph, on the side stream, joined
+    // level by level below: their FP64-bound ||f_h|| passes, on at most SIDE_FH_BLOCKS blocks,
+    // then run beside the small levels, whose latency-bound steps leave most of the GPU idle.
+    auto side = [&](int l) {
+        const Level& v = h->lv[l];
+        return first == 0 && l >= 2 && (int64_t)(v.g.nx + 1) * (v.g.ny + 1) * (v.g.nz + 1) >= SIDE_START_NODES;
+    };
     if (first == 0) {
         launch_stamp(h->stamps, R.s());
         record_setup(R);
     }
     for (int l = first; l < h->L; ++l) {
+        if (l == 2 && first == 0) {
+            bool any = false;
+            for (int m = 2; m < h->L; ++m) any |= side(m);
+            if (any && R.graph) {
+                ck(cudaEventRecord(h->ev_fork, R.s()));
+                ck(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            }
+            for (int m = 2; m < h->L; ++m) {
+                if (!side(m)) continue;
+                if (R.graph) {
+                    level_start(h, true, m, h->side, h->part_side, SIDE_FH_BLOCKS);
+                    ck(cudaEventRecord(h->ev_level[m], h->side));
+                } else {
+                    level_start(h, false, m, R.s(), h->part);
+                }
+            }
+        }
         launch_stamp(h->stamps + 1 + l, R.s());
-        record_level(R, l);
+        if (side(l) && R.graph) ck(cudaStreamWaitEvent(R.s(), h->ev_level[l], 0));
+        record_level(R, l, side(l));
     }
     launch_stamp(h->stamps + 1 + h->L, R.s());
 }
@@ -1288,7 +1344,8 @@ uint64_t workspace_of(const ecmg_problem* p, const ecmg_options& o)
         maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
         if (o.precision == ECMG_MIXED) maxb = std::max(maxb, std::max(max_tma_blocks(g), res_cc_blocks(g)));
     }
-    return b + (uint64_t)maxb * partials_per_block(o) * 8 + sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
+    return b + (uint64_t)maxb * partials_per_block(o) * 8 + (uint64_t)max_stream_blocks() * 8 +
+           sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
 }
 
 // The slot count of ring_slots: ECMG_RING_AUTO takes 64 when the workspace with them stays
@@ -1358,6 +1415,9 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
     h->L = prob->levels;
     try {
         for (int i = 0; i < 3; ++i) ck(cudaStreamCreateWithFlags(&h->cap[i], cudaStreamNonBlocking));
+        ck(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        ck(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        for (auto& e : h->ev_level) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         const bool mixed = opt->precision == ECMG_MIXED;
         if (mixed) {
             ck(k1_prepare());
@@ -1414,6 +1474,8 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
         h->part.buf = dalloc<double>(h, (int64_t)maxb * partials_per_block(*opt));
         h->part.max_blocks = maxb;
         h->part.fs = dalloc<FixedScale>(h, 1);
+        h->part_side.buf = dalloc<double>(h, max_stream_blocks());  // ||f_h||: one partial per block
+        h->part_side.max_blocks = max_stream_blocks();
         h->states = dalloc<SolveState>(h, MAX_LEVELS);
         h->timers = dalloc<KTimer>(h, MAX_LEVELS);
         {
@@ -1786,6 +1848,10 @@ void ecmg_destroy(ecmg_handle* h)
     if (h->host_stamps) cudaFreeHost(h->host_stamps);
     for (int i = 0; i < 3; ++i)
         if (h->cap[i]) cudaStreamDestroy(h->cap[i]);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (auto e : h->ev_level)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 

@@ -1125,7 +1125,7 @@ void launch_apply32(const Grid& g, const Op& op, const float* beta, const float*
                                                                              nullptr);
 }
 void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
-                Partials pr, cudaStream_t s, const int* uniform, double* bc)
+                Partials pr, cudaStream_t s, const int* uniform, double* bc, int max_blocks)
 {
     FhBox B;
     const int n[3] = {g.nx, g.ny, g.nz};
@@ -1137,7 +1137,8 @@ void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x
         B.nhi[a] = dhi ? n[a] - 2 : n[a];
     }
     (has_robin(op) ? (op.cube ? k_fh2<true, true> : k_fh2<true, false>)
-                   : (op.cube ? k_fh2<false, true> : k_fh2<false, false>))<<<update_blocks(g.total), UPD_TPB, 0, s>>>(
+                   : (op.cube ? k_fh2<false, true> : k_fh2<false, false>))<<<
+        max_blocks > 0 ? std::min(update_blocks(g.total), max_blocks) : update_blocks(g.total), UPD_TPB, 0, s>>>(
         g, op, B, beta, x, b, st, pr.buf, uniform, uniform && constant_coefficient_shape(g, op) ? bc : nullptr);
 }
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv, SolveState* st,

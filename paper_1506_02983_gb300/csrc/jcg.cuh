@@ -53,8 +53,9 @@ void launch_apply32(const Grid& g, const Op& op, const float* beta, const float*
 // be a constant-coefficient one (one beta, every face Dirichlet, cubic elements), also
 // bc = b / c (c = -beta h / 36) on the free nodes and max |bc| into st->bcbits: the exact
 // residual's load and scale.
+// max_blocks: a cap on the grid (0: the usual streaming grid); the pass strides over any grid.
 void launch_fh2(const Grid& g, const Op& op, const double* beta, const double* x, const double* b, SolveState* st,
-                Partials pr, cudaStream_t s, const int* uniform = nullptr, double* bc = nullptr);
+                Partials pr, cudaStream_t s, const int* uniform = nullptr, double* bc = nullptr, int max_blocks = 0);
 // r -= alpha q; z = dinv r; r.z and r.r; last block: convergence / next beta.
 void launch_update64(const Grid& g, double* r, const double* q, const double* dinv,
                      SolveState* st, Partials pr, CondHandles ch, cudaStream_t s);
