@@ -288,7 +288,8 @@ class Solver:
         return ms.value, n.value
 
     def autotune(self, reps=3):
-        """Time the candidate stencil tile shapes on every large MIXED level; keep the fastest."""
+        """Try the candidate stencil tile shapes on every large MIXED level inside whole solves
+        (reps solves per shape; overwrites the levels' vectors); each level keeps its fastest."""
         check(ecmg_autotune(self.handle, int(reps)), "ecmg_autotune")
 
     def close(self):
