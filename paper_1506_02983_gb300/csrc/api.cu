@@ -116,6 +116,10 @@ struct ecmg_handle {
     Partials part_side{nullptr, 0, nullptr};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_level[MAX_LEVELS] = {};
+    // the caller's output array of the running solve (device slot, null: none), and the fork and
+    // join of its copy, which runs beside the finest level's EXP_true
+    double** out_slot = nullptr;
+    cudaEvent_t ev_out_fork = nullptr, ev_out_join = nullptr;
 };
 
 namespace {
@@ -618,7 +622,18 @@ void record_level(Rec& R, int l, bool started = false)
     }
     if (!direct) {
         const Level& u1 = h->lv[l - 1];
-        launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s());
+        if (l == h->L - 1 && R.graph) {
+            // the solution's copy into the caller's array reads only U: beside EXP_true
+            ck(cudaEventRecord(h->ev_out_fork, R.s()));
+            ck(cudaStreamWaitEvent(h->side, h->ev_out_fork, 0));
+            unpack_out(v.g, v.U, h->out_slot, h->side);
+            ck(cudaEventRecord(h->ev_out_join, h->side));
+            launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s());
+            ck(cudaStreamWaitEvent(R.s(), h->ev_out_join, 0));
+        } else {
+            launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s());
+            if (l == h->L - 1) unpack_out(v.g, v.U, h->out_slot, R.s());
+        }
     }
 }
 
@@ -675,6 +690,7 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
     if (u_out && !(u_out = resolve_array(u_out)))
         return fail(ECMG_ERR_INVALID_ARG, "u_out must be device memory of the current device or page-locked host memory");
     try {
+        set_out(h->out_slot, u_out, h->user_stream);  // the finest level writes it (record_level)
         if (h->opt.use_graph) {
             if (!h->exec || h->graph_first != first) {
                 // the FP32 stencil path of each level is fixed in the recording: run the set-up
@@ -712,8 +728,6 @@ ecmg_status run_solve(ecmg_handle* h, int first, double* u_out, ecmg_stats* stat
             Rec R{h, false, 0};
             record_solve(R, first);
         }
-        Level& fin = h->lv[h->L - 1];
-        if (u_out) unpack_nodal(fin.g, fin.U, u_out, h->user_stream);
         ck(cudaGetLastError());
         ck(cudaMemcpyAsync(h->host_states, h->states, sizeof(SolveState) * h->L, cudaMemcpyDeviceToHost,
                            h->user_stream));
@@ -1344,7 +1358,7 @@ uint64_t workspace_of(const ecmg_problem* p, const ecmg_options& o)
         maxb = std::max(maxb, std::max(max_stencil_blocks(g), max_stream_blocks()));
         if (o.precision == ECMG_MIXED) maxb = std::max(maxb, std::max(max_tma_blocks(g), res_cc_blocks(g)));
     }
-    return b + (uint64_t)maxb * partials_per_block(o) * 8 + (uint64_t)max_stream_blocks() * 8 +
+    return b + (uint64_t)maxb * partials_per_block(o) * 8 + (uint64_t)max_stream_blocks() * 8 + 8 +
            sizeof(SolveState) * MAX_LEVELS + 1024 * 2 * 8;
 }
 
@@ -1418,6 +1432,8 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
         ck(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
         ck(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         for (auto& e : h->ev_level) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ck(cudaEventCreateWithFlags(&h->ev_out_fork, cudaEventDisableTiming));
+        ck(cudaEventCreateWithFlags(&h->ev_out_join, cudaEventDisableTiming));
         const bool mixed = opt->precision == ECMG_MIXED;
         if (mixed) {
             ck(k1_prepare());
@@ -1476,6 +1492,7 @@ ecmg_status ecmg_create_with_allocator(const ecmg_problem* prob, const ecmg_opti
         h->part.fs = dalloc<FixedScale>(h, 1);
         h->part_side.buf = dalloc<double>(h, max_stream_blocks());  // ||f_h||: one partial per block
         h->part_side.max_blocks = max_stream_blocks();
+        h->out_slot = dalloc<double*>(h, 1);
         h->states = dalloc<SolveState>(h, MAX_LEVELS);
         h->timers = dalloc<KTimer>(h, MAX_LEVELS);
         {
@@ -1850,6 +1867,8 @@ void ecmg_destroy(ecmg_handle* h)
         if (h->cap[i]) cudaStreamDestroy(h->cap[i]);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_out_fork) cudaEventDestroy(h->ev_out_fork);
+    if (h->ev_out_join) cudaEventDestroy(h->ev_out_join);
     for (auto e : h->ev_level)
         if (e) cudaEventDestroy(e);
     delete h;

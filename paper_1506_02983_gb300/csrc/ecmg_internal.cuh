@@ -192,6 +192,10 @@ void pack_nodal(const Grid& g, const double* dense, double* dst, cudaStream_t s)
 void pack_dirichlet(const Grid& g, const Op& op, const double* dense, double* dst, cudaStream_t s);
 void pack_elements(const Grid& g, const double* dense, double* dst, cudaStream_t s);
 void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s);
+// unpack_nodal into the array whose address *slot holds on the device (null: no copy); set_out
+// stores that address (a graph records the copy once and writes a new array at each launch).
+void set_out(double** slot, double* out, cudaStream_t s);
+void unpack_out(const Grid& g, const double* src, double* const* slot, cudaStream_t s);
 void coarsen_beta(const Grid& gc, const double* bf, const Grid& gf, double* bc, cudaStream_t s);
 // The finest beta from the caller's dense array in one pass: packed (beta), in FP32 (beta32, the
 // elements only), the uniform flag (as beta32_uniform) and the beta of the level below (bc, as

@@ -337,6 +337,38 @@ void pack_dirichlet(const Grid& g, const Op& op, const double* dense, double* ds
 {
     k_pack_dirichlet<<<grid3z(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, op, dense, dst);
 }
+// The caller's output array as a device-side pointer (null: nothing to write), so that a recorded
+// graph can write a different array at every launch: k_set_out stores it, k_unpack_out copies.
+__global__ void k_set_out(double** slot, double* out)
+{
+    COUNT_LAUNCH();
+    *slot = out;
+}
+__global__ void k_unpack_out(Grid g, const double* __restrict__ src, double* const* slot)
+{
+    COUNT_LAUNCH();
+    double* dst = *slot;
+    if (!dst) return;
+    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const int k0 = blockIdx.z * ZT, k1 = min(k0 + ZT, g.nz + 1);
+    const int64_t plane = (int64_t)(g.nx + 1) * (g.ny + 1);
+    const int64_t t0 = i + (int64_t)(g.nx + 1) * j;
+    for (int k = k0; k < k1; k += 4) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k + u < k1) v[u] = src[g.off(i, j, k + u)];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k + u < k1) dst[t0 + plane * (k + u)] = v[u];
+    }
+}
+void set_out(double** slot, double* out, cudaStream_t s) { k_set_out<<<1, 1, 0, s>>>(slot, out); }
+void unpack_out(const Grid& g, const double* src, double* const* slot, cudaStream_t s)
+{
+    k_unpack_out<<<grid3z(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, src, slot);
+}
 void unpack_nodal(const Grid& g, const double* src, double* dense, cudaStream_t s)
 {
     k_copy_nodal<true><<<grid3z(g.nx, g.ny, g.nz), dim3(TX, TY), 0, s>>>(g, src, dense);

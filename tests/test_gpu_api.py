@@ -73,6 +73,33 @@ def test_workspace_from_the_torch_caching_allocator(E, precision):
     assert torch.cuda.memory_allocated() == before
 
 
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_output_array_changes_between_solves(E, use_graph):
+    """The copy of the solution into the caller's array is part of the recorded solve and reads
+    the array's address on the device at each launch: one graph writes a new array each time,
+    and a solve without an output array writes none."""
+    import torch
+    p = inputs.exp_cube(levels=4, rtol=1e-10)
+    s = E.solver_from_problem(p, precision=1, use_graph=use_graph)
+    a = torch.full(s.level_shape(), -1.0, dtype=torch.float64, device="cuda")
+    b = torch.full(s.level_shape(), -2.0, dtype=torch.float64, device="cuda")
+    s.solve(a)
+    want = a.clone()
+    assert not torch.equal(want, torch.full_like(want, -1.0))
+    s.solve(b)
+    assert torch.equal(b, want)
+    a.fill_(-3.0)
+    b.fill_(-4.0)
+    s.solve()
+    assert torch.equal(a, torch.full_like(a, -3.0)) and torch.equal(b, torch.full_like(b, -4.0))
+    s.solve(a)
+    assert torch.equal(a, want)
+    # the finest level's U, in the dense layout, is what the array receives
+    U = s.get(E.ECMG_VEC_U, -1)
+    assert torch.equal(U.reshape(-1), want.reshape(-1))
+    s.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_pinned_host_inputs_and_output(E, precision):
     """Inputs in page-locked host memory are read, and the solution written, by the kernels
