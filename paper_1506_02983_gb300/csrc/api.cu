@@ -628,10 +628,10 @@ void record_level(Rec& R, int l, bool started = false)
             ck(cudaStreamWaitEvent(h->side, h->ev_out_fork, 0));
             unpack_out(v.g, v.U, h->out_slot, h->side);
             ck(cudaEventRecord(h->ev_out_join, h->side));
-            launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s());
+            launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s(), h->lv[l - 1].q);
             ck(cudaStreamWaitEvent(R.s(), h->ev_out_join, 0));
         } else {
-            launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s());
+            launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, R.s(), h->lv[l - 1].q);
             if (l == h->L - 1) unpack_out(v.g, v.U, h->out_slot, R.s());
         }
     }
@@ -1092,7 +1092,7 @@ double time_launches(ecmg_handle* h, int l, int which, int reps)
             }
             case 7: {
                 const Level& u1 = h->lv[l - 1];
-                launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, s);
+                launch_exp_true(v.g, v.U, u1.g, u1.U, v.Ut, s, h->lv[l - 1].q);
                 break;
             }
             case 8:  // as a MIXED solve runs it: with b / c on a constant-coefficient level

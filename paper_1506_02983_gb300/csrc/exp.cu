@@ -107,7 +107,36 @@ __global__ void k_norms(Grid g, const double* __restrict__ a, const double* __re
 }
 
 inline int blocks_for(int64_t n) { return (int)((n + TPB - 1) / TPB); }
-inline int64_t nodes(const Grid& g) { return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
+__host__ __device__ inline int64_t nodes(const Grid& g) { return (int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
+
+// EXP_true in two passes: d = U^l - U^{l-1} at every level-(l-1) node into D (grid gc), one
+// subtraction per node; then one thread per level-(l-1) element from D.
+__global__ void __launch_bounds__(TPB) k_exp_true_d(Grid g, const double* __restrict__ U1, Grid gc,
+                                                    const double* __restrict__ U0, double* __restrict__ D)
+{
+    COUNT_LAUNCH();
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nodes(gc)) return;
+    const int i = (int)(t % (gc.nx + 1));
+    const int64_t r_ = t / (gc.nx + 1);
+    const int j = (int)(r_ % (gc.ny + 1));
+    const int k = (int)(r_ / (gc.ny + 1));
+    const int64_t o = gc.off(i, j, k);
+    D[o] = U1[g.off(2 * i, 2 * j, 2 * k)] - U0[o];
+}
+__global__ void __launch_bounds__(128) k_exp_true_from_d(Grid g, const double* __restrict__ U1, Grid gc,
+                                                         const double* __restrict__ D, double* __restrict__ Ut)
+{
+    COUNT_LAUNCH();
+    const int64_t ne = (int64_t)gc.nx * gc.ny * gc.nz;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ne) return;
+    const int ex = (int)(t % gc.nx);
+    const int64_t r_ = t / gc.nx;
+    const int ey = (int)(r_ % gc.ny);
+    const int ez = (int)(r_ / gc.ny);
+    exp_true_element_d(g, U1, gc, D, Ut, ex, ey, ez);
+}
 
 }  // namespace
 
@@ -123,9 +152,14 @@ void launch_exp_finite(int variant, const Grid& g, const Op& op, const Grid& g1,
 }
 
 void launch_exp_true(const Grid& g, const double* U1, const Grid& gc, const double* U0, double* Ut,
-                     cudaStream_t s)
+                     cudaStream_t s, double* D)
 {
     const int64_t ne = (int64_t)gc.nx * gc.ny * gc.nz;
+    if (D) {
+        k_exp_true_d<<<blocks_for(nodes(gc)), TPB, 0, s>>>(g, U1, gc, U0, D);
+        k_exp_true_from_d<<<(int)((ne + 127) / 128), 128, 0, s>>>(g, U1, gc, D, Ut);
+        return;
+    }
     k_exp_true<<<(int)((ne + 127) / 128), 128, 0, s>>>(g, U1, gc, U0, Ut);
 }
 

@@ -181,18 +181,10 @@ __device__ __forceinline__ void exp_finite_element(const Grid& g, const Op& op, 
 // factorisation (x, then y, then z) and each node takes one FMA with the weight 1/(3 2^m):
 // 28 FP64 operations for the 8 owned nodes instead of 62 with averaged values. A thread
 // writes the nodes (2 ex + a, ...), a = 0, 1, plus a = 2 on the last element of an axis.
-__device__ __forceinline__ void exp_true_element(const Grid& g, const double* __restrict__ U1, const Grid& gc,
-                                                 const double* __restrict__ U0, double* __restrict__ Ut, int ex,
-                                                 int ey, int ez)
+__device__ __forceinline__ void exp_true_from_d(const Grid& g, const double* __restrict__ U1, const Grid& gc,
+                                                const double (&d)[2][2][2], double* __restrict__ Ut, int ex, int ey,
+                                                int ez)
 {
-    double d[2][2][2];  // [c][b][a]
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-                d[c][b][a] = U1[g.off(2 * (ex + a), 2 * (ey + b), 2 * (ez + c))] - U0[gc.off(ex + a, ey + b, ez + c)];
     const double w[4] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 12.0, 1.0 / 24.0};  // 1 / (3 2^m)
     const int na = (ex == gc.nx - 1) ? 3 : 2, nb = (ey == gc.ny - 1) ? 3 : 2, nc = (ez == gc.nz - 1) ? 3 : 2;
     // level-l node offset a (0, 1 = midpoint, 2) from the corner pair (v0, v1) along one axis
@@ -218,6 +210,38 @@ __device__ __forceinline__ void exp_true_element(const Grid& g, const double* __
             }
         }
     }
+}
+
+__device__ __forceinline__ void exp_true_element(const Grid& g, const double* __restrict__ U1, const Grid& gc,
+                                                 const double* __restrict__ U0, double* __restrict__ Ut, int ex,
+                                                 int ey, int ez)
+{
+    double d[2][2][2];  // [c][b][a]
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                d[c][b][a] = U1[g.off(2 * (ex + a), 2 * (ey + b), 2 * (ez + c))] - U0[gc.off(ex + a, ey + b, ez + c)];
+    exp_true_from_d(g, U1, gc, d, Ut, ex, ey, ez);
+}
+
+// The same with d already formed at the level-(l-1) nodes (D, on grid gc): a corner difference is
+// then one load instead of a subtraction that the eight elements sharing the node each repeat
+// (7 of the element's 28 FP64 operations); same values, so the same Ut bit for bit.
+__device__ __forceinline__ void exp_true_element_d(const Grid& g, const double* __restrict__ U1, const Grid& gc,
+                                                   const double* __restrict__ D, double* __restrict__ Ut, int ex,
+                                                   int ey, int ez)
+{
+    double d[2][2][2];  // [c][b][a]
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) d[c][b][a] = D[gc.off(ex + a, ey + b, ez + c)];
+    exp_true_from_d(g, U1, gc, d, Ut, ex, ey, ez);
 }
 
 }  // namespace ecmg
