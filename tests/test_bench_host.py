@@ -99,3 +99,17 @@ def test_cpu_baseline_legs(monkeypatch):
     assert one["finest"] == "32^3" and omp["finest"] == "64^3"
     for leg in (one, omp):
         assert leg["seconds_assembly"] > 0 and leg["seconds_solve"] > 0
+
+
+def test_k1_traffic_record_matches_the_byte_model():
+    """The ncu figures the bench line reports as K1's `traffic` (profiles/k_pq_float_traffic.json)
+    belong to the kernel the bench times: the ring form at the recorded size moves 16 bytes per
+    node off the Dirichlet faces (r and p_old in, p and q out), the record's sum is its read plus
+    its write, and the measured traffic stays within a few percent of those bytes."""
+    import json
+    d = json.load(open(os.path.join(ROOT, "profiles", "k_pq_float_traffic.json")))
+    n = d["n"]
+    assert d["algorithmic_bytes_per_launch"] == 16 * (n - 1) ** 3
+    assert abs(d["dram_bytes_per_launch"] - (d["dram_bytes_read"] + d["dram_bytes_write"])) < 1.0
+    assert 1.0 <= d["dram_bytes_per_launch"] / d["algorithmic_bytes_per_launch"] < 1.05
+    assert os.path.exists(os.path.join(ROOT, "profiles", d["source"]))
