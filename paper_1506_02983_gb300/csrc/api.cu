@@ -110,8 +110,9 @@ struct ecmg_handle {
     double* host_norms = nullptr;       // pinned
     int graph_first = -1;               // first level of the recorded graph
     Batch* batch = nullptr;             // batched handle (ecmg_create_batched), else null
-    // the starts of levels >= 2 (state, Dirichlet shell, ||f_h||) on a second stream while the
-    // coarser levels solve: the stream, its partials, one event per level it completes
+    // the starts of the large levels (state, Dirichlet shell, ||f_h||) on a second stream while
+    // the small levels solve (record_solve): the stream, its partials, one event per level it
+    // completes; the same stream takes the copy of the solution beside the last EXP_true
     cudaStream_t side = nullptr;
     Partials part_side{nullptr, 0, nullptr};
     cudaEvent_t ev_fork = nullptr;
